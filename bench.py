@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled Yee-FDTD + kinetic step on GB300.
+
+One "step" is one full time step of the hot path (H stencil, kinetic delta-f
+update + J moment + Ampere source term, E stencil with CPML and the soft
+source) over the whole workload.  Default workload: 2-D TMz 4096 x 4096,
+dx = lam0/20, 10-cell CPML, seeded Gaussian-density plasma cylinder of radius
+512 cells (823 k plasma cells), 32 x 32 Cartesian velocity grid per cell
+(1024 nodes, FP32 delta f = 3.4 GB), i.e. 8.4e8 phase-space nodes per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+Prints one JSON line (rank 0).  N > 1 runs N independent replicas, one per
+rank (weak scaling; no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s + phase-space updates/s at 1 GB300, % HBM roofline; closure vs kinetic"
+UNIT = "Gcell-updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def cells_of(spec) -> int:
+    g = spec["grid"]
+    return int(g["nz"]) if g["ndim"] == 1 else int(g["nx"]) * int(g["ny"]) * (int(g["nz"]) if g["ndim"] == 3 else 1)
+
+
+def make_spec(name: str):
+    from fdtd_inputs import WORKLOADS
+    return WORKLOADS[name]()
+
+
+def sample_spec(name: str):
+    """The bounded CPU sample of a workload: the same recipe with every length
+    scaled down (same plasma fraction, velocity grid and precision choice)."""
+    from fdtd_inputs import spec_1d_slab, spec_2d_cylinder, spec_3d_slab
+    if name.startswith("2d_tmz_4096"):
+        return spec_2d_cylinder(n=512, R=64), "2-D TMz 512x512, cylinder R=64 (all lengths / 8), 32x32 nodes"
+    if name.startswith("3d_512"):
+        return (spec_3d_slab(n=64, cpml=8, slab=(24, 40), src_k=12),
+                "3-D 64^3, slab z in [24,40) (all lengths / 8), Nv=32")
+    return spec_1d_slab(), "1-D Nz=2000 slab (the full workload)"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          f"--id={self.gpu_id}", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(dev) -> str:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+# ------------------------------------------------------------- roofline data
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kinetic_src_sha() -> str:
+    h = hashlib.sha1()
+    for f in ("kinetic.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2211_05647_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = kinetic_src_sha()
+    for ln in open(path):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
+        if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src_sha") == sha:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_throughput(name: str, steps: int, warmup: int, budget_s: float | None):
+    """Time the FP64 oracle on a bounded sample of the workload.  Returns
+    (Gcell-updates/s, phase-space updates/s, steps timed, sample text)."""
+    from oracle import oracle as O
+    from tests.adapters import oracle_sim
+    spec, text = sample_spec(name)
+    sim = oracle_sim(O, spec)
+    sim.step(warmup)
+    n = 0
+    t0 = time.perf_counter()
+    while n < steps:
+        sim.step(1)
+        n += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cells = cells_of(spec)
+    return cells * n / dt / 1e9, sim.nslots * sim.nnode * n / dt, n, text, cells, sim.nslots * sim.nnode
+
+
+# --------------------------------------------------------------------- main
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        g, ps, n, text, cells, nodes = oracle_throughput(args.workload, args.steps, args.warmup, None)
+        line = {"impl": "reference", "metric": METRIC, "value": g, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": n, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "sample": text},
+                "phase_space_updates_per_s": ps,
+                "cpu_baseline": {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{text}; {n} oracle steps, single thread"},
+                "e2e": {"value": g, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2211_05647_gb300 import Solver
+
+    spec = make_spec(args.workload)
+    s = Solver.from_spec(spec, device=local)
+    ns, nn = s.plasma_shape()
+    cells = cells_of(spec)
+    st = s.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    # warm-up (captures the step graphs)
+    s.step(args.warmup)
+    barrier()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(args.steps)
+    e1.record(st)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * cells * args.steps / (ms / 1e3) / 1e9
+    ps_rate = world * ns * nn * args.steps / (ms / 1e3)
+
+    # per-kernel launch durations (eager launches with CUDA events on the solver's stream)
+    kt = s.time_kernels(min(args.steps, 200))
+
+    # end-to-end through the public API: plasma density and initial fields from
+    # pinned host memory, K steps, final fields and J back to pinned host memory
+    s.reset()
+    pol = {1: "ex", 2: "ez", 3: "ex"}[spec["grid"]["ndim"]]
+    dens_h = torch.from_numpy(spec["plasma"]["density"]).pin_memory()
+    outs = {1: ["ex", "hy", "j"], 2: ["ez", "hx", "hy", "j"], 3: ["ex", "ey", "ez", "hx", "hy", "hz", "j"]}[
+        spec["grid"]["ndim"]]
+    init = {n: torch.zeros(s.quantity_bytes(n) // (8 if s.precision == "f64" else 4),
+                           dtype=torch.float64 if s.precision == "f64" else torch.float32).pin_memory()
+            for n in outs if n != "j"}
+    host_out = {n: torch.empty_like(init[n]) if n != "j" else
+                torch.empty(ns, dtype=torch.float64 if s.precision == "f64" else torch.float32).pin_memory()
+                for n in outs}
+    barrier()
+    t_e2e0 = time.perf_counter()
+    p = dict(spec["plasma"])
+    p["density"] = dens_h.numpy()
+    s.set_plasma(**p)
+    qid = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6}
+    for n, v in init.items():   # host -> device through the C ABI
+        assert s.lib.fdtd_plasma_write_fields(s.h, qid[n], v.data_ptr(), v.numel() * v.element_size(), 0) == 0
+    s.step(args.steps)
+    h2d = dens_h.numel() * 8 + sum(v.numel() * v.element_size() for v in init.values())
+    d2h = 0
+    for n in outs:
+        o = host_out[n]
+        rc = s.lib.fdtd_plasma_read_fields(s.h, qid[n], o.data_ptr(), o.numel() * o.element_size(), 0)
+        assert rc == 0, rc
+        d2h += o.numel() * o.element_size()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t_e2e0
+    te = torch.tensor([t_e2e], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * cells * args.steps / float(te.item()) / 1e9
+
+    if rank != 0:
+        dist.destroy_process_group() if world > 1 else None
+        return 0
+
+    # roofline of the dominant kernel (the kinetic delta-f stream)
+    fbytes = {"f32": 4, "bf16": 2, "f64": 8}[spec["plasma"]["f_dtype"]]
+    alg_bytes = 2 * fbytes * ns * nn            # read + write delta f once per node
+    achieved = alg_bytes / (kt["kinetic"] / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    roof = {"bound": "hbm", "kernel": "k_kinetic", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": ncu_traffic("k_kinetic", args.workload),
+            "alg_bytes_per_launch": alg_bytes, "launch_ms": kt["kinetic"],
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
+    fb = 8 if s.precision == "f64" else 4
+    ncomp = {1: 2, 2: 3, 3: 6}[spec["grid"]["ndim"]]
+    step_alg = 2 * fb * ncomp * cells + alg_bytes
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if s.precision == "f32" else "f64",
+            "data": "synthetic (seeded density field, Gaussian-modulated source)",
+            "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"], spec["grid"]["nz"]],
+                       "ndim": spec["grid"]["ndim"], "plasma_cells": ns, "nodes_per_cell": nn,
+                       "f_dtype": spec["plasma"]["f_dtype"], "cpml_cells": spec["grid"]["cpml_cells"],
+                       "l2": "inputs larger than L2 (delta f %.2f GB per GPU)" % (ns * nn * fbytes / 1e9),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "phase_space_updates_per_s": ps_rate,
+            "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
+            "kernel_ms": kt,
+            "roofline": roof,
+            "gpu_launches": args.steps * 3 + math.ceil(args.steps / 32) if ns else args.steps * 2 + math.ceil(args.steps / 32),
+            "clocks": clk,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps}}
+    if world == 1 and not args.no_cpu_baseline:
+        g, psr, n, text, _, _ = oracle_throughput(args.workload, 10 ** 6, 2, budget_s=15.0)
+        line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{text}; {n} oracle steps in ~15 s, single thread",
+                                "phase_space_updates_per_s": psr}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

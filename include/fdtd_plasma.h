@@ -1,0 +1,213 @@
+/*
+ * fdtd_plasma.h -- C ABI of the GB300 (sm_103a) coupled Yee-FDTD + kinetic
+ * electron solver of arXiv 2211.05647.
+ *
+ * One time step n -> n+1 advances, in this order:
+ *   H^{n+1/2}  Yee curl of E^n + CPML psi_h           (Sec. 2, Eq. 1, 7-12)
+ *   df^{n+1/2} Crank-Nicolson f_1 update per plasma cell and velocity node,
+ *              driven by E^n                           (Sec. 5.2, Eq. 22 and the f_1x update)
+ *   J^{n+1/2}  = -e sum_j w_j df_j^{n+1/2}             (Eq. 24 and the Jx sum of Sec. 5.2)
+ *   E^{n+1}    Yee curl of H^{n+1/2} + CPML psi_e - dt/eps0 J^{n+1/2}   (Eq. 2-6)
+ *   soft source g(t^{n+1}) added at its node(s); first-order Mur ends in 1-D.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns an fdtd_status; nothing throws across the ABI.
+ *   - A handle is not thread-safe.  All device work is issued on the stream
+ *     given at create time and is asynchronous unless stated.
+ *   - The caller owns every pointer it passes; inputs are copied before the
+ *     call returns, outputs are written before it returns (for device
+ *     destinations: stream-ordered, see fdtd_plasma_read_fields).
+ *   - Units are SI.  Fields are stored x-fastest, without padding:
+ *       1-D: Ex on nodes k = 0..nz (nz+1 values), Hy on k+1/2 (nz values).
+ *       2-D TMz: Ez(i,j), Hx(i,j+1/2), Hy(i+1/2,j): nx*ny values at j*nx+i;
+ *                Ez on i==0 or j==0 is a PEC node, nodes i==nx / j==ny are PEC ghosts.
+ *       3-D: Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2) Hx(i,j+1/2,k+1/2)
+ *            Hy(i+1/2,j,k+1/2) Hz(i+1/2,j+1/2,k): nx*ny*nz values at (k*ny+j)*nx+i,
+ *            tangential E on the low planes held at 0, high planes are ghosts.
+ *   - The kinetic current sits on the polarisation component: Ex (1-D, 3-D)
+ *     or Ez (2-D TMz).  Plasma cells are polarisation nodes with density > 0
+ *     whose E the curl updates; they are numbered ("slots") in increasing
+ *     linear index.
+ */
+#ifndef FDTD_PLASMA_H
+#define FDTD_PLASMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fdtd_plasma *fdtd_plasma_t;
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_ERR_INVAL = -1,     /* bad argument, size or combination */
+    FDTD_ERR_NOMEM = -2,     /* device allocation failed */
+    FDTD_ERR_CUDA = -3,      /* a CUDA call failed; see fdtd_plasma_last_error */
+    FDTD_ERR_UNSTABLE = -4,  /* Courant / plasma stability bound violated */
+    FDTD_ERR_NONFINITE = -5, /* non-finite input or state */
+    FDTD_ERR_TIMEOUT = -6,   /* a bounded device wait gave up */
+    FDTD_ERR_STATE = -7      /* call not allowed in the handle's current state */
+} fdtd_status;
+
+enum { FDTD_F32 = 0, FDTD_F64 = 1 };                      /* field / accumulation precision */
+enum { FDTD_DF_F32 = 0, FDTD_DF_BF16 = 1, FDTD_DF_F64 = 2 }; /* storage of delta f */
+enum { FDTD_VGRID_SIGNED1D = 0, FDTD_VGRID_CART2D = 1, FDTD_VGRID_SPEED3D = 2 };
+enum { FDTD_NU_NSV = 0, FDTD_NU_CONST = 1 };
+enum { FDTD_SRC_NONE = 0, FDTD_SRC_GAUSS_SINE = 1, FDTD_SRC_GAUSS = 2 };
+enum { FDTD_LOC_POINT = 0, FDTD_LOC_SHEET = 1 };
+enum {                                                      /* fdtd_plasma_read_fields "which" */
+    FDTD_EX = 0, FDTD_EY, FDTD_EZ, FDTD_HX, FDTD_HY, FDTD_HZ,
+    FDTD_J = 6,  /* J^{n+1/2} per plasma slot, field precision */
+    FDTD_DF = 7  /* delta f [slot][node], delta-f storage type, rows packed to nnode */
+};
+
+/* Grid and boundary description (Sec. 2; CPML of Eq. 7-12). */
+typedef struct {
+    int32_t ndim;              /* 1, 2 (TMz) or 3 */
+    int32_t precision;         /* FDTD_F32 or FDTD_F64 */
+    int64_t nx, ny, nz;        /* cells per axis; 1-D uses nz; unused axes ignored */
+    double dx;                 /* cell size on every axis (m) */
+    double courant;            /* S: dt = S dx / c; must satisfy S^2 ndim < 1 */
+    int32_t cpml_cells;        /* 2-D/3-D CPML thickness on every face (0 = PEC walls) */
+    int32_t mur;               /* 1-D: 1 = first-order Mur at both ends, 0 = PEC ends */
+    double cpml_order;         /* n_cpml of Eq. 9-12 */
+    double cpml_sigma_factor;  /* sigma_max = factor (order+1)/(150 pi dx), Eq. 11 */
+    double cpml_kappa_max;
+    double cpml_alpha_min, cpml_alpha_max;   /* S/m, Eq. 12 */
+} fdtd_grid_desc;
+
+/* Runtime plumbing: the stream every call issues on, and an optional device
+ * allocator (e.g. a framework's caching allocator).  alloc must return
+ * 256-byte aligned device memory or NULL; both callbacks may be NULL, in
+ * which case cudaMalloc / cudaFree are used. */
+typedef struct {
+    void *stream;                                   /* cudaStream_t, NULL = legacy default stream */
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} fdtd_runtime_desc;
+
+/* Soft source, added to the polarisation component after the E update at
+ * t^{n+1} (Table 3 pulse):  GAUSS_SINE: amp sin(2 pi fc (t-t0)) exp(-((t-t0)/tau)^2)
+ *                            GAUSS:      amp exp(-((t-t0)/tau)^2)
+ * POINT: node (i,j,k) (1-D uses k; 2-D uses i,j).  SHEET (3-D): every node
+ * (i,j,k) with i0<=i<i1, j0<=j<j1 on plane k. */
+typedef struct {
+    int32_t kind;
+    int32_t location;
+    double amp, fc, tau, t0;
+    int64_t i, j, k;
+    int64_t i0, i1, j0, j1;
+} fdtd_source_desc;
+
+/* Kinetic plasma (Sec. 5.2).  density: one double per polarisation node
+ * (the field's own length), host or device, copied.  F0 is a Maxwellian of
+ * temperature te_ev on a velocity grid of nv (x nv_perp) midpoint nodes over
+ * [-vmax_vth v_th, +vmax_vth v_th] (speed grid: [0, vmax_vth v_th]).
+ * Collisions (Eq. 23): NSV: nu_j = N s |v_j| with N s set so that the grid's
+ * F0-weighted mean of nu is nu0; CONST: nu_j = nu0.
+ * f_dtype: FDTD_DF_F32, FDTD_DF_BF16 (FP32 arithmetic, stochastic rounding on
+ * store, keyed by seed) or FDTD_DF_F64 (only with FDTD_F64 precision).
+ * nonlinear: 1 adds the flux-form advection of delta f in v_par (signed and
+ * Cartesian grids only). */
+typedef struct {
+    const double *density;
+    int32_t density_on_device;
+    int32_t vgrid;
+    int32_t nv, nv_perp;
+    double te_ev, vmax_vth, nu0;
+    int32_t nu_model;
+    int32_t f_dtype;
+    int32_t nonlinear;
+    int32_t reserved;
+    uint64_t seed;
+} fdtd_plasma_desc;
+
+/* FP64 diagnostics (computed on the device with FP64 accumulators). */
+typedef struct {
+    double energy;          /* sum eps0/2 E^2 dV + mu0/2 H . H' dV, H' = H advanced by the vacuum curl
+                               of the current E: the Yee invariant of a lossless PEC cavity */
+    double energy_plain;    /* sum eps0/2 E^2 dV + mu0/2 H^2 dV */
+    double number;          /* sum over plasma cells and nodes of df_j dV_j */
+    double number_max_cell; /* max over cells of |sum_j df_j dV_j| */
+    double number_abs;      /* sum |df_j| dV_j */
+    int64_t finite;         /* 1 if every field and df value is finite */
+    int64_t step;           /* steps done */
+} fdtd_diag;
+
+/* Create a solver.  Validates the grid (sizes >= 2, dx > 0, CPML thinner
+ * than a third of each axis) and the Courant number (FDTD_ERR_UNSTABLE if
+ * S^2 ndim >= 1).  Fields start at zero, there is no plasma and no source.
+ * rt may be NULL.  On error *out is NULL. */
+int fdtd_plasma_create(const fdtd_grid_desc *grid, const fdtd_runtime_desc *rt, fdtd_plasma_t *out);
+
+/* Set (or replace) the soft source.  Validates the node range.
+ * Allowed at any time; takes effect from the next step. */
+int fdtd_plasma_set_source(fdtd_plasma_t h, const fdtd_source_desc *src);
+
+/* Set the plasma: compacts plasma cells, builds the velocity tables and
+ * zeroes delta f and J.  FDTD_ERR_STATE after the first step (call
+ * fdtd_plasma_reset first); FDTD_ERR_NONFINITE for a non-finite or negative
+ * density; FDTD_ERR_UNSTABLE if (w_p,max dt/2)^2 + S^2 ndim >= 1. */
+int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *pl);
+
+/* Advance nsteps >= 0 steps, asynchronously on the handle's stream.  The
+ * first call after a configuration change captures the step sequence into
+ * CUDA graphs; later calls replay them. */
+int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps);
+
+/* Advance nsteps >= 1 steps like fdtd_plasma_step, but launch each kernel
+ * directly (no graph) with CUDA events around each of the three kernels of a
+ * step, synchronising after every step.  ms_out[0..3] receive the average
+ * duration per launch (ms) of the H-stencil kernel, the kinetic (delta f + J)
+ * kernel, the E-stencil kernel (with the Mur ends in 1-D) and of a whole
+ * step.  Meant for measurement; state advances exactly as with step. */
+int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out);
+
+/* Zero every field, psi, delta f and J and the step counter (keeps the
+ * configuration). */
+int fdtd_plasma_reset(fdtd_plasma_t h);
+
+/* Copy one quantity out.  bytes must equal its exact size (see
+ * fdtd_plasma_quantity_bytes).  dst_is_device = 0: host memory, the call
+ * synchronises the handle's stream before returning.  dst_is_device = 1:
+ * device memory, stream-ordered on the handle's stream. */
+int fdtd_plasma_read_fields(fdtd_plasma_t h, int which, void *dst, size_t bytes, int dst_is_device);
+
+/* Overwrite one quantity (same layout as read_fields; FDTD_J is not
+ * writable).  Used to set initial conditions. */
+int fdtd_plasma_write_fields(fdtd_plasma_t h, int which, const void *src, size_t bytes, int src_is_device);
+
+/* Byte size of a quantity for read/write_fields (0 if absent). */
+size_t fdtd_plasma_quantity_bytes(fdtd_plasma_t h, int which);
+
+/* Number of plasma slots and velocity nodes per slot. */
+int fdtd_plasma_plasma_shape(fdtd_plasma_t h, int64_t *nslots, int64_t *nnode);
+
+/* Time step dt (s) and steps done. */
+int fdtd_plasma_info(fdtd_plasma_t h, double *dt, int64_t *steps_done);
+
+/* Compute FP64 diagnostics of the current state (synchronises the stream). */
+int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out);
+
+/* Checkpoint: the full state (fields, psi, delta f, J, step counter) in an
+ * opaque byte blob of fdtd_plasma_state_bytes() bytes, host or device.
+ * load_state requires a handle with the same configuration. */
+size_t fdtd_plasma_state_bytes(fdtd_plasma_t h);
+int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int buf_is_device);
+int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int buf_is_device);
+
+/* Last error message of the handle (or of the last failed create when h is
+ * NULL).  Valid until the next call on the same handle. */
+const char *fdtd_plasma_last_error(fdtd_plasma_t h);
+
+/* Release everything the handle owns.  NULL-safe.  Synchronises the stream. */
+void fdtd_plasma_destroy(fdtd_plasma_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_PLASMA_H */

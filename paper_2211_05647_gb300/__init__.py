@@ -1,0 +1,8 @@
+"""GB300-native coupled Yee-FDTD + kinetic electron solver (arXiv 2211.05647).
+
+The computation lives in the CUDA library built from ``csrc/`` (C ABI:
+``include/fdtd_plasma.h``); this package is its ctypes binding.
+"""
+from .fdtd_plasma import (Solver, FdtdError, load_library, LIB_PATH, SIGNATURES, QUANTITY)  # noqa: F401
+
+__all__ = ["Solver", "FdtdError", "load_library", "LIB_PATH", "SIGNATURES", "QUANTITY"]

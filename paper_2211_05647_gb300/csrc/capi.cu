@@ -1,0 +1,827 @@
+// capi.cu -- the C ABI of include/fdtd_plasma.h: handle lifetime, parameter
+// derivation (time step, CPML profiles of Eq. 9-12, velocity tables of the
+// Sec. 5.2 update), plasma-cell compaction, CUDA-graph capture of the step
+// sequence, stream-ordered I/O, FP64 diagnostics and checkpoints.
+//
+// Every coefficient is derived here from the paper's formulas, in FP64 on the
+// host, then rounded once to the field precision.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace fp;
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kChunk = 32;            // steps per replay of the chunk graph
+constexpr uint64_t kStateMagic = 0x4644544450534d31ull;
+
+thread_local std::string g_create_error;
+
+int fail(fdtd_plasma *h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(fdtd_plasma *h, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return code;
+}
+
+int cuda_fail(fdtd_plasma *h, cudaError_t e, const char *what)
+{
+    return fail(h, FDTD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                                   \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);      \
+    } while (0)
+
+void *dalloc(fdtd_plasma *h, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (h->rt.alloc) {
+        p = h->rt.alloc(bytes, h->rt.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(fdtd_plasma *h, void *p)
+{
+    if (!p) return;
+    if (h->rt.free) h->rt.free(p, h->rt.alloc_ctx);
+    else cudaFree(p);
+}
+
+// ------------------------------------------------------------- CPML tables
+
+// One axis of n cells, L-cell layers at both ends, at E (x = i dx) or H
+// (x = (i+1/2) dx) positions: sigma = smax (rho/delta)^m, kappa = 1 +
+// (kmax-1)(rho/delta)^m, alpha = amin + (amax-amin)(1-rho/delta) (Eq. 12),
+// smax = factor (m+1)/(150 pi dx) (Eq. 11), b = exp(-(sigma/kappa+alpha)dt/eps0)
+// (Eq. 9), a = sigma (b-1)/(dx (sigma kappa + alpha kappa^2)) (Eq. 10).
+void cpml_axis(const fdtd_grid_desc &g, double dt, int64_t n, bool at_h, std::vector<double> &b,
+               std::vector<double> &a, std::vector<double> &ik)
+{
+    const int64_t L = g.cpml_cells;
+    const double delta = (double)L * g.dx;
+    const double smax = g.cpml_sigma_factor * (g.cpml_order + 1.0) / (150.0 * kPi * g.dx);
+    b.assign(n, 0.0);
+    a.assign(n, 0.0);
+    ik.assign(n, 1.0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double x = ((double)i + (at_h ? 0.5 : 0.0)) * g.dx;
+        double rho;
+        if (x < delta) rho = delta - x;
+        else if (x > (double)(n - L) * g.dx) rho = x - (double)(n - L) * g.dx;
+        else continue;
+        const double r = rho / delta;
+        const double rm = std::pow(r, g.cpml_order);
+        const double sig = smax * rm;
+        const double kap = 1.0 + (g.cpml_kappa_max - 1.0) * rm;
+        const double alp = g.cpml_alpha_min + (g.cpml_alpha_max - g.cpml_alpha_min) * (1.0 - r);
+        const double bb = std::exp(-(sig / kap + alp) * dt / kEps0);
+        const double den = g.dx * (sig * kap + alp * kap * kap);
+        b[i] = bb;
+        a[i] = (sig > 0.0 && den > 0.0) ? sig * (bb - 1.0) / den : 0.0;
+        ik[i] = 1.0 / kap;
+    }
+}
+
+// --------------------------------------------------------- velocity tables
+
+struct VTab {
+    std::vector<double> v, w, f0, f0p, nu, dV, speed;
+};
+
+// Node tables of the kinetic update (Sec. 5.2): quadrature weight w of the
+// current moment (Eq. 24), Maxwellian F0 and its v_par derivative (def_f_0),
+// collision frequency (Eq. 23) and volume element.
+bool velocity_tables(const fdtd_plasma_desc &p, VTab &t)
+{
+    const double vth = std::sqrt(kQe * p.te_ev / kMe);
+    const double vmax = p.vmax_vth * vth;
+    const double two_vth2 = 2.0 * vth * vth;
+    if (p.vgrid == FDTD_VGRID_SIGNED1D) {
+        const double dv = 2.0 * vmax / p.nv;
+        for (int a = 0; a < p.nv; ++a) {
+            const double va = ((double)a + 0.5 - 0.5 * p.nv) * dv;
+            const double g = std::exp(-va * va / two_vth2) / std::sqrt(kPi * two_vth2);
+            t.v.push_back(va); t.f0.push_back(g); t.f0p.push_back(-va / (vth * vth) * g);
+            t.w.push_back(va * dv); t.dV.push_back(dv); t.speed.push_back(std::fabs(va));
+        }
+    } else if (p.vgrid == FDTD_VGRID_CART2D) {
+        const double dvp = 2.0 * vmax / p.nv, dvq = 2.0 * vmax / p.nv_perp;
+        for (int a = 0; a < p.nv; ++a) {
+            const double va = ((double)a + 0.5 - 0.5 * p.nv) * dvp;
+            for (int b = 0; b < p.nv_perp; ++b) {
+                const double vb = ((double)b + 0.5 - 0.5 * p.nv_perp) * dvq;
+                const double g = std::exp(-(va * va + vb * vb) / two_vth2) / (kPi * two_vth2);
+                t.v.push_back(va); t.f0.push_back(g); t.f0p.push_back(-va / (vth * vth) * g);
+                t.w.push_back(va * dvp * dvq); t.dV.push_back(dvp * dvq);
+                t.speed.push_back(std::sqrt(va * va + vb * vb));
+            }
+        }
+    } else if (p.vgrid == FDTD_VGRID_SPEED3D) {
+        const double gam = vmax / p.nv;
+        for (int k = 0; k < p.nv; ++k) {
+            const double vk = ((double)k + 0.5) * gam;
+            const double g = std::exp(-vk * vk / two_vth2) / std::pow(kPi * two_vth2, 1.5);
+            t.v.push_back(vk); t.f0.push_back(g); t.f0p.push_back(-vk / (vth * vth) * g);
+            t.w.push_back(4.0 * kPi / 3.0 * vk * vk * vk * gam); t.dV.push_back(4.0 * kPi * vk * vk * gam);
+            t.speed.push_back(vk);
+        }
+    } else {
+        return false;
+    }
+    double num = 0.0, den = 0.0;
+    for (size_t j = 0; j < t.v.size(); ++j) {
+        num += t.speed[j] * t.f0[j] * t.dV[j];
+        den += t.f0[j] * t.dV[j];
+    }
+    const double mean = num / den;
+    for (size_t j = 0; j < t.v.size(); ++j)
+        t.nu.push_back(p.nu_model == FDTD_NU_CONST ? p.nu0 : p.nu0 * t.speed[j] / mean);
+    return true;
+}
+
+// ------------------------------------------------------------------ misc
+
+int64_t pol_len(const fdtd_plasma *h) { return h->g.ndim == 1 ? h->nz + 1 : h->nx * h->ny * h->nz; }
+int pol_comp(const fdtd_plasma *h) { return h->g.ndim == 2 ? FDTD_EZ : FDTD_EX; }
+
+bool pol_updated(const fdtd_plasma *h, int64_t c)
+{
+    if (h->g.ndim == 1) return c >= 1 && c <= h->nz - 1;
+    const int64_t i = c % h->nx, j = (c / h->nx) % h->ny, k = c / (h->nx * h->ny);
+    if (h->g.ndim == 2) return i >= 1 && j >= 1;
+    (void)i;
+    return j >= 1 && k >= 1;
+}
+
+void free_plasma(fdtd_plasma *h)
+{
+    dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot); dfree(h, h->tab);
+    dfree(h, h->dV);
+    h->slot_cell = nullptr; h->dens = h->df = h->jslot = h->tab = nullptr; h->dV = nullptr;
+    h->has_plasma = 0;
+    h->nslots = 0;
+    h->nnode = 0;
+}
+
+void drop_graphs(fdtd_plasma *h)
+{
+    if (h->g1) cudaGraphExecDestroy(h->g1);
+    if (h->gk) cudaGraphExecDestroy(h->gk);
+    h->g1 = h->gk = nullptr;
+    h->graphs_valid = 0;
+}
+
+template <typename T>
+Cpml<T> cpml_view(fdtd_plasma *h)
+{
+    Cpml<T> c{};
+    c.L = h->g.ndim >= 2 ? h->g.cpml_cells : 0;
+    if (!c.L) return c;
+    const T *base = reinterpret_cast<const T *>(h->prof);
+    int64_t n[3] = {h->nx, h->ny, h->nz};
+    int64_t off = 0;
+    for (int ax = 0; ax < h->g.ndim; ++ax) {
+        c.be[ax] = base + off; off += n[ax];
+        c.ae[ax] = base + off; off += n[ax];
+        c.ike[ax] = base + off; off += n[ax];
+        c.bh[ax] = base + off; off += n[ax];
+        c.ah[ax] = base + off; off += n[ax];
+        c.ikh[ax] = base + off; off += n[ax];
+    }
+    for (int q = 0; q < 12; ++q) c.psi[q] = reinterpret_cast<T *>(h->psi[q]);
+    return c;
+}
+
+Source source_view(fdtd_plasma *h)
+{
+    Source s{};
+    if (!h->has_source) return s;
+    s.kind = h->src.kind; s.loc = h->src.location;
+    s.amp = h->src.amp; s.fc = h->src.fc; s.tau = h->src.tau; s.t0 = h->src.t0; s.dt = h->dt;
+    s.i = h->src.i; s.j = h->src.j; s.k = h->src.k;
+    s.i0 = h->src.i0; s.i1 = h->src.i1; s.j0 = h->src.j0; s.j1 = h->src.j1;
+    return s;
+}
+
+// enqueue one step n -> n+1 (kstep = offset of this step inside the chunk);
+// ev (optional) receives records before H, before the kinetic kernel, before E
+// and after E.
+template <typename T>
+cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t *ev = nullptr)
+{
+    const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
+    const T ch = (T)(h->dt / (mu0 * h->g.dx)), ce = (T)(h->dt / (kEps0 * h->g.dx));
+    const T cph = (T)(h->dt / mu0), cpe = (T)(h->dt / kEps0);
+    T *f[6];
+    for (int q = 0; q < 6; ++q) f[q] = reinterpret_cast<T *>(h->f[q]);
+    const Cpml<T> cp = cpml_view<T>(h);
+    const Source src = source_view(h);
+    if (ev) cudaEventRecord(ev[0], st);
+    if (h->g.ndim == 1) launch_h1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->g.mur ? (T *)h->mur_state : nullptr, h->nz, ch);
+    else if (h->g.ndim == 2) launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp);
+    else launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp);
+    if (ev) cudaEventRecord(ev[1], st);
+    if (h->has_plasma && h->nslots > 0) {
+        KinArgs<T> a{};
+        a.slot_cell = h->slot_cell;
+        a.dens = reinterpret_cast<const T *>(h->dens);
+        a.df = h->df;
+        a.E = f[pol_comp(h)];
+        a.jslot = reinterpret_cast<T *>(h->jslot);
+        a.tab = reinterpret_cast<const T *>(h->tab);
+        a.nslots = h->nslots;
+        a.pitch = h->pitch;
+        a.cj = cpe;
+        a.seed = h->pl.seed;
+        a.d_step = h->d_step;
+        a.kstep = kstep;
+        cudaError_t e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms);
+        if (e != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    if (h->g.ndim == 1) {
+        launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep);
+        if (h->g.mur) {
+            const T m = (T)((kC0 * h->dt - h->g.dx) / (kC0 * h->dt + h->g.dx));
+            launch_mur1d<T>(st, f[FDTD_EX], (const T *)h->mur_state, h->nz, m);
+        }
+    } else if (h->g.ndim == 2) {
+        launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, kstep);
+    } else {
+        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep);
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue(fdtd_plasma *h, cudaStream_t st, int nsteps)
+{
+    for (int k = 0; k < nsteps; ++k) {
+        cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_step<double>(h, st, k) : enqueue_step<float>(h, st, k);
+        if (e != cudaSuccess) return e;
+    }
+    launch_advance(st, h->d_step, nsteps);
+    return cudaGetLastError();
+}
+
+int capture(fdtd_plasma *h, int nsteps, cudaGraphExec_t *out)
+{
+    cudaGraph_t graph = nullptr;
+    CK(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = enqueue(h, h->cap, nsteps);
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "capturing the step sequence");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    return FDTD_OK;
+}
+
+size_t field_bytes(const fdtd_plasma *h, int q) { return h->f[q] ? (size_t)h->flen[q] * h->esz : 0; }
+
+}  // namespace
+
+// =================================================================== ABI
+
+extern "C" {
+
+int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdtd_plasma_t *out)
+{
+    if (!out) return fail(nullptr, FDTD_ERR_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!g) return fail(nullptr, FDTD_ERR_INVAL, "grid is NULL");
+    if (g->ndim < 1 || g->ndim > 3) return fail(nullptr, FDTD_ERR_INVAL, "ndim must be 1, 2 or 3");
+    if (g->precision != FDTD_F32 && g->precision != FDTD_F64) return fail(nullptr, FDTD_ERR_INVAL, "bad precision");
+    if (!(g->dx > 0.0) || !std::isfinite(g->dx)) return fail(nullptr, FDTD_ERR_INVAL, "dx must be > 0");
+    if (!(g->courant > 0.0) || !std::isfinite(g->courant)) return fail(nullptr, FDTD_ERR_INVAL, "courant must be > 0");
+    if (g->courant * g->courant * g->ndim >= 1.0)
+        return fail(nullptr, FDTD_ERR_UNSTABLE, "Courant number %g violates S^2 ndim < 1", g->courant);
+    int64_t n[3] = {g->ndim >= 2 ? g->nx : 1, g->ndim >= 2 ? g->ny : 1, g->ndim == 2 ? 1 : g->nz};
+    for (int ax = 0; ax < 3; ++ax) {
+        const bool used = (g->ndim == 1) ? ax == 2 : (g->ndim == 2 ? ax < 2 : true);
+        if (used && (n[ax] < 3 || n[ax] > (int64_t)1 << 30))
+            return fail(nullptr, FDTD_ERR_INVAL, "axis %d size %lld out of range [3, 2^30]", ax, (long long)n[ax]);
+    }
+    const int64_t ncell = n[0] * n[1] * n[2];
+    if (ncell > ((int64_t)1 << 31) - 1) return fail(nullptr, FDTD_ERR_INVAL, "grid has more than 2^31-1 nodes");
+    if (g->cpml_cells < 0) return fail(nullptr, FDTD_ERR_INVAL, "cpml_cells < 0");
+    if (g->ndim == 1 && g->cpml_cells) return fail(nullptr, FDTD_ERR_INVAL, "1-D uses Mur or PEC ends, not CPML");
+    if (g->ndim >= 2 && g->mur) return fail(nullptr, FDTD_ERR_INVAL, "Mur ends are 1-D only");
+    if (g->cpml_cells) {
+        for (int ax = 0; ax < g->ndim; ++ax)
+            if (3 * (int64_t)g->cpml_cells >= n[ax])
+                return fail(nullptr, FDTD_ERR_INVAL, "CPML thicker than a third of axis %d", ax);
+        if (!(g->cpml_order > 0) || !(g->cpml_kappa_max >= 1.0) || !(g->cpml_sigma_factor >= 0) ||
+            g->cpml_alpha_min < 0 || g->cpml_alpha_max < g->cpml_alpha_min)
+            return fail(nullptr, FDTD_ERR_INVAL, "bad CPML parameters");
+    }
+
+    fdtd_plasma *h = new (std::nothrow) fdtd_plasma();
+    if (!h) return fail(nullptr, FDTD_ERR_NOMEM, "host allocation failed");
+    h->g = *g;
+    if (rt) h->rt = *rt;
+    h->stream = (cudaStream_t)h->rt.stream;
+    h->nx = n[0]; h->ny = n[1]; h->nz = n[2];
+    h->dt = g->courant * g->dx / kC0;
+    h->esz = g->precision == FDTD_F64 ? 8 : 4;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) {
+        int r = cuda_fail(nullptr, ce, "device setup");
+        delete h;
+        return r;
+    }
+    int rc = FDTD_OK;
+    auto bail = [&](int code, const char *what) {
+        g_create_error = what;
+        fdtd_plasma_destroy(h);
+        return code;
+    };
+    // fields
+    if (g->ndim == 1) {
+        h->flen[FDTD_EX] = h->nz + 1;
+        h->flen[FDTD_HY] = h->nz;
+    } else if (g->ndim == 2) {
+        h->flen[FDTD_EZ] = h->flen[FDTD_HX] = h->flen[FDTD_HY] = ncell;
+    } else {
+        for (int q = 0; q < 6; ++q) h->flen[q] = ncell;
+    }
+    for (int q = 0; q < 6; ++q)
+        if (h->flen[q]) {
+            h->f[q] = dalloc(h, h->flen[q] * h->esz);
+            if (!h->f[q]) return bail(FDTD_ERR_NOMEM, "field allocation failed");
+        }
+    // CPML: profiles + psi slabs
+    if (g->ndim >= 2 && g->cpml_cells) {
+        const int64_t L2 = 2 * (int64_t)g->cpml_cells;
+        std::vector<double> tabs;
+        for (int ax = 0; ax < g->ndim; ++ax) {
+            std::vector<double> b, a, ik;
+            cpml_axis(*g, h->dt, n[ax], false, b, a, ik);
+            tabs.insert(tabs.end(), b.begin(), b.end());
+            tabs.insert(tabs.end(), a.begin(), a.end());
+            tabs.insert(tabs.end(), ik.begin(), ik.end());
+            cpml_axis(*g, h->dt, n[ax], true, b, a, ik);
+            tabs.insert(tabs.end(), b.begin(), b.end());
+            tabs.insert(tabs.end(), a.begin(), a.end());
+            tabs.insert(tabs.end(), ik.begin(), ik.end());
+        }
+        h->prof_len = (int64_t)tabs.size();
+        h->prof = dalloc(h, tabs.size() * h->esz);
+        if (!h->prof) return bail(FDTD_ERR_NOMEM, "CPML table allocation failed");
+        if (h->esz == 8) {
+            rc = cudaMemcpy(h->prof, tabs.data(), tabs.size() * 8, cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> t32(tabs.begin(), tabs.end());
+            rc = cudaMemcpy(h->prof, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice);
+        }
+        if (rc != cudaSuccess) return bail(FDTD_ERR_CUDA, "CPML table upload failed");
+        if (g->ndim == 2) {
+            h->psilen[0] = h->psilen[3] = h->ny * L2;   // x-slabs
+            h->psilen[1] = h->psilen[2] = L2 * h->nx;   // y-slabs
+        } else {
+            const int64_t xs = h->nz * h->ny * L2, ys = h->nz * L2 * h->nx, zs = L2 * h->ny * h->nx;
+            const int axis_of_slot[12] = {1, 2, 0, 2, 0, 1, 1, 2, 0, 2, 0, 1};
+            for (int q = 0; q < 12; ++q) h->psilen[q] = axis_of_slot[q] == 0 ? xs : (axis_of_slot[q] == 1 ? ys : zs);
+        }
+        for (int q = 0; q < 12; ++q)
+            if (h->psilen[q]) {
+                h->psi[q] = dalloc(h, h->psilen[q] * h->esz);
+                if (!h->psi[q]) return bail(FDTD_ERR_NOMEM, "psi allocation failed");
+            }
+    }
+    h->mur_state = dalloc(h, 4 * 8);
+    h->d_step = (int64_t *)dalloc(h, 256);
+    h->diag_blocks = h->num_sms * 4;
+    h->diag_partials = (double *)dalloc(h, (size_t)h->diag_blocks * 7 * sizeof(double));
+    h->diag_out = (double *)dalloc(h, 8 * sizeof(double));
+    if (!h->mur_state || !h->d_step || !h->diag_partials || !h->diag_out)
+        return bail(FDTD_ERR_NOMEM, "small allocation failed");
+    rc = fdtd_plasma_reset(h);
+    if (rc != FDTD_OK) {
+        g_create_error = h->err;
+        fdtd_plasma_destroy(h);
+        return rc;
+    }
+    cudaError_t se = cudaStreamSynchronize(h->stream);
+    if (se != cudaSuccess) return bail(FDTD_ERR_CUDA, cudaGetErrorString(se));
+    *out = h;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_reset(fdtd_plasma_t h)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    for (int q = 0; q < 6; ++q)
+        if (h->f[q]) CK(h, cudaMemsetAsync(h->f[q], 0, field_bytes(h, q), h->stream));
+    for (int q = 0; q < 12; ++q)
+        if (h->psi[q]) CK(h, cudaMemsetAsync(h->psi[q], 0, h->psilen[q] * h->esz, h->stream));
+    if (h->has_plasma) {
+        CK(h, cudaMemsetAsync(h->df, 0, (size_t)h->nslots * h->pitch * h->df_esz, h->stream));
+        CK(h, cudaMemsetAsync(h->jslot, 0, (size_t)(h->nslots ? h->nslots : 1) * h->esz, h->stream));
+    }
+    CK(h, cudaMemsetAsync(h->mur_state, 0, 32, h->stream));
+    CK(h, cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
+    h->steps_done = 0;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_set_source(fdtd_plasma_t h, const fdtd_source_desc *s)
+{
+    if (!h || !s) return FDTD_ERR_INVAL;
+    if (s->kind == FDTD_SRC_NONE) {
+        h->has_source = 0;
+        drop_graphs(h);
+        return FDTD_OK;
+    }
+    if (s->kind != FDTD_SRC_GAUSS_SINE && s->kind != FDTD_SRC_GAUSS) return fail(h, FDTD_ERR_INVAL, "bad source kind");
+    if (!(s->tau > 0) || !std::isfinite(s->amp) || !std::isfinite(s->fc) || !std::isfinite(s->t0) || !std::isfinite(s->tau))
+        return fail(h, FDTD_ERR_INVAL, "source parameters must be finite, tau > 0");
+    const int nd = h->g.ndim;
+    if (s->location == FDTD_LOC_POINT) {
+        bool ok;
+        if (nd == 1) ok = s->k >= 1 && s->k <= h->nz - 1;
+        else if (nd == 2) ok = s->i >= 1 && s->i < h->nx && s->j >= 1 && s->j < h->ny;
+        else ok = s->i >= 0 && s->i < h->nx && s->j >= 1 && s->j < h->ny && s->k >= 1 && s->k < h->nz;
+        if (!ok) return fail(h, FDTD_ERR_INVAL, "source node outside the updated nodes");
+    } else if (s->location == FDTD_LOC_SHEET) {
+        if (nd != 3) return fail(h, FDTD_ERR_INVAL, "sheet sources are 3-D only");
+        if (!(s->k >= 1 && s->k < h->nz && s->i0 >= 0 && s->i1 <= h->nx && s->i0 < s->i1 && s->j0 >= 1 &&
+              s->j1 <= h->ny && s->j0 < s->j1))
+            return fail(h, FDTD_ERR_INVAL, "sheet outside the updated Ex nodes");
+    } else {
+        return fail(h, FDTD_ERR_INVAL, "bad source location");
+    }
+    h->src = *s;
+    h->has_source = 1;
+    drop_graphs(h);
+    return FDTD_OK;
+}
+
+int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
+{
+    if (!h || !p) return FDTD_ERR_INVAL;
+    if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_plasma after stepping: call fdtd_plasma_reset first");
+    if (!p->density) return fail(h, FDTD_ERR_INVAL, "density is NULL");
+    if (p->vgrid < 0 || p->vgrid > 2) return fail(h, FDTD_ERR_INVAL, "bad vgrid");
+    if (p->nv < 2 || (p->vgrid == FDTD_VGRID_CART2D && p->nv_perp < 1))
+        return fail(h, FDTD_ERR_INVAL, "nv too small");
+    if (!(p->te_ev > 0) || !(p->vmax_vth > 0) || !(p->nu0 >= 0) || !std::isfinite(p->nu0))
+        return fail(h, FDTD_ERR_INVAL, "te_ev, vmax_vth must be > 0 and nu0 >= 0");
+    if (p->nu_model != FDTD_NU_NSV && p->nu_model != FDTD_NU_CONST) return fail(h, FDTD_ERR_INVAL, "bad nu_model");
+    const bool f64 = h->g.precision == FDTD_F64;
+    if (f64 ? p->f_dtype != FDTD_DF_F64 : (p->f_dtype != FDTD_DF_F32 && p->f_dtype != FDTD_DF_BF16))
+        return fail(h, FDTD_ERR_INVAL, "f_dtype does not match the field precision");
+    if (p->nonlinear) return fail(h, FDTD_ERR_INVAL, "the nonlinear advection mode is not available on the GPU path");
+    const int64_t nnode = p->vgrid == FDTD_VGRID_CART2D ? (int64_t)p->nv * p->nv_perp : p->nv;
+    const int pitch = kinetic_pitch((int)nnode, p->f_dtype);
+    const int vec = p->f_dtype == FDTD_DF_BF16 ? 8 : (p->f_dtype == FDTD_DF_F64 ? 2 : 4);
+    if (pitch / vec > 512) return fail(h, FDTD_ERR_INVAL, "too many velocity nodes for this storage type");
+
+    // density: compact the plasma cells
+    const int64_t np = pol_len(h);
+    std::vector<double> dens(np);
+    if (p->density_on_device) CK(h, cudaMemcpy(dens.data(), p->density, np * 8, cudaMemcpyDeviceToHost));
+    else std::memcpy(dens.data(), p->density, np * 8);
+    std::vector<int32_t> cells;
+    std::vector<double> dslot;
+    double nmax = 0.0;
+    for (int64_t c = 0; c < np; ++c) {
+        const double d = dens[c];
+        if (!std::isfinite(d) || d < 0.0) return fail(h, FDTD_ERR_NONFINITE, "density must be finite and >= 0");
+        if (d > 0.0 && pol_updated(h, c)) {
+            cells.push_back((int32_t)c);
+            dslot.push_back(d);
+            if (d > nmax) nmax = d;
+        }
+    }
+    // plasma-modified stability of Yee + Crank-Nicolson current: (w_p dt/2)^2 + S^2 ndim < 1
+    const double wp = std::sqrt(nmax * kQe * kQe / (kEps0 * kMe));
+    if (std::pow(wp * h->dt / 2, 2) + h->g.courant * h->g.courant * h->g.ndim >= 1.0)
+        return fail(h, FDTD_ERR_UNSTABLE, "plasma frequency %g rad/s too high for dt %g", wp, h->dt);
+
+    VTab t;
+    fdtd_plasma_desc pd = *p;
+    if (!velocity_tables(pd, t)) return fail(h, FDTD_ERR_INVAL, "bad velocity grid");
+    // folded tables: alpha, beta, w' = -e w (padding nodes: 0)
+    std::vector<double> tab(3 * (size_t)pitch, 0.0);
+    for (int64_t j = 0; j < nnode; ++j) {
+        const double nu = t.nu[j];
+        tab[j] = (2.0 - h->dt * nu) / (2.0 + h->dt * nu);
+        tab[pitch + j] = 2.0 * h->dt * (kQe / kMe) * t.f0p[j] / (2.0 + h->dt * nu);
+        tab[2 * pitch + j] = -kQe * t.w[j];
+    }
+
+    drop_graphs(h);
+    free_plasma(h);
+    const size_t ns = cells.size();
+    h->pl = *p;
+    h->pl.density = nullptr;
+    h->nslots = (int64_t)ns;
+    h->nnode = nnode;
+    h->pitch = pitch;
+    h->df_esz = p->f_dtype == FDTD_DF_BF16 ? 2 : (p->f_dtype == FDTD_DF_F64 ? 8 : 4);
+    h->slot_cell = (int32_t *)dalloc(h, (ns ? ns : 1) * 4);
+    h->dens = dalloc(h, (ns ? ns : 1) * h->esz);
+    h->df = dalloc(h, (ns ? ns : 1) * pitch * h->df_esz);
+    h->jslot = dalloc(h, (ns ? ns : 1) * h->esz);
+    h->tab = dalloc(h, tab.size() * h->esz);
+    h->dV = (double *)dalloc(h, nnode * 8);
+    if (!h->slot_cell || !h->dens || !h->df || !h->jslot || !h->tab || !h->dV) {
+        free_plasma(h);
+        return fail(h, FDTD_ERR_NOMEM, "plasma allocation failed (%zu cells x %d nodes)", ns, pitch);
+    }
+    h->has_plasma = 1;
+    if (ns) CK(h, cudaMemcpy(h->slot_cell, cells.data(), ns * 4, cudaMemcpyHostToDevice));
+    if (h->esz == 8) {
+        if (ns) CK(h, cudaMemcpy(h->dens, dslot.data(), ns * 8, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> d32(dslot.begin(), dslot.end()), t32(tab.begin(), tab.end());
+        if (ns) CK(h, cudaMemcpy(h->dens, d32.data(), ns * 4, cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->tab, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
+    }
+    CK(h, cudaMemcpy(h->dV, t.dV.data(), nnode * 8, cudaMemcpyHostToDevice));
+    CK(h, cudaMemsetAsync(h->df, 0, (ns ? ns : 1) * pitch * h->df_esz, h->stream));
+    CK(h, cudaMemsetAsync(h->jslot, 0, (ns ? ns : 1) * h->esz, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (nsteps < 0) return fail(h, FDTD_ERR_INVAL, "nsteps < 0");
+    if (nsteps == 0) return FDTD_OK;
+    if (!h->graphs_valid) {
+        int rc = capture(h, 1, &h->g1);
+        if (rc == FDTD_OK) rc = capture(h, kChunk, &h->gk);
+        if (rc != FDTD_OK) {
+            drop_graphs(h);
+            return rc;
+        }
+        h->gk_steps = kChunk;
+        h->graphs_valid = 1;
+    }
+    int64_t left = nsteps;
+    while (left >= h->gk_steps) {
+        CK(h, cudaGraphLaunch(h->gk, h->stream));
+        left -= h->gk_steps;
+    }
+    while (left > 0) {
+        CK(h, cudaGraphLaunch(h->g1, h->stream));
+        --left;
+    }
+    h->steps_done += nsteps;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out)
+{
+    if (!h || !ms_out || nsteps < 1) return FDTD_ERR_INVAL;
+    cudaEvent_t ev[4];
+    for (int q = 0; q < 4; ++q) CK(h, cudaEventCreate(&ev[q]));
+    double acc[4] = {0, 0, 0, 0};
+    int rc = FDTD_OK;
+    for (int64_t s = 0; s < nsteps && rc == FDTD_OK; ++s) {
+        cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_step<double>(h, h->stream, 0, ev)
+                                                   : enqueue_step<float>(h, h->stream, 0, ev);
+        if (e == cudaSuccess) {
+            launch_advance(h->stream, h->d_step, 1);
+            e = cudaEventSynchronize(ev[3]);
+        }
+        if (e != cudaSuccess) {
+            rc = cuda_fail(h, e, "timed step");
+            break;
+        }
+        float ms;
+        for (int q = 0; q < 3; ++q) {
+            cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+            acc[q] += ms;
+        }
+        cudaEventElapsedTime(&ms, ev[0], ev[3]);
+        acc[3] += ms;
+        h->steps_done += 1;
+    }
+    for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
+    if (rc != FDTD_OK) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int q = 0; q < 4; ++q) ms_out[q] = acc[q] / (double)nsteps;
+    return FDTD_OK;
+}
+
+size_t fdtd_plasma_quantity_bytes(fdtd_plasma_t h, int which)
+{
+    if (!h) return 0;
+    if (which >= 0 && which <= 5) return field_bytes(h, which);
+    if (which == FDTD_J) return h->has_plasma ? (size_t)h->nslots * h->esz : 0;
+    if (which == FDTD_DF) return h->has_plasma ? (size_t)h->nslots * h->nnode * h->df_esz : 0;
+    return 0;
+}
+
+static int copy_quantity(fdtd_plasma_t h, int which, void *host_or_dev, size_t bytes, int is_device, bool out)
+{
+    if (!h || !host_or_dev) return FDTD_ERR_INVAL;
+    const size_t need = fdtd_plasma_quantity_bytes(h, which);
+    if (need == 0) return fail(h, FDTD_ERR_INVAL, "quantity %d is absent", which);
+    if (bytes != need) return fail(h, FDTD_ERR_INVAL, "quantity %d needs %zu bytes, got %zu", which, need, bytes);
+    const cudaMemcpyKind kind = out ? (is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
+                                    : (is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+    if (which == FDTD_DF) {
+        const size_t row = (size_t)h->nnode * h->df_esz, dpitch = (size_t)h->pitch * h->df_esz;
+        if (out)
+            CK(h, cudaMemcpy2DAsync(host_or_dev, row, h->df, dpitch, row, h->nslots, kind, h->stream));
+        else
+            CK(h, cudaMemcpy2DAsync(h->df, dpitch, host_or_dev, row, row, h->nslots, kind, h->stream));
+    } else {
+        void *dev = which == FDTD_J ? h->jslot : h->f[which];
+        if (out) CK(h, cudaMemcpyAsync(host_or_dev, dev, bytes, kind, h->stream));
+        else CK(h, cudaMemcpyAsync(dev, host_or_dev, bytes, kind, h->stream));
+    }
+    if (!is_device) CK(h, cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+int fdtd_plasma_read_fields(fdtd_plasma_t h, int which, void *dst, size_t bytes, int dst_is_device)
+{
+    return copy_quantity(h, which, dst, bytes, dst_is_device, true);
+}
+
+int fdtd_plasma_write_fields(fdtd_plasma_t h, int which, const void *src, size_t bytes, int src_is_device)
+{
+    if (h && which == FDTD_J) return fail(h, FDTD_ERR_INVAL, "J is not writable");
+    return copy_quantity(h, which, const_cast<void *>(src), bytes, src_is_device, false);
+}
+
+int fdtd_plasma_plasma_shape(fdtd_plasma_t h, int64_t *nslots, int64_t *nnode)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (nslots) *nslots = h->nslots;
+    if (nnode) *nnode = h->nnode;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_info(fdtd_plasma_t h, double *dt, int64_t *steps)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (dt) *dt = h->dt;
+    if (steps) *steps = h->steps_done;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
+{
+    if (!h || !out) return FDTD_ERR_INVAL;
+    const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
+    DiagArgs a{};
+    a.ndim = h->g.ndim;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    for (int q = 0; q < 6; ++q) { a.f[q] = h->f[q]; a.flen[q] = h->flen[q]; }
+    a.precision = h->g.precision;
+    a.ch = h->dt / (mu0 * h->g.dx);
+    const double dv = std::pow(h->g.dx, h->g.ndim);
+    a.eps0_half_dv = 0.5 * kEps0 * dv;
+    a.mu0_half_dv = 0.5 * mu0 * dv;
+    a.df = h->df;
+    a.nslots = h->has_plasma ? h->nslots : 0;
+    a.nnode = h->nnode;
+    a.pitch = h->pitch;
+    a.f_dtype = h->pl.f_dtype;
+    a.dV = h->dV;
+    CK(h, launch_diag(h->stream, a, h->diag_partials, h->diag_blocks, h->diag_out));
+    double o[6];
+    CK(h, cudaMemcpyAsync(o, h->diag_out, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    out->energy = o[0];
+    out->energy_plain = o[1];
+    out->number = o[2];
+    out->number_max_cell = o[3];
+    out->number_abs = o[4];
+    out->finite = o[5] > 0.5 ? 1 : 0;
+    out->step = h->steps_done;
+    return FDTD_OK;
+}
+
+// ------------------------------------------------------------ checkpoints
+// blob: 8 x uint64 header, then fields, psi, df (raw rows), J, mur state, step
+
+static size_t state_parts(fdtd_plasma_t h, std::vector<std::pair<void *, size_t>> &parts)
+{
+    parts.clear();
+    for (int q = 0; q < 6; ++q)
+        if (h->f[q]) parts.push_back({h->f[q], field_bytes(h, q)});
+    for (int q = 0; q < 12; ++q)
+        if (h->psi[q]) parts.push_back({h->psi[q], (size_t)h->psilen[q] * h->esz});
+    if (h->has_plasma && h->nslots) {
+        parts.push_back({h->df, (size_t)h->nslots * h->pitch * h->df_esz});
+        parts.push_back({h->jslot, (size_t)h->nslots * h->esz});
+    }
+    parts.push_back({h->mur_state, 32});
+    parts.push_back({h->d_step, sizeof(int64_t)});
+    size_t tot = 64;
+    for (auto &p : parts) tot += p.second;
+    return tot;
+}
+
+size_t fdtd_plasma_state_bytes(fdtd_plasma_t h)
+{
+    if (!h) return 0;
+    std::vector<std::pair<void *, size_t>> parts;
+    return state_parts(h, parts);
+}
+
+int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int dev)
+{
+    if (!h || !buf) return FDTD_ERR_INVAL;
+    std::vector<std::pair<void *, size_t>> parts;
+    const size_t need = state_parts(h, parts);
+    if (bytes != need) return fail(h, FDTD_ERR_INVAL, "state needs %zu bytes, got %zu", need, bytes);
+    uint64_t hdr[8] = {kStateMagic, (uint64_t)h->g.ndim, (uint64_t)(h->nx * h->ny * h->nz), (uint64_t)h->nslots,
+                       (uint64_t)h->pitch, (uint64_t)h->df_esz, (uint64_t)h->esz, (uint64_t)h->steps_done};
+    const cudaMemcpyKind k_out = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(h, cudaMemcpyAsync(buf, hdr, 64, dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, h->stream));
+    size_t off = 64;
+    for (auto &p : parts) {
+        CK(h, cudaMemcpyAsync((char *)buf + off, p.first, p.second, k_out, h->stream));
+        off += p.second;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
+int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int dev)
+{
+    if (!h || !buf) return FDTD_ERR_INVAL;
+    std::vector<std::pair<void *, size_t>> parts;
+    const size_t need = state_parts(h, parts);
+    if (bytes != need) return fail(h, FDTD_ERR_INVAL, "state needs %zu bytes, got %zu", need, bytes);
+    uint64_t hdr[8];
+    CK(h, cudaMemcpy(hdr, buf, 64, dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+    if (hdr[0] != kStateMagic || hdr[1] != (uint64_t)h->g.ndim || hdr[2] != (uint64_t)(h->nx * h->ny * h->nz) ||
+        hdr[3] != (uint64_t)h->nslots || hdr[4] != (uint64_t)h->pitch || hdr[5] != (uint64_t)h->df_esz ||
+        hdr[6] != (uint64_t)h->esz)
+        return fail(h, FDTD_ERR_STATE, "state blob does not match this handle's configuration");
+    const cudaMemcpyKind k_in = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    size_t off = 64;
+    for (auto &p : parts) {
+        CK(h, cudaMemcpyAsync(p.first, (const char *)buf + off, p.second, k_in, h->stream));
+        off += p.second;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->steps_done = (int64_t)hdr[7];
+    return FDTD_OK;
+}
+
+const char *fdtd_plasma_last_error(fdtd_plasma_t h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void fdtd_plasma_destroy(fdtd_plasma_t h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    free_plasma(h);
+    for (int q = 0; q < 6; ++q) dfree(h, h->f[q]);
+    for (int q = 0; q < 12; ++q) dfree(h, h->psi[q]);
+    dfree(h, h->prof);
+    dfree(h, h->mur_state);
+    dfree(h, h->d_step);
+    dfree(h, h->diag_partials);
+    dfree(h, h->diag_out);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,171 @@
+// diag.cu -- FP64 diagnostics of the current state: the discrete Yee
+// energy invariant, the plain field energy, the particle-number perturbation
+// sum_j df_j dV_j (total, max per cell, absolute) and a finiteness flag.
+//
+// Pass 1: grid-stride blocks accumulate FP64 partials (one row of 6 per block)
+// into a scratch buffer; pass 2: one block reduces the rows.  The fields are
+// read once; delta f rows are read one warp per row.
+#include "internal.cuh"
+
+namespace fp {
+
+template <typename T>
+__device__ __forceinline__ double ld(const void *p, int64_t i)
+{
+    return (double)reinterpret_cast<const T *>(p)[i];
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T>
+__device__ void field_terms(const DiagArgs &a, int64_t c, double &we, double &wh, double &wh2, int &fin)
+{
+    if (a.ndim == 1) {
+        const int64_t nz = a.nz;
+        if (c <= nz) {
+            double e = ld<T>(a.f[0], c);
+            we += e * e;
+            fin &= isfinite(e);
+        }
+        if (c < nz) {
+            double h = ld<T>(a.f[4], c);
+            double hn = h - a.ch * (ld<T>(a.f[0], c + 1) - ld<T>(a.f[0], c));
+            wh += h * hn;
+            wh2 += h * h;
+            fin &= isfinite(h);
+        }
+    } else if (a.ndim == 2) {
+        const int64_t nx = a.nx, ny = a.ny;
+        const int64_t i = c % nx, j = c / nx;
+        double e = ld<T>(a.f[2], c);
+        double dEy = (j + 1 < ny ? ld<T>(a.f[2], c + nx) : 0.0) - e;
+        double dEx = (i + 1 < nx ? ld<T>(a.f[2], c + 1) : 0.0) - e;
+        double hx = ld<T>(a.f[3], c), hy = ld<T>(a.f[4], c);
+        we += e * e;
+        wh += hx * (hx - a.ch * dEy) + hy * (hy + a.ch * dEx);
+        wh2 += hx * hx + hy * hy;
+        fin &= isfinite(e) && isfinite(hx) && isfinite(hy);
+    } else {
+        const int64_t nx = a.nx, ny = a.ny, nz = a.nz, sxy = nx * ny;
+        const int64_t i = c % nx, j = (c / nx) % ny, k = c / sxy;
+        double ex = ld<T>(a.f[0], c), ey = ld<T>(a.f[1], c), ez = ld<T>(a.f[2], c);
+        double hx = ld<T>(a.f[3], c), hy = ld<T>(a.f[4], c), hz = ld<T>(a.f[5], c);
+        double ez_y = j + 1 < ny ? ld<T>(a.f[2], c + nx) : 0.0, ey_z = k + 1 < nz ? ld<T>(a.f[1], c + sxy) : 0.0;
+        double ex_z = k + 1 < nz ? ld<T>(a.f[0], c + sxy) : 0.0, ez_x = i + 1 < nx ? ld<T>(a.f[2], c + 1) : 0.0;
+        double ey_x = i + 1 < nx ? ld<T>(a.f[1], c + 1) : 0.0, ex_y = j + 1 < ny ? ld<T>(a.f[0], c + nx) : 0.0;
+        double hxn = hx - a.ch * ((ez_y - ez) - (ey_z - ey));
+        double hyn = hy - a.ch * ((ex_z - ex) - (ez_x - ez));
+        double hzn = hz - a.ch * ((ey_x - ey) - (ex_y - ex));
+        we += ex * ex + ey * ey + ez * ez;
+        wh += hx * hxn + hy * hyn + hz * hzn;
+        wh2 += hx * hx + hy * hy + hz * hz;
+        fin &= isfinite(ex) && isfinite(ey) && isfinite(ez) && isfinite(hx) && isfinite(hy) && isfinite(hz);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double df_val(const DiagArgs &a, int64_t row, int64_t j)
+{
+    const int64_t idx = row * a.pitch + j;
+    if (a.f_dtype == FDTD_DF_BF16) {
+        const uint16_t b = reinterpret_cast<const uint16_t *>(a.df)[idx];
+        return (double)__uint_as_float((uint32_t)b << 16);
+    }
+    if (a.f_dtype == FDTD_DF_F64) return reinterpret_cast<const double *>(a.df)[idx];
+    return (double)reinterpret_cast<const float *>(a.df)[idx];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_partial(DiagArgs a, double *partials)
+{
+    __shared__ double red[6][8];
+    double we = 0, wh = 0, wh2 = 0, num = 0, nmax = 0, nabs = 0;
+    int fin = 1;
+    const int64_t ncells = a.ndim == 1 ? a.nz + 1 : a.nx * a.ny * a.nz;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = tid; c < ncells; c += nth) field_terms<T>(a, c, we, wh, wh2, fin);
+    // one warp per delta-f row
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = tid >> 5, nw = nth >> 5;
+    for (int64_t r = wg; r < a.nslots; r += nw) {
+        double sr = 0, sa = 0;
+        for (int64_t j = lane; j < a.nnode; j += 32) {
+            double v = df_val<T>(a, r, j);
+            sr += v * a.dV[j];
+            sa += fabs(v) * a.dV[j];
+            fin &= isfinite(v);
+        }
+        sr = warp_sum(sr);
+        sa = warp_sum(sa);
+        if (lane == 0) {
+            num += sr;
+            nabs += sa;
+            nmax = fmax(nmax, fabs(sr));
+        }
+    }
+    // block reduction
+    we = warp_sum(we); wh = warp_sum(wh); wh2 = warp_sum(wh2);
+    num = warp_sum(num); nabs = warp_sum(nabs); nmax = warp_max(nmax);
+    fin = __all_sync(0xffffffffu, fin);
+    const int w = threadIdx.x >> 5;
+    __shared__ int sfin[8];
+    if (lane == 0) {
+        red[0][w] = we; red[1][w] = wh; red[2][w] = wh2; red[3][w] = num; red[4][w] = nabs; red[5][w] = nmax;
+        sfin[w] = fin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double o[6] = {0, 0, 0, 0, 0, 0};
+        int f = 1;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            for (int t = 0; t < 5; ++t) o[t] += red[t][q];
+            o[5] = fmax(o[5], red[5][q]);
+            f &= sfin[q];
+        }
+        double *p = partials + (int64_t)blockIdx.x * 7;
+        for (int t = 0; t < 6; ++t) p[t] = o[t];
+        p[6] = f ? 1.0 : 0.0;
+    }
+}
+
+__global__ void k_diag_final(const double *partials, int nblocks, double eps_half_dv, double mu_half_dv, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double o[6] = {0, 0, 0, 0, 0, 0};
+    double fin = 1.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double *p = partials + (int64_t)b * 7;
+        for (int t = 0; t < 5; ++t) o[t] += p[t];
+        o[5] = fmax(o[5], p[5]);
+        fin = fmin(fin, p[6]);
+    }
+    out[0] = eps_half_dv * o[0] + mu_half_dv * o[1];   // invariant energy
+    out[1] = eps_half_dv * o[0] + mu_half_dv * o[2];   // plain energy
+    out[2] = o[3];                                      // number
+    out[3] = o[5];                                      // max per cell
+    out[4] = o[4];                                      // abs
+    out[5] = fin;
+}
+
+cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, int max_blocks, double *out)
+{
+    int blocks = max_blocks;
+    if (a.precision == FDTD_F64)
+        k_diag_partial<double><<<blocks, 256, 0, st>>>(a, partials);
+    else
+        k_diag_partial<float><<<blocks, 256, 0, st>>>(a, partials);
+    k_diag_final<<<1, 32, 0, st>>>(partials, blocks, a.eps0_half_dv, a.mu0_half_dv, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fp

@@ -1,0 +1,181 @@
+// internal.cuh -- handle layout, device helpers and kernel launchers shared by
+// the translation units of the fdtd_plasma library (not part of the ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fdtd_plasma.h"
+
+namespace fp {
+
+// ------------------------------------------------------------------ views
+
+// Per-axis CPML profile at E (integer) and H (half-integer) positions, plus
+// the psi slabs.  L == 0 means no CPML.  ik* hold 1/kappa.
+template <typename T>
+struct Cpml {
+    int L;
+    const T *be[3], *ae[3], *ike[3];
+    const T *bh[3], *ah[3], *ikh[3];
+    // 2-D: psi[0] ez_x  [ny][2L], psi[1] ez_y [2L][nx], psi[2] hx_y [2L][nx], psi[3] hy_x [ny][2L]
+    // 3-D: slot 2*f + d (f = Ex..Hz, d = first / second curl axis), see fields.cu
+    T *psi[12];
+};
+
+struct Source {
+    int kind, loc;
+    double amp, fc, tau, t0, dt;
+    int64_t i, j, k, i0, i1, j0, j1;
+};
+
+// g(t) of the soft source, FP64 on the device
+__device__ __forceinline__ double source_value(const Source &s, double t)
+{
+    double u = (t - s.t0) / s.tau;
+    if (s.kind == FDTD_SRC_GAUSS_SINE) return s.amp * sin(6.283185307179586 * s.fc * (t - s.t0)) * exp(-u * u);
+    if (s.kind == FDTD_SRC_GAUSS) return s.amp * exp(-u * u);
+    return 0.0;
+}
+
+template <typename TA>
+struct KinArgs {
+    const int32_t *slot_cell;  // polarisation node of each slot
+    const TA *dens;            // density per slot
+    void *df;                  // rows of `pitch` elements
+    TA *E;                     // polarisation field (updated in place: E -= cj J)
+    TA *jslot;                 // J^{n+1/2} per slot
+    const TA *tab;             // [alpha | beta | w'] each `pitch` long, w' = -e w
+    int64_t nslots;
+    int pitch;
+    TA cj;                     // dt / eps0
+    uint64_t seed;
+    const int64_t *d_step;     // steps done before the chunk
+    int kstep;                 // step offset inside the chunk
+};
+
+// ---------------------------------------------------------- compensated sums
+
+// Knuth TwoSum: s + e == a + b exactly (round-to-nearest, no contraction).
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
+{
+    s = a + b;
+    T z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// ---------------------------------------------- Philox4x32-10 (Salmon et al. 2011)
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// FP32 -> BF16 with stochastic rounding: add 16 random bits below the kept
+// mantissa and truncate (unbiased: rounds up with probability equal to the
+// discarded fraction).
+__device__ __forceinline__ uint16_t f32_to_bf16_sr(float x, uint32_t r16)
+{
+    uint32_t b = __float_as_uint(x);
+    if ((b & 0x7f800000u) == 0x7f800000u) return (uint16_t)(b >> 16);   // inf / nan
+    return (uint16_t)((b + (r16 & 0xffffu)) >> 16);
+}
+
+// -------------------------------------------------------------- launchers
+
+template <typename T>
+void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch);
+template <typename T>
+void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep);
+template <typename T>
+void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m);
+template <typename T>
+void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp);
+template <typename T>
+void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
+                Source src, const int64_t *d_step, int kstep);
+template <typename T>
+void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp);
+template <typename T>
+void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
+                Source src, const int64_t *d_step, int kstep);
+void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by);
+
+// delta-f row pitch (elements) for nnode nodes of the given storage type
+int kinetic_pitch(int nnode, int f_dtype);
+// returns cudaErrorInvalidValue for an unsupported combination
+template <typename TA>
+cudaError_t launch_kinetic(cudaStream_t st, const KinArgs<TA> &a, int f_dtype, int num_sms);
+
+struct DiagArgs {
+    int ndim;
+    int64_t nx, ny, nz;
+    const void *f[6];
+    int64_t flen[6];
+    int precision;
+    double ch;        // dt / (mu0 dx)
+    double eps0_half_dv, mu0_half_dv;
+    const void *df;
+    int64_t nslots, nnode;
+    int pitch, f_dtype;
+    const double *dV; // per node, device
+};
+// out[0..6): energy, energy_plain, number, number_max_cell, number_abs, finite
+cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, int max_blocks, double *out);
+
+}  // namespace fp
+
+// ------------------------------------------------------------------ handle
+
+struct fdtd_plasma {
+    fdtd_grid_desc g;
+    fdtd_runtime_desc rt;
+    cudaStream_t stream;      // caller's stream
+    cudaStream_t cap;         // private stream used for graph capture
+    int num_sms;
+    double dt;
+    int64_t nx, ny, nz;
+    size_t esz;               // field element size
+    void *f[6];
+    int64_t flen[6];
+    void *psi[12];
+    int64_t psilen[12];
+    void *prof;               // CPML tables
+    int64_t prof_len;
+    void *mur_state;
+    int64_t *d_step;
+    int64_t steps_done;
+    // plasma
+    int has_plasma;
+    fdtd_plasma_desc pl;
+    int64_t nslots, nnode;
+    int pitch;
+    int32_t *slot_cell;
+    void *dens, *df, *jslot, *tab;
+    double *dV;               // per node (FP64) for the diagnostics
+    size_t df_esz;
+    // source
+    int has_source;
+    fdtd_source_desc src;
+    // graphs
+    cudaGraphExec_t g1, gk;
+    int gk_steps;
+    int graphs_valid;
+    // diagnostics scratch
+    double *diag_partials;
+    int diag_blocks;
+    double *diag_out;
+    std::string err;
+};

@@ -1,0 +1,330 @@
+"""Thin ctypes binding of the C ABI in ``include/fdtd_plasma.h``.
+
+The functions keep the C names (``fdtd_plasma_create`` ...) and only marshal
+arguments; every step of the computation runs in the CUDA library.  PyTorch
+supplies device memory (through the allocator callback) and the stream.  If
+the library has not been built the import fails loudly: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfdtd_plasma.so")
+
+# ---------------------------------------------------------------- constants
+FDTD_OK, FDTD_ERR_INVAL, FDTD_ERR_NOMEM, FDTD_ERR_CUDA = 0, -1, -2, -3
+FDTD_ERR_UNSTABLE, FDTD_ERR_NONFINITE, FDTD_ERR_TIMEOUT, FDTD_ERR_STATE = -4, -5, -6, -7
+STATUS = {0: "OK", -1: "INVAL", -2: "NOMEM", -3: "CUDA", -4: "UNSTABLE", -5: "NONFINITE", -6: "TIMEOUT", -7: "STATE"}
+PRECISION = {"f32": 0, "f64": 1}
+DF_DTYPE = {"f32": 0, "bf16": 1, "f64": 2}
+VGRID = {"signed1d": 0, "cart2d": 1, "speed3d": 2}
+NU_MODEL = {"nsv": 0, "const": 1}
+SRC_KIND = {"none": 0, "gauss_sine": 1, "gauss": 2}
+SRC_LOC = {"point": 0, "sheet": 1}
+QUANTITY = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7}
+
+
+class FdtdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fdtd_plasma error {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ---------------------------------------------------------------- structs
+class fdtd_grid_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("dx", ctypes.c_double), ("courant", ctypes.c_double),
+                ("cpml_cells", ctypes.c_int32), ("mur", ctypes.c_int32),
+                ("cpml_order", ctypes.c_double), ("cpml_sigma_factor", ctypes.c_double),
+                ("cpml_kappa_max", ctypes.c_double), ("cpml_alpha_min", ctypes.c_double),
+                ("cpml_alpha_max", ctypes.c_double)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class fdtd_runtime_desc(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+
+
+class fdtd_source_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("location", ctypes.c_int32),
+                ("amp", ctypes.c_double), ("fc", ctypes.c_double), ("tau", ctypes.c_double), ("t0", ctypes.c_double),
+                ("i", ctypes.c_int64), ("j", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("i0", ctypes.c_int64), ("i1", ctypes.c_int64), ("j0", ctypes.c_int64), ("j1", ctypes.c_int64)]
+
+
+class fdtd_plasma_desc(ctypes.Structure):
+    _fields_ = [("density", ctypes.c_void_p), ("density_on_device", ctypes.c_int32),
+                ("vgrid", ctypes.c_int32), ("nv", ctypes.c_int32), ("nv_perp", ctypes.c_int32),
+                ("te_ev", ctypes.c_double), ("vmax_vth", ctypes.c_double), ("nu0", ctypes.c_double),
+                ("nu_model", ctypes.c_int32), ("f_dtype", ctypes.c_int32), ("nonlinear", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class fdtd_diag(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("energy_plain", ctypes.c_double), ("number", ctypes.c_double),
+                ("number_max_cell", ctypes.c_double), ("number_abs", ctypes.c_double),
+                ("finite", ctypes.c_int64), ("step", ctypes.c_int64)]
+
+
+# ---------------------------------------------------------------- library
+_lib = None
+_lib_lock = threading.Lock()
+
+# name -> (restype, argtypes); every symbol the header declares
+SIGNATURES = {
+    "fdtd_plasma_create": (ctypes.c_int, [ctypes.POINTER(fdtd_grid_desc), ctypes.POINTER(fdtd_runtime_desc),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "fdtd_plasma_set_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_source_desc)]),
+    "fdtd_plasma_set_plasma": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_plasma_desc)]),
+    "fdtd_plasma_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "fdtd_plasma_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "fdtd_plasma_time_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "fdtd_plasma_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                               ctypes.c_int]),
+    "fdtd_plasma_write_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                                ctypes.c_int]),
+    "fdtd_plasma_quantity_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "fdtd_plasma_plasma_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                                ctypes.POINTER(ctypes.c_int64)]),
+    "fdtd_plasma_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "fdtd_plasma_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_diag)]),
+    "fdtd_plasma_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
+    "fdtd_plasma_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
+    "fdtd_plasma_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
+    "fdtd_plasma_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fdtd_plasma_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it is missing (no fallback)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(lib, h, rc):
+    if rc != FDTD_OK:
+        msg = lib.fdtd_plasma_last_error(h)
+        raise FdtdError(rc, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------- torch plumbing
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, handed to the C side
+    through the fdtd_runtime_desc callbacks."""
+
+    def __init__(self, device):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self.torch.empty(int(nbytes) + 256, dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        p = t.data_ptr()
+        p_al = (p + 255) & ~255
+        self.live[p_al] = t
+        return p_al
+
+    def _free(self, ptr, ctx):
+        self.live.pop(ptr, None)
+
+
+# ------------------------------------------------------------------ Solver
+class Solver:
+    """Owns one ``fdtd_plasma_t``.  All work runs on the given torch stream."""
+
+    def __init__(self, grid: dict, device: int = 0, stream=None, torch_allocator: bool = True):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.grid = dict(grid)
+        g = fdtd_grid_desc()
+        g.ndim = int(grid["ndim"])
+        g.precision = PRECISION[grid.get("precision", "f32")]
+        g.nx, g.ny, g.nz = int(grid.get("nx", 1)), int(grid.get("ny", 1)), int(grid.get("nz", 1))
+        g.dx, g.courant = float(grid["dx"]), float(grid.get("courant", 0.5))
+        g.cpml_cells, g.mur = int(grid.get("cpml_cells", 0)), int(grid.get("mur", 0))
+        g.cpml_order = float(grid.get("cpml_order", 3.0))
+        g.cpml_sigma_factor = float(grid.get("cpml_sigma_factor", 1.3))
+        g.cpml_kappa_max = float(grid.get("cpml_kappa_max", 7.0))
+        g.cpml_alpha_min = float(grid.get("cpml_alpha_min", 0.0))
+        g.cpml_alpha_max = float(grid.get("cpml_alpha_max", 0.05))
+        self._alloc = _TorchAllocator(self.device) if torch_allocator else None
+        rt = fdtd_runtime_desc()
+        rt.stream = self.stream.cuda_stream
+        if self._alloc:
+            rt.alloc, rt.free = self._alloc.alloc_cb, self._alloc.free_cb
+        rt.alloc_ctx = None
+        h = ctypes.c_void_p()
+        rc = self.lib.fdtd_plasma_create(ctypes.byref(g), ctypes.byref(rt), ctypes.byref(h))
+        _check(self.lib, None, rc)
+        self.h = h
+        self.precision = grid.get("precision", "f32")
+        self.f_dtype = None
+
+    @classmethod
+    def from_spec(cls, spec: dict, device: int = 0, stream=None) -> "Solver":
+        s = cls(spec["grid"], device=device, stream=stream)
+        if spec.get("source"):
+            s.set_source(**spec["source"])
+        if spec.get("plasma") is not None:
+            s.set_plasma(**spec["plasma"])
+        return s
+
+    # ---- configuration
+    def set_source(self, kind="gauss_sine", location="point", amp=1.0, fc=0.0, tau=1.0, t0=0.0,
+                   i=0, j=0, k=0, i0=0, i1=0, j0=0, j1=0):
+        d = fdtd_source_desc(SRC_KIND[kind], SRC_LOC[location], amp, fc, tau, t0, i, j, k, i0, i1, j0, j1)
+        _check(self.lib, self.h, self.lib.fdtd_plasma_set_source(self.h, ctypes.byref(d)))
+
+    def set_plasma(self, density, vgrid="signed1d", nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0,
+                   nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0):
+        torch = self.torch
+        if isinstance(density, torch.Tensor):
+            dens = density.to(self.device, torch.float64).contiguous()
+            ptr, on_dev = dens.data_ptr(), 1
+        else:
+            dens = np.ascontiguousarray(density, dtype=np.float64)
+            ptr, on_dev = dens.ctypes.data, 0
+        d = fdtd_plasma_desc()
+        d.density, d.density_on_device = ptr, on_dev
+        d.vgrid, d.nv, d.nv_perp = VGRID[vgrid], int(nv), int(nv_perp)
+        d.te_ev, d.vmax_vth, d.nu0 = float(te_ev), float(vmax_vth), float(nu0)
+        d.nu_model, d.f_dtype, d.nonlinear = NU_MODEL[nu_model], DF_DTYPE[f_dtype], int(nonlinear)
+        d.seed = int(seed)
+        _check(self.lib, self.h, self.lib.fdtd_plasma_set_plasma(self.h, ctypes.byref(d)))
+        self.f_dtype = f_dtype
+
+    # ---- stepping
+    def step(self, n: int = 1):
+        _check(self.lib, self.h, self.lib.fdtd_plasma_step(self.h, int(n)))
+
+    def time_kernels(self, n: int) -> dict:
+        """Eager, event-timed steps: average ms per launch of each kernel."""
+        out = (ctypes.c_double * 4)()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_time_kernels(self.h, int(n), out))
+        return dict(h=out[0], kinetic=out[1], e=out[2], step=out[3])
+
+    def reset(self):
+        _check(self.lib, self.h, self.lib.fdtd_plasma_reset(self.h))
+
+    # ---- I/O
+    def quantity_bytes(self, name: str) -> int:
+        return self.lib.fdtd_plasma_quantity_bytes(self.h, QUANTITY[name])
+
+    def _dtype(self, name):
+        torch = self.torch
+        if name == "df":
+            return {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[self.f_dtype]
+        return torch.float64 if self.precision == "f64" else torch.float32
+
+    def plasma_shape(self):
+        ns, nn = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_plasma_shape(self.h, ctypes.byref(ns), ctypes.byref(nn)))
+        return ns.value, nn.value
+
+    def read(self, name: str, device: bool = True):
+        """Quantity as a torch tensor on the device (stream-ordered) or, with
+        device=False, as a host numpy array (synchronous)."""
+        torch = self.torch
+        nb = self.quantity_bytes(name)
+        dt = self._dtype(name)
+        n = nb // torch.empty((), dtype=dt).element_size()
+        if device:
+            out = torch.empty(n, dtype=dt, device=self.device)
+            _check(self.lib, self.h, self.lib.fdtd_plasma_read_fields(self.h, QUANTITY[name], out.data_ptr(), nb, 1))
+        else:
+            out = torch.empty(n, dtype=dt)
+            _check(self.lib, self.h, self.lib.fdtd_plasma_read_fields(self.h, QUANTITY[name], out.data_ptr(), nb, 0))
+        if name == "df":
+            out = out.view(self.plasma_shape())
+        return out if device else (out.float().numpy() if dt == torch.bfloat16 else out.numpy())
+
+    def write(self, name: str, values):
+        torch = self.torch
+        dt = self._dtype(name)
+        if isinstance(values, torch.Tensor):
+            t = values.to(self.device, dt).contiguous()
+            on_dev = 1
+        else:
+            t = torch.as_tensor(np.ascontiguousarray(values)).to(dt).contiguous()
+            on_dev = 0
+        nb = t.numel() * t.element_size()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_write_fields(self.h, QUANTITY[name], t.data_ptr(), nb, on_dev))
+        if on_dev:
+            self.stream.synchronize()
+
+    def info(self):
+        dt, n = ctypes.c_double(), ctypes.c_int64()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_info(self.h, ctypes.byref(dt), ctypes.byref(n)))
+        return dt.value, n.value
+
+    @property
+    def dt(self) -> float:
+        return self.info()[0]
+
+    def diagnostics(self) -> dict:
+        d = fdtd_diag()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_diagnostics(self.h, ctypes.byref(d)))
+        return dict(energy=d.energy, energy_plain=d.energy_plain, number=d.number,
+                    number_max_cell=d.number_max_cell, number_abs=d.number_abs, finite=bool(d.finite), step=d.step)
+
+    def save_state(self, device: bool = True):
+        torch = self.torch
+        nb = self.lib.fdtd_plasma_state_bytes(self.h)
+        buf = torch.empty(nb, dtype=torch.uint8, device=self.device if device else "cpu")
+        _check(self.lib, self.h, self.lib.fdtd_plasma_save_state(self.h, buf.data_ptr(), nb, int(device)))
+        return buf
+
+    def load_state(self, buf):
+        nb = buf.numel()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_load_state(self.h, buf.data_ptr(), nb, int(buf.is_cuda)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fdtd_plasma_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,221 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 per field over the whole grid, and for J over all
+plasma cells, after the full run):
+  * FP64 instantiation: 1e-12 (rounding-order differences only)
+  * FP32 fields + FP32 delta f: 1e-4
+  * FP32 fields + BF16 delta f with stochastic rounding: 5e-3
+Sizes span several stencil tiles (32 x 8 / 32 x 4 x 2) with ragged tails.
+"""
+import numpy as np
+import pytest
+
+from fdtd_inputs import OMEGA0, critical_density, pulse_params, spec_1d_slab, spec_2d_cylinder, spec_3d_slab
+from tests.adapters import FIELDS, compare, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-4, "bf16": 5e-3}
+
+
+def _solver(spec):
+    from paper_2211_05647_gb300 import Solver
+    return Solver.from_spec(spec)
+
+
+def _run_pair(oracle_lib, spec, steps):
+    sim = oracle_sim(oracle_lib, spec)
+    s = _solver(spec)
+    sim.step(steps)
+    s.step(steps)
+    return s, sim
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_1d_slab_full_run(oracle_lib, prec):
+    """The 1-D slab workload (Nz = 2000, Nv = 64, Mur, source at node 100),
+    run long enough for the pulse to cross the slab."""
+    spec = spec_1d_slab(precision=prec, steps=2600)
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 1)
+    assert np.abs(sim.get("j")).max() > 0
+    assert max(errs.values()) <= TOL[prec], errs
+
+
+def _small_2d(prec="f32", f_dtype="f32", nx=200, ny=150, R=40, steps=500, nv=32, nv_perp=32):
+    spec = spec_2d_cylinder(n=nx, ny=ny, R=R, center=(nx * 0.55, ny * 0.5), src=(int(nx * 0.55) - R - 12, ny // 2),
+                            nv=nv, nv_perp=nv_perp, steps=steps, precision=prec, f_dtype=f_dtype, seed=11)
+    return spec
+
+
+@pytest.mark.parametrize("prec,fdt", [("f64", "f64"), ("f32", "f32"), ("f32", "bf16")])
+def test_2d_tmz_cylinder(oracle_lib, prec, fdt):
+    spec = _small_2d(prec, fdt)
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 2)
+    assert np.abs(sim.get("j")).max() > 0
+    assert max(errs.values()) <= TOL[fdt if fdt == "bf16" else prec], errs
+
+
+def _small_3d(prec="f32", f_dtype="f32", n=(40, 36, 64), steps=220, nv=32):
+    nx, ny, nz = n
+    return spec_3d_slab(n=nx, ny=ny, nz=nz, cpml=8, slab=(28, 44), src_k=12, nv=nv, steps=steps,
+                        precision=prec, f_dtype=f_dtype, seed=13)
+
+
+@pytest.mark.parametrize("prec,fdt", [("f64", "f64"), ("f32", "f32"), ("f32", "bf16")])
+def test_3d_slab(oracle_lib, prec, fdt):
+    spec = _small_3d(prec, fdt)
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 3)
+    assert np.abs(sim.get("j")).max() > 0
+    assert max(errs.values()) <= TOL[fdt if fdt == "bf16" else prec], errs
+
+
+@pytest.mark.parametrize("vgrid,nv,nvp", [("speed3d", 31, 1), ("signed1d", 48, 1), ("cart2d", 8, 6),
+                                         ("signed1d", 2, 1), ("signed1d", 512, 1)])
+def test_velocity_grids_and_ragged_rows(oracle_lib, vgrid, nv, nvp):
+    """Non-power-of-two and tiny / large node counts (padded rows) on every grid kind."""
+    spec = spec_1d_slab(nz=400, slab=(150, 260), src_k=40, precision="f64", steps=700, nv=nv)
+    spec["plasma"].update(vgrid=vgrid, nv=nv, nv_perp=nvp)
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 1)
+    assert np.abs(sim.get("j")).max() > 0
+    assert max(errs.values()) <= 1e-12, errs
+    df = s.read("df", device=False)
+    assert np.allclose(df, sim.get("df"), rtol=1e-11, atol=1e-12 * np.abs(sim.get("df")).max())
+
+
+def test_const_nu_and_random_initial_state(oracle_lib):
+    """Random E, H and delta f as the initial state (2-D, CPML, const nu)."""
+    spec = _small_2d("f64", "f64", nx=130, ny=97, R=30, steps=150)
+    spec["plasma"]["nu_model"] = "const"
+    sim = oracle_sim(oracle_lib, spec)
+    s = _solver(spec)
+    rng = np.random.default_rng(5)
+    for nm in FIELDS[2]:
+        v = rng.standard_normal(sim.get(nm).size) * (1.0 if nm[0] == "e" else 1 / 377.0)
+        if nm == "ez":
+            v.reshape(97, 130)[0, :] = 0
+            v.reshape(97, 130)[:, 0] = 0
+        sim.set(nm, v)
+        s.write(nm, v)
+    df0 = rng.standard_normal((sim.nslots, sim.nnode)) * 1e-2
+    sim.set("df", df0)
+    s.write("df", df0)
+    sim.step(150)
+    s.step(150)
+    errs = compare(s, sim, 2)
+    assert max(errs.values()) <= 1e-12, errs
+
+
+def test_vacuum_and_no_plasma_cells(oracle_lib):
+    """No plasma at all, and a density that is nonzero only on PEC nodes (no slots)."""
+    spec = _small_2d("f64", "f64", nx=64, ny=64, R=10, steps=120)
+    dens = np.zeros(64 * 64)
+    dens.reshape(64, 64)[0, :] = 1e17   # PEC row j = 0: excluded
+    spec["plasma"]["density"] = dens
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    assert sim.nslots == 0 and s.plasma_shape()[0] == 0
+    errs = compare(s, sim, 2)
+    assert max(errs.values()) <= 1e-12, errs
+    spec["plasma"] = None
+    s2, sim2 = _run_pair(oracle_lib, spec, spec["steps"])
+    assert max(compare(s2, sim2, 2).values()) <= 1e-12
+
+
+def test_step_chunking_is_invisible(oracle_lib):
+    """step(1) x N and step(N) (graph chunk of 32 + singles) give identical state."""
+    spec = _small_2d("f32", "f32", nx=96, ny=80, R=20, steps=70)
+    a, b = _solver(spec), _solver(spec)
+    for _ in range(70):
+        a.step(1)
+    b.step(70)
+    for nm in FIELDS[2] + ["j", "df"]:
+        assert np.array_equal(a.read(nm, device=False), b.read(nm, device=False)), nm
+
+
+def test_checkpoint_resume_bit_identical(oracle_lib):
+    spec = _small_3d("f32", "bf16", n=(24, 20, 40), steps=60)
+    a = _solver(spec)
+    a.step(60)
+    b = _solver(spec)
+    b.step(30)
+    blob = b.save_state(device=False)
+    c = _solver(spec)
+    c.load_state(blob)
+    assert c.info()[1] == 30
+    c.step(30)
+    for nm in FIELDS[3] + ["j", "df"]:
+        assert np.array_equal(a.read(nm, device=False), c.read(nm, device=False)), nm
+
+
+def test_diagnostics_match_oracle(oracle_lib):
+    spec = _small_2d("f64", "f64", nx=100, ny=90, R=25, steps=400)
+    spec["plasma"]["density"] = spec["plasma"]["density"]
+    s, sim = _run_pair(oracle_lib, spec, 400)
+    dg, do = s.diagnostics(), sim.diag()
+    for k in ("energy", "energy_plain", "number_abs"):
+        assert dg[k] == pytest.approx(do[k], rel=1e-11), k
+    assert abs(dg["number"]) <= 1e-12 * do["number_abs"]
+    assert dg["finite"] and dg["step"] == 400
+
+
+def test_energy_invariant_gpu_fp32():
+    """Lossless PEC cavity, random fields: the FP64 diagnostic of the FP32 run
+    drifts by at most 1e-5 relative."""
+    from paper_2211_05647_gb300 import Solver
+    s = Solver(dict(ndim=3, nx=48, ny=40, nz=36, dx=1e-3, courant=0.5, precision="f32"))
+    rng = np.random.default_rng(2)
+    for nm in FIELDS[3]:
+        v = rng.standard_normal(48 * 40 * 36).reshape(36, 40, 48) * (1.0 if nm[0] == "e" else 1 / 377.0)
+        if nm == "ex":
+            v[:, 0, :] = 0; v[0, :, :] = 0
+        if nm == "ey":
+            v[:, :, 0] = 0; v[0, :, :] = 0
+        if nm == "ez":
+            v[:, :, 0] = 0; v[:, 0, :] = 0
+        s.write(nm, v.ravel())
+    W0 = s.diagnostics()["energy"]
+    for _ in range(10):
+        s.step(100)
+        assert abs(s.diagnostics()["energy"] - W0) <= 1e-5 * W0
+
+
+def test_abi_errors():
+    from paper_2211_05647_gb300 import FdtdError, Solver
+    from paper_2211_05647_gb300 import fdtd_plasma as F
+    with pytest.raises(FdtdError) as e:
+        Solver(dict(ndim=3, nx=16, ny=16, nz=16, dx=1e-3, courant=0.6))
+    assert e.value.code == F.FDTD_ERR_UNSTABLE
+    with pytest.raises(FdtdError) as e:
+        Solver(dict(ndim=2, nx=2, ny=16, dx=1e-3))
+    assert e.value.code == F.FDTD_ERR_INVAL
+    with pytest.raises(FdtdError):
+        Solver(dict(ndim=2, nx=30, ny=30, dx=1e-3, cpml_cells=10))
+    s = Solver(dict(ndim=1, nz=100, dx=1e-3, mur=1, precision="f32"))
+    with pytest.raises(FdtdError) as e:
+        s.set_plasma(np.full(101, np.nan), f_dtype="f32")
+    assert e.value.code == F.FDTD_ERR_NONFINITE
+    with pytest.raises(FdtdError):
+        s.set_plasma(np.full(101, 1e17), f_dtype="f64")        # f64 storage on an f32 grid
+    with pytest.raises(FdtdError) as e:
+        s.set_plasma(np.full(101, 1e30), f_dtype="f32")        # w_p dt too large
+    assert e.value.code == F.FDTD_ERR_UNSTABLE
+    with pytest.raises(FdtdError):
+        s.set_source(kind="gauss", k=0, tau=1e-10)            # Mur node is not a source node
+    s.set_plasma(np.full(101, 1e17), f_dtype="f32")
+    s.step(3)
+    with pytest.raises(FdtdError) as e:
+        s.set_plasma(np.full(101, 1e17), f_dtype="f32")
+    assert e.value.code == F.FDTD_ERR_STATE
+    with pytest.raises(FdtdError):
+        s.step(-1)
+    lib = F.load_library()
+    assert lib.fdtd_plasma_step(None, 1) == F.FDTD_ERR_INVAL
+    lib.fdtd_plasma_destroy(None)
+    buf = np.zeros(7)
+    assert lib.fdtd_plasma_read_fields(s.h, 0, buf.ctypes.data, 56, 0) == F.FDTD_ERR_INVAL
+    s.reset()
+    s.set_plasma(np.full(101, 1e17), f_dtype="bf16")
+    assert s.info()[1] == 0
