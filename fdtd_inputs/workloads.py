@@ -139,9 +139,15 @@ def spec_3d_slab(n=512, ny=None, nz=None, ppw=20, cpml=8, slab=(192, 320), src_k
         steps=steps)
 
 
-# The benchmark workloads (full sizes) by name
+# The benchmark workloads (full sizes) by name, plus reduced profiling cases
 WORKLOADS = {
     "1d_slab_fp64": lambda: spec_1d_slab(),
+    "1d_slab_fp32": lambda: spec_1d_slab(precision="f32"),
     "2d_tmz_4096_kinetic": lambda: spec_2d_cylinder(),
+    "2d_tmz_4096_kinetic_bf16": lambda: spec_2d_cylinder(f_dtype="bf16"),
     "3d_512_kinetic_bf16": lambda: spec_3d_slab(),
+    "3d_512_kinetic_f32": lambda: spec_3d_slab(f_dtype="f32"),
+    # profiling cases: same recipes at half the lengths (inputs still larger than L2)
+    "2d_tmz_2048_kinetic": lambda: spec_2d_cylinder(n=2048, R=256),
+    "3d_256_kinetic_bf16": lambda: spec_3d_slab(n=256, slab=(96, 160), src_k=12),
 }

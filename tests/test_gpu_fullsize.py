@@ -1,0 +1,62 @@
+"""Full-size parity: the benchmark's own workloads (the launch configuration
+bench.py times) from a seeded random initial E/H state, a few steps, against
+the FP64 oracle run at the same full size.  Every field value and every J is
+compared (relative L2, field-vector normalisation)."""
+import os
+
+import numpy as np
+import pytest
+
+from fdtd_inputs import WORKLOADS, random_state
+from tests.adapters import FIELDS, compare, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+
+def _mem_available_gb():
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable"):
+                return int(ln.split()[1]) / 1e6
+    except Exception:
+        pass
+    return 0.0
+
+
+def _zero_pec(ndim, sizes, st):
+    nx, ny, nz = sizes
+    if ndim == 2:
+        st["ez"].reshape(ny, nx)[0, :] = 0
+        st["ez"].reshape(ny, nx)[:, 0] = 0
+    else:
+        ex, ey, ez = (st[n].reshape(nz, ny, nx) for n in ("ex", "ey", "ez"))
+        ex[:, 0, :] = 0; ex[0] = 0
+        ey[:, :, 0] = 0; ey[0] = 0
+        ez[:, :, 0] = 0; ez[:, 0, :] = 0
+
+
+@pytest.mark.parametrize("name,steps,tol,min_gb", [("2d_tmz_4096_kinetic", 4, 1e-5, 24),
+                                                    ("3d_512_kinetic_bf16", 3, 5e-3, 80)])
+def test_full_size_random_state(oracle_lib, name, steps, tol, min_gb):
+    if _mem_available_gb() < min_gb:
+        pytest.skip(f"needs {min_gb} GB of host memory for the FP64 oracle at full size")
+    from paper_2211_05647_gb300 import Solver
+    spec = WORKLOADS[name]()
+    g = spec["grid"]
+    nd = g["ndim"]
+    n = g["nx"] * g["ny"] * (g["nz"] if nd == 3 else 1)
+    st = random_state({f: n for f in FIELDS[nd]}, seed=99)
+    _zero_pec(nd, (g["nx"], g["ny"], g["nz"]), st)
+    s = Solver.from_spec(spec)
+    for f, v in st.items():
+        s.write(f, v.astype(np.float32))
+    sim = oracle_sim(oracle_lib, spec)
+    for f, v in st.items():
+        sim.set(f, v.astype(np.float32).astype(np.float64))   # same rounded start on both sides
+    del st
+    s.step(steps)
+    sim.step(steps)
+    errs = compare(s, sim, nd)
+    print(f"{name}: " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
+    assert sim.nslots == s.plasma_shape()[0] > 0
+    assert max(errs.values()) <= tol, errs

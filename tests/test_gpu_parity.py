@@ -23,6 +23,10 @@ def _solver(spec):
     return Solver.from_spec(spec)
 
 
+def _report(name, errs):
+    print(f"{name}: " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
+
+
 def _run_pair(oracle_lib, spec, steps):
     sim = oracle_sim(oracle_lib, spec)
     s = _solver(spec)
@@ -38,6 +42,7 @@ def test_1d_slab_full_run(oracle_lib, prec):
     spec = spec_1d_slab(precision=prec, steps=2600)
     s, sim = _run_pair(oracle_lib, spec, spec["steps"])
     errs = compare(s, sim, 1)
+    _report(f"1d {prec}", errs)
     assert np.abs(sim.get("j")).max() > 0
     assert max(errs.values()) <= TOL[prec], errs
 
@@ -53,13 +58,14 @@ def test_2d_tmz_cylinder(oracle_lib, prec, fdt):
     spec = _small_2d(prec, fdt)
     s, sim = _run_pair(oracle_lib, spec, spec["steps"])
     errs = compare(s, sim, 2)
+    _report(f"2d {prec} {fdt}", errs)
     assert np.abs(sim.get("j")).max() > 0
     assert max(errs.values()) <= TOL[fdt if fdt == "bf16" else prec], errs
 
 
-def _small_3d(prec="f32", f_dtype="f32", n=(40, 36, 64), steps=220, nv=32):
+def _small_3d(prec="f32", f_dtype="f32", n=(40, 36, 64), steps=220, nv=32, slab=(28, 44), src_k=12, cpml=8):
     nx, ny, nz = n
-    return spec_3d_slab(n=nx, ny=ny, nz=nz, cpml=8, slab=(28, 44), src_k=12, nv=nv, steps=steps,
+    return spec_3d_slab(n=nx, ny=ny, nz=nz, cpml=cpml, slab=slab, src_k=src_k, nv=nv, steps=steps,
                         precision=prec, f_dtype=f_dtype, seed=13)
 
 
@@ -68,6 +74,7 @@ def test_3d_slab(oracle_lib, prec, fdt):
     spec = _small_3d(prec, fdt)
     s, sim = _run_pair(oracle_lib, spec, spec["steps"])
     errs = compare(s, sim, 3)
+    _report(f"3d {prec} {fdt}", errs)
     assert np.abs(sim.get("j")).max() > 0
     assert max(errs.values()) <= TOL[fdt if fdt == "bf16" else prec], errs
 
@@ -136,7 +143,7 @@ def test_step_chunking_is_invisible(oracle_lib):
 
 
 def test_checkpoint_resume_bit_identical(oracle_lib):
-    spec = _small_3d("f32", "bf16", n=(24, 20, 40), steps=60)
+    spec = _small_3d("f32", "bf16", n=(24, 20, 40), steps=60, slab=(20, 30), src_k=9, cpml=6)
     a = _solver(spec)
     a.step(60)
     b = _solver(spec)
