@@ -11,8 +11,8 @@
 //
 // Layout: rows of `pitch` elements, [slot][node], pitch = a power-of-two
 // number of 16-byte vectors >= nnode (padding nodes have alpha = beta = w = 0
-// and stay 0).  L lanes share a row (L = min(32, vectors per row)), each lane
-// holding VPL vectors; a warp covers 32/L rows.  The whole row is loaded
+// and stay 0).  L lanes share a row, each lane holding VPL >= 4 vectors when
+// the row has that many; a warp covers 32/L rows.  The whole row is loaded
 // before any arithmetic so each lane has VPL 16-byte loads in flight, the
 // loads/stores use the streaming (evict-first) cache hint because delta f is
 // far larger than L2, and the per-node tables sit in shared memory.
@@ -141,20 +141,25 @@ __global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
     const int64_t step = *a.d_step + a.kstep;
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
 
+    // the slot -> cell index of the next row group is fetched one iteration
+    // ahead, so the E gather of a row issues together with its delta-f loads
+    int64_t row = wg * R + sub;
+    int32_t cell_next = row < a.nslots ? __ldg(a.slot_cell + row) : 0;
     for (int64_t base = wg * R; base < a.nslots; base += nw * R) {
-        const int64_t row = base + sub;
+        row = base + sub;
         const bool valid = row < a.nslots;
+        const int32_t cell = cell_next;
         V v[VPL];
         TA E = TA(0), nE = TA(0);
-        int32_t cell = 0;
         V *rp = reinterpret_cast<V *>(a.df) + (valid ? row : 0) * (a.pitch / VEC);
         if (valid) {
-            cell = __ldg(a.slot_cell + row);
 #pragma unroll
             for (int q = 0; q < VPL; ++q) v[q] = __ldcs(rp + q * L + l);
             E = a.E[cell];
             nE = __ldg(a.dens + row) * E;
         }
+        const int64_t row_next = row + nw * R;
+        cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
         TA s = TA(0), c = TA(0);
         if (valid) {
 #pragma unroll
@@ -228,15 +233,18 @@ static cudaError_t run(cudaStream_t st, const KinArgs<TA> &a, int num_sms)
 template <typename TS, typename TA>
 static cudaError_t dispatch(cudaStream_t st, const KinArgs<TA> &a, int num_sms)
 {
-    const int V = a.pitch / Vec<TS>::n;   // vectors per row, a power of two
+    // vectors per row (a power of two): lanes per row L chosen so that every
+    // lane keeps at least 4 sixteen-byte loads in flight (fewer only for rows
+    // shorter than 4 vectors), at most 32 lanes
+    const int V = a.pitch / Vec<TS>::n;
     switch (V) {
     case 1: return run<TS, TA, 1, 1>(st, a, num_sms);
-    case 2: return run<TS, TA, 1, 2>(st, a, num_sms);
-    case 4: return run<TS, TA, 1, 4>(st, a, num_sms);
-    case 8: return run<TS, TA, 1, 8>(st, a, num_sms);
-    case 16: return run<TS, TA, 1, 16>(st, a, num_sms);
-    case 32: return run<TS, TA, 1, 32>(st, a, num_sms);
-    case 64: return run<TS, TA, 2, 32>(st, a, num_sms);
+    case 2: return run<TS, TA, 2, 1>(st, a, num_sms);
+    case 4: return run<TS, TA, 4, 1>(st, a, num_sms);
+    case 8: return run<TS, TA, 4, 2>(st, a, num_sms);
+    case 16: return run<TS, TA, 4, 4>(st, a, num_sms);
+    case 32: return run<TS, TA, 4, 8>(st, a, num_sms);
+    case 64: return run<TS, TA, 4, 16>(st, a, num_sms);
     case 128: return run<TS, TA, 4, 32>(st, a, num_sms);
     case 256: return run<TS, TA, 8, 32>(st, a, num_sms);
     case 512: return run<TS, TA, 16, 32>(st, a, num_sms);
