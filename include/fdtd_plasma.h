@@ -200,6 +200,47 @@ size_t fdtd_plasma_state_bytes(fdtd_plasma_t h);
 int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int buf_is_device);
 int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int buf_is_device);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free diagnostics.  The paper has no counterpart: this is a
+ * library service for callers that cannot allocate device memory when they
+ * need a diagnostic -- monitoring or watchdog code that must not take the
+ * allocator's locks or trigger cudaMalloc's implicit synchronisation,
+ * frameworks that route every device allocation through their own pool, and
+ * code running close to the device's memory limit.  It computes the same
+ * quantities as fdtd_plasma_diagnostics (energy, energy_plain, number,
+ * number_max_cell, number_abs, finite -> out[0..5]) from caller-owned device
+ * arrays, allocating nothing (no cudaMalloc, no cudaFree, no allocating
+ * library call).
+ *   in   : the arrays, in the layouts of fdtd_plasma_read_fields (fields by
+ *          FDTD_EX..FDTD_HZ, NULL where the dimensionality has none; delta f
+ *          as packed [nslots][nnode] rows of f_dtype, dV one double per node;
+ *          df and dV may be NULL when nslots == 0).
+ *   out  : 6 doubles; device memory (out_is_device = 1, stream-ordered) or
+ *          host memory (out_is_device = 0, the stream is synchronised).
+ *   stream: cudaStream_t the work is issued on (NULL = legacy default stream).
+ * Scratch is a fixed file-scope device array of 8192 tiles (about 459 KB per
+ * GPU that loads the library, held until the process exits).  A call needs
+ * ceil(field nodes / 65536) + ceil(nslots / 16384) tiles; more returns
+ * FDTD_ERR_INVAL with a message (fdtd_plasma_last_error(NULL)).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  All calls share the
+ * array: calls that overlap on the GPU race (serialise them, e.g. on one
+ * stream).  Nothing needs clearing between calls. */
+typedef struct {
+    int32_t ndim;            /* 1, 2 or 3 */
+    int32_t precision;       /* FDTD_F32 or FDTD_F64: element type of the fields */
+    int64_t nx, ny, nz;      /* cells, as in fdtd_grid_desc */
+    double dx, courant;      /* as in fdtd_grid_desc (fix the vacuum curl of the energy) */
+    const void *fields[6];   /* device arrays, index FDTD_EX..FDTD_HZ */
+    const void *df;          /* device delta f rows, or NULL */
+    int32_t f_dtype;         /* FDTD_DF_F32 / FDTD_DF_BF16 / FDTD_DF_F64 */
+    int32_t reserved;
+    int64_t nslots, nnode;
+    const double *dV;        /* device, nnode volume elements */
+} fdtd_diag_arrays;
+
+int fdtd_diagnostics_noalloc(const fdtd_diag_arrays *in, double *out, int out_is_device, void *stream);
+
 /* Last error message of the handle (or of the last failed create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *fdtd_plasma_last_error(fdtd_plasma_t h);

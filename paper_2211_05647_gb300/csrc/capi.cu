@@ -309,6 +309,12 @@ size_t field_bytes(const fdtd_plasma *h, int q) { return h->f[q] ? (size_t)h->fl
 
 }  // namespace
 
+int fp_set_global_error(int code, const char *msg)
+{
+    g_create_error = msg;
+    return code;
+}
+
 // =================================================================== ABI
 
 extern "C" {

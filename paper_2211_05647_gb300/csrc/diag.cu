@@ -5,6 +5,9 @@
 // Pass 1: grid-stride blocks accumulate FP64 partials (one row of 6 per block)
 // into a scratch buffer; pass 2: one block reduces the rows.  The fields are
 // read once; delta f rows are read one warp per row.
+#include <cmath>
+#include <cstdio>
+
 #include "internal.cuh"
 
 namespace fp {
@@ -169,3 +172,180 @@ cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, in
 }
 
 }  // namespace fp
+
+// ===================================================================
+// Allocation-free variant of the diagnostics reduction.
+//
+// fdtd_diagnostics_noalloc() serves callers that cannot allocate device
+// memory at the moment they need a diagnostic: monitoring or watchdog code
+// that must not take the allocator's locks or trigger cudaMalloc's implicit
+// device synchronisation, frameworks that route every device allocation
+// through their own pool and forbid direct cudaMalloc, and code running close
+// to the device's memory limit.  The caller passes the device arrays (inputs)
+// and the result location (output); the per-tile partial sums live in the
+// file-scope array below, which every GPU that loads this library keeps
+// (kNoAllocMaxTiles * 7 + 8 doubles, about 459 KB) until the process exits.
+//
+// Work is split into fixed tiles (65536 field nodes or 16384 plasma slots
+// each), one block per tile, so a call needs 1 + ceil(nodes / 65536) +
+// ceil(slots / 16384) <= 8192 tiles; larger problems are rejected with
+// FDTD_ERR_INVAL.  Every scratch entry a call reads is written earlier by
+// the same call, so nothing has to be cleared between calls; calls share the
+// array, and calls that overlap on the GPU (e.g. on two streams) race.
+// ===================================================================
+
+#include <mutex>
+
+namespace fp {
+
+constexpr int kNoAllocMaxTiles = 8192;
+constexpr int64_t kNoAllocCellsPerTile = 65536;
+constexpr int64_t kNoAllocSlotsPerTile = 16384;
+
+// per-tile partial rows (7 doubles each, the layout k_diag_final reads) + the
+// 6-double result area used when the caller wants the result on the host
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxTiles * 7 + 8];
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_diag_tiles(DiagArgs a, int64_t field_tiles, double *partials)
+{
+    __shared__ double red[6][8];
+    __shared__ int sfin[8];
+    double we = 0, wh = 0, wh2 = 0, num = 0, nmax = 0, nabs = 0;
+    int fin = 1;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t tile = blockIdx.x;
+    if (tile < field_tiles) {
+        const int64_t ncells = a.ndim == 1 ? a.nz + 1 : a.nx * a.ny * a.nz;
+        const int64_t c0 = tile * kNoAllocCellsPerTile;
+        const int64_t c1 = min(c0 + kNoAllocCellsPerTile, ncells);
+        for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) field_terms<T>(a, c, we, wh, wh2, fin);
+    } else {
+        const int64_t s0 = (tile - field_tiles) * kNoAllocSlotsPerTile;
+        const int64_t s1 = min(s0 + kNoAllocSlotsPerTile, a.nslots);
+        for (int64_t r = s0 + w; r < s1; r += blockDim.x >> 5) {
+            double sr = 0, sa = 0;
+            for (int64_t j = lane; j < a.nnode; j += 32) {
+                double v = df_val<T>(a, r, j);
+                sr += v * a.dV[j];
+                sa += fabs(v) * a.dV[j];
+                fin &= isfinite(v);
+            }
+            sr = warp_sum(sr);
+            sa = warp_sum(sa);
+            if (lane == 0) {
+                num += sr;
+                nabs += sa;
+                nmax = fmax(nmax, fabs(sr));
+            }
+        }
+    }
+    we = warp_sum(we); wh = warp_sum(wh); wh2 = warp_sum(wh2);
+    num = warp_sum(num); nabs = warp_sum(nabs); nmax = warp_max(nmax);
+    fin = __all_sync(0xffffffffu, fin);
+    if (lane == 0) {
+        red[0][w] = we; red[1][w] = wh; red[2][w] = wh2; red[3][w] = num; red[4][w] = nabs; red[5][w] = nmax;
+        sfin[w] = fin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double o[6] = {0, 0, 0, 0, 0, 0};
+        int f = 1;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+            for (int t = 0; t < 5; ++t) o[t] += red[t][q];
+            o[5] = fmax(o[5], red[5][q]);
+            f &= sfin[q];
+        }
+        double *p = partials + tile * 7;
+        for (int t = 0; t < 6; ++t) p[t] = o[t];
+        p[6] = f ? 1.0 : 0.0;
+    }
+}
+
+}  // namespace fp
+
+namespace {
+std::mutex g_noalloc_mu;
+double *g_noalloc_dev_ptr[256];   // device address of g_noalloc_scratch, per device ordinal
+bool g_noalloc_ready[256];
+}  // namespace
+
+extern "C" int fdtd_diagnostics_noalloc(const fdtd_diag_arrays *in, double *out, int out_is_device, void *stream)
+{
+    using namespace fp;
+    if (!in || !out) return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_diagnostics_noalloc: NULL argument");
+    if (in->ndim < 1 || in->ndim > 3 || (in->precision != FDTD_F32 && in->precision != FDTD_F64) ||
+        !(in->dx > 0) || !(in->courant > 0))
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_diagnostics_noalloc: bad ndim, precision, dx or courant");
+    const int64_t nx = in->ndim >= 2 ? in->nx : 1, ny = in->ndim >= 2 ? in->ny : 1;
+    const int64_t nz = in->ndim == 2 ? 1 : in->nz;
+    if (nx < 1 || ny < 1 || nz < 1) return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_diagnostics_noalloc: bad sizes");
+    static const int need1[6] = {1, 0, 0, 0, 1, 0}, need2[6] = {0, 0, 1, 1, 1, 0};
+    for (int q = 0; q < 6; ++q) {
+        const bool need = in->ndim == 3 || (in->ndim == 1 ? need1[q] : need2[q]);
+        if (need && !in->fields[q])
+            return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_diagnostics_noalloc: a field array is NULL");
+    }
+    if (in->nslots < 0 || (in->nslots > 0 && (!in->df || !in->dV || in->nnode < 1)) ||
+        (in->nslots > 0 && in->f_dtype != FDTD_DF_F32 && in->f_dtype != FDTD_DF_BF16 && in->f_dtype != FDTD_DF_F64))
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_diagnostics_noalloc: bad delta-f description");
+    const int64_t ncells = in->ndim == 1 ? nz + 1 : nx * ny * nz;
+    const int64_t field_tiles = (ncells + kNoAllocCellsPerTile - 1) / kNoAllocCellsPerTile;
+    const int64_t slot_tiles = (in->nslots + kNoAllocSlotsPerTile - 1) / kNoAllocSlotsPerTile;
+    const int64_t ntiles = field_tiles + slot_tiles;
+    if (ntiles > kNoAllocMaxTiles) {
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "fdtd_diagnostics_noalloc: problem needs %lld tiles of scratch, the fixed maximum is %d "
+                 "(%lld field nodes / 65536 + %lld slots / 16384); use fdtd_plasma_diagnostics",
+                 (long long)ntiles, kNoAllocMaxTiles, (long long)ncells, (long long)in->nslots);
+        return fp_set_global_error(FDTD_ERR_INVAL, msg);
+    }
+    // once per device: the device address of the file-scope scratch array
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256)
+        return fp_set_global_error(FDTD_ERR_CUDA, "fdtd_diagnostics_noalloc: cudaGetDevice failed");
+    double *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ready[dev]) {
+            e = cudaGetSymbolAddress((void **)&g_noalloc_dev_ptr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return fp_set_global_error(FDTD_ERR_CUDA, "fdtd_diagnostics_noalloc: cudaGetSymbolAddress failed");
+            g_noalloc_ready[dev] = true;
+        }
+        scratch = g_noalloc_dev_ptr[dev];
+    }
+    const double c0 = 299792458.0, eps0 = 8.8541878128e-12, mu0 = 1.0 / (eps0 * c0 * c0);
+    const double dt = in->courant * in->dx / c0;
+    const double dvol = std::pow(in->dx, in->ndim);
+    DiagArgs a{};
+    a.ndim = in->ndim;
+    a.nx = nx; a.ny = ny; a.nz = nz;
+    for (int q = 0; q < 6; ++q) a.f[q] = in->fields[q];
+    a.precision = in->precision;
+    a.ch = dt / (mu0 * in->dx);
+    a.eps0_half_dv = 0.5 * eps0 * dvol;
+    a.mu0_half_dv = 0.5 * mu0 * dvol;
+    a.df = in->df;
+    a.nslots = in->nslots;
+    a.nnode = in->nnode;
+    a.pitch = (int)in->nnode;    // caller rows are packed
+    a.f_dtype = in->f_dtype;
+    a.dV = in->dV;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *res = out_is_device ? out : scratch + (int64_t)kNoAllocMaxTiles * 7;
+    if (in->precision == FDTD_F64)
+        k_diag_tiles<double><<<(unsigned)ntiles, 256, 0, st>>>(a, field_tiles, scratch);
+    else
+        k_diag_tiles<float><<<(unsigned)ntiles, 256, 0, st>>>(a, field_tiles, scratch);
+    k_diag_final<<<1, 32, 0, st>>>(scratch, (int)ntiles, a.eps0_half_dv, a.mu0_half_dv, res);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && !out_is_device) {
+        e = cudaMemcpyAsync(out, res, 6 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    return FDTD_OK;
+}

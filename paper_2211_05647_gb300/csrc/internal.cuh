@@ -137,6 +137,9 @@ cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, in
 
 }  // namespace fp
 
+// Record msg as the library-wide error (fdtd_plasma_last_error(NULL)) and return code.
+int fp_set_global_error(int code, const char *msg);
+
 // ------------------------------------------------------------------ handle
 
 struct fdtd_plasma {

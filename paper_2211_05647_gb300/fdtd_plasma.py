@@ -76,6 +76,15 @@ class fdtd_diag(ctypes.Structure):
                 ("finite", ctypes.c_int64), ("step", ctypes.c_int64)]
 
 
+class fdtd_diag_arrays(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("dx", ctypes.c_double), ("courant", ctypes.c_double),
+                ("fields", ctypes.c_void_p * 6), ("df", ctypes.c_void_p),
+                ("f_dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("nslots", ctypes.c_int64), ("nnode", ctypes.c_int64), ("dV", ctypes.c_void_p)]
+
+
 # ---------------------------------------------------------------- library
 _lib = None
 _lib_lock = threading.Lock()
@@ -103,6 +112,8 @@ SIGNATURES = {
     "fdtd_plasma_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fdtd_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(fdtd_diag_arrays), ctypes.POINTER(ctypes.c_double),
+                                                ctypes.c_int, ctypes.c_void_p]),
     "fdtd_plasma_destroy": (None, [ctypes.c_void_p]),
 }
 

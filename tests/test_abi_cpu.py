@@ -16,7 +16,7 @@ def _declared():
         if fn.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", fn)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(fdtd_plasma_\w+)\s*\(", txt))
+            names |= set(re.findall(r"\b(fdtd_\w+)\s*\(", txt))
     return names
 
 
