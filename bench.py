@@ -63,6 +63,9 @@ def sample_spec(name: str):
     if name.startswith("3d_512"):
         return (spec_3d_slab(n=64, cpml=8, slab=(24, 40), src_k=12),
                 "3-D 64^3, slab z in [24,40) (all lengths / 8), Nv=32")
+    if name.startswith("batch1d"):
+        from fdtd_inputs import batch_runs_1d
+        return batch_runs_1d(nruns=8, seed=20221114), "8 of the 256 batched 1-D runs (same generator, seed)"
     return spec_1d_slab(), "1-D Nz=2000 slab (the full workload)"
 
 
@@ -166,18 +169,22 @@ def oracle_throughput(name: str, steps: int, warmup: int, budget_s: float | None
     from oracle import oracle as O
     from tests.adapters import oracle_sim
     spec, text = sample_spec(name)
-    sim = oracle_sim(O, spec)
-    sim.step(warmup)
+    specs = spec if isinstance(spec, list) else [spec]
+    sims = [oracle_sim(O, sp) for sp in specs]
+    for sim in sims:
+        sim.step(warmup)
     n = 0
     t0 = time.perf_counter()
     while n < steps:
-        sim.step(1)
+        for sim in sims:
+            sim.step(1)
         n += 1
         if budget_s is not None and time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    cells = cells_of(spec)
-    return cells * n / dt / 1e9, sim.nslots * sim.nnode * n / dt, n, text, cells, sim.nslots * sim.nnode
+    cells = sum(cells_of(sp) for sp in specs)
+    nodes = sum(sim.nslots * sim.nnode for sim in sims)
+    return cells * n / dt / 1e9, nodes * n / dt, n, text, cells, nodes
 
 
 # --------------------------------------------------------------------- main
@@ -210,6 +217,8 @@ def main():
     from paper_2211_05647_gb300 import Solver
 
     spec = make_spec(args.workload)
+    if isinstance(spec, list):
+        return batch_bench(args, spec, rank, world, local)
     s = Solver.from_spec(spec, device=local)
     ns, nn = s.plasma_shape()
     cells = cells_of(spec)
@@ -323,6 +332,92 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def batch_bench(args, specs, rank, world, local):
+    """Batched independent 1-D runs: one persistent kernel launch per chunk of
+    steps (graph replay), chunks of up to 100 steps."""
+    import torch
+    import torch.distributed as dist
+    from paper_2211_05647_gb300 import Batch
+    b = Batch(specs, device=local)
+    info = b.info()
+    cells, nodes = info["cells"], info["nodes"]
+    st = b.stream
+    chunk = min(100, args.steps)
+    rem = args.steps % chunk
+    b.step(max(args.warmup, 1))
+    b.step(chunk)                 # captures the chunk graph outside the timed region
+    if rem:
+        b.step(rem)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps // chunk + 2)]
+    evs[0].record(st)
+    for i in range(args.steps // chunk):
+        b.step(chunk)
+        evs[i + 1].record(st)
+    if rem:
+        b.step(rem)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_end.record(st)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = evs[0].elapsed_time(e_end)
+    launch_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps // chunk)]
+    t = torch.tensor([ms], device=f"cuda:{local}")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = world * cells * args.steps / (ms / 1e3) / 1e9
+    # e2e: creation from host specs (density upload), K steps, every run's E and J back to host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b2 = Batch(specs, device=local)
+    b2.step(args.steps)
+    d2h = 0
+    for r in range(b2.nruns):
+        d2h += b2.read(r, "ex").nbytes + b2.read(r, "j").nbytes
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    h2d = sum(sp["plasma"]["density"].nbytes for sp in specs)
+    b2.close()
+    if rank != 0:
+        return 0
+    fdt = specs[0]["plasma"]["f_dtype"]
+    fb = {"f32": 4, "bf16": 2, "f64": 8}[fdt]
+    eb = 8 if specs[0]["grid"]["precision"] == "f64" else 4
+    alg_step = 2 * eb * (2 * cells + len(specs)) + 2 * fb * nodes
+    per_launch_ms = statistics.median(launch_ms) if launch_ms else ms
+    achieved = alg_step * chunk / (per_launch_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if eb == 4 else "f64", "data": "synthetic (seeded run sizes, slabs, densities)",
+            "config": {"workload": args.workload, "runs": len(specs), "cells": cells, "phase_space_nodes": nodes,
+                       "f_dtype": fdt, "clusters": info["clusters"], "steps_per_launch": chunk,
+                       "l2": "inputs larger than L2 (delta f %.2f GB)" % (nodes * fb / 1e9),
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "phase_space_updates_per_s": world * nodes * args.steps / (ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": "k_batch1d", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg_step * chunk,
+                         "launch_ms": per_launch_ms,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
+            "gpu_launches": 2 * (args.steps // chunk + (1 if rem else 0)),
+            "clocks": clk,
+            "e2e": {"value": world * cells * args.steps / te / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}}
+    if world == 1 and not args.no_cpu_baseline:
+        g, psr, n, text, _, _ = oracle_throughput(args.workload, 10 ** 6, 2, budget_s=15.0)
+        line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{text}; {n} oracle steps in ~15 s, single thread",
+                                "phase_space_updates_per_s": psr}
+    print(json.dumps(line), flush=True)
     return 0
 
 

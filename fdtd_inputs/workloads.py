@@ -139,6 +139,25 @@ def spec_3d_slab(n=512, ny=None, nz=None, ppw=20, cpml=8, slab=(192, 320), src_k
         steps=steps)
 
 
+def batch_runs_1d(nruns=256, seed=20221114, nz_range=(1024, 65536), slab_frac=(0.2, 0.6), wp_w0=(0.1, 1.5),
+                  log_nu_w0=(-3.0, -1.0), nv=64, ppw=40, f_dtype="f32", precision="f32", src_k=100, steps=5000):
+    """Independent 1-D slab runs of uneven size: nz uniform on nz_range, a
+    centred slab of uniform density covering a uniform fraction of the grid,
+    w_p/w0 uniform, nu/w0 log-uniform, Mur ends, source at node src_k."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for r in range(nruns):
+        nz = int(rng.integers(nz_range[0], nz_range[1] + 1))
+        frac = rng.uniform(*slab_frac)
+        w = rng.uniform(*wp_w0)
+        nu = 10.0 ** rng.uniform(*log_nu_w0)
+        half = int(frac * nz / 2)
+        s = spec_1d_slab(nz=nz, ppw=ppw, slab=(nz // 2 - half, nz // 2 + half), wp_w0=w, nu_w0=nu, nv=nv,
+                         src_k=min(src_k, nz // 4), steps=steps, precision=precision, f_dtype=f_dtype, seed=seed + r)
+        specs.append(s)
+    return specs
+
+
 # The benchmark workloads (full sizes) by name, plus reduced profiling cases
 WORKLOADS = {
     "1d_slab_fp64": lambda: spec_1d_slab(),
@@ -150,4 +169,6 @@ WORKLOADS = {
     # profiling cases: same recipes at half the lengths (inputs still larger than L2)
     "2d_tmz_2048_kinetic": lambda: spec_2d_cylinder(n=2048, R=256),
     "3d_256_kinetic_bf16": lambda: spec_3d_slab(n=256, slab=(96, 160), src_k=12),
+    "batch1d_256_f32": lambda: batch_runs_1d(),
+    "batch1d_256_bf16": lambda: batch_runs_1d(f_dtype="bf16"),
 }

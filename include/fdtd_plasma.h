@@ -201,6 +201,37 @@ int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int buf_is_
 int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int buf_is_device);
 
 /* ---------------------------------------------------------------------
+ * Batches of independent 1-D runs (same step as above, per run), advanced by
+ * one persistent kernel launch per fdtd_batch_step call (graph-captured).
+ * Runs may differ in nz, Mur / PEC ends, density profile, nu0 and source;
+ * they must share dx, courant, precision, the velocity grid, te, nu model and
+ * f_dtype.  Runs are bin-packed onto thread-block clusters of 8 CTAs; a
+ * cluster steps its runs with hardware cluster barriers between the H and E
+ * half-steps, and clusters never wait for each other.
+ * run descriptors: grid.ndim must be 1; plasma.density may be NULL (vacuum),
+ * else nz+1 doubles (host or device); source.kind may be FDTD_SRC_NONE. */
+typedef struct fdtd_batch *fdtd_batch_t;
+
+typedef struct {
+    fdtd_grid_desc grid;
+    fdtd_plasma_desc plasma;
+    fdtd_source_desc source;
+} fdtd_run_desc;
+
+/* Create a batch (copies every input).  Errors as fdtd_plasma_create / set_plasma. */
+int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runtime_desc *rt, fdtd_batch_t *out);
+/* Advance every run by nsteps (asynchronous on the batch's stream). */
+int fdtd_batch_step(fdtd_batch_t b, int64_t nsteps);
+/* One quantity of one run: FDTD_EX (nz+1), FDTD_HY (nz), FDTD_J (per slot),
+ * FDTD_DF (packed rows); sizes as fdtd_batch_quantity_bytes. */
+int fdtd_batch_read(fdtd_batch_t b, int32_t run, int which, void *dst, size_t bytes, int dst_is_device);
+size_t fdtd_batch_quantity_bytes(fdtd_batch_t b, int32_t run, int which);
+/* dt, steps done, total cells, total phase-space nodes, clusters launched. */
+int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters);
+const char *fdtd_batch_last_error(fdtd_batch_t b);
+void fdtd_batch_destroy(fdtd_batch_t b);
+
+/* ---------------------------------------------------------------------
  * Allocation-free diagnostics.  The paper has no counterpart: this is a
  * library service for callers that cannot allocate device memory when they
  * need a diagnostic -- monitoring or watchdog code that must not take the

@@ -1,0 +1,653 @@
+// batch1d.cu -- many independent 1-D FDTD + kinetic runs of uneven size in
+// one persistent launch (the step of Sec. 2 / Sec. 5.2 for each run: H, the
+// f_1 update and J moment, E with the Ampere source term, soft source, Mur
+// ends), captured in a CUDA graph.
+//
+// Mapping: runs are bin-packed (longest processing time first) onto
+// thread-block clusters of kClusterCtas CTAs; inside a cluster the runs'
+// nodes are laid end to end and cut into one contiguous, equal-cost range per
+// CTA.  Per step a CTA updates H on its range, the cluster synchronises
+// (hardware barrier: neighbouring ranges exchange their edge values through
+// global memory / L2), the CTA updates the delta-f rows of its plasma nodes
+// (E <- E - dt/eps0 J in place), then E, the source and the Mur ends on its
+// range, and the cluster synchronises again.  Clusters never wait for each
+// other.  Cuts never separate node 0 from node 1 or node nz-1 from node nz,
+// so the thread that advances E_1 (E_{nz-1}) also applies the Mur update to
+// E_0 (E_nz) with values it owns.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "kinetic_row.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace fp {
+
+constexpr int kClusterCtas = 8;
+constexpr int kBatchThreads = 512;
+
+struct BRun {
+    int64_t e_off, h_off, row_off;    // offsets into E_all, H_all and the slot arrays
+    int32_t nz, src_k;                // src_k < 0: no source
+    int32_t mur, src_kind;
+    double mur_m;                     // (c dt - dz) / (c dt + dz)
+    double amp, fc, tau, t0;
+};
+
+struct BSeg {
+    int32_t run, k0, k1;              // E nodes [k0, k1) of the run
+    int32_t s0, s1;                   // the run's plasma slots whose node is in [k0, k1)
+};
+
+template <typename T>
+struct BatchArgs {
+    T *E, *H, *mur;
+    void *df;
+    T *jslot;
+    const T *dens;
+    const int32_t *slot_node;         // run-local E node of every (global) slot
+    const T *tab;                     // per run: alpha[pitch] beta[pitch]
+    const T *tab_w;                   // w' = -e w, shared by all runs
+    const BRun *runs;
+    const BSeg *segs;
+    const int32_t *cta_seg0;          // segments of CTA g: [cta_seg0[g], cta_seg0[g+1])
+    int pitch;
+    T ch, ce, cj;
+    double dt;
+    uint64_t seed;
+    const int64_t *d_step;
+    int nsteps;
+};
+
+__device__ __forceinline__ double batch_source(const BRun &r, double t)
+{
+    const double u = (t - r.t0) / r.tau;
+    if (r.src_kind == FDTD_SRC_GAUSS_SINE) return r.amp * sin(6.283185307179586 * r.fc * (t - r.t0)) * exp(-u * u);
+    if (r.src_kind == FDTD_SRC_GAUSS) return r.amp * exp(-u * u);
+    return 0.0;
+}
+
+template <typename TS, typename T, int VPL, int L>
+__global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    using V = typename Vec<TS>::type;
+    constexpr int VEC = Vec<TS>::n;
+    constexpr int R = 32 / L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane / L, l = lane % L;
+    const int nwarps = blockDim.x >> 5;
+    const int seg0 = a.cta_seg0[blockIdx.x], seg1 = a.cta_seg0[blockIdx.x + 1];
+    const int64_t step0 = *a.d_step;
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+
+    for (int s = 0; s < a.nsteps; ++s) {
+        const int64_t step = step0 + s;
+        // ---- H^{n+1/2} on this CTA's nodes; save E_1^n, E_{nz-1}^n for Mur
+        for (int q = seg0; q < seg1; ++q) {
+            const BSeg sg = a.segs[q];
+            const BRun r = a.runs[sg.run];
+            const T *E = a.E + r.e_off;
+            T *H = a.H + r.h_off;
+            const int kend = min(sg.k1, r.nz);
+            for (int k = sg.k0 + threadIdx.x; k < kend; k += blockDim.x) H[k] -= a.ch * (E[k + 1] - E[k]);
+            if (r.mur && threadIdx.x == 0) {
+                if (sg.k0 <= 1 && 1 < sg.k1) a.mur[2 * sg.run] = E[1];
+                if (sg.k0 <= r.nz - 1 && r.nz - 1 < sg.k1) a.mur[2 * sg.run + 1] = E[r.nz - 1];
+            }
+        }
+        cluster.sync();
+        // ---- delta-f rows of this CTA's plasma nodes; E <- E - dt/eps0 J
+        for (int q = seg0; q < seg1; ++q) {
+            const BSeg sg = a.segs[q];
+            const BRun r = a.runs[sg.run];
+            T *E = a.E + r.e_off;
+            const T *al = a.tab + (int64_t)sg.run * 2 * a.pitch, *be = al + a.pitch;
+            for (int base = sg.s0 + warp * R; base < sg.s1; base += nwarps * R) {
+                const int row = base + sub;
+                const bool valid = row < sg.s1;
+                const int64_t grow = r.row_off + (valid ? row : sg.s0);
+                V *rp = reinterpret_cast<V *>(a.df) + grow * (a.pitch / VEC);
+                V v[VPL];
+                T e = T(0), nE = T(0);
+                int node = 0;
+                if (valid) {
+#pragma unroll
+                    for (int qq = 0; qq < VPL; ++qq) v[qq] = __ldcs(rp + qq * L + l);
+                    node = __ldg(a.slot_node + grow);
+                    e = E[node];
+                    nE = __ldg(a.dens + grow) * e;
+                }
+                T sm = T(0), cm = T(0);
+                if (valid) row_update<TS, T, VPL, L>(rp, v, al, be, a.tab_w, nE, l, (uint32_t)grow, step, key, sm, cm);
+                const T J = row_reduce<T, L>(sm, cm);
+                if (valid && l == 0) {
+                    a.jslot[grow] = J;
+                    E[node] = e - a.cj * J;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- E^{n+1} on this CTA's interior nodes, soft source, Mur ends
+        for (int q = seg0; q < seg1; ++q) {
+            const BSeg sg = a.segs[q];
+            const BRun r = a.runs[sg.run];
+            T *E = a.E + r.e_off;
+            const T *H = a.H + r.h_off;
+            const int kbeg = max(sg.k0, 1), kend = min(sg.k1, r.nz);
+            for (int k = kbeg + threadIdx.x; k < kend; k += blockDim.x) {
+                T v = E[k] - a.ce * (H[k] - H[k - 1]);
+                if (k == r.src_k) v += (T)batch_source(r, (double)(step + 1) * a.dt);
+                E[k] = v;
+                if (r.mur) {
+                    if (k == 1) E[0] = a.mur[2 * sg.run] + (T)r.mur_m * (v - E[0]);
+                    if (k == r.nz - 1) E[r.nz] = a.mur[2 * sg.run + 1] + (T)r.mur_m * (v - E[r.nz]);
+                }
+            }
+        }
+        cluster.sync();
+    }
+}
+
+__global__ void k_batch_advance(int64_t *d_step, int64_t by) { *d_step += by; }
+
+}  // namespace fp
+
+// ================================================================= host side
+
+using namespace fp;
+
+namespace {
+
+constexpr double kC0 = 299792458.0, kQe = 1.602176634e-19, kMe = 9.1093837015e-31, kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+thread_local std::string g_batch_create_error;
+
+}  // namespace
+
+struct fdtd_batch {
+    fdtd_runtime_desc rt;
+    cudaStream_t stream, cap;
+    int precision, f_dtype, nruns, pitch, nnode, nclusters;
+    uint64_t seed;
+    size_t esz, df_esz;
+    double dt, dx;
+    std::vector<int64_t> nz, e_off, h_off, row_off, nslot;
+    int64_t ncell_e, ncell_h, nrows;
+    void *E, *H, *mur, *df, *jslot, *dens, *slot_node, *tab, *runs, *segs, *cta_seg0;
+    int64_t *d_step;
+    int64_t steps_done;
+    std::map<int64_t, cudaGraphExec_t> graphs;
+    std::string err;
+    cudaError_t (*launch)(fdtd_batch *, cudaStream_t, int);
+};
+
+namespace {
+
+int bfail(fdtd_batch *b, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf; else g_batch_create_error = buf;
+    return code;
+}
+
+void *balloc(fdtd_batch *b, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    void *p = nullptr;
+    if (b->rt.alloc) p = b->rt.alloc(bytes, b->rt.alloc_ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); p = nullptr; }
+    return p;
+}
+
+void bfree(fdtd_batch *b, void *p)
+{
+    if (!p) return;
+    if (b->rt.free) b->rt.free(p, b->rt.alloc_ctx);
+    else cudaFree(p);
+}
+
+template <typename TS, typename T, int VPL, int L>
+cudaError_t launch_t(fdtd_batch *b, cudaStream_t st, int nsteps)
+{
+    BatchArgs<T> a{};
+    a.E = (T *)b->E; a.H = (T *)b->H; a.mur = (T *)b->mur;
+    a.df = b->df; a.jslot = (T *)b->jslot; a.dens = (const T *)b->dens; a.slot_node = (const int32_t *)b->slot_node;
+    a.tab = (const T *)b->tab + b->pitch;   // per-run tables follow the shared w'
+    a.tab_w = (const T *)b->tab;
+    a.runs = (const BRun *)b->runs; a.segs = (const BSeg *)b->segs; a.cta_seg0 = (const int32_t *)b->cta_seg0;
+    a.pitch = b->pitch;
+    const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
+    a.ch = (T)(b->dt / (mu0 * b->dx));
+    a.ce = (T)(b->dt / (kEps0 * b->dx));
+    a.cj = (T)(b->dt / kEps0);
+    a.dt = b->dt;
+    a.seed = b->seed;
+    a.d_step = b->d_step;
+    a.nsteps = nsteps;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(b->nclusters * kClusterCtas);
+    cfg.blockDim = dim3(kBatchThreads);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_batch1d<TS, T, VPL, L>, a);
+    if (e != cudaSuccess) return e;
+    k_batch_advance<<<1, 1, 0, st>>>(b->d_step, nsteps);
+    return cudaGetLastError();
+}
+
+template <typename TS, typename T, int VPL, int L>
+int max_clusters()
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(kClusterCtas);
+    cfg.blockDim = dim3(kBatchThreads);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (void *)k_batch1d<TS, T, VPL, L>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        n = 0;
+    }
+    return n;
+}
+
+// pick the kernel instance for (storage, precision, vectors per row)
+template <typename TS, typename T>
+bool pick(int V, cudaError_t (**fn)(fdtd_batch *, cudaStream_t, int), int *maxc)
+{
+    switch (V) {
+    case 1: *fn = launch_t<TS, T, 1, 1>; *maxc = max_clusters<TS, T, 1, 1>(); return true;
+    case 2: *fn = launch_t<TS, T, 2, 1>; *maxc = max_clusters<TS, T, 2, 1>(); return true;
+    case 4: *fn = launch_t<TS, T, 4, 1>; *maxc = max_clusters<TS, T, 4, 1>(); return true;
+    case 8: *fn = launch_t<TS, T, 4, 2>; *maxc = max_clusters<TS, T, 4, 2>(); return true;
+    case 16: *fn = launch_t<TS, T, 4, 4>; *maxc = max_clusters<TS, T, 4, 4>(); return true;
+    case 32: *fn = launch_t<TS, T, 4, 8>; *maxc = max_clusters<TS, T, 4, 8>(); return true;
+    case 64: *fn = launch_t<TS, T, 4, 16>; *maxc = max_clusters<TS, T, 4, 16>(); return true;
+    case 128: *fn = launch_t<TS, T, 4, 32>; *maxc = max_clusters<TS, T, 4, 32>(); return true;
+    default: return false;
+    }
+}
+
+void destroy_batch(fdtd_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+    void *ps[] = {b->E, b->H, b->mur, b->df, b->jslot, b->dens, b->slot_node, b->tab, b->runs, b->segs, b->cta_seg0,
+                  b->d_step};
+    for (void *p : ps) bfree(b, p);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runtime_desc *rt, fdtd_batch_t *out)
+{
+    if (!out) return bfail(nullptr, FDTD_ERR_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!runs || nruns < 1) return bfail(nullptr, FDTD_ERR_INVAL, "need at least one run");
+    const fdtd_grid_desc &g0 = runs[0].grid;
+    const fdtd_plasma_desc &p0 = runs[0].plasma;
+    for (int r = 0; r < nruns; ++r) {
+        const fdtd_grid_desc &g = runs[r].grid;
+        const fdtd_plasma_desc &p = runs[r].plasma;
+        if (g.ndim != 1) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: batches are 1-D", r);
+        if (g.dx != g0.dx || g.courant != g0.courant || g.precision != g0.precision)
+            return bfail(nullptr, FDTD_ERR_INVAL, "run %d: dx, courant and precision must match run 0", r);
+        if (g.nz < 3 || g.nz > (1 << 30)) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nz out of range", r);
+        if (g.cpml_cells) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: 1-D runs use Mur or PEC ends", r);
+        if (p.vgrid != p0.vgrid || p.nv != p0.nv || p.nv_perp != p0.nv_perp || p.te_ev != p0.te_ev ||
+            p.vmax_vth != p0.vmax_vth || p.nu_model != p0.nu_model || p.f_dtype != p0.f_dtype)
+            return bfail(nullptr, FDTD_ERR_INVAL, "run %d: velocity grid, te, nu model and f_dtype must match run 0", r);
+        if (p.nonlinear) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nonlinear mode not available in batches", r);
+        if (!(p.nu0 >= 0) || !std::isfinite(p.nu0)) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nu0", r);
+        const fdtd_source_desc &s = runs[r].source;
+        if (s.kind && (s.k < 1 || s.k > g.nz - 1 || !(s.tau > 0)))
+            return bfail(nullptr, FDTD_ERR_INVAL, "run %d: source node must be in [1, nz-1] and tau > 0", r);
+    }
+    if (!(g0.dx > 0) || !(g0.courant > 0) || g0.courant >= 1.0)
+        return bfail(nullptr, FDTD_ERR_UNSTABLE, "courant must be in (0, 1) in 1-D");
+    const bool f64 = g0.precision == FDTD_F64;
+    if (f64 ? p0.f_dtype != FDTD_DF_F64 : (p0.f_dtype != FDTD_DF_F32 && p0.f_dtype != FDTD_DF_BF16))
+        return bfail(nullptr, FDTD_ERR_INVAL, "f_dtype does not match the field precision");
+
+    fdtd_batch *b = new (std::nothrow) fdtd_batch();
+    if (!b) return bfail(nullptr, FDTD_ERR_NOMEM, "host allocation failed");
+    if (rt) b->rt = *rt;
+    b->stream = (cudaStream_t)b->rt.stream;
+    auto bail = [&](int code, const char *msg) {
+        g_batch_create_error = msg;
+        destroy_batch(b);
+        return code;
+    };
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(FDTD_ERR_CUDA, "stream creation failed");
+    b->precision = g0.precision;
+    b->seed = p0.seed;
+    b->f_dtype = p0.f_dtype;
+    b->nruns = nruns;
+    b->esz = f64 ? 8 : 4;
+    b->df_esz = p0.f_dtype == FDTD_DF_BF16 ? 2 : (p0.f_dtype == FDTD_DF_F64 ? 8 : 4);
+    b->dx = g0.dx;
+    b->dt = g0.courant * g0.dx / kC0;
+    const int nnode = p0.vgrid == FDTD_VGRID_CART2D ? p0.nv * p0.nv_perp : p0.nv;
+    b->nnode = nnode;
+    b->pitch = kinetic_pitch(nnode, p0.f_dtype);
+    const int vec = p0.f_dtype == FDTD_DF_BF16 ? 8 : (p0.f_dtype == FDTD_DF_F64 ? 2 : 4);
+    const int V = b->pitch / vec;
+    int maxc = 0;
+    bool ok = p0.f_dtype == FDTD_DF_F32    ? pick<float, float>(V, &b->launch, &maxc)
+              : p0.f_dtype == FDTD_DF_BF16 ? pick<__nv_bfloat16, float>(V, &b->launch, &maxc)
+                                           : pick<double, double>(V, &b->launch, &maxc);
+    if (!ok) return bail(FDTD_ERR_INVAL, "too many velocity nodes for the batched kernel (at most 128 vectors)");
+    if (maxc < 1) return bail(FDTD_ERR_CUDA, "no cluster of the batched kernel fits on this device");
+
+    // ---- velocity tables (shared node weights; per-run alpha, beta from nu0_r)
+    const double vth = std::sqrt(kQe * p0.te_ev / kMe), vmax = p0.vmax_vth * vth, two_vth2 = 2 * vth * vth;
+    std::vector<double> w(nnode), f0p(nnode), f0(nnode), dV(nnode), speed(nnode);
+    for (int j = 0; j < nnode; ++j) {
+        double va, g, ww, dvv, sp;
+        if (p0.vgrid == FDTD_VGRID_SIGNED1D) {
+            const double dv = 2 * vmax / p0.nv;
+            va = ((double)j + 0.5 - 0.5 * p0.nv) * dv;
+            g = std::exp(-va * va / two_vth2) / std::sqrt(kPi * two_vth2);
+            ww = va * dv; dvv = dv; sp = std::fabs(va);
+        } else if (p0.vgrid == FDTD_VGRID_CART2D) {
+            const int a = j / p0.nv_perp, c = j % p0.nv_perp;
+            const double dvp = 2 * vmax / p0.nv, dvq = 2 * vmax / p0.nv_perp;
+            va = ((double)a + 0.5 - 0.5 * p0.nv) * dvp;
+            const double vb = ((double)c + 0.5 - 0.5 * p0.nv_perp) * dvq;
+            g = std::exp(-(va * va + vb * vb) / two_vth2) / (kPi * two_vth2);
+            ww = va * dvp * dvq; dvv = dvp * dvq; sp = std::sqrt(va * va + vb * vb);
+        } else {
+            const double gam = vmax / p0.nv;
+            va = ((double)j + 0.5) * gam;
+            g = std::exp(-va * va / two_vth2) / std::pow(kPi * two_vth2, 1.5);
+            ww = 4 * kPi / 3 * va * va * va * gam; dvv = 4 * kPi * va * va * gam; sp = va;
+        }
+        f0[j] = g; f0p[j] = -va / (vth * vth) * g; w[j] = ww; dV[j] = dvv; speed[j] = sp;
+    }
+    double num = 0, den = 0;
+    for (int j = 0; j < nnode; ++j) { num += speed[j] * f0[j] * dV[j]; den += f0[j] * dV[j]; }
+    const double mean_speed = num / den;
+    const int P = b->pitch;
+    std::vector<double> tab((size_t)P * (1 + 2 * (size_t)nruns), 0.0);
+    for (int j = 0; j < nnode; ++j) tab[j] = -kQe * w[j];
+    double wpmax = 0;
+    // ---- per-run layout and slots
+    std::vector<BRun> hr(nruns);
+    std::vector<int32_t> slot_node;
+    std::vector<double> dens_slot;
+    b->nz.resize(nruns); b->e_off.resize(nruns); b->h_off.resize(nruns); b->row_off.resize(nruns); b->nslot.resize(nruns);
+    int64_t eo = 0, ho = 0, ro = 0;
+    std::vector<std::vector<double>> dens_run(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        const fdtd_grid_desc &g = runs[r].grid;
+        const fdtd_plasma_desc &p = runs[r].plasma;
+        const int64_t nz = g.nz;
+        b->nz[r] = nz; b->e_off[r] = eo; b->h_off[r] = ho; b->row_off[r] = ro;
+        std::vector<double> d(nz + 1, 0.0);
+        if (p.density) {
+            if (p.density_on_device) {
+                if (cudaMemcpy(d.data(), p.density, (nz + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return bail(FDTD_ERR_CUDA, "density copy failed");
+            } else {
+                std::memcpy(d.data(), p.density, (nz + 1) * 8);
+            }
+        }
+        int64_t ns = 0;
+        for (int64_t k = 0; k <= nz; ++k) {
+            if (!std::isfinite(d[k]) || d[k] < 0) return bail(FDTD_ERR_NONFINITE, "density must be finite and >= 0");
+            if (d[k] > 0 && k >= 1 && k <= nz - 1) {
+                slot_node.push_back((int32_t)k);
+                dens_slot.push_back(d[k]);
+                wpmax = std::max(wpmax, d[k]);
+                ++ns;
+            }
+        }
+        b->nslot[r] = ns;
+        const double nu0 = p.nu0;
+        for (int j = 0; j < nnode; ++j) {
+            const double nu = p.nu_model == FDTD_NU_CONST ? nu0 : nu0 * speed[j] / mean_speed;
+            tab[(size_t)P * (1 + 2 * r) + j] = (2 - b->dt * nu) / (2 + b->dt * nu);
+            tab[(size_t)P * (2 + 2 * r) + j] = 2 * b->dt * (kQe / kMe) * f0p[j] / (2 + b->dt * nu);
+        }
+        BRun &br = hr[r];
+        br.e_off = eo; br.h_off = ho; br.row_off = ro;
+        br.nz = (int32_t)nz;
+        br.mur = g.mur ? 1 : 0;
+        br.mur_m = (kC0 * b->dt - g.dx) / (kC0 * b->dt + g.dx);
+        const fdtd_source_desc &s = runs[r].source;
+        br.src_kind = s.kind;
+        br.src_k = s.kind ? (int32_t)s.k : -1;
+        br.amp = s.amp; br.fc = s.fc; br.tau = s.kind ? s.tau : 1.0; br.t0 = s.t0;
+        eo += nz + 1; ho += nz; ro += ns;
+    }
+    b->ncell_e = eo; b->ncell_h = ho; b->nrows = ro;
+    const double wp = std::sqrt(wpmax * kQe * kQe / (kEps0 * kMe));
+    if (std::pow(wp * b->dt / 2, 2) + g0.courant * g0.courant >= 1.0)
+        return bail(FDTD_ERR_UNSTABLE, "plasma frequency too high for dt");
+
+    // ---- bin packing: runs -> clusters (LPT), then equal-cost CTA ranges
+    const double cell_cost = 4.0 * b->esz, node_cost = 2.0 * nnode * b->df_esz + 20.0;
+    std::vector<double> cost(nruns);
+    for (int r = 0; r < nruns; ++r) cost[r] = cell_cost * (b->nz[r] + 1) + node_cost * b->nslot[r];
+    const int nb = std::max(1, std::min(maxc, nruns));
+    std::vector<int> order(nruns);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<std::vector<int>> bins(nb);
+    std::vector<double> load(nb, 0.0);
+    for (int r : order) {
+        int bi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        bins[bi].push_back(r);
+        load[bi] += cost[r];
+    }
+    b->nclusters = nb;
+    std::vector<BSeg> segs;
+    std::vector<int32_t> cta_seg0;
+    // slot index (run-local) of the first slot at node >= k
+    std::vector<std::vector<int32_t>> slot_at(nruns);
+    for (int r = 0; r < nruns; ++r) {
+        slot_at[r].assign(b->nz[r] + 2, 0);
+        const int32_t *nodes = slot_node.data() + b->row_off[r];
+        int64_t si = 0;
+        for (int64_t k = 0; k <= b->nz[r] + 1; ++k) {
+            while (si < b->nslot[r] && nodes[si] < k) ++si;
+            slot_at[r][k] = (int32_t)si;
+        }
+    }
+    for (int bi = 0; bi < nb; ++bi) {
+        // per-node cost along the bin's concatenated nodes, cut into kClusterCtas ranges
+        const double total = load[bi];
+        double acc = 0;
+        int cta = 0;
+        cta_seg0.push_back((int32_t)segs.size());
+        for (int r : bins[bi]) {
+            const int64_t nz = b->nz[r];
+            int64_t k0 = 0;
+            const int32_t *nodes = slot_node.data() + b->row_off[r];
+            int64_t si = 0;
+            for (int64_t k = 0; k <= nz; ++k) {
+                while (si < b->nslot[r] && nodes[si] < k) ++si;
+                const bool plasma = si < b->nslot[r] && nodes[si] == k;
+                acc += cell_cost + (plasma ? node_cost : 0.0);
+                const double target = total * (cta + 1) / kClusterCtas;
+                // a cut after node k (range [k0, k+1)); never between 0|1 or nz-1|nz
+                const int64_t cut = k + 1;
+                if (acc >= target && cta < kClusterCtas - 1 && cut != 1 && cut != nz && cut <= nz) {
+                    segs.push_back(BSeg{r, (int32_t)k0, (int32_t)cut, slot_at[r][k0], slot_at[r][cut]});
+                    k0 = cut;
+                    ++cta;
+                    cta_seg0.push_back((int32_t)segs.size());
+                }
+            }
+            if (k0 <= nz) segs.push_back(BSeg{r, (int32_t)k0, (int32_t)(nz + 1), slot_at[r][k0], slot_at[r][nz + 1]});
+        }
+        while (cta < kClusterCtas - 1) {   // CTAs left without nodes
+            ++cta;
+            cta_seg0.push_back((int32_t)segs.size());
+        }
+    }
+    cta_seg0.push_back((int32_t)segs.size());
+
+    // ---- device buffers
+    const int64_t nrow = std::max<int64_t>(b->nrows, 1);
+    b->E = balloc(b, eo * b->esz);
+    b->H = balloc(b, ho * b->esz);
+    b->mur = balloc(b, 2 * (size_t)nruns * b->esz);
+    b->df = balloc(b, (size_t)nrow * P * b->df_esz);
+    b->jslot = balloc(b, (size_t)nrow * b->esz);
+    b->dens = balloc(b, (size_t)nrow * b->esz);
+    b->slot_node = balloc(b, (size_t)nrow * 4);
+    b->tab = balloc(b, tab.size() * b->esz);
+    b->runs = balloc(b, hr.size() * sizeof(BRun));
+    b->segs = balloc(b, std::max<size_t>(segs.size(), 1) * sizeof(BSeg));
+    b->cta_seg0 = balloc(b, cta_seg0.size() * 4);
+    b->d_step = (int64_t *)balloc(b, 256);
+    if (!b->E || !b->H || !b->mur || !b->df || !b->jslot || !b->dens || !b->slot_node || !b->tab || !b->runs ||
+        !b->segs || !b->cta_seg0 || !b->d_step)
+        return bail(FDTD_ERR_NOMEM, "batch allocation failed");
+    bool up = true;
+    auto H2D = [&](void *dst, const void *src, size_t n) {
+        if (n && cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice) != cudaSuccess) up = false;
+    };
+    if (b->esz == 8) {
+        H2D(b->tab, tab.data(), tab.size() * 8);
+        H2D(b->dens, dens_slot.data(), dens_slot.size() * 8);
+    } else {
+        std::vector<float> t32(tab.begin(), tab.end()), d32(dens_slot.begin(), dens_slot.end());
+        H2D(b->tab, t32.data(), t32.size() * 4);
+        H2D(b->dens, d32.data(), d32.size() * 4);
+    }
+    H2D(b->slot_node, slot_node.data(), slot_node.size() * 4);
+    H2D(b->runs, hr.data(), hr.size() * sizeof(BRun));
+    H2D(b->segs, segs.data(), segs.size() * sizeof(BSeg));
+    H2D(b->cta_seg0, cta_seg0.data(), cta_seg0.size() * 4);
+    if (!up) return bail(FDTD_ERR_CUDA, "batch upload failed");
+    if (cudaMemset(b->E, 0, eo * b->esz) != cudaSuccess || cudaMemset(b->H, 0, ho * b->esz) != cudaSuccess ||
+        cudaMemset(b->mur, 0, 2 * (size_t)nruns * b->esz) != cudaSuccess ||
+        cudaMemset(b->df, 0, (size_t)nrow * P * b->df_esz) != cudaSuccess ||
+        cudaMemset(b->jslot, 0, (size_t)nrow * b->esz) != cudaSuccess || cudaMemset(b->d_step, 0, 8) != cudaSuccess)
+        return bail(FDTD_ERR_CUDA, "batch clear failed");
+    *out = b;
+    return FDTD_OK;
+}
+
+int fdtd_batch_step(fdtd_batch_t b, int64_t nsteps)
+{
+    if (!b) return FDTD_ERR_INVAL;
+    if (nsteps < 0) return bfail(b, FDTD_ERR_INVAL, "nsteps < 0");
+    int64_t left = nsteps;
+    while (left > 0) {
+        const int64_t n = std::min<int64_t>(left, 1 << 20);
+        auto it = b->graphs.find(n);
+        if (it == b->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+            if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+            cudaError_t el = b->launch(b, b->cap, (int)n);
+            e = cudaStreamEndCapture(b->cap, &graph);
+            if (el != cudaSuccess || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return bfail(b, FDTD_ERR_CUDA, "capturing the batched launch: %s",
+                             cudaGetErrorString(el != cudaSuccess ? el : e));
+            }
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+            it = b->graphs.emplace(n, exec).first;
+        }
+        cudaError_t e = cudaGraphLaunch(it->second, b->stream);
+        if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+        left -= n;
+    }
+    b->steps_done += nsteps;
+    return FDTD_OK;
+}
+
+size_t fdtd_batch_quantity_bytes(fdtd_batch_t b, int32_t run, int which)
+{
+    if (!b || run < 0 || run >= b->nruns) return 0;
+    switch (which) {
+    case FDTD_EX: return (size_t)(b->nz[run] + 1) * b->esz;
+    case FDTD_HY: return (size_t)b->nz[run] * b->esz;
+    case FDTD_J: return (size_t)b->nslot[run] * b->esz;
+    case FDTD_DF: return (size_t)b->nslot[run] * b->nnode * b->df_esz;
+    default: return 0;
+    }
+}
+
+int fdtd_batch_read(fdtd_batch_t b, int32_t run, int which, void *dst, size_t bytes, int dst_is_device)
+{
+    if (!b || !dst) return FDTD_ERR_INVAL;
+    const size_t need = fdtd_batch_quantity_bytes(b, run, which);
+    if (need == 0) return bfail(b, FDTD_ERR_INVAL, "quantity %d of run %d is absent", which, run);
+    if (bytes != need) return bfail(b, FDTD_ERR_INVAL, "needs %zu bytes, got %zu", need, bytes);
+    const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e;
+    if (which == FDTD_DF) {
+        const size_t row = (size_t)b->nnode * b->df_esz, dp = (size_t)b->pitch * b->df_esz;
+        e = cudaMemcpy2DAsync(dst, row, (char *)b->df + b->row_off[run] * dp, dp, row, b->nslot[run], kind,
+                              b->stream);
+    } else {
+        const char *src = which == FDTD_EX   ? (char *)b->E + b->e_off[run] * b->esz
+                          : which == FDTD_HY ? (char *)b->H + b->h_off[run] * b->esz
+                                             : (char *)b->jslot + b->row_off[run] * b->esz;
+        e = cudaMemcpyAsync(dst, src, bytes, kind, b->stream);
+    }
+    if (e == cudaSuccess && !dst_is_device) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "read: %s", cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
+int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters)
+{
+    if (!b) return FDTD_ERR_INVAL;
+    if (dt) *dt = b->dt;
+    if (steps) *steps = b->steps_done;
+    if (cells) {
+        int64_t c = 0;
+        for (int64_t n : b->nz) c += n;
+        *cells = c;
+    }
+    if (nodes) *nodes = b->nrows * b->nnode;
+    if (nclusters) *nclusters = b->nclusters;
+    return FDTD_OK;
+}
+
+const char *fdtd_batch_last_error(fdtd_batch_t b) { return b ? b->err.c_str() : g_batch_create_error.c_str(); }
+
+void fdtd_batch_destroy(fdtd_batch_t b) { destroy_batch(b); }
+
+}  // extern "C"

@@ -224,6 +224,7 @@ Source source_view(fdtd_plasma *h)
     s.amp = h->src.amp; s.fc = h->src.fc; s.tau = h->src.tau; s.t0 = h->src.t0; s.dt = h->dt;
     s.i = h->src.i; s.j = h->src.j; s.k = h->src.k;
     s.i0 = h->src.i0; s.i1 = h->src.i1; s.j0 = h->src.j0; s.j1 = h->src.j1;
+    s.val = h->d_src;
     return s;
 }
 
@@ -241,9 +242,13 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
     const Cpml<T> cp = cpml_view<T>(h);
     const Source src = source_view(h);
     if (ev) cudaEventRecord(ev[0], st);
-    if (h->g.ndim == 1) launch_h1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->g.mur ? (T *)h->mur_state : nullptr, h->nz, ch);
-    else if (h->g.ndim == 2) launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp);
-    else launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp);
+    if (h->g.ndim == 1)
+        launch_h1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->g.mur ? (T *)h->mur_state : nullptr, h->nz, ch, src, h->d_step,
+                      kstep);
+    else if (h->g.ndim == 2)
+        launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, kstep);
+    else
+        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep);
     if (ev) cudaEventRecord(ev[1], st);
     if (h->has_plasma && h->nslots > 0) {
         KinArgs<T> a{};
@@ -428,10 +433,11 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     }
     h->mur_state = dalloc(h, 4 * 8);
     h->d_step = (int64_t *)dalloc(h, 256);
+    h->d_src = (double *)dalloc(h, 256);
     h->diag_blocks = h->num_sms * 4;
     h->diag_partials = (double *)dalloc(h, (size_t)h->diag_blocks * 7 * sizeof(double));
     h->diag_out = (double *)dalloc(h, 8 * sizeof(double));
-    if (!h->mur_state || !h->d_step || !h->diag_partials || !h->diag_out)
+    if (!h->mur_state || !h->d_step || !h->d_src || !h->diag_partials || !h->diag_out)
         return bail(FDTD_ERR_NOMEM, "small allocation failed");
     rc = fdtd_plasma_reset(h);
     if (rc != FDTD_OK) {
@@ -824,6 +830,7 @@ void fdtd_plasma_destroy(fdtd_plasma_t h)
     dfree(h, h->prof);
     dfree(h, h->mur_state);
     dfree(h, h->d_step);
+    dfree(h, h->d_src);
     dfree(h, h->diag_partials);
     dfree(h, h->diag_out);
     if (h->cap) cudaStreamDestroy(h->cap);

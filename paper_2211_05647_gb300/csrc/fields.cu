@@ -25,12 +25,22 @@ __device__ __forceinline__ bool in_slab(int64_t i, int64_t n, int L)
     return i < L || i >= n - L;
 }
 
+// g(t^{n+1}) is evaluated once per step, by the first thread of the H kernel,
+// into a device scalar that the E kernel of the same step reads at the source
+// node(s) -- no FP64 transcendental in the E stencil.
+__device__ __forceinline__ void write_source(const Source &src, const int64_t *d_step, int kstep)
+{
+    if (src.kind) *src.val = source_value(src, (double)(*d_step + kstep + 1) * src.dt);
+}
+
 // ------------------------------------------------------------------- 1-D
 
 template <typename T>
-__global__ void k_h1d(const T *__restrict__ ex, T *__restrict__ hy, T *__restrict__ mur, int64_t nz, T ch)
+__global__ void k_h1d(const T *__restrict__ ex, T *__restrict__ hy, T *__restrict__ mur, int64_t nz, T ch, Source src,
+                      const int64_t *__restrict__ d_step, int kstep)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) write_source(src, d_step, kstep);
     if (k < nz) hy[k] -= ch * (ex[k + 1] - ex[k]);   // mu0 dHy/dt = -dEx/dz
     if (mur) {                                       // E_1^n and E_{nz-1}^n for the Mur ends
         if (k == 1) mur[0] = ex[1];
@@ -45,7 +55,7 @@ __global__ void k_e1d(T *__restrict__ ex, const T *__restrict__ hy, int64_t nz, 
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < 1 || k >= nz) return;
     T v = ex[k] - ce * (hy[k] - hy[k - 1]);           // eps0 dEx/dt = -dHy/dz - Jx
-    if (src.kind && k == src.k) v += (T)source_value(src, (double)(*d_step + kstep + 1) * src.dt);
+    if (src.kind && k == src.k) v += (T)*src.val;
     ex[k] = v;
 }
 
@@ -61,10 +71,12 @@ __global__ void k_mur1d(T *__restrict__ ex, const T *__restrict__ mur, int64_t n
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__restrict__ hx, T *__restrict__ hy,
-                                             int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp)
+                                             int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp, Source src,
+                                             const int64_t *__restrict__ d_step, int kstep)
 {
     const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    if (i == 0 && j == 0) write_source(src, d_step, kstep);
     if (i >= nx || j >= ny) return;
     const int64_t c = j * nx + i;
     const T e = ez[c];
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
         upd = ce * (dHx * kx - dHy * ky) + cpe * (px - py);
     }
     T v = ez[c] + upd;
-    if (src.kind && i == src.i && j == src.j) v += (T)source_value(src, (double)(*d_step + kstep + 1) * src.dt);
+    if (src.kind && i == src.i && j == src.j) v += (T)*src.val;
     ez[c] = v;
 }
 
@@ -156,11 +168,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_h3d(const T *__restrict__ ex, const T *__restrict__ ey,
                                              const T *__restrict__ ez, T *__restrict__ hx, T *__restrict__ hy,
                                              T *__restrict__ hz, int64_t nx, int64_t ny, int64_t nz, T ch, T cph,
-                                             Cpml<T> cp)
+                                             Cpml<T> cp, Source src, const int64_t *__restrict__ d_step, int kstep)
 {
     const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * 4 + threadIdx.y;
     const int64_t k = (int64_t)blockIdx.z * 2 + threadIdx.z;
+    if (i == 0 && j == 0 && k == 0) write_source(src, d_step, kstep);
     if (i >= nx || j >= ny || k >= nz) return;
     const int64_t sxy = nx * ny;
     const int64_t c = k * sxy + j * nx + i;
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
             bool hit = src.loc == FDTD_LOC_SHEET
                            ? (k == src.k && i >= src.i0 && i < src.i1 && j >= src.j0 && j < src.j1)
                            : (i == src.i && j == src.j && k == src.k);
-            if (hit) v += (T)source_value(src, (double)(*d_step + kstep + 1) * src.dt);
+            if (hit) v += (T)*src.val;
         }
         ex[c] = v;
     }
@@ -279,9 +292,10 @@ __global__ void k_advance(int64_t *d_step, int64_t by) { *d_step += by; }
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 template <typename T>
-void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch)
+void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch, Source src,
+                const int64_t *d_step, int kstep)
 {
-    k_h1d<T><<<cdiv(nz + 1, 256), 256, 0, st>>>(ex, hy, mur_state, nz, ch);
+    k_h1d<T><<<cdiv(nz + 1, 256), 256, 0, st>>>(ex, hy, mur_state, nz, ch, src, d_step, kstep);
 }
 template <typename T>
 void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep)
@@ -294,10 +308,11 @@ void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m)
     k_mur1d<T><<<1, 32, 0, st>>>(ex, mur_state, nz, m);
 }
 template <typename T>
-void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp)
+void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
+                Source src, const int64_t *d_step, int kstep)
 {
     dim3 b(32, 8), g(cdiv(nx, 32), cdiv(ny, 8));
-    k_h2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp);
+    k_h2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
@@ -307,10 +322,11 @@ void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, in
     k_e2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
 }
 template <typename T>
-void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp)
+void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
+                Source src, const int64_t *d_step, int kstep)
 {
     dim3 b(32, 4, 2), g(cdiv(nx, 32), cdiv(ny, 4), cdiv(nz, 2));
-    k_h3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp);
+    k_h3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
@@ -322,13 +338,15 @@ void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t 
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by) { k_advance<<<1, 1, 0, st>>>(d_step, by); }
 
 #define FP_INST(T)                                                                                            \
-    template void launch_h1d<T>(cudaStream_t, const T *, T *, T *, int64_t, T);                               \
+    template void launch_h1d<T>(cudaStream_t, const T *, T *, T *, int64_t, T, Source, const int64_t *, int);  \
     template void launch_e1d<T>(cudaStream_t, T *, const T *, int64_t, T, Source, const int64_t *, int);      \
     template void launch_mur1d<T>(cudaStream_t, T *, const T *, int64_t, T);                                  \
-    template void launch_h2d<T>(cudaStream_t, const T *, T *, T *, int64_t, int64_t, T, T, Cpml<T>);          \
+    template void launch_h2d<T>(cudaStream_t, const T *, T *, T *, int64_t, int64_t, T, T, Cpml<T>, Source,   \
+                                const int64_t *, int);                                                        \
     template void launch_e2d<T>(cudaStream_t, T *, const T *, const T *, int64_t, int64_t, T, T, Cpml<T>,     \
                                 Source, const int64_t *, int);                                                \
-    template void launch_h3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>);         \
+    template void launch_h3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>, Source,  \
+                                const int64_t *, int);                                                        \
     template void launch_e3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>, Source,  \
                                 const int64_t *, int);
 FP_INST(float)

@@ -30,6 +30,7 @@ struct Source {
     int kind, loc;
     double amp, fc, tau, t0, dt;
     int64_t i, j, k, i0, i1, j0, j1;
+    double *val;   // device scalar: g(t^{n+1}) of the current step, written by the H kernel
 };
 
 // g(t) of the soft source, FP64 on the device
@@ -68,12 +69,14 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
     e = (a - (s - z)) + (b - z);
 }
 
-// ---------------------------------------------- Philox4x32-10 (Salmon et al. 2011)
+// ------------------------------------------- Philox4x32-7 (Salmon et al. 2011)
+// The 7-round variant, which the authors report passes TestU01's BigCrush;
+// used only to draw stochastic-rounding bits.
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+__device__ __forceinline__ uint4 philox4x32_7(uint4 c, uint2 k)
 {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
+    for (int r = 0; r < 7; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
         c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
@@ -96,18 +99,21 @@ __device__ __forceinline__ uint16_t f32_to_bf16_sr(float x, uint32_t r16)
 // -------------------------------------------------------------- launchers
 
 template <typename T>
-void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch);
+void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch, Source src,
+                const int64_t *d_step, int kstep);
 template <typename T>
 void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep);
 template <typename T>
 void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m);
 template <typename T>
-void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp);
+void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
+                Source src, const int64_t *d_step, int kstep);
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
                 Source src, const int64_t *d_step, int kstep);
 template <typename T>
-void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp);
+void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
+                Source src, const int64_t *d_step, int kstep);
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
                 Source src, const int64_t *d_step, int kstep);
@@ -159,6 +165,7 @@ struct fdtd_plasma {
     int64_t prof_len;
     void *mur_state;
     int64_t *d_step;
+    double *d_src;            // g(t^{n+1}) of the step in flight
     int64_t steps_done;
     // plasma
     int has_plasma;

@@ -85,6 +85,10 @@ class fdtd_diag_arrays(ctypes.Structure):
                 ("nslots", ctypes.c_int64), ("nnode", ctypes.c_int64), ("dV", ctypes.c_void_p)]
 
 
+class fdtd_run_desc(ctypes.Structure):
+    _fields_ = [("grid", fdtd_grid_desc), ("plasma", fdtd_plasma_desc), ("source", fdtd_source_desc)]
+
+
 # ---------------------------------------------------------------- library
 _lib = None
 _lib_lock = threading.Lock()
@@ -112,6 +116,17 @@ SIGNATURES = {
     "fdtd_plasma_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fdtd_batch_create": (ctypes.c_int, [ctypes.POINTER(fdtd_run_desc), ctypes.c_int32,
+                                         ctypes.POINTER(fdtd_runtime_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "fdtd_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "fdtd_batch_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                       ctypes.c_int]),
+    "fdtd_batch_quantity_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int]),
+    "fdtd_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "fdtd_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fdtd_batch_destroy": (None, [ctypes.c_void_p]),
     "fdtd_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(fdtd_diag_arrays), ctypes.POINTER(ctypes.c_double),
                                                 ctypes.c_int, ctypes.c_void_p]),
     "fdtd_plasma_destroy": (None, [ctypes.c_void_p]),
@@ -167,6 +182,114 @@ class _TorchAllocator:
 
     def _free(self, ptr, ctx):
         self.live.pop(ptr, None)
+
+
+def _grid_desc(grid: dict) -> fdtd_grid_desc:
+    g = fdtd_grid_desc()
+    g.ndim = int(grid["ndim"])
+    g.precision = PRECISION[grid.get("precision", "f32")]
+    g.nx, g.ny, g.nz = int(grid.get("nx", 1)), int(grid.get("ny", 1)), int(grid.get("nz", 1))
+    g.dx, g.courant = float(grid["dx"]), float(grid.get("courant", 0.5))
+    g.cpml_cells, g.mur = int(grid.get("cpml_cells", 0)), int(grid.get("mur", 0))
+    g.cpml_order = float(grid.get("cpml_order", 3.0))
+    g.cpml_sigma_factor = float(grid.get("cpml_sigma_factor", 1.3))
+    g.cpml_kappa_max = float(grid.get("cpml_kappa_max", 7.0))
+    g.cpml_alpha_min = float(grid.get("cpml_alpha_min", 0.0))
+    g.cpml_alpha_max = float(grid.get("cpml_alpha_max", 0.05))
+    return g
+
+
+def _source_desc(kind="gauss_sine", location="point", amp=1.0, fc=0.0, tau=1.0, t0=0.0, i=0, j=0, k=0, i0=0, i1=0,
+                 j0=0, j1=0) -> fdtd_source_desc:
+    return fdtd_source_desc(SRC_KIND[kind], SRC_LOC[location], amp, fc, tau, t0, i, j, k, i0, i1, j0, j1)
+
+
+def _plasma_desc(density_ptr, on_device, vgrid="signed1d", nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0,
+                 nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0) -> fdtd_plasma_desc:
+    d = fdtd_plasma_desc()
+    d.density, d.density_on_device = density_ptr, on_device
+    d.vgrid, d.nv, d.nv_perp = VGRID[vgrid], int(nv), int(nv_perp)
+    d.te_ev, d.vmax_vth, d.nu0 = float(te_ev), float(vmax_vth), float(nu0)
+    d.nu_model, d.f_dtype, d.nonlinear = NU_MODEL[nu_model], DF_DTYPE[f_dtype], int(nonlinear)
+    d.seed = int(seed)
+    return d
+
+
+# ------------------------------------------------------------------ Batch
+class Batch:
+    """Owns one ``fdtd_batch_t``: many independent 1-D runs (specs in the
+    ``fdtd_inputs`` format) advanced by one persistent launch per step call."""
+
+    def __init__(self, specs, device: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device("cuda", device)
+        torch.cuda.set_device(self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._alloc = _TorchAllocator(self.device)
+        n = len(specs)
+        arr = (fdtd_run_desc * n)()
+        self._keep = []
+        for r, sp in enumerate(specs):
+            arr[r].grid = _grid_desc(sp["grid"])
+            if sp.get("source"):
+                arr[r].source = _source_desc(**sp["source"])
+            p = sp.get("plasma")
+            if p is not None:
+                dens = np.ascontiguousarray(p["density"], dtype=np.float64)
+                self._keep.append(dens)
+                kw = {k: v for k, v in p.items() if k != "density"}
+                arr[r].plasma = _plasma_desc(dens.ctypes.data, 0, **kw)
+        self.precision = specs[0]["grid"].get("precision", "f32")
+        self.f_dtype = (specs[0].get("plasma") or {}).get("f_dtype", "f32")
+        rt = fdtd_runtime_desc()
+        rt.stream = self.stream.cuda_stream
+        rt.alloc, rt.free = self._alloc.alloc_cb, self._alloc.free_cb
+        h = ctypes.c_void_p()
+        rc = self.lib.fdtd_batch_create(arr, n, ctypes.byref(rt), ctypes.byref(h))
+        if rc != FDTD_OK:
+            raise FdtdError(rc, self.lib.fdtd_batch_last_error(None).decode())
+        self.h = h
+        self.nruns = n
+
+    def _check(self, rc):
+        if rc != FDTD_OK:
+            raise FdtdError(rc, self.lib.fdtd_batch_last_error(self.h).decode())
+
+    def step(self, n: int = 1):
+        self._check(self.lib.fdtd_batch_step(self.h, int(n)))
+
+    def info(self) -> dict:
+        dt, st, c, nd, ncl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        self._check(self.lib.fdtd_batch_info(self.h, ctypes.byref(dt), ctypes.byref(st), ctypes.byref(c),
+                                             ctypes.byref(nd), ctypes.byref(ncl)))
+        return dict(dt=dt.value, steps=st.value, cells=c.value, nodes=nd.value, clusters=ncl.value)
+
+    def read(self, run: int, name: str):
+        """Host numpy copy of one quantity of one run (ex, hy, j, df)."""
+        torch = self.torch
+        q = QUANTITY[name]
+        nb = self.lib.fdtd_batch_quantity_bytes(self.h, int(run), q)
+        if name == "df":
+            dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[self.f_dtype]
+        else:
+            dt = torch.float64 if self.precision == "f64" else torch.float32
+        out = torch.empty(nb // torch.empty((), dtype=dt).element_size(), dtype=dt)
+        if nb:
+            self._check(self.lib.fdtd_batch_read(self.h, int(run), q, out.data_ptr(), nb, 0))
+        return out.float().numpy() if dt == torch.bfloat16 else out.numpy()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fdtd_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ Solver
