@@ -201,6 +201,60 @@ int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int buf_is_
 int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int buf_is_device);
 
 /* ---------------------------------------------------------------------
+ * Learned J closure (not in the paper: a small network standing in for the
+ * Sec. 5.2 velocity-space update).  Per plasma cell with n <= n_train_max:
+ *   x = [E^{n-15} .. E^n] / e_scale ++ [n / n_scale]          (17 inputs)
+ *   y = MLP(x): 17 -> 128 -> 128 -> 1, exact-erf GELU on both hidden layers,
+ *       BF16 tensor-core operands, FP32 accumulation
+ *   J^{n+1/2} = rho J^{n-1/2} + j_scale y   (rho = 0: the direct form)
+ *   E^n <- E^n - dt/eps0 J^{n+1/2}
+ * Cells with n > n_train_max keep the kinetic update.
+ * Parameters: FDTD_MLP_NPARAMS FP32 values packed
+ *   W1[17][128] b1[128] W2[128][128] b2[128] W3[128] b3[1]  (row-major, y = ((x W1 + b1) ...)). */
+#define FDTD_MLP_NIN 17
+#define FDTD_MLP_NHID 128
+#define FDTD_MLP_NPARAMS 18945
+
+typedef struct {
+    const float *params;        /* FDTD_MLP_NPARAMS floats, host or device, copied */
+    int32_t params_on_device;
+    int32_t reserved;
+    double e_scale, j_scale, n_scale, rho, n_train_max;
+} fdtd_closure_desc;
+
+/* Switch a plasma to the closure (FP32 grids, after set_plasma, before the
+ * first step).  Re-lays the slots out: kinetic (fallback) cells first, then
+ * closure cells, each in increasing cell index; FDTD_J follows that order,
+ * FDTD_DF holds only the kinetic rows. */
+int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c);
+int fdtd_plasma_closure_shape(fdtd_plasma_t h, int64_t *n_kinetic, int64_t *n_closure);
+
+/* Training-data recorder (kinetic FP32 runs): from the next step on, every
+ * plasma cell keeps a 16-step ring of E^n, and each (cell, step) pair is
+ * selected with probability `rate` by a counter-based draw keyed by `seed`;
+ * a selected pair appends [E^{n-15} .. E^n, n, J^{n+1/2}, J^{n-1/2}] (19
+ * floats) at samples[19 * atomicAdd(count, 1)] while that index is below
+ * capacity (the counter keeps counting).  samples and count are caller-owned
+ * device memory; the caller zeroes count. */
+int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity, unsigned long long *count, double rate,
+                              uint64_t seed);
+
+/* Training / inference of the closure network on caller-owned device
+ * buffers (stream-ordered on `stream`):
+ *   forward  : y[b] = MLP(x[b]) for x [batch][17]
+ *   loss_grad: loss = mean (y - target)^2 and its gradient (packed like the
+ *              parameters, overwritten) -- BF16 tensor-core forward, FP32
+ *              backward; workspace of fdtd_mlp_workspace_bytes(batch) bytes
+ *   adam     : one Adam step (Kingma & Ba, bias-corrected, step count t >= 1)
+ *              on params with first / second moments m, v. */
+size_t fdtd_mlp_workspace_bytes(int64_t batch);
+int fdtd_mlp_forward(const float *params, const float *x, int64_t batch, float *y, void *stream);
+int fdtd_mlp_loss_grad(const float *params, const float *x, const float *target, int64_t batch, float *grad,
+                       float *loss, void *workspace, size_t workspace_bytes, void *stream);
+int fdtd_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t n, int64_t t, double lr, double beta1,
+                  double beta2, double eps, void *stream);
+
+/* ---------------------------------------------------------------------
  * Batches of independent 1-D runs (same step as above, per run), advanced by
  * one persistent kernel launch per fdtd_batch_step call (graph-captured).
  * Runs may differ in nz, Mur / PEC ends, density profile, nu0 and source;

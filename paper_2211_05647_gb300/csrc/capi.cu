@@ -177,14 +177,28 @@ bool pol_updated(const fdtd_plasma *h, int64_t c)
     return j >= 1 && k >= 1;
 }
 
+void free_closure(fdtd_plasma *h)
+{
+    dfree(h, h->hist); dfree(h, h->jprev); dfree(h, h->params);
+    h->hist = h->jprev = h->params = nullptr;
+    h->has_closure = 0;
+    h->has_recording = 0;
+    h->ncl = 0;
+    h->nkin = h->nslots;
+}
+
 void free_plasma(fdtd_plasma *h)
 {
+    free_closure(h);
     dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot); dfree(h, h->tab);
     dfree(h, h->dV);
     h->slot_cell = nullptr; h->dens = h->df = h->jslot = h->tab = nullptr; h->dV = nullptr;
     h->has_plasma = 0;
     h->nslots = 0;
+    h->nkin = 0;
     h->nnode = 0;
+    h->h_cells.clear();
+    h->h_dens.clear();
 }
 
 void drop_graphs(fdtd_plasma *h)
@@ -250,7 +264,11 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
     else
         launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep);
     if (ev) cudaEventRecord(ev[1], st);
-    if (h->has_plasma && h->nslots > 0) {
+    const bool rec = h->has_recording && sizeof(T) == 4;
+    if (rec)
+        launch_hist_push(st, h->slot_cell, h->nslots, reinterpret_cast<const float *>(f[pol_comp(h)]), h->hist,
+                         h->d_step, kstep);
+    if (h->has_plasma && h->nkin > 0) {
         KinArgs<T> a{};
         a.slot_cell = h->slot_cell;
         a.dens = reinterpret_cast<const T *>(h->dens);
@@ -258,7 +276,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         a.E = f[pol_comp(h)];
         a.jslot = reinterpret_cast<T *>(h->jslot);
         a.tab = reinterpret_cast<const T *>(h->tab);
-        a.nslots = h->nslots;
+        a.nslots = h->nkin;
         a.pitch = h->pitch;
         a.cj = cpe;
         a.seed = h->pl.seed;
@@ -267,6 +285,30 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         cudaError_t e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms);
         if (e != cudaSuccess) return e;
     }
+    if (h->has_closure && h->ncl > 0 && sizeof(T) == 4) {
+        ClosureArgs c{};
+        c.cell = h->slot_cell + h->nkin;
+        c.dens = reinterpret_cast<const float *>(h->dens) + h->nkin;
+        c.hist = h->hist;
+        c.jprev = h->jprev;
+        c.jslot = reinterpret_cast<float *>(h->jslot) + h->nkin;
+        c.E = reinterpret_cast<float *>(f[pol_comp(h)]);
+        c.P = h->params;
+        c.n = h->ncl;
+        c.inv_es = (float)(1.0 / h->cl.e_scale);
+        c.inv_ns = (float)(1.0 / h->cl.n_scale);
+        c.js = (float)h->cl.j_scale;
+        c.rho = (float)h->cl.rho;
+        c.cj = (float)cpe;
+        c.d_step = h->d_step;
+        c.kstep = kstep;
+        cudaError_t e = launch_closure(st, c, h->num_sms);
+        if (e != cudaSuccess) return e;
+    }
+    if (rec)
+        launch_record(st, h->nslots, h->hist, reinterpret_cast<const float *>(h->dens),
+                      reinterpret_cast<const float *>(h->jslot), h->jprev, h->rec_out, h->rec_cap, h->rec_count,
+                      h->rec_threshold, h->rec_seed, h->d_step, kstep);
     if (ev) cudaEventRecord(ev[2], st);
     if (h->g.ndim == 1) {
         launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep);
@@ -459,9 +501,11 @@ int fdtd_plasma_reset(fdtd_plasma_t h)
     for (int q = 0; q < 12; ++q)
         if (h->psi[q]) CK(h, cudaMemsetAsync(h->psi[q], 0, h->psilen[q] * h->esz, h->stream));
     if (h->has_plasma) {
-        CK(h, cudaMemsetAsync(h->df, 0, (size_t)h->nslots * h->pitch * h->df_esz, h->stream));
+        CK(h, cudaMemsetAsync(h->df, 0, (size_t)h->nkin * h->pitch * h->df_esz, h->stream));
         CK(h, cudaMemsetAsync(h->jslot, 0, (size_t)(h->nslots ? h->nslots : 1) * h->esz, h->stream));
     }
+    if (h->hist) CK(h, cudaMemsetAsync(h->hist, 0, (size_t)(h->has_closure ? h->ncl : h->nslots) * 16 * 4, h->stream));
+    if (h->jprev) CK(h, cudaMemsetAsync(h->jprev, 0, (size_t)(h->has_closure ? h->ncl : h->nslots) * 4, h->stream));
     CK(h, cudaMemsetAsync(h->mur_state, 0, 32, h->stream));
     CK(h, cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
     h->steps_done = 0;
@@ -574,6 +618,9 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
         return fail(h, FDTD_ERR_NOMEM, "plasma allocation failed (%zu cells x %d nodes)", ns, pitch);
     }
     h->has_plasma = 1;
+    h->nkin = (int64_t)ns;
+    h->h_cells = cells;
+    h->h_dens = dslot;
     if (ns) CK(h, cudaMemcpy(h->slot_cell, cells.data(), ns * 4, cudaMemcpyHostToDevice));
     if (h->esz == 8) {
         if (ns) CK(h, cudaMemcpy(h->dens, dslot.data(), ns * 8, cudaMemcpyHostToDevice));
@@ -618,6 +665,95 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
     return FDTD_OK;
 }
 
+int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
+{
+    if (!h || !c || !c->params) return FDTD_ERR_INVAL;
+    if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "set_closure needs a plasma (set_plasma first)");
+    if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_closure after stepping: call fdtd_plasma_reset first");
+    if (h->g.precision != FDTD_F32) return fail(h, FDTD_ERR_INVAL, "the closure runs on FP32 grids");
+    if (!(c->e_scale > 0) || !(c->n_scale > 0) || !std::isfinite(c->j_scale) || !std::isfinite(c->rho) ||
+        !(c->n_train_max >= 0))
+        return fail(h, FDTD_ERR_INVAL, "closure scales must be finite, e_scale and n_scale > 0");
+    std::vector<float> P(FDTD_MLP_NPARAMS);
+    if (c->params_on_device) CK(h, cudaMemcpy(P.data(), c->params, P.size() * 4, cudaMemcpyDeviceToHost));
+    else std::memcpy(P.data(), c->params, P.size() * 4);
+    for (float v : P)
+        if (!std::isfinite(v)) return fail(h, FDTD_ERR_NONFINITE, "closure parameters must be finite");
+    // re-layout: kinetic (fallback) slots first, closure slots after, each in cell order
+    std::vector<int32_t> cells;
+    std::vector<double> dens;
+    for (size_t q = 0; q < h->h_cells.size(); ++q)
+        if (h->h_dens[q] > c->n_train_max) { cells.push_back(h->h_cells[q]); dens.push_back(h->h_dens[q]); }
+    const int64_t nk = (int64_t)cells.size();
+    for (size_t q = 0; q < h->h_cells.size(); ++q)
+        if (!(h->h_dens[q] > c->n_train_max)) { cells.push_back(h->h_cells[q]); dens.push_back(h->h_dens[q]); }
+    const int64_t ns = (int64_t)cells.size(), nc = ns - nk;
+    drop_graphs(h);
+    free_closure(h);
+    dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot);
+    h->slot_cell = (int32_t *)dalloc(h, (ns ? ns : 1) * 4);
+    h->dens = dalloc(h, (ns ? ns : 1) * 4);
+    h->df = dalloc(h, (nk ? nk : 1) * h->pitch * h->df_esz);
+    h->jslot = dalloc(h, (ns ? ns : 1) * 4);
+    h->hist = (float *)dalloc(h, (nc ? nc : 1) * 16 * 4);
+    h->jprev = (float *)dalloc(h, (nc ? nc : 1) * 4);
+    h->params = (float *)dalloc(h, P.size() * 4);
+    if (!h->slot_cell || !h->dens || !h->df || !h->jslot || !h->hist || !h->jprev || !h->params) {
+        free_plasma(h);
+        return fail(h, FDTD_ERR_NOMEM, "closure allocation failed");
+    }
+    std::vector<float> d32(dens.begin(), dens.end());
+    if (ns) CK(h, cudaMemcpy(h->slot_cell, cells.data(), ns * 4, cudaMemcpyHostToDevice));
+    if (ns) CK(h, cudaMemcpy(h->dens, d32.data(), ns * 4, cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->params, P.data(), P.size() * 4, cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->df, 0, (nk ? nk : 1) * h->pitch * h->df_esz));
+    CK(h, cudaMemset(h->jslot, 0, (ns ? ns : 1) * 4));
+    CK(h, cudaMemset(h->hist, 0, (nc ? nc : 1) * 16 * 4));
+    CK(h, cudaMemset(h->jprev, 0, (nc ? nc : 1) * 4));
+    h->h_cells = cells;
+    h->h_dens = dens;
+    h->nkin = nk;
+    h->ncl = nc;
+    h->cl = *c;
+    h->cl.params = nullptr;
+    h->has_closure = 1;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_closure_shape(fdtd_plasma_t h, int64_t *n_kinetic, int64_t *n_closure)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (n_kinetic) *n_kinetic = h->nkin;
+    if (n_closure) *n_closure = h->ncl;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity, unsigned long long *count,
+                              double rate, uint64_t seed)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (!h->has_plasma || h->has_closure) return fail(h, FDTD_ERR_STATE, "recording needs a kinetic plasma, no closure");
+    if (h->g.precision != FDTD_F32) return fail(h, FDTD_ERR_INVAL, "recording runs on FP32 grids");
+    if (!samples || !count || capacity < 1 || !(rate > 0) || rate > 1)
+        return fail(h, FDTD_ERR_INVAL, "recording needs a buffer, a counter, capacity >= 1 and 0 < rate <= 1");
+    drop_graphs(h);
+    if (!h->hist) {
+        const int64_t ns = h->nslots ? h->nslots : 1;
+        h->hist = (float *)dalloc(h, ns * 16 * 4);
+        h->jprev = (float *)dalloc(h, ns * 4);
+        if (!h->hist || !h->jprev) return fail(h, FDTD_ERR_NOMEM, "recorder allocation failed");
+        CK(h, cudaMemset(h->hist, 0, ns * 16 * 4));
+        CK(h, cudaMemset(h->jprev, 0, ns * 4));
+    }
+    h->rec_out = samples;
+    h->rec_cap = capacity;
+    h->rec_count = count;
+    h->rec_threshold = rate >= 1.0 ? 0xffffffffu : (uint32_t)(rate * 4294967296.0);
+    h->rec_seed = seed;
+    h->has_recording = 1;
+    return FDTD_OK;
+}
+
 int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out)
 {
     if (!h || !ms_out || nsteps < 1) return FDTD_ERR_INVAL;
@@ -657,7 +793,7 @@ size_t fdtd_plasma_quantity_bytes(fdtd_plasma_t h, int which)
     if (!h) return 0;
     if (which >= 0 && which <= 5) return field_bytes(h, which);
     if (which == FDTD_J) return h->has_plasma ? (size_t)h->nslots * h->esz : 0;
-    if (which == FDTD_DF) return h->has_plasma ? (size_t)h->nslots * h->nnode * h->df_esz : 0;
+    if (which == FDTD_DF) return h->has_plasma ? (size_t)h->nkin * h->nnode * h->df_esz : 0;
     return 0;
 }
 
@@ -672,9 +808,9 @@ static int copy_quantity(fdtd_plasma_t h, int which, void *host_or_dev, size_t b
     if (which == FDTD_DF) {
         const size_t row = (size_t)h->nnode * h->df_esz, dpitch = (size_t)h->pitch * h->df_esz;
         if (out)
-            CK(h, cudaMemcpy2DAsync(host_or_dev, row, h->df, dpitch, row, h->nslots, kind, h->stream));
+            CK(h, cudaMemcpy2DAsync(host_or_dev, row, h->df, dpitch, row, h->nkin, kind, h->stream));
         else
-            CK(h, cudaMemcpy2DAsync(h->df, dpitch, host_or_dev, row, row, h->nslots, kind, h->stream));
+            CK(h, cudaMemcpy2DAsync(h->df, dpitch, host_or_dev, row, row, h->nkin, kind, h->stream));
     } else {
         void *dev = which == FDTD_J ? h->jslot : h->f[which];
         if (out) CK(h, cudaMemcpyAsync(host_or_dev, dev, bytes, kind, h->stream));
@@ -725,7 +861,7 @@ int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
     a.eps0_half_dv = 0.5 * kEps0 * dv;
     a.mu0_half_dv = 0.5 * mu0 * dv;
     a.df = h->df;
-    a.nslots = h->has_plasma ? h->nslots : 0;
+    a.nslots = h->has_plasma ? h->nkin : 0;
     a.nnode = h->nnode;
     a.pitch = h->pitch;
     a.f_dtype = h->pl.f_dtype;
@@ -755,8 +891,13 @@ static size_t state_parts(fdtd_plasma_t h, std::vector<std::pair<void *, size_t>
     for (int q = 0; q < 12; ++q)
         if (h->psi[q]) parts.push_back({h->psi[q], (size_t)h->psilen[q] * h->esz});
     if (h->has_plasma && h->nslots) {
-        parts.push_back({h->df, (size_t)h->nslots * h->pitch * h->df_esz});
+        if (h->nkin) parts.push_back({h->df, (size_t)h->nkin * h->pitch * h->df_esz});
         parts.push_back({h->jslot, (size_t)h->nslots * h->esz});
+    }
+    const int64_t nh = h->has_closure ? h->ncl : (h->has_recording ? h->nslots : 0);
+    if (nh && h->hist) {
+        parts.push_back({h->hist, (size_t)nh * 16 * 4});
+        parts.push_back({h->jprev, (size_t)nh * 4});
     }
     parts.push_back({h->mur_state, 32});
     parts.push_back({h->d_step, sizeof(int64_t)});

@@ -1,0 +1,144 @@
+// closure.cu -- the learned J closure inside the time step, and the recorder
+// that harvests its training data from kinetic runs.
+//
+// The closure stands in for the Sec. 5.2 velocity-space update of a plasma
+// cell: from the cell's last 16 values of E (a ring buffer, E^{n-15..n}) and
+// its density it predicts
+//     J^{n+1/2} = rho J^{n-1/2} + J_s y,   y = MLP(E^{n-15..n} / E_s, n / n_s)
+// (rho = 0 gives the direct form J = J_s y), then applies the Ampere source
+// term E <- E - dt/eps0 J^{n+1/2} like the kinetic kernel.  Cells denser than
+// the training range keep the kinetic update (they are separate slots).
+//
+// Recording (kinetic runs): before the kinetic kernel every plasma cell pushes
+// E^n into its ring; after it, a seeded counter-based draw selects about
+// `rate` of the (cell, step) pairs, and each selected pair appends one sample
+//     [E^{n-15} .. E^n, n, J^{n+1/2}, J^{n-1/2}]   (19 floats)
+// to the caller's buffer.
+#include "mlp.cuh"
+
+namespace fp {
+
+
+__global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
+    __shared__ int32_t s_cell[kMlpRows];
+    __shared__ float s_e[kMlpRows];
+    mlp_load_weights(s, a.P);
+    const int64_t step = *a.d_step + a.kstep;
+    const int ring = (int)(step & 15);
+    const int64_t ntiles = (a.n + kMlpRows - 1) / kMlpRows;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row0 = tile * kMlpRows;
+        const int r = threadIdx.x;
+        if (r < kMlpRows) {
+            const int64_t slot = row0 + r;
+            float x[kMlpK1];
+#pragma unroll
+            for (int k = 0; k < kMlpK1; ++k) x[k] = 0.0f;
+            if (slot < a.n) {
+                const int32_t c = a.cell[slot];
+                const float e = a.E[c];
+                float *h = a.hist + slot * 16;
+                h[ring] = e;
+                float hv[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v = reinterpret_cast<const float4 *>(h)[q];
+                    hv[4 * q] = v.x; hv[4 * q + 1] = v.y; hv[4 * q + 2] = v.z; hv[4 * q + 3] = v.w;
+                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k) x[k] = hv[(ring + 1 + k) & 15] * a.inv_es;   // oldest first
+                x[16] = a.dens[slot] * a.inv_ns;
+                s_cell[r] = c;
+                s_e[r] = e;
+            }
+#pragma unroll
+            for (int k = 0; k < kMlpK1; k += 2)
+                *reinterpret_cast<uint32_t *>(&s.x[r][k]) = pack_bf16(x[k], x[k + 1]);
+        }
+        __syncthreads();
+        mlp_tile_forward(s, nullptr);
+        __syncthreads();
+        if (r < kMlpRows) {
+            const int64_t slot = row0 + r;
+            if (slot < a.n) {
+                const float J = a.rho * a.jprev[slot] + a.js * s.y[r];
+                a.jprev[slot] = J;
+                a.jslot[slot] = J;
+                a.E[s_cell[r]] = s_e[r] - a.cj * J;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_hist_push(const int32_t *__restrict__ cell, int64_t n, const float *__restrict__ E,
+                            float *__restrict__ hist, const int64_t *__restrict__ d_step, int kstep)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int ring = (int)((*d_step + kstep) & 15);
+    hist[s * 16 + ring] = E[cell[s]];
+}
+
+__global__ void k_record(int64_t n, const float *__restrict__ hist, const float *__restrict__ dens,
+                         const float *__restrict__ jslot, float *__restrict__ jprev, float *__restrict__ out,
+                         int64_t capacity, unsigned long long *__restrict__ count, uint32_t threshold, uint64_t seed,
+                         const int64_t *__restrict__ d_step, int kstep)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int64_t step = *d_step + kstep;
+    const float J = jslot[s], Jp = jprev[s];
+    const uint4 r = philox4x32_7(make_uint4((uint32_t)s, (uint32_t)(s >> 32), (uint32_t)step, (uint32_t)(step >> 32)),
+                                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    if (r.x < threshold) {
+        const unsigned long long idx = atomicAdd(count, 1ull);
+        if ((int64_t)idx < capacity) {
+            const int ring = (int)(step & 15);
+            float *o = out + (int64_t)idx * 19;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) o[k] = hist[s * 16 + ((ring + 1 + k) & 15)];
+            o[16] = dens[s];
+            o[17] = J;
+            o[18] = Jp;
+        }
+    }
+    jprev[s] = J;
+}
+
+size_t closure_smem_bytes() { return sizeof(MlpSmem); }
+
+cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
+{
+    if (a.n == 0) return cudaSuccess;
+    const size_t smem = sizeof(MlpSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure, 256, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * std::max(per_sm, 1));
+    k_closure<<<(unsigned)grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+void launch_hist_push(cudaStream_t st, const int32_t *cell, int64_t n, const float *E, float *hist,
+                      const int64_t *d_step, int kstep)
+{
+    if (n) k_hist_push<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cell, n, E, hist, d_step, kstep);
+}
+
+void launch_record(cudaStream_t st, int64_t n, const float *hist, const float *dens, const float *jslot, float *jprev,
+                   float *out, int64_t capacity, unsigned long long *count, uint32_t threshold, uint64_t seed,
+                   const int64_t *d_step, int kstep)
+{
+    if (n)
+        k_record<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, hist, dens, jslot, jprev, out, capacity, count,
+                                                              threshold, seed, d_step, kstep);
+}
+
+}  // namespace fp

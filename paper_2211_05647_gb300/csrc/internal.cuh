@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fdtd_plasma.h"
 
@@ -141,6 +142,26 @@ struct DiagArgs {
 // out[0..6): energy, energy_plain, number, number_max_cell, number_abs, finite
 cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, int max_blocks, double *out);
 
+struct ClosureArgs {
+    const int32_t *cell;
+    const float *dens;
+    float *hist;       // [slot][16] ring of E^{n-15..n}
+    float *jprev;      // J^{n-1/2} per slot
+    float *jslot;      // J^{n+1/2} per slot (output)
+    float *E;
+    const float *P;    // packed FP32 network parameters
+    int64_t n;
+    float inv_es, inv_ns, js, rho, cj;
+    const int64_t *d_step;
+    int kstep;
+};
+cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms);
+void launch_hist_push(cudaStream_t st, const int32_t *cell, int64_t n, const float *E, float *hist,
+                      const int64_t *d_step, int kstep);
+void launch_record(cudaStream_t st, int64_t n, const float *hist, const float *dens, const float *jslot, float *jprev,
+                   float *out, int64_t capacity, unsigned long long *count, uint32_t threshold, uint64_t seed,
+                   const int64_t *d_step, int kstep);
+
 }  // namespace fp
 
 // Record msg as the library-wide error (fdtd_plasma_last_error(NULL)) and return code.
@@ -176,6 +197,21 @@ struct fdtd_plasma {
     void *dens, *df, *jslot, *tab;
     double *dV;               // per node (FP64) for the diagnostics
     size_t df_esz;
+    int64_t nkin;             // slots [0, nkin) take the kinetic update (all, unless a closure is set)
+    std::vector<int32_t> h_cells;   // host copies of the slot layout
+    std::vector<double> h_dens;
+    // learned closure: slots [nkin, nslots)
+    int has_closure;
+    int64_t ncl;
+    float *hist, *jprev, *params;
+    fdtd_closure_desc cl;
+    // training-data recorder
+    int has_recording;
+    float *rec_out;
+    int64_t rec_cap;
+    unsigned long long *rec_count;
+    uint32_t rec_threshold;
+    uint64_t rec_seed;
     // source
     int has_source;
     fdtd_source_desc src;

@@ -85,6 +85,17 @@ class fdtd_diag_arrays(ctypes.Structure):
                 ("nslots", ctypes.c_int64), ("nnode", ctypes.c_int64), ("dV", ctypes.c_void_p)]
 
 
+class fdtd_closure_desc(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("params_on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("e_scale", ctypes.c_double), ("j_scale", ctypes.c_double), ("n_scale", ctypes.c_double),
+                ("rho", ctypes.c_double), ("n_train_max", ctypes.c_double)]
+
+
+MLP_NPARAMS = 18945
+MLP_NIN = 17
+MLP_NHID = 128
+
+
 class fdtd_run_desc(ctypes.Structure):
     _fields_ = [("grid", fdtd_grid_desc), ("plasma", fdtd_plasma_desc), ("source", fdtd_source_desc)]
 
@@ -116,6 +127,20 @@ SIGNATURES = {
     "fdtd_plasma_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "fdtd_plasma_set_closure": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_closure_desc)]),
+    "fdtd_plasma_closure_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_int64)]),
+    "fdtd_plasma_set_recording": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                 ctypes.c_double, ctypes.c_uint64]),
+    "fdtd_mlp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "fdtd_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
+    "fdtd_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
+    "fdtd_mlp_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
     "fdtd_batch_create": (ctypes.c_int, [ctypes.POINTER(fdtd_run_desc), ctypes.c_int32,
                                          ctypes.POINTER(fdtd_runtime_desc), ctypes.POINTER(ctypes.c_void_p)]),
     "fdtd_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -213,6 +238,58 @@ def _plasma_desc(density_ptr, on_device, vgrid="signed1d", nv=64, nv_perp=1, te_
     d.nu_model, d.f_dtype, d.nonlinear = NU_MODEL[nu_model], DF_DTYPE[f_dtype], int(nonlinear)
     d.seed = int(seed)
     return d
+
+
+# ------------------------------------------------------------ closure network
+def mlp_forward(params, x, stream=None):
+    """y = MLP(x) on the GPU (params [18945], x [B, 17]; torch float32 cuda tensors)."""
+    import torch
+    lib = load_library()
+    x = x.contiguous()
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
+    _check(lib, None, lib.fdtd_mlp_forward(params.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr(), st))
+    return y
+
+
+class MlpTrainer:
+    """Mean-squared-error training of the closure network with the library's
+    own GPU kernels: loss + gradient (fdtd_mlp_loss_grad) and Adam
+    (fdtd_mlp_adam), on torch device buffers."""
+
+    def __init__(self, params, batch: int, lr=1e-3, betas=(0.9, 0.999), eps=1e-8):
+        import torch
+        self.torch = torch
+        self.lib = load_library()
+        self.p = params
+        self.dev = params.device
+        self.grad = torch.zeros_like(params)
+        self.m = torch.zeros_like(params)
+        self.v = torch.zeros_like(params)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.dev)
+        self.ws_bytes = self.lib.fdtd_mlp_workspace_bytes(batch)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.dev)
+        self.batch = batch
+        self.t = 0
+        self.lr, self.betas, self.eps = lr, betas, eps
+
+    def loss_grad(self, x, t):
+        st = self.torch.cuda.current_stream(self.dev).cuda_stream
+        assert x.shape[0] <= self.batch
+        _check(self.lib, None, self.lib.fdtd_mlp_loss_grad(self.p.data_ptr(), x.data_ptr(), t.data_ptr(), x.shape[0],
+                                                           self.grad.data_ptr(), self.loss.data_ptr(),
+                                                           self.ws.data_ptr(), self.ws_bytes, st))
+        return self.loss, self.grad
+
+    def step(self, x, t, lr=None):
+        self.loss_grad(x, t)
+        self.t += 1
+        st = self.torch.cuda.current_stream(self.dev).cuda_stream
+        _check(self.lib, None, self.lib.fdtd_mlp_adam(self.p.data_ptr(), self.grad.data_ptr(), self.m.data_ptr(),
+                                                      self.v.data_ptr(), self.p.numel(), self.t,
+                                                      float(self.lr if lr is None else lr), self.betas[0],
+                                                      self.betas[1], self.eps, st))
+        return self.loss
 
 
 # ------------------------------------------------------------------ Batch
@@ -360,6 +437,34 @@ class Solver:
         d.seed = int(seed)
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_plasma(self.h, ctypes.byref(d)))
         self.f_dtype = f_dtype
+
+    def set_closure(self, params, e_scale, j_scale, n_scale, rho, n_train_max):
+        """Install the learned closure (params: torch / numpy FP32, 18945 values)."""
+        torch = self.torch
+        if isinstance(params, torch.Tensor):
+            p = params.detach().to(self.device, torch.float32).contiguous()
+            ptr, dev = p.data_ptr(), 1
+        else:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            ptr, dev = p.ctypes.data, 0
+        n = p.numel() if isinstance(p, torch.Tensor) else p.size
+        if n != MLP_NPARAMS:
+            raise ValueError("closure needs 18945 parameters")
+        d = fdtd_closure_desc(ptr, dev, 0, float(e_scale), float(j_scale), float(n_scale), float(rho),
+                              float(n_train_max))
+        _check(self.lib, self.h, self.lib.fdtd_plasma_set_closure(self.h, ctypes.byref(d)))
+
+    def closure_shape(self):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_closure_shape(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def set_recording(self, samples, count, rate, seed=0):
+        """Record training samples into the device tensors ``samples`` (float32,
+        capacity x 19) and ``count`` (one int64, zeroed by the caller)."""
+        cap = samples.numel() // 19
+        _check(self.lib, self.h, self.lib.fdtd_plasma_set_recording(self.h, samples.data_ptr(), cap, count.data_ptr(),
+                                                                    float(rate), int(seed)))
 
     # ---- stepping
     def step(self, n: int = 1):
