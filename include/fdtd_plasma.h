@@ -206,7 +206,10 @@ int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int b
  *   x = [E^{n-15} .. E^n] / e_scale ++ [n / n_scale]          (17 inputs)
  *   y = MLP(x): 17 -> 128 -> 128 -> 1, exact-erf GELU on both hidden layers,
  *       BF16 tensor-core operands, FP32 accumulation
- *   J^{n+1/2} = rho J^{n-1/2} + j_scale y   (rho = 0: the direct form)
+ *   J^{n+1/2} = rho J^{n-1/2} + beta n E^n + j_scale y
+ *       (beta n E^n is the Drude increment of a constant-collision plasma, so
+ *       the network learns the kinetic correction; rho = beta = 0 gives the
+ *       direct form J = j_scale y)
  *   E^n <- E^n - dt/eps0 J^{n+1/2}
  * Cells with n > n_train_max keep the kinetic update.
  * Parameters: FDTD_MLP_NPARAMS FP32 values packed
@@ -220,6 +223,7 @@ typedef struct {
     int32_t params_on_device;
     int32_t reserved;
     double e_scale, j_scale, n_scale, rho, n_train_max;
+    double beta;                /* Drude increment coefficient (A m / V per unit density) */
 } fdtd_closure_desc;
 
 /* Switch a plasma to the closure (FP32 grids, after set_plasma, before the

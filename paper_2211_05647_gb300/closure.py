@@ -3,11 +3,15 @@ training with the library's own GPU kernels.
 
 The closure replaces, for cells inside the training density range, the
 velocity-space update of Sec. 5.2 (the f_1x update and the Jx moment) by a
-17 -> 128 -> 128 -> 1 GELU network:
+17 -> 128 -> 128 -> 1 GELU network on top of the Crank-Nicolson Drude update
+of a plasma with the mean collision frequency nu:
     x = [E^{n-15} .. E^n] / E_s ++ [n / n_s]
-    J^{n+1/2} = rho J^{n-1/2} + J_s y,   rho = (2 - dt nu)/(2 + dt nu)
-(increment form; rho = 0 is the direct form).  E_s is the RMS of E over the
-training samples, J_s = eps0 w0 E_s, n_s the critical density at w0.  Every
+    J^{n+1/2} = rho J^{n-1/2} + beta n E^n + J_s y
+    rho = (2 - dt nu)/(2 + dt nu),  beta = 2 dt (e^2/m) / (2 + dt nu)
+so the network learns only the kinetic correction (what the velocity-
+dependent collision frequency adds to the Drude response).  E_s is the RMS
+of E over the training samples, n_s the critical density at w0, and J_s the
+RMS of the correction itself (targets of unit variance).  Every
 step of the pipeline runs on the GPU: the kinetic runs record their samples
 in-kernel, and the loss, its gradient and the Adam update are library kernels.
 """
@@ -51,11 +55,24 @@ def record_samples(spec, steps: int, rate: float, seed: int, capacity: int, devi
     return out
 
 
+def _residual(samples, rho, beta):
+    s = samples.double()
+    return s[:, 17] - rho * s[:, 18] - beta * s[:, 16] * s[:, 15]
+
+
 def scales(samples, omega0: float, dt: float, nu_mean: float, increment: bool = True) -> dict:
+    """Normalisations and the Drude part for the closure desc (see module doc);
+    increment=False gives the direct form (rho = beta = 0)."""
     e_s = float(samples[:, :16].double().pow(2).mean().sqrt().item())
     n_c = EPS0 * ME * omega0 ** 2 / QE ** 2
-    rho = (2.0 - dt * nu_mean) / (2.0 + dt * nu_mean) if increment else 0.0
-    return dict(e_scale=e_s, j_scale=EPS0 * omega0 * e_s, n_scale=n_c, rho=rho)
+    if increment:
+        rho = (2.0 - dt * nu_mean) / (2.0 + dt * nu_mean)
+        beta = 2.0 * dt * (QE * QE / ME) / (2.0 + dt * nu_mean)
+    else:
+        rho = beta = 0.0
+    r = _residual(samples, rho, beta)
+    j_s = float(r.pow(2).mean().sqrt().item()) or EPS0 * omega0 * e_s
+    return dict(e_scale=e_s, j_scale=j_s, n_scale=n_c, rho=rho, beta=beta)
 
 
 def dataset(samples, sc: dict):
@@ -64,7 +81,7 @@ def dataset(samples, sc: dict):
     x = torch.empty(samples.shape[0], NIN, dtype=torch.float32, device=samples.device)
     x[:, :16] = samples[:, :16] / sc["e_scale"]
     x[:, 16] = samples[:, 16] / sc["n_scale"]
-    t = (samples[:, 17] - sc["rho"] * samples[:, 18]) / sc["j_scale"]
+    t = (_residual(samples, sc["rho"], sc["beta"]) / sc["j_scale"]).float()
     return x.contiguous(), t.contiguous()
 
 

@@ -9,8 +9,10 @@
 // CTA.  Per step a CTA updates H on its range, the cluster synchronises
 // (hardware barrier: neighbouring ranges exchange their edge values through
 // global memory / L2), the CTA updates the delta-f rows of its plasma nodes
-// (E <- E - dt/eps0 J in place), then E, the source and the Mur ends on its
-// range, and the cluster synchronises again.  Clusters never wait for each
+// (E <- E - dt/eps0 J in place; the run's per-node tables are staged in shared
+// memory, the next row's node index is prefetched), then E, the source and
+// the Mur ends on its range, and the cluster synchronises again.  The H and E
+// loops give each thread four independent nodes per round.  Clusters never wait for each
 // other.  Cuts never separate node 0 from node 1 or node nz-1 from node nz,
 // so the thread that advances E_1 (E_{nz-1}) also applies the Mur update to
 // E_0 (E_nz) with values it owns.
@@ -81,15 +83,20 @@ template <typename TS, typename T, int VPL, int L>
 __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
 {
     cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *s_al = reinterpret_cast<T *>(smem_raw);   // alpha, beta of the segment's run, shared w'
+    T *s_be = s_al + a.pitch, *s_w = s_be + a.pitch;
     using V = typename Vec<TS>::type;
     constexpr int VEC = Vec<TS>::n;
     constexpr int R = 32 / L;
+    constexpr int U = 4;                         // H / E nodes per thread per round (independent loads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane / L, l = lane % L;
     const int nwarps = blockDim.x >> 5;
     const int seg0 = a.cta_seg0[blockIdx.x], seg1 = a.cta_seg0[blockIdx.x + 1];
     const int64_t step0 = *a.d_step;
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    for (int t = threadIdx.x; t < a.pitch; t += blockDim.x) s_w[t] = a.tab_w[t];
 
     for (int s = 0; s < a.nsteps; ++s) {
         const int64_t step = step0 + s;
@@ -100,7 +107,19 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
             const T *E = a.E + r.e_off;
             T *H = a.H + r.h_off;
             const int kend = min(sg.k1, r.nz);
-            for (int k = sg.k0 + threadIdx.x; k < kend; k += blockDim.x) H[k] -= a.ch * (E[k + 1] - E[k]);
+            for (int kb = sg.k0 + threadIdx.x; kb < kend; kb += U * blockDim.x) {
+                T e0[U], e1[U], h[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = kb + u * blockDim.x;
+                    if (k < kend) { e0[u] = E[k]; e1[u] = E[k + 1]; h[u] = H[k]; }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = kb + u * blockDim.x;
+                    if (k < kend) H[k] = h[u] - a.ch * (e1[u] - e0[u]);
+                }
+            }
             if (r.mur && threadIdx.x == 0) {
                 if (sg.k0 <= 1 && 1 < sg.k1) a.mur[2 * sg.run] = E[1];
                 if (sg.k0 <= r.nz - 1 && r.nz - 1 < sg.k1) a.mur[2 * sg.run + 1] = E[r.nz - 1];
@@ -110,26 +129,38 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
         // ---- delta-f rows of this CTA's plasma nodes; E <- E - dt/eps0 J
         for (int q = seg0; q < seg1; ++q) {
             const BSeg sg = a.segs[q];
+            if (sg.s1 <= sg.s0) continue;
             const BRun r = a.runs[sg.run];
             T *E = a.E + r.e_off;
-            const T *al = a.tab + (int64_t)sg.run * 2 * a.pitch, *be = al + a.pitch;
+            const T *al = a.tab + (int64_t)sg.run * 2 * a.pitch;
+            __syncthreads();                           // previous segment's tables no longer in use
+            for (int t = threadIdx.x; t < a.pitch; t += blockDim.x) {
+                s_al[t] = al[t];
+                s_be[t] = al[a.pitch + t];
+            }
+            __syncthreads();
+            // the next row group's node index is fetched one iteration ahead, so
+            // the E gather of a row issues together with its delta-f loads
+            int row = sg.s0 + warp * R + sub;
+            int node_next = row < sg.s1 ? __ldg(a.slot_node + r.row_off + row) : 0;
             for (int base = sg.s0 + warp * R; base < sg.s1; base += nwarps * R) {
-                const int row = base + sub;
+                row = base + sub;
                 const bool valid = row < sg.s1;
                 const int64_t grow = r.row_off + (valid ? row : sg.s0);
+                const int node = node_next;
                 V *rp = reinterpret_cast<V *>(a.df) + grow * (a.pitch / VEC);
                 V v[VPL];
                 T e = T(0), nE = T(0);
-                int node = 0;
                 if (valid) {
 #pragma unroll
                     for (int qq = 0; qq < VPL; ++qq) v[qq] = __ldcs(rp + qq * L + l);
-                    node = __ldg(a.slot_node + grow);
                     e = E[node];
                     nE = __ldg(a.dens + grow) * e;
                 }
+                const int rn = row + nwarps * R;
+                node_next = rn < sg.s1 ? __ldg(a.slot_node + r.row_off + rn) : 0;
                 T sm = T(0), cm = T(0);
-                if (valid) row_update<TS, T, VPL, L>(rp, v, al, be, a.tab_w, nE, l, (uint32_t)grow, step, key, sm, cm);
+                if (valid) row_update<TS, T, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)grow, step, key, sm, cm);
                 const T J = row_reduce<T, L>(sm, cm);
                 if (valid && l == 0) {
                     a.jslot[grow] = J;
@@ -145,13 +176,24 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
             T *E = a.E + r.e_off;
             const T *H = a.H + r.h_off;
             const int kbeg = max(sg.k0, 1), kend = min(sg.k1, r.nz);
-            for (int k = kbeg + threadIdx.x; k < kend; k += blockDim.x) {
-                T v = E[k] - a.ce * (H[k] - H[k - 1]);
-                if (k == r.src_k) v += (T)batch_source(r, (double)(step + 1) * a.dt);
-                E[k] = v;
-                if (r.mur) {
-                    if (k == 1) E[0] = a.mur[2 * sg.run] + (T)r.mur_m * (v - E[0]);
-                    if (k == r.nz - 1) E[r.nz] = a.mur[2 * sg.run + 1] + (T)r.mur_m * (v - E[r.nz]);
+            for (int kb = kbeg + threadIdx.x; kb < kend; kb += U * blockDim.x) {
+                T ev[U], h0[U], h1[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = kb + u * blockDim.x;
+                    if (k < kend) { ev[u] = E[k]; h0[u] = H[k - 1]; h1[u] = H[k]; }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int k = kb + u * blockDim.x;
+                    if (k >= kend) continue;
+                    T v = ev[u] - a.ce * (h1[u] - h0[u]);
+                    if (k == r.src_k) v += (T)batch_source(r, (double)(step + 1) * a.dt);
+                    E[k] = v;
+                    if (r.mur) {
+                        if (k == 1) E[0] = a.mur[2 * sg.run] + (T)r.mur_m * (v - E[0]);
+                        if (k == r.nz - 1) E[r.nz] = a.mur[2 * sg.run + 1] + (T)r.mur_m * (v - E[r.nz]);
+                    }
                 }
             }
         }
@@ -242,6 +284,7 @@ cudaError_t launch_t(fdtd_batch *b, cudaStream_t st, int nsteps)
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(b->nclusters * kClusterCtas);
     cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = 3 * (size_t)b->pitch * sizeof(T);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -262,6 +305,7 @@ int max_clusters()
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(kClusterCtas);
     cfg.blockDim = dim3(kBatchThreads);
+    cfg.dynamicSmemBytes = 3 * 128 * 16;   // tables of the largest row (128 vectors of 16 bytes)
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kClusterCtas;

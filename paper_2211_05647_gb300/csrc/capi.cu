@@ -299,6 +299,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         c.inv_ns = (float)(1.0 / h->cl.n_scale);
         c.js = (float)h->cl.j_scale;
         c.rho = (float)h->cl.rho;
+        c.beta = (float)h->cl.beta;
         c.cj = (float)cpe;
         c.d_step = h->d_step;
         c.kstep = kstep;
@@ -672,6 +673,7 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
     if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_closure after stepping: call fdtd_plasma_reset first");
     if (h->g.precision != FDTD_F32) return fail(h, FDTD_ERR_INVAL, "the closure runs on FP32 grids");
     if (!(c->e_scale > 0) || !(c->n_scale > 0) || !std::isfinite(c->j_scale) || !std::isfinite(c->rho) ||
+        !std::isfinite(c->beta) ||
         !(c->n_train_max >= 0))
         return fail(h, FDTD_ERR_INVAL, "closure scales must be finite, e_scale and n_scale > 0");
     std::vector<float> P(FDTD_MLP_NPARAMS);

@@ -4,8 +4,11 @@
 // The closure stands in for the Sec. 5.2 velocity-space update of a plasma
 // cell: from the cell's last 16 values of E (a ring buffer, E^{n-15..n}) and
 // its density it predicts
-//     J^{n+1/2} = rho J^{n-1/2} + J_s y,   y = MLP(E^{n-15..n} / E_s, n / n_s)
-// (rho = 0 gives the direct form J = J_s y), then applies the Ampere source
+//     J^{n+1/2} = rho J^{n-1/2} + beta n E^n + J_s y,   y = MLP(E^{n-15..n} / E_s, n / n_s)
+// where rho J^{n-1/2} + beta n E^n is the Crank-Nicolson Drude update of a
+// plasma with the mean collision frequency, so the network carries only the
+// kinetic correction (rho = beta = 0 gives the direct form J = J_s y), then
+// applies the Ampere source
 // term E <- E - dt/eps0 J^{n+1/2} like the kinetic kernel.  Cells denser than
 // the training range keep the kinetic update (they are separate slots).
 //
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
         if (r < kMlpRows) {
             const int64_t slot = row0 + r;
             if (slot < a.n) {
-                const float J = a.rho * a.jprev[slot] + a.js * s.y[r];
+                const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * s_e[r] + a.js * s.y[r];
                 a.jprev[slot] = J;
                 a.jslot[slot] = J;
                 a.E[s_cell[r]] = s_e[r] - a.cj * J;

@@ -151,7 +151,7 @@ struct ClosureArgs {
     float *E;
     const float *P;    // packed FP32 network parameters
     int64_t n;
-    float inv_es, inv_ns, js, rho, cj;
+    float inv_es, inv_ns, js, rho, cj, beta;
     const int64_t *d_step;
     int kstep;
 };

@@ -88,7 +88,7 @@ class fdtd_diag_arrays(ctypes.Structure):
 class fdtd_closure_desc(ctypes.Structure):
     _fields_ = [("params", ctypes.c_void_p), ("params_on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("e_scale", ctypes.c_double), ("j_scale", ctypes.c_double), ("n_scale", ctypes.c_double),
-                ("rho", ctypes.c_double), ("n_train_max", ctypes.c_double)]
+                ("rho", ctypes.c_double), ("n_train_max", ctypes.c_double), ("beta", ctypes.c_double)]
 
 
 MLP_NPARAMS = 18945
@@ -438,7 +438,7 @@ class Solver:
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_plasma(self.h, ctypes.byref(d)))
         self.f_dtype = f_dtype
 
-    def set_closure(self, params, e_scale, j_scale, n_scale, rho, n_train_max):
+    def set_closure(self, params, e_scale, j_scale, n_scale, rho, n_train_max, beta=0.0):
         """Install the learned closure (params: torch / numpy FP32, 18945 values)."""
         torch = self.torch
         if isinstance(params, torch.Tensor):
@@ -451,7 +451,7 @@ class Solver:
         if n != MLP_NPARAMS:
             raise ValueError("closure needs 18945 parameters")
         d = fdtd_closure_desc(ptr, dev, 0, float(e_scale), float(j_scale), float(n_scale), float(rho),
-                              float(n_train_max))
+                              float(n_train_max), float(beta))
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_closure(self.h, ctypes.byref(d)))
 
     def closure_shape(self):

@@ -142,7 +142,8 @@ def test_closure_constant_network():
 
 def test_closure_inference_matches_oracle_forward():
     """In-solver closure: after stepping, J of every closure cell equals
-    rho J_prev + J_s MLP(x) with x rebuilt from the E history it saw (FP64 oracle forward)."""
+    rho J_prev + beta n E^n + J_s MLP(x) with x rebuilt from the E history it
+    saw (FP64 oracle forward)."""
     from paper_2211_05647_gb300 import Solver
     spec = _closure_spec()
     s = Solver.from_spec(spec)
@@ -151,8 +152,8 @@ def test_closure_inference_matches_oracle_forward():
     cells = np.nonzero(dens > 0)[0]
     cells = cells[(cells % 160 >= 1) & (cells // 160 >= 1)]
     nmax = dens.max()
-    e_s, j_s, n_s, rho = 0.05, 1e-3, 1e18, 0.95
-    s.set_closure(flat, e_scale=e_s, j_scale=j_s, n_scale=n_s, rho=rho, n_train_max=nmax)
+    e_s, j_s, n_s, rho, beta = 0.05, 1e-3, 1e18, 0.95, 3e-21
+    s.set_closure(flat, e_scale=e_s, j_scale=j_s, n_scale=n_s, rho=rho, n_train_max=nmax, beta=beta)
     hist = []
     Jprev = np.zeros(len(cells))
     for n in range(60):
@@ -163,7 +164,7 @@ def test_closure_inference_matches_oracle_forward():
             H = np.stack(hist[-16:], axis=1) / e_s
             x = np.concatenate([H, (dens[cells] / n_s)[:, None]], axis=1)
             y, _ = M.forward(_oracle_params(flat), x)
-            want = rho * Jprev + j_s * y
+            want = rho * Jprev + beta * dens[cells] * hist[-1] + j_s * y
             err = rel_l2(J, want)
             print(f"closure J vs oracle forward: {err:.3e}")
             assert err <= 1e-2
@@ -187,13 +188,17 @@ def test_trained_closure_tracks_kinetic_solve():
     sc = C.scales(samples, OMEGA0, dt, sp["plasma"]["nu0"])
     x, t = C.dataset(samples, sc)
     params, hist = C.train(x, t, epochs=8, batch=4096, lr=2e-3, seed=3, log=print)
-    assert hist[-1] < 0.05 * hist[0]
+    assert hist[-1] < 0.5 * hist[0]
     kin = Solver.from_spec(sp)
-    clo = Solver.from_spec(sp)
-    nmax = float(np.max([np.max(spec(100 + k)["plasma"]["density"]) for k in range(3)]))
-    clo.set_closure(params, n_train_max=nmax, **sc)
     kin.step(700)
-    clo.step(700)
-    errs = {f: rel_l2(clo.read(f, device=False), kin.read(f, device=False)) for f in ("ez", "hx", "hy")}
-    print(f"closure vs kinetic after 700 steps: {errs}  (closure cells {clo.closure_shape()})")
-    assert max(errs.values()) <= 1e-2
+    nmax = float(np.max([np.max(spec(100 + k)["plasma"]["density"]) for k in range(3)]))
+    errs = {}
+    for name, p in (("drude only", torch.zeros_like(params)), ("trained", params)):
+        clo = Solver.from_spec(sp)
+        clo.set_closure(p, n_train_max=nmax, **sc)
+        clo.step(700)
+        errs[name] = max(rel_l2(clo.read(f, device=False), kin.read(f, device=False)) for f in ("ez", "hx", "hy"))
+        assert clo.closure_shape()[1] > 0
+    print(f"closure vs kinetic after 700 steps (max rel L2 over Ez, Hx, Hy): {errs}")
+    assert errs["trained"] <= 1e-2
+    assert errs["trained"] < errs["drude only"]
