@@ -282,7 +282,15 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         a.seed = h->pl.seed;
         a.d_step = h->d_step;
         a.kstep = kstep;
-        cudaError_t e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms);
+        cudaError_t e;
+        if (h->pl.nonlinear) {
+            const double vth = std::sqrt(kQe * h->pl.te_ev / kMe);
+            const double dvpar = 2.0 * h->pl.vmax_vth * vth / h->pl.nv;
+            const int nperp = h->pl.vgrid == FDTD_VGRID_CART2D ? h->pl.nv_perp : 1;
+            e = launch_kinetic_nl<T>(st, a, h->pl.nv, nperp, dvpar, kQe / kMe, h->dt, h->num_sms);
+        } else {
+            e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms);
+        }
         if (e != cudaSuccess) return e;
     }
     if (h->has_closure && h->ncl > 0 && sizeof(T) == 4) {
@@ -559,7 +567,8 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     const bool f64 = h->g.precision == FDTD_F64;
     if (f64 ? p->f_dtype != FDTD_DF_F64 : (p->f_dtype != FDTD_DF_F32 && p->f_dtype != FDTD_DF_BF16))
         return fail(h, FDTD_ERR_INVAL, "f_dtype does not match the field precision");
-    if (p->nonlinear) return fail(h, FDTD_ERR_INVAL, "the nonlinear advection mode is not available on the GPU path");
+    if (p->nonlinear && (p->vgrid == FDTD_VGRID_SPEED3D || p->f_dtype == FDTD_DF_BF16))
+        return fail(h, FDTD_ERR_INVAL, "the nonlinear mode needs a v_par grid (signed or Cartesian) and FP32/FP64 delta f");
     const int64_t nnode = p->vgrid == FDTD_VGRID_CART2D ? (int64_t)p->nv * p->nv_perp : p->nv;
     const int pitch = kinetic_pitch((int)nnode, p->f_dtype);
     const int vec = p->f_dtype == FDTD_DF_BF16 ? 8 : (p->f_dtype == FDTD_DF_F64 ? 2 : 4);

@@ -125,6 +125,10 @@ int kinetic_pitch(int nnode, int f_dtype);
 // returns cudaErrorInvalidValue for an unsupported combination
 template <typename TA>
 cudaError_t launch_kinetic(cudaStream_t st, const KinArgs<TA> &a, int f_dtype, int num_sms);
+// nonlinear mode (FP32 / FP64 storage): npar x nperp nodes, v_par spacing dvpar, qm = e/m
+template <typename T>
+cudaError_t launch_kinetic_nl(cudaStream_t st, const KinArgs<T> &a, int npar, int nperp, double dvpar, double qm,
+                              double dt, int num_sms);
 
 struct DiagArgs {
     int ndim;

@@ -142,3 +142,97 @@ cudaError_t launch_kinetic<double>(cudaStream_t st, const KinArgs<double> &a, in
 }
 
 }  // namespace fp
+
+// ===================================================================
+// Nonlinear mode: the advection of delta f itself by the acceleration
+// a = -(e/m) E, in flux form with donor-cell fluxes through the faces between
+// neighbouring v_par nodes and zero flux through +-vmax (so sum_j df_j dV_j is
+// conserved exactly), with the elastic collisions acting on the part of
+// delta f that is odd in v_par:
+//   odd^{n+1/2}  = alpha odd^{n-1/2} + beta n E + dt (1 + alpha)/2 A_odd
+//   even^{n+1/2} = even^{n-1/2} + dt A_even,   A_j = -(Phi_{a+1/2} - Phi_{a-1/2}) / dv_par
+// (dt (1 + alpha)/2 = 2 dt / (2 + dt nu)).  One warp per row: the old row is
+// staged in shared memory because every node reads its v_par neighbours and
+// its mirror node.  Node order j = a * nperp + b (a: v_par index).
+// ===================================================================
+
+namespace fp {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_kinetic_nl(KinArgs<T> a, int npar, int nperp, T dvpar, T qm, T dt)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nn = npar * nperp;
+    T *s_al = reinterpret_cast<T *>(smem_raw), *s_be = s_al + a.pitch, *s_w = s_be + a.pitch;
+    T *s_row = s_w + a.pitch + (threadIdx.x >> 5) * a.pitch;   // one row per warp
+    for (int t = threadIdx.x; t < 3 * a.pitch; t += blockDim.x) s_al[t] = a.tab[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    T *df = reinterpret_cast<T *>(a.df);
+    for (int64_t row = wg; row < a.nslots; row += nw) {
+        const int32_t cell = a.slot_cell[row];
+        const T E = a.E[cell];
+        const T nE = a.dens[row] * E;
+        const T acc = -qm * E;
+        T *g = df + row * a.pitch;
+        for (int j = lane; j < nn; j += 32) s_row[j] = g[j];
+        __syncwarp();
+        T s = T(0), c = T(0);
+        for (int j = lane; j < nn; j += 32) {
+            const int ia = j / nperp, ib = j - ia * nperp;
+            const int m = (npar - 1 - ia) * nperp + ib;
+            // A at node j and at its mirror: donor-cell fluxes through the faces of each
+            auto adv = [&](int aa) -> T {
+                T lo = T(0), hi = T(0);
+                if (aa > 0) lo = acc * (acc > T(0) ? s_row[(aa - 1) * nperp + ib] : s_row[aa * nperp + ib]);
+                if (aa < npar - 1) hi = acc * (acc > T(0) ? s_row[aa * nperp + ib] : s_row[(aa + 1) * nperp + ib]);
+                return -(hi - lo) / dvpar;
+            };
+            const T Aj = adv(ia), Am = adv(npar - 1 - ia);
+            const T odd = T(0.5) * (s_row[j] - s_row[m]), even = T(0.5) * (s_row[j] + s_row[m]);
+            const T aodd = T(0.5) * (Aj - Am), aeven = T(0.5) * (Aj + Am);
+            const T al = s_al[j];
+            const T x = even + dt * aeven + al * odd + s_be[j] * nE + dt * (T(1) + al) * T(0.5) * aodd;
+            g[j] = x;
+            T hi2, lo2;
+            two_sum(s, mul_rn(s_w[j], x), hi2, lo2);
+            s = hi2;
+            c += lo2;
+        }
+        __syncwarp();
+        const T J = row_reduce<T, 32>(s, c);
+        if (lane == 0) {
+            a.jslot[row] = J;
+            a.E[cell] = E - a.cj * J;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_kinetic_nl(cudaStream_t st, const KinArgs<T> &a, int npar, int nperp, double dvpar, double qm,
+                              double dt, int num_sms)
+{
+    if (a.nslots == 0) return cudaSuccess;
+    const size_t smem = (3 + 8) * (size_t)a.pitch * sizeof(T);
+    auto kern = k_kinetic_nl<T>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (a.nslots + 7) / 8;
+    blocks = std::min<int64_t>(blocks, (int64_t)num_sms * std::max(per_sm, 1));
+    kern<<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, st>>>(a, npar, nperp, (T)dvpar, (T)qm, (T)dt);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_kinetic_nl<float>(cudaStream_t, const KinArgs<float> &, int, int, double, double, double,
+                                              int);
+template cudaError_t launch_kinetic_nl<double>(cudaStream_t, const KinArgs<double> &, int, int, double, double,
+                                               double, int);
+
+}  // namespace fp

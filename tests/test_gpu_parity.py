@@ -258,3 +258,31 @@ def test_abi_errors():
     s.reset()
     s.set_plasma(np.full(101, 1e17), f_dtype="bf16")
     assert s.info()[1] == 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_nonlinear_mode_1d(oracle_lib, prec):
+    """Flux-form advection of delta f (strong field so it matters) vs the oracle;
+    the particle-number perturbation stays at rounding level."""
+    spec = spec_1d_slab(nz=500, slab=(200, 320), src_k=60, precision=prec, steps=900)
+    spec["source"]["amp"] = 3e5
+    spec["plasma"]["nonlinear"] = 1
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 1)
+    _report(f"1d nonlinear {prec}", errs)
+    # the advection term is really active: the even part of delta f is not small
+    df = sim.get("df")
+    assert np.abs(0.5 * (df + df[:, ::-1])).max() > 1e-6 * np.abs(df).max()
+    assert max(errs.values()) <= TOL[prec], errs
+    d = s.diagnostics()
+    assert abs(d["number"]) <= (1e-13 if prec == "f64" else 1e-6) * d["number_abs"]
+
+
+def test_nonlinear_mode_2d_cartesian(oracle_lib):
+    spec = _small_2d("f64", "f64", nx=120, ny=100, R=25, steps=300, nv=16, nv_perp=8)
+    spec["source"]["amp"] = 3e5
+    spec["plasma"]["nonlinear"] = 1
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 2)
+    _report("2d nonlinear f64", errs)
+    assert max(errs.values()) <= 1e-12, errs
