@@ -219,6 +219,8 @@ def main():
     spec = make_spec(args.workload)
     if isinstance(spec, list):
         return batch_bench(args, spec, rank, world, local)
+    if args.workload.endswith("_closure"):
+        return closure_bench(args, spec, rank, world, local)
     s = Solver.from_spec(spec, device=local)
     ns, nn = s.plasma_shape()
     cells = cells_of(spec)
@@ -332,6 +334,84 @@ def main():
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def closure_bench(args, spec, rank, world, local):
+    """Learned J closure vs the kinetic solve on the same grid.  Training data
+    come from kinetic runs of the 4096^2 cylinder recipe (three density seeds,
+    in-kernel recorder), training uses the library's own loss/grad and Adam
+    kernels (not timed); then the closure run and the kinetic run each do W
+    warm-up + K timed steps, their fields are compared, and the closure and
+    kinetic kernels are timed with events."""
+    import numpy as np
+    import torch
+    from fdtd_inputs import OMEGA0, closure_training_specs
+    from paper_2211_05647_gb300 import Solver
+    from paper_2211_05647_gb300 import closure as C
+    t_train0 = time.perf_counter()
+    tspecs = closure_training_specs()
+    samples = torch.cat([C.record_samples(sp, sp["steps"], 1e-3, 77 + i, 2_500_000, device=local)
+                         for i, sp in enumerate(tspecs)])
+    dt = spec["grid"]["courant"] * spec["grid"]["dx"] / 299792458.0
+    sc = C.scales(samples, OMEGA0, dt, spec["plasma"]["nu0"])
+    x, t = C.dataset(samples, sc)
+    params, hist = C.train(x, t, epochs=8, batch=4096, lr=2e-3, seed=5)
+    del x, t, samples
+    t_train = time.perf_counter() - t_train0
+    nmax = float(max(np.max(sp["plasma"]["density"]) for sp in tspecs))
+
+    def timed(with_closure):
+        s = Solver.from_spec(spec, device=local)
+        if with_closure:
+            s.set_closure(params, n_train_max=nmax, **sc)
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(args.steps)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        fields = {f: s.read(f, device=False) for f in ("ez", "hx", "hy")}
+        kt = s.time_kernels(20)
+        shape = s.closure_shape() if with_closure else (s.plasma_shape()[0], 0)
+        s.close()
+        torch.cuda.empty_cache()
+        return e0.elapsed_time(e1), fields, kt, shape
+
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    ms_c, f_c, kt_c, (n_kin, n_cl) = timed(True)
+    clk = clocks.stop()
+    ms_k, f_k, kt_k, _ = timed(False)
+    err = {f: float(np.linalg.norm(f_c[f].astype(np.float64) - f_k[f]) / np.linalg.norm(f_k[f].astype(np.float64)))
+           for f in f_c}
+    if rank != 0:
+        return 0
+    cells = cells_of(spec)
+    flops = 2 * (17 * 128 + 128 * 128 + 128) * n_cl
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+    achieved = flops / (kt_c["closure"] / 1e3) / 1e12 if kt_c["closure"] > 0 else 0.0
+    line = {"metric": METRIC, "value": cells * args.steps / (ms_c / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
+            "data": "synthetic (seeded density fields; training data from kinetic runs)",
+            "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"]],
+                       "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
+                       "training": {"runs": len(tspecs), "final_mse": hist[-1], "seconds": t_train},
+                       "l2": "inputs larger than L2"},
+            "closure_vs_kinetic": {"kinetic_ms_per_step": ms_k / args.steps, "closure_ms_per_step": ms_c / args.steps,
+                                   "speedup": ms_k / ms_c, "field_rel_l2": err,
+                                   "kinetic_gcell_per_s": cells * args.steps / (ms_k / 1e3) / 1e9},
+            "kernel_ms": {"closure_run": kt_c, "kinetic_run": kt_k},
+            "roofline": {"bound": "tensor", "kernel": "k_closure", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "alg_flops_per_launch": flops, "launch_ms": kt_c["closure"],
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
+            "gpu_launches": args.steps * (4 if n_kin else 3) + math.ceil(args.steps / 32),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
     return 0
 
 

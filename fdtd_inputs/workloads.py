@@ -158,6 +158,19 @@ def batch_runs_1d(nruns=256, seed=20221114, nz_range=(1024, 65536), slab_frac=(0
     return specs
 
 
+def spec_closure_8192(steps=4000, seed=20221115):
+    """Learned-closure comparison grid: 2-D TMz 8192^2, dx = lam0/20, the
+    4096^2 cylinder recipe scaled x2 (radius 1024, centre 4096^2, source at
+    (2048, 4096)) with peak w_p/w0 = 0.9, above the 0.8 of the training runs,
+    so the densest core keeps the kinetic update."""
+    return spec_2d_cylinder(n=8192, R=1024, wp_w0=0.9, steps=steps, seed=seed)
+
+
+def closure_training_specs(k=3, steps=2000, seed0=20221200):
+    """Kinetic training runs: the 4096^2 cylinder recipe with k density seeds."""
+    return [spec_2d_cylinder(steps=steps, seed=seed0 + i) for i in range(k)]
+
+
 # The benchmark workloads (full sizes) by name, plus reduced profiling cases
 WORKLOADS = {
     "1d_slab_fp64": lambda: spec_1d_slab(),
@@ -169,6 +182,7 @@ WORKLOADS = {
     # profiling cases: same recipes at half the lengths (inputs still larger than L2)
     "2d_tmz_2048_kinetic": lambda: spec_2d_cylinder(n=2048, R=256),
     "3d_256_kinetic_bf16": lambda: spec_3d_slab(n=256, slab=(96, 160), src_k=12),
+    "2d_tmz_8192_closure": lambda: spec_closure_8192(),
     "batch1d_256_f32": lambda: batch_runs_1d(),
     "batch1d_256_bf16": lambda: batch_runs_1d(f_dtype="bf16"),
 }

@@ -160,11 +160,12 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *pl);
 int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps);
 
 /* Advance nsteps >= 1 steps like fdtd_plasma_step, but launch each kernel
- * directly (no graph) with CUDA events around each of the three kernels of a
- * step, synchronising after every step.  ms_out[0..3] receive the average
- * duration per launch (ms) of the H-stencil kernel, the kinetic (delta f + J)
- * kernel, the E-stencil kernel (with the Mur ends in 1-D) and of a whole
- * step.  Meant for measurement; state advances exactly as with step. */
+ * directly (no graph) with CUDA events around each kernel of a step,
+ * synchronising after every step.  ms_out[0..4] receive the average duration
+ * per step (ms) of the H-stencil kernel, the kinetic (delta f + J) kernel,
+ * the closure kernel (0 without a closure), the E-stencil kernel (with the
+ * Mur ends in 1-D) and of a whole step.  Meant for measurement; state
+ * advances exactly as with step. */
 int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out);
 
 /* Zero every field, psi, delta f and J and the step counter (keeps the

@@ -243,8 +243,8 @@ Source source_view(fdtd_plasma *h)
 }
 
 // enqueue one step n -> n+1 (kstep = offset of this step inside the chunk);
-// ev (optional) receives records before H, before the kinetic kernel, before E
-// and after E.
+// ev (optional) receives records before H, before the kinetic kernel, before
+// the closure kernel, before E and after E.
 template <typename T>
 cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t *ev = nullptr)
 {
@@ -293,6 +293,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         }
         if (e != cudaSuccess) return e;
     }
+    if (ev) cudaEventRecord(ev[2], st);
     if (h->has_closure && h->ncl > 0 && sizeof(T) == 4) {
         ClosureArgs c{};
         c.cell = h->slot_cell + h->nkin;
@@ -318,7 +319,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         launch_record(st, h->nslots, h->hist, reinterpret_cast<const float *>(h->dens),
                       reinterpret_cast<const float *>(h->jslot), h->jprev, h->rec_out, h->rec_cap, h->rec_count,
                       h->rec_threshold, h->rec_seed, h->d_step, kstep);
-    if (ev) cudaEventRecord(ev[2], st);
+    if (ev) cudaEventRecord(ev[3], st);
     if (h->g.ndim == 1) {
         launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep);
         if (h->g.mur) {
@@ -330,7 +331,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
     } else {
         launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep);
     }
-    if (ev) cudaEventRecord(ev[3], st);
+    if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
 }
 
@@ -768,34 +769,34 @@ int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity,
 int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out)
 {
     if (!h || !ms_out || nsteps < 1) return FDTD_ERR_INVAL;
-    cudaEvent_t ev[4];
-    for (int q = 0; q < 4; ++q) CK(h, cudaEventCreate(&ev[q]));
-    double acc[4] = {0, 0, 0, 0};
+    cudaEvent_t ev[5];
+    for (int q = 0; q < 5; ++q) CK(h, cudaEventCreate(&ev[q]));
+    double acc[5] = {0, 0, 0, 0, 0};
     int rc = FDTD_OK;
     for (int64_t s = 0; s < nsteps && rc == FDTD_OK; ++s) {
         cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_step<double>(h, h->stream, 0, ev)
                                                    : enqueue_step<float>(h, h->stream, 0, ev);
         if (e == cudaSuccess) {
             launch_advance(h->stream, h->d_step, 1);
-            e = cudaEventSynchronize(ev[3]);
+            e = cudaEventSynchronize(ev[4]);
         }
         if (e != cudaSuccess) {
             rc = cuda_fail(h, e, "timed step");
             break;
         }
         float ms;
-        for (int q = 0; q < 3; ++q) {
+        for (int q = 0; q < 4; ++q) {
             cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
             acc[q] += ms;
         }
-        cudaEventElapsedTime(&ms, ev[0], ev[3]);
-        acc[3] += ms;
+        cudaEventElapsedTime(&ms, ev[0], ev[4]);
+        acc[4] += ms;
         h->steps_done += 1;
     }
-    for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
+    for (int q = 0; q < 5; ++q) cudaEventDestroy(ev[q]);
     if (rc != FDTD_OK) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
-    for (int q = 0; q < 4; ++q) ms_out[q] = acc[q] / (double)nsteps;
+    for (int q = 0; q < 5; ++q) ms_out[q] = acc[q] / (double)nsteps;
     return FDTD_OK;
 }
 

@@ -472,9 +472,9 @@ class Solver:
 
     def time_kernels(self, n: int) -> dict:
         """Eager, event-timed steps: average ms per launch of each kernel."""
-        out = (ctypes.c_double * 4)()
+        out = (ctypes.c_double * 5)()
         _check(self.lib, self.h, self.lib.fdtd_plasma_time_kernels(self.h, int(n), out))
-        return dict(h=out[0], kinetic=out[1], e=out[2], step=out[3])
+        return dict(h=out[0], kinetic=out[1], closure=out[2], e=out[3], step=out[4])
 
     def reset(self):
         _check(self.lib, self.h, self.lib.fdtd_plasma_reset(self.h))
