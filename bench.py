@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine", default="mma", choices=["mma", "tcgen05"], help="closure MLP engine")
     return ap.parse_args()
 
 
@@ -364,7 +365,7 @@ def closure_bench(args, spec, rank, world, local):
     def timed(with_closure):
         s = Solver.from_spec(spec, device=local)
         if with_closure:
-            s.set_closure(params, n_train_max=nmax, **sc)
+            s.set_closure(params, n_train_max=nmax, engine=args.engine, **sc)
         s.step(args.warmup)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -398,7 +399,7 @@ def closure_bench(args, spec, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
             "data": "synthetic (seeded density fields; training data from kinetic runs)",
             "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"]],
-                       "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
+                       "closure_engine": args.engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
                        "training": {"runs": len(tspecs), "final_mse": hist[-1], "seconds": t_train},
                        "l2": "inputs larger than L2"},
             "closure_vs_kinetic": {"kinetic_ms_per_step": ms_k / args.steps, "closure_ms_per_step": ms_c / args.steps,

@@ -222,7 +222,9 @@ int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int b
 typedef struct {
     const float *params;        /* FDTD_MLP_NPARAMS floats, host or device, copied */
     int32_t params_on_device;
-    int32_t reserved;
+    int32_t engine;             /* 0: mma.sync warp tiles; 1: tcgen05 MMA with a tensor-memory
+                                   accumulator (bounded completion waits: a wait that gives up makes
+                                   fdtd_plasma_diagnostics return FDTD_ERR_TIMEOUT) */
     double e_scale, j_scale, n_scale, rho, n_train_max;
     double beta;                /* Drude increment coefficient (A m / V per unit density) */
 } fdtd_closure_desc;
@@ -254,6 +256,11 @@ int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity,
  *              on params with first / second moments m, v. */
 size_t fdtd_mlp_workspace_bytes(int64_t batch);
 int fdtd_mlp_forward(const float *params, const float *x, int64_t batch, float *y, void *stream);
+/* The same forward on the 5th-generation tensor cores (tcgen05 MMA into a
+ * tensor-memory accumulator, one warpgroup per 128-row tile).  Its internal
+ * completion waits are bounded: if one gives up, *err (device int, caller
+ * zeroed) is set to 1 and the affected outputs are NaN. */
+int fdtd_mlp_forward_tc(const float *params, const float *x, int64_t batch, float *y, int *err, void *stream);
 int fdtd_mlp_loss_grad(const float *params, const float *x, const float *target, int64_t batch, float *grad,
                        float *loss, void *workspace, size_t workspace_bytes, void *stream);
 int fdtd_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t n, int64_t t, double lr, double beta1,

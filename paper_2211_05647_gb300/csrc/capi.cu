@@ -312,6 +312,8 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         c.cj = (float)cpe;
         c.d_step = h->d_step;
         c.kstep = kstep;
+        c.engine = h->cl.engine;
+        c.err = h->d_err;
         cudaError_t e = launch_closure(st, c, h->num_sms);
         if (e != cudaSuccess) return e;
     }
@@ -486,10 +488,11 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     h->mur_state = dalloc(h, 4 * 8);
     h->d_step = (int64_t *)dalloc(h, 256);
     h->d_src = (double *)dalloc(h, 256);
+    h->d_err = (int *)dalloc(h, 256);
     h->diag_blocks = h->num_sms * 4;
     h->diag_partials = (double *)dalloc(h, (size_t)h->diag_blocks * 7 * sizeof(double));
     h->diag_out = (double *)dalloc(h, 8 * sizeof(double));
-    if (!h->mur_state || !h->d_step || !h->d_src || !h->diag_partials || !h->diag_out)
+    if (!h->mur_state || !h->d_step || !h->d_src || !h->d_err || !h->diag_partials || !h->diag_out)
         return bail(FDTD_ERR_NOMEM, "small allocation failed");
     rc = fdtd_plasma_reset(h);
     if (rc != FDTD_OK) {
@@ -518,6 +521,7 @@ int fdtd_plasma_reset(fdtd_plasma_t h)
     if (h->jprev) CK(h, cudaMemsetAsync(h->jprev, 0, (size_t)(h->has_closure ? h->ncl : h->nslots) * 4, h->stream));
     CK(h, cudaMemsetAsync(h->mur_state, 0, 32, h->stream));
     CK(h, cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
+    CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
     h->steps_done = 0;
     return FDTD_OK;
 }
@@ -687,6 +691,7 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
         !(c->n_train_max >= 0))
         return fail(h, FDTD_ERR_INVAL, "closure scales must be finite, e_scale and n_scale > 0");
     std::vector<float> P(FDTD_MLP_NPARAMS);
+    if (c->engine != 0 && c->engine != 1) return fail(h, FDTD_ERR_INVAL, "closure engine must be 0 or 1");
     if (c->params_on_device) CK(h, cudaMemcpy(P.data(), c->params, P.size() * 4, cudaMemcpyDeviceToHost));
     else std::memcpy(P.data(), c->params, P.size() * 4);
     for (float v : P)
@@ -881,7 +886,10 @@ int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
     CK(h, launch_diag(h->stream, a, h->diag_partials, h->diag_blocks, h->diag_out));
     double o[6];
     CK(h, cudaMemcpyAsync(o, h->diag_out, sizeof(o), cudaMemcpyDeviceToHost, h->stream));
+    int errw = 0;
+    CK(h, cudaMemcpyAsync(&errw, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (errw) return fail(h, FDTD_ERR_TIMEOUT, "a bounded device wait gave up (closure kernel)");
     out->energy = o[0];
     out->energy_plain = o[1];
     out->number = o[2];
@@ -984,6 +992,7 @@ void fdtd_plasma_destroy(fdtd_plasma_t h)
     dfree(h, h->mur_state);
     dfree(h, h->d_step);
     dfree(h, h->d_src);
+    dfree(h, h->d_err);
     dfree(h, h->diag_partials);
     dfree(h, h->diag_out);
     if (h->cap) cudaStreamDestroy(h->cap);

@@ -17,14 +17,14 @@
 // `rate` of the (cell, step) pairs, and each selected pair appends one sample
 //     [E^{n-15} .. E^n, n, J^{n+1/2}, J^{n-1/2}]   (19 floats)
 // to the caller's buffer.
-#include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 namespace fp {
 
 
 __global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
     __shared__ int32_t s_cell[kMlpRows];
     __shared__ float s_e[kMlpRows];
@@ -112,11 +112,76 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
     jprev[s] = J;
 }
 
+// The same closure step with the tcgen05 tile: one warpgroup per CTA, thread
+// r owns row r of the tile (history push, input row, J and E update).  If a
+// bounded MMA-completion wait gives up, *err is set and the CTA stops.
+__global__ void __launch_bounds__(128) k_closure_tc(ClosureArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(smem_raw);
+    mlp_tc_load_weights(s, a.P);
+    mlp_tc_setup(s);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t step = *a.d_step + a.kstep;
+    const int ring = (int)(step & 15);
+    const int64_t ntiles = (a.n + kMlpRows - 1) / kMlpRows;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t slot = tile * kMlpRows + threadIdx.x;
+        const bool valid = slot < a.n;
+        float x[kMlpK1];
+#pragma unroll
+        for (int k = 0; k < kMlpK1; ++k) x[k] = 0.0f;
+        int32_t c = 0;
+        float e = 0.0f;
+        if (valid) {
+            c = a.cell[slot];
+            e = a.E[c];
+            float *h = a.hist + slot * 16;
+            h[ring] = e;
+            float hv[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = reinterpret_cast<const float4 *>(h)[q];
+                hv[4 * q] = v.x; hv[4 * q + 1] = v.y; hv[4 * q + 2] = v.z; hv[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) x[k] = hv[(ring + 1 + k) & 15] * a.inv_es;
+            x[16] = a.dens[slot] * a.inv_ns;
+        }
+        mlp_tc_put_row(s, threadIdx.x, x);
+        const float y = mlp_tc_tile(s, &phase, &ok);
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        if (valid) {
+            const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * e + a.js * y;
+            a.jprev[slot] = J;
+            a.jslot[slot] = J;
+            a.E[c] = e - a.cj * J;
+        }
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
+    mlp_tc_teardown(s);
+}
+
 size_t closure_smem_bytes() { return sizeof(MlpSmem); }
 
 cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
 {
     if (a.n == 0) return cudaSuccess;
+    if (a.engine == 1) {
+        const size_t smem = sizeof(MlpTcSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_closure_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure_tc, 128, smem);
+        if (e != cudaSuccess) return e;
+        // at most 4 CTAs per SM so the 128-column TMEM allocations (512 columns per SM) always fit
+        const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
+        const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * std::min(std::max(per_sm, 1), 4));
+        k_closure_tc<<<(unsigned)grid, 128, smem, st>>>(a);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(MlpSmem);
     cudaError_t e = cudaFuncSetAttribute(k_closure, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

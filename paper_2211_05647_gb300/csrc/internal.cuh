@@ -158,6 +158,8 @@ struct ClosureArgs {
     float inv_es, inv_ns, js, rho, cj, beta;
     const int64_t *d_step;
     int kstep;
+    int engine;        // 0: mma.sync warp tiles, 1: tcgen05 (TMEM accumulator)
+    int *err;          // set to 1 if a bounded wait gave up
 };
 cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms);
 void launch_hist_push(cudaStream_t st, const int32_t *cell, int64_t n, const float *E, float *hist,
@@ -191,6 +193,7 @@ struct fdtd_plasma {
     void *mur_state;
     int64_t *d_step;
     double *d_src;            // g(t^{n+1}) of the step in flight
+    int *d_err;               // device error word (bounded waits that gave up)
     int64_t steps_done;
     // plasma
     int has_plasma;

@@ -13,14 +13,14 @@
 // master parameters in place.
 #include <cstdio>
 
-#include "mlp.cuh"
+#include "mlp_tc.cuh"
 
 namespace fp {
 
 __global__ void __launch_bounds__(256) k_mlp_forward(const float *__restrict__ P, const float *__restrict__ X,
                                                      int64_t B, float *__restrict__ Y, MlpTrace tr, int use_trace)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
     mlp_load_weights(s, P);
     const int64_t ntiles = (B + kMlpRows - 1) / kMlpRows;
@@ -158,6 +158,33 @@ __global__ void k_mlp_adam(float *__restrict__ p, const float *__restrict__ g, f
 
 size_t mlp_smem_bytes() { return sizeof(MlpSmem); }
 
+// tcgen05 forward: one warpgroup per CTA, grid-stride over 128-row tiles.
+// A wait that gives up sets *err and the tile's outputs to NaN.
+__global__ void __launch_bounds__(128) k_mlp_forward_tc(const float *__restrict__ P, const float *__restrict__ X,
+                                                        int64_t B, float *__restrict__ Y, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(smem_raw);
+    mlp_tc_load_weights(s, P);
+    mlp_tc_setup(s);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int64_t ntiles = (B + kMlpRows - 1) / kMlpRows;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t row = tile * kMlpRows + threadIdx.x;
+        float x[kMlpK1];
+#pragma unroll
+        for (int k = 0; k < kMlpK1; ++k) x[k] = (k < kMlpIn && row < B) ? X[row * kMlpIn + k] : 0.0f;
+        mlp_tc_put_row(s, threadIdx.x, x);
+        const float y = mlp_tc_tile(s, &phase, &ok);
+        ok = __syncthreads_and(ok);           // CTA-uniform decision
+        if (row < B) Y[row] = ok ? y : __int_as_float(0x7fc00000);
+        if (!ok) break;
+    }
+    if (!ok) atomicExch(err, 1);
+    mlp_tc_teardown(s);
+}
+
 }  // namespace fp
 
 using namespace fp;
@@ -198,6 +225,22 @@ int fdtd_mlp_forward(const float *params, const float *x, int64_t batch, float *
 {
     if (!params || !x || !y || batch < 1) return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_forward: bad argument");
     cudaError_t e = launch_forward(params, x, batch, y, MlpTrace{}, 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
+int fdtd_mlp_forward_tc(const float *params, const float *x, int64_t batch, float *y, int *err, void *stream)
+{
+    if (!params || !x || !y || !err || batch < 1)
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_forward_tc: bad argument");
+    const size_t smem = sizeof(MlpTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    const int64_t tiles = (batch + kMlpRows - 1) / kMlpRows;
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)mlp_num_sms() * 2);
+    k_mlp_forward_tc<<<(unsigned)std::max<int64_t>(grid, 1), 128, smem, (cudaStream_t)stream>>>(params, x, batch, y,
+                                                                                              err);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
     return FDTD_OK;
 }

@@ -86,7 +86,7 @@ class fdtd_diag_arrays(ctypes.Structure):
 
 
 class fdtd_closure_desc(ctypes.Structure):
-    _fields_ = [("params", ctypes.c_void_p), ("params_on_device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    _fields_ = [("params", ctypes.c_void_p), ("params_on_device", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("e_scale", ctypes.c_double), ("j_scale", ctypes.c_double), ("n_scale", ctypes.c_double),
                 ("rho", ctypes.c_double), ("n_train_max", ctypes.c_double), ("beta", ctypes.c_double)]
 
@@ -135,6 +135,8 @@ SIGNATURES = {
     "fdtd_mlp_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
     "fdtd_mlp_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "fdtd_mlp_forward_tc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
     "fdtd_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
@@ -250,6 +252,19 @@ def mlp_forward(params, x, stream=None):
     st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
     _check(lib, None, lib.fdtd_mlp_forward(params.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr(), st))
     return y
+
+
+def mlp_forward_tc(params, x, stream=None):
+    """tcgen05 forward; returns (y, err) with err the device flag of a bounded wait that gave up."""
+    import torch
+    lib = load_library()
+    x = x.contiguous()
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    err = torch.zeros(1, dtype=torch.int32, device=x.device)
+    st = (stream or torch.cuda.current_stream(x.device)).cuda_stream
+    _check(lib, None, lib.fdtd_mlp_forward_tc(params.data_ptr(), x.data_ptr(), x.shape[0], y.data_ptr(),
+                                              err.data_ptr(), st))
+    return y, err
 
 
 class MlpTrainer:
@@ -438,7 +453,7 @@ class Solver:
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_plasma(self.h, ctypes.byref(d)))
         self.f_dtype = f_dtype
 
-    def set_closure(self, params, e_scale, j_scale, n_scale, rho, n_train_max, beta=0.0):
+    def set_closure(self, params, e_scale, j_scale, n_scale, rho, n_train_max, beta=0.0, engine="mma"):
         """Install the learned closure (params: torch / numpy FP32, 18945 values)."""
         torch = self.torch
         if isinstance(params, torch.Tensor):
@@ -450,8 +465,8 @@ class Solver:
         n = p.numel() if isinstance(p, torch.Tensor) else p.size
         if n != MLP_NPARAMS:
             raise ValueError("closure needs 18945 parameters")
-        d = fdtd_closure_desc(ptr, dev, 0, float(e_scale), float(j_scale), float(n_scale), float(rho),
-                              float(n_train_max), float(beta))
+        d = fdtd_closure_desc(ptr, dev, {"mma": 0, "tcgen05": 1}[engine], float(e_scale), float(j_scale),
+                              float(n_scale), float(rho), float(n_train_max), float(beta))
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_closure(self.h, ctypes.byref(d)))
 
     def closure_shape(self):

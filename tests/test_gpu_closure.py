@@ -51,6 +51,26 @@ def test_mlp_forward_matches_oracle():
     assert err <= 1e-2
 
 
+def test_mlp_forward_tcgen05_matches_oracle_and_mma():
+    """The tcgen05 (tensor-memory accumulator) forward against the FP64 oracle
+    and against the mma.sync forward: same BF16 roundings of the operands,
+    different accumulation order only."""
+    import torch
+    from paper_2211_05647_gb300 import mlp_forward, mlp_forward_tc
+    flat = _flat_params(21)
+    x = np.random.default_rng(22).standard_normal((5000, 17)).astype(np.float32)
+    p, xt = torch.from_numpy(flat).cuda(), torch.from_numpy(x).cuda()
+    y_tc, err = mlp_forward_tc(p, xt)
+    y_mma = mlp_forward(p, xt)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    y_tc, y_mma = y_tc.cpu().numpy(), y_mma.cpu().numpy()
+    yo, _ = M.forward(_oracle_params(flat), x.astype(np.float64))
+    e_or, e_mma = rel_l2(y_tc, yo), rel_l2(y_tc, y_mma)
+    print(f"tcgen05 forward: rel L2 vs FP64 {e_or:.3e}, vs mma.sync {e_mma:.3e}")
+    assert e_or <= 1e-2 and e_mma <= 2e-3
+
+
 def test_mlp_loss_grad_matches_oracle():
     import torch
     from paper_2211_05647_gb300 import MlpTrainer
@@ -140,7 +160,8 @@ def test_closure_constant_network():
     assert np.allclose(J, want, rtol=1e-5)
 
 
-def test_closure_inference_matches_oracle_forward():
+@pytest.mark.parametrize("engine", ["mma", "tcgen05"])
+def test_closure_inference_matches_oracle_forward(engine):
     """In-solver closure: after stepping, J of every closure cell equals
     rho J_prev + beta n E^n + J_s MLP(x) with x rebuilt from the E history it
     saw (FP64 oracle forward)."""
@@ -153,7 +174,7 @@ def test_closure_inference_matches_oracle_forward():
     cells = cells[(cells % 160 >= 1) & (cells // 160 >= 1)]
     nmax = dens.max()
     e_s, j_s, n_s, rho, beta = 0.05, 1e-3, 1e18, 0.95, 3e-21
-    s.set_closure(flat, e_scale=e_s, j_scale=j_s, n_scale=n_s, rho=rho, n_train_max=nmax, beta=beta)
+    s.set_closure(flat, e_scale=e_s, j_scale=j_s, n_scale=n_s, rho=rho, n_train_max=nmax, beta=beta, engine=engine)
     hist = []
     Jprev = np.zeros(len(cells))
     for n in range(60):
@@ -166,9 +187,10 @@ def test_closure_inference_matches_oracle_forward():
             y, _ = M.forward(_oracle_params(flat), x)
             want = rho * Jprev + beta * dens[cells] * hist[-1] + j_s * y
             err = rel_l2(J, want)
-            print(f"closure J vs oracle forward: {err:.3e}")
+            print(f"closure ({engine}) J vs oracle forward: {err:.3e}")
             assert err <= 1e-2
         Jprev = J
+    assert s.diagnostics()["finite"]
 
 
 @pytest.mark.slow
