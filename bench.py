@@ -142,7 +142,7 @@ def measured_peaks():
 
 def kinetic_src_sha() -> str:
     h = hashlib.sha1()
-    for f in ("kinetic.cu", "internal.cuh"):
+    for f in ("kinetic.cu", "kinetic_row.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2211_05647_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 

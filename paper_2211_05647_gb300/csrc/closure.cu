@@ -112,22 +112,26 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
     jprev[s] = J;
 }
 
-// The same closure step with the tcgen05 tile: one warpgroup per CTA, thread
-// r owns row r of the tile (history push, input row, J and E update).  If a
-// bounded MMA-completion wait gives up, *err is set and the CTA stops.
-__global__ void __launch_bounds__(128) k_closure_tc(ClosureArgs a)
+// The same closure step on the tcgen05 tile: one 512-thread CTA per SM with
+// four independent warpgroup pipelines (each its own TMEM accumulator and
+// tiles, one shared copy of the weights); thread r of a warpgroup owns row r
+// of its tile (history push, input row, J and E update).  If a bounded
+// MMA-completion wait gives up, *err is set and the warpgroup stops.
+__global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MlpTcSmem &s = *reinterpret_cast<MlpTcSmem *>(smem_raw);
-    mlp_tc_load_weights(s, a.P);
-    mlp_tc_setup(s);
+    MlpTcSmem4 &s = *reinterpret_cast<MlpTcSmem4 *>(smem_raw);
+    mlp_tc4_load_weights(s.w, a.P);
+    mlp_tc4_setup(s);
+    const int gi = threadIdx.x >> 7, r = threadIdx.x & 127;
+    MlpTcGroup &g = s.g[gi];
     uint32_t phase = 0;
     bool ok = true;
     const int64_t step = *a.d_step + a.kstep;
     const int ring = (int)(step & 15);
     const int64_t ntiles = (a.n + kMlpRows - 1) / kMlpRows;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t slot = tile * kMlpRows + threadIdx.x;
+    for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + gi; tile < ntiles; tile += (int64_t)gridDim.x * kTcGroups) {
+        const int64_t slot = tile * kMlpRows + r;
         const bool valid = slot < a.n;
         float x[kMlpK1];
 #pragma unroll
@@ -149,9 +153,8 @@ __global__ void __launch_bounds__(128) k_closure_tc(ClosureArgs a)
             for (int k = 0; k < 16; ++k) x[k] = hv[(ring + 1 + k) & 15] * a.inv_es;
             x[16] = a.dens[slot] * a.inv_ns;
         }
-        mlp_tc_put_row(s, threadIdx.x, x);
-        const float y = mlp_tc_tile(s, &phase, &ok);
-        ok = __syncthreads_and(ok);
+        mlp_tc4_put_row(g, r, x);
+        const float y = mlp_tc4_tile(s.w, g, gi, r, &phase, &ok);
         if (!ok) break;
         if (valid) {
             const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * e + a.js * y;
@@ -160,8 +163,8 @@ __global__ void __launch_bounds__(128) k_closure_tc(ClosureArgs a)
             a.E[c] = e - a.cj * J;
         }
     }
-    if (!ok && threadIdx.x == 0) atomicExch(a.err, 1);
-    mlp_tc_teardown(s);
+    if (!ok && r == 0) atomicExch(a.err, 1);
+    mlp_tc4_teardown(s);
 }
 
 size_t closure_smem_bytes() { return sizeof(MlpSmem); }
@@ -170,16 +173,13 @@ cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
 {
     if (a.n == 0) return cudaSuccess;
     if (a.engine == 1) {
-        const size_t smem = sizeof(MlpTcSmem);
+        const size_t smem = sizeof(MlpTcSmem4);
         cudaError_t e = cudaFuncSetAttribute(k_closure_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_closure_tc, 128, smem);
-        if (e != cudaSuccess) return e;
-        // at most 4 CTAs per SM so the 128-column TMEM allocations (512 columns per SM) always fit
+        // one CTA per SM: it allocates all 512 TMEM columns
         const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
-        const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * std::min(std::max(per_sm, 1), 4));
-        k_closure_tc<<<(unsigned)grid, 128, smem, st>>>(a);
+        const int64_t grid = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, (int64_t)num_sms);
+        k_closure_tc<<<(unsigned)std::max<int64_t>(grid, 1), 512, smem, st>>>(a);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(MlpSmem);

@@ -235,4 +235,168 @@ __device__ __forceinline__ float mlp_tc_tile(MlpTcSmem &s, uint32_t *phase, bool
     return y;
 }
 
+// ------------------------------------------------------------------------
+// Four independent warpgroup pipelines per CTA (512 threads), one copy of the
+// weights.  Warpgroup g owns TMEM columns [128 g, 128 g + 128), its own input
+// and hidden tiles and mbarrier, and synchronises on named barrier 1 + g, so
+// while one warpgroup waits for its MMAs the others run their epilogues.
+
+constexpr int kTcGroups = 4;
+
+struct MlpTcWeights {
+    __align__(128) __nv_bfloat16 w1[kMlpH * kMlpK1];
+    __align__(128) __nv_bfloat16 w2[kMlpH * kMlpH];
+    float b1[kMlpH], b2[kMlpH], w3[kMlpH];
+    float b3;
+    uint32_t tmem;
+};
+
+struct MlpTcGroup {
+    __align__(128) __nv_bfloat16 x[kMlpRows * kMlpK1];
+    __align__(128) __nv_bfloat16 a2[kMlpRows * kMlpH];
+    __align__(8) uint64_t mbar;
+    int flag;
+};
+
+struct MlpTcSmem4 {
+    MlpTcWeights w;
+    MlpTcGroup g[kTcGroups];
+};
+
+__device__ __forceinline__ void wg_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+__device__ __forceinline__ void mlp_tc4_load_weights(MlpTcWeights &s, const float *__restrict__ P)
+{
+    unsigned char *w1 = reinterpret_cast<unsigned char *>(s.w1), *w2 = reinterpret_cast<unsigned char *>(s.w2);
+    for (int i = threadIdx.x; i < kMlpH * kMlpK1; i += blockDim.x) {
+        const int n = i / kMlpK1, k = i % kMlpK1;
+        *reinterpret_cast<__nv_bfloat16 *>(w1 + core_off(n, k, kMlpK1)) =
+            __float2bfloat16_rn(k < kMlpIn ? P[kOffW1 + k * kMlpH + n] : 0.0f);
+    }
+    for (int i = threadIdx.x; i < kMlpH * kMlpH; i += blockDim.x) {
+        const int k = i / kMlpH, n = i % kMlpH;
+        *reinterpret_cast<__nv_bfloat16 *>(w2 + core_off(n, k, kMlpH)) = __float2bfloat16_rn(P[kOffW2 + i]);
+    }
+    for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) {
+        s.b1[i] = P[kOffB1 + i];
+        s.b2[i] = P[kOffB2 + i];
+        s.w3[i] = P[kOffW3 + i];
+    }
+    if (threadIdx.x == 0) s.b3 = P[kOffB3];
+}
+
+// all 512 threads: TMEM (4 x 128 columns), one mbarrier per warpgroup
+__device__ __forceinline__ void mlp_tc4_setup(MlpTcSmem4 &s)
+{
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s.w.tmem)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x < kTcGroups) {
+        mbar_init(&s.g[threadIdx.x].mbar, 1);
+        s.g[threadIdx.x].flag = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__device__ __forceinline__ void mlp_tc4_teardown(MlpTcSmem4 &s)
+{
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.w.tmem), "r"(512u) : "memory");
+}
+
+__device__ __forceinline__ void mlp_tc4_put_row(MlpTcGroup &g, int r, const float *x)
+{
+    unsigned char *xb = reinterpret_cast<unsigned char *>(g.x);
+#pragma unroll
+    for (int c = 0; c < kMlpK1 / 8; ++c) {
+        uint4 v;
+        v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
+        v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
+        v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
+        v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
+        *reinterpret_cast<uint4 *>(xb + core_off(r, 8 * c, kMlpK1)) = v;
+    }
+}
+
+// forward of warpgroup gi's tile (rows in g.x); thread r (0..127 inside the
+// warpgroup) gets row r's output.  Returns false in every thread of the
+// warpgroup if one of its bounded waits gave up.
+__device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, int gi, int r, uint32_t *phase,
+                                              bool *ok_out)
+{
+    const int warp = r >> 5;
+    const uint32_t tmem = w.tmem + (uint32_t)(gi * 128);
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    constexpr uint32_t kWait = 1u << 22;
+    bool ok = true;
+    fence_proxy_async_smem();
+    tc_fence_before();
+    wg_bar(gi);
+    tc_fence_after();
+    if (r == 0) {
+        const uint32_t xa = smem_addr(g.x), wa = smem_addr(w.w1);
+#pragma unroll
+        for (int kk = 0; kk < kMlpK1 / 16; ++kk)
+            tc_mma(tmem, tc_desc(xa + kk * 256, 128, (kMlpK1 / 8) * 128), tc_desc(wa + kk * 256, 128, (kMlpK1 / 8) * 128),
+                   kTcIdesc, kk > 0);
+        tc_commit(&g.mbar);
+    }
+    if (!mbar_wait(&g.mbar, *phase, kWait)) ok = false;
+    *phase ^= 1u;
+    tc_fence_after();
+    unsigned char *a2 = reinterpret_cast<unsigned char *>(g.a2);
+#pragma unroll
+    for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tc_ld32(tmem + lane_base + c * 32, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k0 = c * 32 + q * 8;
+            uint4 pk;
+            pk.x = pack_bf16(gelu_f(v[q * 8 + 0] + w.b1[k0 + 0]), gelu_f(v[q * 8 + 1] + w.b1[k0 + 1]));
+            pk.y = pack_bf16(gelu_f(v[q * 8 + 2] + w.b1[k0 + 2]), gelu_f(v[q * 8 + 3] + w.b1[k0 + 3]));
+            pk.z = pack_bf16(gelu_f(v[q * 8 + 4] + w.b1[k0 + 4]), gelu_f(v[q * 8 + 5] + w.b1[k0 + 5]));
+            pk.w = pack_bf16(gelu_f(v[q * 8 + 6] + w.b1[k0 + 6]), gelu_f(v[q * 8 + 7] + w.b1[k0 + 7]));
+            *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
+        }
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    wg_bar(gi);
+    tc_fence_after();
+    if (r == 0) {
+        const uint32_t aa = smem_addr(g.a2), wa = smem_addr(w.w2);
+#pragma unroll
+        for (int kk = 0; kk < kMlpH / 16; ++kk)
+            tc_mma(tmem, tc_desc(aa + kk * 256, 128, (kMlpH / 8) * 128), tc_desc(wa + kk * 256, 128, (kMlpH / 8) * 128),
+                   kTcIdesc, kk > 0);
+        tc_commit(&g.mbar);
+    }
+    if (!mbar_wait(&g.mbar, *phase, kWait)) ok = false;
+    *phase ^= 1u;
+    tc_fence_after();
+    float y = w.b3;
+#pragma unroll
+    for (int c = 0; c < kMlpH / 32; ++c) {
+        float v[32];
+        tc_ld32(tmem + lane_base + c * 32, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) y += gelu_f(v[i] + w.b2[c * 32 + i]) * w.w3[c * 32 + i];
+    }
+    tc_fence_before();
+    // warpgroup-uniform verdict
+    if (!ok) g.flag = 1;
+    wg_bar(gi);
+    *ok_out = g.flag == 0;
+    return y;
+}
+
 }  // namespace fp
