@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="mma", choices=["mma", "tcgen05"], help="closure MLP engine")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     return ap.parse_args()
 
 
@@ -142,7 +143,7 @@ def measured_peaks():
 
 def kinetic_src_sha() -> str:
     h = hashlib.sha1()
-    for f in ("kinetic.cu", "kinetic_row.cuh"):
+    for f in ("kinetic_impl.cuh", "kinetic_row.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2211_05647_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -226,6 +227,7 @@ def main():
     ns, nn = s.plasma_shape()
     cells = cells_of(spec)
     st = s.stream
+    tune = None if args.no_autotune else s.autotune()   # untimed: picks the launch shapes
 
     def barrier():
         torch.cuda.synchronize()
@@ -322,6 +324,7 @@ def main():
             "phase_space_updates_per_s": ps_rate,
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "kernel_ms": kt,
+            "launch_shapes": tune,
             "roofline": roof,
             "gpu_launches": args.steps * 3 + math.ceil(args.steps / 32) if ns else args.steps * 2 + math.ceil(args.steps / 32),
             "clocks": clk,

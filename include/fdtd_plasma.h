@@ -168,6 +168,22 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps);
  * advances exactly as with step. */
 int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out);
 
+/* Launch-shape autotuner.  Times, with CUDA events on the handle's stream,
+ * every candidate shape of the kinetic kernel (vectors per lane x lanes per
+ * row x CTAs per SM) and of the curl-stencil kernels (thread-block shape) on
+ * the handle's own buffers, adopts the fastest, and records them in a text
+ * cache ($FDTD_PLASMA_TUNE_CACHE, else $HOME/.cache/fdtd_plasma/autotune.txt)
+ * keyed by GPU name, kernel, precision and size class; later handles of the
+ * same class start from the cached shapes.  The state is saved before and
+ * restored bit for bit after (needs one temporary copy of it on the device).
+ * Synchronous. */
+typedef struct {
+    int32_t kin_vpl, kin_l, kin_blocks_per_sm;   /* 0 = no kinetic kernel tuned */
+    int32_t block_x, block_y, block_z;           /* 0 = no stencil tuned (1-D) */
+    double kin_ms, stencil_ms;                   /* best per-launch times */
+} fdtd_tune_result;
+int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
+
 /* Zero every field, psi, delta f and J and the step counter (keeps the
  * configuration). */
 int fdtd_plasma_reset(fdtd_plasma_t h);

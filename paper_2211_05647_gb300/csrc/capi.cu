@@ -9,8 +9,14 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
+#include <fstream>
+#include <map>
 #include <new>
+#include <sstream>
 #include <vector>
+
+#include <sys/stat.h>
 
 #include "internal.cuh"
 
@@ -242,6 +248,121 @@ Source source_view(fdtd_plasma *h)
     return s;
 }
 
+dim3 stencil_block(const fdtd_plasma *h)
+{
+    if (h->st_bx > 0) return dim3(h->st_bx, h->st_by, h->g.ndim == 3 ? h->st_bz : 1);
+    return h->g.ndim == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1);
+}
+
+template <typename T>
+KinArgs<T> kin_args(fdtd_plasma *h, int kstep)
+{
+    KinArgs<T> a{};
+    a.slot_cell = h->slot_cell;
+    a.dens = reinterpret_cast<const T *>(h->dens);
+    a.df = h->df;
+    a.E = reinterpret_cast<T *>(h->f[pol_comp(h)]);
+    a.jslot = reinterpret_cast<T *>(h->jslot);
+    a.tab = reinterpret_cast<const T *>(h->tab);
+    a.nslots = h->nkin;
+    a.pitch = h->pitch;
+    a.cj = (T)(h->dt / kEps0);
+    a.seed = h->pl.seed;
+    a.d_step = h->d_step;
+    a.kstep = kstep;
+    return a;
+}
+
+// ---------------------------------------------------------------- tune cache
+// Text file, one entry per line: "<key> <v0> <v1> <v2>", keyed by GPU name,
+// kernel, precision and shape class.  Path: $FDTD_PLASMA_TUNE_CACHE, else
+// $HOME/.cache/fdtd_plasma/autotune.txt.
+
+std::string tune_cache_path()
+{
+    const char *p = std::getenv("FDTD_PLASMA_TUNE_CACHE");
+    if (p && *p) return p;
+    const char *home = std::getenv("HOME");
+    return std::string(home ? home : ".") + "/.cache/fdtd_plasma/autotune.txt";
+}
+
+std::string gpu_key()
+{
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "gpu";
+    std::string n = prop.name;
+    for (char &c : n)
+        if (c == ' ') c = '_';
+    return n;
+}
+
+int log2_bucket(int64_t n)
+{
+    int b = 0;
+    while (n > 1) { n >>= 1; ++b; }
+    return b;
+}
+
+std::string kin_key(const fdtd_plasma *h)
+{
+    std::ostringstream o;
+    o << gpu_key() << "|kinetic|dtype" << h->pl.f_dtype << "|pitch" << h->pitch << "|rows2^" << log2_bucket(h->nkin);
+    return o.str();
+}
+
+std::string stencil_key(const fdtd_plasma *h)
+{
+    std::ostringstream o;
+    o << gpu_key() << "|stencil" << h->g.ndim << "d|prec" << h->g.precision << "|cells2^"
+      << log2_bucket(h->nx * h->ny * h->nz) << "|cpml" << (h->g.cpml_cells > 0);
+    return o.str();
+}
+
+std::map<std::string, std::vector<int>> read_cache()
+{
+    std::map<std::string, std::vector<int>> m;
+    std::ifstream f(tune_cache_path());
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream in(line);
+        std::string k;
+        std::vector<int> v;
+        int x;
+        if (!(in >> k)) continue;
+        while (in >> x) v.push_back(x);
+        if (v.size() == 3) m[k] = v;
+    }
+    return m;
+}
+
+void write_cache(const std::map<std::string, std::vector<int>> &m)
+{
+    const std::string path = tune_cache_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos) {
+        std::string dir = path.substr(0, slash);
+        for (size_t i = 1; i <= dir.size(); ++i)
+            if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+    }
+    std::ofstream f(path, std::ios::trunc);
+    for (const auto &kv : m) f << kv.first << " " << kv.second[0] << " " << kv.second[1] << " " << kv.second[2] << "\n";
+}
+
+void apply_cached_kinetic(fdtd_plasma *h)
+{
+    auto m = read_cache();
+    auto it = m.find(kin_key(h));
+    if (it != m.end()) { h->kin_vpl = it->second[0]; h->kin_l = it->second[1]; h->kin_bps = it->second[2]; }
+}
+
+void apply_cached_stencil(fdtd_plasma *h)
+{
+    auto m = read_cache();
+    auto it = m.find(stencil_key(h));
+    if (it != m.end()) { h->st_bx = it->second[0]; h->st_by = it->second[1]; h->st_bz = it->second[2]; }
+}
+
 // enqueue one step n -> n+1 (kstep = offset of this step inside the chunk);
 // ev (optional) receives records before H, before the kinetic kernel, before
 // the closure kernel, before E and after E.
@@ -260,28 +381,17 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         launch_h1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->g.mur ? (T *)h->mur_state : nullptr, h->nz, ch, src, h->d_step,
                       kstep);
     else if (h->g.ndim == 2)
-        launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, kstep);
+        launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, kstep,
+                      stencil_block(h));
     else
-        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep);
+        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep, stencil_block(h));
     if (ev) cudaEventRecord(ev[1], st);
     const bool rec = h->has_recording && sizeof(T) == 4;
     if (rec)
         launch_hist_push(st, h->slot_cell, h->nslots, reinterpret_cast<const float *>(f[pol_comp(h)]), h->hist,
                          h->d_step, kstep);
     if (h->has_plasma && h->nkin > 0) {
-        KinArgs<T> a{};
-        a.slot_cell = h->slot_cell;
-        a.dens = reinterpret_cast<const T *>(h->dens);
-        a.df = h->df;
-        a.E = f[pol_comp(h)];
-        a.jslot = reinterpret_cast<T *>(h->jslot);
-        a.tab = reinterpret_cast<const T *>(h->tab);
-        a.nslots = h->nkin;
-        a.pitch = h->pitch;
-        a.cj = cpe;
-        a.seed = h->pl.seed;
-        a.d_step = h->d_step;
-        a.kstep = kstep;
+        const KinArgs<T> a = kin_args<T>(h, kstep);
         cudaError_t e;
         if (h->pl.nonlinear) {
             const double vth = std::sqrt(kQe * h->pl.te_ev / kMe);
@@ -289,7 +399,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
             const int nperp = h->pl.vgrid == FDTD_VGRID_CART2D ? h->pl.nv_perp : 1;
             e = launch_kinetic_nl<T>(st, a, h->pl.nv, nperp, dvpar, kQe / kMe, h->dt, h->num_sms);
         } else {
-            e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms);
+            e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, h->kin_vpl, h->kin_l, h->kin_bps);
         }
         if (e != cudaSuccess) return e;
     }
@@ -329,9 +439,10 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
             launch_mur1d<T>(st, f[FDTD_EX], (const T *)h->mur_state, h->nz, m);
         }
     } else if (h->g.ndim == 2) {
-        launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, kstep);
+        launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, kstep,
+                      stencil_block(h));
     } else {
-        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep);
+        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep, stencil_block(h));
     }
     if (ev) cudaEventRecord(ev[4], st);
     return cudaGetLastError();
@@ -494,6 +605,7 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     h->diag_out = (double *)dalloc(h, 8 * sizeof(double));
     if (!h->mur_state || !h->d_step || !h->d_src || !h->d_err || !h->diag_partials || !h->diag_out)
         return bail(FDTD_ERR_NOMEM, "small allocation failed");
+    if (g->ndim >= 2) apply_cached_stencil(h);
     rc = fdtd_plasma_reset(h);
     if (rc != FDTD_OK) {
         g_create_error = h->err;
@@ -634,6 +746,8 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     }
     h->has_plasma = 1;
     h->nkin = (int64_t)ns;
+    h->kin_vpl = h->kin_l = h->kin_bps = 0;
+    apply_cached_kinetic(h);
     h->h_cells = cells;
     h->h_dens = dslot;
     if (ns) CK(h, cudaMemcpy(h->slot_cell, cells.data(), ns * 4, cudaMemcpyHostToDevice));
@@ -769,6 +883,114 @@ int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity,
     h->rec_seed = seed;
     h->has_recording = 1;
     return FDTD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
+{
+    const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
+    const T ch = (T)(h->dt / (mu0 * h->g.dx)), ce = (T)(h->dt / (kEps0 * h->g.dx));
+    const T cph = (T)(h->dt / mu0), cpe = (T)(h->dt / kEps0);
+    T *f[6];
+    for (int q = 0; q < 6; ++q) f[q] = reinterpret_cast<T *>(h->f[q]);
+    const Cpml<T> cp = cpml_view<T>(h);
+    const Source src = source_view(h);
+    cudaStream_t st = h->stream;
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    auto time_ms = [&](auto &&launch) -> double {
+        launch();   // warm-up (also sets attributes)
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5; ++r) launch();
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 5.0;
+    };
+    auto m = read_cache();
+    out->block_x = out->block_y = out->block_z = 0;
+    out->stencil_ms = 0;
+    if (h->g.ndim >= 2) {
+        static const int s2[][3] = {{32, 8, 1}, {64, 4, 1}, {128, 2, 1}, {256, 1, 1}, {32, 4, 1}, {64, 2, 1}};
+        static const int s3[][3] = {{32, 4, 2}, {32, 8, 1}, {32, 2, 4}, {64, 4, 1}, {64, 2, 2}, {128, 2, 1}, {32, 4, 1}};
+        const int n = h->g.ndim == 2 ? 6 : 7;
+        double best = 1e30;
+        for (int c = 0; c < n; ++c) {
+            const int *sh = h->g.ndim == 2 ? s2[c] : s3[c];
+            const dim3 b(sh[0], sh[1], sh[2]);
+            const double ms = time_ms([&] {
+                if (h->g.ndim == 2) {
+                    launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, 0, b);
+                    launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, 0, b);
+                } else {
+                    launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, 0, b);
+                    launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, 0, b);
+                }
+            });
+            if (ms < best) {
+                best = ms;
+                out->block_x = sh[0]; out->block_y = sh[1]; out->block_z = sh[2];
+            }
+        }
+        h->st_bx = out->block_x; h->st_by = out->block_y; h->st_bz = out->block_z;
+        out->stencil_ms = best;
+        m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z};
+    }
+    out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = 0;
+    out->kin_ms = 0;
+    if (h->has_plasma && h->nkin > 0 && !h->pl.nonlinear) {
+        int cand[8][2];
+        const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
+        const KinArgs<T> a = kin_args<T>(h, 0);
+        double best = 1e30;
+        for (int c = 0; c < nc; ++c)
+            for (int bps : {0, 2, 3}) {
+                bool bad = false;
+                const double ms = time_ms([&] {
+                    if (launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, cand[c][0], cand[c][1], bps) != cudaSuccess)
+                        bad = true;
+                });
+                if (!bad && ms < best) {
+                    best = ms;
+                    out->kin_vpl = cand[c][0]; out->kin_l = cand[c][1]; out->kin_blocks_per_sm = bps;
+                }
+            }
+        h->kin_vpl = out->kin_vpl; h->kin_l = out->kin_l; h->kin_bps = out->kin_blocks_per_sm;
+        out->kin_ms = best;
+        m[kin_key(h)] = {out->kin_vpl, out->kin_l, out->kin_blocks_per_sm};
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(h, cudaGetLastError());
+    write_cache(m);
+    return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out)
+{
+    if (!h || !out) return FDTD_ERR_INVAL;
+    // the candidates run on the live buffers: save the state and restore it bit for bit afterwards
+    const size_t nb = fdtd_plasma_state_bytes(h);
+    void *blob = dalloc(h, nb);
+    if (!blob) return fail(h, FDTD_ERR_NOMEM, "autotune: no room for the state copy (%zu bytes)", nb);
+    int rc = fdtd_plasma_save_state(h, blob, nb, 1);
+    const int64_t steps = h->steps_done;
+    if (rc == FDTD_OK) rc = h->g.precision == FDTD_F64 ? autotune_t<double>(h, out) : autotune_t<float>(h, out);
+    const int rc2 = fdtd_plasma_load_state(h, blob, nb, 1);
+    h->steps_done = steps;
+    dfree(h, blob);
+    drop_graphs(h);
+    return rc != FDTD_OK ? rc : rc2;
 }
 
 int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out)

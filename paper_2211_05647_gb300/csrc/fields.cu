@@ -3,7 +3,8 @@
 // the soft source and the first-order Mur ends.
 //
 // One thread per Yee cell, x fastest across the warp so every field access is
-// a coalesced 128-byte row segment; the +-1 neighbours along y / z are the
+// a coalesced 128-byte row segment (the block shape is chosen at launch, by
+// default 32 x 8 in 2-D and 32 x 4 x 2 in 3-D, or by the autotuner); the +-1 neighbours along y / z are the
 // rows the neighbouring warps load anyway (served by L1/L2).  PEC walls are
 // the nodes the kernels never write; high-side neighbours past the last
 // stored node read as 0 (PEC ghosts).  The plasma current has already been
@@ -74,8 +75,8 @@ __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__rest
                                              int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp, Source src,
                                              const int64_t *__restrict__ d_step, int kstep)
 {
-    const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i == 0 && j == 0) write_source(src, d_step, kstep);
     if (i >= nx || j >= ny) return;
     const int64_t c = j * nx + i;
@@ -114,8 +115,8 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
                                              int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp, Source src,
                                              const int64_t *__restrict__ d_step, int kstep)
 {
-    const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t j = (int64_t)blockIdx.y * 8 + threadIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i < 1 || j < 1 || i >= nx || j >= ny) return;
     const int64_t c = j * nx + i;
     const T dHx = hy[c] - hy[c - 1];     // dHy along x
@@ -170,9 +171,9 @@ __global__ void __launch_bounds__(256) k_h3d(const T *__restrict__ ex, const T *
                                              T *__restrict__ hz, int64_t nx, int64_t ny, int64_t nz, T ch, T cph,
                                              Cpml<T> cp, Source src, const int64_t *__restrict__ d_step, int kstep)
 {
-    const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t j = (int64_t)blockIdx.y * 4 + threadIdx.y;
-    const int64_t k = (int64_t)blockIdx.z * 2 + threadIdx.z;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
     if (i == 0 && j == 0 && k == 0) write_source(src, d_step, kstep);
     if (i >= nx || j >= ny || k >= nz) return;
     const int64_t sxy = nx * ny;
@@ -227,9 +228,9 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
                                              T cpe, Cpml<T> cp, Source src, const int64_t *__restrict__ d_step,
                                              int kstep)
 {
-    const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
-    const int64_t j = (int64_t)blockIdx.y * 4 + threadIdx.y;
-    const int64_t k = (int64_t)blockIdx.z * 2 + threadIdx.z;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
     if (i >= nx || j >= ny || k >= nz) return;
     const int64_t sxy = nx * ny;
     const int64_t c = k * sxy + j * nx + i;
@@ -309,30 +310,30 @@ void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m)
 }
 template <typename T>
 void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep)
+                Source src, const int64_t *d_step, int kstep, dim3 b)
 {
-    dim3 b(32, 8), g(cdiv(nx, 32), cdiv(ny, 8));
+    dim3 g(cdiv(nx, b.x), cdiv(ny, b.y));
     k_h2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep)
+                Source src, const int64_t *d_step, int kstep, dim3 b)
 {
-    dim3 b(32, 8), g(cdiv(nx, 32), cdiv(ny, 8));
+    dim3 g(cdiv(nx, b.x), cdiv(ny, b.y));
     k_e2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep)
+                Source src, const int64_t *d_step, int kstep, dim3 b)
 {
-    dim3 b(32, 4, 2), g(cdiv(nx, 32), cdiv(ny, 4), cdiv(nz, 2));
+    dim3 g(cdiv(nx, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
     k_h3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep)
+                Source src, const int64_t *d_step, int kstep, dim3 b)
 {
-    dim3 b(32, 4, 2), g(cdiv(nx, 32), cdiv(ny, 4), cdiv(nz, 2));
+    dim3 g(cdiv(nx, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
     k_e3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step, kstep);
 }
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by) { k_advance<<<1, 1, 0, st>>>(d_step, by); }
@@ -342,13 +343,13 @@ void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by) { k_advance<<<
     template void launch_e1d<T>(cudaStream_t, T *, const T *, int64_t, T, Source, const int64_t *, int);      \
     template void launch_mur1d<T>(cudaStream_t, T *, const T *, int64_t, T);                                  \
     template void launch_h2d<T>(cudaStream_t, const T *, T *, T *, int64_t, int64_t, T, T, Cpml<T>, Source,   \
-                                const int64_t *, int);                                                        \
+                                const int64_t *, int, dim3);                                                  \
     template void launch_e2d<T>(cudaStream_t, T *, const T *, const T *, int64_t, int64_t, T, T, Cpml<T>,     \
-                                Source, const int64_t *, int);                                                \
+                                Source, const int64_t *, int, dim3);                                          \
     template void launch_h3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>, Source,  \
-                                const int64_t *, int);                                                        \
+                                const int64_t *, int, dim3);                                                  \
     template void launch_e3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>, Source,  \
-                                const int64_t *, int);
+                                const int64_t *, int, dim3);
 FP_INST(float)
 FP_INST(double)
 

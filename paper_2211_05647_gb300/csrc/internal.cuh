@@ -108,23 +108,27 @@ template <typename T>
 void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m);
 template <typename T>
 void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep);
+                Source src, const int64_t *d_step, int kstep, dim3 block);
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep);
+                Source src, const int64_t *d_step, int kstep, dim3 block);
 template <typename T>
 void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep);
+                Source src, const int64_t *d_step, int kstep, dim3 block);
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep);
+                Source src, const int64_t *d_step, int kstep, dim3 block);
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by);
 
 // delta-f row pitch (elements) for nnode nodes of the given storage type
 int kinetic_pitch(int nnode, int f_dtype);
-// returns cudaErrorInvalidValue for an unsupported combination
+// launch shape candidates (vectors per lane, lanes per row) for a row pitch; the first is the default
+int kinetic_candidates(int pitch, int f_dtype, int (*out)[2]);
+// returns cudaErrorInvalidValue for an unsupported combination; vpl <= 0 picks the default shape,
+// bps > 0 caps the CTAs per SM
 template <typename TA>
-cudaError_t launch_kinetic(cudaStream_t st, const KinArgs<TA> &a, int f_dtype, int num_sms);
+cudaError_t launch_kinetic(cudaStream_t st, const KinArgs<TA> &a, int f_dtype, int num_sms, int vpl = 0, int l = 0,
+                           int bps = 0);
 // nonlinear mode (FP32 / FP64 storage): npar x nperp nodes, v_par spacing dvpar, qm = e/m
 template <typename T>
 cudaError_t launch_kinetic_nl(cudaStream_t st, const KinArgs<T> &a, int npar, int nperp, double dvpar, double qm,
@@ -213,6 +217,10 @@ struct fdtd_plasma {
     float *hist, *jprev, *params;
     fdtd_closure_desc cl;
     // training-data recorder
+    // launch shapes (autotuner / cache): kinetic (vectors per lane, lanes per row, CTAs per SM; 0 = default),
+    // stencil block (0 = default)
+    int kin_vpl, kin_l, kin_bps;
+    int st_bx, st_by, st_bz;
     int has_recording;
     float *rec_out;
     int64_t rec_cap;

@@ -19,57 +19,9 @@
 // BF16 storage: FP32 arithmetic, stochastic rounding on store with 16 random
 // bits per node from Philox4x32-7 keyed by the seed and counted by
 // (slot, vector, step).
-#include "kinetic_row.cuh"
+#include "kinetic_impl.cuh"
 
 namespace fp {
-
-template <typename TS, typename TA, int VPL, int L>
-__global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TA *s_tab = reinterpret_cast<TA *>(smem_raw);
-    for (int t = threadIdx.x; t < 3 * a.pitch; t += blockDim.x) s_tab[t] = a.tab[t];
-    __syncthreads();
-    const TA *s_al = s_tab, *s_be = s_tab + a.pitch, *s_w = s_tab + 2 * a.pitch;
-
-    using V = typename Vec<TS>::type;
-    constexpr int VEC = Vec<TS>::n;
-    constexpr int R = 32 / L;   // rows per warp
-    const int lane = threadIdx.x & 31;
-    const int sub = lane / L, l = lane % L;
-    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t step = *a.d_step + a.kstep;
-    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-
-    // the slot -> cell index of the next row group is fetched one iteration
-    // ahead, so the E gather of a row issues together with its delta-f loads
-    int64_t row = wg * R + sub;
-    int32_t cell_next = row < a.nslots ? __ldg(a.slot_cell + row) : 0;
-    for (int64_t base = wg * R; base < a.nslots; base += nw * R) {
-        row = base + sub;
-        const bool valid = row < a.nslots;
-        const int32_t cell = cell_next;
-        V v[VPL];
-        TA E = TA(0), nE = TA(0);
-        V *rp = reinterpret_cast<V *>(a.df) + (valid ? row : 0) * (a.pitch / VEC);
-        if (valid) {
-#pragma unroll
-            for (int q = 0; q < VPL; ++q) v[q] = __ldcs(rp + q * L + l);
-            E = a.E[cell];
-            nE = __ldg(a.dens + row) * E;
-        }
-        const int64_t row_next = row + nw * R;
-        cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
-        TA s = TA(0), c = TA(0);
-        if (valid) row_update<TS, TA, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)row, step, key, s, c);
-        const TA J = row_reduce<TA, L>(s, c);
-        if (valid && l == 0) {
-            a.jslot[row] = J;
-            a.E[cell] = E - a.cj * J;
-        }
-    }
-}
 
 int kinetic_pitch(int nnode, int f_dtype)
 {
@@ -80,64 +32,43 @@ int kinetic_pitch(int nnode, int f_dtype)
     return p2 * vec;
 }
 
-template <typename TS, typename TA, int VPL, int L>
-static cudaError_t run(cudaStream_t st, const KinArgs<TA> &a, int num_sms)
+int kinetic_candidates(int nnode_pitch, int f_dtype, int (*out)[2])
 {
-    auto kern = k_kinetic<TS, TA, VPL, L>;
-    const size_t smem = 3 * (size_t)a.pitch * sizeof(TA);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t rows_per_block = (256 / 32) * (32 / L);
-    int64_t blocks = (a.nslots + rows_per_block - 1) / rows_per_block;
-    const int64_t cap = (int64_t)num_sms * per_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, 256, smem, st>>>(a);
-    return cudaGetLastError();
+    const int vec = f_dtype == FDTD_DF_BF16 ? 8 : (f_dtype == FDTD_DF_F64 ? 2 : 4);
+    return kinetic_shape_candidates(nnode_pitch / vec, out);
 }
 
-template <typename TS, typename TA>
-static cudaError_t dispatch(cudaStream_t st, const KinArgs<TA> &a, int num_sms)
-{
-    // vectors per row (a power of two): lanes per row L chosen so that every
-    // lane keeps at least 4 sixteen-byte loads in flight (fewer only for rows
-    // shorter than 4 vectors), at most 32 lanes
-    const int V = a.pitch / Vec<TS>::n;
-    switch (V) {
-    case 1: return run<TS, TA, 1, 1>(st, a, num_sms);
-    case 2: return run<TS, TA, 2, 1>(st, a, num_sms);
-    case 4: return run<TS, TA, 4, 1>(st, a, num_sms);
-    case 8: return run<TS, TA, 4, 2>(st, a, num_sms);
-    case 16: return run<TS, TA, 4, 4>(st, a, num_sms);
-    case 32: return run<TS, TA, 4, 8>(st, a, num_sms);
-    case 64: return run<TS, TA, 4, 16>(st, a, num_sms);
-    case 128: return run<TS, TA, 4, 32>(st, a, num_sms);
-    case 256: return run<TS, TA, 8, 32>(st, a, num_sms);
-    case 512: return run<TS, TA, 16, 32>(st, a, num_sms);
-    default: return cudaErrorInvalidValue;
-    }
-}
+cudaError_t dispatch_kinetic_bf16(cudaStream_t st, const KinArgs<float> &a, int num_sms, int vpl, int l, int bps);
+cudaError_t dispatch_kinetic_f64(cudaStream_t st, const KinArgs<double> &a, int num_sms, int vpl, int l, int bps);
 
 template <>
-cudaError_t launch_kinetic<float>(cudaStream_t st, const KinArgs<float> &a, int f_dtype, int num_sms)
+cudaError_t launch_kinetic<float>(cudaStream_t st, const KinArgs<float> &a, int f_dtype, int num_sms, int vpl, int l,
+                                  int bps)
 {
     if (a.nslots == 0) return cudaSuccess;
-    if (f_dtype == FDTD_DF_F32) return dispatch<float, float>(st, a, num_sms);
-    if (f_dtype == FDTD_DF_BF16) return dispatch<__nv_bfloat16, float>(st, a, num_sms);
+    if (vpl <= 0) {
+        int c[8][2];
+        kinetic_candidates(a.pitch, f_dtype, c);
+        vpl = c[0][0];
+        l = c[0][1];
+    }
+    if (f_dtype == FDTD_DF_F32) return dispatch_kinetic<float, float>(st, a, num_sms, vpl, l, bps);
+    if (f_dtype == FDTD_DF_BF16) return dispatch_kinetic_bf16(st, a, num_sms, vpl, l, bps);
     return cudaErrorInvalidValue;
 }
 
 template <>
-cudaError_t launch_kinetic<double>(cudaStream_t st, const KinArgs<double> &a, int f_dtype, int num_sms)
+cudaError_t launch_kinetic<double>(cudaStream_t st, const KinArgs<double> &a, int f_dtype, int num_sms, int vpl, int l,
+                                   int bps)
 {
     if (a.nslots == 0) return cudaSuccess;
-    if (f_dtype == FDTD_DF_F64) return dispatch<double, double>(st, a, num_sms);
+    if (vpl <= 0) {
+        int c[8][2];
+        kinetic_candidates(a.pitch, f_dtype, c);
+        vpl = c[0][0];
+        l = c[0][1];
+    }
+    if (f_dtype == FDTD_DF_F64) return dispatch_kinetic_f64(st, a, num_sms, vpl, l, bps);
     return cudaErrorInvalidValue;
 }
 

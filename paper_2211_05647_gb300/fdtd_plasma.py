@@ -85,6 +85,12 @@ class fdtd_diag_arrays(ctypes.Structure):
                 ("nslots", ctypes.c_int64), ("nnode", ctypes.c_int64), ("dV", ctypes.c_void_p)]
 
 
+class fdtd_tune_result(ctypes.Structure):
+    _fields_ = [("kin_vpl", ctypes.c_int32), ("kin_l", ctypes.c_int32), ("kin_blocks_per_sm", ctypes.c_int32),
+                ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("block_z", ctypes.c_int32),
+                ("kin_ms", ctypes.c_double), ("stencil_ms", ctypes.c_double)]
+
+
 class fdtd_closure_desc(ctypes.Structure):
     _fields_ = [("params", ctypes.c_void_p), ("params_on_device", ctypes.c_int32), ("engine", ctypes.c_int32),
                 ("e_scale", ctypes.c_double), ("j_scale", ctypes.c_double), ("n_scale", ctypes.c_double),
@@ -113,6 +119,7 @@ SIGNATURES = {
     "fdtd_plasma_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "fdtd_plasma_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "fdtd_plasma_time_kernels": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
+    "fdtd_plasma_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_tune_result)]),
     "fdtd_plasma_read_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                                ctypes.c_int]),
     "fdtd_plasma_write_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
@@ -490,6 +497,13 @@ class Solver:
         out = (ctypes.c_double * 5)()
         _check(self.lib, self.h, self.lib.fdtd_plasma_time_kernels(self.h, int(n), out))
         return dict(h=out[0], kinetic=out[1], closure=out[2], e=out[3], step=out[4])
+
+    def autotune(self) -> dict:
+        """Time the candidate launch shapes on this handle's buffers and keep
+        the fastest (state restored afterwards); see fdtd_plasma_autotune."""
+        r = fdtd_tune_result()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_autotune(self.h, ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in fdtd_tune_result._fields_}
 
     def reset(self):
         _check(self.lib, self.h, self.lib.fdtd_plasma_reset(self.h))

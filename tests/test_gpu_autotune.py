@@ -1,0 +1,45 @@
+"""Launch-shape autotuner: it leaves the simulation state bit-for-bit as it
+found it, writes its choices to the cache, later handles of the same class
+start from them, and the tuned shapes give the same physics (FP32 rounding
+order only)."""
+import os
+
+import numpy as np
+import pytest
+
+from fdtd_inputs import spec_2d_cylinder, spec_3d_slab
+from tests.adapters import FIELDS, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("kind", ["2d", "3d"])
+def test_autotune_restores_state_and_caches(tmp_path, monkeypatch, kind):
+    from paper_2211_05647_gb300 import Solver
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(cache))
+    if kind == "2d":
+        spec = spec_2d_cylinder(n=300, ny=260, R=60, center=(170, 130), src=(80, 130), steps=120, seed=4)
+        names = FIELDS[2]
+    else:
+        spec = spec_3d_slab(n=48, ny=40, nz=64, cpml=8, slab=(28, 44), src_k=12, steps=120, f_dtype="f32")
+        names = FIELDS[3]
+    s = Solver.from_spec(spec)
+    s.step(60)
+    before = {n: s.read(n, device=False).copy() for n in names + ["j", "df"]}
+    res = s.autotune()
+    print(f"autotune {kind}: {res}")
+    for n, v in before.items():
+        assert np.array_equal(s.read(n, device=False), v), n
+    assert res["kin_vpl"] > 0 and res["kin_l"] > 0 and res["block_x"] > 0
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 2 and any("|kinetic|" in ln for ln in lines) and any("|stencil" in ln for ln in lines)
+    s.step(60)
+    ref = Solver.from_spec(spec)      # picks the cached shapes up at create / set_plasma
+    ref.step(120)
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "empty.txt"))
+    dflt = Solver.from_spec(spec)     # default shapes
+    dflt.step(120)
+    for n in names:
+        assert np.array_equal(s.read(n, device=False), ref.read(n, device=False)), n
+        assert rel_l2(s.read(n, device=False), dflt.read(n, device=False)) <= 1e-5, n
