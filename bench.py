@@ -148,9 +148,9 @@ def kinetic_src_sha() -> str:
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel: str, workload: str):
+def ncu_traffic(kernel: str, workload: str, shape=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source and the same launch shape (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -160,6 +160,8 @@ def ncu_traffic(kernel: str, workload: str):
             continue
         kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
         if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src_sha") == sha:
+            if shape is not None and (int(kv.get("vpl", 0)), int(kv.get("l", 0))) != tuple(shape):
+                return None
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -305,7 +307,9 @@ def main():
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     roof = {"bound": "hbm", "kernel": "k_kinetic", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic("k_kinetic", args.workload),
+            "frac": achieved / peak,
+            "traffic": ncu_traffic("k_kinetic", args.workload,
+                                   (tune["kin_vpl"], tune["kin_l"]) if tune and tune["kin_vpl"] else (8, 32)),
             "alg_bytes_per_launch": alg_bytes, "launch_ms": kt["kinetic"],
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
     fb = 8 if s.precision == "f64" else 4
