@@ -749,3 +749,100 @@ void or_kinetic_drive(const or_params *p, double dt, double density, const doubl
     if (df_out) memcpy(df_out, row, sizeof(double) * nn);
     free(v); free(w); free(f0); free(f0p); free(nu); free(dV); free(al); free(be); free(row);
 }
+
+/* ------------------------------------------------------------ Poynting flux */
+
+/* Electromagnetic power out of an axis-aligned box, S = E x H, at time n:
+ * E^n on the E-node planes that bound the box, H time-centred at n -- the mean
+ * of the stored H^{n-1/2} and of H^{n+1/2} = H^{n-1/2} - dt/mu0 curl E^n (vacuum
+ * curl) -- and averaged in space onto the plane from the two neighbouring H
+ * planes (an H plane outside the grid counts as 0).
+ * box = {i0, i1, j0, j1, k0, k1}: the faces are the E-node planes i0, i1 (x),
+ * j0, j1 (y), k0, k1 (z), each summed over the cell indices [lo, hi) of the
+ * other two axes and weighted by the face element (dx^2 in 3-D, dx in 2-D, 1
+ * in 1-D).  1-D uses the z faces k0, k1 (Ex Hy); 2-D TMz the x and y faces.
+ * out[0..5] = power through the faces x0, x1, y0, y1, z0, z1 along +axis;
+ * out[6] = net outward power = x1 - x0 + y1 - y0 + z1 - z0. */
+void or_poynting(const or_sim *s, const int64_t *box, double *out)
+{
+    const int64_t nx = s->nx, ny = s->ny, nz = s->nz;
+    const double mu0 = 1.0 / (OR_EPS0 * OR_C0 * OR_C0);
+    const double ch = s->dt / (mu0 * s->p.dx);
+    for (int q = 0; q < 7; ++q) out[q] = 0.0;
+    if (s->p.ndim == 1) {
+        const double *ex = s->f[EX], *hy = s->f[HY];
+        for (int f = 0; f < 2; ++f) {
+            const int64_t k = box[4 + f];
+            double hb = 0.0;   /* time-centred Hy averaged onto node k */
+            for (int64_t kk = k - 1; kk <= k; ++kk)
+                if (kk >= 0 && kk < nz) hb += 0.5 * (hy[kk] - 0.5 * ch * (ex[kk + 1] - ex[kk]));
+            out[4 + f] = ex[k] * hb;
+        }
+    } else if (s->p.ndim == 2) {
+        const double *ez = s->f[EZ], *hx = s->f[HX], *hy = s->f[HY];
+#define EZ2(i, j) ((i) < nx && (j) < ny ? ez[(j) * nx + (i)] : 0.0)
+        /* time-centred H at its own position, 0 outside the grid */
+#define HXT(i, j) ((i) >= 0 && (j) >= 0 && (i) < nx && (j) < ny ? hx[(j) * nx + (i)] - 0.5 * ch * (EZ2(i, (j) + 1) - EZ2(i, j)) : 0.0)
+#define HYT(i, j) ((i) >= 0 && (j) >= 0 && (i) < nx && (j) < ny ? hy[(j) * nx + (i)] + 0.5 * ch * (EZ2((i) + 1, j) - EZ2(i, j)) : 0.0)
+        const double dA = s->p.dx;
+        for (int f = 0; f < 2; ++f) {
+            const int64_t i = box[f];
+            double acc = 0.0;
+            for (int64_t j = box[2]; j < box[3]; ++j)   /* S_x = -Ez Hy */
+                acc += -EZ2(i, j) * 0.5 * (HYT(i - 1, j) + HYT(i, j));
+            out[f] = acc * dA;
+        }
+        for (int f = 0; f < 2; ++f) {
+            const int64_t j = box[2 + f];
+            double acc = 0.0;
+            for (int64_t i = box[0]; i < box[1]; ++i)   /* S_y = Ez Hx */
+                acc += EZ2(i, j) * 0.5 * (HXT(i, j - 1) + HXT(i, j));
+            out[2 + f] = acc * dA;
+        }
+#undef EZ2
+#undef HXT
+#undef HYT
+    } else {
+        const double *ex = s->f[EX], *ey = s->f[EY], *ez = s->f[EZ];
+        const double *hx = s->f[HX], *hy = s->f[HY], *hz = s->f[HZ];
+#define E3(a, i, j, k) ((i) < nx && (j) < ny && (k) < nz ? (a)[((k) * ny + (j)) * nx + (i)] : 0.0)
+#define IN3(i, j, k) ((i) >= 0 && (j) >= 0 && (k) >= 0 && (i) < nx && (j) < ny && (k) < nz)
+#define HXT(i, j, k) (IN3(i, j, k) ? hx[((k) * ny + (j)) * nx + (i)] - 0.5 * ch * ((E3(ez, i, (j) + 1, k) - E3(ez, i, j, k)) - (E3(ey, i, j, (k) + 1) - E3(ey, i, j, k))) : 0.0)
+#define HYT(i, j, k) (IN3(i, j, k) ? hy[((k) * ny + (j)) * nx + (i)] - 0.5 * ch * ((E3(ex, i, j, (k) + 1) - E3(ex, i, j, k)) - (E3(ez, (i) + 1, j, k) - E3(ez, i, j, k))) : 0.0)
+#define HZT(i, j, k) (IN3(i, j, k) ? hz[((k) * ny + (j)) * nx + (i)] - 0.5 * ch * ((E3(ey, (i) + 1, j, k) - E3(ey, i, j, k)) - (E3(ex, i, (j) + 1, k) - E3(ex, i, j, k))) : 0.0)
+        const double dA = s->p.dx * s->p.dx;
+        for (int f = 0; f < 2; ++f) {   /* S_x = Ey Hz - Ez Hy */
+            const int64_t i = box[f];
+            double acc = 0.0;
+            for (int64_t k = box[4]; k < box[5]; ++k)
+                for (int64_t j = box[2]; j < box[3]; ++j)
+                    acc += E3(ey, i, j, k) * 0.5 * (HZT(i - 1, j, k) + HZT(i, j, k)) -
+                           E3(ez, i, j, k) * 0.5 * (HYT(i - 1, j, k) + HYT(i, j, k));
+            out[f] = acc * dA;
+        }
+        for (int f = 0; f < 2; ++f) {   /* S_y = Ez Hx - Ex Hz */
+            const int64_t j = box[2 + f];
+            double acc = 0.0;
+            for (int64_t k = box[4]; k < box[5]; ++k)
+                for (int64_t i = box[0]; i < box[1]; ++i)
+                    acc += E3(ez, i, j, k) * 0.5 * (HXT(i, j - 1, k) + HXT(i, j, k)) -
+                           E3(ex, i, j, k) * 0.5 * (HZT(i, j - 1, k) + HZT(i, j, k));
+            out[2 + f] = acc * dA;
+        }
+        for (int f = 0; f < 2; ++f) {   /* S_z = Ex Hy - Ey Hx */
+            const int64_t k = box[4 + f];
+            double acc = 0.0;
+            for (int64_t j = box[2]; j < box[3]; ++j)
+                for (int64_t i = box[0]; i < box[1]; ++i)
+                    acc += E3(ex, i, j, k) * 0.5 * (HYT(i, j, k - 1) + HYT(i, j, k)) -
+                           E3(ey, i, j, k) * 0.5 * (HXT(i, j, k - 1) + HXT(i, j, k));
+            out[4 + f] = acc * dA;
+        }
+#undef E3
+#undef IN3
+#undef HXT
+#undef HYT
+#undef HZT
+    }
+    out[6] = out[1] - out[0] + out[3] - out[2] + out[5] - out[4];
+}

@@ -98,6 +98,7 @@ def _load():
         lib.or_source.restype = ctypes.c_double
         lib.or_source.argtypes = [P, ctypes.c_double]
         lib.or_kinetic_drive.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64, dp, dp]
+        lib.or_poynting.argtypes = [vp, ip, dp]
         _lib = lib
         return lib
 
@@ -201,6 +202,13 @@ class Sim:
 
     def step(self, n: int = 1):
         self._lib.or_step(self._h, int(n))
+
+    def poynting(self, box) -> np.ndarray:
+        """Power through the faces of box (i0, i1, j0, j1, k0, k1): [x0, x1, y0, y1, z0, z1, net outward]."""
+        b = np.ascontiguousarray(box, dtype=np.int64)
+        out = np.zeros(7)
+        self._lib.or_poynting(self._h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(out))
+        return out
 
     def diag(self) -> dict:
         out = np.zeros(6)
