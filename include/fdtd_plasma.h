@@ -210,6 +210,24 @@ int fdtd_plasma_info(fdtd_plasma_t h, double *dt, int64_t *steps_done);
 /* Compute FP64 diagnostics of the current state (synchronises the stream). */
 int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out);
 
+/* Electromagnetic power out of an axis-aligned box at the current step (the
+ * Poynting vector S = E x H of the field equations of Sec. 2, Eq. 1-2),
+ * computed in FP64 whatever the field precision; synchronises the stream.
+ *   box = {i0, i1, j0, j1, k0, k1} (host, 6 values): the faces are the E-node
+ *     planes i = i0, i1 (x), j = j0, j1 (y), k = k0, k1 (z); each face sums
+ *     over cell indices [lo, hi) of its two in-plane axes.  Axes the grid does
+ *     not have are ignored (1-D: only k0, k1, 0 <= k <= nz; 2-D: only x and y).
+ *     Used axes need 0 <= lo <= hi < number of E nodes on that axis.
+ *   E is E^n; H is time-centred at n, (H^{n-1/2} + H^{n+1/2}) / 2 with the
+ *     vacuum curl of E^n, averaged onto the face plane from the H nodes on
+ *     either side (nodes off the grid count as 0); face element dx^2 (3-D),
+ *     dx (2-D), 1 (1-D).
+ *   out (host, 7 doubles): power through faces x0, x1, y0, y1, z0, z1 along
+ *     +axis (W, W/m or W/m^2 for 3-D, 2-D, 1-D), out[6] = net outward power
+ *     x1 - x0 + y1 - y0 + z1 - z0.
+ * Returns FDTD_ERR_INVAL for a NULL argument or a face outside the grid. */
+int fdtd_plasma_poynting(fdtd_plasma_t h, const int64_t *box, double *out);
+
 /* Checkpoint: the full state (fields, psi, delta f, J, step counter) in an
  * opaque byte blob of fdtd_plasma_state_bytes() bytes, host or device.
  * load_state requires a handle with the same configuration. */

@@ -1122,6 +1122,48 @@ int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
     return FDTD_OK;
 }
 
+int fdtd_plasma_poynting(fdtd_plasma_t h, const int64_t *box, double *out)
+{
+    if (!h || !box || !out) return FDTD_ERR_INVAL;
+    const int nd = h->g.ndim;
+    // E-node extent per axis; axes a 1-D or 2-D grid does not have are ignored
+    const int64_t ne[3] = {nd == 1 ? 1 : h->nx, nd == 1 ? 1 : h->ny, nd == 1 ? h->nz + 1 : nd == 2 ? 1 : h->nz};
+    const bool used[3] = {nd >= 2, nd >= 2, nd != 2};
+    PoyntingBox b{};
+    for (int ax = 0; ax < 3; ++ax) {
+        b.lo[ax] = used[ax] ? box[2 * ax] : 0;
+        b.hi[ax] = used[ax] ? box[2 * ax + 1] : 0;
+        if (used[ax] && !(0 <= b.lo[ax] && b.lo[ax] <= b.hi[ax] && b.hi[ax] < ne[ax]))
+            return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_poynting: box faces must satisfy 0 <= lo <= hi < E nodes");
+        b.plane[2 * ax] = b.lo[ax];
+        b.plane[2 * ax + 1] = b.hi[ax];
+    }
+    b.off[0] = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int ax = f >> 1;
+        int64_t np = 0;
+        if (nd == 1) np = ax == 2 ? 1 : 0;
+        else if (nd == 2) np = ax == 2 ? 0 : (ax == 0 ? b.hi[1] - b.lo[1] : b.hi[0] - b.lo[0]);
+        else {
+            const int u = ax == 0 ? 1 : 0, w = ax == 2 ? 1 : 2;
+            np = (b.hi[u] - b.lo[u]) * (b.hi[w] - b.lo[w]);
+        }
+        b.off[f + 1] = b.off[f] + np;
+    }
+    const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
+    DiagArgs a{};
+    a.ndim = nd;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    for (int q = 0; q < 6; ++q) { a.f[q] = h->f[q]; a.flen[q] = h->flen[q]; }
+    a.precision = h->g.precision;
+    a.ch = h->dt / (mu0 * h->g.dx);
+    const double dA = nd == 3 ? h->g.dx * h->g.dx : nd == 2 ? h->g.dx : 1.0;
+    CK(h, launch_poynting(h->stream, a, b, dA, h->diag_partials, h->diag_blocks, h->diag_out));
+    CK(h, cudaMemcpyAsync(out, h->diag_out, 7 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
 // ------------------------------------------------------------ checkpoints
 // blob: 8 x uint64 header, then fields, psi, df (raw rows), J, mur state, step
 

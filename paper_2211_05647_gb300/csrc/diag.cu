@@ -5,6 +5,7 @@
 // Pass 1: grid-stride blocks accumulate FP64 partials (one row of 6 per block)
 // into a scratch buffer; pass 2: one block reduces the rows.  The fields are
 // read once; delta f rows are read one warp per row.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -168,6 +169,135 @@ cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, in
     else
         k_diag_partial<float><<<blocks, 256, 0, st>>>(a, partials);
     k_diag_final<<<1, 32, 0, st>>>(partials, blocks, a.eps0_half_dv, a.mu0_half_dv, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ Poynting flux
+// S = E x H through the six faces of an axis-aligned box at step n: E^n on
+// the face's E-node plane; H time-centred, (H^{n-1/2} + H^{n+1/2}) / 2 with
+// the vacuum curl of E^n, then averaged onto the plane from the H nodes on
+// either side (nodes off the grid read 0).  All face points of all faces are
+// one flat index space; each block keeps one FP64 sum per face.
+
+template <typename T>
+struct PoyntingView {
+    const DiagArgs &a;
+    __device__ double e(int q, int64_t i, int64_t j, int64_t k) const   // E_q at node (i,j,k), 0 off the grid
+    {
+        if (i < 0 || j < 0 || k < 0 || i >= a.nx || j >= a.ny || k >= a.nz) return 0.0;
+        return ld<T>(a.f[q], (k * a.ny + j) * a.nx + i);
+    }
+    __device__ bool on(int64_t i, int64_t j, int64_t k) const
+    {
+        return i >= 0 && j >= 0 && k >= 0 && i < a.nx && j < a.ny && k < a.nz;
+    }
+    // time-centred H components at their own Yee positions (index of the node)
+    __device__ double hx(int64_t i, int64_t j, int64_t k) const
+    {
+        if (!on(i, j, k)) return 0.0;
+        const double curl = a.ndim == 2 ? e(2, i, j + 1, k) - e(2, i, j, k)
+                                        : (e(2, i, j + 1, k) - e(2, i, j, k)) - (e(1, i, j, k + 1) - e(1, i, j, k));
+        return ld<T>(a.f[3], (k * a.ny + j) * a.nx + i) - 0.5 * a.ch * curl;
+    }
+    __device__ double hy(int64_t i, int64_t j, int64_t k) const
+    {
+        if (!on(i, j, k)) return 0.0;
+        const double curl = a.ndim == 2 ? -(e(2, i + 1, j, k) - e(2, i, j, k))
+                                        : (e(0, i, j, k + 1) - e(0, i, j, k)) - (e(2, i + 1, j, k) - e(2, i, j, k));
+        return ld<T>(a.f[4], (k * a.ny + j) * a.nx + i) - 0.5 * a.ch * curl;
+    }
+    __device__ double hz(int64_t i, int64_t j, int64_t k) const
+    {
+        if (!on(i, j, k)) return 0.0;
+        const double curl = (e(1, i + 1, j, k) - e(1, i, j, k)) - (e(0, i, j + 1, k) - e(0, i, j, k));
+        return ld<T>(a.f[5], (k * a.ny + j) * a.nx + i) - 0.5 * a.ch * curl;
+    }
+};
+
+// Normal component of E x H at face point t of face f (before the area factor).
+template <typename T>
+__device__ double face_flux(const DiagArgs &a, const PoyntingBox &b, int f, int64_t t)
+{
+    const int ax = f >> 1;
+    const int64_t p = b.plane[f];
+    if (a.ndim == 1) {   // Ex(k) Hy averaged from k - 1/2 and k + 1/2
+        const int64_t k = p;
+        double hb = 0.0;
+        for (int64_t kk = k - 1; kk <= k; ++kk) {
+            if (kk < 0 || kk >= a.nz) continue;
+            const double h = ld<T>(a.f[4], kk) - 0.5 * a.ch * (ld<T>(a.f[0], kk + 1) - ld<T>(a.f[0], kk));
+            hb += 0.5 * h;
+        }
+        return k <= a.nz ? ld<T>(a.f[0], k) * hb : 0.0;
+    }
+    PoyntingView<T> v{a};
+    // the two in-plane axes, lower-numbered first
+    const int u = ax == 0 ? 1 : 0, w = ax == 2 ? 1 : 2;
+    const int64_t nu = b.hi[u] - b.lo[u];
+    int64_t c[3];
+    c[ax] = p;
+    c[u] = b.lo[u] + t % nu;
+    c[w] = a.ndim == 2 ? 0 : b.lo[w] + t / nu;
+    const int64_t i = c[0], j = c[1], k = c[2];
+    if (a.ndim == 2) {
+        const double ez = v.e(2, i, j, 0);
+        if (ax == 0) return -ez * 0.5 * (v.hy(i - 1, j, 0) + v.hy(i, j, 0));   // S_x = -Ez Hy
+        return ez * 0.5 * (v.hx(i, j - 1, 0) + v.hx(i, j, 0));                 // S_y =  Ez Hx
+    }
+    if (ax == 0)   // S_x = Ey Hz - Ez Hy
+        return v.e(1, i, j, k) * 0.5 * (v.hz(i - 1, j, k) + v.hz(i, j, k)) -
+               v.e(2, i, j, k) * 0.5 * (v.hy(i - 1, j, k) + v.hy(i, j, k));
+    if (ax == 1)   // S_y = Ez Hx - Ex Hz
+        return v.e(2, i, j, k) * 0.5 * (v.hx(i, j - 1, k) + v.hx(i, j, k)) -
+               v.e(0, i, j, k) * 0.5 * (v.hz(i, j - 1, k) + v.hz(i, j, k));
+    return v.e(0, i, j, k) * 0.5 * (v.hy(i, j, k - 1) + v.hy(i, j, k)) -   // S_z = Ex Hy - Ey Hx
+           v.e(1, i, j, k) * 0.5 * (v.hx(i, j, k - 1) + v.hx(i, j, k));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_poynting_partial(DiagArgs a, PoyntingBox b, double *partials)
+{
+    __shared__ double red[6][8];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = tid; g < b.off[6]; g += nth) {
+        int f = 0;
+        while (g >= b.off[f + 1]) ++f;
+        acc[f] += face_flux<T>(a, b, f, g - b.off[f]);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int f = 0; f < 6; ++f) {
+        const double s = warp_sum(acc[f]);
+        if (lane == 0) red[f][w] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[threadIdx.x][q];
+        partials[(int64_t)blockIdx.x * 7 + threadIdx.x] = s;
+    }
+}
+
+__global__ void k_poynting_final(const double *partials, int nblocks, double dA, double *out)
+{
+    if (threadIdx.x != 0) return;
+    double o[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int f = 0; f < 6; ++f) o[f] += partials[(int64_t)b * 7 + f];
+    for (int f = 0; f < 6; ++f) out[f] = o[f] * dA;
+    out[6] = (o[1] - o[0] + o[3] - o[2] + o[5] - o[4]) * dA;
+}
+
+cudaError_t launch_poynting(cudaStream_t st, const DiagArgs &a, const PoyntingBox &b, double dA, double *partials,
+                            int max_blocks, double *out)
+{
+    int blocks = (int)std::min<int64_t>(max_blocks, std::max<int64_t>(1, (b.off[6] + 255) / 256));
+    if (a.precision == FDTD_F64)
+        k_poynting_partial<double><<<blocks, 256, 0, st>>>(a, b, partials);
+    else
+        k_poynting_partial<float><<<blocks, 256, 0, st>>>(a, b, partials);
+    k_poynting_final<<<1, 32, 0, st>>>(partials, blocks, dA, out);
     return cudaGetLastError();
 }
 

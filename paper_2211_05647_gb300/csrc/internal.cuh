@@ -150,6 +150,18 @@ struct DiagArgs {
 // out[0..6): energy, energy_plain, number, number_max_cell, number_abs, finite
 cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, int max_blocks, double *out);
 
+// Faces of a Poynting box: f = 2 * axis + (0 lower, 1 upper); plane[f] is the
+// E-node index of the face along its axis, lo/hi the cell range of the box on
+// each axis, off[f] the first flat face-point index of face f (off[6] = total).
+struct PoyntingBox {
+    int64_t lo[3], hi[3];
+    int64_t plane[6];
+    int64_t off[7];
+};
+// out[0..6): power through faces x0, x1, y0, y1, z0, z1 along +axis; out[6] net outward
+cudaError_t launch_poynting(cudaStream_t st, const DiagArgs &a, const PoyntingBox &b, double dA, double *partials,
+                            int max_blocks, double *out);
+
 struct ClosureArgs {
     const int32_t *cell;
     const float *dens;

@@ -130,6 +130,8 @@ SIGNATURES = {
     "fdtd_plasma_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]),
     "fdtd_plasma_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_diag)]),
+    "fdtd_plasma_poynting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_double)]),
     "fdtd_plasma_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "fdtd_plasma_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
@@ -568,6 +570,14 @@ class Solver:
         _check(self.lib, self.h, self.lib.fdtd_plasma_diagnostics(self.h, ctypes.byref(d)))
         return dict(energy=d.energy, energy_plain=d.energy_plain, number=d.number,
                     number_max_cell=d.number_max_cell, number_abs=d.number_abs, finite=bool(d.finite), step=d.step)
+
+    def poynting(self, box) -> list:
+        """Power out of the box (i0, i1, j0, j1, k0, k1) at the current step:
+        [x0, x1, y0, y1, z0, z1, net outward] (FP64)."""
+        b = (ctypes.c_int64 * 6)(*[int(v) for v in box])
+        out = (ctypes.c_double * 7)()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_poynting(self.h, b, out))
+        return list(out)
 
     def save_state(self, device: bool = True):
         torch = self.torch

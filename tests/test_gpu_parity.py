@@ -200,6 +200,38 @@ def test_diagnostics_match_oracle(oracle_lib):
     assert dg["finite"] and dg["step"] == 400
 
 
+@pytest.mark.parametrize("ndim,prec", [(1, "f64"), (2, "f64"), (3, "f64"), (1, "f32"), (2, "f32"), (3, "f32")])
+def test_poynting_matches_oracle(oracle_lib, ndim, prec):
+    """Random fields written to both sides (FP32-representable values for the
+    FP32 solver, so both start from the same numbers): the FP64 Poynting
+    diagnostic agrees face by face to rounding order.  Boxes include faces on
+    the grid edges, a box with coincident faces and a single plane."""
+    from paper_2211_05647_gb300 import FdtdError, Solver
+    shape = {1: dict(nz=300), 2: dict(nx=70, ny=53), 3: dict(nx=37, ny=29, nz=23)}[ndim]
+    s = Solver(dict(ndim=ndim, dx=1e-3, courant=0.5, precision=prec, **shape))
+    sim = oracle_lib.Sim(oracle_lib.params(ndim=ndim, dx=1e-3, courant=0.5, **shape))
+    rng = np.random.default_rng(40 + ndim)
+    for nm in FIELDS[ndim]:
+        v = rng.standard_normal(sim.get(nm).size) * (1.0 if nm[0] == "e" else 1 / 377.0)
+        if prec == "f32":
+            v = v.astype(np.float32).astype(np.float64)
+        s.write(nm, v)
+        sim.set(nm, v)
+    boxes = {1: [[0, 0, 0, 0, 0, 300], [0, 0, 0, 0, 17, 250], [0, 0, 0, 0, 5, 5]],
+             2: [[0, 69, 0, 52, 0, 0], [10, 50, 7, 40, 0, 0], [3, 3, 5, 30, 0, 0]],
+             3: [[0, 36, 0, 28, 0, 22], [5, 30, 4, 20, 3, 19], [10, 10, 2, 27, 4, 9]]}[ndim]
+    for box in boxes:
+        got, want = np.array(s.poynting(box)), sim.poynting(box)
+        scale = np.abs(want[:6]).sum()
+        assert scale > 0
+        err = np.abs(got - want).max() / scale
+        print(f"poynting {ndim}-D {prec} box {box}: max face error / scale {err:.2e}")
+        assert err <= 1e-12, (got, want)
+    bad = {1: [0, 0, 0, 0, 3, 301], 2: [0, 70, 0, 10, 0, 0], 3: [5, 4, 0, 1, 0, 1]}[ndim]
+    with pytest.raises(FdtdError):
+        s.poynting(bad)
+
+
 def test_energy_invariant_gpu_fp32():
     """Lossless PEC cavity, random fields: the FP64 diagnostic of the FP32 run
     drifts by at most 1e-5 relative."""
