@@ -119,6 +119,9 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i < 1 || j < 1 || i >= nx || j >= ny) return;
     const int64_t c = j * nx + i;
+    // E^n is read before any psi store: the compiler cannot prove the psi
+    // slabs and Ez apart, so a later load would be a second round trip.
+    const T ezc = ez[c];
     const T dHx = hy[c] - hy[c - 1];     // dHy along x
     const T dHy = hx[c] - hx[c - nx];    // dHx along y
     T upd;
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
         }
         upd = ce * (dHx * kx - dHy * ky) + cpe * (px - py);
     }
-    T v = ez[c] + upd;
+    T v = ezc + upd;
     if (src.kind && i == src.i && j == src.j) v += (T)*src.val;
     ez[c] = v;
 }
@@ -235,6 +238,8 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
     const int64_t sxy = nx * ny;
     const int64_t c = k * sxy + j * nx + i;
     const T hxc = hx[c], hyc = hy[c], hzc = hz[c];
+    // E^n is read up front, before any psi store (see k_e2d).
+    const T exc = ex[c], eyc = ey[c], ezc = ez[c];
     const T dHz_y = j > 0 ? hzc - hz[c - nx] : T(0);
     const T dHy_z = k > 0 ? hyc - hy[c - sxy] : T(0);
     const T dHx_z = k > 0 ? hxc - hx[c - sxy] : T(0);
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
         uz = ce * (dHy_x * kx - dHx_y * ky) + cpe * (p4 - p5);
     }
     if (j > 0 && k > 0) {
-        T v = ex[c] + ux;
+        T v = exc + ux;
         if (src.kind) {
             bool hit = src.loc == FDTD_LOC_SHEET
                            ? (k == src.k && i >= src.i0 && i < src.i1 && j >= src.j0 && j < src.j1)
@@ -282,8 +287,8 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
         }
         ex[c] = v;
     }
-    if (i > 0 && k > 0) ey[c] += uy;
-    if (i > 0 && j > 0) ez[c] += uz;
+    if (i > 0 && k > 0) ey[c] = eyc + uy;
+    if (i > 0 && j > 0) ez[c] = ezc + uz;
 }
 
 __global__ void k_advance(int64_t *d_step, int64_t by) { *d_step += by; }
