@@ -65,8 +65,12 @@ typedef struct or_params {
     int64_t vgrid;                /* 0 signed 1-D, 1 Cartesian (v_par, v_perp), 2 speed 3-D */
     int64_t nv, nv_perp;
     double te_ev, vmax_vth, nu0;
-    int64_t nu_model;             /* 0: nu = N s |v| scaled to mean nu0; 1: nu = nu0 */
+    int64_t nu_model;             /* 0: nu = N s |v| scaled to mean nu0; 1: nu = nu0; 2: s(v) from the table */
     int64_t nonlinear;            /* 1: add flux-form advection of delta f in v_par */
+    int64_t f0_model;             /* 0: Maxwellian, 1: Druyvesteyn (same mean energy 3/2 e Te) */
+    int64_t s_n;                  /* nu_model 2: points of the cross-section table */
+    const double *s_speed;        /* ascending speeds (m/s) */
+    const double *s_sigma;        /* s(v) at those speeds (any unit: only the shape matters) */
 } or_params;
 
 typedef struct or_sim {
@@ -129,21 +133,79 @@ int64_t or_nnode_of(const or_params *p)
     return p->nv;
 }
 
+/* Druyvesteyn F0 of unit density: A exp(-(eps/eps0)^2), eps = m v^2 / 2.
+ * Its mean energy is eps0 Gamma(5/4) / Gamma(3/4); it is set to (3/2) e Te so
+ * that te_ev is the effective temperature, and A normalises the integral of
+ * F0 over velocity space to 1. */
+static double dr_eps0(double te_ev) { return 1.5 * OR_QE * te_ev * tgamma(0.75) / tgamma(1.25); }
+static double dr_amp(double eps0) { return 1.0 / (OR_PI * tgamma(0.75) * pow(2.0 * eps0 / OR_ME, 1.5)); }
+static double dr_f0(double A, double eps0, double v2)   /* F0 at |v|^2 = v2 */
+{
+    const double x = 0.5 * OR_ME * v2 / eps0;
+    return A * exp(-x * x);
+}
+
+/* Cartesian 2-D grid, Druyvesteyn: the marginal over the third velocity
+ * component t, h = int F0 dt, and its v_par derivative
+ * dh/du = int F0'(r) u / r dt = -(2 m u / eps0^2) int eps F0 dt, by composite
+ * Simpson on t in [0, 6 sqrt(2 eps0 / m)] (the integrand is even in t and
+ * below 1e-300 of its peak beyond). */
+static void dr_marginal2(double A, double eps0, double u, double w, double *h, double *dh)
+{
+    const int N = 20000;
+    const double T = 6.0 * sqrt(2.0 * eps0 / OR_ME), dt = T / N;
+    double s0 = 0.0, s1 = 0.0;
+    for (int q = 0; q <= N; ++q) {
+        const double t = q * dt;
+        const double v2 = u * u + w * w + t * t;
+        const double f = dr_f0(A, eps0, v2);
+        const double c = (q == 0 || q == N) ? 1.0 : (q % 2 ? 4.0 : 2.0);
+        s0 += c * f;
+        s1 += c * 0.5 * OR_ME * v2 * f;
+    }
+    *h = 2.0 * s0 * dt / 3.0;
+    *dh = -(2.0 * OR_ME * u / (eps0 * eps0)) * 2.0 * s1 * dt / 3.0;
+}
+
+/* s(v) of the cross-section table, linear between points, constant beyond the ends */
+static double table_sigma(const or_params *p, double v)
+{
+    const int64_t n = p->s_n;
+    if (v <= p->s_speed[0]) return p->s_sigma[0];
+    if (v >= p->s_speed[n - 1]) return p->s_sigma[n - 1];
+    int64_t k = 0;
+    while (p->s_speed[k + 1] < v) ++k;
+    const double r = (v - p->s_speed[k]) / (p->s_speed[k + 1] - p->s_speed[k]);
+    return p->s_sigma[k] + r * (p->s_sigma[k + 1] - p->s_sigma[k]);
+}
+
+/* Velocity-grid tables (Sec. 5.2, Eq. 20-24).  F0 enters through its value and
+ * its v_par derivative on each grid: the 3-D F0 on the speed grid, its 1-D
+ * marginal on the signed grid (Maxwellian: a Gaussian; Druyvesteyn:
+ * (pi^{3/2}/2) A (2 eps0/m) erfc(m u^2 / (2 eps0)), derivative -2 pi u F0(|u|)),
+ * its 2-D marginal on the Cartesian grid. */
 void or_vtables(const or_params *p, double dt, double *v, double *w, double *f0,
                 double *f0p, double *nu, double *dV, double *alpha, double *beta)
 {
     const double vth = sqrt(OR_QE * p->te_ev / OR_ME);
     const double vmax = p->vmax_vth * vth;
     const int64_t nn = or_nnode_of(p);
+    const int dru = p->f0_model == 1;
+    const double eps0 = dr_eps0(p->te_ev), A = dr_amp(eps0);
     double *speed = (double *)malloc(sizeof(double) * nn);
     if (p->vgrid == 0) {
         const double dv = 2.0 * vmax / (double)p->nv;
         for (int64_t a = 0; a < p->nv; ++a) {
             double va = ((double)a + 0.5 - 0.5 * (double)p->nv) * dv;
-            double g = exp(-va * va / (2.0 * vth * vth)) / sqrt(2.0 * OR_PI * vth * vth);
             v[a] = va;
-            f0[a] = g;
-            f0p[a] = -va / (vth * vth) * g;
+            if (dru) {
+                f0[a] = 0.5 * pow(OR_PI, 1.5) * A * (2.0 * eps0 / OR_ME) * erfc(0.5 * OR_ME * va * va / eps0);
+                f0p[a] = -2.0 * OR_PI * va * dr_f0(A, eps0, va * va);
+            } else {
+                double g = exp(-va * va / (2.0 * vth * vth)) / sqrt(2.0 * OR_PI * vth * vth);
+                f0[a] = g;
+                f0p[a] = -va / (vth * vth) * g;
+            }
             w[a] = va * dv;
             dV[a] = dv;
             speed[a] = fabs(va);
@@ -156,10 +218,14 @@ void or_vtables(const or_params *p, double dt, double *v, double *w, double *f0,
             for (int64_t b = 0; b < p->nv_perp; ++b) {
                 double vb = ((double)b + 0.5 - 0.5 * (double)p->nv_perp) * dvq;
                 int64_t j = a * p->nv_perp + b;
-                double g = exp(-(va * va + vb * vb) / (2.0 * vth * vth)) / (2.0 * OR_PI * vth * vth);
                 v[j] = va;
-                f0[j] = g;
-                f0p[j] = -va / (vth * vth) * g;
+                if (dru) {
+                    dr_marginal2(A, eps0, va, vb, &f0[j], &f0p[j]);
+                } else {
+                    double g = exp(-(va * va + vb * vb) / (2.0 * vth * vth)) / (2.0 * OR_PI * vth * vth);
+                    f0[j] = g;
+                    f0p[j] = -va / (vth * vth) * g;
+                }
                 w[j] = va * dvp * dvq;
                 dV[j] = dvp * dvq;
                 speed[j] = sqrt(va * va + vb * vb);
@@ -169,24 +235,33 @@ void or_vtables(const or_params *p, double dt, double *v, double *w, double *f0,
         const double gam = vmax / (double)p->nv;
         for (int64_t k = 0; k < p->nv; ++k) {
             double vk = ((double)k + 0.5) * gam;
-            double g = exp(-vk * vk / (2.0 * vth * vth)) / pow(2.0 * OR_PI * vth * vth, 1.5);
             v[k] = vk;
-            f0[k] = g;
-            f0p[k] = -vk / (vth * vth) * g;
+            if (dru) {
+                const double g = dr_f0(A, eps0, vk * vk);
+                f0[k] = g;
+                f0p[k] = -(OR_ME * OR_ME * vk * vk * vk / (eps0 * eps0)) * g;   /* dF0/dv */
+            } else {
+                double g = exp(-vk * vk / (2.0 * vth * vth)) / pow(2.0 * OR_PI * vth * vth, 1.5);
+                f0[k] = g;
+                f0p[k] = -vk / (vth * vth) * g;
+            }
             w[k] = (4.0 * OR_PI / 3.0) * vk * vk * vk * gam;
             dV[k] = 4.0 * OR_PI * vk * vk * gam;
             speed[k] = vk;
         }
     }
-    /* collision frequency (Eq. 23): nu = N s |v|; N s fixed by the mean */
+    /* collision frequency (Eq. 23): nu = N s(v) |v|; N fixed by the F0-weighted
+     * mean of nu = nu0; s constant (model 0) or tabulated (model 2) */
     double num = 0.0, den = 0.0;
     for (int64_t j = 0; j < nn; ++j) {
-        num += speed[j] * f0[j] * dV[j];
+        const double sv = (p->nu_model == 2 ? table_sigma(p, speed[j]) : 1.0) * speed[j];
+        num += sv * f0[j] * dV[j];
         den += f0[j] * dV[j];
     }
-    const double mean_speed = num / den;
+    const double mean_sv = num / den;
     for (int64_t j = 0; j < nn; ++j) {
-        nu[j] = (p->nu_model == 1) ? p->nu0 : p->nu0 * speed[j] / mean_speed;
+        const double sv = (p->nu_model == 2 ? table_sigma(p, speed[j]) : 1.0) * speed[j];
+        nu[j] = (p->nu_model == 1) ? p->nu0 : p->nu0 * sv / mean_sv;
         alpha[j] = (2.0 - dt * nu[j]) / (2.0 + dt * nu[j]);
         beta[j] = 2.0 * dt * (OR_QE / OR_ME) * f0p[j] / (2.0 + dt * nu[j]);
     }

@@ -27,7 +27,8 @@ _lib = None
 FIELDS = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7}
 VGRID = {"signed1d": 0, "cart2d": 1, "speed3d": 2}
 SRC = {"none": 0, "gauss_sine": 1, "gauss": 2}
-NU = {"nsv": 0, "const": 1}
+NU = {"nsv": 0, "const": 1, "table": 2}
+F0 = {"maxwell": 0, "druyvesteyn": 1}
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +62,8 @@ class Params(ctypes.Structure):
         ("vgrid", ctypes.c_int64), ("nv", ctypes.c_int64), ("nv_perp", ctypes.c_int64),
         ("te_ev", ctypes.c_double), ("vmax_vth", ctypes.c_double), ("nu0", ctypes.c_double),
         ("nu_model", ctypes.c_int64), ("nonlinear", ctypes.c_int64),
+        ("f0_model", ctypes.c_int64), ("s_n", ctypes.c_int64),
+        ("s_speed", ctypes.POINTER(ctypes.c_double)), ("s_sigma", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -114,6 +117,7 @@ DEFAULTS = dict(
     mur=0, src_kind=0, src_amp=1.0, src_fc=0.0, src_tau=1.0, src_t0=0.0,
     src_i=0, src_j=0, src_k=0, src_sheet=0, sheet_i0=0, sheet_i1=0, sheet_j0=0, sheet_j1=0,
     vgrid=0, nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0, nu_model=0, nonlinear=0,
+    f0_model=0, s_table=None,
 )
 
 
@@ -130,10 +134,24 @@ def params(**kw) -> Params:
             v = SRC[v]
         if k == "nu_model" and isinstance(v, str):
             v = NU[v]
+        if k == "f0_model" and isinstance(v, str):
+            v = F0[v]
         d[k] = v
     p = Params()
+    table = d.pop("s_table")
     for k, v in d.items():
         setattr(p, k, v)
+    if table is not None:
+        sp = np.ascontiguousarray(table[0], dtype=np.float64)
+        sg = np.ascontiguousarray(table[1], dtype=np.float64)
+        if sp.size != sg.size or sp.size < 2 or np.any(np.diff(sp) <= 0):
+            raise ValueError("s_table: two arrays of equal length >= 2, speeds strictly ascending")
+        p._keep = (sp, sg)          # the C side holds raw pointers into these
+        p.s_n = sp.size
+        p.s_speed = sp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.s_sigma = sg.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    elif d["nu_model"] == 2:
+        raise ValueError("nu_model 'table' needs s_table=(speeds, sigma)")
     return p
 
 
