@@ -263,3 +263,28 @@ def kinetic_drive(p: Params, dt: float, density: float, E: np.ndarray):
     df = np.zeros(n)
     lib.or_kinetic_drive(ctypes.byref(p), dt, density, _dp(E), E.size, _dp(J), _dp(df))
     return J, df
+
+
+def port_spectra(sims, ports, freqs, steps: int) -> list:
+    """Running DFT at ports (Sec. 5.3: the slab's S-parameters come from port
+    spectra).  Steps every simulation in sims `steps` times; after step n the
+    polarisation field E^n at t_n = n dt, averaged over each port's node
+    indices, is accumulated into X[p, f] = sum_n E_p(t_n) exp(-i 2 pi f t_n) dt.
+    Returns one complex array [nports, nfreq] per simulation."""
+    freqs = np.asarray(freqs, dtype=np.float64)
+    comp = {1: "ex", 2: "ez", 3: "ex"}
+    out = []
+    for sim in sims:
+        X = np.zeros((len(ports), freqs.size), dtype=np.complex128)
+        name = comp[int(sim.p.ndim)]
+        dt = sim.dt
+        for _ in range(steps):
+            sim.step(1)
+            t = sim.steps_done * dt
+            e = sim.get(name)
+            phase = np.exp(-2j * np.pi * freqs * t) * dt
+            for q, cells in enumerate(ports):
+                X[q] += np.mean(e[np.asarray(cells, dtype=np.int64)]) * phase
+        out.append(X)
+    return out
+

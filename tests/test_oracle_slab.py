@@ -33,28 +33,46 @@ def test_slab_reflection_transmission(oracle_lib):
     sv, ss = O.Sim(O.params(**base)), O.Sim(O.params(**base), dens)
     p1, p2 = 700, 1800
     M = 12000
-    r = np.zeros((4, M))
-    for m in range(M):
-        r[0, m] = sv.get("ex")[p1]; r[1, m] = ss.get("ex")[p1]
-        r[2, m] = sv.get("ex")[p2]; r[3, m] = ss.get("ex")[p2]
-        sv.step(1); ss.step(1)
+    freqs = np.linspace(0.55, 1.55, 21) * F0
+    Xv, Xs = O.port_spectra([sv, ss], [[p1], [p2]], freqs, M)
     dt = sv.dt
-    F = np.fft.rfft(r, axis=1)
-    fr = np.fft.rfftfreq(M, dt)
     t = O.vtables(ss.p, dt)
     weff = plasma_omega(n) * np.sqrt(-np.sum(t["w"] * t["f0p"]))
     d = (k2 - k1 + 1) * dz          # plasma nodes k1..k2 each own one cell
     worst = 0.0
-    for f in np.linspace(0.55, 1.55, 21) * F0:
-        i = np.argmin(abs(fr - f))
-        w = 2 * np.pi * fr[i]
+    for i, f in enumerate(freqs):
+        w = 2 * np.pi * f
         R, T = slab_rt(w, drude_eps(w, weff, nu), d)
-        Rm = abs((F[1, i] - F[0, i]) / F[0, i])
-        Tm = abs(F[3, i] / F[2, i])
+        Rm = abs((Xs[0, i] - Xv[0, i]) / Xv[0, i])      # S11 from the port spectra
+        Tm = abs(Xs[1, i] / Xv[1, i])                   # S21
         worst = max(worst, abs(Rm - abs(R)), abs(Tm - abs(T)))
-        if fr[i] < 0.75 * F0:        # below f_p = 0.8 f0: (almost) total reflection
+        if f < 0.75 * F0:            # below f_p = 0.8 f0: (almost) total reflection
             assert Rm > 0.93 and Tm < 0.05
     assert worst < 2e-2, worst
+
+
+def test_port_spectra_equal_fft_at_bin_frequencies(oracle_lib):
+    """At the FFT's bin frequencies k / (M dt) the running DFT of a pulse that
+    has passed the port is dt times the discrete Fourier transform (numpy's
+    FFT) of the recorded series, with the phase of the t_n = n dt time origin;
+    a port of several nodes averages their fields."""
+    O = oracle_lib
+    dz, nz = LAM0 / 40, 1200
+    base = dict(ndim=1, nz=nz, dx=dz, courant=0.5, mur=1, src_kind="gauss_sine", src_amp=1.0, src_fc=F0,
+                src_tau=0.5 * T0, src_t0=3 * T0, src_k=200)
+    s1, s2 = O.Sim(O.params(**base)), O.Sim(O.params(**base))
+    M = 2048
+    dt = s1.dt
+    cells = [400, 401, 405]
+    rec = np.zeros(M)
+    for m in range(M):
+        s2.step(1)
+        rec[m] = np.mean(s2.get("ex")[cells])
+    fr = np.arange(1, 60) / (M * dt)
+    (X,) = O.port_spectra([s1], [cells], fr, M)
+    # t_n = (m + 1) dt for record m: shift the FFT's origin by one step
+    want = dt * np.fft.fft(rec)[1:60] * np.exp(-2j * np.pi * fr * dt)
+    assert np.abs(X[0] - want).max() <= 1e-10 * np.abs(want).max()
 
 
 def test_mur_reflection_matches_discrete_theory(oracle_lib):
