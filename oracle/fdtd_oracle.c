@@ -71,6 +71,9 @@ typedef struct or_params {
     int64_t s_n;                  /* nu_model 2: points of the cross-section table */
     const double *s_speed;        /* ascending speeds (m/s) */
     const double *s_sigma;        /* s(v) at those speeds (any unit: only the shape matters) */
+    int64_t evolve_f0;            /* speed grid: 1 = F0 evolves (heating + elastic collisions) */
+    double mass_ratio;            /* m / M of the gas atom (elastic energy exchange) */
+    double tg_ev;                 /* gas temperature (eV) */
 } or_params;
 
 typedef struct or_sim {
@@ -85,6 +88,7 @@ typedef struct or_sim {
     int64_t *slot_cell;
     double *dens;                 /* density per slot (m^-3) */
     double *df;                   /* delta f, [slot][node] */
+    double *g0;                   /* evolve_f0: F0 - F0(table) per unit density, [slot][node] */
     double *jslot;                /* J^{n+1/2} per slot */
     double *jnode;                /* J on the polarisation array (0 off plasma) */
     double *v, *w, *f0, *f0p, *nu, *dV, *alpha, *beta;
@@ -384,6 +388,7 @@ or_sim *or_create(const or_params *p, const double *density)
     s->dens = (double *)malloc(sizeof(double) * (s->nslots ? s->nslots : 1));
     s->jslot = (double *)calloc((size_t)(s->nslots ? s->nslots : 1), sizeof(double));
     s->df = (double *)calloc((size_t)((s->nslots ? s->nslots : 1) * s->nnode), sizeof(double));
+    s->g0 = (double *)calloc((size_t)((s->nslots ? s->nslots : 1) * s->nnode), sizeof(double));
     int64_t q = 0;
     if (density) {
         for (int64_t c = 0; c < np; ++c)
@@ -421,7 +426,7 @@ void or_destroy(or_sim *s)
         free(s->pe_b[ax]); free(s->pe_a[ax]); free(s->pe_k[ax]);
         free(s->ph_b[ax]); free(s->ph_a[ax]); free(s->ph_k[ax]);
     }
-    free(s->slot_cell); free(s->dens); free(s->jslot); free(s->df); free(s->jnode);
+    free(s->slot_cell); free(s->dens); free(s->jslot); free(s->df); free(s->g0); free(s->jnode);
     free(s->v); free(s->w); free(s->f0); free(s->f0p); free(s->nu); free(s->dV);
     free(s->alpha); free(s->beta); free(s->mirror);
     free(s);
@@ -433,7 +438,7 @@ int64_t or_nnode(const or_sim *s) { return s->nnode; }
 int64_t or_steps_done(const or_sim *s) { return s->step; }
 void or_slot_cells(const or_sim *s, int64_t *out) { memcpy(out, s->slot_cell, sizeof(int64_t) * s->nslots); }
 
-/* which: 0..5 fields, 6 = J per slot, 7 = delta f [slot][node] */
+/* which: 0..5 fields, 6 = J per slot, 7 = delta f [slot][node], 8 = F0 correction [slot][node] */
 int or_get(const or_sim *s, int which, double *out)
 {
     if (which >= 0 && which <= 5) {
@@ -444,6 +449,7 @@ int or_get(const or_sim *s, int which, double *out)
     }
     if (which == 6) { memcpy(out, s->jslot, sizeof(double) * s->nslots); return 0; }
     if (which == 7) { memcpy(out, s->df, sizeof(double) * s->nslots * s->nnode); return 0; }
+    if (which == 8) { memcpy(out, s->g0, sizeof(double) * s->nslots * s->nnode); return 0; }
     return -1;
 }
 
@@ -461,6 +467,7 @@ int or_set(or_sim *s, int which, const double *in)
         return 0;
     }
     if (which == 7) { memcpy(s->df, in, sizeof(double) * s->nslots * s->nnode); return 0; }
+    if (which == 8) { memcpy(s->g0, in, sizeof(double) * s->nslots * s->nnode); return 0; }
     return -1;
 }
 
@@ -478,6 +485,58 @@ int or_set(or_sim *s, int which, const double *in)
  *   even^{n+1/2} = even^{n-1/2} + dt A_even
  * with A_j = -(Phi_{a+1/2} - Phi_{a-1/2}) / dv_par.  (The linear mode is the
  * paper's model; with delta f odd it is the same update without A.) */
+/* Isotropic F0 evolution on the speed grid (the F0 equation of the two-term
+ * expansion, Sec. 5.2, without the spatial term of the local model):
+ *   dF0/dt = (e E / (3 m v^2)) d/dv (v^2 F1) + C0(F0),
+ *   C0 = (m/M) (1/v^2) d/dv [ v^3 nu (F0 + (k Tg / (m v)) dF0/dv) ]  (elastic).
+ * F0 = F0(table) + g with g per unit density; F1 = delta f / n.  One step,
+ * with E = E^n, F1 and g at n - 1/2 on entry:
+ *  1. F0' = F0'(table) + central differences of g (g mirrored at v = 0,
+ *     zero beyond the last node);
+ *  2. delta f^{n+1/2} = alpha delta f^{n-1/2} + 2 dt (e/m) F0' / (2 + dt nu) n E;
+ *  3. J from the new delta f;
+ *  4. g += dt (heating + collisions), both in flux form over the cell edges
+ *     v_{k+1/2} = (k+1) gamma with zero flux through v = 0 and v_max: heating
+ *     flux (v_k^3 F1_k + v_{k+1}^3 F1_{k+1}) / (2 v_{k+1/2}) of the time-centred
+ *     F1 = (delta f^{n-1/2} + delta f^{n+1/2}) / (2 n); collision flux
+ *     (m/M) v^3 nu (F0 + (k Tg/(m v)) dF0/dv) at the edge with edge averages of
+ *     F0 and nu and the one-cell difference of F0, from the F0 at n - 1/2.
+ * Rows are plain arrays of nn nodes; fold, old, hflux, cflux are scratch. */
+static void evolve_row(const or_params *p, double dt, const double *v, const double *f0, const double *f0p,
+                       const double *nu, const double *alpha, const double *w, double n, double E, double *row,
+                       double *g, double *old, double *hflux, double *cflux, double *J)
+{
+    const int64_t nn = p->nv;
+    const double gam = v[0] * 2.0;     /* nodes at (k + 1/2) gamma */
+    const double qm = OR_QE / OR_ME;
+    memcpy(old, row, sizeof(double) * nn);
+    for (int64_t k = 0; k < nn; ++k) {
+        const double gl = k > 0 ? g[k - 1] : g[0];
+        const double gr = k + 1 < nn ? g[k + 1] : 0.0;
+        const double d = f0p[k] + (gr - gl) / (2.0 * gam);
+        row[k] = alpha[k] * row[k] + 2.0 * dt * qm * d / (2.0 + dt * nu[k]) * n * E;
+    }
+    double j = 0.0;
+    for (int64_t k = 0; k < nn; ++k) j += w[k] * row[k];
+    *J = -OR_QE * j;
+    const double kTg_m = OR_QE * p->tg_ev / OR_ME;
+    for (int64_t k = 0; k + 1 < nn; ++k) {    /* edge k + 1/2 */
+        const double ve = (double)(k + 1) * gam;
+        const double a0 = v[k] * v[k] * v[k] * 0.5 * (old[k] + row[k]) / n;
+        const double a1 = v[k + 1] * v[k + 1] * v[k + 1] * 0.5 * (old[k + 1] + row[k + 1]) / n;
+        hflux[k] = 0.5 * (a0 + a1) / ve;
+        const double F0k = f0[k] + g[k], F0k1 = f0[k + 1] + g[k + 1];
+        const double nue = 0.5 * (nu[k] + nu[k + 1]);
+        cflux[k] = p->mass_ratio * ve * ve * ve * nue * (0.5 * (F0k + F0k1) + kTg_m / ve * (F0k1 - F0k) / gam);
+    }
+    for (int64_t k = 0; k < nn; ++k) {
+        const double hr = k + 1 < nn ? hflux[k] : 0.0, hl = k > 0 ? hflux[k - 1] : 0.0;
+        const double cr = k + 1 < nn ? cflux[k] : 0.0, cl = k > 0 ? cflux[k - 1] : 0.0;
+        const double v2g = v[k] * v[k] * gam;
+        g[k] += dt * ((qm * E / 3.0) * (hr - hl) / v2g + (cr - cl) / v2g);
+    }
+}
+
 static void kinetic_step(or_sim *s)
 {
     const int64_t nn = s->nnode;
@@ -490,6 +549,16 @@ static void kinetic_step(or_sim *s)
         const double E = Ep[c];
         const double nE = s->dens[q] * E;
         double *row = s->df + q * nn;
+        if (s->p.evolve_f0) {
+            double *scratch = (double *)malloc(sizeof(double) * 2 * nn);
+            double J;
+            evolve_row(&s->p, dt, s->v, s->f0, s->f0p, s->nu, s->alpha, s->w, s->dens[q], E, row, s->g0 + q * nn,
+                       old, scratch, scratch + nn, &J);
+            free(scratch);
+            s->jslot[q] = J;
+            s->jnode[c] = J;
+            continue;
+        }
         if (!s->p.nonlinear) {
             for (int64_t j = 0; j < nn; ++j) row[j] = s->alpha[j] * row[j] + s->beta[j] * nE;
         } else {
@@ -804,7 +873,7 @@ void or_diag(const or_sim *s, double *out)
  * with the same Sec. 5.2 update: returns J^{m+1/2} for every step and the
  * final delta f row.  Used to check the update against closed forms. */
 void or_kinetic_drive(const or_params *p, double dt, double density, const double *E, int64_t nsteps,
-                      double *J_out, double *df_out)
+                      double *J_out, double *df_out, double *g_out)
 {
     const int64_t nn = or_nnode_of(p);
     double *v = malloc(sizeof(double) * nn), *w = malloc(sizeof(double) * nn);
@@ -813,7 +882,14 @@ void or_kinetic_drive(const or_params *p, double dt, double density, const doubl
     double *al = malloc(sizeof(double) * nn), *be = malloc(sizeof(double) * nn);
     or_vtables(p, dt, v, w, f0, f0p, nu, dV, al, be);
     double *row = (double *)calloc((size_t)nn, sizeof(double));
+    double *g = (double *)calloc((size_t)nn, sizeof(double));
+    double *scratch = (double *)malloc(sizeof(double) * 3 * nn);
     for (int64_t m = 0; m < nsteps; ++m) {
+        if (p->evolve_f0) {
+            evolve_row(p, dt, v, f0, f0p, nu, al, w, density, E[m], row, g, scratch, scratch + nn, scratch + 2 * nn,
+                       &J_out[m]);
+            continue;
+        }
         double J = 0.0;
         for (int64_t j = 0; j < nn; ++j) {
             row[j] = al[j] * row[j] + be[j] * density * E[m];
@@ -822,7 +898,8 @@ void or_kinetic_drive(const or_params *p, double dt, double density, const doubl
         J_out[m] = -OR_QE * J;
     }
     if (df_out) memcpy(df_out, row, sizeof(double) * nn);
-    free(v); free(w); free(f0); free(f0p); free(nu); free(dV); free(al); free(be); free(row);
+    if (g_out) memcpy(g_out, g, sizeof(double) * nn);
+    free(v); free(w); free(f0); free(f0p); free(nu); free(dV); free(al); free(be); free(row); free(g); free(scratch);
 }
 
 /* ------------------------------------------------------------ Poynting flux */

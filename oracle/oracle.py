@@ -24,7 +24,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FIELDS = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7}
+FIELDS = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7, "f0": 8}
 VGRID = {"signed1d": 0, "cart2d": 1, "speed3d": 2}
 SRC = {"none": 0, "gauss_sine": 1, "gauss": 2}
 NU = {"nsv": 0, "const": 1, "table": 2}
@@ -64,6 +64,7 @@ class Params(ctypes.Structure):
         ("nu_model", ctypes.c_int64), ("nonlinear", ctypes.c_int64),
         ("f0_model", ctypes.c_int64), ("s_n", ctypes.c_int64),
         ("s_speed", ctypes.POINTER(ctypes.c_double)), ("s_sigma", ctypes.POINTER(ctypes.c_double)),
+        ("evolve_f0", ctypes.c_int64), ("mass_ratio", ctypes.c_double), ("tg_ev", ctypes.c_double),
     ]
 
 
@@ -100,7 +101,7 @@ def _load():
         lib.or_cpml_profile.argtypes = [P, ctypes.c_double, ctypes.c_int64, ctypes.c_int, dp, dp, dp]
         lib.or_source.restype = ctypes.c_double
         lib.or_source.argtypes = [P, ctypes.c_double]
-        lib.or_kinetic_drive.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64, dp, dp]
+        lib.or_kinetic_drive.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64, dp, dp, dp]
         lib.or_poynting.argtypes = [vp, ip, dp]
         _lib = lib
         return lib
@@ -117,7 +118,7 @@ DEFAULTS = dict(
     mur=0, src_kind=0, src_amp=1.0, src_fc=0.0, src_tau=1.0, src_t0=0.0,
     src_i=0, src_j=0, src_k=0, src_sheet=0, sheet_i0=0, sheet_i1=0, sheet_j0=0, sheet_j1=0,
     vgrid=0, nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0, nu_model=0, nonlinear=0,
-    f0_model=0, s_table=None,
+    f0_model=0, s_table=None, evolve_f0=0, mass_ratio=0.0, tg_ev=0.0,
 )
 
 
@@ -137,6 +138,8 @@ def params(**kw) -> Params:
         if k == "f0_model" and isinstance(v, str):
             v = F0[v]
         d[k] = v
+    if d["evolve_f0"] and d["vgrid"] != 2:
+        raise ValueError("evolve_f0 needs the speed grid (vgrid 'speed3d')")
     p = Params()
     table = d.pop("s_table")
     for k, v in d.items():
@@ -197,7 +200,7 @@ class Sim:
     def _len(self, which: int) -> int:
         if which == 6:
             return self.nslots
-        if which == 7:
+        if which in (7, 8):
             return self.nslots * self.nnode
         return self._lib.or_field_len(self._h, which)
 
@@ -208,7 +211,7 @@ class Sim:
         if n and self._lib.or_get(self._h, w, _dp(out)) != 0:
             raise ValueError(name)
         out = out[:n]
-        return out.reshape(self.nslots, self.nnode) if name == "df" else out
+        return out.reshape(self.nslots, self.nnode) if name in ("df", "f0") else out
 
     def set(self, name: str, arr: np.ndarray):
         w = FIELDS[name]
@@ -254,15 +257,17 @@ def source(p: Params, t: float) -> float:
     return _load().or_source(ctypes.byref(p), float(t))
 
 
-def kinetic_drive(p: Params, dt: float, density: float, E: np.ndarray):
-    """0-D plasma cell driven by E^m; returns (J^{m+1/2} series, final delta f row)."""
+def kinetic_drive(p: Params, dt: float, density: float, E: np.ndarray, with_f0: bool = False):
+    """0-D plasma cell driven by E^m; returns (J^{m+1/2} series, final delta f
+    row), and the final F0 correction row when with_f0."""
     lib = _load()
     E = np.ascontiguousarray(E, dtype=np.float64)
     n = lib.or_nnode_of(ctypes.byref(p))
     J = np.zeros(E.size)
     df = np.zeros(n)
-    lib.or_kinetic_drive(ctypes.byref(p), dt, density, _dp(E), E.size, _dp(J), _dp(df))
-    return J, df
+    g = np.zeros(n)
+    lib.or_kinetic_drive(ctypes.byref(p), dt, density, _dp(E), E.size, _dp(J), _dp(df), _dp(g))
+    return (J, df, g) if with_f0 else (J, df)
 
 
 def port_spectra(sims, ports, freqs, steps: int) -> list:

@@ -26,7 +26,9 @@ def oracle_params(O, spec):
     if p is not None:
         kw.update(vgrid=p["vgrid"], nv=p["nv"], nv_perp=p.get("nv_perp", 1), te_ev=p.get("te_ev", 1.0),
                   vmax_vth=p.get("vmax_vth", 6.0), nu0=p.get("nu0", 0.0), nu_model=p.get("nu_model", "nsv"),
-                  nonlinear=p.get("nonlinear", 0))
+                  nonlinear=p.get("nonlinear", 0), f0_model=p.get("f0_model", "maxwell"),
+                  s_table=p.get("s_table"), evolve_f0=p.get("evolve_f0", 0), mass_ratio=p.get("mass_ratio", 0.0),
+                  tg_ev=p.get("tg_ev", 0.0))
     return O.params(**kw)
 
 
