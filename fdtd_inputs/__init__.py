@@ -19,9 +19,9 @@ the tests' oracle adapter):
 from .workloads import (C0, LAM0, F0, OMEGA0, QE, ME, EPS0, critical_density, pulse_params,
                         cylinder_density, gaussian_random_field, spec_1d_slab, spec_2d_cylinder,
                         spec_3d_slab, random_state, batch_runs_1d, spec_closure_8192, closure_training_specs,
-                        WORKLOADS)
+                        cross_section_table, WORKLOADS)
 
 __all__ = ["C0", "LAM0", "F0", "OMEGA0", "QE", "ME", "EPS0", "critical_density", "pulse_params",
            "cylinder_density", "gaussian_random_field", "spec_1d_slab", "spec_2d_cylinder", "spec_3d_slab",
            "random_state", "batch_runs_1d", "spec_closure_8192",
-           "closure_training_specs", "WORKLOADS"]
+           "closure_training_specs", "cross_section_table", "WORKLOADS"]

@@ -75,6 +75,21 @@ def random_state(sizes: dict, seed: int, e_scale: float = 1.0) -> dict:
             for k, n in sizes.items()}
 
 
+def cross_section_table(te_ev: float = 1.0, n: int = 24, vmax_vth: float = 8.0, seed: int = 7):
+    """Synthetic elastic cross-section s(v) for the tabulated collision law: a
+    smooth positive curve with a deep minimum near 0.6 v_th (the shape of a
+    Ramsauer-Townsend minimum) rising to a broad maximum, sampled at n
+    ascending speeds from 0 to vmax_vth v_th, with seeded +-5 % jitter of the
+    sample values.  Returns (speeds in m/s, s in arbitrary units): only the
+    shape enters nu = N s(v) v, whose mean is fixed separately."""
+    rng = np.random.default_rng(seed)
+    vth = np.sqrt(QE * te_ev / ME)
+    u = np.linspace(0.0, vmax_vth, n)
+    s = 0.05 + (u - 0.6) ** 2 * np.exp(-u / 2.5)
+    s *= 1.0 + 0.05 * rng.uniform(-1.0, 1.0, n)
+    return u * vth, s
+
+
 def spec_1d_slab(nz=2000, ppw=40, slab=(1000, 1500), wp_w0=0.5, nu_w0=0.01, nv=64, src_k=100, steps=2000,
                  precision="f64", f_dtype=None, te_ev=1.0, nu_model="nsv", seed=1) -> dict:
     """1-D FDTD + kinetic: uniform slab on E nodes slab[0]..slab[1]-1, Mur ends,

@@ -55,7 +55,8 @@ typedef enum {
 enum { FDTD_F32 = 0, FDTD_F64 = 1 };                      /* field / accumulation precision */
 enum { FDTD_DF_F32 = 0, FDTD_DF_BF16 = 1, FDTD_DF_F64 = 2 }; /* storage of delta f */
 enum { FDTD_VGRID_SIGNED1D = 0, FDTD_VGRID_CART2D = 1, FDTD_VGRID_SPEED3D = 2 };
-enum { FDTD_NU_NSV = 0, FDTD_NU_CONST = 1 };
+enum { FDTD_NU_NSV = 0, FDTD_NU_CONST = 1, FDTD_NU_TABLE = 2 };
+enum { FDTD_F0_MAXWELL = 0, FDTD_F0_DRUYVESTEYN = 1 };
 enum { FDTD_SRC_NONE = 0, FDTD_SRC_GAUSS_SINE = 1, FDTD_SRC_GAUSS = 2 };
 enum { FDTD_LOC_POINT = 0, FDTD_LOC_SHEET = 1 };
 enum {                                                      /* fdtd_plasma_read_fields "which" */
@@ -104,11 +105,22 @@ typedef struct {
 } fdtd_source_desc;
 
 /* Kinetic plasma (Sec. 5.2).  density: one double per polarisation node
- * (the field's own length), host or device, copied.  F0 is a Maxwellian of
- * temperature te_ev on a velocity grid of nv (x nv_perp) midpoint nodes over
- * [-vmax_vth v_th, +vmax_vth v_th] (speed grid: [0, vmax_vth v_th]).
+ * (the field's own length), host or device, copied.  The velocity grid has nv
+ * (x nv_perp) midpoint nodes over [-vmax_vth v_th, +vmax_vth v_th] (speed
+ * grid: [0, vmax_vth v_th]), v_th = sqrt(e te_ev / m).
+ * F0 (isotropic, fixed): f0_model MAXWELL, of temperature te_ev; DRUYVESTEYN,
+ * A exp(-(eps/eps0)^2) with eps = m v^2/2 and mean energy 3/2 e te_ev
+ * (eps0 = 3/2 e te_ev Gamma(3/4)/Gamma(5/4)).  The signed grid carries the
+ * 1-D marginal of F0 and the Cartesian grid the 2-D marginal (for the
+ * Druyvesteyn F0 by quadrature over the third component), with their v_par
+ * derivatives.
  * Collisions (Eq. 23): NSV: nu_j = N s |v_j| with N s set so that the grid's
- * F0-weighted mean of nu is nu0; CONST: nu_j = nu0.
+ * F0-weighted mean of nu is nu0; CONST: nu_j = nu0; TABLE: nu_j = N s(|v_j|)
+ * |v_j|, N set the same way, s(v) linear between the s_n >= 2 points of the
+ * table (s_speed strictly ascending, m/s; s_sigma >= 0, any unit: only its
+ * shape matters) and held at the end values outside it.  The table is host
+ * memory, read during set_plasma only.  |v_j| is |v_par| on the signed grid,
+ * sqrt(v_par^2 + v_perp^2) on the Cartesian grid, the speed on the speed grid.
  * f_dtype: FDTD_DF_F32, FDTD_DF_BF16 (FP32 arithmetic, stochastic rounding on
  * store, keyed by seed) or FDTD_DF_F64 (only with FDTD_F64 precision).
  * nonlinear: 1 adds the flux-form advection of delta f in v_par (signed and
@@ -122,8 +134,11 @@ typedef struct {
     int32_t nu_model;
     int32_t f_dtype;
     int32_t nonlinear;
-    int32_t reserved;
+    int32_t f0_model;
     uint64_t seed;
+    const double *s_speed;     /* FDTD_NU_TABLE only (else ignored) */
+    const double *s_sigma;
+    int64_t s_n;
 } fdtd_plasma_desc;
 
 /* FP64 diagnostics (computed on the device with FP64 accumulators). */
@@ -181,8 +196,15 @@ typedef struct {
     int32_t kin_vpl, kin_l, kin_blocks_per_sm;   /* 0 = no kinetic kernel tuned */
     int32_t block_x, block_y, block_z;           /* 0 = no stencil tuned (1-D) */
     double kin_ms, stencil_ms;                   /* best per-launch times */
+    int32_t cells_per_thread;                    /* stencils: 1, or 4 (FP32 rows of a multiple of 4 cells;
+                                                    block_x then counts groups of 4 cells) */
+    int32_t reserved;
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
+
+/* The launch shapes the handle uses now (tuned, cached or default; kinetic
+ * fields 0 = the built-in choice); times are 0. */
+int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out);
 
 /* Zero every field, psi, delta f and J and the step counter (keeps the
  * configuration). */
@@ -209,6 +231,27 @@ int fdtd_plasma_info(fdtd_plasma_t h, double *dt, int64_t *steps_done);
 
 /* Compute FP64 diagnostics of the current state (synchronises the stream). */
 int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out);
+
+/* Running-DFT ports (Sec. 5.3: the slab's S-parameters S11, S21 come from the
+ * spectra of the field at two ports).  Port p is the set of polarisation-field
+ * nodes cells[port_offsets[p] .. port_offsets[p+1]) (indices into Ex in 1-D
+ * and 3-D, Ez in 2-D, x fastest; port_offsets[0] = 0, every port non-empty).
+ * After every step, the port's field E^{n+1} averaged over its nodes is
+ * accumulated in FP64 as X[p][f] += E_p(t) exp(-i 2 pi freqs[f] t) dt with
+ * t = (n+1) dt.  All arrays are host memory, copied; the call synchronises.
+ * set_ports zeroes the sums (as does fdtd_plasma_reset); nports = 0 removes
+ * the ports.  The sums are not part of the checkpoint state.
+ * S11 = (X_plasma[in] - X_vacuum[in]) / X_vacuum[in] and
+ * S21 = X_plasma[out] / X_vacuum[out] with a vacuum run of the same source.
+ * Errors: FDTD_ERR_INVAL for counts outside 1..4096 ports / 1..2^20
+ * frequencies, NULL arrays, empty ports, nodes outside the field or
+ * non-finite frequencies. */
+int fdtd_plasma_set_ports(fdtd_plasma_t h, int32_t nports, const int64_t *port_offsets, const int64_t *cells,
+                          int32_t nfreq, const double *freqs);
+
+/* Copy the port sums out: out (host) holds nports x nfreq x {re, im} doubles,
+ * bytes must be exactly that size; synchronises.  FDTD_ERR_STATE without ports. */
+int fdtd_plasma_read_ports(fdtd_plasma_t h, double *out, size_t bytes);
 
 /* Electromagnetic power out of an axis-aligned box at the current step (the
  * Poynting vector S = E x H of the field equations of Sec. 2, Eq. 1-2),

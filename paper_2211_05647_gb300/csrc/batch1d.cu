@@ -211,8 +211,6 @@ using namespace fp;
 
 namespace {
 
-constexpr double kC0 = 299792458.0, kQe = 1.602176634e-19, kMe = 9.1093837015e-31, kEps0 = 8.8541878128e-12;
-constexpr double kPi = 3.14159265358979323846;
 thread_local std::string g_batch_create_error;
 
 }  // namespace
@@ -370,8 +368,15 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
         if (g.nz < 3 || g.nz > (1 << 30)) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nz out of range", r);
         if (g.cpml_cells) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: 1-D runs use Mur or PEC ends", r);
         if (p.vgrid != p0.vgrid || p.nv != p0.nv || p.nv_perp != p0.nv_perp || p.te_ev != p0.te_ev ||
-            p.vmax_vth != p0.vmax_vth || p.nu_model != p0.nu_model || p.f_dtype != p0.f_dtype)
-            return bfail(nullptr, FDTD_ERR_INVAL, "run %d: velocity grid, te, nu model and f_dtype must match run 0", r);
+            p.vmax_vth != p0.vmax_vth || p.nu_model != p0.nu_model || p.f_dtype != p0.f_dtype ||
+            p.f0_model != p0.f0_model)
+            return bfail(nullptr, FDTD_ERR_INVAL,
+                         "run %d: velocity grid, te, F0 and nu models and f_dtype must match run 0", r);
+        if (const char *why = check_velocity_model(p)) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: %s", r, why);
+        if (p.nu_model == FDTD_NU_TABLE &&
+            (p.s_n != p0.s_n || !std::equal(p.s_speed, p.s_speed + p.s_n, p0.s_speed) ||
+             !std::equal(p.s_sigma, p.s_sigma + p.s_n, p0.s_sigma)))
+            return bfail(nullptr, FDTD_ERR_INVAL, "run %d: the s(v) table must match run 0", r);
         if (p.nonlinear) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nonlinear mode not available in batches", r);
         if (!(p.nu0 >= 0) || !std::isfinite(p.nu0)) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nu0", r);
         const fdtd_source_desc &s = runs[r].source;
@@ -416,33 +421,9 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
     if (maxc < 1) return bail(FDTD_ERR_CUDA, "no cluster of the batched kernel fits on this device");
 
     // ---- velocity tables (shared node weights; per-run alpha, beta from nu0_r)
-    const double vth = std::sqrt(kQe * p0.te_ev / kMe), vmax = p0.vmax_vth * vth, two_vth2 = 2 * vth * vth;
-    std::vector<double> w(nnode), f0p(nnode), f0(nnode), dV(nnode), speed(nnode);
-    for (int j = 0; j < nnode; ++j) {
-        double va, g, ww, dvv, sp;
-        if (p0.vgrid == FDTD_VGRID_SIGNED1D) {
-            const double dv = 2 * vmax / p0.nv;
-            va = ((double)j + 0.5 - 0.5 * p0.nv) * dv;
-            g = std::exp(-va * va / two_vth2) / std::sqrt(kPi * two_vth2);
-            ww = va * dv; dvv = dv; sp = std::fabs(va);
-        } else if (p0.vgrid == FDTD_VGRID_CART2D) {
-            const int a = j / p0.nv_perp, c = j % p0.nv_perp;
-            const double dvp = 2 * vmax / p0.nv, dvq = 2 * vmax / p0.nv_perp;
-            va = ((double)a + 0.5 - 0.5 * p0.nv) * dvp;
-            const double vb = ((double)c + 0.5 - 0.5 * p0.nv_perp) * dvq;
-            g = std::exp(-(va * va + vb * vb) / two_vth2) / (kPi * two_vth2);
-            ww = va * dvp * dvq; dvv = dvp * dvq; sp = std::sqrt(va * va + vb * vb);
-        } else {
-            const double gam = vmax / p0.nv;
-            va = ((double)j + 0.5) * gam;
-            g = std::exp(-va * va / two_vth2) / std::pow(kPi * two_vth2, 1.5);
-            ww = 4 * kPi / 3 * va * va * va * gam; dvv = 4 * kPi * va * va * gam; sp = va;
-        }
-        f0[j] = g; f0p[j] = -va / (vth * vth) * g; w[j] = ww; dV[j] = dvv; speed[j] = sp;
-    }
-    double num = 0, den = 0;
-    for (int j = 0; j < nnode; ++j) { num += speed[j] * f0[j] * dV[j]; den += f0[j] * dV[j]; }
-    const double mean_speed = num / den;
+    VTab vt;
+    if (!velocity_tables(p0, vt)) return bail(FDTD_ERR_INVAL, "bad velocity grid");
+    const std::vector<double> &w = vt.w, &f0p = vt.f0p;
     const int P = b->pitch;
     std::vector<double> tab((size_t)P * (1 + 2 * (size_t)nruns), 0.0);
     for (int j = 0; j < nnode; ++j) tab[j] = -kQe * w[j];
@@ -481,7 +462,7 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
         b->nslot[r] = ns;
         const double nu0 = p.nu0;
         for (int j = 0; j < nnode; ++j) {
-            const double nu = p.nu_model == FDTD_NU_CONST ? nu0 : nu0 * speed[j] / mean_speed;
+            const double nu = node_nu(p, vt, (size_t)j, nu0);
             tab[(size_t)P * (1 + 2 * r) + j] = (2 - b->dt * nu) / (2 + b->dt * nu);
             tab[(size_t)P * (2 + 2 * r) + j] = 2 * b->dt * (kQe / kMe) * f0p[j] / (2 + b->dt * nu);
         }

@@ -24,11 +24,6 @@ using namespace fp;
 
 namespace {
 
-constexpr double kC0 = 299792458.0;
-constexpr double kQe = 1.602176634e-19;
-constexpr double kMe = 9.1093837015e-31;
-constexpr double kEps0 = 8.8541878128e-12;
-constexpr double kPi = 3.14159265358979323846;
 constexpr int kChunk = 32;            // steps per replay of the chunk graph
 constexpr uint64_t kStateMagic = 0x4644544450534d31ull;
 
@@ -63,6 +58,11 @@ void *dalloc(fdtd_plasma *h, size_t bytes)
     void *p = nullptr;
     if (h->rt.alloc) {
         p = h->rt.alloc(bytes, h->rt.alloc_ctx);
+        if (p && (reinterpret_cast<uintptr_t>(p) & 255u)) {   // the 16-byte vector stencils rely on it
+            h->err = "the allocator callback returned memory that is not 256-byte aligned";
+            if (h->rt.free) h->rt.free(p, h->rt.alloc_ctx);
+            p = nullptr;
+        }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
@@ -110,63 +110,6 @@ void cpml_axis(const fdtd_grid_desc &g, double dt, int64_t n, bool at_h, std::ve
         a[i] = (sig > 0.0 && den > 0.0) ? sig * (bb - 1.0) / den : 0.0;
         ik[i] = 1.0 / kap;
     }
-}
-
-// --------------------------------------------------------- velocity tables
-
-struct VTab {
-    std::vector<double> v, w, f0, f0p, nu, dV, speed;
-};
-
-// Node tables of the kinetic update (Sec. 5.2): quadrature weight w of the
-// current moment (Eq. 24), Maxwellian F0 and its v_par derivative (def_f_0),
-// collision frequency (Eq. 23) and volume element.
-bool velocity_tables(const fdtd_plasma_desc &p, VTab &t)
-{
-    const double vth = std::sqrt(kQe * p.te_ev / kMe);
-    const double vmax = p.vmax_vth * vth;
-    const double two_vth2 = 2.0 * vth * vth;
-    if (p.vgrid == FDTD_VGRID_SIGNED1D) {
-        const double dv = 2.0 * vmax / p.nv;
-        for (int a = 0; a < p.nv; ++a) {
-            const double va = ((double)a + 0.5 - 0.5 * p.nv) * dv;
-            const double g = std::exp(-va * va / two_vth2) / std::sqrt(kPi * two_vth2);
-            t.v.push_back(va); t.f0.push_back(g); t.f0p.push_back(-va / (vth * vth) * g);
-            t.w.push_back(va * dv); t.dV.push_back(dv); t.speed.push_back(std::fabs(va));
-        }
-    } else if (p.vgrid == FDTD_VGRID_CART2D) {
-        const double dvp = 2.0 * vmax / p.nv, dvq = 2.0 * vmax / p.nv_perp;
-        for (int a = 0; a < p.nv; ++a) {
-            const double va = ((double)a + 0.5 - 0.5 * p.nv) * dvp;
-            for (int b = 0; b < p.nv_perp; ++b) {
-                const double vb = ((double)b + 0.5 - 0.5 * p.nv_perp) * dvq;
-                const double g = std::exp(-(va * va + vb * vb) / two_vth2) / (kPi * two_vth2);
-                t.v.push_back(va); t.f0.push_back(g); t.f0p.push_back(-va / (vth * vth) * g);
-                t.w.push_back(va * dvp * dvq); t.dV.push_back(dvp * dvq);
-                t.speed.push_back(std::sqrt(va * va + vb * vb));
-            }
-        }
-    } else if (p.vgrid == FDTD_VGRID_SPEED3D) {
-        const double gam = vmax / p.nv;
-        for (int k = 0; k < p.nv; ++k) {
-            const double vk = ((double)k + 0.5) * gam;
-            const double g = std::exp(-vk * vk / two_vth2) / std::pow(kPi * two_vth2, 1.5);
-            t.v.push_back(vk); t.f0.push_back(g); t.f0p.push_back(-vk / (vth * vth) * g);
-            t.w.push_back(4.0 * kPi / 3.0 * vk * vk * vk * gam); t.dV.push_back(4.0 * kPi * vk * vk * gam);
-            t.speed.push_back(vk);
-        }
-    } else {
-        return false;
-    }
-    double num = 0.0, den = 0.0;
-    for (size_t j = 0; j < t.v.size(); ++j) {
-        num += t.speed[j] * t.f0[j] * t.dV[j];
-        den += t.f0[j] * t.dV[j];
-    }
-    const double mean = num / den;
-    for (size_t j = 0; j < t.v.size(); ++j)
-        t.nu.push_back(p.nu_model == FDTD_NU_CONST ? p.nu0 : p.nu0 * t.speed[j] / mean);
-    return true;
 }
 
 // ------------------------------------------------------------------ misc
@@ -254,6 +197,15 @@ dim3 stencil_block(const fdtd_plasma *h)
     return h->g.ndim == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1);
 }
 
+// cells per thread of the curl stencils: tuned, else 4 in 2-D (measured
+// faster on GB300) and 1 in 3-D (the four-cell 3-D kernels need 80 registers
+// and lose more to the lower occupancy than they save in instructions)
+int stencil_cpt(const fdtd_plasma *h)
+{
+    if (h->st_cpt > 0) return h->st_cpt;
+    return h->g.ndim == 2 ? 4 : 1;
+}
+
 template <typename T>
 KinArgs<T> kin_args(fdtd_plasma *h, int kstep)
 {
@@ -315,7 +267,8 @@ std::string stencil_key(const fdtd_plasma *h)
 {
     std::ostringstream o;
     o << gpu_key() << "|stencil" << h->g.ndim << "d|prec" << h->g.precision << "|cells2^"
-      << log2_bucket(h->nx * h->ny * h->nz) << "|cpml" << (h->g.cpml_cells > 0);
+      << log2_bucket(h->nx * h->ny * h->nz) << "|cpml" << (h->g.cpml_cells > 0) << "|rows4="
+      << (h->g.precision == FDTD_F32 && h->nx % 4 == 0);
     return o.str();
 }
 
@@ -331,7 +284,7 @@ std::map<std::string, std::vector<int>> read_cache()
         int x;
         if (!(in >> k)) continue;
         while (in >> x) v.push_back(x);
-        if (v.size() == 3) m[k] = v;
+        if (v.size() == 3 || v.size() == 4) m[k] = v;
     }
     return m;
 }
@@ -346,7 +299,11 @@ void write_cache(const std::map<std::string, std::vector<int>> &m)
             if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
     }
     std::ofstream f(path, std::ios::trunc);
-    for (const auto &kv : m) f << kv.first << " " << kv.second[0] << " " << kv.second[1] << " " << kv.second[2] << "\n";
+    for (const auto &kv : m) {
+        f << kv.first;
+        for (int x : kv.second) f << " " << x;
+        f << "\n";
+    }
 }
 
 void apply_cached_kinetic(fdtd_plasma *h)
@@ -360,7 +317,9 @@ void apply_cached_stencil(fdtd_plasma *h)
 {
     auto m = read_cache();
     auto it = m.find(stencil_key(h));
-    if (it != m.end()) { h->st_bx = it->second[0]; h->st_by = it->second[1]; h->st_bz = it->second[2]; }
+    if (it != m.end() && it->second.size() == 4) {
+        h->st_bx = it->second[0]; h->st_by = it->second[1]; h->st_bz = it->second[2]; h->st_cpt = it->second[3];
+    }
 }
 
 // enqueue one step n -> n+1 (kstep = offset of this step inside the chunk);
@@ -382,9 +341,9 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
                       kstep);
     else if (h->g.ndim == 2)
         launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, kstep,
-                      stencil_block(h));
+                      stencil_block(h), stencil_cpt(h));
     else
-        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep, stencil_block(h));
+        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep, stencil_block(h), stencil_cpt(h));
     if (ev) cudaEventRecord(ev[1], st);
     const bool rec = h->has_recording && sizeof(T) == 4;
     if (rec)
@@ -440,11 +399,16 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         }
     } else if (h->g.ndim == 2) {
         launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, kstep,
-                      stencil_block(h));
+                      stencil_block(h), stencil_cpt(h));
     } else {
-        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep, stencil_block(h));
+        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep, stencil_block(h), stencil_cpt(h));
     }
     if (ev) cudaEventRecord(ev[4], st);
+    if (h->nports > 0) {
+        cudaError_t e = launch_ports<T>(st, f[pol_comp(h)], h->nports, h->port_off, h->port_cells, h->port_freq,
+                                        h->port_acc, h->nfreq, h->dt, h->d_step, kstep);
+        if (e != cudaSuccess) return e;
+    }
     return cudaGetLastError();
 }
 
@@ -539,7 +503,7 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     }
     int rc = FDTD_OK;
     auto bail = [&](int code, const char *what) {
-        g_create_error = what;
+        g_create_error = h->err.empty() ? std::string(what) : std::string(what) + ": " + h->err;
         fdtd_plasma_destroy(h);
         return code;
     };
@@ -618,6 +582,21 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     return FDTD_OK;
 }
 
+int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out)
+{
+    if (!h || !out) return FDTD_ERR_INVAL;
+    *out = fdtd_tune_result{};
+    out->kin_vpl = h->kin_vpl;
+    out->kin_l = h->kin_l;
+    out->kin_blocks_per_sm = h->kin_bps;
+    if (h->g.ndim >= 2) {
+        const dim3 b = stencil_block(h);
+        out->block_x = (int32_t)b.x; out->block_y = (int32_t)b.y; out->block_z = (int32_t)b.z;
+        out->cells_per_thread = stencil_cpt(h);
+    }
+    return FDTD_OK;
+}
+
 int fdtd_plasma_reset(fdtd_plasma_t h)
 {
     if (!h) return FDTD_ERR_INVAL;
@@ -631,6 +610,7 @@ int fdtd_plasma_reset(fdtd_plasma_t h)
     }
     if (h->hist) CK(h, cudaMemsetAsync(h->hist, 0, (size_t)(h->has_closure ? h->ncl : h->nslots) * 16 * 4, h->stream));
     if (h->jprev) CK(h, cudaMemsetAsync(h->jprev, 0, (size_t)(h->has_closure ? h->ncl : h->nslots) * 4, h->stream));
+    if (h->port_acc) CK(h, cudaMemsetAsync(h->port_acc, 0, (size_t)h->nports * h->nfreq * 2 * sizeof(double), h->stream));
     CK(h, cudaMemsetAsync(h->mur_state, 0, 32, h->stream));
     CK(h, cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
@@ -680,7 +660,7 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
         return fail(h, FDTD_ERR_INVAL, "nv too small");
     if (!(p->te_ev > 0) || !(p->vmax_vth > 0) || !(p->nu0 >= 0) || !std::isfinite(p->nu0))
         return fail(h, FDTD_ERR_INVAL, "te_ev, vmax_vth must be > 0 and nu0 >= 0");
-    if (p->nu_model != FDTD_NU_NSV && p->nu_model != FDTD_NU_CONST) return fail(h, FDTD_ERR_INVAL, "bad nu_model");
+    if (const char *why = check_velocity_model(*p)) return fail(h, FDTD_ERR_INVAL, "%s", why);
     const bool f64 = h->g.precision == FDTD_F64;
     if (f64 ? p->f_dtype != FDTD_DF_F64 : (p->f_dtype != FDTD_DF_F32 && p->f_dtype != FDTD_DF_BF16))
         return fail(h, FDTD_ERR_INVAL, "f_dtype does not match the field precision");
@@ -730,6 +710,8 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     const size_t ns = cells.size();
     h->pl = *p;
     h->pl.density = nullptr;
+    h->pl.s_speed = h->pl.s_sigma = nullptr;   // caller memory, read above only
+    h->pl.s_n = 0;
     h->nslots = (int64_t)ns;
     h->nnode = nnode;
     h->pitch = pitch;
@@ -914,33 +896,39 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
         return ms / 5.0;
     };
     auto m = read_cache();
-    out->block_x = out->block_y = out->block_z = 0;
+    out->block_x = out->block_y = out->block_z = out->cells_per_thread = 0;
     out->stencil_ms = 0;
     if (h->g.ndim >= 2) {
         static const int s2[][3] = {{32, 8, 1}, {64, 4, 1}, {128, 2, 1}, {256, 1, 1}, {32, 4, 1}, {64, 2, 1}};
         static const int s3[][3] = {{32, 4, 2}, {32, 8, 1}, {32, 2, 4}, {64, 4, 1}, {64, 2, 2}, {128, 2, 1}, {32, 4, 1}};
         const int n = h->g.ndim == 2 ? 6 : 7;
+        const bool quads = h->g.precision == FDTD_F32 && h->nx % 4 == 0;
         double best = 1e30;
-        for (int c = 0; c < n; ++c) {
-            const int *sh = h->g.ndim == 2 ? s2[c] : s3[c];
-            const dim3 b(sh[0], sh[1], sh[2]);
-            const double ms = time_ms([&] {
-                if (h->g.ndim == 2) {
-                    launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, 0, b);
-                    launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, 0, b);
-                } else {
-                    launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, 0, b);
-                    launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, 0, b);
+        for (int cpt : {1, 4}) {
+            if (cpt == 4 && !quads) continue;
+            for (int c = 0; c < n; ++c) {
+                const int *sh = h->g.ndim == 2 ? s2[c] : s3[c];
+                const dim3 b(sh[0], sh[1], sh[2]);
+                const double ms = time_ms([&] {
+                    if (h->g.ndim == 2) {
+                        launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step,
+                                      0, b, cpt);
+                        launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step,
+                                      0, b, cpt);
+                    } else {
+                        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, 0, b, cpt);
+                        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, 0, b, cpt);
+                    }
+                });
+                if (ms < best) {
+                    best = ms;
+                    out->block_x = sh[0]; out->block_y = sh[1]; out->block_z = sh[2]; out->cells_per_thread = cpt;
                 }
-            });
-            if (ms < best) {
-                best = ms;
-                out->block_x = sh[0]; out->block_y = sh[1]; out->block_z = sh[2];
             }
         }
-        h->st_bx = out->block_x; h->st_by = out->block_y; h->st_bz = out->block_z;
+        h->st_bx = out->block_x; h->st_by = out->block_y; h->st_bz = out->block_z; h->st_cpt = out->cells_per_thread;
         out->stencil_ms = best;
-        m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z};
+        m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z, out->cells_per_thread};
     }
     out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = 0;
     out->kin_ms = 0;
@@ -1122,6 +1110,69 @@ int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
     return FDTD_OK;
 }
 
+void free_ports(fdtd_plasma *h)
+{
+    dfree(h, h->port_off); dfree(h, h->port_cells); dfree(h, h->port_freq); dfree(h, h->port_acc);
+    h->port_off = h->port_cells = nullptr;
+    h->port_freq = h->port_acc = nullptr;
+    h->nports = h->nfreq = 0;
+}
+
+int fdtd_plasma_set_ports(fdtd_plasma_t h, int32_t nports, const int64_t *port_offsets, const int64_t *cells,
+                          int32_t nfreq, const double *freqs)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (nports == 0) {
+        drop_graphs(h);
+        free_ports(h);
+        return FDTD_OK;
+    }
+    if (nports < 0 || nports > 4096 || nfreq < 1 || nfreq > (1 << 20) || !port_offsets || !cells || !freqs)
+        return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_set_ports: bad counts or NULL array");
+    if (port_offsets[0] != 0) return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_set_ports: port_offsets[0] must be 0");
+    const int64_t np = pol_len(h);
+    for (int p = 0; p < nports; ++p)
+        if (!(port_offsets[p + 1] > port_offsets[p]))
+            return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_set_ports: port %d has no nodes", p);
+    const int64_t ncell = port_offsets[nports];
+    for (int64_t q = 0; q < ncell; ++q)
+        if (cells[q] < 0 || cells[q] >= np)
+            return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_set_ports: node %lld outside the polarisation field",
+                        (long long)cells[q]);
+    for (int f = 0; f < nfreq; ++f)
+        if (!std::isfinite(freqs[f])) return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_set_ports: non-finite frequency");
+    drop_graphs(h);
+    free_ports(h);
+    h->port_off = (int64_t *)dalloc(h, (nports + 1) * sizeof(int64_t));
+    h->port_cells = (int64_t *)dalloc(h, ncell * sizeof(int64_t));
+    h->port_freq = (double *)dalloc(h, nfreq * sizeof(double));
+    h->port_acc = (double *)dalloc(h, (size_t)nports * nfreq * 2 * sizeof(double));
+    if (!h->port_off || !h->port_cells || !h->port_freq || !h->port_acc) {
+        free_ports(h);
+        return fail(h, FDTD_ERR_NOMEM, "fdtd_plasma_set_ports: allocation failed");
+    }
+    CK(h, cudaMemcpyAsync(h->port_off, port_offsets, (nports + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaMemcpyAsync(h->port_cells, cells, ncell * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->port_freq, freqs, nfreq * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemsetAsync(h->port_acc, 0, (size_t)nports * nfreq * 2 * sizeof(double), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));   // the host arrays may go away after return
+    h->nports = nports;
+    h->nfreq = nfreq;
+    return FDTD_OK;
+}
+
+int fdtd_plasma_read_ports(fdtd_plasma_t h, double *out, size_t bytes)
+{
+    if (!h || !out) return FDTD_ERR_INVAL;
+    const size_t need = (size_t)h->nports * h->nfreq * 2 * sizeof(double);
+    if (h->nports == 0) return fail(h, FDTD_ERR_STATE, "fdtd_plasma_read_ports: no ports set");
+    if (bytes != need) return fail(h, FDTD_ERR_INVAL, "fdtd_plasma_read_ports: need %zu bytes", need);
+    CK(h, cudaMemcpyAsync(out, h->port_acc, need, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+
 int fdtd_plasma_poynting(fdtd_plasma_t h, const int64_t *box, double *out)
 {
     if (!h || !box || !out) return FDTD_ERR_INVAL;
@@ -1257,6 +1308,7 @@ void fdtd_plasma_destroy(fdtd_plasma_t h)
     dfree(h, h->d_step);
     dfree(h, h->d_src);
     dfree(h, h->d_err);
+    free_ports(h);
     dfree(h, h->diag_partials);
     dfree(h, h->diag_out);
     if (h->cap) cudaStreamDestroy(h->cap);

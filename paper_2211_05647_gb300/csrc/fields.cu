@@ -10,6 +10,8 @@
 // stored node read as 0 (PEC ghosts).  The plasma current has already been
 // subtracted from E in place by the kinetic kernel, so the E kernels only add
 // the curl.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace fp {
@@ -70,6 +72,52 @@ __global__ void k_mur1d(T *__restrict__ ex, const T *__restrict__ mur, int64_t n
 
 // ------------------------------------------------------------------- 2-D TMz
 
+// CPML H update of one 2-D cell (Eq. 7-12): psi <- b psi + a dE, curl scaled by 1/kappa.
+template <typename T>
+__device__ __forceinline__ void h2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ch, T cph,
+                                        T dEy, T dEx, T &hxv, T &hyv)
+{
+    const int L = cp.L;
+    if (in_slab<T>(j, ny, L)) {
+        T *p = cp.psi[2] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        T ps = cp.bh[1][j] * *p + cp.ah[1][j] * dEy;
+        *p = ps;
+        hxv -= ch * dEy * cp.ikh[1][j] + cph * ps;
+    } else {
+        hxv -= ch * dEy;
+    }
+    if (in_slab<T>(i, nx, L)) {
+        T *p = cp.psi[3] + j * (2 * L) + slab_slot<T>(i, nx, L);
+        T ps = cp.bh[0][i] * *p + cp.ah[0][i] * dEx;
+        *p = ps;
+        hyv += ch * dEx * cp.ikh[0][i] + cph * ps;
+    } else {
+        hyv += ch * dEx;
+    }
+}
+
+// CPML curl term of the E update of one 2-D cell.
+template <typename T>
+__device__ __forceinline__ T e2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ce, T cpe,
+                                     T dHx, T dHy)
+{
+    const int L = cp.L;
+    T px = T(0), py = T(0), kx = T(1), ky = T(1);
+    if (in_slab<T>(i, nx, L)) {
+        T *p = cp.psi[0] + j * (2 * L) + slab_slot<T>(i, nx, L);
+        px = cp.be[0][i] * *p + cp.ae[0][i] * dHx;
+        *p = px;
+        kx = cp.ike[0][i];
+    }
+    if (in_slab<T>(j, ny, L)) {
+        T *p = cp.psi[1] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        py = cp.be[1][j] * *p + cp.ae[1][j] * dHy;
+        *p = py;
+        ky = cp.ike[1][j];
+    }
+    return ce * (dHx * kx - dHy * ky) + cpe * (px - py);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__restrict__ hx, T *__restrict__ hy,
                                              int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp, Source src,
@@ -84,27 +132,11 @@ __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__rest
     const T dEy = (j + 1 < ny ? ez[c + nx] : T(0)) - e;   // dEz along y at (i, j+1/2)
     const T dEx = (i + 1 < nx ? ez[c + 1] : T(0)) - e;    // dEz along x at (i+1/2, j)
     T hxv = hx[c], hyv = hy[c];
-    const int L = cp.L;
-    if (L == 0) {
+    if (cp.L == 0) {
         hxv -= ch * dEy;                                  // mu0 dHx/dt = -dEz/dy
         hyv += ch * dEx;                                  // mu0 dHy/dt = +dEz/dx
     } else {
-        if (in_slab<T>(j, ny, L)) {
-            T *p = cp.psi[2] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
-            T ps = cp.bh[1][j] * *p + cp.ah[1][j] * dEy;
-            *p = ps;
-            hxv -= ch * dEy * cp.ikh[1][j] + cph * ps;
-        } else {
-            hxv -= ch * dEy;
-        }
-        if (in_slab<T>(i, nx, L)) {
-            T *p = cp.psi[3] + j * (2 * L) + slab_slot<T>(i, nx, L);
-            T ps = cp.bh[0][i] * *p + cp.ah[0][i] * dEx;
-            *p = ps;
-            hyv += ch * dEx * cp.ikh[0][i] + cph * ps;
-        } else {
-            hyv += ch * dEx;
-        }
+        h2d_pml<T>(cp, nx, ny, i, j, ch, cph, dEy, dEx, hxv, hyv);
     }
     hx[c] = hxv;
     hy[c] = hyv;
@@ -124,26 +156,8 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
     const T ezc = ez[c];
     const T dHx = hy[c] - hy[c - 1];     // dHy along x
     const T dHy = hx[c] - hx[c - nx];    // dHx along y
-    T upd;
-    const int L = cp.L;
-    if (L == 0) {
-        upd = ce * (dHx - dHy);          // eps0 dEz/dt = dHy/dx - dHx/dy - Jz
-    } else {
-        T px = T(0), py = T(0), kx = T(1), ky = T(1);
-        if (in_slab<T>(i, nx, L)) {
-            T *p = cp.psi[0] + j * (2 * L) + slab_slot<T>(i, nx, L);
-            px = cp.be[0][i] * *p + cp.ae[0][i] * dHx;
-            *p = px;
-            kx = cp.ike[0][i];
-        }
-        if (in_slab<T>(j, ny, L)) {
-            T *p = cp.psi[1] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
-            py = cp.be[1][j] * *p + cp.ae[1][j] * dHy;
-            *p = py;
-            ky = cp.ike[1][j];
-        }
-        upd = ce * (dHx * kx - dHy * ky) + cpe * (px - py);
-    }
+    // eps0 dEz/dt = dHy/dx - dHx/dy - Jz
+    const T upd = cp.L == 0 ? ce * (dHx - dHy) : e2d_pml<T>(cp, nx, ny, i, j, ce, cpe, dHx, dHy);
     T v = ezc + upd;
     if (src.kind && i == src.i && j == src.j) v += (T)*src.val;
     ez[c] = v;
@@ -168,6 +182,68 @@ struct Pml3 {
     }
 };
 
+// CPML H update of one 3-D cell: six psi recursions on the slabs the cell is in.
+template <typename T>
+__device__ __forceinline__ void h3d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t nz, int64_t i, int64_t j,
+                                        int64_t k, T ch, T cph, T dEz_y, T dEy_z, T dEx_z, T dEz_x, T dEy_x, T dEx_y,
+                                        T &hxv, T &hyv, T &hzv)
+{
+    const int L = cp.L;
+    Pml3<T> P{cp, nx, ny, nz, i, j, k};
+    const bool sx = in_slab<T>(i, nx, L), sy = in_slab<T>(j, ny, L), sz = in_slab<T>(k, nz, L);
+    const T kx = sx ? cp.ikh[0][i] : T(1), ky = sy ? cp.ikh[1][j] : T(1), kz = sz ? cp.ikh[2][k] : T(1);
+    T p6 = 0, p7 = 0, p8 = 0, p9 = 0, p10 = 0, p11 = 0;
+    if (sy) {
+        T *a = P.slot_ptr(6, 1), *b = P.slot_ptr(11, 1);
+        p6 = cp.bh[1][j] * *a + cp.ah[1][j] * dEz_y; *a = p6;
+        p11 = cp.bh[1][j] * *b + cp.ah[1][j] * dEx_y; *b = p11;
+    }
+    if (sz) {
+        T *a = P.slot_ptr(7, 2), *b = P.slot_ptr(9, 2);
+        p7 = cp.bh[2][k] * *a + cp.ah[2][k] * dEy_z; *a = p7;
+        p9 = cp.bh[2][k] * *b + cp.ah[2][k] * dEx_z; *b = p9;
+    }
+    if (sx) {
+        T *a = P.slot_ptr(8, 0), *b = P.slot_ptr(10, 0);
+        p8 = cp.bh[0][i] * *a + cp.ah[0][i] * dEz_x; *a = p8;
+        p10 = cp.bh[0][i] * *b + cp.ah[0][i] * dEy_x; *b = p10;
+    }
+    hxv -= ch * (dEz_y * ky - dEy_z * kz) + cph * (p6 - p7);
+    hyv -= ch * (dEx_z * kz - dEz_x * kx) + cph * (p9 - p8);
+    hzv -= ch * (dEy_x * kx - dEx_y * ky) + cph * (p10 - p11);
+}
+
+// CPML curl terms (ux, uy, uz) of the E update of one 3-D cell.
+template <typename T>
+__device__ __forceinline__ void e3d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t nz, int64_t i, int64_t j,
+                                        int64_t k, T ce, T cpe, T dHz_y, T dHy_z, T dHx_z, T dHz_x, T dHy_x, T dHx_y,
+                                        T &ux, T &uy, T &uz)
+{
+    const int L = cp.L;
+    Pml3<T> P{cp, nx, ny, nz, i, j, k};
+    const bool sx = in_slab<T>(i, nx, L), sy = in_slab<T>(j, ny, L), sz = in_slab<T>(k, nz, L);
+    const T kx = sx ? cp.ike[0][i] : T(1), ky = sy ? cp.ike[1][j] : T(1), kz = sz ? cp.ike[2][k] : T(1);
+    T p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0;
+    if (sy) {
+        T *a = P.slot_ptr(0, 1), *b = P.slot_ptr(5, 1);
+        p0 = cp.be[1][j] * *a + cp.ae[1][j] * dHz_y; *a = p0;
+        p5 = cp.be[1][j] * *b + cp.ae[1][j] * dHx_y; *b = p5;
+    }
+    if (sz) {
+        T *a = P.slot_ptr(1, 2), *b = P.slot_ptr(3, 2);
+        p1 = cp.be[2][k] * *a + cp.ae[2][k] * dHy_z; *a = p1;
+        p3 = cp.be[2][k] * *b + cp.ae[2][k] * dHx_z; *b = p3;
+    }
+    if (sx) {
+        T *a = P.slot_ptr(2, 0), *b = P.slot_ptr(4, 0);
+        p2 = cp.be[0][i] * *a + cp.ae[0][i] * dHz_x; *a = p2;
+        p4 = cp.be[0][i] * *b + cp.ae[0][i] * dHy_x; *b = p4;
+    }
+    ux = ce * (dHz_y * ky - dHy_z * kz) + cpe * (p0 - p1);
+    uy = ce * (dHx_z * kz - dHz_x * kx) + cpe * (p3 - p2);
+    uz = ce * (dHy_x * kx - dHx_y * ky) + cpe * (p4 - p5);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_h3d(const T *__restrict__ ex, const T *__restrict__ ey,
                                              const T *__restrict__ ez, T *__restrict__ hx, T *__restrict__ hy,
@@ -189,39 +265,23 @@ __global__ void __launch_bounds__(256) k_h3d(const T *__restrict__ ex, const T *
     const T dEy_x = (i + 1 < nx ? ey[c + 1] : T(0)) - eyc;
     const T dEx_y = (j + 1 < ny ? ex[c + nx] : T(0)) - exc;
     T hxv = hx[c], hyv = hy[c], hzv = hz[c];
-    const int L = cp.L;
-    if (L == 0) {
+    if (cp.L == 0) {
         // mu0 dH/dt = -curl E
         hxv -= ch * (dEz_y - dEy_z);
         hyv -= ch * (dEx_z - dEz_x);
         hzv -= ch * (dEy_x - dEx_y);
     } else {
-        Pml3<T> P{cp, nx, ny, nz, i, j, k};
-        const bool sx = in_slab<T>(i, nx, L), sy = in_slab<T>(j, ny, L), sz = in_slab<T>(k, nz, L);
-        const T kx = sx ? cp.ikh[0][i] : T(1), ky = sy ? cp.ikh[1][j] : T(1), kz = sz ? cp.ikh[2][k] : T(1);
-        T p6 = 0, p7 = 0, p8 = 0, p9 = 0, p10 = 0, p11 = 0;
-        if (sy) {
-            T *a = P.slot_ptr(6, 1), *b = P.slot_ptr(11, 1);
-            p6 = cp.bh[1][j] * *a + cp.ah[1][j] * dEz_y; *a = p6;
-            p11 = cp.bh[1][j] * *b + cp.ah[1][j] * dEx_y; *b = p11;
-        }
-        if (sz) {
-            T *a = P.slot_ptr(7, 2), *b = P.slot_ptr(9, 2);
-            p7 = cp.bh[2][k] * *a + cp.ah[2][k] * dEy_z; *a = p7;
-            p9 = cp.bh[2][k] * *b + cp.ah[2][k] * dEx_z; *b = p9;
-        }
-        if (sx) {
-            T *a = P.slot_ptr(8, 0), *b = P.slot_ptr(10, 0);
-            p8 = cp.bh[0][i] * *a + cp.ah[0][i] * dEz_x; *a = p8;
-            p10 = cp.bh[0][i] * *b + cp.ah[0][i] * dEy_x; *b = p10;
-        }
-        hxv -= ch * (dEz_y * ky - dEy_z * kz) + cph * (p6 - p7);
-        hyv -= ch * (dEx_z * kz - dEz_x * kx) + cph * (p9 - p8);
-        hzv -= ch * (dEy_x * kx - dEx_y * ky) + cph * (p10 - p11);
+        h3d_pml<T>(cp, nx, ny, nz, i, j, k, ch, cph, dEz_y, dEy_z, dEx_z, dEz_x, dEy_x, dEx_y, hxv, hyv, hzv);
     }
     hx[c] = hxv;
     hy[c] = hyv;
     hz[c] = hzv;
+}
+
+__device__ __forceinline__ bool source_hits(const Source &src, int64_t i, int64_t j, int64_t k)
+{
+    return src.loc == FDTD_LOC_SHEET ? (k == src.k && i >= src.i0 && i < src.i1 && j >= src.j0 && j < src.j1)
+                                     : (i == src.i && j == src.j && k == src.k);
 }
 
 template <typename T>
@@ -246,49 +306,342 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
     const T dHz_x = i > 0 ? hzc - hz[c - 1] : T(0);
     const T dHy_x = i > 0 ? hyc - hy[c - 1] : T(0);
     const T dHx_y = j > 0 ? hxc - hx[c - nx] : T(0);
-    const int L = cp.L;
     T ux, uy, uz;
-    if (L == 0) {
+    if (cp.L == 0) {
         // eps0 dE/dt = curl H (- J, already applied to Ex)
         ux = ce * (dHz_y - dHy_z);
         uy = ce * (dHx_z - dHz_x);
         uz = ce * (dHy_x - dHx_y);
     } else {
-        Pml3<T> P{cp, nx, ny, nz, i, j, k};
-        const bool sx = in_slab<T>(i, nx, L), sy = in_slab<T>(j, ny, L), sz = in_slab<T>(k, nz, L);
-        const T kx = sx ? cp.ike[0][i] : T(1), ky = sy ? cp.ike[1][j] : T(1), kz = sz ? cp.ike[2][k] : T(1);
-        T p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0;
-        if (sy) {
-            T *a = P.slot_ptr(0, 1), *b = P.slot_ptr(5, 1);
-            p0 = cp.be[1][j] * *a + cp.ae[1][j] * dHz_y; *a = p0;
-            p5 = cp.be[1][j] * *b + cp.ae[1][j] * dHx_y; *b = p5;
-        }
-        if (sz) {
-            T *a = P.slot_ptr(1, 2), *b = P.slot_ptr(3, 2);
-            p1 = cp.be[2][k] * *a + cp.ae[2][k] * dHy_z; *a = p1;
-            p3 = cp.be[2][k] * *b + cp.ae[2][k] * dHx_z; *b = p3;
-        }
-        if (sx) {
-            T *a = P.slot_ptr(2, 0), *b = P.slot_ptr(4, 0);
-            p2 = cp.be[0][i] * *a + cp.ae[0][i] * dHz_x; *a = p2;
-            p4 = cp.be[0][i] * *b + cp.ae[0][i] * dHy_x; *b = p4;
-        }
-        ux = ce * (dHz_y * ky - dHy_z * kz) + cpe * (p0 - p1);
-        uy = ce * (dHx_z * kz - dHz_x * kx) + cpe * (p3 - p2);
-        uz = ce * (dHy_x * kx - dHx_y * ky) + cpe * (p4 - p5);
+        e3d_pml<T>(cp, nx, ny, nz, i, j, k, ce, cpe, dHz_y, dHy_z, dHx_z, dHz_x, dHy_x, dHx_y, ux, uy, uz);
     }
     if (j > 0 && k > 0) {
         T v = exc + ux;
-        if (src.kind) {
-            bool hit = src.loc == FDTD_LOC_SHEET
-                           ? (k == src.k && i >= src.i0 && i < src.i1 && j >= src.j0 && j < src.j1)
-                           : (i == src.i && j == src.j && k == src.k);
-            if (hit) v += (T)*src.val;
-        }
+        if (src.kind && source_hits(src, i, j, k)) v += (T)*src.val;
         ex[c] = v;
     }
     if (i > 0 && k > 0) ey[c] = eyc + uy;
     if (i > 0 && j > 0) ez[c] = ezc + uz;
+}
+
+// ------------------------------------------------- FP32, four cells per thread
+// Rows of a multiple of 4 cells: each thread owns 4 consecutive x cells and
+// moves them with 16-byte loads and stores, so a warp covers a 512-byte row
+// segment per field and a quarter of the instructions per cell.  The x
+// neighbour one past the quad (x + 1 for H, x - 1 for E) comes from the
+// adjacent lane by a shuffle; a lane whose neighbour quad sits in another
+// warp or row loads that one value directly.  Cells inside a CPML slab take
+// the same per-cell code as the scalar kernels.  Block sizes are a multiple
+// of 32 threads (the launcher checks), so every shuffle has all lanes.
+
+struct Q4 {
+    float v[4];
+};
+__device__ __forceinline__ Q4 ld4(const float *p)
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    return Q4{{t.x, t.y, t.z, t.w}};
+}
+__device__ __forceinline__ void st4(float *p, const Q4 &q)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+__device__ __forceinline__ Q4 ld4_if(bool ok, const float *p) { return ok ? ld4(p) : Q4{{0.f, 0.f, 0.f, 0.f}}; }
+__device__ __forceinline__ unsigned lane_id()
+{
+    return (threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z)) & 31u;
+}
+
+__global__ void __launch_bounds__(256) k_h2d_v4(const float *__restrict__ ez, float *__restrict__ hx,
+                                                float *__restrict__ hy, int64_t nx, int64_t ny, float ch, float cph,
+                                                Cpml<float> cp, Source src, const int64_t *__restrict__ d_step,
+                                                int kstep)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    if (q == 0 && j == 0) write_source(src, d_step, kstep);
+    const int64_t i0 = 4 * q;
+    const bool live = i0 < nx && j < ny;
+    const int64_t c = live ? j * nx + i0 : 0;
+    // the lane at the end of a warp row loads its x neighbour with the others,
+    // not after the shuffle (that would be a second round trip for the warp)
+    const bool edge = threadIdx.x + 1 >= blockDim.x || lane_id() == 31;
+    const float eh = edge && live && i0 + 4 < nx ? ez[c + 4] : 0.f;
+    const Q4 E = ld4_if(live, ez + c);
+    const Q4 Ey = ld4_if(live && j + 1 < ny, ez + c + nx);
+    Q4 Hx = ld4_if(live, hx + c), Hy = ld4_if(live, hy + c);   // every load before the shuffle
+    float er = __shfl_down_sync(0xffffffffu, E.v[0], 1);
+    if (edge) er = eh;
+    if (!live) return;
+    const int L = cp.L;
+    const bool pml = L > 0 && (in_slab<float>(j, ny, L) || i0 < L || i0 + 3 >= nx - L);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float dEy = Ey.v[e] - E.v[e];
+        const float dEx = (e < 3 ? E.v[e + 1] : er) - E.v[e];
+        if (!pml) {
+            Hx.v[e] -= ch * dEy;
+            Hy.v[e] += ch * dEx;
+        } else {
+            h2d_pml<float>(cp, nx, ny, i0 + e, j, ch, cph, dEy, dEx, Hx.v[e], Hy.v[e]);
+        }
+    }
+    st4(hx + c, Hx);
+    st4(hy + c, Hy);
+}
+
+__global__ void __launch_bounds__(256) k_e2d_v4(float *__restrict__ ez, const float *__restrict__ hx,
+                                                const float *__restrict__ hy, int64_t nx, int64_t ny, float ce,
+                                                float cpe, Cpml<float> cp, Source src,
+                                                const int64_t *__restrict__ d_step, int kstep)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t i0 = 4 * q;
+    const bool live = i0 < nx && j < ny;
+    const int64_t c = live ? j * nx + i0 : 0;
+    const bool edge = threadIdx.x == 0 || lane_id() == 0;
+    const float hh = edge && live && i0 > 0 ? hy[c - 1] : 0.f;
+    const Q4 Hy = ld4_if(live, hy + c);
+    const bool row = live && j >= 1;   // row 0 is the PEC wall
+    const Q4 Hx = ld4_if(row, hx + c), Hxm = ld4_if(row, hx + c - nx);
+    Q4 E = ld4_if(row, ez + c);        // every load before the shuffle
+    float hl = __shfl_up_sync(0xffffffffu, Hy.v[3], 1);
+    if (edge) hl = hh;
+    if (!row) return;
+    const int L = cp.L;
+    const bool pml = L > 0 && (in_slab<float>(j, ny, L) || i0 < L || i0 + 3 >= nx - L);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int64_t i = i0 + e;
+        if (i < 1) continue;      // column 0 is the PEC wall
+        const float dHx = Hy.v[e] - (e > 0 ? Hy.v[e - 1] : hl);
+        const float dHy = Hx.v[e] - Hxm.v[e];
+        E.v[e] += pml ? e2d_pml<float>(cp, nx, ny, i, j, ce, cpe, dHx, dHy) : ce * (dHx - dHy);
+        if (src.kind && i == src.i && j == src.j) E.v[e] += (float)*src.val;
+    }
+    st4(ez + c, E);
+}
+
+// 3-D CPML with four cells per thread: a row lies wholly inside or outside a
+// y or z slab, so those psi recursions run for the whole quad with 16-byte
+// psi accesses and no divergence within the warp.  The x slab cuts rows, and
+// is applied per cell as a correction to the update with kappa_x = 1 and no
+// x psi: (kappa_x^-1 - 1) times the x difference, plus the x psi term.
+
+__global__ void __launch_bounds__(256) k_h3d_v4(const float *__restrict__ ex, const float *__restrict__ ey,
+                                                const float *__restrict__ ez, float *__restrict__ hx,
+                                                float *__restrict__ hy, float *__restrict__ hz, int64_t nx,
+                                                int64_t ny, int64_t nz, float ch, float cph, Cpml<float> cp,
+                                                Source src, const int64_t *__restrict__ d_step, int kstep)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
+    if (q == 0 && j == 0 && k == 0) write_source(src, d_step, kstep);
+    const int64_t i0 = 4 * q, sxy = nx * ny;
+    const bool live = i0 < nx && j < ny && k < nz;
+    const int64_t c = live ? k * sxy + j * nx + i0 : 0;
+    const bool edge = threadIdx.x + 1 >= blockDim.x || lane_id() == 31;
+    const bool hin = edge && live && i0 + 4 < nx;
+    const float ezh = hin ? ez[c + 4] : 0.f, eyh = hin ? ey[c + 4] : 0.f;
+    const Q4 Ex = ld4_if(live, ex + c), Ey = ld4_if(live, ey + c), Ez = ld4_if(live, ez + c);
+    const Q4 Ezy = ld4_if(live && j + 1 < ny, ez + c + nx), Exy = ld4_if(live && j + 1 < ny, ex + c + nx);
+    const Q4 Eyz = ld4_if(live && k + 1 < nz, ey + c + sxy), Exz = ld4_if(live && k + 1 < nz, ex + c + sxy);
+    Q4 Hx = ld4_if(live, hx + c), Hy = ld4_if(live, hy + c), Hz = ld4_if(live, hz + c);   // all loads first
+    float ezr = __shfl_down_sync(0xffffffffu, Ez.v[0], 1);
+    float eyr = __shfl_down_sync(0xffffffffu, Ey.v[0], 1);
+    if (edge) {
+        ezr = ezh;
+        eyr = eyh;
+    }
+    if (!live) return;
+    float dEz_y[4], dEy_z[4], dEx_z[4], dEz_x[4], dEy_x[4], dEx_y[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        dEz_y[e] = Ezy.v[e] - Ez.v[e];
+        dEy_z[e] = Eyz.v[e] - Ey.v[e];
+        dEx_z[e] = Exz.v[e] - Ex.v[e];
+        dEz_x[e] = (e < 3 ? Ez.v[e + 1] : ezr) - Ez.v[e];
+        dEy_x[e] = (e < 3 ? Ey.v[e + 1] : eyr) - Ey.v[e];
+        dEx_y[e] = Exy.v[e] - Ex.v[e];
+    }
+    const int L = cp.L;
+    if (L == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {   // mu0 dH/dt = -curl E
+            Hx.v[e] -= ch * (dEz_y[e] - dEy_z[e]);
+            Hy.v[e] -= ch * (dEx_z[e] - dEz_x[e]);
+            Hz.v[e] -= ch * (dEy_x[e] - dEx_y[e]);
+        }
+    } else {
+        float ky = 1.f, kz = 1.f;
+        Q4 p6{}, p7{}, p9{}, p11{};
+        if (in_slab<float>(j, ny, L)) {   // slots 6 (Hx, dEz/dy) and 11 (Hz, dEx/dy)
+            const int64_t o = (k * (2 * L) + slab_slot<float>(j, ny, L)) * nx + i0;
+            const float bb = cp.bh[1][j], aa = cp.ah[1][j];
+            ky = cp.ikh[1][j];
+            const Q4 s6 = ld4(cp.psi[6] + o), s11 = ld4(cp.psi[11] + o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                p6.v[e] = bb * s6.v[e] + aa * dEz_y[e];
+                p11.v[e] = bb * s11.v[e] + aa * dEx_y[e];
+            }
+            st4(cp.psi[6] + o, p6);
+            st4(cp.psi[11] + o, p11);
+        }
+        if (in_slab<float>(k, nz, L)) {   // slots 7 (Hx, dEy/dz) and 9 (Hy, dEx/dz)
+            const int64_t o = ((int64_t)slab_slot<float>(k, nz, L) * ny + j) * nx + i0;
+            const float bb = cp.bh[2][k], aa = cp.ah[2][k];
+            kz = cp.ikh[2][k];
+            const Q4 s7 = ld4(cp.psi[7] + o), s9 = ld4(cp.psi[9] + o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                p7.v[e] = bb * s7.v[e] + aa * dEy_z[e];
+                p9.v[e] = bb * s9.v[e] + aa * dEx_z[e];
+            }
+            st4(cp.psi[7] + o, p7);
+            st4(cp.psi[9] + o, p9);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            Hx.v[e] -= ch * (dEz_y[e] * ky - dEy_z[e] * kz) + cph * (p6.v[e] - p7.v[e]);
+            Hy.v[e] -= ch * (dEx_z[e] * kz - dEz_x[e]) + cph * p9.v[e];
+            Hz.v[e] -= ch * (dEy_x[e] - dEx_y[e] * ky) - cph * p11.v[e];
+        }
+        if (i0 < L || i0 + 3 >= nx - L) {   // slots 8 (Hy, dEz/dx) and 10 (Hz, dEy/dx)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t i = i0 + e;
+                if (!in_slab<float>(i, nx, L)) continue;
+                const float bb = cp.bh[0][i], aa = cp.ah[0][i], kx1 = cp.ikh[0][i] - 1.f;
+                const int64_t o = (k * ny + j) * (2 * L) + slab_slot<float>(i, nx, L);
+                const float p8 = bb * cp.psi[8][o] + aa * dEz_x[e];
+                const float p10 = bb * cp.psi[10][o] + aa * dEy_x[e];
+                cp.psi[8][o] = p8;
+                cp.psi[10][o] = p10;
+                Hy.v[e] += ch * dEz_x[e] * kx1 + cph * p8;
+                Hz.v[e] -= ch * dEy_x[e] * kx1 + cph * p10;
+            }
+        }
+    }
+    st4(hx + c, Hx);
+    st4(hy + c, Hy);
+    st4(hz + c, Hz);
+}
+
+__global__ void __launch_bounds__(256) k_e3d_v4(float *__restrict__ ex, float *__restrict__ ey,
+                                                float *__restrict__ ez, const float *__restrict__ hx,
+                                                const float *__restrict__ hy, const float *__restrict__ hz,
+                                                int64_t nx, int64_t ny, int64_t nz, float ce, float cpe,
+                                                Cpml<float> cp, Source src, const int64_t *__restrict__ d_step,
+                                                int kstep)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
+    const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
+    const int64_t i0 = 4 * q, sxy = nx * ny;
+    const bool live = i0 < nx && j < ny && k < nz;
+    const int64_t c = live ? k * sxy + j * nx + i0 : 0;
+    const bool edge = threadIdx.x == 0 || lane_id() == 0;
+    const bool hin = edge && live && i0 > 0;
+    const float hzh = hin ? hz[c - 1] : 0.f, hyh = hin ? hy[c - 1] : 0.f;
+    const Q4 Hx = ld4_if(live, hx + c), Hy = ld4_if(live, hy + c), Hz = ld4_if(live, hz + c);
+    const Q4 Hzy = ld4_if(live && j > 0, hz + c - nx), Hxy = ld4_if(live && j > 0, hx + c - nx);
+    const Q4 Hyz = ld4_if(live && k > 0, hy + c - sxy), Hxz = ld4_if(live && k > 0, hx + c - sxy);
+    // E^n too, before the shuffles and any psi store (see k_e2d)
+    Q4 Ex = ld4_if(live, ex + c), Ey = ld4_if(live, ey + c), Ez = ld4_if(live, ez + c);
+    float hzl = __shfl_up_sync(0xffffffffu, Hz.v[3], 1);
+    float hyl = __shfl_up_sync(0xffffffffu, Hy.v[3], 1);
+    if (edge) {
+        hzl = hzh;
+        hyl = hyh;
+    }
+    if (!live) return;
+    float dHz_y[4], dHy_z[4], dHx_z[4], dHz_x[4], dHy_x[4], dHx_y[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const bool xi = i0 + e > 0;
+        dHz_y[e] = j > 0 ? Hz.v[e] - Hzy.v[e] : 0.f;
+        dHy_z[e] = k > 0 ? Hy.v[e] - Hyz.v[e] : 0.f;
+        dHx_z[e] = k > 0 ? Hx.v[e] - Hxz.v[e] : 0.f;
+        dHz_x[e] = xi ? Hz.v[e] - (e > 0 ? Hz.v[e - 1] : hzl) : 0.f;
+        dHy_x[e] = xi ? Hy.v[e] - (e > 0 ? Hy.v[e - 1] : hyl) : 0.f;
+        dHx_y[e] = j > 0 ? Hx.v[e] - Hxy.v[e] : 0.f;
+    }
+    float ux[4], uy[4], uz[4];
+    const int L = cp.L;
+    if (L == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {   // eps0 dE/dt = curl H (- J, already applied to Ex)
+            ux[e] = ce * (dHz_y[e] - dHy_z[e]);
+            uy[e] = ce * (dHx_z[e] - dHz_x[e]);
+            uz[e] = ce * (dHy_x[e] - dHx_y[e]);
+        }
+    } else {
+        float ky = 1.f, kz = 1.f;
+        Q4 p0{}, p1{}, p3{}, p5{};
+        if (in_slab<float>(j, ny, L)) {   // slots 0 (Ex, dHz/dy) and 5 (Ez, dHx/dy)
+            const int64_t o = (k * (2 * L) + slab_slot<float>(j, ny, L)) * nx + i0;
+            const float bb = cp.be[1][j], aa = cp.ae[1][j];
+            ky = cp.ike[1][j];
+            const Q4 s0 = ld4(cp.psi[0] + o), s5 = ld4(cp.psi[5] + o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                p0.v[e] = bb * s0.v[e] + aa * dHz_y[e];
+                p5.v[e] = bb * s5.v[e] + aa * dHx_y[e];
+            }
+            st4(cp.psi[0] + o, p0);
+            st4(cp.psi[5] + o, p5);
+        }
+        if (in_slab<float>(k, nz, L)) {   // slots 1 (Ex, dHy/dz) and 3 (Ey, dHx/dz)
+            const int64_t o = ((int64_t)slab_slot<float>(k, nz, L) * ny + j) * nx + i0;
+            const float bb = cp.be[2][k], aa = cp.ae[2][k];
+            kz = cp.ike[2][k];
+            const Q4 s1 = ld4(cp.psi[1] + o), s3 = ld4(cp.psi[3] + o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                p1.v[e] = bb * s1.v[e] + aa * dHy_z[e];
+                p3.v[e] = bb * s3.v[e] + aa * dHx_z[e];
+            }
+            st4(cp.psi[1] + o, p1);
+            st4(cp.psi[3] + o, p3);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            ux[e] = ce * (dHz_y[e] * ky - dHy_z[e] * kz) + cpe * (p0.v[e] - p1.v[e]);
+            uy[e] = ce * (dHx_z[e] * kz - dHz_x[e]) + cpe * p3.v[e];
+            uz[e] = ce * (dHy_x[e] - dHx_y[e] * ky) - cpe * p5.v[e];
+        }
+        if (i0 < L || i0 + 3 >= nx - L) {   // slots 2 (Ey, dHz/dx) and 4 (Ez, dHy/dx)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t i = i0 + e;
+                if (!in_slab<float>(i, nx, L)) continue;
+                const float bb = cp.be[0][i], aa = cp.ae[0][i], kx1 = cp.ike[0][i] - 1.f;
+                const int64_t o = (k * ny + j) * (2 * L) + slab_slot<float>(i, nx, L);
+                const float p2 = bb * cp.psi[2][o] + aa * dHz_x[e];
+                const float p4 = bb * cp.psi[4][o] + aa * dHy_x[e];
+                cp.psi[2][o] = p2;
+                cp.psi[4][o] = p4;
+                uy[e] -= ce * dHz_x[e] * kx1 + cpe * p2;
+                uz[e] += ce * dHy_x[e] * kx1 + cpe * p4;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int64_t i = i0 + e;
+        if (j > 0 && k > 0) {
+            Ex.v[e] += ux[e];
+            if (src.kind && source_hits(src, i, j, k)) Ex.v[e] += (float)*src.val;
+        }
+        if (i > 0 && k > 0) Ey.v[e] += uy[e];
+        if (i > 0 && j > 0) Ez.v[e] += uz[e];
+    }
+    st4(ex + c, Ex);
+    st4(ey + c, Ey);
+    st4(ez + c, Ez);
 }
 
 __global__ void k_advance(int64_t *d_step, int64_t by) { *d_step += by; }
@@ -313,31 +666,70 @@ void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m)
 {
     k_mur1d<T><<<1, 32, 0, st>>>(ex, mur_state, nz, m);
 }
+// cpt = cells per thread.  The four-cells-per-thread kernels (cpt = 4) take
+// FP32 rows of a multiple of 4 cells and whole-warp blocks, b.x then counting
+// quads of cells; anything else runs one cell per thread.
+template <typename T>
+bool use_v4(int64_t nx, dim3 b, int cpt)
+{
+    return cpt == 4 && std::is_same<T, float>::value && nx % 4 == 0 && (b.x * b.y * b.z) % 32 == 0;
+}
+
 template <typename T>
 void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 b)
+                Source src, const int64_t *d_step, int kstep, dim3 b, int cpt)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_v4<T>(nx, b, cpt)) {
+            dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y));
+            k_h2d_v4<<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
+            return;
+        }
+    }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y));
     k_h2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 b)
+                Source src, const int64_t *d_step, int kstep, dim3 b, int cpt)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_v4<T>(nx, b, cpt)) {
+            dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y));
+            k_e2d_v4<<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
+            return;
+        }
+    }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y));
     k_e2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 b)
+                Source src, const int64_t *d_step, int kstep, dim3 b, int cpt)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_v4<T>(nx, b, cpt)) {
+            dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
+            k_h3d_v4<<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step,
+                                      kstep);
+            return;
+        }
+    }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
     k_h3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 b)
+                Source src, const int64_t *d_step, int kstep, dim3 b, int cpt)
 {
+    if constexpr (std::is_same<T, float>::value) {
+        if (use_v4<T>(nx, b, cpt)) {
+            dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
+            k_e3d_v4<<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step,
+                                      kstep);
+            return;
+        }
+    }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
     k_e3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step, kstep);
 }
@@ -348,13 +740,13 @@ void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by) { k_advance<<<
     template void launch_e1d<T>(cudaStream_t, T *, const T *, int64_t, T, Source, const int64_t *, int);      \
     template void launch_mur1d<T>(cudaStream_t, T *, const T *, int64_t, T);                                  \
     template void launch_h2d<T>(cudaStream_t, const T *, T *, T *, int64_t, int64_t, T, T, Cpml<T>, Source,   \
-                                const int64_t *, int, dim3);                                                  \
+                                const int64_t *, int, dim3, int);                                                  \
     template void launch_e2d<T>(cudaStream_t, T *, const T *, const T *, int64_t, int64_t, T, T, Cpml<T>,     \
-                                Source, const int64_t *, int, dim3);                                          \
+                                Source, const int64_t *, int, dim3, int);                                          \
     template void launch_h3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>, Source,  \
-                                const int64_t *, int, dim3);                                                  \
+                                const int64_t *, int, dim3, int);                                                  \
     template void launch_e3d<T>(cudaStream_t, T *const[6], int64_t, int64_t, int64_t, T, T, Cpml<T>, Source,  \
-                                const int64_t *, int, dim3);
+                                const int64_t *, int, dim3, int);
 FP_INST(float)
 FP_INST(double)
 

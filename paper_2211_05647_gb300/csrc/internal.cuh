@@ -13,6 +13,13 @@
 
 namespace fp {
 
+// SI constants (CODATA 2018 exact / recommended values)
+constexpr double kC0 = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+
 // ------------------------------------------------------------------ views
 
 // Per-axis CPML profile at E (integer) and H (half-integer) positions, plus
@@ -108,16 +115,16 @@ template <typename T>
 void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m);
 template <typename T>
 void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 block);
+                Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 block);
+                Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
 template <typename T>
 void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 block);
+                Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
-                Source src, const int64_t *d_step, int kstep, dim3 block);
+                Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by);
 
 // delta-f row pitch (elements) for nnode nodes of the given storage type
@@ -148,6 +155,28 @@ struct DiagArgs {
     const double *dV; // per node, device
 };
 // out[0..6): energy, energy_plain, number, number_max_cell, number_abs, finite
+// Running-DFT ports: block p averages pol[cells[off[p] .. off[p+1])] and adds
+// it times exp(-i 2 pi freq[f] t^{n+1}) dt into acc[p][f][re, im].
+template <typename T>
+cudaError_t launch_ports(cudaStream_t st, const T *pol, int nports, const int64_t *off, const int64_t *cells,
+                         const double *freq, double *acc, int nfreq, double dt, const int64_t *d_step, int kstep);
+
+// Velocity-grid tables (host, FP64): node v_par (speed on the speed grid),
+// current weight w, F0 and dF0/dv_par, volume element, |v|, s(|v|)|v| and its
+// F0-weighted mean, nu.  velocity_tables() returns false for a bad grid kind;
+// check_velocity_model() returns why the F0 / collision model is invalid, or NULL.
+struct VTab {
+    std::vector<double> v, w, f0, f0p, nu, dV, speed, sv;
+    double mean_sv = 0.0;
+};
+const char *check_velocity_model(const fdtd_plasma_desc &p);
+bool velocity_tables(const fdtd_plasma_desc &p, VTab &t);
+// collision frequency of node j for a mean collision frequency nu0
+inline double node_nu(const fdtd_plasma_desc &p, const VTab &t, size_t j, double nu0)
+{
+    return p.nu_model == FDTD_NU_CONST ? nu0 : nu0 * t.sv[j] / t.mean_sv;
+}
+
 cudaError_t launch_diag(cudaStream_t st, const DiagArgs &a, double *partials, int max_blocks, double *out);
 
 // Faces of a Poynting box: f = 2 * axis + (0 lower, 1 upper); plane[f] is the
@@ -232,7 +261,7 @@ struct fdtd_plasma {
     // launch shapes (autotuner / cache): kinetic (vectors per lane, lanes per row, CTAs per SM; 0 = default),
     // stencil block (0 = default)
     int kin_vpl, kin_l, kin_bps;
-    int st_bx, st_by, st_bz;
+    int st_bx, st_by, st_bz, st_cpt;
     int has_recording;
     float *rec_out;
     int64_t rec_cap;
@@ -246,6 +275,10 @@ struct fdtd_plasma {
     cudaGraphExec_t g1, gk;
     int gk_steps;
     int graphs_valid;
+    // running-DFT ports (device arrays; nports = 0: none)
+    int nports, nfreq;
+    int64_t *port_off, *port_cells;
+    double *port_freq, *port_acc;
     // diagnostics scratch
     double *diag_partials;
     int diag_blocks;

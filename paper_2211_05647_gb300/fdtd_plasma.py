@@ -24,7 +24,8 @@ STATUS = {0: "OK", -1: "INVAL", -2: "NOMEM", -3: "CUDA", -4: "UNSTABLE", -5: "NO
 PRECISION = {"f32": 0, "f64": 1}
 DF_DTYPE = {"f32": 0, "bf16": 1, "f64": 2}
 VGRID = {"signed1d": 0, "cart2d": 1, "speed3d": 2}
-NU_MODEL = {"nsv": 0, "const": 1}
+NU_MODEL = {"nsv": 0, "const": 1, "table": 2}
+F0_MODEL = {"maxwell": 0, "druyvesteyn": 1}
 SRC_KIND = {"none": 0, "gauss_sine": 1, "gauss": 2}
 SRC_LOC = {"point": 0, "sheet": 1}
 QUANTITY = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7}
@@ -67,7 +68,8 @@ class fdtd_plasma_desc(ctypes.Structure):
                 ("vgrid", ctypes.c_int32), ("nv", ctypes.c_int32), ("nv_perp", ctypes.c_int32),
                 ("te_ev", ctypes.c_double), ("vmax_vth", ctypes.c_double), ("nu0", ctypes.c_double),
                 ("nu_model", ctypes.c_int32), ("f_dtype", ctypes.c_int32), ("nonlinear", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("f0_model", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("s_speed", ctypes.c_void_p), ("s_sigma", ctypes.c_void_p), ("s_n", ctypes.c_int64)]
 
 
 class fdtd_diag(ctypes.Structure):
@@ -88,7 +90,8 @@ class fdtd_diag_arrays(ctypes.Structure):
 class fdtd_tune_result(ctypes.Structure):
     _fields_ = [("kin_vpl", ctypes.c_int32), ("kin_l", ctypes.c_int32), ("kin_blocks_per_sm", ctypes.c_int32),
                 ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("block_z", ctypes.c_int32),
-                ("kin_ms", ctypes.c_double), ("stencil_ms", ctypes.c_double)]
+                ("kin_ms", ctypes.c_double), ("stencil_ms", ctypes.c_double),
+                ("cells_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class fdtd_closure_desc(ctypes.Structure):
@@ -132,6 +135,11 @@ SIGNATURES = {
     "fdtd_plasma_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_diag)]),
     "fdtd_plasma_poynting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
+    "fdtd_plasma_launch_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_tune_result)]),
+    "fdtd_plasma_set_ports": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                             ctypes.POINTER(ctypes.c_double)]),
+    "fdtd_plasma_read_ports": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]),
     "fdtd_plasma_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p]),
     "fdtd_plasma_save_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
     "fdtd_plasma_load_state": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]),
@@ -241,14 +249,25 @@ def _source_desc(kind="gauss_sine", location="point", amp=1.0, fc=0.0, tau=1.0, 
 
 
 def _plasma_desc(density_ptr, on_device, vgrid="signed1d", nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0,
-                 nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0) -> fdtd_plasma_desc:
+                 nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0, f0_model="maxwell", s_table=None):
+    """Returns (descriptor, arrays the descriptor points into: keep them alive
+    until the create / set_plasma call has returned)."""
     d = fdtd_plasma_desc()
     d.density, d.density_on_device = density_ptr, on_device
     d.vgrid, d.nv, d.nv_perp = VGRID[vgrid], int(nv), int(nv_perp)
     d.te_ev, d.vmax_vth, d.nu0 = float(te_ev), float(vmax_vth), float(nu0)
     d.nu_model, d.f_dtype, d.nonlinear = NU_MODEL[nu_model], DF_DTYPE[f_dtype], int(nonlinear)
+    d.f0_model = F0_MODEL[f0_model]
     d.seed = int(seed)
-    return d
+    keep = ()
+    if s_table is not None:
+        sp = np.ascontiguousarray(s_table[0], dtype=np.float64)
+        sg = np.ascontiguousarray(s_table[1], dtype=np.float64)
+        if sp.shape != sg.shape or sp.ndim != 1:
+            raise ValueError("s_table: (speeds, cross-sections), two 1-D arrays of equal length")
+        d.s_speed, d.s_sigma, d.s_n = sp.ctypes.data, sg.ctypes.data, sp.size
+        keep = (sp, sg)
+    return d, keep
 
 
 # ------------------------------------------------------------ closure network
@@ -341,7 +360,8 @@ class Batch:
                 dens = np.ascontiguousarray(p["density"], dtype=np.float64)
                 self._keep.append(dens)
                 kw = {k: v for k, v in p.items() if k != "density"}
-                arr[r].plasma = _plasma_desc(dens.ctypes.data, 0, **kw)
+                arr[r].plasma, keep = _plasma_desc(dens.ctypes.data, 0, **kw)
+                self._keep.append(keep)
         self.precision = specs[0]["grid"].get("precision", "f32")
         self.f_dtype = (specs[0].get("plasma") or {}).get("f_dtype", "f32")
         rt = fdtd_runtime_desc()
@@ -445,7 +465,9 @@ class Solver:
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_source(self.h, ctypes.byref(d)))
 
     def set_plasma(self, density, vgrid="signed1d", nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0,
-                   nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0):
+                   nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0, f0_model="maxwell", s_table=None):
+        """s_table = (speeds, cross-sections) for nu_model "table"; f0_model
+        "maxwell" or "druyvesteyn"."""
         torch = self.torch
         if isinstance(density, torch.Tensor):
             dens = density.to(self.device, torch.float64).contiguous()
@@ -453,13 +475,10 @@ class Solver:
         else:
             dens = np.ascontiguousarray(density, dtype=np.float64)
             ptr, on_dev = dens.ctypes.data, 0
-        d = fdtd_plasma_desc()
-        d.density, d.density_on_device = ptr, on_dev
-        d.vgrid, d.nv, d.nv_perp = VGRID[vgrid], int(nv), int(nv_perp)
-        d.te_ev, d.vmax_vth, d.nu0 = float(te_ev), float(vmax_vth), float(nu0)
-        d.nu_model, d.f_dtype, d.nonlinear = NU_MODEL[nu_model], DF_DTYPE[f_dtype], int(nonlinear)
-        d.seed = int(seed)
+        d, keep = _plasma_desc(ptr, on_dev, vgrid, nv, nv_perp, te_ev, vmax_vth, nu0, nu_model, f_dtype, nonlinear,
+                               seed, f0_model, s_table)
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_plasma(self.h, ctypes.byref(d)))
+        del keep
         self.f_dtype = f_dtype
 
     def set_closure(self, params, e_scale, j_scale, n_scale, rho, n_train_max, beta=0.0, engine="mma"):
@@ -506,6 +525,12 @@ class Solver:
         r = fdtd_tune_result()
         _check(self.lib, self.h, self.lib.fdtd_plasma_autotune(self.h, ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in fdtd_tune_result._fields_}
+
+    def launch_shapes(self) -> dict:
+        """The launch shapes in use (tuned, cached or default)."""
+        r = fdtd_tune_result()
+        _check(self.lib, self.h, self.lib.fdtd_plasma_launch_shapes(self.h, ctypes.byref(r)))
+        return {k: getattr(r, k) for k, _ in fdtd_tune_result._fields_ if not k.endswith("_ms") and k != "reserved"}
 
     def reset(self):
         _check(self.lib, self.h, self.lib.fdtd_plasma_reset(self.h))
@@ -578,6 +603,27 @@ class Solver:
         out = (ctypes.c_double * 7)()
         _check(self.lib, self.h, self.lib.fdtd_plasma_poynting(self.h, b, out))
         return list(out)
+
+    def set_ports(self, ports, freqs):
+        """Running-DFT ports: ports = list of polarisation-node index arrays,
+        freqs in Hz; see fdtd_plasma_set_ports."""
+        cells = [np.ascontiguousarray(c, dtype=np.int64).ravel() for c in ports]
+        off = np.zeros(len(cells) + 1, dtype=np.int64)
+        off[1:] = np.cumsum([c.size for c in cells])
+        flat = np.concatenate(cells) if cells else np.zeros(1, np.int64)
+        fr = np.ascontiguousarray(freqs, dtype=np.float64).ravel()
+        i64 = ctypes.POINTER(ctypes.c_int64)
+        _check(self.lib, self.h, self.lib.fdtd_plasma_set_ports(
+            self.h, len(cells), off.ctypes.data_as(i64), flat.ctypes.data_as(i64), fr.size,
+            fr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        self._nports, self._nfreq = len(cells), fr.size
+
+    def port_spectra(self) -> np.ndarray:
+        """The port sums X[p, f] (complex128, [nports, nfreq])."""
+        out = np.zeros((getattr(self, "_nports", 0), getattr(self, "_nfreq", 0), 2), dtype=np.float64)
+        _check(self.lib, self.h, self.lib.fdtd_plasma_read_ports(
+            self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.nbytes))
+        return out[..., 0] + 1j * out[..., 1]
 
     def save_state(self, device: bool = True):
         torch = self.torch

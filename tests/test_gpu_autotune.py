@@ -36,10 +36,17 @@ def test_autotune_restores_state_and_caches(tmp_path, monkeypatch, kind):
     assert len(lines) == 2 and any("|kinetic|" in ln for ln in lines) and any("|stencil" in ln for ln in lines)
     s.step(60)
     ref = Solver.from_spec(spec)      # picks the cached shapes up at create / set_plasma
+    tuned = {k: v for k, v in res.items() if not k.endswith("_ms") and k != "reserved"}
+    assert ref.launch_shapes() == tuned
     ref.step(120)
+    again = Solver.from_spec(spec)    # same shapes throughout: bit-identical
+    again.step(120)
     monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "empty.txt"))
     dflt = Solver.from_spec(spec)     # default shapes
+    assert dflt.launch_shapes()["block_x"] > 0 or kind == "1d"
     dflt.step(120)
     for n in names:
-        assert np.array_equal(s.read(n, device=False), ref.read(n, device=False)), n
+        assert np.array_equal(again.read(n, device=False), ref.read(n, device=False)), n
+        # other shapes (one or four cells per thread) differ only in rounding order
+        assert rel_l2(s.read(n, device=False), ref.read(n, device=False)) <= 1e-5, n
         assert rel_l2(s.read(n, device=False), dflt.read(n, device=False)) <= 1e-5, n

@@ -46,6 +46,27 @@ def test_batch_runs_match_oracle(oracle_lib, precision, f_dtype, tol):
             assert np.linalg.norm(b.read(r, "j") - jr) / den <= tol
 
 
+def test_batch_druyvesteyn_table_matches_oracle(oracle_lib):
+    """Batched runs with the Druyvesteyn F0 and a tabulated s(v), FP64."""
+    from fdtd_inputs import cross_section_table
+    from paper_2211_05647_gb300 import Batch
+    specs = _mixed_runs("f64", "f64")
+    tab = cross_section_table()
+    for s in specs:
+        s["plasma"].update(f0_model="druyvesteyn", nu_model="table", s_table=tab)
+    b = Batch(specs)
+    b.step(specs[0]["steps"])
+    for r, sp in enumerate(specs):
+        sim = oracle_sim(oracle_lib, sp)
+        sim.step(sp["steps"])
+        for f in ("ex", "hy"):
+            assert rel_l2(b.read(r, f), sim.get(f)) <= 1e-12, (r, f)
+        if sim.nslots:
+            jr = sim.get("j")
+            den = max(np.linalg.norm(jr), 1e-6 * np.sqrt(jr.size))
+            assert np.linalg.norm(b.read(r, "j") - jr) / den <= 1e-12, r
+
+
 def test_batch_fp32_bit_identical_to_single_runs():
     from paper_2211_05647_gb300 import Batch, Solver
     specs = _mixed_runs("f32", "f32")

@@ -13,7 +13,8 @@ Sizes span several stencil tiles (32 x 8 / 32 x 4 x 2) with ragged tails.
 import numpy as np
 import pytest
 
-from fdtd_inputs import OMEGA0, critical_density, pulse_params, spec_1d_slab, spec_2d_cylinder, spec_3d_slab
+from fdtd_inputs import (OMEGA0, critical_density, cross_section_table, pulse_params, spec_1d_slab, spec_2d_cylinder,
+                         spec_3d_slab)
 from tests.adapters import FIELDS, compare, oracle_sim
 
 pytestmark = pytest.mark.gpu
@@ -89,6 +90,25 @@ def test_3d_slab(oracle_lib, prec, fdt):
     _check(errs, prec, fdt)
 
 
+@pytest.mark.parametrize("ndim,nx,cpml", [(2, 201, 10), (2, 196, 6), (3, 38, 8), (3, 44, 6)])
+def test_fp32_stencil_paths(oracle_lib, ndim, nx, cpml):
+    """FP32 stencils on both code paths: rows that are not a multiple of 4
+    cells run one cell per thread (nx = 201, 38); rows that are run four cells
+    per thread with shuffled x neighbours, here with CPML slabs of 6 cells that
+    end inside a quad (nx = 196, 44)."""
+    if ndim == 2:
+        spec = spec_2d_cylinder(n=nx, ny=131, R=30, cpml=cpml, center=(nx * 0.55, 65), src=(int(nx * 0.55) - 42, 65),
+                                nv=16, nv_perp=8, steps=500, precision="f32", f_dtype="f32", seed=17)
+    else:
+        spec = spec_3d_slab(n=nx, ny=34, nz=60, cpml=cpml, slab=(26, 42), src_k=12, nv=16, steps=400,
+                            precision="f32", f_dtype="f32", seed=19)
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, ndim)
+    _report(f"{ndim}d f32 nx={nx} cpml={cpml}", errs)
+    assert np.abs(sim.get("j")).max() > 0
+    _check(errs, "f32", "f32")
+
+
 @pytest.mark.parametrize("vgrid,nv,nvp", [("speed3d", 31, 1), ("signed1d", 48, 1), ("cart2d", 8, 6),
                                          ("signed1d", 2, 1), ("signed1d", 512, 1)])
 def test_velocity_grids_and_ragged_rows(oracle_lib, vgrid, nv, nvp):
@@ -101,6 +121,35 @@ def test_velocity_grids_and_ragged_rows(oracle_lib, vgrid, nv, nvp):
     assert max(errs.values()) <= 1e-12, errs
     df = s.read("df", device=False)
     assert np.allclose(df, sim.get("df"), rtol=1e-11, atol=1e-12 * np.abs(sim.get("df")).max())
+
+
+@pytest.mark.parametrize("vgrid,nv,nvp", [("signed1d", 48, 1), ("speed3d", 31, 1), ("cart2d", 14, 10)])
+@pytest.mark.parametrize("nu_model", ["nsv", "table"])
+def test_druyvesteyn_and_cross_section_table(oracle_lib, vgrid, nv, nvp, nu_model):
+    """Druyvesteyn F0 (Sec. 5.2) with the N s v collision law, s constant or
+    tabulated (Eq. 23), FP64 on every grid kind against the oracle, whose
+    tables come from its own formulas and quadrature."""
+    spec = spec_1d_slab(nz=400, slab=(150, 260), src_k=40, precision="f64", steps=700, nv=nv)
+    spec["plasma"].update(vgrid=vgrid, nv=nv, nv_perp=nvp, f0_model="druyvesteyn", nu_model=nu_model)
+    if nu_model == "table":
+        spec["plasma"]["s_table"] = cross_section_table(te_ev=spec["plasma"]["te_ev"])
+    s, sim = _run_pair(oracle_lib, spec, spec["steps"])
+    errs = compare(s, sim, 1)
+    _report(f"druyvesteyn {vgrid} {nu_model}", errs)
+    assert np.abs(sim.get("j")).max() > 0
+    assert max(errs.values()) <= 1e-12, errs
+    df = s.read("df", device=False)
+    assert np.allclose(df, sim.get("df"), rtol=1e-11, atol=1e-12 * np.abs(sim.get("df")).max())
+
+
+def test_cross_section_table_rejected_when_malformed():
+    from paper_2211_05647_gb300 import FdtdError
+    spec = spec_1d_slab(nz=200, slab=(80, 120), precision="f32", steps=1, nv=16)
+    sp, sg = cross_section_table()
+    for bad in ((sp[::-1].copy(), sg), (sp, -sg), (sp[:1], sg[:1])):
+        spec["plasma"].update(nu_model="table", s_table=bad)
+        with pytest.raises(FdtdError):
+            _solver(spec)
 
 
 def test_bf16_stochastic_rounding_is_unbiased(oracle_lib):
