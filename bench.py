@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="mma", choices=["mma", "tcgen05"], help="closure MLP engine")
-    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
     return ap.parse_args()
 
 
@@ -65,6 +66,11 @@ def sample_spec(name: str):
     if name.startswith("3d_512"):
         return (spec_3d_slab(n=64, cpml=8, slab=(24, 40), src_k=12),
                 "3-D 64^3, slab z in [24,40) (all lengths / 8), Nv=32")
+    if name.startswith("3d_256"):
+        spec = spec_3d_slab(n=32, cpml=4, slab=(12, 20), src_k=6, f_dtype="f32")
+        if "f0evolve" in name:
+            spec["plasma"].update(vgrid="speed3d", evolve_f0=1, mass_ratio=1.37e-5, tg_ev=0.026)
+        return spec, "3-D 32^3, slab z in [12,20) (all lengths / 8), Nv=32"
     if name.startswith("batch1d"):
         from fdtd_inputs import batch_runs_1d
         return batch_runs_1d(nruns=8, seed=20221114), "8 of the 256 batched 1-D runs (same generator, seed)"
@@ -141,9 +147,11 @@ def measured_peaks():
         return None
 
 
-def kinetic_src_sha() -> str:
+def kinetic_src_sha(kernel: str = "k_kinetic") -> str:
+    """Hash of the sources a kinetic kernel is built from (its ncu figures stay valid while it matches)."""
+    files = ("kinetic.cu", "kinetic_row.cuh") if kernel == "k_kinetic_f0" else ("kinetic_impl.cuh", "kinetic_row.cuh")
     h = hashlib.sha1()
-    for f in ("kinetic_impl.cuh", "kinetic_row.cuh"):
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_2211_05647_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -154,14 +162,14 @@ def ncu_traffic(kernel: str, workload: str, shape=None):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = kinetic_src_sha()
+    sha = kinetic_src_sha(kernel)
     for ln in open(path):
         if ln.startswith("#") or not ln.strip():
             continue
         kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
         if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src_sha") == sha:
             if shape is not None and (int(kv.get("vpl", 0)), int(kv.get("l", 0))) != tuple(shape):
-                return None
+                continue
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -230,6 +238,7 @@ def main():
     cells = cells_of(spec)
     st = s.stream
     tune = None if args.no_autotune else s.autotune()   # untimed: picks the launch shapes
+    shapes = s.launch_shapes()                           # the shapes in use (tuned, cached or default)
 
     def barrier():
         torch.cuda.synchronize()
@@ -302,14 +311,18 @@ def main():
 
     # roofline of the dominant kernel (the kinetic delta-f stream)
     fbytes = {"f32": 4, "bf16": 2, "f64": 8}[spec["plasma"]["f_dtype"]]
-    alg_bytes = 2 * fbytes * ns * nn            # read + write delta f once per node
+    evolve = bool(spec["plasma"].get("evolve_f0"))
+    # read + write delta f once per node (and the F0 correction rows when F0 evolves)
+    alg_bytes = 2 * fbytes * ns * nn * (2 if evolve else 1)
     achieved = alg_bytes / (kt["kinetic"] / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    roof = {"bound": "hbm", "kernel": "k_kinetic", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    kname = "k_kinetic_f0" if evolve else "k_kinetic"
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": ncu_traffic("k_kinetic", args.workload,
-                                   (tune["kin_vpl"], tune["kin_l"]) if tune and tune["kin_vpl"] else (8, 32)),
+            "traffic": ncu_traffic(kname, args.workload,
+                                   None if evolve else
+                                   (shapes["kin_vpl"], shapes["kin_l"]) if shapes["kin_vpl"] else (8, 32)),
             "alg_bytes_per_launch": alg_bytes, "launch_ms": kt["kinetic"],
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
     fb = 8 if s.precision == "f64" else 4
@@ -328,7 +341,7 @@ def main():
             "phase_space_updates_per_s": ps_rate,
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "kernel_ms": kt,
-            "launch_shapes": tune,
+            "launch_shapes": dict(shapes, tuned=tune is not None),
             "roofline": roof,
             "gpu_launches": args.steps * 3 + math.ceil(args.steps / 32) if ns else args.steps * 2 + math.ceil(args.steps / 32),
             "clocks": clk,
@@ -488,7 +501,7 @@ def batch_bench(args, specs, rank, world, local):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if eb == 4 else "f64", "data": "synthetic (seeded run sizes, slabs, densities)",
             "config": {"workload": args.workload, "runs": len(specs), "cells": cells, "phase_space_nodes": nodes,
-                       "f_dtype": fdt, "clusters": info["clusters"], "steps_per_launch": chunk,
+                       "f_dtype": fdt, "clusters": info["clusters"], "ctas_per_cluster": info["cluster_ctas"], "steps_per_launch": chunk,
                        "l2": "inputs larger than L2 (delta f %.2f GB)" % (nodes * fb / 1e9),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "phase_space_updates_per_s": world * nodes * args.steps / (ms / 1e3),

@@ -187,6 +187,11 @@ def closure_training_specs(k=3, steps=2000, seed0=20221200):
 
 
 # The benchmark workloads (full sizes) by name, plus reduced profiling cases
+def _evolving(spec: dict) -> dict:
+    spec["plasma"].update(vgrid="speed3d", evolve_f0=1, mass_ratio=1.37e-5, tg_ev=0.026)
+    return spec
+
+
 WORKLOADS = {
     "1d_slab_fp64": lambda: spec_1d_slab(),
     "1d_slab_fp32": lambda: spec_1d_slab(precision="f32"),
@@ -197,6 +202,9 @@ WORKLOADS = {
     # profiling cases: same recipes at half the lengths (inputs still larger than L2)
     "2d_tmz_2048_kinetic": lambda: spec_2d_cylinder(n=2048, R=256),
     "3d_256_kinetic_bf16": lambda: spec_3d_slab(n=256, slab=(96, 160), src_k=12),
+    # evolving isotropic F0 on the speed grid (Joule heating + elastic collisions with argon, m/M = 1.37e-5,
+    # gas at 0.026 eV), FP32 delta f
+    "3d_256_f0evolve_f32": lambda: _evolving(spec_3d_slab(n=256, slab=(96, 160), src_k=12, f_dtype="f32")),
     "2d_tmz_8192_closure": lambda: spec_closure_8192(),
     "batch1d_256_f32": lambda: batch_runs_1d(),
     "batch1d_256_bf16": lambda: batch_runs_1d(f_dtype="bf16"),

@@ -62,7 +62,8 @@ enum { FDTD_LOC_POINT = 0, FDTD_LOC_SHEET = 1 };
 enum {                                                      /* fdtd_plasma_read_fields "which" */
     FDTD_EX = 0, FDTD_EY, FDTD_EZ, FDTD_HX, FDTD_HY, FDTD_HZ,
     FDTD_J = 6,  /* J^{n+1/2} per plasma slot, field precision */
-    FDTD_DF = 7  /* delta f [slot][node], delta-f storage type, rows packed to nnode */
+    FDTD_DF = 7, /* delta f [slot][node], delta-f storage type, rows packed to nnode */
+    FDTD_F0 = 8  /* evolve_f0: F0 - F0(table) per unit density [slot][node], delta-f storage type */
 };
 
 /* Grid and boundary description (Sec. 2; CPML of Eq. 7-12). */
@@ -124,7 +125,15 @@ typedef struct {
  * f_dtype: FDTD_DF_F32, FDTD_DF_BF16 (FP32 arithmetic, stochastic rounding on
  * store, keyed by seed) or FDTD_DF_F64 (only with FDTD_F64 precision).
  * nonlinear: 1 adds the flux-form advection of delta f in v_par (signed and
- * Cartesian grids only). */
+ * Cartesian grids only).
+ * evolve_f0: 1 lets the isotropic part evolve per cell (speed grid, FP32 or
+ * FP64 delta f, no closure): F0 = F0(table) + g, g per unit density, with the
+ * two-term F0 equation dF0/dt = (e E / (3 m v^2)) d/dv (v^2 F1) + C0(F0),
+ * C0 = (m/M)(1/v^2) d/dv [v^3 nu (F0 + (k Tg/(m v)) dF0/dv)] (elastic
+ * collisions with gas atoms of mass ratio mass_ratio = m/M at temperature
+ * tg_ev), both in flux form on the speed cells (zero flux at 0 and v_max),
+ * heating from the time-centred F1 = delta f / n; the F1 update then uses
+ * F0' = F0'(table) + central differences of g. */
 typedef struct {
     const double *density;
     int32_t density_on_device;
@@ -139,6 +148,9 @@ typedef struct {
     const double *s_speed;     /* FDTD_NU_TABLE only (else ignored) */
     const double *s_sigma;
     int64_t s_n;
+    int32_t evolve_f0;
+    int32_t reserved;
+    double mass_ratio, tg_ev;  /* evolve_f0 only */
 } fdtd_plasma_desc;
 
 /* FP64 diagnostics (computed on the device with FP64 accumulators). */
@@ -369,8 +381,10 @@ int fdtd_batch_step(fdtd_batch_t b, int64_t nsteps);
  * FDTD_DF (packed rows); sizes as fdtd_batch_quantity_bytes. */
 int fdtd_batch_read(fdtd_batch_t b, int32_t run, int which, void *dst, size_t bytes, int dst_is_device);
 size_t fdtd_batch_quantity_bytes(fdtd_batch_t b, int32_t run, int which);
-/* dt, steps done, total cells, total phase-space nodes, clusters launched. */
-int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters);
+/* dt, steps done, total cells, total phase-space nodes, clusters launched and
+ * CTAs per cluster (any pointer may be NULL). */
+int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters,
+                    int32_t *cluster_ctas);
 const char *fdtd_batch_last_error(fdtd_batch_t b);
 void fdtd_batch_destroy(fdtd_batch_t b);
 

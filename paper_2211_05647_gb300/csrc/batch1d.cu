@@ -4,7 +4,9 @@
 // ends), captured in a CUDA graph.
 //
 // Mapping: runs are bin-packed (longest processing time first) onto
-// thread-block clusters of kClusterCtas CTAs; inside a cluster the runs'
+// thread-block clusters of C CTAs (C in {8, 4, 2, 1}, the one whose packing
+// has the smallest largest per-CTA load among the clusters that fit on the
+// GPU at once); inside a cluster the runs'
 // nodes are laid end to end and cut into one contiguous, equal-cost range per
 // CTA.  Per step a CTA updates H on its range, the cluster synchronises
 // (hardware barrier: neighbouring ranges exchange their edge values through
@@ -35,7 +37,6 @@ namespace cg = cooperative_groups;
 
 namespace fp {
 
-constexpr int kClusterCtas = 8;
 constexpr int kBatchThreads = 512;
 
 struct BRun {
@@ -218,7 +219,7 @@ thread_local std::string g_batch_create_error;
 struct fdtd_batch {
     fdtd_runtime_desc rt;
     cudaStream_t stream, cap;
-    int precision, f_dtype, nruns, pitch, nnode, nclusters;
+    int precision, f_dtype, nruns, pitch, nnode, nclusters, cluster_ctas;
     uint64_t seed;
     size_t esz, df_esz;
     double dt, dx;
@@ -280,13 +281,13 @@ cudaError_t launch_t(fdtd_batch *b, cudaStream_t st, int nsteps)
     a.d_step = b->d_step;
     a.nsteps = nsteps;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(b->nclusters * kClusterCtas);
+    cfg.gridDim = dim3(b->nclusters * b->cluster_ctas);
     cfg.blockDim = dim3(kBatchThreads);
     cfg.dynamicSmemBytes = 3 * (size_t)b->pitch * sizeof(T);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.x = b->cluster_ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -297,16 +298,17 @@ cudaError_t launch_t(fdtd_batch *b, cudaStream_t st, int nsteps)
     return cudaGetLastError();
 }
 
+// clusters of `ctas` CTAs that can be resident at once (0: none fits)
 template <typename TS, typename T, int VPL, int L>
-int max_clusters()
+int max_clusters(int ctas)
 {
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(kClusterCtas);
+    cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kBatchThreads);
     cfg.dynamicSmemBytes = 3 * 128 * 16;   // tables of the largest row (128 vectors of 16 bytes)
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kClusterCtas;
+    attr[0].val.clusterDim.x = ctas;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -321,17 +323,17 @@ int max_clusters()
 
 // pick the kernel instance for (storage, precision, vectors per row)
 template <typename TS, typename T>
-bool pick(int V, cudaError_t (**fn)(fdtd_batch *, cudaStream_t, int), int *maxc)
+bool pick(int V, cudaError_t (**fn)(fdtd_batch *, cudaStream_t, int), int (**maxc)(int))
 {
     switch (V) {
-    case 1: *fn = launch_t<TS, T, 1, 1>; *maxc = max_clusters<TS, T, 1, 1>(); return true;
-    case 2: *fn = launch_t<TS, T, 2, 1>; *maxc = max_clusters<TS, T, 2, 1>(); return true;
-    case 4: *fn = launch_t<TS, T, 4, 1>; *maxc = max_clusters<TS, T, 4, 1>(); return true;
-    case 8: *fn = launch_t<TS, T, 4, 2>; *maxc = max_clusters<TS, T, 4, 2>(); return true;
-    case 16: *fn = launch_t<TS, T, 4, 4>; *maxc = max_clusters<TS, T, 4, 4>(); return true;
-    case 32: *fn = launch_t<TS, T, 4, 8>; *maxc = max_clusters<TS, T, 4, 8>(); return true;
-    case 64: *fn = launch_t<TS, T, 4, 16>; *maxc = max_clusters<TS, T, 4, 16>(); return true;
-    case 128: *fn = launch_t<TS, T, 4, 32>; *maxc = max_clusters<TS, T, 4, 32>(); return true;
+    case 1: *fn = launch_t<TS, T, 1, 1>; *maxc = max_clusters<TS, T, 1, 1>; return true;
+    case 2: *fn = launch_t<TS, T, 2, 1>; *maxc = max_clusters<TS, T, 2, 1>; return true;
+    case 4: *fn = launch_t<TS, T, 4, 1>; *maxc = max_clusters<TS, T, 4, 1>; return true;
+    case 8: *fn = launch_t<TS, T, 4, 2>; *maxc = max_clusters<TS, T, 4, 2>; return true;
+    case 16: *fn = launch_t<TS, T, 4, 4>; *maxc = max_clusters<TS, T, 4, 4>; return true;
+    case 32: *fn = launch_t<TS, T, 4, 8>; *maxc = max_clusters<TS, T, 4, 8>; return true;
+    case 64: *fn = launch_t<TS, T, 4, 16>; *maxc = max_clusters<TS, T, 4, 16>; return true;
+    case 128: *fn = launch_t<TS, T, 4, 32>; *maxc = max_clusters<TS, T, 4, 32>; return true;
     default: return false;
     }
 }
@@ -377,7 +379,8 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
             (p.s_n != p0.s_n || !std::equal(p.s_speed, p.s_speed + p.s_n, p0.s_speed) ||
              !std::equal(p.s_sigma, p.s_sigma + p.s_n, p0.s_sigma)))
             return bfail(nullptr, FDTD_ERR_INVAL, "run %d: the s(v) table must match run 0", r);
-        if (p.nonlinear) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nonlinear mode not available in batches", r);
+        if (p.nonlinear || p.evolve_f0)
+            return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nonlinear / evolving-F0 modes not available in batches", r);
         if (!(p.nu0 >= 0) || !std::isfinite(p.nu0)) return bfail(nullptr, FDTD_ERR_INVAL, "run %d: nu0", r);
         const fdtd_source_desc &s = runs[r].source;
         if (s.kind && (s.k < 1 || s.k > g.nz - 1 || !(s.tau > 0)))
@@ -413,12 +416,19 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
     b->pitch = kinetic_pitch(nnode, p0.f_dtype);
     const int vec = p0.f_dtype == FDTD_DF_BF16 ? 8 : (p0.f_dtype == FDTD_DF_F64 ? 2 : 4);
     const int V = b->pitch / vec;
-    int maxc = 0;
-    bool ok = p0.f_dtype == FDTD_DF_F32    ? pick<float, float>(V, &b->launch, &maxc)
-              : p0.f_dtype == FDTD_DF_BF16 ? pick<__nv_bfloat16, float>(V, &b->launch, &maxc)
-                                           : pick<double, double>(V, &b->launch, &maxc);
+    int (*maxc_of)(int) = nullptr;
+    bool ok = p0.f_dtype == FDTD_DF_F32    ? pick<float, float>(V, &b->launch, &maxc_of)
+              : p0.f_dtype == FDTD_DF_BF16 ? pick<__nv_bfloat16, float>(V, &b->launch, &maxc_of)
+                                           : pick<double, double>(V, &b->launch, &maxc_of);
     if (!ok) return bail(FDTD_ERR_INVAL, "too many velocity nodes for the batched kernel (at most 128 vectors)");
-    if (maxc < 1) return bail(FDTD_ERR_CUDA, "no cluster of the batched kernel fits on this device");
+    int maxc_c[4];
+    const int csizes[4] = {8, 4, 2, 1};
+    bool any = false;
+    for (int i = 0; i < 4; ++i) {
+        maxc_c[i] = maxc_of(csizes[i]);
+        any = any || maxc_c[i] > 0;
+    }
+    if (!any) return bail(FDTD_ERR_CUDA, "no cluster of the batched kernel fits on this device");
 
     // ---- velocity tables (shared node weights; per-run alpha, beta from nu0_r)
     VTab vt;
@@ -482,22 +492,45 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
     if (std::pow(wp * b->dt / 2, 2) + g0.courant * g0.courant >= 1.0)
         return bail(FDTD_ERR_UNSTABLE, "plasma frequency too high for dt");
 
-    // ---- bin packing: runs -> clusters (LPT), then equal-cost CTA ranges
+    // ---- bin packing: runs -> clusters (LPT), then equal-cost CTA ranges.  Every cluster size
+    // that fits is packed; the one with the smallest largest per-CTA load (bin load / cluster
+    // size) is kept, larger clusters winning ties.
     const double cell_cost = 4.0 * b->esz, node_cost = 2.0 * nnode * b->df_esz + 20.0;
     std::vector<double> cost(nruns);
     for (int r = 0; r < nruns; ++r) cost[r] = cell_cost * (b->nz[r] + 1) + node_cost * b->nslot[r];
-    const int nb = std::max(1, std::min(maxc, nruns));
     std::vector<int> order(nruns);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    std::vector<std::vector<int>> bins(nb);
-    std::vector<double> load(nb, 0.0);
-    for (int r : order) {
-        int bi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        bins[bi].push_back(r);
-        load[bi] += cost[r];
+    auto pack = [&](int nb, std::vector<std::vector<int>> &bins, std::vector<double> &load) {
+        bins.assign(nb, {});
+        load.assign(nb, 0.0);
+        for (int r : order) {
+            int bi = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            bins[bi].push_back(r);
+            load[bi] += cost[r];
+        }
+        return *std::max_element(load.begin(), load.end());
+    };
+    std::vector<std::vector<int>> bins;
+    std::vector<double> load;
+    double best = 0.0;
+    int nb = 0, csize = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (maxc_c[i] < 1) continue;
+        const int n = std::max(1, std::min(maxc_c[i], nruns));
+        std::vector<std::vector<int>> bb;
+        std::vector<double> ll;
+        const double span = pack(n, bb, ll) / csizes[i];
+        if (csize == 0 || span < best * (1.0 - 1e-9)) {
+            best = span;
+            nb = n;
+            csize = csizes[i];
+            bins.swap(bb);
+            load.swap(ll);
+        }
     }
     b->nclusters = nb;
+    b->cluster_ctas = csize;
     std::vector<BSeg> segs;
     std::vector<int32_t> cta_seg0;
     // slot index (run-local) of the first slot at node >= k
@@ -512,7 +545,7 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
         }
     }
     for (int bi = 0; bi < nb; ++bi) {
-        // per-node cost along the bin's concatenated nodes, cut into kClusterCtas ranges
+        // per-node cost along the bin's concatenated nodes, cut into csize ranges
         const double total = load[bi];
         double acc = 0;
         int cta = 0;
@@ -526,10 +559,10 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
                 while (si < b->nslot[r] && nodes[si] < k) ++si;
                 const bool plasma = si < b->nslot[r] && nodes[si] == k;
                 acc += cell_cost + (plasma ? node_cost : 0.0);
-                const double target = total * (cta + 1) / kClusterCtas;
+                const double target = total * (cta + 1) / csize;
                 // a cut after node k (range [k0, k+1)); never between 0|1 or nz-1|nz
                 const int64_t cut = k + 1;
-                if (acc >= target && cta < kClusterCtas - 1 && cut != 1 && cut != nz && cut <= nz) {
+                if (acc >= target && cta < csize - 1 && cut != 1 && cut != nz && cut <= nz) {
                     segs.push_back(BSeg{r, (int32_t)k0, (int32_t)cut, slot_at[r][k0], slot_at[r][cut]});
                     k0 = cut;
                     ++cta;
@@ -538,7 +571,7 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
             }
             if (k0 <= nz) segs.push_back(BSeg{r, (int32_t)k0, (int32_t)(nz + 1), slot_at[r][k0], slot_at[r][nz + 1]});
         }
-        while (cta < kClusterCtas - 1) {   // CTAs left without nodes
+        while (cta < csize - 1) {   // CTAs left without nodes
             ++cta;
             cta_seg0.push_back((int32_t)segs.size());
         }
@@ -656,7 +689,8 @@ int fdtd_batch_read(fdtd_batch_t b, int32_t run, int which, void *dst, size_t by
     return FDTD_OK;
 }
 
-int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters)
+int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters,
+                    int32_t *cluster_ctas)
 {
     if (!b) return FDTD_ERR_INVAL;
     if (dt) *dt = b->dt;
@@ -668,6 +702,7 @@ int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, 
     }
     if (nodes) *nodes = b->nrows * b->nnode;
     if (nclusters) *nclusters = b->nclusters;
+    if (cluster_ctas) *cluster_ctas = b->cluster_ctas;
     return FDTD_OK;
 }
 

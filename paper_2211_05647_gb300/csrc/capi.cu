@@ -140,8 +140,9 @@ void free_plasma(fdtd_plasma *h)
 {
     free_closure(h);
     dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot); dfree(h, h->tab);
-    dfree(h, h->dV);
+    dfree(h, h->dV); dfree(h, h->g0); dfree(h, h->tab_f0);
     h->slot_cell = nullptr; h->dens = h->df = h->jslot = h->tab = nullptr; h->dV = nullptr;
+    h->g0 = h->tab_f0 = nullptr;
     h->has_plasma = 0;
     h->nslots = 0;
     h->nkin = 0;
@@ -352,7 +353,21 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
     if (h->has_plasma && h->nkin > 0) {
         const KinArgs<T> a = kin_args<T>(h, kstep);
         cudaError_t e;
-        if (h->pl.nonlinear) {
+        if (h->pl.evolve_f0) {
+            const double vth = std::sqrt(kQe * h->pl.te_ev / kMe);
+            const double gam = h->pl.vmax_vth * vth / h->pl.nv;
+            F0Args<T> f{};
+            f.tab = reinterpret_cast<const T *>(h->tab_f0);
+            f.g = reinterpret_cast<T *>(h->g0);
+            f.nv = h->pl.nv;
+            f.gam = (T)gam;
+            f.inv2gam = (T)(1.0 / (2.0 * gam));
+            f.qm3 = (T)(kQe / kMe / 3.0);
+            f.mr = (T)h->pl.mass_ratio;
+            f.kTg_m = (T)(kQe * h->pl.tg_ev / kMe);
+            f.dt = (T)h->dt;
+            e = launch_kinetic_f0<T>(st, a, f, h->num_sms);
+        } else if (h->pl.nonlinear) {
             const double vth = std::sqrt(kQe * h->pl.te_ev / kMe);
             const double dvpar = 2.0 * h->pl.vmax_vth * vth / h->pl.nv;
             const int nperp = h->pl.vgrid == FDTD_VGRID_CART2D ? h->pl.nv_perp : 1;
@@ -606,6 +621,7 @@ int fdtd_plasma_reset(fdtd_plasma_t h)
         if (h->psi[q]) CK(h, cudaMemsetAsync(h->psi[q], 0, h->psilen[q] * h->esz, h->stream));
     if (h->has_plasma) {
         CK(h, cudaMemsetAsync(h->df, 0, (size_t)h->nkin * h->pitch * h->df_esz, h->stream));
+        if (h->g0) CK(h, cudaMemsetAsync(h->g0, 0, (size_t)h->nkin * h->pitch * h->df_esz, h->stream));
         CK(h, cudaMemsetAsync(h->jslot, 0, (size_t)(h->nslots ? h->nslots : 1) * h->esz, h->stream));
     }
     if (h->hist) CK(h, cudaMemsetAsync(h->hist, 0, (size_t)(h->has_closure ? h->ncl : h->nslots) * 16 * 4, h->stream));
@@ -666,6 +682,11 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
         return fail(h, FDTD_ERR_INVAL, "f_dtype does not match the field precision");
     if (p->nonlinear && (p->vgrid == FDTD_VGRID_SPEED3D || p->f_dtype == FDTD_DF_BF16))
         return fail(h, FDTD_ERR_INVAL, "the nonlinear mode needs a v_par grid (signed or Cartesian) and FP32/FP64 delta f");
+    if (p->evolve_f0 && (p->vgrid != FDTD_VGRID_SPEED3D || p->f_dtype == FDTD_DF_BF16 || p->nonlinear))
+        return fail(h, FDTD_ERR_INVAL, "evolve_f0 needs the speed grid and FP32/FP64 delta f (not the nonlinear mode)");
+    if (p->evolve_f0 && (!(p->mass_ratio >= 0) || !std::isfinite(p->mass_ratio) || !(p->tg_ev >= 0) ||
+                         !std::isfinite(p->tg_ev)))
+        return fail(h, FDTD_ERR_INVAL, "evolve_f0: mass_ratio and tg_ev must be finite and >= 0");
     const int64_t nnode = p->vgrid == FDTD_VGRID_CART2D ? (int64_t)p->nv * p->nv_perp : p->nv;
     const int pitch = kinetic_pitch((int)nnode, p->f_dtype);
     const int vec = p->f_dtype == FDTD_DF_BF16 ? 8 : (p->f_dtype == FDTD_DF_F64 ? 2 : 4);
@@ -704,6 +725,28 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
         tab[pitch + j] = 2.0 * h->dt * (kQe / kMe) * t.f0p[j] / (2.0 + h->dt * nu);
         tab[2 * pitch + j] = -kQe * t.w[j];
     }
+    // evolve_f0 tables (padding 0): f0, f0', bq = 2 dt (e/m) / (2 + dt nu), v^3, 1/(v^2 gam), and for
+    // the upper cell edge v_e = (j+1) gam of each node but the last: 1/(2 v_e), (m/M) v_e^3 nu_e
+    // (nu_e the mean of the two nodes), k Tg / (m v_e gam)
+    std::vector<double> tabf0(p->evolve_f0 ? 8 * (size_t)pitch : 0, 0.0);
+    if (p->evolve_f0) {
+        const double gam = 2.0 * t.v[0];
+        const double kTg_m = kQe * p->tg_ev / kMe;
+        for (int64_t j = 0; j < nnode; ++j) {
+            const double v = t.v[j];
+            tabf0[j] = t.f0[j];
+            tabf0[pitch + j] = t.f0p[j];
+            tabf0[2 * pitch + j] = 2.0 * h->dt * (kQe / kMe) / (2.0 + h->dt * t.nu[j]);
+            tabf0[3 * pitch + j] = v * v * v;
+            tabf0[4 * pitch + j] = 1.0 / (v * v * gam);
+            if (j + 1 < nnode) {
+                const double ve = (double)(j + 1) * gam;
+                tabf0[5 * pitch + j] = 1.0 / (2.0 * ve);
+                tabf0[6 * pitch + j] = p->mass_ratio * ve * ve * ve * 0.5 * (t.nu[j] + t.nu[j + 1]);
+                tabf0[7 * pitch + j] = kTg_m / (ve * gam);
+            }
+        }
+    }
 
     drop_graphs(h);
     free_plasma(h);
@@ -722,7 +765,12 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     h->jslot = dalloc(h, (ns ? ns : 1) * h->esz);
     h->tab = dalloc(h, tab.size() * h->esz);
     h->dV = (double *)dalloc(h, nnode * 8);
-    if (!h->slot_cell || !h->dens || !h->df || !h->jslot || !h->tab || !h->dV) {
+    if (p->evolve_f0) {
+        h->g0 = dalloc(h, (ns ? ns : 1) * pitch * h->df_esz);
+        h->tab_f0 = dalloc(h, 8 * (size_t)pitch * h->esz);
+    }
+    if (!h->slot_cell || !h->dens || !h->df || !h->jslot || !h->tab || !h->dV ||
+        (p->evolve_f0 && (!h->g0 || !h->tab_f0))) {
         free_plasma(h);
         return fail(h, FDTD_ERR_NOMEM, "plasma allocation failed (%zu cells x %d nodes)", ns, pitch);
     }
@@ -742,6 +790,15 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
         CK(h, cudaMemcpy(h->tab, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
     }
     CK(h, cudaMemcpy(h->dV, t.dV.data(), nnode * 8, cudaMemcpyHostToDevice));
+    if (p->evolve_f0) {
+        if (h->esz == 8) {
+            CK(h, cudaMemcpy(h->tab_f0, tabf0.data(), tabf0.size() * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> t32(tabf0.begin(), tabf0.end());
+            CK(h, cudaMemcpy(h->tab_f0, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
+        }
+        CK(h, cudaMemsetAsync(h->g0, 0, (ns ? ns : 1) * pitch * h->df_esz, h->stream));
+    }
     CK(h, cudaMemsetAsync(h->df, 0, (ns ? ns : 1) * pitch * h->df_esz, h->stream));
     CK(h, cudaMemsetAsync(h->jslot, 0, (ns ? ns : 1) * h->esz, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -782,6 +839,7 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
     if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "set_closure needs a plasma (set_plasma first)");
     if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_closure after stepping: call fdtd_plasma_reset first");
     if (h->g.precision != FDTD_F32) return fail(h, FDTD_ERR_INVAL, "the closure runs on FP32 grids");
+    if (h->pl.evolve_f0) return fail(h, FDTD_ERR_INVAL, "the closure replaces a fixed-F0 plasma (evolve_f0 is set)");
     if (!(c->e_scale > 0) || !(c->n_scale > 0) || !std::isfinite(c->j_scale) || !std::isfinite(c->rho) ||
         !std::isfinite(c->beta) ||
         !(c->n_train_max >= 0))
@@ -932,7 +990,7 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
     }
     out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = 0;
     out->kin_ms = 0;
-    if (h->has_plasma && h->nkin > 0 && !h->pl.nonlinear) {
+    if (h->has_plasma && h->nkin > 0 && !h->pl.nonlinear && !h->pl.evolve_f0) {
         int cand[8][2];
         const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
         const KinArgs<T> a = kin_args<T>(h, 0);
@@ -1021,6 +1079,7 @@ size_t fdtd_plasma_quantity_bytes(fdtd_plasma_t h, int which)
     if (which >= 0 && which <= 5) return field_bytes(h, which);
     if (which == FDTD_J) return h->has_plasma ? (size_t)h->nslots * h->esz : 0;
     if (which == FDTD_DF) return h->has_plasma ? (size_t)h->nkin * h->nnode * h->df_esz : 0;
+    if (which == FDTD_F0) return h->has_plasma && h->g0 ? (size_t)h->nkin * h->nnode * h->df_esz : 0;
     return 0;
 }
 
@@ -1032,12 +1091,13 @@ static int copy_quantity(fdtd_plasma_t h, int which, void *host_or_dev, size_t b
     if (bytes != need) return fail(h, FDTD_ERR_INVAL, "quantity %d needs %zu bytes, got %zu", which, need, bytes);
     const cudaMemcpyKind kind = out ? (is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost)
                                     : (is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
-    if (which == FDTD_DF) {
+    if (which == FDTD_DF || which == FDTD_F0) {
+        void *rows = which == FDTD_DF ? h->df : h->g0;
         const size_t row = (size_t)h->nnode * h->df_esz, dpitch = (size_t)h->pitch * h->df_esz;
         if (out)
-            CK(h, cudaMemcpy2DAsync(host_or_dev, row, h->df, dpitch, row, h->nkin, kind, h->stream));
+            CK(h, cudaMemcpy2DAsync(host_or_dev, row, rows, dpitch, row, h->nkin, kind, h->stream));
         else
-            CK(h, cudaMemcpy2DAsync(h->df, dpitch, host_or_dev, row, row, h->nkin, kind, h->stream));
+            CK(h, cudaMemcpy2DAsync(rows, dpitch, host_or_dev, row, row, h->nkin, kind, h->stream));
     } else {
         void *dev = which == FDTD_J ? h->jslot : h->f[which];
         if (out) CK(h, cudaMemcpyAsync(host_or_dev, dev, bytes, kind, h->stream));
@@ -1227,6 +1287,7 @@ static size_t state_parts(fdtd_plasma_t h, std::vector<std::pair<void *, size_t>
         if (h->psi[q]) parts.push_back({h->psi[q], (size_t)h->psilen[q] * h->esz});
     if (h->has_plasma && h->nslots) {
         if (h->nkin) parts.push_back({h->df, (size_t)h->nkin * h->pitch * h->df_esz});
+        if (h->nkin && h->g0) parts.push_back({h->g0, (size_t)h->nkin * h->pitch * h->df_esz});
         parts.push_back({h->jslot, (size_t)h->nslots * h->esz});
     }
     const int64_t nh = h->has_closure ? h->ncl : (h->has_recording ? h->nslots : 0);

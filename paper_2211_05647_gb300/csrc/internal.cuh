@@ -66,6 +66,21 @@ struct KinArgs {
     int kstep;                 // step offset inside the chunk
 };
 
+// Isotropic-F0 evolution (speed grid): per-node tables, each `pitch` long,
+// [f0 | f0' | bq | v^3 | 1/(v^2 gam) | 1/(2 v_e) | (m/M) v_e^3 nu_e | k Tg/(m v_e gam)]
+// with bq = 2 dt (e/m) / (2 + dt nu) and v_e the node's upper cell edge (edge
+// entries 0 at and past the last node); g = F0 - F0(table) rows.
+template <typename TA>
+struct F0Args {
+    const TA *tab;
+    TA *g;
+    int nv;
+    TA gam, inv2gam;   // speed-cell width and 1 / (2 gam)
+    TA qm3;            // e / (3 m)
+    TA mr, kTg_m;      // m / M, k Tg / m
+    TA dt;
+};
+
 // ---------------------------------------------------------- compensated sums
 
 // Knuth TwoSum: s + e == a + b exactly (round-to-nearest, no contraction).
@@ -137,6 +152,8 @@ template <typename TA>
 cudaError_t launch_kinetic(cudaStream_t st, const KinArgs<TA> &a, int f_dtype, int num_sms, int vpl = 0, int l = 0,
                            int bps = 0);
 // nonlinear mode (FP32 / FP64 storage): npar x nperp nodes, v_par spacing dvpar, qm = e/m
+template <typename T>
+cudaError_t launch_kinetic_f0(cudaStream_t st, const KinArgs<T> &a, const F0Args<T> &f, int num_sms);
 template <typename T>
 cudaError_t launch_kinetic_nl(cudaStream_t st, const KinArgs<T> &a, int npar, int nperp, double dvpar, double qm,
                               double dt, int num_sms);
@@ -247,6 +264,7 @@ struct fdtd_plasma {
     int pitch;
     int32_t *slot_cell;
     void *dens, *df, *jslot, *tab;
+    void *g0, *tab_f0;        // evolve_f0: F0 correction rows and the F0 tables
     double *dV;               // per node (FP64) for the diagnostics
     size_t df_esz;
     int64_t nkin;             // slots [0, nkin) take the kinetic update (all, unless a closure is set)

@@ -166,4 +166,264 @@ template cudaError_t launch_kinetic_nl<float>(cudaStream_t, const KinArgs<float>
 template cudaError_t launch_kinetic_nl<double>(cudaStream_t, const KinArgs<double> &, int, int, double, double,
                                                double, int);
 
+// --------------------------------------------------------- evolving F0
+// Speed grid with an evolving isotropic part (the F0 equation of the two-term
+// expansion, Sec. 5.2).  Per row, with E = E^n:
+//   F0' = F0'(table) + (g_{k+1} - g_{k-1}) / (2 gam)   (g mirrored at v = 0, 0 past the last node)
+//   F1  <- alpha F1 + bq F0' n E,   J = sum w' F1 (TwoSum), E -= dt/eps0 J
+//   g   += dt [ (e E / 3m) (Phi_{k+1/2} - Phi_{k-1/2}) + (Psi_{k+1/2} - Psi_{k-1/2}) ] / (v_k^2 gam)
+// with the heating flux Phi = (a_k + a_{k+1}) / (2 v_{k+1/2}), a = v^3 (F1_old + F1_new) / (2n), and
+// the elastic flux Psi = (m/M) v^3 nu (F0 + (k Tg/(m v)) dF0/dv) at the cell edge, both zero at
+// v = 0 and past the last node.  The F0 table holds, per node, [f0 | f0' | bq | v^3 | 1/(v^2 gam) |
+// 1/(2 v_e) | (m/M) v_e^3 nu_e | k Tg/(m v_e gam)] with v_e the node's upper edge (edge entries 0 at
+// and past the last node), so the kernels multiply only.
+//
+// Fast kernel: L lanes per row, each lane owns one 16-byte vector of VEC consecutive nodes; the
+// neighbours one node across a lane boundary come from segment shuffles.  Bytes per node: delta f
+// and g, each read and written once (streaming).
+
+template <typename T>
+struct F0Tab {
+    const T *al, *w, *f0, *f0p, *bq, *v3, *ivg, *e1, *c1, *c2;
+};
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256) k_kinetic_f0(KinArgs<T> a, F0Args<T> f)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = a.pitch;
+    T *s = reinterpret_cast<T *>(smem_raw);
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        s[t] = a.tab[t];               // alpha
+        s[P + t] = a.tab[2 * P + t];   // w' = -e w
+    }
+    for (int t = threadIdx.x; t < 8 * P; t += blockDim.x) s[2 * P + t] = f.tab[t];
+    __syncthreads();
+    const F0Tab<T> tb{s, s + P, s + 2 * P, s + 3 * P, s + 4 * P, s + 5 * P, s + 6 * P, s + 7 * P, s + 8 * P, s + 9 * P};
+
+    using V = typename Vec<T>::type;
+    constexpr int VEC = Vec<T>::n;
+    constexpr int R = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / L, l = lane % L;
+    const int k0 = l * VEC;            // first node of this lane
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int k1 = k0 + VEC < P ? k0 + VEC : k0;   // one node past the lane (its edge entries are 0 at the end)
+    V *df = reinterpret_cast<V *>(a.df);
+    V *gv = reinterpret_cast<V *>(f.g);
+    const int vpr = P / VEC;
+
+    int64_t row = wg * R + sub;
+    int32_t cell_next = row < a.nslots ? __ldg(a.slot_cell + row) : 0;
+    for (int64_t base = wg * R; base < a.nslots; base += nw * R) {
+        row = base + sub;
+        const bool valid = row < a.nslots;
+        const int32_t cell = cell_next;
+        const int64_t ri = (valid ? row : 0) * vpr + l;
+        T x[VEC], g[VEC];
+        T E = T(0), n = T(1);
+        if (valid) {
+            unpack(__ldcs(df + ri), x);
+            unpack(__ldcs(gv + ri), g);
+            E = a.E[cell];
+            n = __ldg(a.dens + row);
+        } else {
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) x[t] = g[t] = T(0);
+        }
+        const int64_t row_next = row + nw * R;
+        cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
+        // g one node to the left / right of the lane's vector
+        T gl = __shfl_up_sync(0xffffffffu, g[VEC - 1], 1, L);
+        T gr = __shfl_down_sync(0xffffffffu, g[0], 1, L);
+        if (l == 0) gl = g[0];         // mirror at v = 0
+        if (l == L - 1) gr = T(0);     // past the last node
+        const T nE = n * E;
+        T xn[VEC], sum = T(0), cmp = T(0);
+        {
+            T al[VEC], w[VEC], bq[VEC], f0p[VEC];
+            lds<VEC>(tb.al + k0, al); lds<VEC>(tb.w + k0, w); lds<VEC>(tb.bq + k0, bq); lds<VEC>(tb.f0p + k0, f0p);
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) {
+                const T gm = t > 0 ? g[t - 1] : gl, gp = t + 1 < VEC ? g[t + 1] : gr;
+                xn[t] = al[t] * x[t] + bq[t] * (f0p[t] + (gp - gm) * f.inv2gam) * nE;
+                T hi, lo;
+                two_sum(sum, mul_rn(w[t], xn[t]), hi, lo);
+                sum = hi;
+                cmp += lo;
+            }
+        }
+        // heating and collision fluxes through each node's upper edge
+        const T inv_n = T(1) / n;
+        T av[VEC];
+        {
+            T v3[VEC];
+            lds<VEC>(tb.v3 + k0, v3);
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) av[t] = v3[t] * T(0.5) * (x[t] + xn[t]) * inv_n;
+        }
+        T a_r = __shfl_down_sync(0xffffffffu, av[0], 1, L);
+        if (l == L - 1) a_r = T(0);
+        T phi[VEC], psi[VEC];
+        {
+            T f0[VEC], e1[VEC], c1[VEC], c2[VEC];
+            lds<VEC>(tb.f0 + k0, f0); lds<VEC>(tb.e1 + k0, e1); lds<VEC>(tb.c1 + k0, c1); lds<VEC>(tb.c2 + k0, c2);
+            const T f0_next = tb.f0[k1];
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) {
+                const T an = t + 1 < VEC ? av[t + 1] : a_r;
+                phi[t] = (av[t] + an) * e1[t];
+                const T F0k = f0[t] + g[t];
+                const T F0k1 = (t + 1 < VEC ? f0[t + 1] + g[t + 1] : f0_next + gr);
+                psi[t] = c1[t] * (T(0.5) * (F0k + F0k1) + c2[t] * (F0k1 - F0k));
+            }
+        }
+        T phi_l = __shfl_up_sync(0xffffffffu, phi[VEC - 1], 1, L);
+        T psi_l = __shfl_up_sync(0xffffffffu, psi[VEC - 1], 1, L);
+        if (l == 0) phi_l = psi_l = T(0);
+        const T qE = f.qm3 * E;
+        T gn[VEC];
+        {
+            T ivg[VEC];
+            lds<VEC>(tb.ivg + k0, ivg);
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) {
+                const T pl = t > 0 ? phi[t - 1] : phi_l, ql = t > 0 ? psi[t - 1] : psi_l;
+                gn[t] = g[t] + f.dt * (qE * (phi[t] - pl) + (psi[t] - ql)) * ivg[t];
+            }
+        }
+        const T J = row_reduce<T, L>(sum, cmp);
+        if (valid) {
+            Store<T>::st(df + ri, xn, uint4{}, uint2{});
+            Store<T>::st(gv + ri, gn, uint4{}, uint2{});
+            if (l == 0) {
+                a.jslot[row] = J;
+                a.E[cell] = E - a.cj * J;
+            }
+        }
+    }
+}
+
+// Rows of more than 32 vectors: one warp per row, rows staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kinetic_f0_wide(KinArgs<T> a, F0Args<T> f)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int P = a.pitch, nv = f.nv;
+    T *s = reinterpret_cast<T *>(smem_raw);
+    for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        s[t] = a.tab[t];
+        s[P + t] = a.tab[2 * P + t];
+    }
+    for (int t = threadIdx.x; t < 8 * P; t += blockDim.x) s[2 * P + t] = f.tab[t];
+    __syncthreads();
+    const F0Tab<T> tb{s, s + P, s + 2 * P, s + 3 * P, s + 4 * P, s + 5 * P, s + 6 * P, s + 7 * P, s + 8 * P, s + 9 * P};
+    T *s_old = s + 10 * P + (threadIdx.x >> 5) * 4 * P, *s_new = s_old + P, *s_g = s_new + P, *s_ph = s_g + P;
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    T *df = reinterpret_cast<T *>(a.df);
+    for (int64_t row = wg; row < a.nslots; row += nw) {
+        const int32_t cell = a.slot_cell[row];
+        const T E = a.E[cell];
+        const T n = a.dens[row];
+        T *d = df + row * P, *g = f.g + row * P;
+        for (int j = lane; j < P; j += 32) {
+            s_old[j] = d[j];
+            s_g[j] = g[j];
+        }
+        __syncwarp();
+        T sum = T(0), cmp = T(0);
+        for (int j = lane; j < P; j += 32) {
+            const T gm = j > 0 ? s_g[j - 1] : s_g[0];
+            const T gp = j + 1 < nv ? s_g[j + 1] : T(0);
+            const T xv = tb.al[j] * s_old[j] + tb.bq[j] * (tb.f0p[j] + (gp - gm) * f.inv2gam) * (n * E);
+            s_new[j] = xv;
+            T hi, lo;
+            two_sum(sum, mul_rn(tb.w[j], xv), hi, lo);
+            sum = hi;
+            cmp += lo;
+        }
+        __syncwarp();
+        const T J = row_reduce<T, 32>(sum, cmp);
+        const T inv_n = T(1) / n;
+        // fluxes through the upper edge of each node: heating into s_ph, collisions kept per lane
+        for (int j = lane; j < P; j += 32) {
+            const T a0 = tb.v3[j] * T(0.5) * (s_old[j] + s_new[j]) * inv_n;
+            const T a1 = j + 1 < P ? tb.v3[j + 1] * T(0.5) * (s_old[j + 1] + s_new[j + 1]) * inv_n : T(0);
+            s_ph[j] = (a0 + a1) * tb.e1[j];
+        }
+        __syncwarp();
+        for (int j = lane; j < P; j += 32) {
+            auto psi = [&](int k) -> T {
+                const T F0k = tb.f0[k] + s_g[k];
+                const T F0k1 = k + 1 < P ? tb.f0[k + 1] + s_g[k + 1] : T(0);
+                return tb.c1[k] * (T(0.5) * (F0k + F0k1) + tb.c2[k] * (F0k1 - F0k));
+            };
+            const T pr = s_ph[j], pl = j > 0 ? s_ph[j - 1] : T(0);
+            const T qr = psi(j), ql = j > 0 ? psi(j - 1) : T(0);
+            g[j] = s_g[j] + f.dt * (f.qm3 * E * (pr - pl) + (qr - ql)) * tb.ivg[j];
+            d[j] = s_new[j];
+        }
+        if (lane == 0) {
+            a.jslot[row] = J;
+            a.E[cell] = E - a.cj * J;
+        }
+        __syncwarp();   // the next row reuses the staging rows
+    }
+}
+
+template <typename T, int L>
+cudaError_t run_kinetic_f0(cudaStream_t st, const KinArgs<T> &a, const F0Args<T> &f, int num_sms)
+{
+    const size_t smem = 10 * (size_t)a.pitch * sizeof(T);
+    auto kern = k_kinetic_f0<T, L>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t rows_per_block = 8 * (32 / L);
+    int64_t blocks = (a.nslots + rows_per_block - 1) / rows_per_block;
+    blocks = std::min<int64_t>(blocks, (int64_t)num_sms * std::max(per_sm, 1));
+    kern<<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, st>>>(a, f);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_kinetic_f0(cudaStream_t st, const KinArgs<T> &a, const F0Args<T> &f, int num_sms)
+{
+    if (a.nslots == 0) return cudaSuccess;
+    const int V = a.pitch / Vec<T>::n;   // vectors per row (a power of two)
+    switch (V) {
+    case 1: return run_kinetic_f0<T, 1>(st, a, f, num_sms);
+    case 2: return run_kinetic_f0<T, 2>(st, a, f, num_sms);
+    case 4: return run_kinetic_f0<T, 4>(st, a, f, num_sms);
+    case 8: return run_kinetic_f0<T, 8>(st, a, f, num_sms);
+    case 16: return run_kinetic_f0<T, 16>(st, a, f, num_sms);
+    case 32: return run_kinetic_f0<T, 32>(st, a, f, num_sms);
+    default: break;
+    }
+    const size_t smem = (10 + 8 * 4) * (size_t)a.pitch * sizeof(T);
+    auto kern = k_kinetic_f0_wide<T>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;   // row too long for shared memory
+    int64_t blocks = (a.nslots + 7) / 8;
+    blocks = std::min<int64_t>(blocks, (int64_t)num_sms * per_sm);
+    kern<<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, st>>>(a, f);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_kinetic_f0<float>(cudaStream_t, const KinArgs<float> &, const F0Args<float> &, int);
+template cudaError_t launch_kinetic_f0<double>(cudaStream_t, const KinArgs<double> &, const F0Args<double> &, int);
+
 }  // namespace fp

@@ -28,7 +28,7 @@ NU_MODEL = {"nsv": 0, "const": 1, "table": 2}
 F0_MODEL = {"maxwell": 0, "druyvesteyn": 1}
 SRC_KIND = {"none": 0, "gauss_sine": 1, "gauss": 2}
 SRC_LOC = {"point": 0, "sheet": 1}
-QUANTITY = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7}
+QUANTITY = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7, "f0": 8}
 
 
 class FdtdError(RuntimeError):
@@ -69,7 +69,9 @@ class fdtd_plasma_desc(ctypes.Structure):
                 ("te_ev", ctypes.c_double), ("vmax_vth", ctypes.c_double), ("nu0", ctypes.c_double),
                 ("nu_model", ctypes.c_int32), ("f_dtype", ctypes.c_int32), ("nonlinear", ctypes.c_int32),
                 ("f0_model", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("s_speed", ctypes.c_void_p), ("s_sigma", ctypes.c_void_p), ("s_n", ctypes.c_int64)]
+                ("s_speed", ctypes.c_void_p), ("s_sigma", ctypes.c_void_p), ("s_n", ctypes.c_int64),
+                ("evolve_f0", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mass_ratio", ctypes.c_double), ("tg_ev", ctypes.c_double)]
 
 
 class fdtd_diag(ctypes.Structure):
@@ -168,7 +170,7 @@ SIGNATURES = {
     "fdtd_batch_quantity_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int]),
     "fdtd_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
-                                       ctypes.POINTER(ctypes.c_int32)]),
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "fdtd_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "fdtd_batch_destroy": (None, [ctypes.c_void_p]),
     "fdtd_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(fdtd_diag_arrays), ctypes.POINTER(ctypes.c_double),
@@ -249,7 +251,8 @@ def _source_desc(kind="gauss_sine", location="point", amp=1.0, fc=0.0, tau=1.0, 
 
 
 def _plasma_desc(density_ptr, on_device, vgrid="signed1d", nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0,
-                 nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0, f0_model="maxwell", s_table=None):
+                 nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0, f0_model="maxwell", s_table=None,
+                 evolve_f0=0, mass_ratio=0.0, tg_ev=0.0):
     """Returns (descriptor, arrays the descriptor points into: keep them alive
     until the create / set_plasma call has returned)."""
     d = fdtd_plasma_desc()
@@ -258,6 +261,7 @@ def _plasma_desc(density_ptr, on_device, vgrid="signed1d", nv=64, nv_perp=1, te_
     d.te_ev, d.vmax_vth, d.nu0 = float(te_ev), float(vmax_vth), float(nu0)
     d.nu_model, d.f_dtype, d.nonlinear = NU_MODEL[nu_model], DF_DTYPE[f_dtype], int(nonlinear)
     d.f0_model = F0_MODEL[f0_model]
+    d.evolve_f0, d.mass_ratio, d.tg_ev = int(evolve_f0), float(mass_ratio), float(tg_ev)
     d.seed = int(seed)
     keep = ()
     if s_table is not None:
@@ -382,10 +386,12 @@ class Batch:
         self._check(self.lib.fdtd_batch_step(self.h, int(n)))
 
     def info(self) -> dict:
-        dt, st, c, nd, ncl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        dt, st, c, nd = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        ncl, cc = ctypes.c_int32(), ctypes.c_int32()
         self._check(self.lib.fdtd_batch_info(self.h, ctypes.byref(dt), ctypes.byref(st), ctypes.byref(c),
-                                             ctypes.byref(nd), ctypes.byref(ncl)))
-        return dict(dt=dt.value, steps=st.value, cells=c.value, nodes=nd.value, clusters=ncl.value)
+                                             ctypes.byref(nd), ctypes.byref(ncl), ctypes.byref(cc)))
+        return dict(dt=dt.value, steps=st.value, cells=c.value, nodes=nd.value, clusters=ncl.value,
+                    cluster_ctas=cc.value)
 
     def read(self, run: int, name: str):
         """Host numpy copy of one quantity of one run (ex, hy, j, df)."""
@@ -465,9 +471,11 @@ class Solver:
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_source(self.h, ctypes.byref(d)))
 
     def set_plasma(self, density, vgrid="signed1d", nv=64, nv_perp=1, te_ev=1.0, vmax_vth=6.0, nu0=0.0,
-                   nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0, f0_model="maxwell", s_table=None):
+                   nu_model="nsv", f_dtype="f32", nonlinear=0, seed=0, f0_model="maxwell", s_table=None,
+                   evolve_f0=0, mass_ratio=0.0, tg_ev=0.0):
         """s_table = (speeds, cross-sections) for nu_model "table"; f0_model
-        "maxwell" or "druyvesteyn"."""
+        "maxwell" or "druyvesteyn"; evolve_f0 with mass_ratio = m/M and tg_ev
+        lets F0 evolve (speed grid)."""
         torch = self.torch
         if isinstance(density, torch.Tensor):
             dens = density.to(self.device, torch.float64).contiguous()
@@ -476,7 +484,7 @@ class Solver:
             dens = np.ascontiguousarray(density, dtype=np.float64)
             ptr, on_dev = dens.ctypes.data, 0
         d, keep = _plasma_desc(ptr, on_dev, vgrid, nv, nv_perp, te_ev, vmax_vth, nu0, nu_model, f_dtype, nonlinear,
-                               seed, f0_model, s_table)
+                               seed, f0_model, s_table, evolve_f0, mass_ratio, tg_ev)
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_plasma(self.h, ctypes.byref(d)))
         del keep
         self.f_dtype = f_dtype
@@ -541,7 +549,7 @@ class Solver:
 
     def _dtype(self, name):
         torch = self.torch
-        if name == "df":
+        if name in ("df", "f0"):
             return {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[self.f_dtype]
         return torch.float64 if self.precision == "f64" else torch.float32
 
@@ -563,7 +571,7 @@ class Solver:
         else:
             out = torch.empty(n, dtype=dt)
             _check(self.lib, self.h, self.lib.fdtd_plasma_read_fields(self.h, QUANTITY[name], out.data_ptr(), nb, 0))
-        if name == "df":
+        if name in ("df", "f0"):
             out = out.view(self.plasma_shape())
         return out if device else (out.float().numpy() if dt == torch.bfloat16 else out.numpy())
 
