@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="mma", choices=["mma", "tcgen05"], help="closure MLP engine")
+    ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
+                    help="3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
     return ap.parse_args()
@@ -237,6 +239,7 @@ def main():
     ns, nn = s.plasma_shape()
     cells = cells_of(spec)
     st = s.stream
+    s.set_option("fused_stencils", args.fused)
     tune = None if args.no_autotune else s.autotune()   # untimed: picks the launch shapes
     shapes = s.launch_shapes()                           # the shapes in use (tuned, cached or default)
 
@@ -268,6 +271,7 @@ def main():
 
     # per-kernel launch durations (eager launches with CUDA events on the solver's stream)
     kt = s.time_kernels(min(args.steps, 200))
+    fused = bool(args.fused) and spec["grid"]["ndim"] == 3 and s.precision == "f32"
 
     # end-to-end through the public API: plasma density and initial fields from
     # pinned host memory, K steps, final fields and J back to pinned host memory
@@ -341,6 +345,10 @@ def main():
             "phase_space_updates_per_s": ps_rate,
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "kernel_ms": kt,
+            # kernel_ms times one unfused step; on 3-D FP32 grids the timed steps fuse each E update with the
+            # next H update, so their stencil time is the step time less the kinetic and closure kernels
+            "fused_stencils": fused,
+            "stencil_ms_in_step": ms_step - kt["kinetic"] - kt["closure"],
             "launch_shapes": dict(shapes, tuned=tune is not None),
             "roofline": roof,
             "gpu_launches": args.steps * 3 + math.ceil(args.steps / 32) if ns else args.steps * 2 + math.ceil(args.steps / 32),

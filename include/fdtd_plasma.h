@@ -214,6 +214,17 @@ typedef struct {
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
+/* Runtime options.  FDTD_OPT_FUSED_STENCILS (default 0): 1 makes the step
+ * sequence on 3-D FP32 grids fuse each E update with the next H update into
+ * one pass (fields and CPML psi double-buffered: one extra copy of them is
+ * allocated on first use; the fields are back in place when
+ * fdtd_plasma_step returns).  It moves a third fewer bytes but is slower than
+ * the two separate passes on GB300 at present.  Results equal the unfused
+ * sequence up to FP32 rounding order.  0 turns it off (and frees the copy).
+ * FDTD_ERR_INVAL for an unknown option or value. */
+enum { FDTD_OPT_FUSED_STENCILS = 1 };
+int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);
+
 /* The launch shapes the handle uses now (tuned, cached or default; kinetic
  * fields 0 = the built-in choice); times are 0. */
 int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out);

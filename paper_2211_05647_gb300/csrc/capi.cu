@@ -323,35 +323,55 @@ void apply_cached_stencil(fdtd_plasma *h)
     }
 }
 
-// enqueue one step n -> n+1 (kstep = offset of this step inside the chunk);
-// ev (optional) receives records before H, before the kinetic kernel, before
-// the closure kernel, before E and after E.
+// Field / psi sets: set 0 is h->f / h->psi (where the state lives between
+// calls), set 1 the second copy used by the fused 3-D E+H kernel.
 template <typename T>
-cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t *ev = nullptr)
+struct FieldSet {
+    T *f[6];
+    Cpml<T> cp;
+};
+
+template <typename T>
+FieldSet<T> field_set(fdtd_plasma *h, int set)
+{
+    FieldSet<T> fs{};
+    for (int q = 0; q < 6; ++q) fs.f[q] = reinterpret_cast<T *>(set ? h->f2[q] : h->f[q]);
+    fs.cp = cpml_view<T>(h);
+    if (set)
+        for (int q = 0; q < 12; ++q) fs.cp.psi[q] = reinterpret_cast<T *>(h->psi2[q]);
+    return fs;
+}
+
+template <typename T>
+cudaError_t part_h(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs)
 {
     const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
-    const T ch = (T)(h->dt / (mu0 * h->g.dx)), ce = (T)(h->dt / (kEps0 * h->g.dx));
-    const T cph = (T)(h->dt / mu0), cpe = (T)(h->dt / kEps0);
-    T *f[6];
-    for (int q = 0; q < 6; ++q) f[q] = reinterpret_cast<T *>(h->f[q]);
-    const Cpml<T> cp = cpml_view<T>(h);
+    const T ch = (T)(h->dt / (mu0 * h->g.dx)), cph = (T)(h->dt / mu0);
+    T *const *f = fs.f;
     const Source src = source_view(h);
-    if (ev) cudaEventRecord(ev[0], st);
     if (h->g.ndim == 1)
         launch_h1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->g.mur ? (T *)h->mur_state : nullptr, h->nz, ch, src, h->d_step,
                       kstep);
     else if (h->g.ndim == 2)
-        launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, cp, src, h->d_step, kstep,
+        launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
     else
-        launch_h3d<T>(st, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, kstep, stencil_block(h), stencil_cpt(h));
-    if (ev) cudaEventRecord(ev[1], st);
+        launch_h3d<T>(st, const_cast<T *const *>(f), h->nx, h->ny, h->nz, ch, cph, fs.cp, src, h->d_step, kstep,
+                      stencil_block(h), stencil_cpt(h));
+    return cudaGetLastError();
+}
+
+// the work between the H and E updates: E-history push, kinetic update (E -= dt/eps0 J), closure, recorder
+template <typename T>
+cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs, cudaEvent_t *ev)
+{
+    T *E = fs.f[pol_comp(h)];
     const bool rec = h->has_recording && sizeof(T) == 4;
     if (rec)
-        launch_hist_push(st, h->slot_cell, h->nslots, reinterpret_cast<const float *>(f[pol_comp(h)]), h->hist,
-                         h->d_step, kstep);
+        launch_hist_push(st, h->slot_cell, h->nslots, reinterpret_cast<const float *>(E), h->hist, h->d_step, kstep);
     if (h->has_plasma && h->nkin > 0) {
-        const KinArgs<T> a = kin_args<T>(h, kstep);
+        KinArgs<T> a = kin_args<T>(h, kstep);
+        a.E = E;
         cudaError_t e;
         if (h->pl.evolve_f0) {
             const double vth = std::sqrt(kQe * h->pl.te_ev / kMe);
@@ -385,7 +405,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         c.hist = h->hist;
         c.jprev = h->jprev;
         c.jslot = reinterpret_cast<float *>(h->jslot) + h->nkin;
-        c.E = reinterpret_cast<float *>(f[pol_comp(h)]);
+        c.E = reinterpret_cast<float *>(E);
         c.P = h->params;
         c.n = h->ncl;
         c.inv_es = (float)(1.0 / h->cl.e_scale);
@@ -393,7 +413,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         c.js = (float)h->cl.j_scale;
         c.rho = (float)h->cl.rho;
         c.beta = (float)h->cl.beta;
-        c.cj = (float)cpe;
+        c.cj = (float)(h->dt / kEps0);
         c.d_step = h->d_step;
         c.kstep = kstep;
         c.engine = h->cl.engine;
@@ -405,7 +425,15 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
         launch_record(st, h->nslots, h->hist, reinterpret_cast<const float *>(h->dens),
                       reinterpret_cast<const float *>(h->jslot), h->jprev, h->rec_out, h->rec_cap, h->rec_count,
                       h->rec_threshold, h->rec_seed, h->d_step, kstep);
-    if (ev) cudaEventRecord(ev[3], st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t part_e(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs)
+{
+    const T ce = (T)(h->dt / (kEps0 * h->g.dx)), cpe = (T)(h->dt / kEps0);
+    T *const *f = fs.f;
+    const Source src = source_view(h);
     if (h->g.ndim == 1) {
         launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep);
         if (h->g.mur) {
@@ -413,26 +441,113 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
             launch_mur1d<T>(st, f[FDTD_EX], (const T *)h->mur_state, h->nz, m);
         }
     } else if (h->g.ndim == 2) {
-        launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, cp, src, h->d_step, kstep,
+        launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
     } else {
-        launch_e3d<T>(st, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, h->d_step, kstep, stencil_block(h), stencil_cpt(h));
-    }
-    if (ev) cudaEventRecord(ev[4], st);
-    if (h->nports > 0) {
-        cudaError_t e = launch_ports<T>(st, f[pol_comp(h)], h->nports, h->port_off, h->port_cells, h->port_freq,
-                                        h->port_acc, h->nfreq, h->dt, h->d_step, kstep);
-        if (e != cudaSuccess) return e;
+        launch_e3d<T>(st, const_cast<T *const *>(f), h->nx, h->ny, h->nz, ce, cpe, fs.cp, src, h->d_step, kstep,
+                      stencil_block(h), stencil_cpt(h));
     }
     return cudaGetLastError();
 }
 
-cudaError_t enqueue(fdtd_plasma *h, cudaStream_t st, int nsteps)
+template <typename T>
+cudaError_t part_ports(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs)
 {
+    if (h->nports <= 0) return cudaSuccess;
+    return launch_ports<T>(st, fs.f[pol_comp(h)], h->nports, h->port_off, h->port_cells, h->port_freq, h->port_acc,
+                           h->nfreq, h->dt, h->d_step, kstep);
+}
+
+// enqueue one step n -> n+1 on field set 0 (kstep = offset of this step inside
+// the chunk); ev (optional) receives records before H, before the kinetic
+// kernel, before the closure kernel, before E and after E.
+template <typename T>
+cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t *ev = nullptr)
+{
+    const FieldSet<T> fs = field_set<T>(h, 0);
+    if (ev) cudaEventRecord(ev[0], st);
+    cudaError_t e = part_h<T>(h, st, kstep, fs);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    e = part_mid<T>(h, st, kstep, fs, ev);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
+    e = part_e<T>(h, st, kstep, fs);
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[4], st);
+    return part_ports<T>(h, st, kstep, fs);
+}
+
+void free_second_set(fdtd_plasma *h)
+{
+    for (int q = 0; q < 6; ++q) { dfree(h, h->f2[q]); h->f2[q] = nullptr; }
+    for (int q = 0; q < 12; ++q) { dfree(h, h->psi2[q]); h->psi2[q] = nullptr; }
+}
+
+// allocate the second field / psi set when the fused sequence applies; on failure the steps run unfused
+void ensure_second_set(fdtd_plasma *h)
+{
+    if (!h->fuse || h->g.ndim != 3 || h->g.precision != FDTD_F32 || h->f2[0]) return;
+    bool ok = true;
+    for (int q = 0; q < 6 && ok; ++q)
+        if (h->flen[q]) ok = (h->f2[q] = dalloc(h, h->flen[q] * h->esz)) != nullptr;
+    for (int q = 0; q < 12 && ok; ++q)
+        if (h->psi[q]) ok = (h->psi2[q] = dalloc(h, h->psilen[q] * h->esz)) != nullptr;
+    if (!ok) {
+        free_second_set(h);
+        h->err.clear();
+    }
+}
+
+// whether the step sequence fuses E^{n+1} with H^{n+3/2} (3-D FP32, second field set allocated)
+bool fused_stencils(const fdtd_plasma *h)
+{
+    return h->fuse && h->g.ndim == 3 && h->g.precision == FDTD_F32 && h->f2[0] != nullptr;
+}
+
+// nsteps steps: H_0, then per step the middle part and either E_k alone (then
+// H_{k+1} on the same set) or the fused E_k + H_{k+1} from one set into the
+// other.  The number of fused transitions is kept even so the sequence ends on
+// set 0; with an odd count the first transition runs unfused.
+template <typename T>
+cudaError_t enqueue_seq(fdtd_plasma *h, cudaStream_t st, int nsteps)
+{
+    const bool fuse = sizeof(T) == 4 && fused_stencils(h);
+    const int trans = nsteps - 1;
+    const int unfused_first = fuse && (trans % 2) ? 1 : 0;
+    int set = 0;
+    cudaError_t e = part_h<T>(h, st, 0, field_set<T>(h, set));
+    if (e != cudaSuccess) return e;
     for (int k = 0; k < nsteps; ++k) {
-        cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_step<double>(h, st, k) : enqueue_step<float>(h, st, k);
+        const FieldSet<T> fs = field_set<T>(h, set);
+        e = part_mid<T>(h, st, k, fs, nullptr);
+        if (e != cudaSuccess) return e;
+        const bool last = k == nsteps - 1;
+        if (!last && fuse && k >= unfused_first) {
+            const FieldSet<T> to = field_set<T>(h, set ^ 1);
+            const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
+            if constexpr (sizeof(T) == 4) {
+                launch_eh3d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, h->nz, (float)(h->dt / (kEps0 * h->g.dx)),
+                            (float)(h->dt / kEps0), (float)(h->dt / (mu0 * h->g.dx)), (float)(h->dt / mu0), fs.cp,
+                            source_view(h), h->d_step, k);
+            }
+            set ^= 1;
+            e = part_ports<T>(h, st, k, to);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        e = part_e<T>(h, st, k, fs);
+        if (e == cudaSuccess) e = part_ports<T>(h, st, k, fs);
+        if (e == cudaSuccess && !last) e = part_h<T>(h, st, k + 1, fs);
         if (e != cudaSuccess) return e;
     }
+    return set == 0 ? cudaGetLastError() : cudaErrorInvalidValue;   // the state must end on set 0
+}
+
+cudaError_t enqueue(fdtd_plasma *h, cudaStream_t st, int nsteps)
+{
+    cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_seq<double>(h, st, nsteps) : enqueue_seq<float>(h, st, nsteps);
+    if (e != cudaSuccess) return e;
     launch_advance(st, h->d_step, nsteps);
     return cudaGetLastError();
 }
@@ -500,6 +615,7 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     }
 
     fdtd_plasma *h = new (std::nothrow) fdtd_plasma();
+    if (h) h->fuse = 0;
     if (!h) return fail(nullptr, FDTD_ERR_NOMEM, "host allocation failed");
     h->g = *g;
     if (rt) h->rt = *rt;
@@ -595,6 +711,20 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     if (se != cudaSuccess) return bail(FDTD_ERR_CUDA, cudaGetErrorString(se));
     *out = h;
     return FDTD_OK;
+}
+
+int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
+{
+    if (!h) return FDTD_ERR_INVAL;
+    if (option == FDTD_OPT_FUSED_STENCILS) {
+        if (value != 0 && value != 1) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_FUSED_STENCILS takes 0 or 1");
+        CK(h, cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        h->fuse = (int)value;
+        if (!h->fuse) free_second_set(h);
+        return FDTD_OK;
+    }
+    return fail(h, FDTD_ERR_INVAL, "unknown option %d", option);
 }
 
 int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out)
@@ -811,6 +941,7 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
     if (nsteps < 0) return fail(h, FDTD_ERR_INVAL, "nsteps < 0");
     if (nsteps == 0) return FDTD_OK;
     if (!h->graphs_valid) {
+        ensure_second_set(h);
         int rc = capture(h, 1, &h->g1);
         if (rc == FDTD_OK) rc = capture(h, kChunk, &h->gk);
         if (rc != FDTD_OK) {
@@ -1370,6 +1501,7 @@ void fdtd_plasma_destroy(fdtd_plasma_t h)
     dfree(h, h->d_src);
     dfree(h, h->d_err);
     free_ports(h);
+    free_second_set(h);
     dfree(h, h->diag_partials);
     dfree(h, h->diag_out);
     if (h->cap) cudaStreamDestroy(h->cap);

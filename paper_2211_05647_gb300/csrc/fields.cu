@@ -173,20 +173,22 @@ template <typename T>
 struct Pml3 {
     const Cpml<T> &cp;
     int64_t nx, ny, nz, i, j, k;
-    __device__ __forceinline__ T *slot_ptr(int s, int axis) const
+    __device__ __forceinline__ int64_t off(int axis) const   // element of the cell in a slab of `axis`
     {
         const int L = cp.L;
-        if (axis == 0) return cp.psi[s] + (k * ny + j) * (2 * L) + slab_slot<T>(i, nx, L);
-        if (axis == 1) return cp.psi[s] + (k * (2 * L) + slab_slot<T>(j, ny, L)) * nx + i;
-        return cp.psi[s] + ((int64_t)slab_slot<T>(k, nz, L) * ny + j) * nx + i;
+        if (axis == 0) return (k * ny + j) * (2 * L) + slab_slot<T>(i, nx, L);
+        if (axis == 1) return (k * (2 * L) + slab_slot<T>(j, ny, L)) * nx + i;
+        return ((int64_t)slab_slot<T>(k, nz, L) * ny + j) * nx + i;
     }
+    __device__ __forceinline__ T *slot_ptr(int s, int axis) const { return cp.psi[s] + off(axis); }
 };
 
-// CPML H update of one 3-D cell: six psi recursions on the slabs the cell is in.
+// CPML H update of one 3-D cell: six psi recursions on the slabs the cell is in,
+// read from cp.psi and written to psi_out when store (psi_out == cp.psi: in place).
 template <typename T>
-__device__ __forceinline__ void h3d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t nz, int64_t i, int64_t j,
-                                        int64_t k, T ch, T cph, T dEz_y, T dEy_z, T dEx_z, T dEz_x, T dEy_x, T dEx_y,
-                                        T &hxv, T &hyv, T &hzv)
+__device__ __forceinline__ void h3d_pml_io(const Cpml<T> &cp, T *const *psi_out, bool store, int64_t nx, int64_t ny,
+                                           int64_t nz, int64_t i, int64_t j, int64_t k, T ch, T cph, T dEz_y,
+                                           T dEy_z, T dEx_z, T dEz_x, T dEy_x, T dEx_y, T &hxv, T &hyv, T &hzv)
 {
     const int L = cp.L;
     Pml3<T> P{cp, nx, ny, nz, i, j, k};
@@ -194,30 +196,43 @@ __device__ __forceinline__ void h3d_pml(const Cpml<T> &cp, int64_t nx, int64_t n
     const T kx = sx ? cp.ikh[0][i] : T(1), ky = sy ? cp.ikh[1][j] : T(1), kz = sz ? cp.ikh[2][k] : T(1);
     T p6 = 0, p7 = 0, p8 = 0, p9 = 0, p10 = 0, p11 = 0;
     if (sy) {
-        T *a = P.slot_ptr(6, 1), *b = P.slot_ptr(11, 1);
-        p6 = cp.bh[1][j] * *a + cp.ah[1][j] * dEz_y; *a = p6;
-        p11 = cp.bh[1][j] * *b + cp.ah[1][j] * dEx_y; *b = p11;
+        const int64_t o = P.off(1);
+        p6 = cp.bh[1][j] * cp.psi[6][o] + cp.ah[1][j] * dEz_y;
+        p11 = cp.bh[1][j] * cp.psi[11][o] + cp.ah[1][j] * dEx_y;
+        if (store) { psi_out[6][o] = p6; psi_out[11][o] = p11; }
     }
     if (sz) {
-        T *a = P.slot_ptr(7, 2), *b = P.slot_ptr(9, 2);
-        p7 = cp.bh[2][k] * *a + cp.ah[2][k] * dEy_z; *a = p7;
-        p9 = cp.bh[2][k] * *b + cp.ah[2][k] * dEx_z; *b = p9;
+        const int64_t o = P.off(2);
+        p7 = cp.bh[2][k] * cp.psi[7][o] + cp.ah[2][k] * dEy_z;
+        p9 = cp.bh[2][k] * cp.psi[9][o] + cp.ah[2][k] * dEx_z;
+        if (store) { psi_out[7][o] = p7; psi_out[9][o] = p9; }
     }
     if (sx) {
-        T *a = P.slot_ptr(8, 0), *b = P.slot_ptr(10, 0);
-        p8 = cp.bh[0][i] * *a + cp.ah[0][i] * dEz_x; *a = p8;
-        p10 = cp.bh[0][i] * *b + cp.ah[0][i] * dEy_x; *b = p10;
+        const int64_t o = P.off(0);
+        p8 = cp.bh[0][i] * cp.psi[8][o] + cp.ah[0][i] * dEz_x;
+        p10 = cp.bh[0][i] * cp.psi[10][o] + cp.ah[0][i] * dEy_x;
+        if (store) { psi_out[8][o] = p8; psi_out[10][o] = p10; }
     }
     hxv -= ch * (dEz_y * ky - dEy_z * kz) + cph * (p6 - p7);
     hyv -= ch * (dEx_z * kz - dEz_x * kx) + cph * (p9 - p8);
     hzv -= ch * (dEy_x * kx - dEx_y * ky) + cph * (p10 - p11);
 }
 
-// CPML curl terms (ux, uy, uz) of the E update of one 3-D cell.
 template <typename T>
-__device__ __forceinline__ void e3d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t nz, int64_t i, int64_t j,
-                                        int64_t k, T ce, T cpe, T dHz_y, T dHy_z, T dHx_z, T dHz_x, T dHy_x, T dHx_y,
-                                        T &ux, T &uy, T &uz)
+__device__ __forceinline__ void h3d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t nz, int64_t i, int64_t j,
+                                        int64_t k, T ch, T cph, T dEz_y, T dEy_z, T dEx_z, T dEz_x, T dEy_x, T dEx_y,
+                                        T &hxv, T &hyv, T &hzv)
+{
+    h3d_pml_io<T>(cp, cp.psi, true, nx, ny, nz, i, j, k, ch, cph, dEz_y, dEy_z, dEx_z, dEz_x, dEy_x, dEx_y, hxv, hyv,
+                  hzv);
+}
+
+// CPML curl terms (ux, uy, uz) of the E update of one 3-D cell; psi read from
+// cp.psi, written to psi_out when store.
+template <typename T>
+__device__ __forceinline__ void e3d_pml_io(const Cpml<T> &cp, T *const *psi_out, bool store, int64_t nx, int64_t ny,
+                                           int64_t nz, int64_t i, int64_t j, int64_t k, T ce, T cpe, T dHz_y,
+                                           T dHy_z, T dHx_z, T dHz_x, T dHy_x, T dHx_y, T &ux, T &uy, T &uz)
 {
     const int L = cp.L;
     Pml3<T> P{cp, nx, ny, nz, i, j, k};
@@ -225,23 +240,34 @@ __device__ __forceinline__ void e3d_pml(const Cpml<T> &cp, int64_t nx, int64_t n
     const T kx = sx ? cp.ike[0][i] : T(1), ky = sy ? cp.ike[1][j] : T(1), kz = sz ? cp.ike[2][k] : T(1);
     T p0 = 0, p1 = 0, p2 = 0, p3 = 0, p4 = 0, p5 = 0;
     if (sy) {
-        T *a = P.slot_ptr(0, 1), *b = P.slot_ptr(5, 1);
-        p0 = cp.be[1][j] * *a + cp.ae[1][j] * dHz_y; *a = p0;
-        p5 = cp.be[1][j] * *b + cp.ae[1][j] * dHx_y; *b = p5;
+        const int64_t o = P.off(1);
+        p0 = cp.be[1][j] * cp.psi[0][o] + cp.ae[1][j] * dHz_y;
+        p5 = cp.be[1][j] * cp.psi[5][o] + cp.ae[1][j] * dHx_y;
+        if (store) { psi_out[0][o] = p0; psi_out[5][o] = p5; }
     }
     if (sz) {
-        T *a = P.slot_ptr(1, 2), *b = P.slot_ptr(3, 2);
-        p1 = cp.be[2][k] * *a + cp.ae[2][k] * dHy_z; *a = p1;
-        p3 = cp.be[2][k] * *b + cp.ae[2][k] * dHx_z; *b = p3;
+        const int64_t o = P.off(2);
+        p1 = cp.be[2][k] * cp.psi[1][o] + cp.ae[2][k] * dHy_z;
+        p3 = cp.be[2][k] * cp.psi[3][o] + cp.ae[2][k] * dHx_z;
+        if (store) { psi_out[1][o] = p1; psi_out[3][o] = p3; }
     }
     if (sx) {
-        T *a = P.slot_ptr(2, 0), *b = P.slot_ptr(4, 0);
-        p2 = cp.be[0][i] * *a + cp.ae[0][i] * dHz_x; *a = p2;
-        p4 = cp.be[0][i] * *b + cp.ae[0][i] * dHy_x; *b = p4;
+        const int64_t o = P.off(0);
+        p2 = cp.be[0][i] * cp.psi[2][o] + cp.ae[0][i] * dHz_x;
+        p4 = cp.be[0][i] * cp.psi[4][o] + cp.ae[0][i] * dHy_x;
+        if (store) { psi_out[2][o] = p2; psi_out[4][o] = p4; }
     }
     ux = ce * (dHz_y * ky - dHy_z * kz) + cpe * (p0 - p1);
     uy = ce * (dHx_z * kz - dHz_x * kx) + cpe * (p3 - p2);
     uz = ce * (dHy_x * kx - dHx_y * ky) + cpe * (p4 - p5);
+}
+
+template <typename T>
+__device__ __forceinline__ void e3d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t nz, int64_t i, int64_t j,
+                                        int64_t k, T ce, T cpe, T dHz_y, T dHy_z, T dHx_z, T dHz_x, T dHy_x, T dHx_y,
+                                        T &ux, T &uy, T &uz)
+{
+    e3d_pml_io<T>(cp, cp.psi, true, nx, ny, nz, i, j, k, ce, cpe, dHz_y, dHy_z, dHx_z, dHz_x, dHy_x, dHx_y, ux, uy, uz);
 }
 
 template <typename T>
@@ -644,11 +670,220 @@ __global__ void __launch_bounds__(256) k_e3d_v4(float *__restrict__ ex, float *_
     st4(ez + c, Ez);
 }
 
+// ------------------------------------------ 3-D fused E^{n+1} + H^{n+3/2} (FP32)
+// The E update of step n and the H update of step n+1 in one pass: a block owns
+// a 32 x 8 column tile and marches up its z range; per plane it stages H^{n+1/2}
+// (with the -x / -y halo), E' (E^n after the current density term, with the
+// +x / +y halo) in shared memory, forms E^{n+1} on the tile and its +x / +y halo
+// (the halo values are recomputed, not exchanged), stores the tile's E^{n+1},
+// then forms H^{n+3/2} of the plane below from the two staged E^{n+1} planes.
+// Everything is read from field / psi set `in` and written to set `out`, so no
+// block reads what another block writes in the same launch.  The source term
+// of E^{n+1} is evaluated per block; block (0,0,0) also stores g(t^{n+2}) for a
+// following unfused E update.  DRAM: fields read once and written once per step
+// (12 x 4 B per cell) instead of twice read and once written per half step.
+
+constexpr int kEhX = 32, kEhY = 8;
+
+struct FieldPtrs {
+    const float *ex, *ey, *ez, *hx, *hy, *hz;
+};
+struct FieldOut {
+    float *ex, *ey, *ez, *hx, *hy, *hz;
+};
+struct PsiOut {
+    float *psi[12];
+};
+
+__global__ void __launch_bounds__(kEhX * kEhY, 3) k_eh3d(FieldPtrs in, FieldOut out, int64_t nx, int64_t ny, int64_t nz,
+                                                     int tz, float ce, float cpe, float ch, float cph, Cpml<float> cin,
+                                                     PsiOut pout, Source src, const int64_t *__restrict__ d_step,
+                                                     int kstep)
+{
+    __shared__ float sH[2][3][kEhY + 2][kEhX + 2];   // H^{n+1/2}: x0-1..x0+32, y0-1..y0+8
+    __shared__ float sEp[3][kEhY + 1][kEhX + 1];     // E': x0..x0+32, y0..y0+8
+    __shared__ float sE[2][3][kEhY + 1][kEhX + 1];   // E^{n+1}: x0..x0+32, y0..y0+8
+    __shared__ float s_g;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kEhX + tx;
+    const int64_t x0 = (int64_t)blockIdx.x * kEhX, y0 = (int64_t)blockIdx.y * kEhY, z0 = (int64_t)blockIdx.z * tz;
+    const int64_t z1 = min(z0 + (int64_t)tz, nz);
+    const int64_t n1 = *d_step + kstep + 1;   // E^{n+1} is at t^{n+1}
+    if (tid == 0) {
+        s_g = src.kind && src.k >= z0 && src.k <= z1 ? (float)source_value(src, (double)n1 * src.dt) : 0.f;
+        if (src.kind && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+            *src.val = source_value(src, (double)(n1 + 1) * src.dt);
+    }
+    const int64_t sxy = nx * ny;
+    // Staging of one plane: each thread fetches its share of the plane's H (with the -x / -y halo) and E'
+    // (with the +x / +y halo) into registers, and later commits them to shared memory, so the global loads
+    // of plane k+2 are in flight while plane k+1 is computed.
+    constexpr int NH = ((kEhY + 2) * (kEhX + 2) + kEhX * kEhY - 1) / (kEhX * kEhY);
+    constexpr int NE = ((kEhY + 1) * (kEhX + 1) + kEhX * kEhY - 1) / (kEhX * kEhY);
+    float rh[NH][3], re[NE][3];
+    auto fetch = [&](int64_t k) {
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+            const int r = tid + q * kEhX * kEhY;
+            const int rx = r % (kEhX + 2), ry = r / (kEhX + 2);
+            const int64_t i = x0 - 1 + rx, j = y0 - 1 + ry;
+            const bool ok = r < (kEhY + 2) * (kEhX + 2) && k >= 0 && k < nz && i >= 0 && i < nx && j >= 0 && j < ny;
+            const int64_t c = ok ? k * sxy + j * nx + i : 0;
+            rh[q][0] = ok ? in.hx[c] : 0.f;
+            rh[q][1] = ok ? in.hy[c] : 0.f;
+            rh[q][2] = ok ? in.hz[c] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < NE; ++q) {
+            const int r = tid + q * kEhX * kEhY;
+            const int rx = r % (kEhX + 1), ry = r / (kEhX + 1);
+            const int64_t i = x0 + rx, j = y0 + ry;
+            const bool ok = r < (kEhY + 1) * (kEhX + 1) && k >= 0 && k < nz && i < nx && j < ny;
+            const int64_t c = ok ? k * sxy + j * nx + i : 0;
+            re[q][0] = ok ? in.ex[c] : 0.f;
+            re[q][1] = ok ? in.ey[c] : 0.f;
+            re[q][2] = ok ? in.ez[c] : 0.f;
+        }
+    };
+    auto commit = [&](int b) {   // H into sH[b], E' into sEp
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+            const int r = tid + q * kEhX * kEhY;
+            if (r < (kEhY + 2) * (kEhX + 2)) {
+                const int rx = r % (kEhX + 2), ry = r / (kEhX + 2);
+                sH[b][0][ry][rx] = rh[q][0];
+                sH[b][1][ry][rx] = rh[q][1];
+                sH[b][2][ry][rx] = rh[q][2];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NE; ++q) {
+            const int r = tid + q * kEhX * kEhY;
+            if (r < (kEhY + 1) * (kEhX + 1)) {
+                const int rx = r % (kEhX + 1), ry = r / (kEhX + 1);
+                sEp[0][ry][rx] = re[q][0];
+                sEp[1][ry][rx] = re[q][1];
+                sEp[2][ry][rx] = re[q][2];
+            }
+        }
+    };
+    // whether the block's columns (with their halo) meet an x / y CPML slab; per plane add the z slabs
+    const int L = cin.L;
+    const bool xy_pml = L > 0 && (x0 < L || x0 + kEhX >= nx - L || y0 < L || y0 + kEhY >= ny - L);
+    auto pml_plane = [&](int64_t k) { return xy_pml || (L > 0 && (k < L || k >= nz - L)); };
+    // E^{n+1} of plane k over the tile and its +x / +y halo into sE[b]; bk / bm: sH buffers of planes k, k-1
+    auto compE = [&](int b, int bk, int bm, int64_t k) {
+        const bool pml = pml_plane(k);
+        for (int r = tid; r < (kEhY + 1) * (kEhX + 1); r += kEhX * kEhY) {
+            const int rx = r % (kEhX + 1), ry = r / (kEhX + 1);
+            const int64_t i = x0 + rx, j = y0 + ry;
+            float exn = 0.f, eyn = 0.f, ezn = 0.f;
+            if (k < nz && i < nx && j < ny) {
+                const int hx_ = rx + 1, hy_ = ry + 1;
+                const float hxc = sH[bk][0][hy_][hx_], hyc = sH[bk][1][hy_][hx_], hzc = sH[bk][2][hy_][hx_];
+                const float dHz_y = j > 0 ? hzc - sH[bk][2][hy_ - 1][hx_] : 0.f;
+                const float dHy_z = k > 0 ? hyc - sH[bm][1][hy_][hx_] : 0.f;
+                const float dHx_z = k > 0 ? hxc - sH[bm][0][hy_][hx_] : 0.f;
+                const float dHz_x = i > 0 ? hzc - sH[bk][2][hy_][hx_ - 1] : 0.f;
+                const float dHy_x = i > 0 ? hyc - sH[bk][1][hy_][hx_ - 1] : 0.f;
+                const float dHx_y = j > 0 ? hxc - sH[bk][0][hy_ - 1][hx_] : 0.f;
+                const float exc = sEp[0][ry][rx], eyc = sEp[1][ry][rx], ezc = sEp[2][ry][rx];
+                const bool own = rx < kEhX && ry < kEhY && k < z1;
+                float ux, uy, uz;
+                if (!pml) {   // no CPML cell in this block's plane: psi untouched
+                    ux = ce * (dHz_y - dHy_z);
+                    uy = ce * (dHx_z - dHz_x);
+                    uz = ce * (dHy_x - dHx_y);
+                } else {
+                    e3d_pml_io<float>(cin, pout.psi, own, nx, ny, nz, i, j, k, ce, cpe, dHz_y, dHy_z, dHx_z, dHz_x,
+                                      dHy_x, dHx_y, ux, uy, uz);
+                }
+                exn = exc; eyn = eyc; ezn = ezc;
+                if (j > 0 && k > 0) {
+                    exn = exc + ux;
+                    if (src.kind && source_hits(src, i, j, k)) exn += s_g;
+                }
+                if (i > 0 && k > 0) eyn = eyc + uy;
+                if (i > 0 && j > 0) ezn = ezc + uz;
+                if (own) {
+                    const int64_t c = k * sxy + j * nx + i;
+                    out.ex[c] = exn;
+                    out.ey[c] = eyn;
+                    out.ez[c] = ezn;
+                }
+            }
+            sE[b][0][ry][rx] = exn;
+            sE[b][1][ry][rx] = eyn;
+            sE[b][2][ry][rx] = ezn;
+        }
+    };
+    // H^{n+3/2} of plane k on the tile; bk: sH buffer of plane k, ek / ek1: sE buffers of planes k, k+1
+    auto compH = [&](int bk, int ek, int ek1, int64_t k) {
+        const bool pml = pml_plane(k);
+        const int64_t i = x0 + tx, j = y0 + ty;
+        if (k >= nz || i >= nx || j >= ny) return;
+        float hxv = sH[bk][0][ty + 1][tx + 1], hyv = sH[bk][1][ty + 1][tx + 1], hzv = sH[bk][2][ty + 1][tx + 1];
+        const float exc = sE[ek][0][ty][tx], eyc = sE[ek][1][ty][tx], ezc = sE[ek][2][ty][tx];
+        const float dEz_y = sE[ek][2][ty + 1][tx] - ezc;
+        const float dEy_z = sE[ek1][1][ty][tx] - eyc;
+        const float dEx_z = sE[ek1][0][ty][tx] - exc;
+        const float dEz_x = sE[ek][2][ty][tx + 1] - ezc;
+        const float dEy_x = sE[ek][1][ty][tx + 1] - eyc;
+        const float dEx_y = sE[ek][0][ty + 1][tx] - exc;
+        if (!pml) {
+            hxv -= ch * (dEz_y - dEy_z);
+            hyv -= ch * (dEx_z - dEz_x);
+            hzv -= ch * (dEy_x - dEx_y);
+        } else {
+            h3d_pml_io<float>(cin, pout.psi, true, nx, ny, nz, i, j, k, ch, cph, dEz_y, dEy_z, dEx_z, dEz_x, dEy_x,
+                              dEx_y, hxv, hyv, hzv);
+        }
+        const int64_t c = k * sxy + j * nx + i;
+        out.hx[c] = hxv;
+        out.hy[c] = hyv;
+        out.hz[c] = hzv;
+    };
+    // prologue: H of plane z0-1 (for dH/dz of E^{n+1}(z0)) into sH[1], plane z0 into sH[0], E'(z0)
+    fetch(z0 - 1);
+    commit(1);
+    fetch(z0);
+    commit(0);
+    __syncthreads();
+    fetch(z0 + 1);                     // in flight during E^{n+1}(z0)
+    compE(0, 0, 1, z0);
+    __syncthreads();
+    int cur = 0;
+    for (int64_t k = z0; k < z1; ++k) {
+        const int nxt = cur ^ 1;
+        commit(nxt);                   // plane k+1 (the buffer held plane k-1, no longer needed)
+        __syncthreads();
+        if (k + 1 < z1) fetch(k + 2);  // plane k+2 in flight during this iteration's compute
+        compE(nxt, nxt, cur, k + 1);
+        __syncthreads();
+        compH(cur, cur, nxt, k);
+        __syncthreads();               // plane k's buffers are overwritten next iteration
+        cur = nxt;
+    }
+}
+
 __global__ void k_advance(int64_t *d_step, int64_t by) { *d_step += by; }
 
 // ------------------------------------------------------------------ launchers
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
+                 int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
+                 const int64_t *d_step, int kstep)
+{
+    const int tz = 32;
+    dim3 g(cdiv(nx, kEhX), cdiv(ny, kEhY), cdiv(nz, tz));
+    FieldPtrs a{fin[0], fin[1], fin[2], fin[3], fin[4], fin[5]};
+    FieldOut o{fout[0], fout[1], fout[2], fout[3], fout[4], fout[5]};
+    PsiOut po{};
+    for (int q = 0; q < 12; ++q) po.psi[q] = psi_out[q];
+    k_eh3d<<<g, dim3(kEhX, kEhY), 0, st>>>(a, o, nx, ny, nz, tz, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
+}
+
 
 template <typename T>
 void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch, Source src,

@@ -140,6 +140,10 @@ void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t 
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
                 Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
+// 3-D FP32 fused E^{n+1} + H^{n+3/2}: reads fields fin and psi cin.psi, writes fout and psi_out
+void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
+                 int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
+                 const int64_t *d_step, int kstep);
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by);
 
 // delta-f row pitch (elements) for nnode nodes of the given storage type
@@ -250,6 +254,10 @@ struct fdtd_plasma {
     int64_t flen[6];
     void *psi[12];
     int64_t psilen[12];
+    // second field / psi set for the fused 3-D E+H kernel (allocated on first use)
+    void *f2[6];
+    void *psi2[12];
+    int fuse;                 // FDTD_OPT_FUSED_STENCILS (default 1)
     void *prof;               // CPML tables
     int64_t prof_len;
     void *mur_state;

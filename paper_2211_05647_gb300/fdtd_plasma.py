@@ -137,6 +137,7 @@ SIGNATURES = {
     "fdtd_plasma_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_diag)]),
     "fdtd_plasma_poynting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
+    "fdtd_plasma_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "fdtd_plasma_launch_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_tune_result)]),
     "fdtd_plasma_set_ports": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
@@ -533,6 +534,11 @@ class Solver:
         r = fdtd_tune_result()
         _check(self.lib, self.h, self.lib.fdtd_plasma_autotune(self.h, ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in fdtd_tune_result._fields_}
+
+    def set_option(self, option: str, value: int):
+        """Runtime option: "fused_stencils" (0 / 1, default 0; see FDTD_OPT_FUSED_STENCILS)."""
+        code = {"fused_stencils": 1}[option]
+        _check(self.lib, self.h, self.lib.fdtd_plasma_set_option(self.h, code, int(value)))
 
     def launch_shapes(self) -> dict:
         """The launch shapes in use (tuned, cached or default)."""

@@ -1,0 +1,83 @@
+"""Fused 3-D E^{n+1} + H^{n+3/2} stencil pass (FP32, opt-in): the same physics as the
+unfused sequence (FP32 rounding order only), for step counts that exercise the
+parity rule (an odd number of fused transitions runs the first one unfused),
+the 32-step graph chunks and the 1-step graph, with CPML, a sheet source and a
+kinetic slab; and against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from fdtd_inputs import spec_3d_slab
+from tests.adapters import FIELDS, compare, oracle_sim, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _spec(steps, n=(44, 36, 70), cpml=6, slab=(34, 52)):
+    nx, ny, nz = n
+    return spec_3d_slab(n=nx, ny=ny, nz=nz, cpml=cpml, slab=slab, src_k=12, nv=16, steps=steps,
+                        precision="f32", f_dtype="f32", seed=31)
+
+
+def _pair(spec, calls):
+    from paper_2211_05647_gb300 import Solver
+    fused, plain = Solver.from_spec(spec), Solver.from_spec(spec)
+    fused.set_option("fused_stencils", 1)
+    for n in calls:
+        fused.step(n)
+        plain.step(n)
+    return fused, plain
+
+
+@pytest.mark.parametrize("calls", [(1,), (2,), (3,), (33,), (64, 5), (7, 1, 40)])
+def test_fused_equals_unfused(calls):
+    fused, plain = _pair(_spec(sum(calls)), calls)
+    worst = 0.0
+    for q in FIELDS[3] + ["j", "df"]:
+        a, b = fused.read(q, device=False), plain.read(q, device=False)
+        if np.abs(b).max() == 0:
+            assert np.abs(a).max() == 0, q
+            continue
+        worst = max(worst, rel_l2(a, b))
+    print(f"calls {calls}: fused vs unfused max rel L2 {worst:.2e}")
+    assert worst <= 1e-6
+
+
+def test_fused_matches_oracle(oracle_lib):
+    spec = _spec(260)
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec)
+    s.set_option("fused_stencils", 1)
+    s.step(100)
+    s.step(160)
+    sim = oracle_sim(oracle_lib, spec)
+    sim.step(260)
+    errs = compare(s, sim, 3)
+    print("fused 3-D f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
+
+
+def test_fused_no_cpml_and_ragged_tiles():
+    """Grid sizes that leave partial 32 x 8 x 32 tiles on every axis, PEC walls."""
+    spec = _spec(50, n=(37, 13, 45), cpml=0, slab=(24, 36))
+    spec["source"].update(i0=0, i1=37, j0=1, j1=13)   # the whole updated Ex plane (no CPML frame)
+    fused, plain = _pair(spec, (50,))
+    for q in FIELDS[3]:
+        assert rel_l2(fused.read(q, device=False), plain.read(q, device=False)) <= 1e-6, q
+
+
+def test_fused_option_errors_and_checkpoint():
+    from paper_2211_05647_gb300 import FdtdError, Solver
+    spec = _spec(40)
+    s = Solver.from_spec(spec)
+    with pytest.raises(FdtdError):
+        s.set_option("fused_stencils", 2)
+    s.set_option("fused_stencils", 1)
+    s.step(21)
+    blob = s.save_state(device=False)
+    s.step(19)
+    r = Solver.from_spec(spec)
+    r.set_option("fused_stencils", 1)
+    r.load_state(blob)
+    r.step(19)
+    for q in FIELDS[3] + ["j"]:
+        assert np.array_equal(s.read(q, device=False), r.read(q, device=False)), q
