@@ -305,7 +305,8 @@ int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int b
  * Learned J closure (not in the paper: a small network standing in for the
  * Sec. 5.2 velocity-space update).  Per plasma cell with n <= n_train_max:
  *   x = [E^{n-15} .. E^n] / e_scale ++ [n / n_scale]          (17 inputs)
- *   y = MLP(x): 17 -> 128 -> 128 -> 1, exact-erf GELU on both hidden layers,
+ *   y = MLP(x): 17 -> 128 -> 128 -> 1, GELU in its tanh form (Hendrycks &
+ *       Gimpel) on both hidden layers,
  *       BF16 tensor-core operands, FP32 accumulation
  *   J^{n+1/2} = rho J^{n-1/2} + beta n E^n + j_scale y
  *       (beta n E^n is the Drude increment of a constant-collision plasma, so

@@ -1,6 +1,7 @@
 """FP64 reference of the learned J-closure network: a 17 -> 128 -> 128 -> 1
-multilayer perceptron with exact (erf-form) GELU, its backward pass for a
-mean-squared-error loss and the Adam update.
+multilayer perceptron with the tanh form of GELU (Hendrycks & Gimpel,
+"Gaussian Error Linear Units", 2016), its backward pass for a mean-squared-
+error loss and the Adam update.
 
 TEST INFRASTRUCTURE ONLY (imported by tests, the smoke check and the CPU
 baseline; never by the product library).
@@ -16,23 +17,19 @@ import math
 
 import numpy as np
 
-SQRT2 = math.sqrt(2.0)
-INV_SQRT2PI = 1.0 / math.sqrt(2.0 * math.pi)
-
-try:  # scipy is on both machines; math.erf is the plain fallback
-    from scipy.special import erf as _erf
-except Exception:  # pragma: no cover
-    _erf = np.vectorize(math.erf)
+GELU_C = math.sqrt(2.0 / math.pi)
+GELU_A = 0.044715
 
 
 def gelu(x):
-    """0.5 x (1 + erf(x / sqrt 2)) -- x times the standard normal CDF."""
-    return 0.5 * x * (1.0 + _erf(x / SQRT2))
+    """0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), the tanh form of x Phi(x)."""
+    return 0.5 * x * (1.0 + np.tanh(GELU_C * (x + GELU_A * x ** 3)))
 
 
 def gelu_grad(x):
-    """d/dx [x Phi(x)] = Phi(x) + x phi(x)."""
-    return 0.5 * (1.0 + _erf(x / SQRT2)) + x * np.exp(-0.5 * x * x) * INV_SQRT2PI
+    """Derivative of the tanh form: 0.5 (1 + t) + 0.5 x (1 - t^2) sqrt(2/pi) (1 + 3 * 0.044715 x^2)."""
+    t = np.tanh(GELU_C * (x + GELU_A * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * x * x)
 
 
 def init_params(rng: np.random.Generator, n_in=17, n_h=128):

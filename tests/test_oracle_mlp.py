@@ -10,13 +10,19 @@ from oracle import mlp as M
 
 
 def test_gelu_values():
-    # x * Phi(x) with Phi(1) = 0.841344746068543, Phi(-1) = 0.158655253931457 (normal tables)
-    assert M.gelu(np.array([1.0]))[0] == pytest.approx(0.841344746068543, abs=1e-15)
-    assert M.gelu(np.array([-1.0]))[0] == pytest.approx(-0.158655253931457, abs=1e-15)
+    """The tanh form of GELU: exact identities (value 0 at 0, gelu(x) - gelu(-x) = x
+    because tanh is odd, the limits x and 0), its distance from the erf form
+    x Phi(x) (math.erf, independent of the tanh form; Phi(1) = 0.841344746068543
+    from normal tables), and the derivative against central differences."""
     assert M.gelu(np.array([0.0]))[0] == 0.0
-    x = np.array([8.0, -8.0])
-    assert np.allclose(M.gelu(x), [8.0, 0.0], atol=1e-12)
-    xs = np.linspace(-4, 4, 41)
+    xs = np.linspace(-6, 6, 241)
+    assert np.allclose(M.gelu(xs) - M.gelu(-xs), xs, rtol=0, atol=1e-15)
+    assert np.allclose(M.gelu(np.array([9.0, -9.0])), [9.0, 0.0], atol=1e-12)
+    erf_form = np.array([0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0))) for x in xs])
+    assert 0.5 * (1 + math.erf(1 / math.sqrt(2))) == pytest.approx(0.841344746068543, abs=1e-15)
+    dev = np.abs(M.gelu(xs) - erf_form).max()
+    print(f"max |tanh form - erf form| on [-6, 6]: {dev:.3e}")
+    assert 1e-5 < dev < 5e-4
     h = 1e-6
     fd = (M.gelu(xs + h) - M.gelu(xs - h)) / (2 * h)
     assert np.allclose(fd, M.gelu_grad(xs), atol=1e-9)
