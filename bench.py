@@ -235,6 +235,8 @@ def main():
         return batch_bench(args, spec, rank, world, local)
     if args.workload.endswith("_closure"):
         return closure_bench(args, spec, rank, world, local)
+    if args.workload.endswith("_closure_cost"):
+        return closure_cost_bench(args, spec, rank, world, local)
     s = Solver.from_spec(spec, device=local)
     ns, nn = s.plasma_shape()
     cells = cells_of(spec)
@@ -437,6 +439,56 @@ def closure_bench(args, spec, rank, world, local):
             "roofline": {"bound": "tensor", "kernel": "k_closure", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "alg_flops_per_launch": flops, "launch_ms": kt_c["closure"],
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
+            "gpu_launches": args.steps * (4 if n_kin else 3) + math.ceil(args.steps / 32),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def closure_cost_bench(args, spec, rank, world, local):
+    """Inference cost of the learned closure: every plasma cell of the grid on
+    the closure, seeded random weights (the cost does not depend on their
+    values), K timed graph-replayed steps; roofline of the closure kernel against
+    the sustained BF16 tensor peak."""
+    import numpy as np
+    import torch
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec, device=local)
+    params = (np.random.default_rng(20221201).standard_normal(18945) * 0.05).astype(np.float32)
+    s.set_closure(params, e_scale=1.0, j_scale=1e-3, n_scale=1e18, rho=0.9, n_train_max=1e30, beta=1e-21,
+                  engine=args.engine)
+    n_kin, n_cl = s.closure_shape()
+    s.step(max(args.warmup, 3))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(args.steps)
+    e1.record(s.stream)
+    e1.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kt = s.time_kernels(min(args.steps, 50))
+    if rank != 0:
+        return 0
+    cells = cells_of(spec)
+    flops = 2 * (17 * 128 + 128 * 128 + 128) * n_cl
+    peaks = measured_peaks()
+    peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+    achieved = flops / (kt["closure"] / 1e3) / 1e12
+    line = {"metric": METRIC, "value": world * cells * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
+            "data": "synthetic (seeded density field, seeded random closure weights)",
+            "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"]],
+                       "closure_engine": args.engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
+                       "l2": "inputs larger than L2"},
+            "kernel_ms": kt,
+            "roofline": {"bound": "tensor", "kernel": "k_closure", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "alg_flops_per_launch": flops, "launch_ms": kt["closure"],
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
             "gpu_launches": args.steps * (4 if n_kin else 3) + math.ceil(args.steps / 32),
             "clocks": clk}

@@ -206,6 +206,8 @@ WORKLOADS = {
     # gas at 0.026 eV), FP32 delta f
     "3d_256_f0evolve_f32": lambda: _evolving(spec_3d_slab(n=256, slab=(96, 160), src_k=12, f_dtype="f32")),
     "2d_tmz_8192_closure": lambda: spec_closure_8192(),
+    # inference cost of the closure on every plasma cell of the 2048^2 cylinder (seeded random weights)
+    "2d_tmz_2048_closure_cost": lambda: spec_2d_cylinder(n=2048, R=512),
     "batch1d_256_f32": lambda: batch_runs_1d(),
     "batch1d_256_bf16": lambda: batch_runs_1d(f_dtype="bf16"),
 }
