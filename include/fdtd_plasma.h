@@ -214,6 +214,23 @@ typedef struct {
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
+/* Guard bytes (no counterpart in the paper; a stand-in for a memory checker):
+ * when the environment variable FDTD_PLASMA_CANARIES is "1" at
+ * fdtd_plasma_create, every device allocation of the handle gets 256 bytes of
+ * a fixed pattern before and after it.  This call synchronises the handle's
+ * stream and stores in *corrupted (host) how many allocations have a changed
+ * guard byte; FDTD_ERR_STATE when the handle was created without guards. */
+int fdtd_plasma_check_canaries(fdtd_plasma_t h, int64_t *corrupted);
+
+/* Self-test of the bounded waits (no counterpart in the paper): the tcgen05
+ * kernels wait for their tensor-core results on an mbarrier with an iteration
+ * limit, after which they set an error word (reported as FDTD_ERR_TIMEOUT by
+ * fdtd_plasma_diagnostics) and return instead of hanging.  This launches one
+ * CTA that waits, with the same helper, on a barrier nothing arrives at, for
+ * max_iter tries (1..2^20), and stores 1 in *gave_up (host) when the wait gave
+ * up as designed, 0 if it completed.  Synchronous, on the legacy stream. */
+int fdtd_selftest_wait_timeout(uint32_t max_iter, int32_t *gave_up);
+
 /* Runtime options.  FDTD_OPT_FUSED_STENCILS (default 0): 1 makes the step
  * sequence on 3-D FP32 grids fuse each E update with the next H update into
  * one pass (fields and CPML psi double-buffered: one extra copy of them is

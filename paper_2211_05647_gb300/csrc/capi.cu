@@ -18,6 +18,8 @@
 
 #include <sys/stat.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 using namespace fp;
@@ -52,9 +54,42 @@ int cuda_fail(fdtd_plasma *h, cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);      \
     } while (0)
 
+// Canary pads: with h->canary every allocation gets kCanaryPad guard bytes of
+// kCanaryByte before and after the user range (alignment is kept: the pad is
+// 256 bytes); fdtd_plasma_check_canaries compares them with the pattern.
+// NVTX range around a public entry point (visible in Nsight Systems / Compute timelines)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+constexpr size_t kCanaryPad = 256;
+constexpr unsigned char kCanaryByte = 0xA5;
+
+void *dalloc_raw(fdtd_plasma *h, size_t bytes);
+
 void *dalloc(fdtd_plasma *h, size_t bytes)
 {
     if (bytes == 0) bytes = 256;
+    if (!h->canary) return dalloc_raw(h, bytes);
+    char *raw = static_cast<char *>(dalloc_raw(h, bytes + 2 * kCanaryPad));
+    if (!raw) return nullptr;
+    if (cudaMemset(raw, kCanaryByte, kCanaryPad) != cudaSuccess ||
+        cudaMemset(raw + kCanaryPad + bytes, kCanaryByte, kCanaryPad) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {   // done before any work on the handle's stream
+        cudaGetLastError();
+        if (h->rt.free) h->rt.free(raw, h->rt.alloc_ctx);
+        else cudaFree(raw);
+        return nullptr;
+    }
+    h->canary_allocs.push_back({raw + kCanaryPad, bytes});
+    return raw + kCanaryPad;
+}
+
+void *dalloc_raw(fdtd_plasma *h, size_t bytes)
+{
     void *p = nullptr;
     if (h->rt.alloc) {
         p = h->rt.alloc(bytes, h->rt.alloc_ctx);
@@ -73,6 +108,15 @@ void *dalloc(fdtd_plasma *h, size_t bytes)
 void dfree(fdtd_plasma *h, void *p)
 {
     if (!p) return;
+    if (h->canary) {
+        auto &v = h->canary_allocs;
+        for (size_t q = 0; q < v.size(); ++q)
+            if (v[q].first == p) {
+                v.erase(v.begin() + (std::ptrdiff_t)q);
+                p = static_cast<char *>(p) - kCanaryPad;
+                break;
+            }
+    }
     if (h->rt.free) h->rt.free(p, h->rt.alloc_ctx);
     else cudaFree(p);
 }
@@ -615,7 +659,11 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     }
 
     fdtd_plasma *h = new (std::nothrow) fdtd_plasma();
-    if (h) h->fuse = 0;
+    if (h) {
+        h->fuse = 0;
+        const char *cv = std::getenv("FDTD_PLASMA_CANARIES");
+        h->canary = cv && cv[0] == '1';
+    }
     if (!h) return fail(nullptr, FDTD_ERR_NOMEM, "host allocation failed");
     h->g = *g;
     if (rt) h->rt = *rt;
@@ -713,6 +761,27 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     return FDTD_OK;
 }
 
+int fdtd_plasma_check_canaries(fdtd_plasma_t h, int64_t *corrupted)
+{
+    NvtxRange nvtx_("fdtd_plasma_check_canaries");
+    if (!h || !corrupted) return FDTD_ERR_INVAL;
+    if (!h->canary) return fail(h, FDTD_ERR_STATE, "canaries are off (set FDTD_PLASMA_CANARIES=1 before create)");
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::vector<unsigned char> pad(2 * kCanaryPad);
+    int64_t bad = 0;
+    for (const auto &a : h->canary_allocs) {
+        CK(h, cudaMemcpy(pad.data(), a.first - kCanaryPad, kCanaryPad, cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(pad.data() + kCanaryPad, a.first + a.second, kCanaryPad, cudaMemcpyDeviceToHost));
+        for (unsigned char c : pad)
+            if (c != kCanaryByte) {
+                ++bad;
+                break;
+            }
+    }
+    *corrupted = bad;
+    return FDTD_OK;
+}
+
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
 {
     if (!h) return FDTD_ERR_INVAL;
@@ -798,6 +867,7 @@ int fdtd_plasma_set_source(fdtd_plasma_t h, const fdtd_source_desc *s)
 
 int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
 {
+    NvtxRange nvtx_("fdtd_plasma_set_plasma");
     if (!h || !p) return FDTD_ERR_INVAL;
     if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_plasma after stepping: call fdtd_plasma_reset first");
     if (!p->density) return fail(h, FDTD_ERR_INVAL, "density is NULL");
@@ -937,6 +1007,7 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
 
 int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
 {
+    NvtxRange nvtx_("fdtd_plasma_step");
     if (!h) return FDTD_ERR_INVAL;
     if (nsteps < 0) return fail(h, FDTD_ERR_INVAL, "nsteps < 0");
     if (nsteps == 0) return FDTD_OK;
@@ -966,6 +1037,7 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
 
 int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
 {
+    NvtxRange nvtx_("fdtd_plasma_set_closure");
     if (!h || !c || !c->params) return FDTD_ERR_INVAL;
     if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "set_closure needs a plasma (set_plasma first)");
     if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_closure after stepping: call fdtd_plasma_reset first");
@@ -1155,6 +1227,7 @@ extern "C" {
 
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out)
 {
+    NvtxRange nvtx_("fdtd_plasma_autotune");
     if (!h || !out) return FDTD_ERR_INVAL;
     // the candidates run on the live buffers: save the state and restore it bit for bit afterwards
     const size_t nb = fdtd_plasma_state_bytes(h);
@@ -1172,6 +1245,7 @@ int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out)
 
 int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out)
 {
+    NvtxRange nvtx_("fdtd_plasma_time_kernels");
     if (!h || !ms_out || nsteps < 1) return FDTD_ERR_INVAL;
     cudaEvent_t ev[5];
     for (int q = 0; q < 5; ++q) CK(h, cudaEventCreate(&ev[q]));
@@ -1240,11 +1314,13 @@ static int copy_quantity(fdtd_plasma_t h, int which, void *host_or_dev, size_t b
 
 int fdtd_plasma_read_fields(fdtd_plasma_t h, int which, void *dst, size_t bytes, int dst_is_device)
 {
+    NvtxRange nvtx_("fdtd_plasma_read_fields");
     return copy_quantity(h, which, dst, bytes, dst_is_device, true);
 }
 
 int fdtd_plasma_write_fields(fdtd_plasma_t h, int which, const void *src, size_t bytes, int src_is_device)
 {
+    NvtxRange nvtx_("fdtd_plasma_write_fields");
     if (h && which == FDTD_J) return fail(h, FDTD_ERR_INVAL, "J is not writable");
     return copy_quantity(h, which, const_cast<void *>(src), bytes, src_is_device, false);
 }
@@ -1267,6 +1343,7 @@ int fdtd_plasma_info(fdtd_plasma_t h, double *dt, int64_t *steps)
 
 int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
 {
+    NvtxRange nvtx_("fdtd_plasma_diagnostics");
     if (!h || !out) return FDTD_ERR_INVAL;
     const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
     DiagArgs a{};
@@ -1312,6 +1389,7 @@ void free_ports(fdtd_plasma *h)
 int fdtd_plasma_set_ports(fdtd_plasma_t h, int32_t nports, const int64_t *port_offsets, const int64_t *cells,
                           int32_t nfreq, const double *freqs)
 {
+    NvtxRange nvtx_("fdtd_plasma_set_ports");
     if (!h) return FDTD_ERR_INVAL;
     if (nports == 0) {
         drop_graphs(h);
@@ -1355,6 +1433,7 @@ int fdtd_plasma_set_ports(fdtd_plasma_t h, int32_t nports, const int64_t *port_o
 
 int fdtd_plasma_read_ports(fdtd_plasma_t h, double *out, size_t bytes)
 {
+    NvtxRange nvtx_("fdtd_plasma_read_ports");
     if (!h || !out) return FDTD_ERR_INVAL;
     const size_t need = (size_t)h->nports * h->nfreq * 2 * sizeof(double);
     if (h->nports == 0) return fail(h, FDTD_ERR_STATE, "fdtd_plasma_read_ports: no ports set");
@@ -1366,6 +1445,7 @@ int fdtd_plasma_read_ports(fdtd_plasma_t h, double *out, size_t bytes)
 
 int fdtd_plasma_poynting(fdtd_plasma_t h, const int64_t *box, double *out)
 {
+    NvtxRange nvtx_("fdtd_plasma_poynting");
     if (!h || !box || !out) return FDTD_ERR_INVAL;
     const int nd = h->g.ndim;
     // E-node extent per axis; axes a 1-D or 2-D grid does not have are ignored
@@ -1442,6 +1522,7 @@ size_t fdtd_plasma_state_bytes(fdtd_plasma_t h)
 
 int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int dev)
 {
+    NvtxRange nvtx_("fdtd_plasma_save_state");
     if (!h || !buf) return FDTD_ERR_INVAL;
     std::vector<std::pair<void *, size_t>> parts;
     const size_t need = state_parts(h, parts);
@@ -1461,6 +1542,7 @@ int fdtd_plasma_save_state(fdtd_plasma_t h, void *buf, size_t bytes, int dev)
 
 int fdtd_plasma_load_state(fdtd_plasma_t h, const void *buf, size_t bytes, int dev)
 {
+    NvtxRange nvtx_("fdtd_plasma_load_state");
     if (!h || !buf) return FDTD_ERR_INVAL;
     std::vector<std::pair<void *, size_t>> parts;
     const size_t need = state_parts(h, parts);

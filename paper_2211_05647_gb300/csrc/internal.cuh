@@ -257,7 +257,10 @@ struct fdtd_plasma {
     // second field / psi set for the fused 3-D E+H kernel (allocated on first use)
     void *f2[6];
     void *psi2[12];
-    int fuse;                 // FDTD_OPT_FUSED_STENCILS (default 1)
+    int fuse;                 // FDTD_OPT_FUSED_STENCILS (default 0)
+    // guard bytes around every device allocation ($FDTD_PLASMA_CANARIES=1 at create)
+    int canary;
+    std::vector<std::pair<char *, size_t>> canary_allocs;   // (user pointer, user bytes)
     void *prof;               // CPML tables
     int64_t prof_len;
     void *mur_state;

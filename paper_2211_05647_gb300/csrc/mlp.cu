@@ -185,6 +185,18 @@ __global__ void __launch_bounds__(128) k_mlp_forward_tc(const float *__restrict_
     mlp_tc_teardown(s);
 }
 
+// Self-test of the bounded mbarrier wait the tcgen05 kernels use: one CTA
+// waits on a barrier that nothing arrives at; the wait gives up after max_iter
+// tries and the kernel records that it did, instead of hanging.
+__global__ void k_wait_selftest(uint32_t max_iter, int *gave_up)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool done = mbar_wait(&bar, 0u, max_iter);
+    if (threadIdx.x == 0) *gave_up = done ? 0 : 1;
+}
+
 }  // namespace fp
 
 using namespace fp;
@@ -289,6 +301,25 @@ int fdtd_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t 
                                                                             c1, c2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
+int fdtd_selftest_wait_timeout(uint32_t max_iter, int32_t *gave_up)
+{
+    if (!gave_up || max_iter == 0 || max_iter > (1u << 20))
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_selftest_wait_timeout: gave_up NULL or max_iter not in 1..2^20");
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return fp_set_global_error(FDTD_ERR_NOMEM, "cudaMalloc failed");
+    int h = -1;
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(max_iter, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    *gave_up = h;
     return FDTD_OK;
 }
 

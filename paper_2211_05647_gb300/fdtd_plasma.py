@@ -137,6 +137,8 @@ SIGNATURES = {
     "fdtd_plasma_diagnostics": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_diag)]),
     "fdtd_plasma_poynting": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
+    "fdtd_plasma_check_canaries": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "fdtd_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
     "fdtd_plasma_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "fdtd_plasma_launch_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_tune_result)]),
     "fdtd_plasma_set_ports": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -276,6 +278,14 @@ def _plasma_desc(density_ptr, on_device, vgrid="signed1d", nv=64, nv_perp=1, te_
 
 
 # ------------------------------------------------------------ closure network
+def selftest_wait_timeout(max_iter: int = 1000) -> bool:
+    """Run the bounded-wait self-test; True when the wait gave up as designed."""
+    lib = load_library()
+    out = ctypes.c_int32(-1)
+    _check(lib, None, lib.fdtd_selftest_wait_timeout(int(max_iter), ctypes.byref(out)))
+    return out.value == 1
+
+
 def mlp_forward(params, x, stream=None):
     """y = MLP(x) on the GPU (params [18945], x [B, 17]; torch float32 cuda tensors)."""
     import torch
@@ -534,6 +544,12 @@ class Solver:
         r = fdtd_tune_result()
         _check(self.lib, self.h, self.lib.fdtd_plasma_autotune(self.h, ctypes.byref(r)))
         return {k: getattr(r, k) for k, _ in fdtd_tune_result._fields_}
+
+    def check_canaries(self) -> int:
+        """Allocations whose guard bytes changed (needs FDTD_PLASMA_CANARIES=1 at create)."""
+        n = ctypes.c_int64(-1)
+        _check(self.lib, self.h, self.lib.fdtd_plasma_check_canaries(self.h, ctypes.byref(n)))
+        return n.value
 
     def set_option(self, option: str, value: int):
         """Runtime option: "fused_stencils" (0 / 1, default 0; see FDTD_OPT_FUSED_STENCILS)."""
