@@ -59,6 +59,23 @@ def make_spec(name: str):
     return WORKLOADS[name]()
 
 
+def reduce_max(x: float, world: int, device=None) -> float:
+    """The largest x over the ranks of the job (x itself for a one-rank job):
+    the job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes units_per_rank in the job's time."""
+    return world * units_per_rank / seconds
+
+
 def sample_spec(name: str):
     """The bounded CPU sample of a workload: the same recipe with every length
     scaled down (same plasma fraction, velocity grid and precision choice)."""
@@ -262,14 +279,10 @@ def main():
     e1.record(st)
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1), world, f"cuda:{local}")
     ms_step = ms / args.steps
-    value = world * cells * args.steps / (ms / 1e3) / 1e9
-    ps_rate = world * ns * nn * args.steps / (ms / 1e3)
+    value = job_rate(cells * args.steps, world, ms / 1e3) / 1e9
+    ps_rate = job_rate(ns * nn * args.steps, world, ms / 1e3)
 
     # per-kernel launch durations (eager launches with CUDA events on the solver's stream)
     kt = s.time_kernels(min(args.steps, 200))
@@ -306,10 +319,7 @@ def main():
         d2h += o.numel() * o.element_size()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t_e2e0
-    te = torch.tensor([t_e2e], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * cells * args.steps / float(te.item()) / 1e9
+    e2e_value = job_rate(cells * args.steps, world, reduce_max(t_e2e, world, f"cuda:{local}")) / 1e9
 
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
@@ -417,6 +427,8 @@ def closure_bench(args, spec, rank, world, local):
     ms_k, f_k, kt_k, _ = timed(False)
     err = {f: float(np.linalg.norm(f_c[f].astype(np.float64) - f_k[f]) / np.linalg.norm(f_k[f].astype(np.float64)))
            for f in f_c}
+    ms_c = reduce_max(ms_c, world, f"cuda:{local}")
+    ms_k = reduce_max(ms_k, world, f"cuda:{local}")
     if rank != 0:
         return 0
     cells = cells_of(spec)
@@ -424,7 +436,8 @@ def closure_bench(args, spec, rank, world, local):
     peaks = measured_peaks()
     peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
     achieved = flops / (kt_c["closure"] / 1e3) / 1e12 if kt_c["closure"] > 0 else 0.0
-    line = {"metric": METRIC, "value": cells * args.steps / (ms_c / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC, "value": job_rate(cells * args.steps, world, ms_c / 1e3) / 1e9, "unit": UNIT,
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
             "data": "synthetic (seeded density fields; training data from kinetic runs)",
@@ -434,7 +447,7 @@ def closure_bench(args, spec, rank, world, local):
                        "l2": "inputs larger than L2"},
             "closure_vs_kinetic": {"kinetic_ms_per_step": ms_k / args.steps, "closure_ms_per_step": ms_c / args.steps,
                                    "speedup": ms_k / ms_c, "field_rel_l2": err,
-                                   "kinetic_gcell_per_s": cells * args.steps / (ms_k / 1e3) / 1e9},
+                                   "kinetic_gcell_per_s": job_rate(cells * args.steps, world, ms_k / 1e3) / 1e9},
             "kernel_ms": {"closure_run": kt_c, "kinetic_run": kt_k},
             "roofline": {"bound": "tensor", "kernel": "k_closure", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
@@ -469,7 +482,7 @@ def closure_cost_bench(args, spec, rank, world, local):
     e1.record(s.stream)
     e1.synchronize()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = reduce_max(e0.elapsed_time(e1), world, f"cuda:{local}")
     kt = s.time_kernels(min(args.steps, 50))
     if rank != 0:
         return 0
@@ -478,9 +491,9 @@ def closure_cost_bench(args, spec, rank, world, local):
     peaks = measured_peaks()
     peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
     achieved = flops / (kt["closure"] / 1e3) / 1e12
-    line = {"metric": METRIC, "value": world * cells * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
+    line = {"metric": METRIC, "value": job_rate(cells * args.steps, world, ms / 1e3) / 1e9, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
             "data": "synthetic (seeded density field, seeded random closure weights)",
             "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"]],
                        "closure_engine": args.engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
@@ -530,11 +543,8 @@ def batch_bench(args, specs, rank, world, local):
     clk = clocks.stop()
     ms = evs[0].elapsed_time(e_end)
     launch_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps // chunk)]
-    t = torch.tensor([ms], device=f"cuda:{local}")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = world * cells * args.steps / (ms / 1e3) / 1e9
+    ms = reduce_max(ms, world, f"cuda:{local}")
+    value = job_rate(cells * args.steps, world, ms / 1e3) / 1e9
     # e2e: creation from host specs (density upload), K steps, every run's E and J back to host
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -544,7 +554,7 @@ def batch_bench(args, specs, rank, world, local):
     for r in range(b2.nruns):
         d2h += b2.read(r, "ex").nbytes + b2.read(r, "j").nbytes
     torch.cuda.synchronize()
-    te = time.perf_counter() - t0
+    te = reduce_max(time.perf_counter() - t0, world, f"cuda:{local}")
     h2d = sum(sp["plasma"]["density"].nbytes for sp in specs)
     b2.close()
     if rank != 0:
@@ -564,14 +574,14 @@ def batch_bench(args, specs, rank, world, local):
                        "f_dtype": fdt, "clusters": info["clusters"], "ctas_per_cluster": info["cluster_ctas"], "steps_per_launch": chunk,
                        "l2": "inputs larger than L2 (delta f %.2f GB)" % (nodes * fb / 1e9),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "phase_space_updates_per_s": world * nodes * args.steps / (ms / 1e3),
+            "phase_space_updates_per_s": job_rate(nodes * args.steps, world, ms / 1e3),
             "roofline": {"bound": "hbm", "kernel": "k_batch1d", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg_step * chunk,
                          "launch_ms": per_launch_ms,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
             "gpu_launches": 2 * (args.steps // chunk + (1 if rem else 0)),
             "clocks": clk,
-            "e2e": {"value": world * cells * args.steps / te / 1e9, "unit": UNIT,
+            "e2e": {"value": job_rate(cells * args.steps, world, te) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}}
     if world == 1 and not args.no_cpu_baseline:
         g, psr, n, text, _, _ = oracle_throughput(args.workload, 10 ** 6, 2, budget_s=15.0)
