@@ -18,7 +18,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -43,7 +42,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="mma", choices=["mma", "tcgen05"], help="closure MLP engine")
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
-                    help="3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
+                    help="2-D / 3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
     return ap.parse_args()
@@ -69,6 +68,19 @@ def reduce_max(x: float, world: int, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def step_launches(steps, mid_per_step, fused):
+    """Kernels the solver launches for `steps` steps: 32-step graph replays,
+    then 1-step graphs.  An n-step sequence runs H_0, per step the middle
+    kernels and E, H for all but the last step, and one step-counter advance;
+    each fused transition (an even number of the n - 1) makes E_k + H_{k+1}
+    one launch."""
+    def seq(n):
+        f = (n - 1) - (n - 1) % 2 if fused else 0
+        return mid_per_step * n + 2 * n - f + 1
+    chunks, rem = divmod(steps, 32)
+    return chunks * seq(32) + rem * seq(1)
 
 
 def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
@@ -286,7 +298,7 @@ def main():
 
     # per-kernel launch durations (eager launches with CUDA events on the solver's stream)
     kt = s.time_kernels(min(args.steps, 200))
-    fused = bool(args.fused) and spec["grid"]["ndim"] == 3 and s.precision == "f32"
+    fused = bool(args.fused) and spec["grid"]["ndim"] >= 2 and s.precision == "f32"
 
     # end-to-end through the public API: plasma density and initial fields from
     # pinned host memory, K steps, final fields and J back to pinned host memory
@@ -357,13 +369,13 @@ def main():
             "phase_space_updates_per_s": ps_rate,
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "kernel_ms": kt,
-            # kernel_ms times one unfused step; on 3-D FP32 grids the timed steps fuse each E update with the
-            # next H update, so their stencil time is the step time less the kinetic and closure kernels
+            # kernel_ms times one unfused step; with fused_stencils the timed steps fuse each E update with
+            # the next H update, so their stencil time is the step time less the kinetic and closure kernels
             "fused_stencils": fused,
             "stencil_ms_in_step": ms_step - kt["kinetic"] - kt["closure"],
             "launch_shapes": dict(shapes, tuned=tune is not None),
             "roofline": roof,
-            "gpu_launches": args.steps * 3 + math.ceil(args.steps / 32) if ns else args.steps * 2 + math.ceil(args.steps / 32),
+            "gpu_launches": step_launches(args.steps, 1 if ns else 0, fused),
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps}}
@@ -453,7 +465,7 @@ def closure_bench(args, spec, rank, world, local):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "alg_flops_per_launch": flops, "launch_ms": kt_c["closure"],
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
-            "gpu_launches": args.steps * (4 if n_kin else 3) + math.ceil(args.steps / 32),
+            "gpu_launches": step_launches(args.steps, 2 if n_kin else 1, False),
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
@@ -503,7 +515,7 @@ def closure_cost_bench(args, spec, rank, world, local):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "alg_flops_per_launch": flops, "launch_ms": kt["closure"],
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
-            "gpu_launches": args.steps * (4 if n_kin else 3) + math.ceil(args.steps / 32),
+            "gpu_launches": step_launches(args.steps, 2 if n_kin else 1, False),
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0

@@ -232,7 +232,7 @@ int fdtd_plasma_check_canaries(fdtd_plasma_t h, int64_t *corrupted);
 int fdtd_selftest_wait_timeout(uint32_t max_iter, int32_t *gave_up);
 
 /* Runtime options.  FDTD_OPT_FUSED_STENCILS (default 0): 1 makes the step
- * sequence on 3-D FP32 grids fuse each E update with the next H update into
+ * sequence on 2-D and 3-D FP32 grids fuse each E update with the next H update into
  * one pass (fields and CPML psi double-buffered: one extra copy of them is
  * allocated on first use; the fields are back in place when
  * fdtd_plasma_step returns).  It moves a third fewer bytes but is slower than

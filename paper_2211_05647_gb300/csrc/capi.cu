@@ -531,7 +531,7 @@ void free_second_set(fdtd_plasma *h)
 // allocate the second field / psi set when the fused sequence applies; on failure the steps run unfused
 void ensure_second_set(fdtd_plasma *h)
 {
-    if (!h->fuse || h->g.ndim != 3 || h->g.precision != FDTD_F32 || h->f2[0]) return;
+    if (!h->fuse || h->g.ndim < 2 || h->g.precision != FDTD_F32 || h->f2[FDTD_EZ]) return;
     bool ok = true;
     for (int q = 0; q < 6 && ok; ++q)
         if (h->flen[q]) ok = (h->f2[q] = dalloc(h, h->flen[q] * h->esz)) != nullptr;
@@ -543,10 +543,10 @@ void ensure_second_set(fdtd_plasma *h)
     }
 }
 
-// whether the step sequence fuses E^{n+1} with H^{n+3/2} (3-D FP32, second field set allocated)
+// whether the step sequence fuses E^{n+1} with H^{n+3/2} (2-D / 3-D FP32, second field set allocated)
 bool fused_stencils(const fdtd_plasma *h)
 {
-    return h->fuse && h->g.ndim == 3 && h->g.precision == FDTD_F32 && h->f2[0] != nullptr;
+    return h->fuse && h->g.ndim >= 2 && h->g.precision == FDTD_F32 && h->f2[FDTD_EZ] != nullptr;
 }
 
 // nsteps steps: H_0, then per step the middle part and either E_k alone (then
@@ -571,9 +571,14 @@ cudaError_t enqueue_seq(fdtd_plasma *h, cudaStream_t st, int nsteps)
             const FieldSet<T> to = field_set<T>(h, set ^ 1);
             const double mu0 = 1.0 / (kEps0 * kC0 * kC0);
             if constexpr (sizeof(T) == 4) {
-                launch_eh3d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, h->nz, (float)(h->dt / (kEps0 * h->g.dx)),
-                            (float)(h->dt / kEps0), (float)(h->dt / (mu0 * h->g.dx)), (float)(h->dt / mu0), fs.cp,
-                            source_view(h), h->d_step, k);
+                const float ce = (float)(h->dt / (kEps0 * h->g.dx)), cpe = (float)(h->dt / kEps0);
+                const float ch = (float)(h->dt / (mu0 * h->g.dx)), cph = (float)(h->dt / mu0);
+                if (h->g.ndim == 3)
+                    launch_eh3d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, h->nz, ce, cpe, ch, cph, fs.cp,
+                                source_view(h), h->d_step, k);
+                else
+                    launch_eh2d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, ce, cpe, ch, cph, fs.cp, source_view(h),
+                                h->d_step, k);
             }
             set ^= 1;
             e = part_ports<T>(h, st, k, to);

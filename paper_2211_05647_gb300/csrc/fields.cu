@@ -865,11 +865,149 @@ __global__ void __launch_bounds__(kEhX * kEhY, 3) k_eh3d(FieldPtrs in, FieldOut 
     }
 }
 
+// ------------------------------------------- 2-D fused E^{n+1} + H^{n+3/2} (FP32)
+// A block owns a 64 x 16 tile: it stages H^{n+1/2} (with the -x / -y halo) and
+// E' (E^n after the density term, with the +x / +y halo) in shared memory,
+// forms E^{n+1} on the tile and its +x / +y halo, stores the tile's E^{n+1},
+// then forms H^{n+3/2} on the tile.  Reads set `in`, writes set `out` (fields
+// and psi), so no block reads what another writes; two barriers per tile.
+constexpr int kF2X = 64, kF2Y = 16, kF2T = 256;
+
+__global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, const float *__restrict__ hx_in,
+                                               const float *__restrict__ hy_in, float *__restrict__ ez_out,
+                                               float *__restrict__ hx_out, float *__restrict__ hy_out, int64_t nx,
+                                               int64_t ny, float ce, float cpe, float ch, float cph, Cpml<float> cin,
+                                               PsiOut pout, Source src, const int64_t *__restrict__ d_step, int kstep)
+{
+    __shared__ float sHx[kF2Y + 2][kF2X + 2], sHy[kF2Y + 2][kF2X + 2];   // x0-1..x0+64, y0-1..y0+16
+    __shared__ float sEp[kF2Y + 1][kF2X + 1];                           // E': x0..x0+64, y0..y0+16
+    __shared__ float sE[kF2Y + 1][kF2X + 1];                            // E^{n+1}
+    __shared__ float s_g;
+    const int tid = threadIdx.x;
+    const int64_t x0 = (int64_t)blockIdx.x * kF2X, y0 = (int64_t)blockIdx.y * kF2Y;
+    const int64_t n1 = *d_step + kstep + 1;
+    if (tid == 0) {
+        const bool near = src.kind && src.i >= x0 && src.i <= x0 + kF2X && src.j >= y0 && src.j <= y0 + kF2Y;
+        s_g = near ? (float)source_value(src, (double)n1 * src.dt) : 0.f;
+        if (src.kind && blockIdx.x == 0 && blockIdx.y == 0) *src.val = source_value(src, (double)(n1 + 1) * src.dt);
+    }
+    for (int r = tid; r < (kF2Y + 2) * (kF2X + 2); r += kF2T) {
+        const int rx = r % (kF2X + 2), ry = r / (kF2X + 2);
+        const int64_t i = x0 - 1 + rx, j = y0 - 1 + ry;
+        const bool ok = i >= 0 && i < nx && j >= 0 && j < ny;
+        const int64_t c = ok ? j * nx + i : 0;
+        sHx[ry][rx] = ok ? hx_in[c] : 0.f;
+        sHy[ry][rx] = ok ? hy_in[c] : 0.f;
+    }
+    for (int r = tid; r < (kF2Y + 1) * (kF2X + 1); r += kF2T) {
+        const int rx = r % (kF2X + 1), ry = r / (kF2X + 1);
+        const int64_t i = x0 + rx, j = y0 + ry;
+        const bool ok = i < nx && j < ny;
+        sEp[ry][rx] = ok ? ez_in[j * nx + i] : 0.f;
+    }
+    __syncthreads();
+    const int L = cin.L;
+    const bool pml = L > 0 && (x0 < L || x0 + kF2X >= nx - L || y0 < L || y0 + kF2Y >= ny - L);
+    // E^{n+1} on the tile and its +x / +y halo (PEC rows and columns keep E')
+    for (int r = tid; r < (kF2Y + 1) * (kF2X + 1); r += kF2T) {
+        const int rx = r % (kF2X + 1), ry = r / (kF2X + 1);
+        const int64_t i = x0 + rx, j = y0 + ry;
+        float e = 0.f;
+        if (i < nx && j < ny) {
+            e = sEp[ry][rx];
+            if (i >= 1 && j >= 1) {
+                const float dHx = sHy[ry + 1][rx + 1] - sHy[ry + 1][rx];   // dHy along x
+                const float dHy = sHx[ry + 1][rx + 1] - sHx[ry][rx + 1];   // dHx along y
+                const bool own = rx < kF2X && ry < kF2Y;
+                float upd;
+                if (!pml) {
+                    upd = ce * (dHx - dHy);
+                } else {
+                    float px = 0.f, py = 0.f, kx = 1.f, ky = 1.f;
+                    if (in_slab<float>(i, nx, L)) {
+                        const int64_t o = j * (2 * L) + slab_slot<float>(i, nx, L);
+                        px = cin.be[0][i] * cin.psi[0][o] + cin.ae[0][i] * dHx;
+                        if (own) pout.psi[0][o] = px;
+                        kx = cin.ike[0][i];
+                    }
+                    if (in_slab<float>(j, ny, L)) {
+                        const int64_t o = (int64_t)slab_slot<float>(j, ny, L) * nx + i;
+                        py = cin.be[1][j] * cin.psi[1][o] + cin.ae[1][j] * dHy;
+                        if (own) pout.psi[1][o] = py;
+                        ky = cin.ike[1][j];
+                    }
+                    upd = ce * (dHx * kx - dHy * ky) + cpe * (px - py);
+                }
+                e += upd;
+                if (src.kind && i == src.i && j == src.j) e += s_g;
+            } else if (pml && rx < kF2X && ry < kF2Y) {
+                // PEC wall cell: the E update leaves its psi as it is; carry it into the out set
+                if (in_slab<float>(i, nx, L)) {
+                    const int64_t o = j * (2 * L) + slab_slot<float>(i, nx, L);
+                    pout.psi[0][o] = cin.psi[0][o];
+                }
+                if (in_slab<float>(j, ny, L)) {
+                    const int64_t o = (int64_t)slab_slot<float>(j, ny, L) * nx + i;
+                    pout.psi[1][o] = cin.psi[1][o];
+                }
+            }
+            if (rx < kF2X && ry < kF2Y) ez_out[j * nx + i] = e;
+        }
+        sE[ry][rx] = e;
+    }
+    __syncthreads();
+    // H^{n+3/2} on the tile
+    for (int r = tid; r < kF2Y * kF2X; r += kF2T) {
+        const int rx = r % kF2X, ry = r / kF2X;
+        const int64_t i = x0 + rx, j = y0 + ry;
+        if (i >= nx || j >= ny) continue;
+        const float e = sE[ry][rx];
+        const float dEy = sE[ry + 1][rx] - e;   // dEz along y (0 past the last row)
+        const float dEx = sE[ry][rx + 1] - e;   // dEz along x
+        float hxv = sHx[ry + 1][rx + 1], hyv = sHy[ry + 1][rx + 1];
+        if (!pml) {
+            hxv -= ch * dEy;
+            hyv += ch * dEx;
+        } else {
+            if (in_slab<float>(j, ny, L)) {
+                const int64_t o = (int64_t)slab_slot<float>(j, ny, L) * nx + i;
+                const float ps = cin.bh[1][j] * cin.psi[2][o] + cin.ah[1][j] * dEy;
+                pout.psi[2][o] = ps;
+                hxv -= ch * dEy * cin.ikh[1][j] + cph * ps;
+            } else {
+                hxv -= ch * dEy;
+            }
+            if (in_slab<float>(i, nx, L)) {
+                const int64_t o = j * (2 * L) + slab_slot<float>(i, nx, L);
+                const float ps = cin.bh[0][i] * cin.psi[3][o] + cin.ah[0][i] * dEx;
+                pout.psi[3][o] = ps;
+                hyv += ch * dEx * cin.ikh[0][i] + cph * ps;
+            } else {
+                hyv += ch * dEx;
+            }
+        }
+        const int64_t c = j * nx + i;
+        hx_out[c] = hxv;
+        hy_out[c] = hyv;
+    }
+}
+
 __global__ void k_advance(int64_t *d_step, int64_t by) { *d_step += by; }
 
 // ------------------------------------------------------------------ launchers
 
 static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+void launch_eh2d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
+                 int64_t ny, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
+                 const int64_t *d_step, int kstep)
+{
+    dim3 g(cdiv(nx, kF2X), cdiv(ny, kF2Y));
+    PsiOut po{};
+    for (int q = 0; q < 12; ++q) po.psi[q] = psi_out[q];
+    k_eh2d<<<g, kF2T, 0, st>>>(fin[FDTD_EZ], fin[FDTD_HX], fin[FDTD_HY], fout[FDTD_EZ], fout[FDTD_HX], fout[FDTD_HY],
+                               nx, ny, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
+}
 
 void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
                  int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,

@@ -140,7 +140,10 @@ void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t 
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
                 Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
-// 3-D FP32 fused E^{n+1} + H^{n+3/2}: reads fields fin and psi cin.psi, writes fout and psi_out
+// 2-D / 3-D FP32 fused E^{n+1} + H^{n+3/2}: read fields fin and psi cin.psi, write fout and psi_out
+void launch_eh2d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
+                 int64_t ny, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
+                 const int64_t *d_step, int kstep);
 void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
                  int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
                  const int64_t *d_step, int kstep);

@@ -1,12 +1,13 @@
-"""Fused 3-D E^{n+1} + H^{n+3/2} stencil pass (FP32, opt-in): the same physics as the
-unfused sequence (FP32 rounding order only), for step counts that exercise the
-parity rule (an odd number of fused transitions runs the first one unfused),
-the 32-step graph chunks and the 1-step graph, with CPML, a sheet source and a
-kinetic slab; and against the FP64 oracle."""
+"""Fused E^{n+1} + H^{n+3/2} stencil pass (2-D TMz and 3-D, FP32, opt-in): the
+same physics as the unfused sequence (FP32 rounding order only), for step
+counts that exercise the parity rule (an odd number of fused transitions runs
+the first one unfused), the 32-step graph chunks and the 1-step graph, with
+CPML, the source (a 3-D sheet; a 2-D point, also on a tile's halo node) and a
+kinetic region; and against the FP64 oracle."""
 import numpy as np
 import pytest
 
-from fdtd_inputs import spec_3d_slab
+from fdtd_inputs import spec_2d_cylinder, spec_3d_slab
 from tests.adapters import FIELDS, compare, oracle_sim, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -80,4 +81,79 @@ def test_fused_option_errors_and_checkpoint():
     r.load_state(blob)
     r.step(19)
     for q in FIELDS[3] + ["j"]:
+        assert np.array_equal(s.read(q, device=False), r.read(q, device=False)), q
+
+
+# ---------------------------------------------------------------- 2-D TMz
+# 150 x 70 cells leave ragged 64 x 16 tiles on both axes; with an 8-cell CPML
+# frame the tiles at x0 = 64, y0 = 16 / 32 are the CPML-free ones.
+
+def _spec2(steps, n=(150, 70), cpml=8, src=(40, 35)):
+    nx, ny = n
+    return spec_2d_cylinder(n=nx, ny=ny, cpml=cpml, R=min(nx, ny) // 4, center=(0.6 * nx, 0.5 * ny), src=src,
+                            nv=8, nv_perp=8, steps=steps, precision="f32", f_dtype="f32", seed=32)
+
+
+def _worst(fused, plain, quantities):
+    worst = 0.0
+    for q in quantities:
+        a, b = fused.read(q, device=False), plain.read(q, device=False)
+        if np.abs(b).max() == 0:
+            assert np.abs(a).max() == 0, q
+            continue
+        worst = max(worst, rel_l2(a, b))
+    return worst
+
+
+@pytest.mark.parametrize("calls", [(1,), (2,), (3,), (33,), (64, 5), (7, 1, 40)])
+def test_fused_2d_equals_unfused(calls):
+    fused, plain = _pair(_spec2(sum(calls)), calls)
+    worst = _worst(fused, plain, FIELDS[2] + ["j", "df"])
+    print(f"2-D calls {calls}: fused vs unfused max rel L2 {worst:.2e}")
+    assert worst <= 1e-6
+
+
+@pytest.mark.parametrize("src", [(64, 48), (63, 47), (149, 69)])
+def test_fused_2d_source_on_tile_edges(src):
+    """The point source on a node that one tile computes as halo and another
+    owns, on the last node of a tile, and on the grid's last node."""
+    spec = _spec2(70, cpml=0 if src == (149, 69) else 8, src=src)
+    fused, plain = _pair(spec, (70,))
+    assert _worst(fused, plain, FIELDS[2] + ["j"]) <= 1e-6
+
+
+def test_fused_2d_matches_oracle(oracle_lib):
+    spec = _spec2(260)
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec)
+    s.set_option("fused_stencils", 1)
+    s.step(100)
+    s.step(160)
+    sim = oracle_sim(oracle_lib, spec)
+    sim.step(260)
+    errs = compare(s, sim, 2)
+    print("fused 2-D f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
+
+
+def test_fused_2d_no_cpml_small_grid():
+    """A grid smaller than one tile (PEC walls only) and one a tile wide."""
+    for n, src in (((37, 13), (20, 6)), ((64, 16), (30, 8))):
+        fused, plain = _pair(_spec2(45, n=n, cpml=0, src=src), (45,))
+        assert _worst(fused, plain, FIELDS[2]) <= 1e-6, n
+
+
+def test_fused_2d_checkpoint():
+    from paper_2211_05647_gb300 import Solver
+    spec = _spec2(40)
+    s = Solver.from_spec(spec)
+    s.set_option("fused_stencils", 1)
+    s.step(21)
+    blob = s.save_state(device=False)
+    s.step(19)
+    r = Solver.from_spec(spec)
+    r.set_option("fused_stencils", 1)
+    r.load_state(blob)
+    r.step(19)
+    for q in FIELDS[2] + ["j", "df"]:
         assert np.array_equal(s.read(q, device=False), r.read(q, device=False)), q
