@@ -197,7 +197,8 @@ int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out);
 
 /* Launch-shape autotuner.  Times, with CUDA events on the handle's stream,
  * every candidate shape of the kinetic kernel (vectors per lane x lanes per
- * row x CTAs per SM) and of the curl-stencil kernels (thread-block shape) on
+ * row x CTAs per SM) and of the curl-stencil kernels (thread-block shape,
+ * cells per thread, and on 3-D FP32 grids the TMA column kernels) on
  * the handle's own buffers, adopts the fastest, and records them in a text
  * cache ($FDTD_PLASMA_TUNE_CACHE, else $HOME/.cache/fdtd_plasma/autotune.txt)
  * keyed by GPU name, kernel, precision and size class; later handles of the
@@ -210,7 +211,9 @@ typedef struct {
     double kin_ms, stencil_ms;                   /* best per-launch times */
     int32_t cells_per_thread;                    /* stencils: 1, or 4 (FP32 rows of a multiple of 4 cells;
                                                     block_x then counts groups of 4 cells) */
-    int32_t reserved;
+    int32_t stencil_tz;                          /* 3-D FP32 (nx a multiple of 4): > 0 when the TMA column
+                                                    stencils won -- 32 x 8 threads, each block walking
+                                                    stencil_tz planes along z; 0 = grid-of-cells kernels */
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
@@ -223,13 +226,21 @@ int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 int fdtd_plasma_check_canaries(fdtd_plasma_t h, int64_t *corrupted);
 
 /* Self-test of the bounded waits (no counterpart in the paper): the tcgen05
- * kernels wait for their tensor-core results on an mbarrier with an iteration
- * limit, after which they set an error word (reported as FDTD_ERR_TIMEOUT by
- * fdtd_plasma_diagnostics) and return instead of hanging.  This launches one
+ * kernels wait for their tensor-core results, and the TMA column stencils for
+ * their plane loads, on mbarriers with an iteration limit, after which they
+ * set an error word (reported as FDTD_ERR_TIMEOUT by fdtd_plasma_diagnostics
+ * and by host reads of fdtd_plasma_read_fields) and return instead of hanging.  This launches one
  * CTA that waits, with the same helper, on a barrier nothing arrives at, for
  * max_iter tries (1..2^20), and stores 1 in *gave_up (host) when the wait gave
  * up as designed, 0 if it completed.  Synchronous, on the legacy stream. */
 int fdtd_selftest_wait_timeout(uint32_t max_iter, int32_t *gave_up);
+
+/* The same for the wall-clock-bounded wait of the TMA column stencils (the
+ * waiting thread sleeps in the barrier between polls): one CTA waits on a
+ * barrier nothing arrives at until limit_us microseconds (1..10^6) have
+ * passed on the GPU's global timer, then stores 1 in *gave_up (host).
+ * Synchronous, on the legacy stream; FDTD_ERR_INVAL for a bad argument. */
+int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
 
 /* Runtime options.  FDTD_OPT_FUSED_STENCILS (default 0): 1 makes the step
  * sequence on 2-D and 3-D FP32 grids fuse each E update with the next H update into
@@ -238,8 +249,14 @@ int fdtd_selftest_wait_timeout(uint32_t max_iter, int32_t *gave_up);
  * fdtd_plasma_step returns).  It moves a third fewer bytes but is slower than
  * the two separate passes on GB300 at present.  Results equal the unfused
  * sequence up to FP32 rounding order.  0 turns it off (and frees the copy).
+ * FDTD_OPT_STENCIL_TZ: 0 selects the grid-of-cells 3-D stencil kernels; a
+ * value tz in 1..1024 selects the TMA column kernels (3-D FP32, nx a multiple
+ * of 4): 32 x 8 threads per block, each block walking tz planes along z with
+ * its planes staged in shared memory by tensor copies.  The autotuner sets it
+ * too (fdtd_tune_result.stencil_tz).  Results equal the grid-of-cells kernels
+ * bit for bit.
  * FDTD_ERR_INVAL for an unknown option or value. */
-enum { FDTD_OPT_FUSED_STENCILS = 1 };
+enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);
 
 /* The launch shapes the handle uses now (tuned, cached or default; kinetic

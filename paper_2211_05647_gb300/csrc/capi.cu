@@ -329,7 +329,7 @@ std::map<std::string, std::vector<int>> read_cache()
         int x;
         if (!(in >> k)) continue;
         while (in >> x) v.push_back(x);
-        if (v.size() == 3 || v.size() == 4) m[k] = v;
+        if (v.size() >= 3 && v.size() <= 5) m[k] = v;
     }
     return m;
 }
@@ -362,8 +362,9 @@ void apply_cached_stencil(fdtd_plasma *h)
 {
     auto m = read_cache();
     auto it = m.find(stencil_key(h));
-    if (it != m.end() && it->second.size() == 4) {
+    if (it != m.end() && it->second.size() >= 4) {
         h->st_bx = it->second[0]; h->st_by = it->second[1]; h->st_bz = it->second[2]; h->st_cpt = it->second[3];
+        h->st_tz = it->second.size() == 5 ? it->second[4] : 0;
     }
 }
 
@@ -386,6 +387,16 @@ FieldSet<T> field_set(fdtd_plasma *h, int set)
     return fs;
 }
 
+// the TMA column kernels' tensor maps when they are the selected 3-D stencils for this field set
+// (FP32, set 0); nullptr = run the grid-of-cells kernels
+template <typename T>
+const TmaMaps *tma_for(fdtd_plasma *h, const FieldSet<T> &fs)
+{
+    if (sizeof(T) != 4 || h->g.ndim != 3 || h->st_tz <= 0) return nullptr;
+    if (!h->tma) h->tma = tma_maps_create(reinterpret_cast<float *const *>(h->f), h->nx, h->ny, h->nz);
+    return tma_maps_match(h->tma, reinterpret_cast<float *const *>(fs.f)) ? h->tma : nullptr;
+}
+
 template <typename T>
 cudaError_t part_h(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs)
 {
@@ -399,9 +410,17 @@ cudaError_t part_h(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T>
     else if (h->g.ndim == 2)
         launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
-    else
+    else {
+        if constexpr (sizeof(T) == 4) {
+            if (const TmaMaps *t = tma_for(h, fs)) {
+                launch_h3d_tma(st, t, f, h->nx, h->ny, h->nz, ch, cph, fs.cp, src, h->d_step, kstep, h->st_tz,
+                               h->d_err);
+                return cudaGetLastError();
+            }
+        }
         launch_h3d<T>(st, const_cast<T *const *>(f), h->nx, h->ny, h->nz, ch, cph, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
+    }
     return cudaGetLastError();
 }
 
@@ -488,6 +507,12 @@ cudaError_t part_e(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T>
         launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
     } else {
+        if constexpr (sizeof(T) == 4) {
+            if (const TmaMaps *t = tma_for(h, fs)) {
+                launch_e3d_tma(st, t, f, h->nx, h->ny, h->nz, ce, cpe, fs.cp, src, h->st_tz, h->d_err);
+                return cudaGetLastError();
+            }
+        }
         launch_e3d<T>(st, const_cast<T *const *>(f), h->nx, h->ny, h->nz, ce, cpe, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
     }
@@ -798,6 +823,20 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
         if (!h->fuse) free_second_set(h);
         return FDTD_OK;
     }
+    if (option == FDTD_OPT_STENCIL_TZ) {
+        if (value < 0 || value > 1024) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_STENCIL_TZ takes 0 .. 1024");
+        if (value > 0) {
+            if (h->g.ndim != 3 || h->g.precision != FDTD_F32)
+                return fail(h, FDTD_ERR_INVAL, "the TMA column stencils run on 3-D FP32 grids");
+            if (!h->tma) h->tma = tma_maps_create(reinterpret_cast<float *const *>(h->f), h->nx, h->ny, h->nz);
+            if (!h->tma) return fail(h, FDTD_ERR_INVAL, "the TMA column stencils need nx a multiple of 4");
+        }
+        CK(h, cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        h->st_tz = (int)value;
+        if (value > 0) { h->st_bx = 32; h->st_by = 8; h->st_bz = 1; h->st_cpt = 1; }
+        return FDTD_OK;
+    }
     return fail(h, FDTD_ERR_INVAL, "unknown option %d", option);
 }
 
@@ -812,6 +851,7 @@ int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out)
         const dim3 b = stencil_block(h);
         out->block_x = (int32_t)b.x; out->block_y = (int32_t)b.y; out->block_z = (int32_t)b.z;
         out->cells_per_thread = stencil_cpt(h);
+        out->stencil_tz = h->st_tz;
     }
     return FDTD_OK;
 }
@@ -1162,7 +1202,7 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
         return ms / 5.0;
     };
     auto m = read_cache();
-    out->block_x = out->block_y = out->block_z = out->cells_per_thread = 0;
+    out->block_x = out->block_y = out->block_z = out->cells_per_thread = out->stencil_tz = 0;
     out->stencil_ms = 0;
     if (h->g.ndim >= 2) {
         static const int s2[][3] = {{32, 8, 1}, {64, 4, 1}, {128, 2, 1}, {256, 1, 1}, {32, 4, 1}, {64, 2, 1}};
@@ -1192,9 +1232,29 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
                 }
             }
         }
+        // 3-D FP32: the TMA column kernels, tz planes per block
+        if constexpr (sizeof(T) == 4) {
+            if (h->g.ndim == 3 && !h->tma) h->tma = tma_maps_create(f, h->nx, h->ny, h->nz);
+            if (h->g.ndim == 3 && h->tma) {
+                for (int tz : {8, 12, 16, 24, 32}) {
+                    if (tz > 2 * h->nz) continue;
+                    const double ms = time_ms([&] {
+                        launch_h3d_tma(st, h->tma, f, h->nx, h->ny, h->nz, ch, cph, cp, src, h->d_step, 0, tz,
+                                       h->d_err);
+                        launch_e3d_tma(st, h->tma, f, h->nx, h->ny, h->nz, ce, cpe, cp, src, tz, h->d_err);
+                    });
+                    if (ms < best) {
+                        best = ms;
+                        out->block_x = 32; out->block_y = 8; out->block_z = 1; out->cells_per_thread = 1;
+                        out->stencil_tz = tz;
+                    }
+                }
+            }
+        }
         h->st_bx = out->block_x; h->st_by = out->block_y; h->st_bz = out->block_z; h->st_cpt = out->cells_per_thread;
+        h->st_tz = out->stencil_tz;
         out->stencil_ms = best;
-        m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z, out->cells_per_thread};
+        m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z, out->cells_per_thread, out->stencil_tz};
     }
     out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = 0;
     out->kin_ms = 0;
@@ -1293,6 +1353,13 @@ size_t fdtd_plasma_quantity_bytes(fdtd_plasma_t h, int which)
     return 0;
 }
 
+// the device error word: bit 1 closure tensor-core waits, bit 2 TMA stencil waits
+static const char *wait_error_text(int errw)
+{
+    if (errw & 2) return "a bounded device wait gave up (TMA stencil kernel)";
+    return "a bounded device wait gave up (closure kernel)";
+}
+
 static int copy_quantity(fdtd_plasma_t h, int which, void *host_or_dev, size_t bytes, int is_device, bool out)
 {
     if (!h || !host_or_dev) return FDTD_ERR_INVAL;
@@ -1313,7 +1380,12 @@ static int copy_quantity(fdtd_plasma_t h, int which, void *host_or_dev, size_t b
         if (out) CK(h, cudaMemcpyAsync(host_or_dev, dev, bytes, kind, h->stream));
         else CK(h, cudaMemcpyAsync(dev, host_or_dev, bytes, kind, h->stream));
     }
-    if (!is_device) CK(h, cudaStreamSynchronize(h->stream));
+    if (!is_device) {
+        int errw = 0;
+        if (out) CK(h, cudaMemcpyAsync(&errw, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        if (errw) return fail(h, FDTD_ERR_TIMEOUT, "%s", wait_error_text(errw));
+    }
     return FDTD_OK;
 }
 
@@ -1372,7 +1444,7 @@ int fdtd_plasma_diagnostics(fdtd_plasma_t h, fdtd_diag *out)
     int errw = 0;
     CK(h, cudaMemcpyAsync(&errw, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (errw) return fail(h, FDTD_ERR_TIMEOUT, "a bounded device wait gave up (closure kernel)");
+    if (errw) return fail(h, FDTD_ERR_TIMEOUT, "%s", wait_error_text(errw));
     out->energy = o[0];
     out->energy_plain = o[1];
     out->number = o[2];
@@ -1589,6 +1661,7 @@ void fdtd_plasma_destroy(fdtd_plasma_t h)
     dfree(h, h->d_err);
     free_ports(h);
     free_second_set(h);
+    tma_maps_free(h->tma);
     dfree(h, h->diag_partials);
     dfree(h, h->diag_out);
     if (h->cap) cudaStreamDestroy(h->cap);

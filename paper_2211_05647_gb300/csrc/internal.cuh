@@ -148,6 +148,17 @@ void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], flo
                  int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
                  const int64_t *d_step, int kstep);
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by);
+// 3-D FP32 curl stencils fed by TMA (32 x 8 columns walking tz planes along z); the tensor maps
+// describe one field set (nx a multiple of 4); timeouts of their bounded waits set bit 2 of *err
+struct TmaMaps;
+bool tma_stencil_eligible(int64_t nx, int64_t ny, int64_t nz);
+TmaMaps *tma_maps_create(float *const f[6], int64_t nx, int64_t ny, int64_t nz);   // nullptr if not possible
+void tma_maps_free(TmaMaps *t);
+bool tma_maps_match(const TmaMaps *t, float *const f[6]);
+void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
+                    float ch, float cph, Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int tz, int *err);
+void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
+                    float ce, float cpe, Cpml<float> cp, Source src, int tz, int *err);
 
 // delta-f row pitch (elements) for nnode nodes of the given storage type
 int kinetic_pitch(int nnode, int f_dtype);
@@ -294,6 +305,8 @@ struct fdtd_plasma {
     // stencil block (0 = default)
     int kin_vpl, kin_l, kin_bps;
     int st_bx, st_by, st_bz, st_cpt;
+    int st_tz;                // > 0: 3-D FP32 stencils run the TMA column kernels with tz planes per block
+    fp::TmaMaps *tma;         // their tensor maps (field set 0), made on first use
     int has_recording;
     float *rec_out;
     int64_t rec_cap;

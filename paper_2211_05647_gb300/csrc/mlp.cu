@@ -197,6 +197,17 @@ __global__ void k_wait_selftest(uint32_t max_iter, int *gave_up)
     if (threadIdx.x == 0) *gave_up = done ? 0 : 1;
 }
 
+// Self-test of the wall-clock-bounded wait the TMA stencil kernels use (the
+// thread sleeps in the barrier between polls): gives up after limit_ns.
+__global__ void k_timed_wait_selftest(uint64_t limit_ns, int *gave_up)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool done = mbar_wait_timed(&bar, 0u, limit_ns);
+    if (threadIdx.x == 0) *gave_up = done ? 0 : 1;
+}
+
 }  // namespace fp
 
 using namespace fp;
@@ -314,6 +325,25 @@ int fdtd_selftest_wait_timeout(uint32_t max_iter, int32_t *gave_up)
     cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
     if (e == cudaSuccess) {
         k_wait_selftest<<<1, 32>>>(max_iter, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    *gave_up = h;
+    return FDTD_OK;
+}
+
+int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up)
+{
+    if (!gave_up || limit_us == 0 || limit_us > 1000000u)
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_selftest_timed_wait: gave_up NULL or limit_us not in 1..10^6");
+    int *d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return fp_set_global_error(FDTD_ERR_NOMEM, "cudaMalloc failed");
+    int h = -1;
+    cudaError_t e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        k_timed_wait_selftest<<<1, 32>>>((uint64_t)limit_us * 1000u, d);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);

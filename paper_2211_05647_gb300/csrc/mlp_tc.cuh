@@ -17,6 +17,7 @@
 // its stride byte offset (next 8-row group) is K/8 * 128.
 #pragma once
 
+#include "async.cuh"
 #include "mlp.cuh"
 
 namespace fp {
@@ -31,8 +32,6 @@ struct MlpTcSmem {
     __align__(8) uint64_t mbar;
     uint32_t tmem;
 };
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // byte offset of element (row, k) in a core-matrix K-major tile with K columns
 __device__ __forceinline__ uint32_t core_off(int row, int k, int K)
@@ -68,28 +67,6 @@ __device__ __forceinline__ void tc_commit(uint64_t *mbar)
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// bounded wait on the mbarrier phase; returns false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, uint32_t max_iter)
-{
-    for (uint32_t it = 0; it < max_iter; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(smem_addr(m)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
 
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
 {

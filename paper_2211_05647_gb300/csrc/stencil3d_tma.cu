@@ -1,0 +1,334 @@
+// stencil3d_tma.cu -- 3-D FP32 curl stencils (Sec. 2, Eq. 1-6; CPML Eq. 7-12)
+// fed by the tensor memory accelerator.
+//
+// A block owns a 32 x 8 column of cells and walks `tz` planes of it along z.
+// Per plane one thread issues six tiled TMA loads into a ring of shared-memory
+// stages: the three components the curl differentiates, as a 36 x 9 box that
+// carries the one-cell x / y neighbours (x is widened to 36 so every box row
+// is a whole number of 16-byte units), and the three components being
+// updated, as the 32 x 8 tile.  The z neighbour is the previous plane's value
+// of the same thread, kept in registers: the H update needs E^{k+1} and walks
+// z downwards, the E update needs H^{k-1} and walks upwards.  Ghost nodes past
+// the grid read as zero (the TMA fill value), as in the one-cell kernels; the
+// low-side differences of the E update at i, j, k = 0 are set to zero
+// explicitly, like there.  Stage s of the ring holds plane s, s + S, ...; per
+// plane, warp 0 waits on the stage's mbarrier while the other warps sleep in
+// the one block barrier of the plane, which also frees the stage of the
+// previous plane for the next load: with S = 4 stages three planes (21 KB)
+// per block, six blocks per SM, are in flight while one is computed.
+//
+// Every mbarrier wait is bounded: a block whose wait gives up stops storing,
+// waits (again bounded) for the loads it issued, sets bit 2 of the device
+// error word and returns; blocks that start after that return at once.
+#include <cuda.h>
+
+#include "async.cuh"
+#include "stencil_common.cuh"
+
+namespace fp {
+
+namespace {
+
+constexpr int kTX = 32, kTY = 8, kTT = kTX * kTY;   // tile; one thread per column cell
+constexpr int kBX = kTX + 4, kBY = kTY + 1;          // neighbour box
+constexpr int kBoxPitch = 352;                       // floats per box in shared memory (324 rounded to 128 B)
+constexpr int kStageFloats = 3 * kBoxPitch + 3 * kTT;
+constexpr int kStages = 4;
+// 6 resident blocks per SM (40 registers a thread): on GB300 occupancy, not the
+// ring depth, sets how many bytes are in flight (3 to 5 stages time the same)
+constexpr int kMinBlocks = 6;
+constexpr uint32_t kStageBytes = 3 * kBX * kBY * 4 + 3 * kTT * 4;   // what one plane's six loads deliver
+constexpr uint64_t kWaitNs = 1000000000ull;   // 1 s: a plane load takes microseconds
+constexpr size_t kSmemBytes = (size_t)kStages * kStageFloats * 4;
+
+struct Boxes {
+    CUtensorMap nb[3];     // neighbour boxes (36 x 9 x 1) of the differentiated components
+    CUtensorMap tile[3];   // tiles (32 x 8 x 1) of the updated components
+};
+
+struct TmaSmem {
+    __align__(8) uint64_t full[kStages];
+    int quit;
+};
+
+// block-uniform: whether a wait of an earlier block gave up in this launch sequence
+__device__ __forceinline__ bool quit_early(const int *err, int *quit)
+{
+    if (threadIdx.x == 0) *quit = *(const volatile int *)err & 2;
+    __syncthreads();
+    return *quit != 0;
+}
+
+// issue plane p of the block's walk into stage p % S (one thread)
+__device__ __forceinline__ void issue_plane(const Boxes &bx, float *ring, uint64_t *full, int p, int xn, int yn, int xt,
+                                            int yt, int z)
+{
+    float *st = ring + (p % kStages) * kStageFloats;
+    uint64_t *m = &full[p % kStages];
+    mbar_arrive_expect_tx(m, kStageBytes);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load_3d(st + c * kBoxPitch, &bx.nb[c], m, xn, yn, z);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load_3d(st + 3 * kBoxPitch + c * kTT, &bx.tile[c], m, xt, yt, z);
+}
+
+// Plane q of the walk is in its stage: warp 0 waits on the stage's barrier
+// while the other warps sleep in the block barrier (which also tells that
+// every warp is done with plane q - 1, whose stage the caller then refills).
+// If the wait gave up, every thread waits (bounded) for the loads still in
+// flight, planes q .. issued - 1, so the block's shared memory is quiet when
+// it ends; bit 2 of the error word is set and false returned (block-uniform).
+__device__ __forceinline__ bool plane_ready(uint64_t *full, int q, int np, int warp, int *err)
+{
+    bool ok = true;
+    if (warp == 0) ok = mbar_wait_timed(&full[q % kStages], (uint32_t)((q / kStages) & 1), kWaitNs);
+    if (!__syncthreads_or(!ok)) return true;
+    const int issued = min(np, kStages + max(q - 1, 0));
+    for (int p = q; p < issued; ++p) mbar_wait_timed(&full[p % kStages], (uint32_t)((p / kStages) & 1), kWaitNs);
+    if (threadIdx.x == 0) atomicOr(err, 2);
+    return false;
+}
+
+// whether a cell of column (i, j) lies in an x or y CPML slab (constant along the walk)
+__device__ __forceinline__ bool column_in_slab(const Cpml<float> &cp, int64_t i, int64_t j, int nx, int ny)
+{
+    return cp.L > 0 && (in_slab<float>(i, nx, cp.L) || in_slab<float>(j, ny, cp.L));
+}
+
+// H^{n+1/2} = H^{n-1/2} - dt/mu0 curl E^n; neighbour boxes: Ex, Ey, Ez at
+// (x0 .. x0+35, y0 .. y0+8); tiles: Hx, Hy, Hz.  Walks z from the top plane down.
+__global__ void __launch_bounds__(kTT, kMinBlocks) k_h3d_tma(const __grid_constant__ Boxes bx, const float *__restrict__ ex,
+                                                 const float *__restrict__ ey, float *__restrict__ hx,
+                                                 float *__restrict__ hy, float *__restrict__ hz, int nx, int ny, int nz,
+                                                 int tz, float ch, float cph, Cpml<float> cp, Source src,
+                                                 const int64_t *__restrict__ d_step, int kstep, int *err)
+{
+    extern __shared__ __align__(128) float ring[];
+    __shared__ TmaSmem s;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * tz;
+    const int z1 = min(z0 + tz, nz), np = z1 - z0;
+    const int64_t i = x0 + tx, j = y0 + ty;
+    const bool own = i < nx && j < ny;
+    if (quit_early(err, &s.quit)) return;   // an earlier block's wait gave up: the step is void
+    if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) write_source(src, d_step, kstep);
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&s.full[q], 1);
+        fence_proxy_async_smem();
+        for (int p = 0; p < min(kStages, np); ++p) issue_plane(bx, ring, s.full, p, x0, y0, x0, y0, z1 - 1 - p);
+    }
+    const int64_t sxy = (int64_t)nx * ny;
+    // E^{k+1} of this thread's cell above the top plane (a PEC ghost past nz)
+    float exn = 0.f, eyn = 0.f;
+    if (own && z1 < nz) {
+        const int64_t c = (int64_t)z1 * sxy + j * nx + i;
+        exn = ex[c];
+        eyn = ey[c];
+    }
+    __syncthreads();
+    const int hc = ty * kBX + tx;
+    const bool col_slab = column_in_slab(cp, i, j, nx, ny);
+    int64_t c = (int64_t)(z1 - 1) * sxy + j * nx + i;   // this thread's cell in plane k
+    for (int q = 0; q < np; ++q, c -= sxy) {
+        const int k = z1 - 1 - q;
+        if (!plane_ready(s.full, q, np, ty, err)) return;
+        if (tid == 0 && q >= 1 && q - 1 + kStages < np)
+            issue_plane(bx, ring, s.full, q - 1 + kStages, x0, y0, x0, y0, z1 - (q + kStages));
+        const float *st = ring + (q % kStages) * kStageFloats;
+        const float *Ex = st, *Ey = st + kBoxPitch, *Ez = st + 2 * kBoxPitch, *Ht = st + 3 * kBoxPitch;
+        const float exc = Ex[hc], eyc = Ey[hc], ezc = Ez[hc];
+        const float dEz_y = Ez[hc + kBX] - ezc;
+        const float dEy_z = eyn - eyc;
+        const float dEx_z = exn - exc;
+        const float dEz_x = Ez[hc + 1] - ezc;
+        const float dEy_x = Ey[hc + 1] - eyc;
+        const float dEx_y = Ex[hc + kBX] - exc;
+        float hxv = Ht[tid], hyv = Ht[kTT + tid], hzv = Ht[2 * kTT + tid];
+        exn = exc;
+        eyn = eyc;
+        if (own) {
+            if (!col_slab && !(cp.L > 0 && in_slab<float>(k, nz, cp.L))) {
+                hxv -= ch * (dEz_y - dEy_z);
+                hyv -= ch * (dEx_z - dEz_x);
+                hzv -= ch * (dEy_x - dEx_y);
+            } else {
+                h3d_pml<float>(cp, nx, ny, nz, i, j, k, ch, cph, dEz_y, dEy_z, dEx_z, dEz_x, dEy_x, dEx_y, hxv, hyv,
+                               hzv);
+            }
+            hx[c] = hxv;
+            hy[c] = hyv;
+            hz[c] = hzv;
+        }
+    }
+}
+
+// E^{n+1} = E^n + dt/eps0 curl H^{n+1/2} (J already applied to E); neighbour
+// boxes: Hx, Hy, Hz at (x0-4 .. x0+31, y0-1 .. y0+7); tiles: Ex, Ey, Ez.
+// Walks z upwards.
+__global__ void __launch_bounds__(kTT, kMinBlocks) k_e3d_tma(const __grid_constant__ Boxes bx, const float *__restrict__ hx,
+                                                 const float *__restrict__ hy, float *__restrict__ ex,
+                                                 float *__restrict__ ey, float *__restrict__ ez, int nx, int ny, int nz,
+                                                 int tz, float ce, float cpe, Cpml<float> cp, Source src, int *err)
+{
+    extern __shared__ __align__(128) float ring[];
+    __shared__ TmaSmem s;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * tz;
+    const int z1 = min(z0 + tz, nz), np = z1 - z0;
+    const int64_t i = x0 + tx, j = y0 + ty;
+    const bool own = i < nx && j < ny;
+    if (quit_early(err, &s.quit)) return;
+    if (tid == 0) {
+        for (int q = 0; q < kStages; ++q) mbar_init(&s.full[q], 1);
+        fence_proxy_async_smem();
+        for (int p = 0; p < min(kStages, np); ++p) issue_plane(bx, ring, s.full, p, x0 - 4, y0 - 1, x0, y0, z0 + p);
+    }
+    const int64_t sxy = (int64_t)nx * ny;
+    // H^{k-1} of this thread's cell below the first plane (unused at k = 0)
+    float hxp = 0.f, hyp = 0.f;
+    if (own && z0 > 0) {
+        const int64_t c = (int64_t)(z0 - 1) * sxy + j * nx + i;
+        hxp = hx[c];
+        hyp = hy[c];
+    }
+    const float g = src.kind ? (float)*src.val : 0.f;
+    // whether the source covers this column (then it hits the cell of plane src.k)
+    const bool src_col = src.kind && (src.loc == FDTD_LOC_SHEET
+                                          ? (i >= src.i0 && i < src.i1 && j >= src.j0 && j < src.j1)
+                                          : (i == src.i && j == src.j));
+    __syncthreads();
+    const int hc = (ty + 1) * kBX + tx + 4;
+    const bool col_slab = column_in_slab(cp, i, j, nx, ny);
+    int64_t c = (int64_t)z0 * sxy + j * nx + i;   // this thread's cell in plane k
+    for (int q = 0; q < np; ++q, c += sxy) {
+        const int k = z0 + q;
+        if (!plane_ready(s.full, q, np, ty, err)) return;
+        if (tid == 0 && q >= 1 && q - 1 + kStages < np)
+            issue_plane(bx, ring, s.full, q - 1 + kStages, x0 - 4, y0 - 1, x0, y0, z0 + q - 1 + kStages);
+        const float *st = ring + (q % kStages) * kStageFloats;
+        const float *Hx = st, *Hy = st + kBoxPitch, *Hz = st + 2 * kBoxPitch, *Et = st + 3 * kBoxPitch;
+        const float hxc = Hx[hc], hyc = Hy[hc], hzc = Hz[hc];
+        const float exc = Et[tid], eyc = Et[kTT + tid], ezc = Et[2 * kTT + tid];
+        const float dHz_y = j > 0 ? hzc - Hz[hc - kBX] : 0.f;
+        const float dHy_z = k > 0 ? hyc - hyp : 0.f;
+        const float dHx_z = k > 0 ? hxc - hxp : 0.f;
+        const float dHz_x = i > 0 ? hzc - Hz[hc - 1] : 0.f;
+        const float dHy_x = i > 0 ? hyc - Hy[hc - 1] : 0.f;
+        const float dHx_y = j > 0 ? hxc - Hx[hc - kBX] : 0.f;
+        hxp = hxc;
+        hyp = hyc;
+        if (own) {
+            float ux, uy, uz;
+            if (!col_slab && !(cp.L > 0 && in_slab<float>(k, nz, cp.L))) {
+                ux = ce * (dHz_y - dHy_z);
+                uy = ce * (dHx_z - dHz_x);
+                uz = ce * (dHy_x - dHx_y);
+            } else {
+                e3d_pml<float>(cp, nx, ny, nz, i, j, k, ce, cpe, dHz_y, dHy_z, dHx_z, dHz_x, dHy_x, dHx_y, ux, uy, uz);
+            }
+            if (j > 0 && k > 0) {
+                float v = exc + ux;
+                if (src_col && k == src.k) v += g;
+                ex[c] = v;
+            }
+            if (i > 0 && k > 0) ey[c] = eyc + uy;
+            if (i > 0 && j > 0) ez[c] = ezc + uz;
+        }
+    }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiled>(p);
+    }();
+    return fn;
+}
+
+bool encode(CUtensorMap *m, float *base, int64_t nx, int64_t ny, int64_t nz, uint32_t box_x, uint32_t box_y)
+{
+    const EncodeTiled fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)(nx * ny) * 4};
+    const cuuint32_t box[3] = {box_x, box_y, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+struct TmaMaps {
+    Boxes h;   // for the H update: neighbour boxes of Ex, Ey, Ez; tiles of Hx, Hy, Hz
+    Boxes e;   // for the E update: neighbour boxes of Hx, Hy, Hz; tiles of Ex, Ey, Ez
+    const void *f[6];
+};
+
+bool tma_stencil_eligible(int64_t nx, int64_t ny, int64_t nz)
+{
+    // 16-byte row and plane strides; coordinates and plane counts fit int
+    return nx % 4 == 0 && nx <= (1 << 24) && ny <= (1 << 24) && nz <= (1 << 24) && nx * ny * nz < (int64_t)1 << 40;
+}
+
+TmaMaps *tma_maps_create(float *const f[6], int64_t nx, int64_t ny, int64_t nz)
+{
+    if (!tma_stencil_eligible(nx, ny, nz)) return nullptr;
+    for (int q = 0; q < 6; ++q)
+        if (!f[q] || reinterpret_cast<uintptr_t>(f[q]) % 16) return nullptr;
+    TmaMaps *t = new TmaMaps{};
+    bool ok = true;
+    for (int c = 0; c < 3 && ok; ++c) {
+        ok = encode(&t->h.nb[c], f[FDTD_EX + c], nx, ny, nz, kBX, kBY) &&
+             encode(&t->h.tile[c], f[FDTD_HX + c], nx, ny, nz, kTX, kTY) &&
+             encode(&t->e.nb[c], f[FDTD_HX + c], nx, ny, nz, kBX, kBY) &&
+             encode(&t->e.tile[c], f[FDTD_EX + c], nx, ny, nz, kTX, kTY);
+    }
+    for (int q = 0; q < 6; ++q) t->f[q] = f[q];
+    if (!ok) {
+        delete t;
+        return nullptr;
+    }
+    return t;
+}
+
+void tma_maps_free(TmaMaps *t) { delete t; }
+
+bool tma_maps_match(const TmaMaps *t, float *const f[6])
+{
+    if (!t) return false;
+    for (int q = 0; q < 6; ++q)
+        if (t->f[q] != f[q]) return false;
+    return true;
+}
+
+static inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
+                    float ch, float cph, Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int tz, int *err)
+{
+    const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
+    k_h3d_tma<<<g, kTT, kSmemBytes, st>>>(t->h, f[FDTD_EX], f[FDTD_EY], f[FDTD_HX], f[FDTD_HY], f[FDTD_HZ], (int)nx,
+                                          (int)ny, (int)nz, tz, ch, cph, cp, src, d_step, kstep, err);
+}
+
+void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
+                    float ce, float cpe, Cpml<float> cp, Source src, int tz, int *err)
+{
+    const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
+    k_e3d_tma<<<g, kTT, kSmemBytes, st>>>(t->e, f[FDTD_HX], f[FDTD_HY], f[FDTD_EX], f[FDTD_EY], f[FDTD_EZ], (int)nx,
+                                          (int)ny, (int)nz, tz, ce, cpe, cp, src, err);
+}
+
+}  // namespace fp

@@ -93,7 +93,7 @@ class fdtd_tune_result(ctypes.Structure):
     _fields_ = [("kin_vpl", ctypes.c_int32), ("kin_l", ctypes.c_int32), ("kin_blocks_per_sm", ctypes.c_int32),
                 ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("block_z", ctypes.c_int32),
                 ("kin_ms", ctypes.c_double), ("stencil_ms", ctypes.c_double),
-                ("cells_per_thread", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cells_per_thread", ctypes.c_int32), ("stencil_tz", ctypes.c_int32)]
 
 
 class fdtd_closure_desc(ctypes.Structure):
@@ -139,6 +139,7 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_double)]),
     "fdtd_plasma_check_canaries": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "fdtd_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
+    "fdtd_selftest_timed_wait": (ctypes.c_int, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_int32)]),
     "fdtd_plasma_set_option": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64]),
     "fdtd_plasma_launch_shapes": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(fdtd_tune_result)]),
     "fdtd_plasma_set_ports": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
@@ -283,6 +284,14 @@ def selftest_wait_timeout(max_iter: int = 1000) -> bool:
     lib = load_library()
     out = ctypes.c_int32(-1)
     _check(lib, None, lib.fdtd_selftest_wait_timeout(int(max_iter), ctypes.byref(out)))
+    return out.value == 1
+
+
+def selftest_timed_wait(limit_us: int = 2000) -> bool:
+    """Run the wall-clock-bounded wait self-test; True when the wait gave up as designed."""
+    lib = load_library()
+    out = ctypes.c_int32(-1)
+    _check(lib, None, lib.fdtd_selftest_timed_wait(int(limit_us), ctypes.byref(out)))
     return out.value == 1
 
 
@@ -552,8 +561,9 @@ class Solver:
         return n.value
 
     def set_option(self, option: str, value: int):
-        """Runtime option: "fused_stencils" (0 / 1, default 0; see FDTD_OPT_FUSED_STENCILS)."""
-        code = {"fused_stencils": 1}[option]
+        """Runtime option: "fused_stencils" (0 / 1, default 0; FDTD_OPT_FUSED_STENCILS) or
+        "stencil_tz" (0 / planes per block of the TMA column stencils; FDTD_OPT_STENCIL_TZ)."""
+        code = {"fused_stencils": 1, "stencil_tz": 2}[option]
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_option(self.h, code, int(value)))
 
     def launch_shapes(self) -> dict:

@@ -21,6 +21,23 @@ def test_bounded_wait_gives_up_and_context_survives():
     assert d["finite"] and d["energy"] > 0
 
 
+def test_timed_wait_gives_up_after_its_limit():
+    """The wall-clock-bounded wait of the TMA stencils: a barrier that nothing
+    arrives at is given up on after the limit (2 ms here), not sooner and not
+    never; the context stays usable."""
+    import time
+    from paper_2211_05647_gb300 import FdtdError, selftest_timed_wait
+    selftest_timed_wait(10)                       # load and warm the module
+    t0 = time.perf_counter()
+    assert selftest_timed_wait(2000) is True
+    dt = time.perf_counter() - t0
+    print(f"timed wait of 2 ms gave up after {dt * 1e3:.2f} ms (host clock)")
+    assert 2e-3 <= dt < 1.0
+    for bad in (0, 10 ** 7):
+        with pytest.raises(FdtdError):
+            selftest_timed_wait(bad)
+
+
 def test_canaries_clean_after_a_run_and_catch_a_stray_byte(monkeypatch):
     monkeypatch.setenv("FDTD_PLASMA_CANARIES", "1")
     from paper_2211_05647_gb300 import FdtdError, Solver

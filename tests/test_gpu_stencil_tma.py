@@ -1,0 +1,110 @@
+"""TMA column stencils (3-D FP32): blocks of 32 x 8 threads walking tz planes
+along z, planes staged in shared memory by tensor copies.  They compute the
+same cell formulas as the grid-of-cells kernels, so the fields must agree bit
+for bit on grids with ragged tiles on every axis (partial 32-cell rows, partial
+8-row tiles, a last block with fewer than tz planes), with and without CPML,
+with the sheet source and a kinetic slab; and within the FP32 tolerance of the
+FP64 oracle."""
+import numpy as np
+import pytest
+
+from fdtd_inputs import spec_3d_slab
+from tests.adapters import FIELDS, compare, oracle_sim
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _no_tune_cache(monkeypatch, tmp_path):
+    # default launch shapes (one cell per thread) for the grid-of-cells side
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "none.txt"))
+
+
+def _spec(steps, n=(44, 36, 70), cpml=6, slab=(34, 52), src_k=12):
+    nx, ny, nz = n
+    return spec_3d_slab(n=nx, ny=ny, nz=nz, cpml=cpml, slab=slab, src_k=src_k, nv=16, steps=steps,
+                        precision="f32", f_dtype="f32", seed=37)
+
+
+def _pair(spec, tz, calls):
+    from paper_2211_05647_gb300 import Solver
+    tma, cells = Solver.from_spec(spec), Solver.from_spec(spec)
+    tma.set_option("stencil_tz", tz)
+    assert tma.launch_shapes()["stencil_tz"] == tz and cells.launch_shapes()["stencil_tz"] == 0
+    for n in calls:
+        tma.step(n)
+        cells.step(n)
+    return tma, cells
+
+
+@pytest.mark.parametrize("tz", [1, 3, 16, 64])
+def test_tma_equals_cells_bitwise(tz):
+    tma, cells = _pair(_spec(45), tz, (7, 38))
+    for q in FIELDS[3] + ["j", "df"]:
+        a, b = tma.read(q, device=False), cells.read(q, device=False)
+        assert np.abs(b).max() > 0, q
+        assert np.array_equal(a, b), (q, np.abs(a - b).max())
+
+
+@pytest.mark.parametrize("n,tz", [((64, 40, 33), 8), ((36, 9, 5), 2), ((96, 17, 3), 4)])
+def test_tma_no_cpml_ragged(n, tz):
+    """PEC walls only: x a multiple of 4 but not of 32, y not a multiple of 8,
+    nz not a multiple of tz (and the smallest nz, 3)."""
+    nx, ny, nz = n
+    spec = _spec(30, n=n, cpml=0, slab=(0, nz) if nz < 4 else (nz // 3, 2 * nz // 3), src_k=min(2, nz - 1))
+    spec["source"].update(i0=0, i1=nx, j0=1, j1=ny)
+    tma, cells = _pair(spec, tz, (30,))
+    for q in FIELDS[3]:
+        assert np.array_equal(tma.read(q, device=False), cells.read(q, device=False)), q
+
+
+def test_tma_matches_oracle(oracle_lib):
+    spec = _spec(260)
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec)
+    s.set_option("stencil_tz", 16)
+    s.step(100)
+    s.step(160)
+    sim = oracle_sim(oracle_lib, spec)
+    sim.step(260)
+    errs = compare(s, sim, 3)
+    print("TMA column stencils 3-D f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
+
+
+def test_tma_with_fused_option_and_checkpoint():
+    """The opt-in fused pass runs its own kernel on the second field set; the
+    unfused transitions and the last E update of each sequence use the TMA
+    kernels on set 0.  A checkpoint resumes bit for bit."""
+    from paper_2211_05647_gb300 import Solver
+    spec = _spec(40)
+    a = Solver.from_spec(spec)
+    a.set_option("stencil_tz", 8)
+    a.set_option("fused_stencils", 1)
+    a.step(21)
+    blob = a.save_state(device=False)
+    a.step(19)
+    b = Solver.from_spec(spec)
+    b.set_option("stencil_tz", 8)
+    b.set_option("fused_stencils", 1)
+    b.load_state(blob)
+    b.step(19)
+    for q in FIELDS[3] + ["j"]:
+        assert np.array_equal(a.read(q, device=False), b.read(q, device=False)), q
+
+
+def test_tma_option_errors():
+    from fdtd_inputs import spec_2d_cylinder
+    from paper_2211_05647_gb300 import FdtdError, Solver
+    pec = _spec(1, n=(38, 16, 20), cpml=0, slab=(8, 12), src_k=3)   # nx not a multiple of 4
+    pec["source"].update(i0=0, i1=38, j0=1, j1=16)
+    s = Solver.from_spec(pec)
+    s3 = Solver.from_spec(_spec(1))
+    s2 = Solver.from_spec(spec_2d_cylinder(n=64, ny=32, R=8, nv=4, nv_perp=4, steps=1, precision="f32",
+                                           f_dtype="f32"))
+    for solver, v in ((s, 8), (s2, 8), (s3, -1), (s3, 2000)):
+        with pytest.raises(FdtdError):
+            solver.set_option("stencil_tz", v)
+    s3.set_option("stencil_tz", 8)
+    s3.set_option("stencil_tz", 0)
+    assert s3.launch_shapes()["stencil_tz"] == 0
