@@ -248,7 +248,9 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * allocated on first use; the fields are back in place when
  * fdtd_plasma_step returns).  It moves a third fewer bytes but is slower than
  * the two separate passes on GB300 at present.  Results equal the unfused
- * sequence up to FP32 rounding order.  0 turns it off (and frees the copy).
+ * sequence up to FP32 rounding order (bit for bit where the TMA column
+ * stencils below are selected: their fused pass then runs on TMA-staged
+ * planes too).  0 turns it off (and frees the copy).
  * FDTD_OPT_STENCIL_TZ: 0 selects the grid-of-cells 3-D stencil kernels; a
  * value tz in 1..1024 selects the TMA column kernels (3-D FP32, nx a multiple
  * of 4): 32 x 8 threads per block, each block walking tz planes along z with

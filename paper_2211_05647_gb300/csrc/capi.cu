@@ -549,6 +549,7 @@ cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t
 
 void free_second_set(fdtd_plasma *h)
 {
+    tma_fused_forget(h->tma);
     for (int q = 0; q < 6; ++q) { dfree(h, h->f2[q]); h->f2[q] = nullptr; }
     for (int q = 0; q < 12; ++q) { dfree(h, h->psi2[q]); h->psi2[q] = nullptr; }
 }
@@ -582,6 +583,13 @@ template <typename T>
 cudaError_t enqueue_seq(fdtd_plasma *h, cudaStream_t st, int nsteps)
 {
     const bool fuse = sizeof(T) == 4 && fused_stencils(h);
+    // the fused pass on TMA-staged planes when the TMA column stencils are selected (3-D FP32)
+    bool tma_fused = false;
+    if (fuse && h->g.ndim == 3 && h->st_tz > 0) {
+        if (!h->tma) h->tma = tma_maps_create(reinterpret_cast<float *const *>(h->f), h->nx, h->ny, h->nz);
+        tma_fused = h->tma && tma_fused_prepare(h->tma, reinterpret_cast<float *const *>(h->f),
+                                                reinterpret_cast<float *const *>(h->f2));
+    }
     const int trans = nsteps - 1;
     const int unfused_first = fuse && (trans % 2) ? 1 : 0;
     int set = 0;
@@ -598,9 +606,12 @@ cudaError_t enqueue_seq(fdtd_plasma *h, cudaStream_t st, int nsteps)
             if constexpr (sizeof(T) == 4) {
                 const float ce = (float)(h->dt / (kEps0 * h->g.dx)), cpe = (float)(h->dt / kEps0);
                 const float ch = (float)(h->dt / (mu0 * h->g.dx)), cph = (float)(h->dt / mu0);
-                if (h->g.ndim == 3)
-                    launch_eh3d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, h->nz, ce, cpe, ch, cph, fs.cp,
-                                source_view(h), h->d_step, k);
+                if (h->g.ndim == 3) {
+                    if (!(tma_fused && launch_eh3d_tma(st, h->tma, fs.f, to.f, to.cp.psi, ce, cpe, ch, cph, fs.cp,
+                                                       source_view(h), h->d_step, k, h->st_tz, h->d_err)))
+                        launch_eh3d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, h->nz, ce, cpe, ch, cph, fs.cp,
+                                    source_view(h), h->d_step, k);
+                }
                 else
                     launch_eh2d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, ce, cpe, ch, cph, fs.cp, source_view(h),
                                 h->d_step, k);

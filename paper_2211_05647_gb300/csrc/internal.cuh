@@ -159,6 +159,13 @@ void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_
                     float ch, float cph, Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int tz, int *err);
 void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
                     float ce, float cpe, Cpml<float> cp, Source src, int tz, int *err);
+// fused E^{n+1} + H^{n+3/2} on TMA-staged planes between field sets 0 and 1 (both given to prepare);
+// launch returns false (nothing launched) when fin is neither prepared set
+bool tma_fused_prepare(TmaMaps *t, float *const f0[6], float *const f1[6]);
+void tma_fused_forget(TmaMaps *t);
+bool launch_eh3d_tma(cudaStream_t st, const TmaMaps *t, float *const fin[6], float *const fout[6],
+                     float *const psi_out[12], float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
+                     const int64_t *d_step, int kstep, int tz, int *err);
 
 // delta-f row pitch (elements) for nnode nodes of the given storage type
 int kinetic_pitch(int nnode, int f_dtype);

@@ -46,10 +46,12 @@ struct Boxes {
     CUtensorMap tile[3];   // tiles (32 x 8 x 1) of the updated components
 };
 
-struct TmaSmem {
-    __align__(8) uint64_t full[kStages];
+template <int S>
+struct TmaSmemN {
+    __align__(8) uint64_t full[S];
     int quit;
 };
+using TmaSmem = TmaSmemN<kStages>;
 
 // block-uniform: whether a wait of an earlier block gave up in this launch sequence
 __device__ __forceinline__ bool quit_early(const int *err, int *quit)
@@ -74,17 +76,21 @@ __device__ __forceinline__ void issue_plane(const Boxes &bx, float *ring, uint64
 
 // Plane q of the walk is in its stage: warp 0 waits on the stage's barrier
 // while the other warps sleep in the block barrier (which also tells that
-// every warp is done with plane q - 1, whose stage the caller then refills).
+// every warp is done with the previous iteration, so the caller can refill
+// the stage that iteration read last).
 // If the wait gave up, every thread waits (bounded) for the loads still in
 // flight, planes q .. issued - 1, so the block's shared memory is quiet when
 // it ends; bit 2 of the error word is set and false returned (block-uniform).
-__device__ __forceinline__ bool plane_ready(uint64_t *full, int q, int np, int warp, int *err)
+// `lag`: the caller refills the stage of plane q - lag after this barrier, so
+// planes up to q - lag - 1 + S have been issued when it runs.
+template <int S = kStages>
+__device__ __forceinline__ bool plane_ready(uint64_t *full, int q, int np, int warp, int *err, int lag = 1)
 {
     bool ok = true;
-    if (warp == 0) ok = mbar_wait_timed(&full[q % kStages], (uint32_t)((q / kStages) & 1), kWaitNs);
+    if (warp == 0) ok = mbar_wait_timed(&full[q % S], (uint32_t)((q / S) & 1), kWaitNs);
     if (!__syncthreads_or(!ok)) return true;
-    const int issued = min(np, kStages + max(q - 1, 0));
-    for (int p = q; p < issued; ++p) mbar_wait_timed(&full[p % kStages], (uint32_t)((p / kStages) & 1), kWaitNs);
+    const int issued = min(np, S + max(q - lag, 0));
+    for (int p = q; p < issued; ++p) mbar_wait_timed(&full[p % S], (uint32_t)((p / S) & 1), kWaitNs);
     if (threadIdx.x == 0) atomicOr(err, 2);
     return false;
 }
@@ -237,6 +243,181 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_e3d_tma(const __grid_consta
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused E^{n+1} + H^{n+3/2} (the opt-in fused step sequence) on TMA-staged
+// planes.  Reads field set A (E' = E^n after the plasma current, H^{n+1/2},
+// psi) and writes set B, so no block reads what another writes.  A block owns
+// a 32 x 8 column and walks up z: per plane z the stage holds the H^{n+1/2}
+// box x0-4 .. x0+35, y0-1 .. y0+8 (40 x 10) and the E' box x0 .. x0+35,
+// y0 .. y0+8 (36 x 9); E^{n+1}(z) is formed on the tile and its +x / +y halo
+// (33 x 9 cells, the halo recomputed by the neighbouring block too) into one
+// of two shared buffers, the tile stored; then H^{n+3/2}(z-1) is formed on
+// the tile from E^{n+1} of planes z-1 and z.  The walk covers planes
+// z0-1 (H only, for dH/dz) .. z1 (E only, for dE/dz of H^{n+3/2}(z1-1)); at
+// the top of the grid E^{n+1}(nz) is the PEC ghost 0.  Two block barriers a
+// plane; the stage of plane z-2 is refilled after the first.  Every field is
+// read once and written once from DRAM: 48 B a cell against 72 B for the two
+// separate passes.
+
+constexpr int kFHX = 40, kFHY = 10, kFHPitch = 416;   // H box; 400 floats rounded to 128 B
+constexpr int kFEX = 36, kFEY = 9, kFEPitch = 352;    // E' box; 324 floats rounded to 128 B
+constexpr int kFStage = 3 * kFHPitch + 3 * kFEPitch;
+constexpr uint32_t kFStageBytes = 3 * kFHX * kFHY * 4 + 3 * kFEX * kFEY * 4;
+constexpr int kFBX = kTX + 1, kFBY = kTY + 1, kFBuf = kFBX * kFBY;   // E^{n+1} on tile + halo
+constexpr int kFStages = 4;
+constexpr size_t kFSmemBytes = (size_t)(kFStages * kFStage + 2 * 3 * kFBuf) * 4;
+constexpr int kFMinBlocks = 4;
+
+struct FusedBoxes {
+    CUtensorMap h[3];   // 40 x 10 x 1 boxes of Hx, Hy, Hz
+    CUtensorMap e[3];   // 36 x 9 x 1 boxes of Ex, Ey, Ez
+};
+
+struct FusedOut {
+    float *f[6];
+    float *psi[12];
+};
+
+__device__ __forceinline__ void issue_fused_plane(const FusedBoxes &bx, float *ring, uint64_t *full, int p, int x0,
+                                                  int y0, int z)
+{
+    float *st = ring + (p % kFStages) * kFStage;
+    uint64_t *m = &full[p % kFStages];
+    mbar_arrive_expect_tx(m, kFStageBytes);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load_3d(st + c * kFHPitch, &bx.h[c], m, x0 - 4, y0 - 1, z);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tma_load_3d(st + 3 * kFHPitch + c * kFEPitch, &bx.e[c], m, x0, y0, z);
+}
+
+__device__ __forceinline__ bool source_column(const Source &src, int64_t i, int64_t j)
+{
+    return src.kind && (src.loc == FDTD_LOC_SHEET ? (i >= src.i0 && i < src.i1 && j >= src.j0 && j < src.j1)
+                                                  : (i == src.i && j == src.j));
+}
+
+__global__ void __launch_bounds__(kTT, kFMinBlocks) k_eh3d_tma(const __grid_constant__ FusedBoxes bx, FusedOut out,
+                                                              int nx, int ny, int nz, int tz, float ce, float cpe,
+                                                              float ch, float cph, Cpml<float> cin, Source src,
+                                                              const int64_t *__restrict__ d_step, int kstep, int *err)
+{
+    extern __shared__ __align__(128) float ring[];
+    float *ebuf = ring + kFStages * kFStage;   // [2][3][kFBuf]: E^{n+1} of planes of even / odd z
+    __shared__ TmaSmemN<kFStages> s;
+    __shared__ float s_g;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY, z0 = blockIdx.z * tz;
+    const int z1 = min(z0 + tz, nz);
+    const int zs = z0 > 0 ? z0 - 1 : 0, ze = z1 < nz ? z1 : z1 - 1, np = ze - zs + 1;
+    if (quit_early(err, &s.quit)) return;
+    if (tid == 0) {
+        const int64_t n1 = *d_step + kstep + 1;   // E^{n+1} is at t^{n+1}
+        s_g = src.kind && src.k >= zs && src.k <= ze ? (float)source_value(src, (double)n1 * src.dt) : 0.f;
+        if (src.kind && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+            *src.val = source_value(src, (double)(n1 + 1) * src.dt);   // for an unfused E update that follows
+        for (int q = 0; q < kFStages; ++q) mbar_init(&s.full[q], 1);
+        fence_proxy_async_smem();
+        for (int p = 0; p < min(kFStages, np); ++p) issue_fused_plane(bx, ring, s.full, p, x0, y0, zs + p);
+    }
+    __syncthreads();
+    const int64_t sxy = (int64_t)nx * ny;
+    const int L = cin.L;
+    // E^{n+1}(z) of local cell (lx, ly) of the tile + halo; stores the tile's cells (and their psi) to set B
+    auto e_cell = [&](const float *cur, const float *prv, int lx, int ly, int z, float *eb) {
+        const int64_t i = x0 + lx, j = y0 + ly;
+        float exn = 0.f, eyn = 0.f, ezn = 0.f;
+        if (i < nx && j < ny) {
+            const int hb = (ly + 1) * kFHX + lx + 4, eb_ = ly * kFEX + lx;
+            const float *Hx = cur, *Hy = cur + kFHPitch, *Hz = cur + 2 * kFHPitch, *Ep = cur + 3 * kFHPitch;
+            const float hxc = Hx[hb], hyc = Hy[hb], hzc = Hz[hb];
+            const float dHz_y = j > 0 ? hzc - Hz[hb - kFHX] : 0.f;
+            const float dHy_z = z > 0 ? hyc - prv[kFHPitch + hb] : 0.f;
+            const float dHx_z = z > 0 ? hxc - prv[hb] : 0.f;
+            const float dHz_x = i > 0 ? hzc - Hz[hb - 1] : 0.f;
+            const float dHy_x = i > 0 ? hyc - Hy[hb - 1] : 0.f;
+            const float dHx_y = j > 0 ? hxc - Hx[hb - kFHX] : 0.f;
+            const float exc = Ep[eb_], eyc = Ep[kFEPitch + eb_], ezc = Ep[2 * kFEPitch + eb_];
+            const bool own = lx < kTX && ly < kTY && z < z1;
+            float ux, uy, uz;
+            if (!(L > 0 && (in_slab<float>(i, nx, L) || in_slab<float>(j, ny, L) || in_slab<float>(z, nz, L)))) {
+                ux = ce * (dHz_y - dHy_z);
+                uy = ce * (dHx_z - dHz_x);
+                uz = ce * (dHy_x - dHx_y);
+            } else {
+                e3d_pml_io<float>(cin, out.psi, own, nx, ny, nz, i, j, z, ce, cpe, dHz_y, dHy_z, dHx_z, dHz_x, dHy_x,
+                                  dHx_y, ux, uy, uz);
+            }
+            exn = exc;
+            eyn = eyc;
+            ezn = ezc;
+            if (j > 0 && z > 0) {
+                exn = exc + ux;
+                if (z == src.k && source_column(src, i, j)) exn += s_g;
+            }
+            if (i > 0 && z > 0) eyn = eyc + uy;
+            if (i > 0 && j > 0) ezn = ezc + uz;
+            if (own) {
+                const int64_t c = (int64_t)z * sxy + j * nx + i;
+                out.f[FDTD_EX][c] = exn;
+                out.f[FDTD_EY][c] = eyn;
+                out.f[FDTD_EZ][c] = ezn;
+            }
+        }
+        const int e = ly * kFBX + lx;
+        eb[e] = exn;
+        eb[kFBuf + e] = eyn;
+        eb[2 * kFBuf + e] = ezn;
+    };
+    // H^{n+3/2}(k) of this thread's cell: H^{n+1/2}(k) from stage hs, E^{n+1}(k) from ek, E^{n+1}(k+1) from ek1
+    // (nullptr: the ghost plane above the grid)
+    auto h_cell = [&](const float *hs, const float *ek, const float *ek1, int k) {
+        const int64_t i = x0 + tx, j = y0 + ty;
+        if (i >= nx || j >= ny) return;
+        const int hb = (ty + 1) * kFHX + tx + 4, e = ty * kFBX + tx;
+        float hxv = hs[hb], hyv = hs[kFHPitch + hb], hzv = hs[2 * kFHPitch + hb];
+        const float exc = ek[e], eyc = ek[kFBuf + e], ezc = ek[2 * kFBuf + e];
+        const float dEz_y = ek[2 * kFBuf + e + kFBX] - ezc;
+        const float dEy_z = (ek1 ? ek1[kFBuf + e] : 0.f) - eyc;
+        const float dEx_z = (ek1 ? ek1[e] : 0.f) - exc;
+        const float dEz_x = ek[2 * kFBuf + e + 1] - ezc;
+        const float dEy_x = ek[kFBuf + e + 1] - eyc;
+        const float dEx_y = ek[e + kFBX] - exc;
+        if (!(L > 0 && (in_slab<float>(i, nx, L) || in_slab<float>(j, ny, L) || in_slab<float>(k, nz, L)))) {
+            hxv -= ch * (dEz_y - dEy_z);
+            hyv -= ch * (dEx_z - dEz_x);
+            hzv -= ch * (dEy_x - dEx_y);
+        } else {
+            h3d_pml_io<float>(cin, out.psi, true, nx, ny, nz, i, j, k, ch, cph, dEz_y, dEy_z, dEx_z, dEz_x, dEy_x,
+                              dEx_y, hxv, hyv, hzv);
+        }
+        const int64_t c = (int64_t)k * sxy + j * nx + i;
+        out.f[FDTD_HX][c] = hxv;
+        out.f[FDTD_HY][c] = hyv;
+        out.f[FDTD_HZ][c] = hzv;
+    };
+    for (int p = 0; p < np; ++p) {
+        const int z = zs + p;
+        if (!plane_ready<kFStages>(s.full, p, np, ty, err, 2)) return;
+        if (tid == 0 && p >= 2 && p - 2 + kFStages < np)
+            issue_fused_plane(bx, ring, s.full, p - 2 + kFStages, x0, y0, zs + p - 2 + kFStages);
+        if (z < z0) continue;   // plane z0-1: its H^{n+1/2} serves dH/dz of E^{n+1}(z0)
+        const float *cur = ring + (p % kFStages) * kFStage;
+        const float *prv = ring + ((p + kFStages - 1) % kFStages) * kFStage;
+        float *eb = ebuf + (z & 1) * 3 * kFBuf;
+        e_cell(cur, prv, tx, ty, z, eb);
+        if (tid < kFBuf - kTT) {   // the +x column (9 cells) and the +y row (32 cells)
+            const int hx_ = tid < kFBY ? kTX : tid - kFBY, hy_ = tid < kFBY ? tid : kTY;
+            e_cell(cur, prv, hx_, hy_, z, eb);
+        }
+        __syncthreads();
+        if (z - 1 >= z0) h_cell(prv, ebuf + ((z - 1) & 1) * 3 * kFBuf, eb, z - 1);
+    }
+    if (z1 == nz) {   // H^{n+3/2} of the top plane: E^{n+1} above it is the PEC ghost
+        const int p = np - 1;
+        h_cell(ring + (p % kFStages) * kFStage, ebuf + ((nz - 1) & 1) * 3 * kFBuf, nullptr, nz - 1);
+    }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -274,6 +455,11 @@ struct TmaMaps {
     Boxes h;   // for the H update: neighbour boxes of Ex, Ey, Ez; tiles of Hx, Hy, Hz
     Boxes e;   // for the E update: neighbour boxes of Hx, Hy, Hz; tiles of Ex, Ey, Ez
     const void *f[6];
+    int64_t nx, ny, nz;
+    // fused E + H pass: boxes of field sets 0 and 1 (made when both sets exist)
+    bool fused_ready;
+    FusedBoxes fused[2];
+    const void *fset[2][6];
 };
 
 bool tma_stencil_eligible(int64_t nx, int64_t ny, int64_t nz)
@@ -296,6 +482,9 @@ TmaMaps *tma_maps_create(float *const f[6], int64_t nx, int64_t ny, int64_t nz)
              encode(&t->e.tile[c], f[FDTD_EX + c], nx, ny, nz, kTX, kTY);
     }
     for (int q = 0; q < 6; ++q) t->f[q] = f[q];
+    t->nx = nx;
+    t->ny = ny;
+    t->nz = nz;
     if (!ok) {
         delete t;
         return nullptr;
@@ -304,6 +493,34 @@ TmaMaps *tma_maps_create(float *const f[6], int64_t nx, int64_t ny, int64_t nz)
 }
 
 void tma_maps_free(TmaMaps *t) { delete t; }
+
+bool tma_fused_prepare(TmaMaps *t, float *const f0[6], float *const f1[6])
+{
+    if (!t) return false;
+    float *const *sets[2] = {f0, f1};
+    bool same = t->fused_ready;
+    for (int b = 0; b < 2 && same; ++b)
+        for (int q = 0; q < 6; ++q) same = same && t->fset[b][q] == sets[b][q];
+    if (same) return true;
+    t->fused_ready = false;
+    for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < 6; ++q)
+            if (!sets[b][q] || reinterpret_cast<uintptr_t>(sets[b][q]) % 16) return false;
+    for (int b = 0; b < 2; ++b) {
+        for (int c = 0; c < 3; ++c)
+            if (!encode(&t->fused[b].h[c], sets[b][FDTD_HX + c], t->nx, t->ny, t->nz, kFHX, kFHY) ||
+                !encode(&t->fused[b].e[c], sets[b][FDTD_EX + c], t->nx, t->ny, t->nz, kFEX, kFEY))
+                return false;
+        for (int q = 0; q < 6; ++q) t->fset[b][q] = sets[b][q];
+    }
+    t->fused_ready = true;
+    return true;
+}
+
+void tma_fused_forget(TmaMaps *t)
+{
+    if (t) t->fused_ready = false;
+}
 
 bool tma_maps_match(const TmaMaps *t, float *const f[6])
 {
@@ -321,6 +538,27 @@ void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_
     const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
     k_h3d_tma<<<g, kTT, kSmemBytes, st>>>(t->h, f[FDTD_EX], f[FDTD_EY], f[FDTD_HX], f[FDTD_HY], f[FDTD_HZ], (int)nx,
                                           (int)ny, (int)nz, tz, ch, cph, cp, src, d_step, kstep, err);
+}
+
+bool launch_eh3d_tma(cudaStream_t st, const TmaMaps *t, float *const fin[6], float *const fout[6],
+                     float *const psi_out[12], float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
+                     const int64_t *d_step, int kstep, int tz, int *err)
+{
+    if (!t || !t->fused_ready) return false;
+    int b = -1;
+    for (int q = 0; q < 2 && b < 0; ++q)
+        if (t->fset[q][0] == fin[0] && t->fset[q][5] == fin[5]) b = q;
+    if (b < 0) return false;
+    FusedOut o{};
+    for (int q = 0; q < 6; ++q) o.f[q] = fout[q];
+    for (int q = 0; q < 12; ++q) o.psi[q] = psi_out[q];
+    static const bool attr = cudaFuncSetAttribute(k_eh3d_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)kFSmemBytes) == cudaSuccess;
+    if (!attr) return false;
+    const dim3 g(cdivu(t->nx, kTX), cdivu(t->ny, kTY), cdivu(t->nz, tz));
+    k_eh3d_tma<<<g, kTT, kFSmemBytes, st>>>(t->fused[b], o, (int)t->nx, (int)t->ny, (int)t->nz, tz, ce, cpe, ch, cph,
+                                            cin, src, d_step, kstep, err);
+    return true;
 }
 
 void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,

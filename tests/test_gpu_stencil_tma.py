@@ -108,3 +108,56 @@ def test_tma_option_errors():
     s3.set_option("stencil_tz", 8)
     s3.set_option("stencil_tz", 0)
     assert s3.launch_shapes()["stencil_tz"] == 0
+
+
+# ------------------------------------------- fused E + H pass on TMA-staged planes
+# With both options set, every fused transition of the step sequence runs
+# k_eh3d_tma (reading one field set, writing the other); the first transition of
+# an odd count and the last E update run the separate TMA kernels.  The cell
+# formulas are the separate kernels', so the fields agree with the grid-of-cells
+# sequence bit for bit.
+
+def _fused_tma(spec, tz, calls):
+    from paper_2211_05647_gb300 import Solver
+    f, cells = Solver.from_spec(spec), Solver.from_spec(spec)
+    f.set_option("stencil_tz", tz)
+    f.set_option("fused_stencils", 1)
+    for n in calls:
+        f.step(n)
+        cells.step(n)
+    return f, cells
+
+
+@pytest.mark.parametrize("tz,calls", [(12, (1,)), (12, (2,)), (12, (3,)), (12, (33,)), (3, (64, 5)), (1, (7, 1, 40)),
+                                      (70, (36,))])
+def test_fused_tma_equals_cells_bitwise(tz, calls):
+    f, cells = _fused_tma(_spec(sum(calls)), tz, calls)
+    assert np.abs(cells.read("ex", device=False)).max() > 0
+    for q in FIELDS[3] + ["j", "df"]:
+        a, b = f.read(q, device=False), cells.read(q, device=False)
+        assert np.array_equal(a, b), (q, np.abs(a - b).max())
+
+
+@pytest.mark.parametrize("n,tz", [((64, 40, 33), 8), ((36, 9, 5), 2), ((96, 17, 3), 4)])
+def test_fused_tma_no_cpml_ragged(n, tz):
+    nx, ny, nz = n
+    spec = _spec(30, n=n, cpml=0, slab=(0, nz) if nz < 4 else (nz // 3, 2 * nz // 3), src_k=min(2, nz - 1))
+    spec["source"].update(i0=0, i1=nx, j0=1, j1=ny)
+    f, cells = _fused_tma(spec, tz, (30,))
+    for q in FIELDS[3]:
+        assert np.array_equal(f.read(q, device=False), cells.read(q, device=False)), q
+
+
+def test_fused_tma_matches_oracle(oracle_lib):
+    spec = _spec(260)
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec)
+    s.set_option("stencil_tz", 12)
+    s.set_option("fused_stencils", 1)
+    s.step(100)
+    s.step(160)
+    sim = oracle_sim(oracle_lib, spec)
+    sim.step(260)
+    errs = compare(s, sim, 3)
+    print("fused TMA pass 3-D f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
