@@ -12,9 +12,12 @@
 // (hardware barrier: neighbouring ranges exchange their edge values through
 // global memory / L2), the CTA updates the delta-f rows of its plasma nodes
 // (E <- E - dt/eps0 J in place; the run's per-node tables are staged in shared
-// memory, the next row's node index is prefetched), then E, the source and
-// the Mur ends on its range, and the cluster synchronises again.  The H and E
-// loops give each thread four independent nodes per round.  Clusters never wait for each
+// memory, the next row is loaded while the current one is updated), then E,
+// the source and the Mur ends on its range, and the cluster synchronises again.  The H and E
+// loops move 4-node quads (16-byte loads and stores: run arrays are aligned and
+// padded, CTA ranges start on a multiple of 4 nodes), the +-1 neighbour from the
+// adjacent lane; partial quads, the source node and the Mur ends are stored
+// node by node.  Clusters never wait for each
 // other.  Cuts never separate node 0 from node 1 or node nz-1 from node nz,
 // so the thread that advances E_1 (E_{nz-1}) also applies the Mur update to
 // E_0 (E_nz) with values it owns.
@@ -80,6 +83,37 @@ __device__ __forceinline__ double batch_source(const BRun &r, double t)
     return 0.0;
 }
 
+// four consecutive field nodes moved as 16-byte units (the run arrays start on 16-byte boundaries)
+template <typename T>
+struct Quad {
+    T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ Quad<T> ld_quad(const T *p)
+{
+    Quad<T> q;
+    if constexpr (sizeof(T) == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        q.v[0] = x.x; q.v[1] = x.y; q.v[2] = x.z; q.v[3] = x.w;
+    } else {
+        const double2 x = reinterpret_cast<const double2 *>(p)[0], y = reinterpret_cast<const double2 *>(p)[1];
+        q.v[0] = x.x; q.v[1] = x.y; q.v[2] = y.x; q.v[3] = y.y;
+    }
+    return q;
+}
+
+template <typename T>
+__device__ __forceinline__ void st_quad(T *p, const Quad<T> &q)
+{
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(q.v[0], q.v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(q.v[2], q.v[3]);
+    }
+}
+
 template <typename TS, typename T, int VPL, int L>
 __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
 {
@@ -90,7 +124,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
     using V = typename Vec<TS>::type;
     constexpr int VEC = Vec<TS>::n;
     constexpr int R = 32 / L;
-    constexpr int U = 4;                         // H / E nodes per thread per round (independent loads)
+    constexpr int U = 2;                         // H / E quads (4 nodes each) per thread per round
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane / L, l = lane % L;
     const int nwarps = blockDim.x >> 5;
@@ -108,17 +142,37 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
             const T *E = a.E + r.e_off;
             T *H = a.H + r.h_off;
             const int kend = min(sg.k1, r.nz);
-            for (int kb = sg.k0 + threadIdx.x; kb < kend; kb += U * blockDim.x) {
-                T e0[U], e1[U], h[U];
+            const int nq = (kend - sg.k0 + 3) / 4;   // quads of H nodes [k0, kend); k0 is a multiple of 4
+            for (int qi0 = 0; qi0 < nq; qi0 += U * blockDim.x) {   // block-uniform rounds
+                Quad<T> e[U], h[U];
+                T e4[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int k = kb + u * blockDim.x;
-                    if (k < kend) { e0[u] = E[k]; e1[u] = E[k + 1]; h[u] = H[k]; }
+                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    if (kq < kend) {
+                        e[u] = ld_quad(E + kq);
+                        h[u] = ld_quad(H + kq);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int k = kb + u * blockDim.x;
-                    if (k < kend) H[k] = h[u] - a.ch * (e1[u] - e0[u]);
+                    // E at kq + 4: the next lane's first node, loaded here at a warp's end or past kend
+                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    e4[u] = __shfl_down_sync(0xffffffffu, e[u].v[0], 1);
+                    if (kq < kend && (lane == 31 || kq + 4 >= kend)) e4[u] = E[kq + 4];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    if (kq >= kend) continue;
+                    Quad<T> o;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) o.v[c] = h[u].v[c] - a.ch * ((c < 3 ? e[u].v[c + 1] : e4[u]) - e[u].v[c]);
+                    if (kq + 4 <= kend) {
+                        st_quad(H + kq, o);
+                    } else {
+                        for (int c = 0; kq + c < kend; ++c) H[kq + c] = o.v[c];
+                    }
                 }
             }
             if (r.mur && threadIdx.x == 0) {
@@ -140,33 +194,49 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
                 s_be[t] = al[a.pitch + t];
             }
             __syncthreads();
-            // the next row group's node index is fetched one iteration ahead, so
-            // the E gather of a row issues together with its delta-f loads
-            int row = sg.s0 + warp * R + sub;
-            int node_next = row < sg.s1 ? __ldg(a.slot_node + r.row_off + row) : 0;
-            for (int base = sg.s0 + warp * R; base < sg.s1; base += nwarps * R) {
-                row = base + sub;
-                const bool valid = row < sg.s1;
-                const int64_t grow = r.row_off + (valid ? row : sg.s0);
-                const int node = node_next;
-                V *rp = reinterpret_cast<V *>(a.df) + grow * (a.pitch / VEC);
+            // software pipeline: the next row's node index, delta-f vectors, E and
+            // density are loaded before the current row is updated, so a lane
+            // keeps two rows of loads in flight (one 512-thread CTA per SM leaves
+            // the registers for it).  Rows of a segment have distinct nodes, so
+            // reading the next row's E ahead of this row's E store is safe.
+            const int stride = nwarps * R;
+            struct RowIn {
                 V v[VPL];
-                T e = T(0), nE = T(0);
-                if (valid) {
+                T e, dn;
+                int node;
+                int64_t grow;
+                bool valid;
+            };
+            auto fetch_row = [&](int row, RowIn &in) {
+                in.valid = row < sg.s1;
+                in.grow = r.row_off + (in.valid ? row : sg.s0);
+                in.e = T(0);
+                in.dn = T(0);
+                in.node = 0;
+                if (in.valid) {
+                    const V *rp = reinterpret_cast<const V *>(a.df) + in.grow * (a.pitch / VEC);
 #pragma unroll
-                    for (int qq = 0; qq < VPL; ++qq) v[qq] = __ldcs(rp + qq * L + l);
-                    e = E[node];
-                    nE = __ldg(a.dens + grow) * e;
+                    for (int qq = 0; qq < VPL; ++qq) in.v[qq] = __ldcs(rp + qq * L + l);
+                    in.node = __ldg(a.slot_node + in.grow);
+                    in.e = E[in.node];
+                    in.dn = __ldg(a.dens + in.grow);
                 }
-                const int rn = row + nwarps * R;
-                node_next = rn < sg.s1 ? __ldg(a.slot_node + r.row_off + rn) : 0;
+            };
+            RowIn cur, nxt;
+            fetch_row(sg.s0 + warp * R + sub, cur);
+            for (int base = sg.s0 + warp * R; base < sg.s1; base += stride) {
+                fetch_row(base + stride + sub, nxt);
+                V *rp = reinterpret_cast<V *>(a.df) + cur.grow * (a.pitch / VEC);
                 T sm = T(0), cm = T(0);
-                if (valid) row_update<TS, T, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)grow, step, key, sm, cm);
+                if (cur.valid)
+                    row_update<TS, T, VPL, L>(rp, cur.v, s_al, s_be, s_w, cur.dn * cur.e, l, (uint32_t)cur.grow, step,
+                                              key, sm, cm);
                 const T J = row_reduce<T, L>(sm, cm);
-                if (valid && l == 0) {
-                    a.jslot[grow] = J;
-                    E[node] = e - a.cj * J;
+                if (cur.valid && l == 0) {
+                    a.jslot[cur.grow] = J;
+                    E[cur.node] = cur.e - a.cj * J;
                 }
+                cur = nxt;
             }
         }
         __syncthreads();
@@ -176,24 +246,49 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
             const BRun r = a.runs[sg.run];
             T *E = a.E + r.e_off;
             const T *H = a.H + r.h_off;
-            const int kbeg = max(sg.k0, 1), kend = min(sg.k1, r.nz);
-            for (int kb = kbeg + threadIdx.x; kb < kend; kb += U * blockDim.x) {
-                T ev[U], h0[U], h1[U];
+            const int kbeg = max(sg.k0, 1), kend = min(sg.k1, r.nz);   // E nodes updated: [kbeg, kend)
+            const int nq = (kend - sg.k0 + 3) / 4;
+            for (int qi0 = 0; qi0 < nq; qi0 += U * blockDim.x) {
+                Quad<T> ev[U], h[U];
+                T hm[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int k = kb + u * blockDim.x;
-                    if (k < kend) { ev[u] = E[k]; h0[u] = H[k - 1]; h1[u] = H[k]; }
+                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    if (kq < kend) {
+                        ev[u] = ld_quad(E + kq);
+                        h[u] = ld_quad(H + kq);
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int k = kb + u * blockDim.x;
-                    if (k >= kend) continue;
-                    T v = ev[u] - a.ce * (h1[u] - h0[u]);
-                    if (k == r.src_k) v += (T)batch_source(r, (double)(step + 1) * a.dt);
-                    E[k] = v;
-                    if (r.mur) {
-                        if (k == 1) E[0] = a.mur[2 * sg.run] + (T)r.mur_m * (v - E[0]);
-                        if (k == r.nz - 1) E[r.nz] = a.mur[2 * sg.run + 1] + (T)r.mur_m * (v - E[r.nz]);
+                    // H at kq - 1: the previous lane's last node, loaded here at a warp's start
+                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    hm[u] = __shfl_up_sync(0xffffffffu, h[u].v[3], 1);
+                    if (kq < kend && lane == 0) hm[u] = kq > 0 ? H[kq - 1] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    if (kq >= kend) continue;
+                    Quad<T> o = ev[u];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) o.v[c] = ev[u].v[c] - a.ce * (h[u].v[c] - (c > 0 ? h[u].v[c - 1] : hm[u]));
+                    const bool special = kq < kbeg || kq + 4 > kend || (r.src_k >= kq && r.src_k < kq + 4) ||
+                                         (r.mur && (kq <= 1 || kq + 4 > r.nz - 1));
+                    if (!special) {
+                        st_quad(E + kq, o);
+                        continue;
+                    }
+                    for (int c = 0; c < 4; ++c) {
+                        const int k = kq + c;
+                        if (k < kbeg || k >= kend) continue;
+                        T v = o.v[c];
+                        if (k == r.src_k) v += (T)batch_source(r, (double)(step + 1) * a.dt);
+                        E[k] = v;
+                        if (r.mur) {
+                            if (k == 1) E[0] = a.mur[2 * sg.run] + (T)r.mur_m * (v - E[0]);
+                            if (k == r.nz - 1) E[r.nz] = a.mur[2 * sg.run + 1] + (T)r.mur_m * (v - E[r.nz]);
+                        }
                     }
                 }
             }
@@ -485,7 +580,10 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
         br.src_kind = s.kind;
         br.src_k = s.kind ? (int32_t)s.k : -1;
         br.amp = s.amp; br.fc = s.fc; br.tau = s.kind ? s.tau : 1.0; br.t0 = s.t0;
-        eo += nz + 1; ho += nz; ro += ns;
+        // 16-byte aligned run arrays, padded so a 4-node quad read never leaves the run's extent
+        eo += (nz + 1 + 3) / 4 * 4 + 4;
+        ho += (nz + 3) / 4 * 4 + 4;
+        ro += ns;
     }
     b->ncell_e = eo; b->ncell_h = ho; b->nrows = ro;
     const double wp = std::sqrt(wpmax * kQe * kQe / (kEps0 * kMe));
@@ -560,9 +658,10 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
                 const bool plasma = si < b->nslot[r] && nodes[si] == k;
                 acc += cell_cost + (plasma ? node_cost : 0.0);
                 const double target = total * (cta + 1) / csize;
-                // a cut after node k (range [k0, k+1)); never between 0|1 or nz-1|nz
+                // a cut after node k (range [k0, k+1)) at a multiple of 4 nodes (ranges start on a quad);
+                // never between 0|1 or nz-1|nz
                 const int64_t cut = k + 1;
-                if (acc >= target && cta < csize - 1 && cut != 1 && cut != nz && cut <= nz) {
+                if (acc >= target && cta < csize - 1 && cut % 4 == 0 && cut != nz && cut <= nz) {
                     segs.push_back(BSeg{r, (int32_t)k0, (int32_t)cut, slot_at[r][k0], slot_at[r][cut]});
                     k0 = cut;
                     ++cta;
