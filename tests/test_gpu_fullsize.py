@@ -1,7 +1,8 @@
-"""Full-size parity: the benchmark's own workloads (the launch configuration
-bench.py times) from a seeded random initial E/H state, a few steps, against
-the FP64 oracle run at the same full size.  Every field value and every J is
-compared (relative L2, field-vector normalisation)."""
+"""Full-size parity: the benchmark's own workloads in the launch configuration
+bench.py times (the autotuner runs first, as in the bench: on the 3-D grids it
+selects the TMA column stencils), from a seeded random initial E/H state, a
+few steps, against the FP64 oracle run at the same full size.  Every field
+value and every J is compared (relative L2, field-vector normalisation)."""
 import os
 
 import numpy as np
@@ -39,9 +40,10 @@ def _zero_pec(ndim, sizes, st):
                                                     ("3d_512_kinetic_bf16", 3, 5e-3, 80),
                                                     ("3d_256_kinetic_bf16", 3, 5e-3, 12),
                                                     ("3d_256_f0evolve_f32", 3, 1e-4, 14)])
-def test_full_size_random_state(oracle_lib, name, steps, tol, min_gb):
+def test_full_size_random_state(oracle_lib, name, steps, tol, min_gb, monkeypatch, tmp_path):
     if _mem_available_gb() < min_gb:
         pytest.skip(f"needs {min_gb} GB of host memory for the FP64 oracle at full size")
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "tune.txt"))
     from paper_2211_05647_gb300 import Solver
     spec = WORKLOADS[name]()
     g = spec["grid"]
@@ -50,6 +52,8 @@ def test_full_size_random_state(oracle_lib, name, steps, tol, min_gb):
     st = random_state({f: n for f in FIELDS[nd]}, seed=99)
     _zero_pec(nd, (g["nx"], g["ny"], g["nz"]), st)
     s = Solver.from_spec(spec)
+    s.autotune()
+    shapes = s.launch_shapes()
     for f, v in st.items():
         s.write(f, v.astype(np.float32))
     sim = oracle_sim(oracle_lib, spec)
@@ -62,7 +66,7 @@ def test_full_size_random_state(oracle_lib, name, steps, tol, min_gb):
     if spec["plasma"].get("evolve_f0"):
         from tests.adapters import rel_l2
         errs["f0"] = rel_l2(s.read("f0", device=False), sim.get("f0"))
-    print(f"{name}: " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
+    print(f"{name} {shapes}: " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
     assert sim.nslots == s.plasma_shape()[0] > 0
     assert max(v for k, v in errs.items() if k != "f0") <= tol, errs
     assert errs.get("f0", 0.0) <= 2e-3, errs
