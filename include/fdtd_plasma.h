@@ -227,7 +227,7 @@ int fdtd_plasma_check_canaries(fdtd_plasma_t h, int64_t *corrupted);
 
 /* Self-test of the bounded waits (no counterpart in the paper): the tcgen05
  * kernels wait for their tensor-core results, and the TMA column stencils for
- * their plane loads, on mbarriers with an iteration limit, after which they
+ * their plane loads, on mbarriers with an iteration or wall-clock limit, after which they
  * set an error word (reported as FDTD_ERR_TIMEOUT by fdtd_plasma_diagnostics
  * and by host reads of fdtd_plasma_read_fields) and return instead of hanging.  This launches one
  * CTA that waits, with the same helper, on a barrier nothing arrives at, for

@@ -52,6 +52,13 @@ __device__ __forceinline__ float gelu_f(float z)
     const float hz = 0.5f * z;
     return fmaf(hz, t, hz);
 }
+// 2 gelu(z) = z + z tanh(u), u = z (sqrt(2/pi) + sqrt(2/pi) 0.044715 z^2): four FP32 operations and one tanh
+constexpr float kGeluCA = kGeluC * kGeluA;
+__device__ __forceinline__ float gelu2_f(float z)
+{
+    const float t = tanh_fast(z * fmaf(kGeluCA, z * z, kGeluC));
+    return fmaf(z, t, z);
+}
 // d gelu / dz = 0.5 (1 + t) + 0.5 z (1 - t^2) sqrt(2/pi) (1 + 3 * 0.044715 z^2)
 __device__ __forceinline__ float gelu_grad_f(float z)
 {

@@ -223,7 +223,9 @@ constexpr int kTcGroups = 4;
 struct MlpTcWeights {
     __align__(128) __nv_bfloat16 w1[kMlpH * kMlpK1];
     __align__(128) __nv_bfloat16 w2[kMlpH * kMlpH];
-    float b1[kMlpH], b2[kMlpH], w3[kMlpH];
+    __align__(16) float b1[kMlpH];
+    __align__(16) float b2[kMlpH];
+    __align__(16) float w3[kMlpH];   // half scale (see mlp_tc4_load_weights)
     float b3;
     uint32_t tmem;
 };
@@ -242,6 +244,9 @@ struct MlpTcSmem4 {
 
 __device__ __forceinline__ void wg_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
+// The epilogues form 2 gelu(z) = z + z tanh(u) (one multiply fewer than gelu); W2 and w3 are stored at
+// half scale to compensate.  Both scalings are by a power of two, so the BF16 operands and every product
+// equal those of the unscaled form exactly.
 __device__ __forceinline__ void mlp_tc4_load_weights(MlpTcWeights &s, const float *__restrict__ P)
 {
     unsigned char *w1 = reinterpret_cast<unsigned char *>(s.w1), *w2 = reinterpret_cast<unsigned char *>(s.w2);
@@ -252,12 +257,12 @@ __device__ __forceinline__ void mlp_tc4_load_weights(MlpTcWeights &s, const floa
     }
     for (int i = threadIdx.x; i < kMlpH * kMlpH; i += blockDim.x) {
         const int k = i / kMlpH, n = i % kMlpH;
-        *reinterpret_cast<__nv_bfloat16 *>(w2 + core_off(n, k, kMlpH)) = __float2bfloat16_rn(P[kOffW2 + i]);
+        *reinterpret_cast<__nv_bfloat16 *>(w2 + core_off(n, k, kMlpH)) = __float2bfloat16_rn(0.5f * P[kOffW2 + i]);
     }
     for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) {
         s.b1[i] = P[kOffB1 + i];
         s.b2[i] = P[kOffB2 + i];
-        s.w3[i] = P[kOffW3 + i];
+        s.w3[i] = 0.5f * P[kOffW3 + i];
     }
     if (threadIdx.x == 0) s.b3 = P[kOffB3];
 }
@@ -312,7 +317,7 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
     const int warp = r >> 5;
     const uint32_t tmem = w.tmem + (uint32_t)(gi * 128);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    constexpr uint32_t kWait = 1u << 22;
+    constexpr uint64_t kWaitNs = 1000000000ull;   // the waiting warps sleep in the barrier, not poll it
     bool ok = true;
     fence_proxy_async_smem();
     tc_fence_before();
@@ -326,7 +331,7 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
                    kTcIdesc, kk > 0);
         tc_commit(&g.mbar);
     }
-    if (!mbar_wait(&g.mbar, *phase, kWait)) ok = false;
+    if (!mbar_wait_timed(&g.mbar, *phase, kWaitNs)) ok = false;
     *phase ^= 1u;
     tc_fence_after();
     unsigned char *a2 = reinterpret_cast<unsigned char *>(g.a2);
@@ -337,11 +342,13 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int k0 = c * 32 + q * 8;
+            const float4 ba = *reinterpret_cast<const float4 *>(&w.b1[k0]);
+            const float4 bb = *reinterpret_cast<const float4 *>(&w.b1[k0 + 4]);
             uint4 pk;
-            pk.x = pack_bf16(gelu_f(v[q * 8 + 0] + w.b1[k0 + 0]), gelu_f(v[q * 8 + 1] + w.b1[k0 + 1]));
-            pk.y = pack_bf16(gelu_f(v[q * 8 + 2] + w.b1[k0 + 2]), gelu_f(v[q * 8 + 3] + w.b1[k0 + 3]));
-            pk.z = pack_bf16(gelu_f(v[q * 8 + 4] + w.b1[k0 + 4]), gelu_f(v[q * 8 + 5] + w.b1[k0 + 5]));
-            pk.w = pack_bf16(gelu_f(v[q * 8 + 6] + w.b1[k0 + 6]), gelu_f(v[q * 8 + 7] + w.b1[k0 + 7]));
+            pk.x = pack_bf16(gelu2_f(v[q * 8 + 0] + ba.x), gelu2_f(v[q * 8 + 1] + ba.y));
+            pk.y = pack_bf16(gelu2_f(v[q * 8 + 2] + ba.z), gelu2_f(v[q * 8 + 3] + ba.w));
+            pk.z = pack_bf16(gelu2_f(v[q * 8 + 4] + bb.x), gelu2_f(v[q * 8 + 5] + bb.y));
+            pk.w = pack_bf16(gelu2_f(v[q * 8 + 6] + bb.z), gelu2_f(v[q * 8 + 7] + bb.w));
             *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
         }
     }
@@ -357,7 +364,7 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
                    kTcIdesc, kk > 0);
         tc_commit(&g.mbar);
     }
-    if (!mbar_wait(&g.mbar, *phase, kWait)) ok = false;
+    if (!mbar_wait_timed(&g.mbar, *phase, kWaitNs)) ok = false;
     *phase ^= 1u;
     tc_fence_after();
     float y = w.b3;
@@ -366,7 +373,14 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
         float v[32];
         tc_ld32(tmem + lane_base + c * 32, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) y += gelu_f(v[i] + w.b2[c * 32 + i]) * w.w3[c * 32 + i];
+        for (int i = 0; i < 32; i += 4) {
+            const float4 b = *reinterpret_cast<const float4 *>(&w.b2[c * 32 + i]);
+            const float4 o = *reinterpret_cast<const float4 *>(&w.w3[c * 32 + i]);
+            y = fmaf(gelu2_f(v[i + 0] + b.x), o.x, y);
+            y = fmaf(gelu2_f(v[i + 1] + b.y), o.y, y);
+            y = fmaf(gelu2_f(v[i + 2] + b.z), o.z, y);
+            y = fmaf(gelu2_f(v[i + 3] + b.w), o.w, y);
+        }
     }
     tc_fence_before();
     // warpgroup-uniform verdict
