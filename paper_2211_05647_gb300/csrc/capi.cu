@@ -498,11 +498,9 @@ cudaError_t part_e(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T>
     T *const *f = fs.f;
     const Source src = source_view(h);
     if (h->g.ndim == 1) {
-        launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep);
-        if (h->g.mur) {
-            const T m = (T)((kC0 * h->dt - h->g.dx) / (kC0 * h->dt + h->g.dx));
-            launch_mur1d<T>(st, f[FDTD_EX], (const T *)h->mur_state, h->nz, m);
-        }
+        const T m = (T)((kC0 * h->dt - h->g.dx) / (kC0 * h->dt + h->g.dx));
+        launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep,
+                      h->g.mur ? (const T *)h->mur_state : nullptr, m);
     } else if (h->g.ndim == 2) {
         launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));

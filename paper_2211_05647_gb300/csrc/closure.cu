@@ -24,6 +24,7 @@ namespace fp {
 
 __global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpSmem &s = *reinterpret_cast<MlpSmem *>(smem_raw);
     __shared__ int32_t s_cell[kMlpRows];
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
 __global__ void k_hist_push(const int32_t *__restrict__ cell, int64_t n, const float *__restrict__ E,
                             float *__restrict__ hist, const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int ring = (int)((*d_step + kstep) & 15);
@@ -91,6 +93,7 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
                          int64_t capacity, unsigned long long *__restrict__ count, uint32_t threshold, uint64_t seed,
                          const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int64_t step = *d_step + kstep;
@@ -119,6 +122,7 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
 // MMA-completion wait gives up, *err is set and the warpgroup stops.
 __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
 {
+    pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTcSmem4 &s = *reinterpret_cast<MlpTcSmem4 *>(smem_raw);
     mlp_tc4_load_weights(s.w, a.P);
@@ -179,7 +183,7 @@ cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
         // one CTA per SM: it allocates all 512 TMEM columns
         const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
         const int64_t grid = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, (int64_t)num_sms);
-        k_closure_tc<<<(unsigned)std::max<int64_t>(grid, 1), 512, smem, st>>>(a);
+        launch_pdl(k_closure_tc, dim3((unsigned)std::max<int64_t>(grid, 1)), dim3(512), smem, st, a);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(MlpSmem);
@@ -190,14 +194,14 @@ cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
     if (e != cudaSuccess) return e;
     const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
     const int64_t grid = std::min<int64_t>(tiles, (int64_t)num_sms * std::max(per_sm, 1));
-    k_closure<<<(unsigned)grid, 256, smem, st>>>(a);
+    launch_pdl(k_closure, dim3((unsigned)grid), dim3(256), smem, st, a);
     return cudaGetLastError();
 }
 
 void launch_hist_push(cudaStream_t st, const int32_t *cell, int64_t n, const float *E, float *hist,
                       const int64_t *d_step, int kstep)
 {
-    if (n) k_hist_push<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cell, n, E, hist, d_step, kstep);
+    if (n) launch_pdl(k_hist_push, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, cell, n, E, hist, d_step, kstep);
 }
 
 void launch_record(cudaStream_t st, int64_t n, const float *hist, const float *dens, const float *jslot, float *jprev,
@@ -205,7 +209,7 @@ void launch_record(cudaStream_t st, int64_t n, const float *hist, const float *d
                    const int64_t *d_step, int kstep)
 {
     if (n)
-        k_record<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, hist, dens, jslot, jprev, out, capacity, count,
+        launch_pdl(k_record, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, n, hist, dens, jslot, jprev, out, capacity, count,
                                                               threshold, seed, d_step, kstep);
 }
 

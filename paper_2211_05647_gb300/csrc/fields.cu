@@ -23,6 +23,7 @@ template <typename T>
 __global__ void k_h1d(const T *__restrict__ ex, T *__restrict__ hy, T *__restrict__ mur, int64_t nz, T ch, Source src,
                       const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k == 0) write_source(src, d_step, kstep);
     if (k < nz) hy[k] -= ch * (ex[k + 1] - ex[k]);   // mu0 dHy/dt = -dEx/dz
@@ -32,23 +33,23 @@ __global__ void k_h1d(const T *__restrict__ ex, T *__restrict__ hy, T *__restric
     }
 }
 
+// E update of the interior nodes; with Mur ends (mur != nullptr) the thread that
+// advances E_1 (E_{nz-1}) also sets E_0^{n+1} = E_1^n + m (E_1^{n+1} - E_0^n)
+// (and the mirror image at nz), so a step needs no separate boundary launch.
 template <typename T>
 __global__ void k_e1d(T *__restrict__ ex, const T *__restrict__ hy, int64_t nz, T ce, Source src,
-                      const int64_t *__restrict__ d_step, int kstep)
+                      const int64_t *__restrict__ d_step, int kstep, const T *__restrict__ mur, T m)
 {
+    pdl_enter();
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < 1 || k >= nz) return;
     T v = ex[k] - ce * (hy[k] - hy[k - 1]);           // eps0 dEx/dt = -dHy/dz - Jx
     if (src.kind && k == src.k) v += (T)*src.val;
     ex[k] = v;
-}
-
-template <typename T>
-__global__ void k_mur1d(T *__restrict__ ex, const T *__restrict__ mur, int64_t nz, T m)
-{
-    // E_0^{n+1} = E_1^n + m (E_1^{n+1} - E_0^n), and the mirror image at nz
-    if (threadIdx.x == 0) ex[0] = mur[0] + m * (ex[1] - ex[0]);
-    if (threadIdx.x == 1) ex[nz] = mur[1] + m * (ex[nz - 1] - ex[nz]);
+    if (mur) {
+        if (k == 1) ex[0] = mur[0] + m * (v - ex[0]);
+        if (k == nz - 1) ex[nz] = mur[1] + m * (v - ex[nz]);
+    }
 }
 
 // ------------------------------------------------------------------- 2-D TMz
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__rest
                                              int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp, Source src,
                                              const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i == 0 && j == 0) write_source(src, d_step, kstep);
@@ -128,6 +130,7 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
                                              int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp, Source src,
                                              const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (i < 1 || j < 1 || i >= nx || j >= ny) return;
@@ -154,6 +157,7 @@ __global__ void __launch_bounds__(256) k_h3d(const T *__restrict__ ex, const T *
                                              T *__restrict__ hz, int64_t nx, int64_t ny, int64_t nz, T ch, T cph,
                                              Cpml<T> cp, Source src, const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
@@ -190,6 +194,7 @@ __global__ void __launch_bounds__(256) k_e3d(T *__restrict__ ex, T *__restrict__
                                              T cpe, Cpml<T> cp, Source src, const int64_t *__restrict__ d_step,
                                              int kstep)
 {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
@@ -256,6 +261,7 @@ __global__ void __launch_bounds__(256) k_h2d_v4(const float *__restrict__ ez, fl
                                                 Cpml<float> cp, Source src, const int64_t *__restrict__ d_step,
                                                 int kstep)
 {
+    pdl_enter();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     if (q == 0 && j == 0) write_source(src, d_step, kstep);
@@ -294,6 +300,7 @@ __global__ void __launch_bounds__(256) k_e2d_v4(float *__restrict__ ez, const fl
                                                 float cpe, Cpml<float> cp, Source src,
                                                 const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     const int64_t i0 = 4 * q;
@@ -334,6 +341,7 @@ __global__ void __launch_bounds__(256) k_h3d_v4(const float *__restrict__ ex, co
                                                 int64_t ny, int64_t nz, float ch, float cph, Cpml<float> cp,
                                                 Source src, const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
@@ -436,6 +444,7 @@ __global__ void __launch_bounds__(256) k_e3d_v4(float *__restrict__ ex, float *_
                                                 Cpml<float> cp, Source src, const int64_t *__restrict__ d_step,
                                                 int kstep)
 {
+    pdl_enter();
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t j = (int64_t)blockIdx.y * blockDim.y + threadIdx.y;
     const int64_t k = (int64_t)blockIdx.z * blockDim.z + threadIdx.z;
@@ -573,6 +582,7 @@ __global__ void __launch_bounds__(kEhX * kEhY, 3) k_eh3d(FieldPtrs in, FieldOut 
                                                      PsiOut pout, Source src, const int64_t *__restrict__ d_step,
                                                      int kstep)
 {
+    pdl_enter();
     __shared__ float sH[2][3][kEhY + 2][kEhX + 2];   // H^{n+1/2}: x0-1..x0+32, y0-1..y0+8
     __shared__ float sEp[3][kEhY + 1][kEhX + 1];     // E': x0..x0+32, y0..y0+8
     __shared__ float sE[2][3][kEhY + 1][kEhX + 1];   // E^{n+1}: x0..x0+32, y0..y0+8
@@ -752,6 +762,7 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
                                                int64_t ny, float ce, float cpe, float ch, float cph, Cpml<float> cin,
                                                PsiOut pout, Source src, const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     __shared__ float sHx[kF2Y + 2][kF2X + 2], sHy[kF2Y + 2][kF2X + 2];   // x0-1..x0+64, y0-1..y0+16
     __shared__ float sEp[kF2Y + 1][kF2X + 1];                           // E': x0..x0+64, y0..y0+16
     __shared__ float sE[kF2Y + 1][kF2X + 1];                            // E^{n+1}
@@ -865,7 +876,11 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
     }
 }
 
-__global__ void k_advance(int64_t *d_step, int64_t by) { *d_step += by; }
+__global__ void k_advance(int64_t *d_step, int64_t by)
+{
+    pdl_enter();
+    *d_step += by;
+}
 
 // ------------------------------------------------------------------ launchers
 
@@ -878,7 +893,7 @@ void launch_eh2d(cudaStream_t st, float *const fin[6], float *const fout[6], flo
     dim3 g(cdiv(nx, kF2X), cdiv(ny, kF2Y));
     PsiOut po{};
     for (int q = 0; q < 12; ++q) po.psi[q] = psi_out[q];
-    k_eh2d<<<g, kF2T, 0, st>>>(fin[FDTD_EZ], fin[FDTD_HX], fin[FDTD_HY], fout[FDTD_EZ], fout[FDTD_HX], fout[FDTD_HY],
+    launch_pdl(k_eh2d, dim3(g), dim3(kF2T), 0, st, fin[FDTD_EZ], fin[FDTD_HX], fin[FDTD_HY], fout[FDTD_EZ], fout[FDTD_HX], fout[FDTD_HY],
                                nx, ny, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
 }
 
@@ -892,7 +907,7 @@ void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], flo
     FieldOut o{fout[0], fout[1], fout[2], fout[3], fout[4], fout[5]};
     PsiOut po{};
     for (int q = 0; q < 12; ++q) po.psi[q] = psi_out[q];
-    k_eh3d<<<g, dim3(kEhX, kEhY), 0, st>>>(a, o, nx, ny, nz, tz, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
+    launch_pdl(k_eh3d, dim3(g), dim3(dim3(kEhX, kEhY)), 0, st, a, o, nx, ny, nz, tz, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
 }
 
 
@@ -900,21 +915,14 @@ template <typename T>
 void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch, Source src,
                 const int64_t *d_step, int kstep)
 {
-    k_h1d<T><<<cdiv(nz + 1, 256), 256, 0, st>>>(ex, hy, mur_state, nz, ch, src, d_step, kstep);
+    launch_pdl(k_h1d<T>, dim3(cdiv(nz + 1, 256)), dim3(256), 0, st, ex, hy, mur_state, nz, ch, src, d_step, kstep);
 }
 template <typename T>
-void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep)
+void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep,
+                const T *mur_state, T m)
 {
-    k_e1d<T><<<cdiv(nz + 1, 256), 256, 0, st>>>(ex, hy, nz, ce, src, d_step, kstep);
+    launch_pdl(k_e1d<T>, dim3(cdiv(nz, 256)), dim3(256), 0, st, ex, hy, nz, ce, src, d_step, kstep, mur_state, m);
 }
-template <typename T>
-void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m)
-{
-    k_mur1d<T><<<1, 32, 0, st>>>(ex, mur_state, nz, m);
-}
-// cpt = cells per thread.  The four-cells-per-thread kernels (cpt = 4) take
-// FP32 rows of a multiple of 4 cells and whole-warp blocks, b.x then counting
-// quads of cells; anything else runs one cell per thread.
 template <typename T>
 bool use_v4(int64_t nx, dim3 b, int cpt)
 {
@@ -928,12 +936,12 @@ void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t 
     if constexpr (std::is_same<T, float>::value) {
         if (use_v4<T>(nx, b, cpt)) {
             dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y));
-            k_h2d_v4<<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
+            launch_pdl(k_h2d_v4, dim3(g), dim3(b), 0, st, ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
             return;
         }
     }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y));
-    k_h2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
+    launch_pdl(k_h2d<T>, dim3(g), dim3(b), 0, st, ez, hx, hy, nx, ny, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, int64_t ny, T ce, T cpe, Cpml<T> cp,
@@ -942,12 +950,12 @@ void launch_e2d(cudaStream_t st, T *ez, const T *hx, const T *hy, int64_t nx, in
     if constexpr (std::is_same<T, float>::value) {
         if (use_v4<T>(nx, b, cpt)) {
             dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y));
-            k_e2d_v4<<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
+            launch_pdl(k_e2d_v4, dim3(g), dim3(b), 0, st, ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
             return;
         }
     }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y));
-    k_e2d<T><<<g, b, 0, st>>>(ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
+    launch_pdl(k_e2d<T>, dim3(g), dim3(b), 0, st, ez, hx, hy, nx, ny, ce, cpe, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ch, T cph, Cpml<T> cp,
@@ -956,13 +964,13 @@ void launch_h3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t 
     if constexpr (std::is_same<T, float>::value) {
         if (use_v4<T>(nx, b, cpt)) {
             dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
-            k_h3d_v4<<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step,
+            launch_pdl(k_h3d_v4, dim3(g), dim3(b), 0, st, f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step,
                                       kstep);
             return;
         }
     }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
-    k_h3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step, kstep);
+    launch_pdl(k_h3d<T>, dim3(g), dim3(b), 0, st, f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ch, cph, cp, src, d_step, kstep);
 }
 template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
@@ -971,20 +979,20 @@ void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t 
     if constexpr (std::is_same<T, float>::value) {
         if (use_v4<T>(nx, b, cpt)) {
             dim3 g(cdiv(nx / 4, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
-            k_e3d_v4<<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step,
+            launch_pdl(k_e3d_v4, dim3(g), dim3(b), 0, st, f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step,
                                       kstep);
             return;
         }
     }
     dim3 g(cdiv(nx, b.x), cdiv(ny, b.y), cdiv(nz, b.z));
-    k_e3d<T><<<g, b, 0, st>>>(f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step, kstep);
+    launch_pdl(k_e3d<T>, dim3(g), dim3(b), 0, st, f[0], f[1], f[2], f[3], f[4], f[5], nx, ny, nz, ce, cpe, cp, src, d_step, kstep);
 }
-void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by) { k_advance<<<1, 1, 0, st>>>(d_step, by); }
+void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by) { launch_pdl(k_advance, dim3(1), dim3(1), 0, st, d_step, by); }
 
 #define FP_INST(T)                                                                                            \
     template void launch_h1d<T>(cudaStream_t, const T *, T *, T *, int64_t, T, Source, const int64_t *, int);  \
-    template void launch_e1d<T>(cudaStream_t, T *, const T *, int64_t, T, Source, const int64_t *, int);      \
-    template void launch_mur1d<T>(cudaStream_t, T *, const T *, int64_t, T);                                  \
+    template void launch_e1d<T>(cudaStream_t, T *, const T *, int64_t, T, Source, const int64_t *, int, const T *, \
+                                T);                                                                          \
     template void launch_h2d<T>(cudaStream_t, const T *, T *, T *, int64_t, int64_t, T, T, Cpml<T>, Source,   \
                                 const int64_t *, int, dim3, int);                                                  \
     template void launch_e2d<T>(cudaStream_t, T *, const T *, const T *, int64_t, int64_t, T, T, Cpml<T>,     \

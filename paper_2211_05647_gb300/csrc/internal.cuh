@@ -20,6 +20,36 @@ constexpr double kMe = 9.1093837015e-31;
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kPi = 3.14159265358979323846;
 
+// ------------------------------------------------ programmatic dependent launch
+// The kernels of a step are launched with launch_pdl: each may be scheduled
+// while its predecessor on the stream is still finishing (the launch latency
+// overlaps the predecessor's last wave), and begins with pdl_enter(), which
+// waits for the predecessor grid to complete with its memory visible before any
+// global access, then lets its own successor be scheduled.  Launched without
+// the attribute (or after a non-kernel node) the wait returns at once.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ------------------------------------------------------------------ views
 
 // Per-axis CPML profile at E (integer) and H (half-integer) positions, plus
@@ -125,9 +155,8 @@ template <typename T>
 void launch_h1d(cudaStream_t st, const T *ex, T *hy, T *mur_state, int64_t nz, T ch, Source src,
                 const int64_t *d_step, int kstep);
 template <typename T>
-void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep);
-template <typename T>
-void launch_mur1d(cudaStream_t st, T *ex, const T *mur_state, int64_t nz, T m);
+void launch_e1d(cudaStream_t st, T *ex, const T *hy, int64_t nz, T ce, Source src, const int64_t *d_step, int kstep,
+                const T *mur_state, T m);   // mur_state == nullptr: PEC ends
 template <typename T>
 void launch_h2d(cudaStream_t st, const T *ez, T *hx, T *hy, int64_t nx, int64_t ny, T ch, T cph, Cpml<T> cp,
                 Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);

@@ -92,6 +92,7 @@ namespace fp {
 template <typename T>
 __global__ void __launch_bounds__(256) k_kinetic_nl(KinArgs<T> a, int npar, int nperp, T dvpar, T qm, T dt)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nn = npar * nperp;
     T *s_al = reinterpret_cast<T *>(smem_raw), *s_be = s_al + a.pitch, *s_w = s_be + a.pitch;
@@ -157,7 +158,7 @@ cudaError_t launch_kinetic_nl(cudaStream_t st, const KinArgs<T> &a, int npar, in
     if (e != cudaSuccess) return e;
     int64_t blocks = (a.nslots + 7) / 8;
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms * std::max(per_sm, 1));
-    kern<<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, st>>>(a, npar, nperp, (T)dvpar, (T)qm, (T)dt);
+    launch_pdl(kern, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), smem, st, a, npar, nperp, (T)dvpar, (T)qm, (T)dt);
     return cudaGetLastError();
 }
 
@@ -190,6 +191,7 @@ struct F0Tab {
 template <typename T, int L>
 __global__ void __launch_bounds__(256) k_kinetic_f0(KinArgs<T> a, F0Args<T> f)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = a.pitch;
     T *s = reinterpret_cast<T *>(smem_raw);
@@ -309,6 +311,7 @@ __global__ void __launch_bounds__(256) k_kinetic_f0(KinArgs<T> a, F0Args<T> f)
 template <typename T>
 __global__ void __launch_bounds__(256) k_kinetic_f0_wide(KinArgs<T> a, F0Args<T> f)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int P = a.pitch, nv = f.nv;
     T *s = reinterpret_cast<T *>(smem_raw);
@@ -389,7 +392,7 @@ cudaError_t run_kinetic_f0(cudaStream_t st, const KinArgs<T> &a, const F0Args<T>
     const int64_t rows_per_block = 8 * (32 / L);
     int64_t blocks = (a.nslots + rows_per_block - 1) / rows_per_block;
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms * std::max(per_sm, 1));
-    kern<<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, st>>>(a, f);
+    launch_pdl(kern, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), smem, st, a, f);
     return cudaGetLastError();
 }
 
@@ -419,7 +422,7 @@ cudaError_t launch_kinetic_f0(cudaStream_t st, const KinArgs<T> &a, const F0Args
     if (per_sm < 1) return cudaErrorInvalidConfiguration;   // row too long for shared memory
     int64_t blocks = (a.nslots + 7) / 8;
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms * per_sm);
-    kern<<<(unsigned)std::max<int64_t>(blocks, 1), 256, smem, st>>>(a, f);
+    launch_pdl(kern, dim3((unsigned)std::max<int64_t>(blocks, 1)), dim3(256), smem, st, a, f);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ namespace fp {
 template <typename TS, typename TA, int VPL, int L>
 __global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
 {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TA *s_tab = reinterpret_cast<TA *>(smem_raw);
     for (int t = threadIdx.x; t < 3 * a.pitch; t += blockDim.x) s_tab[t] = a.tab[t];
@@ -74,7 +75,7 @@ cudaError_t run_kinetic(cudaStream_t st, const KinArgs<TA> &a, int num_sms, int 
     const int64_t cap = (int64_t)num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, 256, smem, st>>>(a);
+    launch_pdl(kern, dim3((unsigned)blocks), dim3(256), smem, st, a);
     return cudaGetLastError();
 }
 

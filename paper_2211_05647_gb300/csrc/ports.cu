@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(256) k_ports(const T *__restrict__ pol, const 
                                                double *__restrict__ acc, int nfreq, double dt,
                                                const int64_t *__restrict__ d_step, int kstep)
 {
+    pdl_enter();
     __shared__ double red[8];
     __shared__ double mean_dt;
     const int p = blockIdx.x;
@@ -43,7 +44,7 @@ template <typename T>
 cudaError_t launch_ports(cudaStream_t st, const T *pol, int nports, const int64_t *off, const int64_t *cells,
                          const double *freq, double *acc, int nfreq, double dt, const int64_t *d_step, int kstep)
 {
-    k_ports<T><<<nports, 256, 0, st>>>(pol, off, cells, freq, acc, nfreq, dt, d_step, kstep);
+    launch_pdl(k_ports<T>, dim3(nports), dim3(256), 0, st, pol, off, cells, freq, acc, nfreq, dt, d_step, kstep);
     return cudaGetLastError();
 }
 

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_h3d_tma(const __grid_consta
                                                  int tz, float ch, float cph, Cpml<float> cp, Source src,
                                                  const int64_t *__restrict__ d_step, int kstep, int *err)
 {
+    pdl_enter();
     extern __shared__ __align__(128) float ring[];
     __shared__ TmaSmem s;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_e3d_tma(const __grid_consta
                                                  float *__restrict__ ey, float *__restrict__ ez, int nx, int ny, int nz,
                                                  int tz, float ce, float cpe, Cpml<float> cp, Source src, int *err)
 {
+    pdl_enter();
     extern __shared__ __align__(128) float ring[];
     __shared__ TmaSmem s;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(kTT, kFMinBlocks) k_eh3d_tma(const __grid_cons
                                                               float ch, float cph, Cpml<float> cin, Source src,
                                                               const int64_t *__restrict__ d_step, int kstep, int *err)
 {
+    pdl_enter();
     extern __shared__ __align__(128) float ring[];
     float *ebuf = ring + kFStages * kFStage;   // [2][3][kFBuf]: E^{n+1} of planes of even / odd z
     __shared__ TmaSmemN<kFStages> s;
@@ -536,7 +539,7 @@ void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_
                     float ch, float cph, Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int tz, int *err)
 {
     const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
-    k_h3d_tma<<<g, kTT, kSmemBytes, st>>>(t->h, f[FDTD_EX], f[FDTD_EY], f[FDTD_HX], f[FDTD_HY], f[FDTD_HZ], (int)nx,
+    launch_pdl(k_h3d_tma, dim3(g), dim3(kTT), kSmemBytes, st, t->h, f[FDTD_EX], f[FDTD_EY], f[FDTD_HX], f[FDTD_HY], f[FDTD_HZ], (int)nx,
                                           (int)ny, (int)nz, tz, ch, cph, cp, src, d_step, kstep, err);
 }
 
@@ -556,7 +559,7 @@ bool launch_eh3d_tma(cudaStream_t st, const TmaMaps *t, float *const fin[6], flo
                                                   (int)kFSmemBytes) == cudaSuccess;
     if (!attr) return false;
     const dim3 g(cdivu(t->nx, kTX), cdivu(t->ny, kTY), cdivu(t->nz, tz));
-    k_eh3d_tma<<<g, kTT, kFSmemBytes, st>>>(t->fused[b], o, (int)t->nx, (int)t->ny, (int)t->nz, tz, ce, cpe, ch, cph,
+    launch_pdl(k_eh3d_tma, dim3(g), dim3(kTT), kFSmemBytes, st, t->fused[b], o, (int)t->nx, (int)t->ny, (int)t->nz, tz, ce, cpe, ch, cph,
                                             cin, src, d_step, kstep, err);
     return true;
 }
@@ -565,7 +568,7 @@ void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_
                     float ce, float cpe, Cpml<float> cp, Source src, int tz, int *err)
 {
     const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
-    k_e3d_tma<<<g, kTT, kSmemBytes, st>>>(t->e, f[FDTD_HX], f[FDTD_HY], f[FDTD_EX], f[FDTD_EY], f[FDTD_EZ], (int)nx,
+    launch_pdl(k_e3d_tma, dim3(g), dim3(kTT), kSmemBytes, st, t->e, f[FDTD_HX], f[FDTD_HY], f[FDTD_EX], f[FDTD_EY], f[FDTD_EZ], (int)nx,
                                           (int)ny, (int)nz, tz, ce, cpe, cp, src, err);
 }
 
