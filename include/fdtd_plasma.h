@@ -428,6 +428,10 @@ int fdtd_batch_step(fdtd_batch_t b, int64_t nsteps);
 /* One quantity of one run: FDTD_EX (nz+1), FDTD_HY (nz), FDTD_J (per slot),
  * FDTD_DF (packed rows); sizes as fdtd_batch_quantity_bytes. */
 int fdtd_batch_read(fdtd_batch_t b, int32_t run, int which, void *dst, size_t bytes, int dst_is_device);
+/* Overwrite a field of one run (FDTD_EX: nz+1 values, FDTD_HY: nz, in the
+ * batch precision; host or device source, copied on the batch's stream and
+ * synchronised for host sources).  Other quantities: FDTD_ERR_INVAL. */
+int fdtd_batch_write(fdtd_batch_t b, int32_t run, int which, const void *src, size_t bytes, int src_is_device);
 size_t fdtd_batch_quantity_bytes(fdtd_batch_t b, int32_t run, int which);
 /* dt, steps done, total cells, total phase-space nodes, clusters launched and
  * CTAs per cluster (any pointer may be NULL). */

@@ -788,6 +788,21 @@ int fdtd_batch_read(fdtd_batch_t b, int32_t run, int which, void *dst, size_t by
     return FDTD_OK;
 }
 
+int fdtd_batch_write(fdtd_batch_t b, int32_t run, int which, const void *src, size_t bytes, int src_is_device)
+{
+    if (!b || !src) return FDTD_ERR_INVAL;
+    if (which != FDTD_EX && which != FDTD_HY) return bfail(b, FDTD_ERR_INVAL, "only FDTD_EX and FDTD_HY are writable");
+    const size_t need = fdtd_batch_quantity_bytes(b, run, which);
+    if (need == 0) return bfail(b, FDTD_ERR_INVAL, "quantity %d of run %d is absent", which, run);
+    if (bytes != need) return bfail(b, FDTD_ERR_INVAL, "needs %zu bytes, got %zu", need, bytes);
+    char *dst = which == FDTD_EX ? (char *)b->E + b->e_off[run] * b->esz : (char *)b->H + b->h_off[run] * b->esz;
+    cudaError_t e = cudaMemcpyAsync(dst, src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "write: %s", cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
 int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters,
                     int32_t *cluster_ctas)
 {

@@ -171,6 +171,8 @@ SIGNATURES = {
     "fdtd_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "fdtd_batch_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_int]),
+    "fdtd_batch_write": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_int]),
     "fdtd_batch_quantity_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int]),
     "fdtd_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -426,6 +428,13 @@ class Batch:
         if nb:
             self._check(self.lib.fdtd_batch_read(self.h, int(run), q, out.data_ptr(), nb, 0))
         return out.float().numpy() if dt == torch.bfloat16 else out.numpy()
+
+    def write(self, run: int, name: str, values):
+        """Overwrite a field (ex: nz+1 values, hy: nz) of one run from host values."""
+        q = QUANTITY[name]
+        dt = np.float64 if self.precision == "f64" else np.float32
+        v = np.ascontiguousarray(np.asarray(values, dtype=dt))
+        self._check(self.lib.fdtd_batch_write(self.h, int(run), q, v.ctypes.data, v.nbytes, 0))
 
     def close(self):
         if getattr(self, "h", None):

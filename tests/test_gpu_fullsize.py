@@ -70,3 +70,42 @@ def test_full_size_random_state(oracle_lib, name, steps, tol, min_gb, monkeypatc
     assert sim.nslots == s.plasma_shape()[0] > 0
     assert max(v for k, v in errs.items() if k != "f0") <= tol, errs
     assert errs.get("f0", 0.0) <= 2e-3, errs
+
+
+@pytest.mark.parametrize("name,tol", [("batch1d_256_f32", 1e-5), ("batch1d_256_bf16", 5e-3)])
+def test_batch_full_size_random_state(oracle_lib, name, tol):
+    """The 256-run batched workload as bench.py builds and launches it (same
+    Batch construction, so the same cluster packing and row shapes), every run
+    from a seeded random E/H state, 4 steps, against each run's FP64 oracle:
+    fields of every run and J of every plasma slot."""
+    if _mem_available_gb() < 8:
+        pytest.skip("needs 8 GB of host memory for the FP64 oracle of 256 runs")
+    from paper_2211_05647_gb300 import Batch
+    specs = WORKLOADS[name]()
+    b = Batch(specs)
+    sims = []
+    for r, sp in enumerate(specs):
+        nz = sp["grid"]["nz"]
+        st = random_state({"ex": nz + 1, "hy": nz}, seed=1000 + r)
+        sim = oracle_sim(oracle_lib, sp)
+        for f, v in st.items():
+            v32 = v.astype(np.float32)
+            b.write(r, f, v32)
+            sim.set(f, v32.astype(np.float64))
+        sims.append(sim)
+    b.step(4)
+    worst = {"ex": 0.0, "hy": 0.0, "j": 0.0}
+    nslots = 0
+    for r, sim in enumerate(sims):
+        sim.step(4)
+        for f in ("ex", "hy"):
+            ref = sim.get(f)
+            worst[f] = max(worst[f], float(np.linalg.norm(b.read(r, f) - ref) / np.linalg.norm(ref)))
+        if sim.nslots:
+            nslots += sim.nslots
+            jr = sim.get("j")
+            worst["j"] = max(worst["j"], float(np.linalg.norm(b.read(r, "j") - jr) / np.linalg.norm(jr)))
+    info = b.info()
+    print(f"{name}: {len(specs)} runs, {info['clusters']} clusters x {info['cluster_ctas']} CTAs, {nslots} slots: "
+          + " ".join(f"{k}={v:.3e}" for k, v in worst.items()))
+    assert nslots > 0 and max(worst.values()) <= tol, worst
