@@ -418,6 +418,8 @@ def closure_bench(args, spec, rank, world, local):
         s = Solver.from_spec(spec, device=local)
         if with_closure:
             s.set_closure(params, n_train_max=nmax, engine=args.engine, **sc)
+        if not args.no_autotune:
+            s.autotune()                   # untimed: stencil (and fallback kinetic) launch shapes
         s.step(args.warmup)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -427,6 +429,7 @@ def closure_bench(args, spec, rank, world, local):
         torch.cuda.synchronize()
         fields = {f: s.read(f, device=False) for f in ("ez", "hx", "hy")}
         kt = s.time_kernels(20)
+        kt["launch_shapes"] = s.launch_shapes()
         shape = s.closure_shape() if with_closure else (s.plasma_shape()[0], 0)
         s.close()
         torch.cuda.empty_cache()

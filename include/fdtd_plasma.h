@@ -211,9 +211,9 @@ typedef struct {
     double kin_ms, stencil_ms;                   /* best per-launch times */
     int32_t cells_per_thread;                    /* stencils: 1, or 4 (FP32 rows of a multiple of 4 cells;
                                                     block_x then counts groups of 4 cells) */
-    int32_t stencil_tz;                          /* 3-D FP32 (nx a multiple of 4): > 0 when the TMA column
-                                                    stencils won -- 32 x 8 threads, each block walking
-                                                    stencil_tz planes along z; 0 = grid-of-cells kernels */
+    int32_t stencil_tz;                          /* FP32, nx a multiple of 4: > 0 when the TMA stencils won
+                                                    -- 32 x 8 threads, each block walking stencil_tz planes
+                                                    (3-D) or rows (2-D); 0 = grid-of-cells kernels */
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
@@ -251,12 +251,13 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * sequence up to FP32 rounding order (bit for bit where the TMA column
  * stencils below are selected: their fused pass then runs on TMA-staged
  * planes too).  0 turns it off (and frees the copy).
- * FDTD_OPT_STENCIL_TZ: 0 selects the grid-of-cells 3-D stencil kernels; a
- * value tz in 1..1024 selects the TMA column kernels (3-D FP32, nx a multiple
- * of 4): 32 x 8 threads per block, each block walking tz planes along z with
- * its planes staged in shared memory by tensor copies.  The autotuner sets it
- * too (fdtd_tune_result.stencil_tz).  Results equal the grid-of-cells kernels
- * bit for bit.
+ * FDTD_OPT_STENCIL_TZ: 0 selects the grid-of-cells stencil kernels; a value
+ * tz in 1..1024 selects the TMA kernels (2-D and 3-D FP32, nx a multiple of 4):
+ * 32 x 8 threads per block; in 3-D each block walks tz planes along z, in 2-D
+ * tz rows (rounded up to a multiple of 8) of a 32-cell strip, in 8-row chunks;
+ * planes / chunks are staged in shared memory by tensor copies.  The
+ * autotuner sets it too (fdtd_tune_result.stencil_tz).  Results equal the
+ * one-cell-per-thread kernels bit for bit.
  * FDTD_ERR_INVAL for an unknown option or value. */
 enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);

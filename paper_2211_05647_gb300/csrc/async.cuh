@@ -70,6 +70,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t byte
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
 }
 
+// tiled 2-D tensor load global -> shared (as tma_load_3d, one dimension fewer)
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_t *m, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_addr(dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(m))
+        : "memory");
+}
+
 // tiled 3-D tensor load global -> shared (box given by the tensor map),
 // completion counted in bytes on mbarrier m; coordinates are element
 // indices (x innermost), out-of-range elements are filled with zero

@@ -392,7 +392,7 @@ FieldSet<T> field_set(fdtd_plasma *h, int set)
 template <typename T>
 const TmaMaps *tma_for(fdtd_plasma *h, const FieldSet<T> &fs)
 {
-    if (sizeof(T) != 4 || h->g.ndim != 3 || h->st_tz <= 0) return nullptr;
+    if (sizeof(T) != 4 || h->g.ndim < 2 || h->st_tz <= 0) return nullptr;
     if (!h->tma) h->tma = tma_maps_create(reinterpret_cast<float *const *>(h->f), h->nx, h->ny, h->nz);
     return tma_maps_match(h->tma, reinterpret_cast<float *const *>(fs.f)) ? h->tma : nullptr;
 }
@@ -407,9 +407,16 @@ cudaError_t part_h(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T>
     if (h->g.ndim == 1)
         launch_h1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->g.mur ? (T *)h->mur_state : nullptr, h->nz, ch, src, h->d_step,
                       kstep);
-    else if (h->g.ndim == 2)
+    else if (h->g.ndim == 2) {
+        if constexpr (sizeof(T) == 4) {
+            if (const TmaMaps *t = tma_for(h, fs)) {
+                launch_h2d_tma(st, t, f, h->nx, h->ny, ch, cph, fs.cp, src, h->d_step, kstep, h->st_tz, h->d_err);
+                return cudaGetLastError();
+            }
+        }
         launch_h2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ch, cph, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
+    }
     else {
         if constexpr (sizeof(T) == 4) {
             if (const TmaMaps *t = tma_for(h, fs)) {
@@ -502,6 +509,12 @@ cudaError_t part_e(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T>
         launch_e1d<T>(st, f[FDTD_EX], f[FDTD_HY], h->nz, ce, src, h->d_step, kstep,
                       h->g.mur ? (const T *)h->mur_state : nullptr, m);
     } else if (h->g.ndim == 2) {
+        if constexpr (sizeof(T) == 4) {
+            if (const TmaMaps *t = tma_for(h, fs)) {
+                launch_e2d_tma(st, t, f, h->nx, h->ny, ce, cpe, fs.cp, src, h->st_tz, h->d_err);
+                return cudaGetLastError();
+            }
+        }
         launch_e2d<T>(st, f[FDTD_EZ], f[FDTD_HX], f[FDTD_HY], h->nx, h->ny, ce, cpe, fs.cp, src, h->d_step, kstep,
                       stencil_block(h), stencil_cpt(h));
     } else {
@@ -835,10 +848,10 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
     if (option == FDTD_OPT_STENCIL_TZ) {
         if (value < 0 || value > 1024) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_STENCIL_TZ takes 0 .. 1024");
         if (value > 0) {
-            if (h->g.ndim != 3 || h->g.precision != FDTD_F32)
-                return fail(h, FDTD_ERR_INVAL, "the TMA column stencils run on 3-D FP32 grids");
+            if (h->g.ndim < 2 || h->g.precision != FDTD_F32)
+                return fail(h, FDTD_ERR_INVAL, "the TMA stencils run on 2-D and 3-D FP32 grids");
             if (!h->tma) h->tma = tma_maps_create(reinterpret_cast<float *const *>(h->f), h->nx, h->ny, h->nz);
-            if (!h->tma) return fail(h, FDTD_ERR_INVAL, "the TMA column stencils need nx a multiple of 4");
+            if (!h->tma) return fail(h, FDTD_ERR_INVAL, "the TMA stencils need nx a multiple of 4");
         }
         CK(h, cudaStreamSynchronize(h->stream));
         drop_graphs(h);
@@ -1241,9 +1254,23 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
                 }
             }
         }
-        // 3-D FP32: the TMA column kernels, tz planes per block
+        // FP32: the TMA kernels (2-D: rows per block; 3-D: planes per block)
         if constexpr (sizeof(T) == 4) {
-            if (h->g.ndim == 3 && !h->tma) h->tma = tma_maps_create(f, h->nx, h->ny, h->nz);
+            if (!h->tma) h->tma = tma_maps_create(f, h->nx, h->ny, h->nz);
+            if (h->g.ndim == 2 && h->tma) {
+                for (int rows : {32, 48, 64, 96, 128}) {
+                    if (rows > 4 * h->ny) continue;
+                    const double ms = time_ms([&] {
+                        launch_h2d_tma(st, h->tma, f, h->nx, h->ny, ch, cph, cp, src, h->d_step, 0, rows, h->d_err);
+                        launch_e2d_tma(st, h->tma, f, h->nx, h->ny, ce, cpe, cp, src, rows, h->d_err);
+                    });
+                    if (ms < best) {
+                        best = ms;
+                        out->block_x = 32; out->block_y = 8; out->block_z = 1; out->cells_per_thread = 1;
+                        out->stencil_tz = rows;
+                    }
+                }
+            }
             if (h->g.ndim == 3 && h->tma) {
                 for (int tz : {8, 12, 16, 24, 32}) {
                     if (tz > 2 * h->nz) continue;

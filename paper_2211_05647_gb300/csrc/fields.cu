@@ -54,51 +54,7 @@ __global__ void k_e1d(T *__restrict__ ex, const T *__restrict__ hy, int64_t nz, 
 
 // ------------------------------------------------------------------- 2-D TMz
 
-// CPML H update of one 2-D cell (Eq. 7-12): psi <- b psi + a dE, curl scaled by 1/kappa.
-template <typename T>
-__device__ __forceinline__ void h2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ch, T cph,
-                                        T dEy, T dEx, T &hxv, T &hyv)
-{
-    const int L = cp.L;
-    if (in_slab<T>(j, ny, L)) {
-        T *p = cp.psi[2] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
-        T ps = cp.bh[1][j] * *p + cp.ah[1][j] * dEy;
-        *p = ps;
-        hxv -= ch * dEy * cp.ikh[1][j] + cph * ps;
-    } else {
-        hxv -= ch * dEy;
-    }
-    if (in_slab<T>(i, nx, L)) {
-        T *p = cp.psi[3] + j * (2 * L) + slab_slot<T>(i, nx, L);
-        T ps = cp.bh[0][i] * *p + cp.ah[0][i] * dEx;
-        *p = ps;
-        hyv += ch * dEx * cp.ikh[0][i] + cph * ps;
-    } else {
-        hyv += ch * dEx;
-    }
-}
-
-// CPML curl term of the E update of one 2-D cell.
-template <typename T>
-__device__ __forceinline__ T e2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ce, T cpe,
-                                     T dHx, T dHy)
-{
-    const int L = cp.L;
-    T px = T(0), py = T(0), kx = T(1), ky = T(1);
-    if (in_slab<T>(i, nx, L)) {
-        T *p = cp.psi[0] + j * (2 * L) + slab_slot<T>(i, nx, L);
-        px = cp.be[0][i] * *p + cp.ae[0][i] * dHx;
-        *p = px;
-        kx = cp.ike[0][i];
-    }
-    if (in_slab<T>(j, ny, L)) {
-        T *p = cp.psi[1] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
-        py = cp.be[1][j] * *p + cp.ae[1][j] * dHy;
-        *p = py;
-        ky = cp.ike[1][j];
-    }
-    return ce * (dHx * kx - dHy * ky) + cpe * (px - py);
-}
+// (2-D CPML cell updates h2d_pml / e2d_pml: stencil_common.cuh)
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__restrict__ hx, T *__restrict__ hy,

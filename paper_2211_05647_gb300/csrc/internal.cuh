@@ -33,6 +33,22 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Launch without programmatic serialization, for kernels that must not share
+// SMs with early-launched neighbours: the TMA stencils hold up to ~170 KB of
+// shared memory per SM, and dependent CTAs waiting beside them (a different
+// shared-memory configuration) stalled the replayed 2-D step by 17 %.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_plain(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                               Args... args)
@@ -188,6 +204,11 @@ void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_
                     float ch, float cph, Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int tz, int *err);
 void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
                     float ce, float cpe, Cpml<float> cp, Source src, int tz, int *err);
+// 2-D TMz strips fed by TMA (32-cell strips walking `rows` rows in 8-row chunks; maps made with nz == 1)
+void launch_h2d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, float ch, float cph,
+                    Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int rows, int *err);
+void launch_e2d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, float ce, float cpe,
+                    Cpml<float> cp, Source src, int rows, int *err);
 // fused E^{n+1} + H^{n+3/2} on TMA-staged planes between field sets 0 and 1 (both given to prepare);
 // launch returns false (nothing launched) when fin is neither prepared set
 bool tma_fused_prepare(TmaMaps *t, float *const f0[6], float *const f1[6]);

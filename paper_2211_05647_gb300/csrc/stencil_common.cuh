@@ -27,6 +27,52 @@ __device__ __forceinline__ void write_source(const Source &src, const int64_t *d
     if (src.kind) *src.val = source_value(src, (double)(*d_step + kstep + 1) * src.dt);
 }
 
+// CPML H update of one 2-D cell (Eq. 7-12): psi <- b psi + a dE, curl scaled by 1/kappa.
+template <typename T>
+__device__ __forceinline__ void h2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ch, T cph,
+                                        T dEy, T dEx, T &hxv, T &hyv)
+{
+    const int L = cp.L;
+    if (in_slab<T>(j, ny, L)) {
+        T *p = cp.psi[2] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        T ps = cp.bh[1][j] * *p + cp.ah[1][j] * dEy;
+        *p = ps;
+        hxv -= ch * dEy * cp.ikh[1][j] + cph * ps;
+    } else {
+        hxv -= ch * dEy;
+    }
+    if (in_slab<T>(i, nx, L)) {
+        T *p = cp.psi[3] + j * (2 * L) + slab_slot<T>(i, nx, L);
+        T ps = cp.bh[0][i] * *p + cp.ah[0][i] * dEx;
+        *p = ps;
+        hyv += ch * dEx * cp.ikh[0][i] + cph * ps;
+    } else {
+        hyv += ch * dEx;
+    }
+}
+
+// CPML curl term of the E update of one 2-D cell.
+template <typename T>
+__device__ __forceinline__ T e2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ce, T cpe,
+                                     T dHx, T dHy)
+{
+    const int L = cp.L;
+    T px = T(0), py = T(0), kx = T(1), ky = T(1);
+    if (in_slab<T>(i, nx, L)) {
+        T *p = cp.psi[0] + j * (2 * L) + slab_slot<T>(i, nx, L);
+        px = cp.be[0][i] * *p + cp.ae[0][i] * dHx;
+        *p = px;
+        kx = cp.ike[0][i];
+    }
+    if (in_slab<T>(j, ny, L)) {
+        T *p = cp.psi[1] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        py = cp.be[1][j] * *p + cp.ae[1][j] * dHy;
+        *p = py;
+        ky = cp.ike[1][j];
+    }
+    return ce * (dHx * kx - dHy * ky) + cpe * (px - py);
+}
+
 // 3-D psi slot 2*f + d: f = Ex,Ey,Ez,Hx,Hy,Hz; d = 0 for the lower-numbered of
 // the two curl axes of the component, 1 for the other.  Derivative axis per slot:
 //   0:y 1:z | 2:x 3:z | 4:x 5:y | 6:y 7:z | 8:x 9:z | 10:x 11:y

@@ -1,5 +1,5 @@
-// stencil3d_tma.cu -- 3-D FP32 curl stencils (Sec. 2, Eq. 1-6; CPML Eq. 7-12)
-// fed by the tensor memory accelerator.
+// stencil_tma.cu -- FP32 curl stencils (Sec. 2, Eq. 1-6; CPML Eq. 7-12) fed by
+// the tensor memory accelerator: 3-D column kernels and 2-D strip kernels.
 //
 // A block owns a 32 x 8 column of cells and walks `tz` planes of it along z.
 // Per plane one thread issues six tiled TMA loads into a ring of shared-memory
@@ -16,6 +16,9 @@
 // the one block barrier of the plane, which also frees the stage of the
 // previous plane for the next load: with S = 4 stages three planes (21 KB)
 // per block, six blocks per SM, are in flight while one is computed.
+//
+// These kernels are launched without programmatic dependent launch (see
+// launch_plain) and do not let their successors start early.
 //
 // Every mbarrier wait is bounded: a block whose wait gives up stops storing,
 // waits (again bounded) for the loads it issued, sets bit 2 of the device
@@ -109,7 +112,6 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_h3d_tma(const __grid_consta
                                                  int tz, float ch, float cph, Cpml<float> cp, Source src,
                                                  const int64_t *__restrict__ d_step, int kstep, int *err)
 {
-    pdl_enter();
     extern __shared__ __align__(128) float ring[];
     __shared__ TmaSmem s;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -177,7 +179,6 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_e3d_tma(const __grid_consta
                                                  float *__restrict__ ey, float *__restrict__ ez, int nx, int ny, int nz,
                                                  int tz, float ce, float cpe, Cpml<float> cp, Source src, int *err)
 {
-    pdl_enter();
     extern __shared__ __align__(128) float ring[];
     __shared__ TmaSmem s;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
@@ -303,7 +304,6 @@ __global__ void __launch_bounds__(kTT, kFMinBlocks) k_eh3d_tma(const __grid_cons
                                                               float ch, float cph, Cpml<float> cin, Source src,
                                                               const int64_t *__restrict__ d_step, int kstep, int *err)
 {
-    pdl_enter();
     extern __shared__ __align__(128) float ring[];
     float *ebuf = ring + kFStages * kFStage;   // [2][3][kFBuf]: E^{n+1} of planes of even / odd z
     __shared__ TmaSmemN<kFStages> s;
@@ -421,6 +421,138 @@ __global__ void __launch_bounds__(kTT, kFMinBlocks) k_eh3d_tma(const __grid_cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// 2-D TMz strips.  A block of 32 x 8 threads owns a 32-cell strip of x and walks
+// `rows` rows of it in chunks of kC2 = 8 * kR2 rows (each thread takes rows ty,
+// ty + 8, ...); per chunk one thread issues the tiled 2-D loads of the
+// differentiated component(s) as 36 x (kC2 + 1) boxes (the one-cell x / y
+// neighbours, zero-filled past the grid) and of the updated component(s) as
+// 32 x kC2 tiles into a stage of the same 4-stage ring; one waiting warp and one
+// block barrier per chunk.  The cell formulas are those of k_h2d / k_e2d.
+
+constexpr int kR2 = 2;                              // rows per thread and chunk
+constexpr int kS2Stages = 4;                        // stages of the 2-D ring
+constexpr int kC2 = kTY * kR2;                      // rows per chunk
+constexpr int kB2Y = kC2 + 1;
+constexpr int kB2Pitch = (kBX * kB2Y + 31) / 32 * 32;   // floats per box, a multiple of 128 bytes
+constexpr int kT2 = kTX * kC2;                      // floats per tile
+constexpr int kS2H = kB2Pitch + 2 * kT2;            // H update stage: Ez box, Hx and Hy tiles
+constexpr int kS2E = 2 * kB2Pitch + kT2;            // E update stage: Hx and Hy boxes, Ez tile
+constexpr uint32_t kS2HBytes = kBX * kB2Y * 4 + 2 * kT2 * 4;
+constexpr uint32_t kS2EBytes = 2 * kBX * kB2Y * 4 + kT2 * 4;
+constexpr size_t kSmem2H = (size_t)kS2Stages * kS2H * 4, kSmem2E = (size_t)kS2Stages * kS2E * 4;
+
+struct Boxes2 {
+    CUtensorMap ez_nb, hx_nb, hy_nb;   // 36 x (kC2 + 1) boxes
+    CUtensorMap ez_t, hx_t, hy_t;      // 32 x kC2 tiles
+};
+
+__global__ void __launch_bounds__(kTT, kMinBlocks) k_h2d_tma(const __grid_constant__ Boxes2 bx, float *__restrict__ hx,
+                                                            float *__restrict__ hy, int nx, int ny, int rows, float ch,
+                                                            float cph, Cpml<float> cp, Source src,
+                                                            const int64_t *__restrict__ d_step, int kstep, int *err)
+{
+    extern __shared__ __align__(128) float ring[];
+    __shared__ TmaSmemN<kS2Stages> s;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * rows;
+    const int np = (min(rows, ny - y0) + kC2 - 1) / kC2;   // chunks
+    const int64_t i = x0 + tx;
+    if (quit_early(err, &s.quit)) return;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) write_source(src, d_step, kstep);
+    auto issue = [&](int p) {
+        float *st = ring + (p % kS2Stages) * kS2H;
+        uint64_t *m = &s.full[p % kS2Stages];
+        const int y = y0 + p * kC2;
+        mbar_arrive_expect_tx(m, kS2HBytes);
+        tma_load_2d(st, &bx.ez_nb, m, x0, y);
+        tma_load_2d(st + kB2Pitch, &bx.hx_t, m, x0, y);
+        tma_load_2d(st + kB2Pitch + kT2, &bx.hy_t, m, x0, y);
+    };
+    if (tid == 0) {
+        for (int q = 0; q < kS2Stages; ++q) mbar_init(&s.full[q], 1);
+        fence_proxy_async_smem();
+        for (int p = 0; p < min(kS2Stages, np); ++p) issue(p);
+    }
+    __syncthreads();
+    for (int q = 0; q < np; ++q) {
+        if (!plane_ready<kS2Stages>(s.full, q, np, ty, err)) return;
+        if (tid == 0 && q >= 1 && q - 1 + kS2Stages < np) issue(q - 1 + kS2Stages);
+        const float *st = ring + (q % kS2Stages) * kS2H;
+        const float *Ez = st, *Hx = st + kB2Pitch, *Hy = Hx + kT2;
+#pragma unroll
+        for (int r = 0; r < kR2; ++r) {
+            const int ly = ty + r * kTY;
+            const int64_t j = y0 + q * kC2 + ly;
+            if (i >= nx || j >= ny) continue;
+            const int hc = ly * kBX + tx, tc = ly * kTX + tx;
+            const float e = Ez[hc];
+            const float dEy = Ez[hc + kBX] - e;   // dEz along y (0 past the last row: TMA fill)
+            const float dEx = Ez[hc + 1] - e;     // dEz along x
+            float hxv = Hx[tc], hyv = Hy[tc];
+            if (cp.L == 0 || !(in_slab<float>(i, nx, cp.L) || in_slab<float>(j, ny, cp.L))) {
+                hxv -= ch * dEy;
+                hyv += ch * dEx;
+            } else {
+                h2d_pml<float>(cp, nx, ny, i, j, ch, cph, dEy, dEx, hxv, hyv);
+            }
+            const int64_t c = j * nx + i;
+            hx[c] = hxv;
+            hy[c] = hyv;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTT, kMinBlocks) k_e2d_tma(const __grid_constant__ Boxes2 bx, float *__restrict__ ez,
+                                                            int nx, int ny, int rows, float ce, float cpe, Cpml<float> cp,
+                                                            Source src, int *err)
+{
+    extern __shared__ __align__(128) float ring[];
+    __shared__ TmaSmemN<kS2Stages> s;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * rows;
+    const int np = (min(rows, ny - y0) + kC2 - 1) / kC2;
+    const int64_t i = x0 + tx;
+    if (quit_early(err, &s.quit)) return;
+    auto issue = [&](int p) {
+        float *st = ring + (p % kS2Stages) * kS2E;
+        uint64_t *m = &s.full[p % kS2Stages];
+        const int y = y0 + p * kC2;
+        mbar_arrive_expect_tx(m, kS2EBytes);
+        tma_load_2d(st, &bx.hx_nb, m, x0 - 4, y - 1);
+        tma_load_2d(st + kB2Pitch, &bx.hy_nb, m, x0 - 4, y - 1);
+        tma_load_2d(st + 2 * kB2Pitch, &bx.ez_t, m, x0, y);
+    };
+    if (tid == 0) {
+        for (int q = 0; q < kS2Stages; ++q) mbar_init(&s.full[q], 1);
+        fence_proxy_async_smem();
+        for (int p = 0; p < min(kS2Stages, np); ++p) issue(p);
+    }
+    const float g = src.kind ? (float)*src.val : 0.f;
+    __syncthreads();
+    for (int q = 0; q < np; ++q) {
+        if (!plane_ready<kS2Stages>(s.full, q, np, ty, err)) return;
+        if (tid == 0 && q >= 1 && q - 1 + kS2Stages < np) issue(q - 1 + kS2Stages);
+        const float *st = ring + (q % kS2Stages) * kS2E;
+        const float *Hx = st, *Hy = st + kB2Pitch, *Ezt = st + 2 * kB2Pitch;
+#pragma unroll
+        for (int r = 0; r < kR2; ++r) {
+            const int ly = ty + r * kTY;
+            const int64_t j = y0 + q * kC2 + ly;
+            if (i < 1 || j < 1 || i >= nx || j >= ny) continue;   // PEC nodes are not updated
+            const int hc = (ly + 1) * kBX + tx + 4;
+            const float dHx = Hy[hc] - Hy[hc - 1];     // dHy along x
+            const float dHy = Hx[hc] - Hx[hc - kBX];   // dHx along y
+            const float upd = cp.L == 0 || !(in_slab<float>(i, nx, cp.L) || in_slab<float>(j, ny, cp.L))
+                                  ? ce * (dHx - dHy)
+                                  : e2d_pml<float>(cp, nx, ny, i, j, ce, cpe, dHx, dHy);
+            float v = Ezt[ly * kTX + tx] + upd;
+            if (src.kind && i == src.i && j == src.j) v += g;
+            ez[j * nx + i] = v;
+        }
+    }
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -452,6 +584,19 @@ bool encode(CUtensorMap *m, float *base, int64_t nx, int64_t ny, int64_t nz, uin
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool encode2(CUtensorMap *m, float *base, int64_t nx, int64_t ny, uint32_t box_x, uint32_t box_y)
+{
+    const EncodeTiled fn = encoder();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    const cuuint64_t strides[1] = {(cuuint64_t)nx * 4};
+    const cuuint32_t box[2] = {box_x, box_y};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 struct TmaMaps {
@@ -463,6 +608,8 @@ struct TmaMaps {
     bool fused_ready;
     FusedBoxes fused[2];
     const void *fset[2][6];
+    int ndim;
+    Boxes2 b2;   // 2-D strips
 };
 
 bool tma_stencil_eligible(int64_t nx, int64_t ny, int64_t nz)
@@ -474,9 +621,31 @@ bool tma_stencil_eligible(int64_t nx, int64_t ny, int64_t nz)
 TmaMaps *tma_maps_create(float *const f[6], int64_t nx, int64_t ny, int64_t nz)
 {
     if (!tma_stencil_eligible(nx, ny, nz)) return nullptr;
+    if (nz == 1) {   // 2-D TMz: Ez, Hx, Hy
+        for (int q : {FDTD_EZ, FDTD_HX, FDTD_HY})
+            if (!f[q] || reinterpret_cast<uintptr_t>(f[q]) % 16) return nullptr;
+        TmaMaps *t = new TmaMaps{};
+        t->ndim = 2;
+        const bool ok2 = encode2(&t->b2.ez_nb, f[FDTD_EZ], nx, ny, kBX, kB2Y) &&
+                         encode2(&t->b2.hx_nb, f[FDTD_HX], nx, ny, kBX, kB2Y) &&
+                         encode2(&t->b2.hy_nb, f[FDTD_HY], nx, ny, kBX, kB2Y) &&
+                         encode2(&t->b2.ez_t, f[FDTD_EZ], nx, ny, kTX, kC2) &&
+                         encode2(&t->b2.hx_t, f[FDTD_HX], nx, ny, kTX, kC2) &&
+                         encode2(&t->b2.hy_t, f[FDTD_HY], nx, ny, kTX, kC2);
+        for (int q = 0; q < 6; ++q) t->f[q] = f[q];
+        t->nx = nx;
+        t->ny = ny;
+        t->nz = 1;
+        if (!ok2) {
+            delete t;
+            return nullptr;
+        }
+        return t;
+    }
     for (int q = 0; q < 6; ++q)
         if (!f[q] || reinterpret_cast<uintptr_t>(f[q]) % 16) return nullptr;
     TmaMaps *t = new TmaMaps{};
+    t->ndim = 3;
     bool ok = true;
     for (int c = 0; c < 3 && ok; ++c) {
         ok = encode(&t->h.nb[c], f[FDTD_EX + c], nx, ny, nz, kBX, kBY) &&
@@ -525,6 +694,8 @@ void tma_fused_forget(TmaMaps *t)
     if (t) t->fused_ready = false;
 }
 
+static inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
 bool tma_maps_match(const TmaMaps *t, float *const f[6])
 {
     if (!t) return false;
@@ -533,13 +704,29 @@ bool tma_maps_match(const TmaMaps *t, float *const f[6])
     return true;
 }
 
-static inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+void launch_h2d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, float ch, float cph,
+                    Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int rows, int *err)
+{
+    rows = (rows + kC2 - 1) / kC2 * kC2;
+    const dim3 g(cdivu(nx, kTX), cdivu(ny, rows));
+    launch_plain(k_h2d_tma, g, dim3(kTT), kSmem2H, st, t->b2, f[FDTD_HX], f[FDTD_HY], (int)nx, (int)ny, rows, ch, cph,
+               cp, src, d_step, kstep, err);
+}
+
+void launch_e2d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, float ce, float cpe,
+                    Cpml<float> cp, Source src, int rows, int *err)
+{
+    rows = (rows + kC2 - 1) / kC2 * kC2;
+    const dim3 g(cdivu(nx, kTX), cdivu(ny, rows));
+    launch_plain(k_e2d_tma, g, dim3(kTT), kSmem2E, st, t->b2, f[FDTD_EZ], (int)nx, (int)ny, rows, ce, cpe, cp, src, err);
+}
+
 
 void launch_h3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_t nx, int64_t ny, int64_t nz,
                     float ch, float cph, Cpml<float> cp, Source src, const int64_t *d_step, int kstep, int tz, int *err)
 {
     const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
-    launch_pdl(k_h3d_tma, dim3(g), dim3(kTT), kSmemBytes, st, t->h, f[FDTD_EX], f[FDTD_EY], f[FDTD_HX], f[FDTD_HY], f[FDTD_HZ], (int)nx,
+    launch_plain(k_h3d_tma, dim3(g), dim3(kTT), kSmemBytes, st, t->h, f[FDTD_EX], f[FDTD_EY], f[FDTD_HX], f[FDTD_HY], f[FDTD_HZ], (int)nx,
                                           (int)ny, (int)nz, tz, ch, cph, cp, src, d_step, kstep, err);
 }
 
@@ -559,7 +746,7 @@ bool launch_eh3d_tma(cudaStream_t st, const TmaMaps *t, float *const fin[6], flo
                                                   (int)kFSmemBytes) == cudaSuccess;
     if (!attr) return false;
     const dim3 g(cdivu(t->nx, kTX), cdivu(t->ny, kTY), cdivu(t->nz, tz));
-    launch_pdl(k_eh3d_tma, dim3(g), dim3(kTT), kFSmemBytes, st, t->fused[b], o, (int)t->nx, (int)t->ny, (int)t->nz, tz, ce, cpe, ch, cph,
+    launch_plain(k_eh3d_tma, dim3(g), dim3(kTT), kFSmemBytes, st, t->fused[b], o, (int)t->nx, (int)t->ny, (int)t->nz, tz, ce, cpe, ch, cph,
                                             cin, src, d_step, kstep, err);
     return true;
 }
@@ -568,7 +755,7 @@ void launch_e3d_tma(cudaStream_t st, const TmaMaps *t, float *const f[6], int64_
                     float ce, float cpe, Cpml<float> cp, Source src, int tz, int *err)
 {
     const dim3 g(cdivu(nx, kTX), cdivu(ny, kTY), cdivu(nz, tz));
-    launch_pdl(k_e3d_tma, dim3(g), dim3(kTT), kSmemBytes, st, t->e, f[FDTD_HX], f[FDTD_HY], f[FDTD_EX], f[FDTD_EY], f[FDTD_EZ], (int)nx,
+    launch_plain(k_e3d_tma, dim3(g), dim3(kTT), kSmemBytes, st, t->e, f[FDTD_HX], f[FDTD_HY], f[FDTD_EX], f[FDTD_EY], f[FDTD_EZ], (int)nx,
                                           (int)ny, (int)nz, tz, ce, cpe, cp, src, err);
 }
 

@@ -1,5 +1,6 @@
-"""TMA column stencils (3-D FP32): blocks of 32 x 8 threads walking tz planes
-along z, planes staged in shared memory by tensor copies.  They compute the
+"""TMA stencils (FP32): 3-D column kernels (blocks of 32 x 8 threads walking tz
+planes along z) and 2-D strip kernels (walking rows in 8-row chunks), planes /
+chunks staged in shared memory by tensor copies.  They compute the
 same cell formulas as the grid-of-cells kernels, so the fields must agree bit
 for bit on grids with ragged tiles on every axis (partial 32-cell rows, partial
 8-row tiles, a last block with fewer than tz planes), with and without CPML,
@@ -102,9 +103,10 @@ def test_tma_option_errors():
     s3 = Solver.from_spec(_spec(1))
     s2 = Solver.from_spec(spec_2d_cylinder(n=64, ny=32, R=8, nv=4, nv_perp=4, steps=1, precision="f32",
                                            f_dtype="f32"))
-    for solver, v in ((s, 8), (s2, 8), (s3, -1), (s3, 2000)):
+    for solver, v in ((s, 8), (s3, -1), (s3, 2000)):
         with pytest.raises(FdtdError):
             solver.set_option("stencil_tz", v)
+    s2.set_option("stencil_tz", 16)          # 2-D FP32 with nx a multiple of 4: the TMA strips
     s3.set_option("stencil_tz", 8)
     s3.set_option("stencil_tz", 0)
     assert s3.launch_shapes()["stencil_tz"] == 0
@@ -160,4 +162,41 @@ def test_fused_tma_matches_oracle(oracle_lib):
     sim.step(260)
     errs = compare(s, sim, 3)
     print("fused TMA pass 3-D f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
+
+
+# ------------------------------------------------------------ 2-D TMz strips
+# 148 x 70 cells: x a multiple of 4 but not of 32 (a partial strip), y not a multiple of 8 (a partial chunk).
+
+def _spec2(steps, n=(148, 70), cpml=8, src=(40, 35)):
+    from fdtd_inputs import spec_2d_cylinder
+    nx, ny = n
+    return spec_2d_cylinder(n=nx, ny=ny, cpml=cpml, R=min(nx, ny) // 4, center=(0.6 * nx, 0.5 * ny), src=src,
+                            nv=8, nv_perp=8, steps=steps, precision="f32", f_dtype="f32", seed=33)
+
+
+@pytest.mark.parametrize("rows,src", [(8, (40, 35)), (24, (64, 48)), (64, (147, 69))])
+def test_tma_2d_equals_cells(rows, src):
+    spec = _spec2(45, cpml=0 if src == (147, 69) else 8, src=src)
+    tma, cells = _pair(spec, rows, (7, 38))
+    worst = 0.0
+    for q in FIELDS[2] + ["j", "df"]:
+        a, b = tma.read(q, device=False), cells.read(q, device=False)
+        d = np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+        worst = max(worst, d)
+    print(f"2-D TMA rows={rows} vs grid-of-cells: max |diff| / max |value| = {worst:.2e}")
+    assert worst <= 1e-6
+
+
+def test_tma_2d_matches_oracle(oracle_lib):
+    spec = _spec2(260)
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec)
+    s.set_option("stencil_tz", 32)
+    s.step(100)
+    s.step(160)
+    sim = oracle_sim(oracle_lib, spec)
+    sim.step(260)
+    errs = compare(s, sim, 2)
+    print("TMA strips 2-D f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
     assert max(errs.values()) <= 1e-4, errs
