@@ -216,26 +216,45 @@ __global__ void __launch_bounds__(256) k_kinetic_f0(KinArgs<T> a, F0Args<T> f)
     V *gv = reinterpret_cast<V *>(f.g);
     const int vpr = P / VEC;
 
+    // Software pipeline: the next row's vectors, E and density are loaded while this row is
+    // updated (two rows of loads in flight per lane), its cell index one further row ahead so the
+    // E gather does not wait on it.  Rows have distinct cells: reading the next row's E before this
+    // row's E store is safe.
+    const int64_t stride = nw * R;
+    auto fetch = [&](int64_t r, int32_t c, V &xv, V &gw, T &Ev, T &nv) {
+        if (r < a.nslots) {
+            const int64_t i = r * vpr + l;
+            xv = __ldcs(df + i);
+            gw = __ldcs(gv + i);
+            Ev = a.E[c];
+            nv = __ldg(a.dens + r);
+        }
+    };
     int64_t row = wg * R + sub;
-    int32_t cell_next = row < a.nslots ? __ldg(a.slot_cell + row) : 0;
-    for (int64_t base = wg * R; base < a.nslots; base += nw * R) {
+    int32_t cell = row < a.nslots ? __ldg(a.slot_cell + row) : 0;
+    int32_t cell_next = row + stride < a.nslots ? __ldg(a.slot_cell + row + stride) : 0;
+    V xv{}, gw{};
+    T Ev = T(0), nv = T(1);
+    fetch(row, cell, xv, gw, Ev, nv);
+    for (int64_t base = wg * R; base < a.nslots; base += stride) {
         row = base + sub;
         const bool valid = row < a.nslots;
-        const int32_t cell = cell_next;
         const int64_t ri = (valid ? row : 0) * vpr + l;
         T x[VEC], g[VEC];
-        T E = T(0), n = T(1);
+        const T E = valid ? Ev : T(0), n = valid ? nv : T(1);
         if (valid) {
-            unpack(__ldcs(df + ri), x);
-            unpack(__ldcs(gv + ri), g);
-            E = a.E[cell];
-            n = __ldg(a.dens + row);
+            unpack(xv, x);
+            unpack(gw, g);
         } else {
 #pragma unroll
             for (int t = 0; t < VEC; ++t) x[t] = g[t] = T(0);
         }
-        const int64_t row_next = row + nw * R;
-        cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
+        const int32_t cell_cur = cell;
+        // the next row in flight during this row's update
+        const int64_t row_next = row + stride;
+        fetch(row_next, cell_next, xv, gw, Ev, nv);
+        cell = cell_next;
+        cell_next = row_next + stride < a.nslots ? __ldg(a.slot_cell + row_next + stride) : 0;
         // g one node to the left / right of the lane's vector
         T gl = __shfl_up_sync(0xffffffffu, g[VEC - 1], 1, L);
         T gr = __shfl_down_sync(0xffffffffu, g[0], 1, L);
@@ -301,7 +320,7 @@ __global__ void __launch_bounds__(256) k_kinetic_f0(KinArgs<T> a, F0Args<T> f)
             Store<T>::st(gv + ri, gn, uint4{}, uint2{});
             if (l == 0) {
                 a.jslot[row] = J;
-                a.E[cell] = E - a.cj * J;
+                a.E[cell_cur] = E - a.cj * J;
             }
         }
     }
