@@ -193,8 +193,9 @@ void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], flo
                  int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
                  const int64_t *d_step, int kstep);
 void launch_advance(cudaStream_t st, int64_t *d_step, int64_t by);
-// 3-D FP32 curl stencils fed by TMA (32 x 8 columns walking tz planes along z); the tensor maps
-// describe one field set (nx a multiple of 4); timeouts of their bounded waits set bit 2 of *err
+// FP32 curl stencils fed by TMA (3-D: 32 x 8 columns walking tz planes along z; 2-D: 32-cell strips
+// walking rows in 16-row chunks); the tensor maps describe one field set (nx a multiple of 4; maps made
+// with nz == 1 are 2-D); timeouts of their bounded waits set bit 2 of *err
 struct TmaMaps;
 bool tma_stencil_eligible(int64_t nx, int64_t ny, int64_t nz);
 TmaMaps *tma_maps_create(float *const f[6], int64_t nx, int64_t ny, int64_t nz);   // nullptr if not possible
