@@ -531,6 +531,7 @@ def batch_bench(args, specs, rank, world, local):
     import torch.distributed as dist
     from paper_2211_05647_gb300 import Batch
     b = Batch(specs, device=local)
+    tune = None if args.no_autotune else b.autotune()   # untimed: row shape of the persistent kernel
     info = b.info()
     cells, nodes = info["cells"], info["nodes"]
     st = b.stream
@@ -587,6 +588,7 @@ def batch_bench(args, specs, rank, world, local):
             "vs_baseline": None, "dtype": "f32" if eb == 4 else "f64", "data": "synthetic (seeded run sizes, slabs, densities)",
             "config": {"workload": args.workload, "runs": len(specs), "cells": cells, "phase_space_nodes": nodes,
                        "f_dtype": fdt, "clusters": info["clusters"], "ctas_per_cluster": info["cluster_ctas"], "steps_per_launch": chunk,
+                       "row_shape": tune,
                        "l2": "inputs larger than L2 (delta f %.2f GB)" % (nodes * fb / 1e9),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "phase_space_updates_per_s": job_rate(nodes * args.steps, world, ms / 1e3),

@@ -436,6 +436,15 @@ int fdtd_batch_write(fdtd_batch_t b, int32_t run, int which, const void *src, si
 size_t fdtd_batch_quantity_bytes(fdtd_batch_t b, int32_t run, int which);
 /* dt, steps done, total cells, total phase-space nodes, clusters launched and
  * CTAs per cluster (any pointer may be NULL). */
+/* Row-shape autotuner of the batched kernel (no counterpart in the paper):
+ * times a few steps of every candidate shape for the batch's row length
+ * (vectors per lane x lanes per row; FP32 and BF16 rows have two or three,
+ * FP64 rows one) on the batch's own buffers, keeps the fastest (a later
+ * candidate must be more than 1 % faster than the built-in first one) and
+ * restores the state bit for bit (needs one temporary copy of it on the
+ * device).  The cluster packing stays as created.  Synchronous; outputs
+ * (host, each may be NULL): the shape kept and its time per step in ms. */
+int fdtd_batch_autotune(fdtd_batch_t b, int32_t *vpl, int32_t *lanes, double *ms_per_step);
 int fdtd_batch_info(fdtd_batch_t b, double *dt, int64_t *steps, int64_t *cells, int64_t *nodes, int32_t *nclusters,
                     int32_t *cluster_ctas);
 const char *fdtd_batch_last_error(fdtd_batch_t b);

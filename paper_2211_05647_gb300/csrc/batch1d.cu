@@ -32,6 +32,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kinetic_row.cuh"
@@ -326,6 +327,13 @@ struct fdtd_batch {
     std::map<int64_t, cudaGraphExec_t> graphs;
     std::string err;
     cudaError_t (*launch)(fdtd_batch *, cudaStream_t, int);
+    // row-shape candidates (vectors per lane, lanes per row) for this row length; [0] is the default
+    struct Shape {
+        int vpl, l;
+        cudaError_t (*launch)(fdtd_batch *, cudaStream_t, int);
+    };
+    std::vector<Shape> shapes;
+    int shape;
 };
 
 namespace {
@@ -416,21 +424,60 @@ int max_clusters(int ctas)
     return n;
 }
 
-// pick the kernel instance for (storage, precision, vectors per row)
-template <typename TS, typename T>
-bool pick(int V, cudaError_t (**fn)(fdtd_batch *, cudaStream_t, int), int (**maxc)(int))
+// Row-shape candidates (storage, precision, vectors per row): the first is the built-in choice and
+// fixes the cluster packing; fdtd_batch_autotune may switch to another (two vectors a lane, twice the
+// lanes: eight vectors a lane spill at the kernel's 128 registers).  The FP64 validation instantiation
+// keeps the built-in shape only.
+template <typename TS, typename T, int VPL, int L>
+fdtd_batch::Shape shape_of()
 {
+    return fdtd_batch::Shape{VPL, L, launch_t<TS, T, VPL, L>};
+}
+
+template <typename TS, typename T>
+bool pick(int V, std::vector<fdtd_batch::Shape> &sh, int (**maxc)(int))
+{
+    sh.clear();
+    constexpr bool more = !std::is_same<T, double>::value;
     switch (V) {
-    case 1: *fn = launch_t<TS, T, 1, 1>; *maxc = max_clusters<TS, T, 1, 1>; return true;
-    case 2: *fn = launch_t<TS, T, 2, 1>; *maxc = max_clusters<TS, T, 2, 1>; return true;
-    case 4: *fn = launch_t<TS, T, 4, 1>; *maxc = max_clusters<TS, T, 4, 1>; return true;
-    case 8: *fn = launch_t<TS, T, 4, 2>; *maxc = max_clusters<TS, T, 4, 2>; return true;
-    case 16: *fn = launch_t<TS, T, 4, 4>; *maxc = max_clusters<TS, T, 4, 4>; return true;
-    case 32: *fn = launch_t<TS, T, 4, 8>; *maxc = max_clusters<TS, T, 4, 8>; return true;
-    case 64: *fn = launch_t<TS, T, 4, 16>; *maxc = max_clusters<TS, T, 4, 16>; return true;
-    case 128: *fn = launch_t<TS, T, 4, 32>; *maxc = max_clusters<TS, T, 4, 32>; return true;
+    case 1: sh = {shape_of<TS, T, 1, 1>()}; *maxc = max_clusters<TS, T, 1, 1>; break;
+    case 2:
+        sh = {shape_of<TS, T, 2, 1>()};
+        if constexpr (more) sh.push_back(shape_of<TS, T, 1, 2>());
+        *maxc = max_clusters<TS, T, 2, 1>;
+        break;
+    case 4:
+        sh = {shape_of<TS, T, 4, 1>()};
+        if constexpr (more) sh.push_back(shape_of<TS, T, 2, 2>());
+        *maxc = max_clusters<TS, T, 4, 1>;
+        break;
+    case 8:
+        sh = {shape_of<TS, T, 4, 2>()};
+        if constexpr (more) sh.push_back(shape_of<TS, T, 2, 4>());
+        *maxc = max_clusters<TS, T, 4, 2>;
+        break;
+    case 16:
+        sh = {shape_of<TS, T, 4, 4>()};
+        if constexpr (more) sh.push_back(shape_of<TS, T, 2, 8>());
+        *maxc = max_clusters<TS, T, 4, 4>;
+        break;
+    case 32:
+        sh = {shape_of<TS, T, 4, 8>()};
+        if constexpr (more) sh.push_back(shape_of<TS, T, 2, 16>());
+        *maxc = max_clusters<TS, T, 4, 8>;
+        break;
+    case 64:
+        sh = {shape_of<TS, T, 4, 16>()};
+        if constexpr (more) sh.push_back(shape_of<TS, T, 2, 32>());
+        *maxc = max_clusters<TS, T, 4, 16>;
+        break;
+    case 128:
+        sh = {shape_of<TS, T, 4, 32>()};
+        *maxc = max_clusters<TS, T, 4, 32>;
+        break;
     default: return false;
     }
+    return true;
 }
 
 void destroy_batch(fdtd_batch *b)
@@ -512,10 +559,12 @@ int fdtd_batch_create(const fdtd_run_desc *runs, int32_t nruns, const fdtd_runti
     const int vec = p0.f_dtype == FDTD_DF_BF16 ? 8 : (p0.f_dtype == FDTD_DF_F64 ? 2 : 4);
     const int V = b->pitch / vec;
     int (*maxc_of)(int) = nullptr;
-    bool ok = p0.f_dtype == FDTD_DF_F32    ? pick<float, float>(V, &b->launch, &maxc_of)
-              : p0.f_dtype == FDTD_DF_BF16 ? pick<__nv_bfloat16, float>(V, &b->launch, &maxc_of)
-                                           : pick<double, double>(V, &b->launch, &maxc_of);
+    bool ok = p0.f_dtype == FDTD_DF_F32    ? pick<float, float>(V, b->shapes, &maxc_of)
+              : p0.f_dtype == FDTD_DF_BF16 ? pick<__nv_bfloat16, float>(V, b->shapes, &maxc_of)
+                                           : pick<double, double>(V, b->shapes, &maxc_of);
     if (!ok) return bail(FDTD_ERR_INVAL, "too many velocity nodes for the batched kernel (at most 128 vectors)");
+    b->shape = 0;
+    b->launch = b->shapes[0].launch;
     int maxc_c[4];
     const int csizes[4] = {8, 4, 2, 1};
     bool any = false;
@@ -800,6 +849,65 @@ int fdtd_batch_write(fdtd_batch_t b, int32_t run, int which, const void *src, si
                                     b->stream);
     if (e == cudaSuccess && !src_is_device) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "write: %s", cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
+int fdtd_batch_autotune(fdtd_batch_t b, int32_t *vpl, int32_t *lanes, double *ms_per_step)
+{
+    if (!b) return FDTD_ERR_INVAL;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, FDTD_ERR_CUDA, "autotune: stream");
+    // save the state the timed steps change, restore it afterwards
+    const int64_t nrow = std::max<int64_t>(b->nrows, 1);
+    const size_t nE = b->ncell_e * b->esz, nH = b->ncell_h * b->esz, nM = 2 * (size_t)b->nruns * b->esz;
+    const size_t nD = (size_t)nrow * b->pitch * b->df_esz, nJ = (size_t)nrow * b->esz, nS = 16;
+    const size_t sizes[6] = {nE, nH, nM, nD, nJ, nS};
+    void *live[6] = {b->E, b->H, b->mur, b->df, b->jslot, b->d_step};
+    void *saved[6] = {};
+    bool ok = true;
+    for (int i = 0; i < 6 && ok; ++i) ok = (saved[i] = balloc(b, sizes[i])) != nullptr;
+    auto release = [&]() {
+        for (int i = 0; i < 6; ++i) bfree(b, saved[i]);
+    };
+    if (!ok) {
+        release();
+        return bfail(b, FDTD_ERR_NOMEM, "autotune: no room for a copy of the state");
+    }
+    for (int i = 0; i < 6 && ok; ++i)
+        ok = cudaMemcpyAsync(saved[i], live[i], sizes[i], cudaMemcpyDeviceToDevice, b->stream) == cudaSuccess;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    constexpr int kSteps = 20;
+    double best = 1e30;
+    int best_i = b->shape;
+    for (int c = 0; c < (int)b->shapes.size() && ok; ++c) {
+        auto fn = b->shapes[c].launch;
+        ok = fn(b, b->stream, 2) == cudaSuccess;   // warm-up
+        ok = ok && cudaEventRecord(e0, b->stream) == cudaSuccess && fn(b, b->stream, kSteps) == cudaSuccess &&
+             cudaEventRecord(e1, b->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0;
+        if (ok) cudaEventElapsedTime(&ms, e0, e1);
+        // a later candidate replaces the best only when more than 1 % faster
+        if (ok && ms / kSteps < best * 0.99) {
+            best = ms / kSteps;
+            best_i = c;
+        }
+    }
+    for (int i = 0; i < 6 && ok; ++i)
+        ok = cudaMemcpyAsync(live[i], saved[i], sizes[i], cudaMemcpyDeviceToDevice, b->stream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(b->stream) == cudaSuccess;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    release();
+    if (!ok) return bfail(b, FDTD_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+    if (best_i != b->shape) {
+        for (auto &g : b->graphs) cudaGraphExecDestroy(g.second);
+        b->graphs.clear();
+        b->shape = best_i;
+        b->launch = b->shapes[best_i].launch;
+    }
+    if (vpl) *vpl = b->shapes[b->shape].vpl;
+    if (lanes) *lanes = b->shapes[b->shape].l;
+    if (ms_per_step) *ms_per_step = best;
     return FDTD_OK;
 }
 

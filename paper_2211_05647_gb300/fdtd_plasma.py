@@ -171,6 +171,8 @@ SIGNATURES = {
     "fdtd_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "fdtd_batch_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                        ctypes.c_int]),
+    "fdtd_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_double)]),
     "fdtd_batch_write": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                                          ctypes.c_int]),
     "fdtd_batch_quantity_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int]),
@@ -428,6 +430,12 @@ class Batch:
         if nb:
             self._check(self.lib.fdtd_batch_read(self.h, int(run), q, out.data_ptr(), nb, 0))
         return out.float().numpy() if dt == torch.bfloat16 else out.numpy()
+
+    def autotune(self) -> dict:
+        """Time the row-shape candidates on this batch's buffers and keep the fastest (state restored)."""
+        vpl, lanes, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+        self._check(self.lib.fdtd_batch_autotune(self.h, ctypes.byref(vpl), ctypes.byref(lanes), ctypes.byref(ms)))
+        return {"vpl": vpl.value, "lanes": lanes.value, "ms_per_step": ms.value}
 
     def write(self, run: int, name: str, values):
         """Overwrite a field (ex: nz+1 values, hy: nz) of one run from host values."""

@@ -97,3 +97,30 @@ def test_batch_rejects_mixed_grids():
     specs[1]["grid"]["dx"] *= 1.5
     with pytest.raises(FdtdError):
         Batch(specs)
+
+
+def test_batch_autotune_restores_state_and_keeps_results(oracle_lib):
+    """The row-shape tuner times its candidates on the batch's buffers and
+    restores the state bit for bit; stepping on with the shape it kept still
+    matches the FP64 oracle."""
+    from paper_2211_05647_gb300 import Batch
+    specs = _mixed_runs("f32", "f32")
+    for s in specs:
+        s["plasma"]["nu_model"] = specs[0]["plasma"]["nu_model"]
+    b = Batch(specs)
+    b.step(300)
+    before = [(b.read(r, "ex"), b.read(r, "hy"), b.read(r, "j"), b.read(r, "df")) for r in range(len(specs))]
+    t = b.autotune()
+    print(f"batch row shape kept: {t}")
+    assert t["vpl"] * t["lanes"] >= 1 and t["ms_per_step"] > 0
+    for r in range(len(specs)):
+        after = (b.read(r, "ex"), b.read(r, "hy"), b.read(r, "j"), b.read(r, "df"))
+        for x, y in zip(before[r], after):
+            assert np.array_equal(x, y), r
+    assert b.info()["steps"] == 300
+    b.step(600)
+    for r, sp in enumerate(specs):
+        sim = oracle_sim(oracle_lib, sp)
+        sim.step(900)
+        e = np.linalg.norm(b.read(r, "ex") - sim.get("ex")) / np.linalg.norm(sim.get("ex"))
+        assert e <= 1e-4, (r, e)
