@@ -244,6 +244,47 @@ struct MlpTcSmem4 {
 
 __device__ __forceinline__ void wg_bar(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
+// Two-lane FP32 arithmetic (add / mul / fma .f32x2 on a register pair): each
+// lane rounds exactly as the scalar instruction does, at one issue slot for
+// two activations.
+__device__ __forceinline__ uint64_t f2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2_split(uint64_t r)
+{
+    float2 o;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+    return o;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+// gelu2_f on two activations, lane by lane the same roundings: z z, the polynomial, u = z p, tanh, z t + z
+__device__ __forceinline__ float2 gelu2_f2(uint64_t z)
+{
+    const uint64_t u = f2_mul(z, f2_fma(f2(kGeluCA, kGeluCA), f2_mul(z, z), f2(kGeluC, kGeluC)));
+    const float2 uu = f2_split(u);
+    return f2_split(f2_fma(z, f2(tanh_fast(uu.x), tanh_fast(uu.y)), z));
+}
+
 // The epilogues form 2 gelu(z) = z + z tanh(u) (one multiply fewer than gelu); W2 and w3 are stored at
 // half scale to compensate.  Both scalings are by a power of two, so the BF16 operands and every product
 // equal those of the unscaled form exactly.
@@ -344,11 +385,15 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
             const int k0 = c * 32 + q * 8;
             const float4 ba = *reinterpret_cast<const float4 *>(&w.b1[k0]);
             const float4 bb = *reinterpret_cast<const float4 *>(&w.b1[k0 + 4]);
+            const float2 g0 = gelu2_f2(f2_add(f2(v[q * 8 + 0], v[q * 8 + 1]), f2(ba.x, ba.y)));
+            const float2 g1 = gelu2_f2(f2_add(f2(v[q * 8 + 2], v[q * 8 + 3]), f2(ba.z, ba.w)));
+            const float2 g2 = gelu2_f2(f2_add(f2(v[q * 8 + 4], v[q * 8 + 5]), f2(bb.x, bb.y)));
+            const float2 g3 = gelu2_f2(f2_add(f2(v[q * 8 + 6], v[q * 8 + 7]), f2(bb.z, bb.w)));
             uint4 pk;
-            pk.x = pack_bf16(gelu2_f(v[q * 8 + 0] + ba.x), gelu2_f(v[q * 8 + 1] + ba.y));
-            pk.y = pack_bf16(gelu2_f(v[q * 8 + 2] + ba.z), gelu2_f(v[q * 8 + 3] + ba.w));
-            pk.z = pack_bf16(gelu2_f(v[q * 8 + 4] + bb.x), gelu2_f(v[q * 8 + 5] + bb.y));
-            pk.w = pack_bf16(gelu2_f(v[q * 8 + 6] + bb.z), gelu2_f(v[q * 8 + 7] + bb.w));
+            pk.x = pack_bf16(g0.x, g0.y);
+            pk.y = pack_bf16(g1.x, g1.y);
+            pk.z = pack_bf16(g2.x, g2.y);
+            pk.w = pack_bf16(g3.x, g3.y);
             *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
         }
     }
@@ -376,10 +421,12 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
         for (int i = 0; i < 32; i += 4) {
             const float4 b = *reinterpret_cast<const float4 *>(&w.b2[c * 32 + i]);
             const float4 o = *reinterpret_cast<const float4 *>(&w.w3[c * 32 + i]);
-            y = fmaf(gelu2_f(v[i + 0] + b.x), o.x, y);
-            y = fmaf(gelu2_f(v[i + 1] + b.y), o.y, y);
-            y = fmaf(gelu2_f(v[i + 2] + b.z), o.z, y);
-            y = fmaf(gelu2_f(v[i + 3] + b.w), o.w, y);
+            const float2 g0 = gelu2_f2(f2_add(f2(v[i + 0], v[i + 1]), f2(b.x, b.y)));
+            const float2 g1 = gelu2_f2(f2_add(f2(v[i + 2], v[i + 3]), f2(b.z, b.w)));
+            y = fmaf(g0.x, o.x, y);
+            y = fmaf(g0.y, o.y, y);
+            y = fmaf(g1.x, o.z, y);
+            y = fmaf(g1.y, o.w, y);
         }
     }
     tc_fence_before();
