@@ -92,6 +92,11 @@ struct Store<double> {
         __stcs(p, make_double2(x[0], x[1]));
     }
 };
+// BF16 storage: one Philox4x32-7 call per 8 nodes (16 bits a node).  A vector
+// whose 8 values sum to a finite number holds no infinity or NaN, so each value
+// takes the plain rule (add the draw, keep the high half; two halves packed by
+// one byte permute); otherwise (or if the sum overflows) every value goes
+// through f32_to_bf16_sr, which keeps infinities and NaNs.
 template <>
 struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(uint4 *p, const float *x, uint4 ctr, uint2 key)
@@ -99,11 +104,19 @@ struct Store<__nv_bfloat16> {
         const uint4 r = philox4x32_7(ctr, key);
         const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
         uint32_t w[4];
+        const float2 h = f2_split(f2_add(f2_add(f2(x[0], x[1]), f2(x[2], x[3])), f2_add(f2(x[4], x[5]), f2(x[6], x[7]))));
+        if (fabsf(h.x + h.y) < INFINITY) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t lo = f32_to_bf16_sr(x[2 * q], rr[q] & 0xffffu);
-            uint32_t hi = f32_to_bf16_sr(x[2 * q + 1], rr[q] >> 16);
-            w[q] = lo | (hi << 16);
+            for (int q = 0; q < 4; ++q)
+                w[q] = __byte_perm(__float_as_uint(x[2 * q]) + (rr[q] & 0xffffu),
+                                   __float_as_uint(x[2 * q + 1]) + (rr[q] >> 16), 0x7632);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t lo = f32_to_bf16_sr(x[2 * q], rr[q] & 0xffffu);
+                const uint32_t hi = f32_to_bf16_sr(x[2 * q + 1], rr[q] >> 16);
+                w[q] = lo | (hi << 16);
+            }
         }
         __stcs(p, make_uint4(w[0], w[1], w[2], w[3]));
     }
@@ -114,35 +127,59 @@ struct Store<__nv_bfloat16> {
 // lane's partial sum of w' df in (s, c): compensated (TwoSum) for FP32 / FP64
 // rows; for BF16 rows a plain FP32 accumulation, whose rounding (~1e-6 of the
 // sum for a row of <= 1024 nodes) is far below the 2^-8 storage rounding of the
-// terms, and which takes a fifth of the row's instructions.
+// terms, and which takes a fifth of the row's instructions.  BF16 rows run on
+// the two-lane FP32 instructions: node pairs (2t, 2t+1) get alpha df + (beta nE)
+// with the roundings of the scalar fma, and the sum is kept as two partial sums
+// (even and odd nodes) added at the end.
 template <typename TS, typename TA, int VPL, int L>
 __device__ __forceinline__ void row_update(typename Vec<TS>::type *rp, const typename Vec<TS>::type *v,
                                            const TA *al_tab, const TA *be_tab, const TA *w_tab, TA nE, int l,
                                            uint32_t row_id, int64_t step, uint2 key, TA &s, TA &c)
 {
     constexpr int VEC = Vec<TS>::n;
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+        uint64_t s2 = f2(0.0f, 0.0f);
+        const uint64_t ne2 = f2(nE, nE);
 #pragma unroll
-    for (int q = 0; q < VPL; ++q) {
-        const int vi = q * L + l;
-        TA x[VEC], al[VEC], be[VEC], w[VEC];
-        unpack(v[q], x);
-        lds<VEC>(al_tab + vi * VEC, al);
-        lds<VEC>(be_tab + vi * VEC, be);
-        lds<VEC>(w_tab + vi * VEC, w);
+        for (int q = 0; q < VPL; ++q) {
+            const int vi = q * L + l;
+            float x[VEC], al[VEC], be[VEC], w[VEC];
+            unpack(v[q], x);
+            lds<VEC>(al_tab + vi * VEC, al);
+            lds<VEC>(be_tab + vi * VEC, be);
+            lds<VEC>(w_tab + vi * VEC, w);
 #pragma unroll
-        for (int t = 0; t < VEC; ++t) {
-            x[t] = al[t] * x[t] + be[t] * nE;
-            if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
-                s = fmaf(w[t], x[t], s);
-            } else {
+            for (int t = 0; t < VEC; t += 2) {
+                const uint64_t xn = f2_fma(f2(al[t], al[t + 1]), f2(x[t], x[t + 1]), f2_mul(f2(be[t], be[t + 1]), ne2));
+                s2 = f2_fma(f2(w[t], w[t + 1]), xn, s2);
+                const float2 xs = f2_split(xn);
+                x[t] = xs.x;
+                x[t + 1] = xs.y;
+            }
+            const uint4 ctr = make_uint4(row_id, (uint32_t)vi, (uint32_t)step, (uint32_t)(step >> 32));
+            Store<TS>::st(rp + vi, x, ctr, key);
+        }
+        const float2 ss = f2_split(s2);
+        s += ss.x + ss.y;
+    } else {
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) {
+            const int vi = q * L + l;
+            TA x[VEC], al[VEC], be[VEC], w[VEC];
+            unpack(v[q], x);
+            lds<VEC>(al_tab + vi * VEC, al);
+            lds<VEC>(be_tab + vi * VEC, be);
+            lds<VEC>(w_tab + vi * VEC, w);
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) {
+                x[t] = al[t] * x[t] + be[t] * nE;
                 TA hi, lo;
                 two_sum(s, mul_rn(w[t], x[t]), hi, lo);
                 s = hi;
                 c += lo;
             }
+            Store<TS>::st(rp + vi, x, uint4{}, uint2{});
         }
-        const uint4 ctr = make_uint4(row_id, (uint32_t)vi, (uint32_t)step, (uint32_t)(step >> 32));
-        Store<TS>::st(rp + vi, x, ctr, key);
     }
 }
 
