@@ -324,6 +324,9 @@ def test_abi_errors():
     assert e.value.code == F.FDTD_ERR_UNSTABLE
     with pytest.raises(FdtdError):
         s.set_source(kind="gauss", k=0, tau=1e-10)            # Mur node is not a source node
+    for bad in (dict(amp=float("nan")), dict(fc=float("inf")), dict(t0=float("nan")), dict(tau=0.0)):
+        with pytest.raises(FdtdError):
+            s.set_source(**dict(dict(kind="gauss_sine", k=10, tau=1e-10, fc=1e10, t0=4e-10), **bad))
     s.set_plasma(np.full(101, 1e17), f_dtype="f32")
     s.step(3)
     with pytest.raises(FdtdError) as e:
