@@ -41,7 +41,7 @@ namespace cg = cooperative_groups;
 
 namespace fp {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 256;
 
 struct BRun {
     int64_t e_off, h_off, row_off;    // offsets into E_all, H_all and the slot arrays
@@ -116,7 +116,7 @@ __device__ __forceinline__ void st_quad(T *p, const Quad<T> &q)
 }
 
 template <typename TS, typename T, int VPL, int L>
-__global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
 {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch1d(BatchArgs<T> a)
             __syncthreads();
             // software pipeline: the next row's node index, delta-f vectors, E and
             // density are loaded before the current row is updated, so a lane
-            // keeps two rows of loads in flight (one 512-thread CTA per SM leaves
-            // the registers for it).  Rows of a segment have distinct nodes, so
+            // keeps two rows of loads in flight (128 registers a thread, two
+            // 256-thread CTAs per SM).  Rows of a segment have distinct nodes, so
             // reading the next row's E ahead of this row's E store is safe.
             const int stride = nwarps * R;
             struct RowIn {
