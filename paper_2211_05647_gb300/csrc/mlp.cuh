@@ -1,6 +1,6 @@
 // mlp.cuh -- the closure network's forward tile on the tensor cores.
 //
-// Network: x[17] -> 128 -> 128 -> 1, GELU (exact erf form) after both hidden
+// Network: x[17] -> 128 -> 128 -> 1, GELU (tanh form, see gelu_f below) after both hidden
 // layers.  Parameters are FP32 "master" values packed as
 //   W1[17][128] b1[128] W2[128][128] b2[128] W3[128] b3[1]   (18945 floats);
 // the tile converts the weights to BF16 once per CTA and keeps them in shared

@@ -3,7 +3,8 @@
 Each test checks the oracle against something other than itself: exact
 discrete eigenmodes of a PEC cavity, the discrete energy invariant, the
 paper's vacuum Gaussian-pulse convergence order and a brute-force
-oversized-domain run for the CPML.
+oversized-domain run for the CPML, and the closed-form reflection of a
+PEC-backed graded PML for the CPML profiles.
 """
 import json
 import os
@@ -231,3 +232,91 @@ def test_cpml_profile_shape(oracle_lib):
     # symmetry of the two layers
     h = O.cpml_profile(p, dt, 60, True)
     assert np.allclose(h["b"][:10], h["b"][::-1][:10])
+
+
+# ------------------------------------------- CPML reflection (Eq. 9-12, P-k)
+
+def _cpml_line(O, n, L, dx, sigma_factor, kappa_max, alpha_max, src, probe, steps, fc):
+    """1-D line of the oracle's CPML profiles (or_cpml_profile at E and H
+    positions, PEC behind both layers), stepped with the textbook CPML
+    recursion psi <- b psi + a dF, curl term dF / (kappa dx) + psi; returns E
+    at `probe` after each step.  Only the profile values come from the oracle."""
+    p = O.params(ndim=2, nx=n, ny=n, dx=dx, cpml=L, cpml_sigma_factor=sigma_factor, cpml_kappa_max=kappa_max,
+                 cpml_alpha_min=0.0, cpml_alpha_max=alpha_max)
+    dt = 0.5 * dx / C0
+    pe, ph = O.cpml_profile(p, dt, n, False), O.cpml_profile(p, dt, n, True)
+    ez, hy = np.zeros(n + 1), np.zeros(n)
+    pse, psh = np.zeros(n - 1), np.zeros(n)
+    be, ae, ke = pe["b"][1:n], pe["a"][1:n], pe["kappa"][1:n]
+    tau, t0 = 1.0 / fc, 4.0 / fc
+    rec = np.zeros(steps)
+    for s in range(steps):
+        dE = ez[1:] - ez[:-1]
+        psh = ph["b"] * psh + ph["a"] * dE
+        hy += dt / (MU0 * dx) * dE / ph["kappa"] + dt / MU0 * psh
+        dH = hy[1:] - hy[:-1]
+        pse = be * pse + ae * dH
+        ez[1:n] += dt / (EPS0 * dx) * dH / ke + dt / EPS0 * pse
+        t = (s + 1) * dt
+        ez[src] += np.sin(2 * np.pi * fc * (t - t0)) * np.exp(-((t - t0) / tau) ** 2)
+        rec[s] = ez[probe]
+    return rec, dt
+
+
+def _cpml_reflection(O, sigma_factor, kappa_max, alpha_max):
+    """Measured normal-incidence reflection R(f) of a PEC-backed L-cell layer,
+    referred to the bare PEC at the same depth (sigma = 0, kappa = 1), with the
+    incident wave removed by an unbounded reference line."""
+    dx, L, lam = 5e-3, 40, 200
+    fc = C0 / (lam * dx)
+    n, steps = 1200, 4000
+    src, probe = n - L - 200, n - L - 150
+    big = 6000
+    ref, dt = _cpml_line(O, big, 0, dx, 0.0, 1.0, 0.0, big // 2, big // 2 + probe - src, steps, fc)
+    pec, _ = _cpml_line(O, n, L, dx, 0.0, 1.0, 0.0, src, probe, steps, fc)
+    lay, _ = _cpml_line(O, n, L, dx, sigma_factor, kappa_max, alpha_max, src, probe, steps, fc)
+    nfft = 16384
+    f = np.fft.rfftfreq(nfft, dt)
+    band = (f > 0.5 * fc) & (f < 1.6 * fc)
+    R = np.fft.rfft(lay - ref, nfft)[band] / np.fft.rfft(pec - ref, nfft)[band]
+    return f[band], R, L * dx, dx
+
+
+def test_cpml_sigma_max_attenuation(oracle_lib):
+    """Weak graded layer, kappa = 1, alpha = 0: a PEC-backed PML returns the
+    wave attenuated by exp(-2 int_0^delta sigma(rho) d rho / (eps0 c)) =
+    exp(-2 sigma_max delta / ((n+1) eps0 c)) at every frequency, with sigma_max
+    of Eq. 11.  A wrong constant in Eq. 11 (120 pi for 150 pi, a missing n + 1,
+    delta for the cell size) moves the exponent by 25 % or more."""
+    O = oracle_lib
+    sf, order = 0.0125, 3.0
+    f, R, delta, dx = _cpml_reflection(O, sf, 1.0, 0.0)
+    sigma_max = sf * (order + 1) / (150 * np.pi * dx)
+    expo = -2 * sigma_max * delta / ((order + 1) * EPS0 * C0)
+    ratio = np.log(np.abs(R)) / expo
+    assert np.abs(ratio - 1).max() < 0.02, ratio
+    assert np.abs(np.angle(R)).max() < 0.05
+
+
+def test_cpml_cfs_reflection(oracle_lib):
+    """Complex-frequency-shifted layer with the paper's kappa_max = 7 and
+    alpha_max = 0.05 S/m: the reflection equals exp(-2i (w/c) int (s - 1) d rho)
+    with s = kappa + sigma / (alpha + i w eps0) and the gradings of Eq. 12
+    (alpha largest at the inner interface, kappa and sigma rising as
+    (rho/delta)^n), by quadrature of the continuous profiles.  Reversing the
+    alpha grading changes the attenuation by ~90 % in this band; kappa sets the
+    phase."""
+    O = oracle_lib
+    sf, km, am, order = 0.0125, 7.0, 0.05, 3.0
+    f, R, delta, dx = _cpml_reflection(O, sf, km, am)
+    m = 20000
+    rho = (np.arange(m) + 0.5) / m * delta
+    r = rho / delta
+    sigma = sf * (order + 1) / (150 * np.pi * dx) * r ** order
+    kappa = 1 + (km - 1) * r ** order
+    alpha = am * (1 - r)
+    w = 2 * np.pi * f[:, None]
+    s = kappa + sigma / (alpha + 1j * w * EPS0)
+    Rth = np.exp(-2j * w[:, 0] / C0 * np.sum(s - 1, axis=1) * (delta / m))
+    assert (np.abs(R - Rth) / np.abs(Rth)).max() < 0.05
+    assert np.abs(np.log(np.abs(R)) / np.log(np.abs(Rth)) - 1).max() < 0.02
