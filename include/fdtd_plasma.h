@@ -471,9 +471,12 @@ void fdtd_batch_destroy(fdtd_batch_t b);
  * Scratch is a fixed file-scope device array of 8192 tiles (about 459 KB per
  * GPU that loads the library, held until the process exits).  A call needs
  * ceil(field nodes / 65536) + ceil(nslots / 16384) tiles; more returns
- * FDTD_ERR_INVAL with a message (fdtd_plasma_last_error(NULL)).  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture.  All calls share the
+ * FDTD_ERR_INVAL with a message (fdtd_plasma_last_error(NULL)).  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing), so the address stays right
+ * after cudaDeviceReset; the first call on a device may also load the
+ * library's device code, so make that first call before any stream capture.
+ * All calls share the
  * array: calls that overlap on the GPU race (serialise them, e.g. on one
  * stream).  Nothing needs clearing between calls. */
 typedef struct {

@@ -317,14 +317,15 @@ cudaError_t launch_poynting(cudaStream_t st, const DiagArgs &a, const PoyntingBo
 // (kNoAllocMaxTiles * 7 + 8 doubles, about 459 KB) until the process exits.
 //
 // Work is split into fixed tiles (65536 field nodes or 16384 plasma slots
-// each), one block per tile, so a call needs 1 + ceil(nodes / 65536) +
+// each), one block per tile, so a call needs ceil(nodes / 65536) +
 // ceil(slots / 16384) <= 8192 tiles; larger problems are rejected with
 // FDTD_ERR_INVAL.  Every scratch entry a call reads is written earlier by
 // the same call, so nothing has to be cleared between calls; calls share the
 // array, and calls that overlap on the GPU (e.g. on two streams) race.
+// Every call looks the array's device address up again (cudaGetSymbolAddress
+// allocates nothing), so the address stays right after a cudaDeviceReset or a
+// new primary context.
 // ===================================================================
-
-#include <mutex>
 
 namespace fp {
 
@@ -394,12 +395,6 @@ __global__ void __launch_bounds__(256) k_diag_tiles(DiagArgs a, int64_t field_ti
 
 }  // namespace fp
 
-namespace {
-std::mutex g_noalloc_mu;
-double *g_noalloc_dev_ptr[256];   // device address of g_noalloc_scratch, per device ordinal
-bool g_noalloc_ready[256];
-}  // namespace
-
 extern "C" int fdtd_diagnostics_noalloc(const fdtd_diag_arrays *in, double *out, int out_is_device, void *stream)
 {
     using namespace fp;
@@ -431,22 +426,12 @@ extern "C" int fdtd_diagnostics_noalloc(const fdtd_diag_arrays *in, double *out,
                  (long long)ntiles, kNoAllocMaxTiles, (long long)ncells, (long long)in->nslots);
         return fp_set_global_error(FDTD_ERR_INVAL, msg);
     }
-    // once per device: the device address of the file-scope scratch array
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 256)
-        return fp_set_global_error(FDTD_ERR_CUDA, "fdtd_diagnostics_noalloc: cudaGetDevice failed");
+    // the device address of the file-scope scratch array on the current device
+    // (looked up on every call: it allocates nothing and survives device resets)
     double *scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ready[dev]) {
-            e = cudaGetSymbolAddress((void **)&g_noalloc_dev_ptr[dev], g_noalloc_scratch);
-            if (e != cudaSuccess)
-                return fp_set_global_error(FDTD_ERR_CUDA, "fdtd_diagnostics_noalloc: cudaGetSymbolAddress failed");
-            g_noalloc_ready[dev] = true;
-        }
-        scratch = g_noalloc_dev_ptr[dev];
-    }
+    cudaError_t e = cudaGetSymbolAddress((void **)&scratch, g_noalloc_scratch);
+    if (e != cudaSuccess || !scratch)
+        return fp_set_global_error(FDTD_ERR_CUDA, "fdtd_diagnostics_noalloc: cudaGetSymbolAddress failed");
     const double c0 = 299792458.0, eps0 = 8.8541878128e-12, mu0 = 1.0 / (eps0 * c0 * c0);
     const double dt = in->courant * in->dx / c0;
     const double dvol = std::pow(in->dx, in->ndim);
