@@ -404,6 +404,55 @@ int fdtd_mlp_loss_grad(const float *params, const float *x, const float *target,
 int fdtd_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t n, int64_t t, double lr, double beta1,
                   double beta2, double eps, void *stream);
 
+/* Closure training pipeline on recorded samples (caller-owned device
+ * buffers; see fdtd_plasma_set_recording for the 19-float sample layout).
+ *
+ * fdtd_closure_scales: the closure desc's normalisation and Drude part.
+ *   rho  = (2 - dt nu_mean) / (2 + dt nu_mean),
+ *   beta = 2 dt (e^2/m) / (2 + dt nu_mean)  -- the Crank-Nicolson f_1x update
+ *          and Jx sum of Sec. 5.2 with nu(v) = nu_mean, which reduce to a
+ *          Drude current (rho = beta = 0 when increment == 0: direct form);
+ *   n_scale = n_c = eps0 m omega0^2 / e^2 (critical density at omega0, rad/s);
+ *   e_scale = RMS of the 16 recorded E values over all samples;
+ *   j_scale = RMS of r = J^{n+1/2} - rho J^{n-1/2} - beta n E^n over all
+ *             samples (eps0 omega0 e_scale if every r is 0).
+ *   FP64 sums on the device; `out` is host memory (the stream is
+ *   synchronised).  workspace: fdtd_closure_workspace_bytes() bytes of device
+ *   memory.  Errors: FDTD_ERR_INVAL (NULL, n < 1, dt / omega0 not > 0),
+ *   FDTD_ERR_NONFINITE (E all zero or not finite).
+ * fdtd_closure_dataset: network inputs x [n][17] = [E^{n-15..n} / e_scale,
+ *   n / n_scale] and targets t [n] = r / j_scale, computed in FP64, stored
+ *   FP32 (device, stream-ordered).
+ * fdtd_mlp_init: seeded He-style initial parameters (W1 ~ N(0, 2/17),
+ *   W2 ~ N(0, 2/128), W3 ~ N(0, 1/128), biases 0; Philox4x32-7 + Box-Muller).
+ * fdtd_mlp_gather: rows first .. first + batch - 1 of a seeded permutation of
+ *   [0, n) for `epoch` (a four-round Feistel network with cycle walking),
+ *   copied to xb [batch][17], tb [batch]; needs first + batch <= n.
+ * fdtd_mlp_train_epoch: one epoch of minibatch training: for each of the
+ *   n / batch full batches of the epoch's permuted order (the ragged tail is
+ *   left out), gather, fdtd_mlp_loss_grad, and fdtd_mlp_adam with step count
+ *   iter0 + b + 1 and the cosine-decayed rate lr (1 + cos(pi (iter0 + b) /
+ *   total_iters)) / 2.  *loss_mean (device double) receives the mean of the
+ *   batch losses.  grad, m, v: FDTD_MLP_NPARAMS floats each (m, v zeroed by
+ *   the caller before the first epoch); workspace of
+ *   fdtd_mlp_train_workspace_bytes(batch) bytes.  Nothing is synchronised. */
+typedef struct {
+    double e_scale, j_scale, n_scale, rho, beta;
+} fdtd_closure_scales_t;
+size_t fdtd_closure_workspace_bytes(void);
+int fdtd_closure_scales(const float *samples, int64_t n, double omega0, double dt, double nu_mean, int increment,
+                        fdtd_closure_scales_t *out, void *workspace, size_t workspace_bytes, void *stream);
+int fdtd_closure_dataset(const float *samples, int64_t n, const fdtd_closure_scales_t *sc, float *x, float *t,
+                         void *stream);
+int fdtd_mlp_init(float *params, uint64_t seed, void *stream);
+int fdtd_mlp_gather(const float *x, const float *t, int64_t n, uint64_t seed, int64_t epoch, int64_t first,
+                    int64_t batch, float *xb, float *tb, void *stream);
+size_t fdtd_mlp_train_workspace_bytes(int64_t batch);
+int fdtd_mlp_train_epoch(float *params, float *grad, float *m, float *v, const float *x, const float *t, int64_t n,
+                         int64_t batch, uint64_t seed, int64_t epoch, int64_t iter0, int64_t total_iters, double lr,
+                         double beta1, double beta2, double eps, double *loss_mean, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
 /* ---------------------------------------------------------------------
  * Batches of independent 1-D runs (same step as above, per run), advanced by
  * one persistent kernel launch per fdtd_batch_step call (graph-captured).

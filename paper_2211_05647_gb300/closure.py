@@ -1,5 +1,5 @@
 """Learned J closure: training data from kinetic runs, normalisation, and
-training with the library's own GPU kernels.
+training, each step a call into the CUDA library.
 
 The closure replaces, for cells inside the training density range, the
 velocity-space update of Sec. 5.2 (the f_1x update and the Jx moment) by a
@@ -11,30 +11,33 @@ of a plasma with the mean collision frequency nu:
 so the network learns only the kinetic correction (what the velocity-
 dependent collision frequency adds to the Drude response).  E_s is the RMS
 of E over the training samples, n_s the critical density at w0, and J_s the
-RMS of the correction itself (targets of unit variance).  Every
-step of the pipeline runs on the GPU: the kinetic runs record their samples
-in-kernel, and the loss, its gradient and the Adam update are library kernels.
+RMS of the correction itself (targets of unit variance).  This module only
+sequences library calls and allocates their buffers: the kinetic runs record
+their samples in-kernel (fdtd_plasma_set_recording), the scales, inputs and
+targets come from fdtd_closure_scales / fdtd_closure_dataset, and training
+from fdtd_mlp_init and fdtd_mlp_train_epoch.
 """
 from __future__ import annotations
 
-import math
+import ctypes
 
-import numpy as np
+from .fdtd_plasma import MLP_NPARAMS, MlpTrainer, _check, fdtd_closure_scales_t, load_library
 
-EPS0 = 8.8541878128e-12
-QE = 1.602176634e-19
-ME = 9.1093837015e-31
-NIN, NHID, NPARAMS = 17, 128, 18945
+NIN, NHID, NPARAMS = 17, 128, MLP_NPARAMS
+
+
+def _stream(device):
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
 
 
 def init_params(seed: int, device):
-    """He-style initialisation of the packed FP32 parameters (seeded)."""
+    """Seeded He-style initial parameters (fdtd_mlp_init), FP32 device tensor."""
     import torch
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    parts = [torch.randn(NIN * NHID, generator=g) * math.sqrt(2.0 / NIN), torch.zeros(NHID),
-             torch.randn(NHID * NHID, generator=g) * math.sqrt(2.0 / NHID), torch.zeros(NHID),
-             torch.randn(NHID, generator=g) * math.sqrt(1.0 / NHID), torch.zeros(1)]
-    return torch.cat(parts).to(device=device, dtype=torch.float32).contiguous()
+    lib = load_library()
+    p = torch.empty(NPARAMS, dtype=torch.float32, device=device)
+    _check(lib, None, lib.fdtd_mlp_init(p.data_ptr(), int(seed), _stream(p.device)))
+    return p
 
 
 def record_samples(spec, steps: int, rate: float, seed: int, capacity: int, device=0):
@@ -55,60 +58,48 @@ def record_samples(spec, steps: int, rate: float, seed: int, capacity: int, devi
     return out
 
 
-def _residual(samples, rho, beta):
-    s = samples.double()
-    return s[:, 17] - rho * s[:, 18] - beta * s[:, 16] * s[:, 15]
-
-
 def scales(samples, omega0: float, dt: float, nu_mean: float, increment: bool = True) -> dict:
-    """Normalisations and the Drude part for the closure desc (see module doc);
-    increment=False gives the direct form (rho = beta = 0)."""
-    e_s = float(samples[:, :16].double().pow(2).mean().sqrt().item())
-    n_c = EPS0 * ME * omega0 ** 2 / QE ** 2
-    if increment:
-        rho = (2.0 - dt * nu_mean) / (2.0 + dt * nu_mean)
-        beta = 2.0 * dt * (QE * QE / ME) / (2.0 + dt * nu_mean)
-    else:
-        rho = beta = 0.0
-    r = _residual(samples, rho, beta)
-    j_s = float(r.pow(2).mean().sqrt().item()) or EPS0 * omega0 * e_s
-    return dict(e_scale=e_s, j_scale=j_s, n_scale=n_c, rho=rho, beta=beta)
+    """Normalisations and the Drude part for the closure desc (see module
+    doc; fdtd_closure_scales); increment=False gives the direct form
+    (rho = beta = 0)."""
+    import torch
+    lib = load_library()
+    s = samples.contiguous()
+    ws_bytes = lib.fdtd_closure_workspace_bytes()
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=s.device)
+    out = fdtd_closure_scales_t()
+    _check(lib, None, lib.fdtd_closure_scales(s.data_ptr(), s.shape[0], float(omega0), float(dt), float(nu_mean),
+                                              int(bool(increment)), ctypes.byref(out), ws.data_ptr(), ws_bytes,
+                                              _stream(s.device)))
+    return dict(e_scale=out.e_scale, j_scale=out.j_scale, n_scale=out.n_scale, rho=out.rho, beta=out.beta)
 
 
 def dataset(samples, sc: dict):
-    """Network inputs and targets (float32 device tensors) from raw samples."""
+    """Network inputs [N, 17] and targets [N] (float32 device tensors) from
+    raw samples (fdtd_closure_dataset)."""
     import torch
-    x = torch.empty(samples.shape[0], NIN, dtype=torch.float32, device=samples.device)
-    x[:, :16] = samples[:, :16] / sc["e_scale"]
-    x[:, 16] = samples[:, 16] / sc["n_scale"]
-    t = (_residual(samples, sc["rho"], sc["beta"]) / sc["j_scale"]).float()
-    return x.contiguous(), t.contiguous()
+    lib = load_library()
+    s = samples.contiguous()
+    n = s.shape[0]
+    x = torch.empty(n, NIN, dtype=torch.float32, device=s.device)
+    t = torch.empty(n, dtype=torch.float32, device=s.device)
+    d = fdtd_closure_scales_t(sc["e_scale"], sc["j_scale"], sc["n_scale"], sc["rho"], sc["beta"])
+    _check(lib, None, lib.fdtd_closure_dataset(s.data_ptr(), n, ctypes.byref(d), x.data_ptr(), t.data_ptr(),
+                                               _stream(s.device)))
+    return x, t
 
 
 def train(x, t, epochs: int = 10, batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None):
     """Adam on the mean-squared error, cosine-decayed learning rate, seeded
-    shuffles; returns (params, per-epoch mean losses)."""
-    import torch
-    from .fdtd_plasma import MlpTrainer
-    dev = x.device
-    params = init_params(seed, dev)
+    shuffles (fdtd_mlp_train_epoch per epoch); returns (params, per-epoch
+    mean losses)."""
+    params = init_params(seed, x.device)
     tr = MlpTrainer(params, batch, lr=lr)
-    n = x.shape[0]
-    nb = n // batch
+    nb = x.shape[0] // batch
     total = max(epochs * nb, 1)
-    g = torch.Generator(device=dev).manual_seed(seed + 1)
     hist = []
-    it = 0
     for ep in range(epochs):
-        perm = torch.randperm(n, generator=g, device=dev)
-        acc = torch.zeros((), dtype=torch.float64, device=dev)
-        for b in range(nb):
-            idx = perm[b * batch:(b + 1) * batch]
-            lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * it / total))
-            loss = tr.step(x[idx].contiguous(), t[idx].contiguous(), lr=lr_t)
-            acc += loss.double()[0]
-            it += 1
-        hist.append(float(acc.item()) / max(nb, 1))
+        hist.append(float(tr.epoch(x, t, seed + 1, ep, ep * nb, total).item()))
         if log:
             log(f"epoch {ep}: mse {hist[-1]:.3e}")
     return params, hist

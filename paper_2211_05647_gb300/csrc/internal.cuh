@@ -140,7 +140,8 @@ __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e)
 
 // ------------------------------------------- Philox4x32-7 (Salmon et al. 2011)
 // The 7-round variant, which the authors report passes TestU01's BigCrush;
-// used only to draw stochastic-rounding bits.
+// draws the stochastic-rounding bits, the recorder's sample selection and the
+// closure training's initial weights and minibatch permutations.
 
 __device__ __forceinline__ uint4 philox4x32_7(uint4 c, uint2 k)
 {

@@ -102,6 +102,11 @@ class fdtd_closure_desc(ctypes.Structure):
                 ("rho", ctypes.c_double), ("n_train_max", ctypes.c_double), ("beta", ctypes.c_double)]
 
 
+class fdtd_closure_scales_t(ctypes.Structure):
+    _fields_ = [("e_scale", ctypes.c_double), ("j_scale", ctypes.c_double), ("n_scale", ctypes.c_double),
+                ("rho", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
 MLP_NPARAMS = 18945
 MLP_NIN = 17
 MLP_NHID = 128
@@ -166,6 +171,22 @@ SIGNATURES = {
     "fdtd_mlp_adam": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_int64, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_void_p]),
+    "fdtd_closure_workspace_bytes": (ctypes.c_size_t, []),
+    "fdtd_closure_scales": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.POINTER(fdtd_closure_scales_t),
+                                           ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "fdtd_closure_dataset": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(fdtd_closure_scales_t),
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fdtd_mlp_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "fdtd_mlp_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]),
+    "fdtd_mlp_train_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int64]),
+    "fdtd_mlp_train_epoch": (ctypes.c_int, [ctypes.c_void_p] * 6 + [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                                   ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                                                   ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                                                   ctypes.c_size_t, ctypes.c_void_p]),
     "fdtd_batch_create": (ctypes.c_int, [ctypes.POINTER(fdtd_run_desc), ctypes.c_int32,
                                          ctypes.POINTER(fdtd_runtime_desc), ctypes.POINTER(ctypes.c_void_p)]),
     "fdtd_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -351,6 +372,24 @@ class MlpTrainer:
                                                            self.grad.data_ptr(), self.loss.data_ptr(),
                                                            self.ws.data_ptr(), self.ws_bytes, st))
         return self.loss, self.grad
+
+    def epoch(self, x, t, seed: int, epoch: int, iter0: int, total_iters: int):
+        """One training epoch in one library call (fdtd_mlp_train_epoch):
+        seeded shuffled minibatches of x [n, 17] / t [n], loss and gradient,
+        Adam with the cosine-decayed rate; returns the epoch's mean batch loss
+        as a device FP64 scalar."""
+        torch = self.torch
+        if not hasattr(self, "tws"):
+            self.tws_bytes = self.lib.fdtd_mlp_train_workspace_bytes(self.batch)
+            self.tws = torch.empty(self.tws_bytes, dtype=torch.uint8, device=self.dev)
+            self.loss_mean = torch.zeros(1, dtype=torch.float64, device=self.dev)
+        st = torch.cuda.current_stream(self.dev).cuda_stream
+        _check(self.lib, None, self.lib.fdtd_mlp_train_epoch(
+            self.p.data_ptr(), self.grad.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), x.data_ptr(), t.data_ptr(),
+            x.shape[0], self.batch, int(seed), int(epoch), int(iter0), int(total_iters), float(self.lr),
+            self.betas[0], self.betas[1], self.eps, self.loss_mean.data_ptr(), self.tws.data_ptr(), self.tws_bytes,
+            st))
+        return self.loss_mean
 
     def step(self, x, t, lr=None):
         self.loss_grad(x, t)

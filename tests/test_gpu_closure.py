@@ -224,3 +224,118 @@ def test_trained_closure_tracks_kinetic_solve():
     print(f"closure vs kinetic after 700 steps (max rel L2 over Ez, Hx, Hy): {errs}")
     assert errs["trained"] <= 1e-2
     assert errs["trained"] < errs["drude only"]
+
+
+def _random_samples(n, seed):
+    rng = np.random.default_rng(seed)
+    s = np.zeros((n, 19), np.float32)
+    s[:, :16] = rng.standard_normal((n, 16)) * 0.3
+    s[:, 16] = rng.uniform(1e17, 8e17, n)
+    s[:, 18] = rng.standard_normal(n) * 1e-2
+    s[:, 17] = 0.99 * s[:, 18] + rng.standard_normal(n) * 1e-4
+    return s
+
+
+@pytest.mark.parametrize("increment", [True, False])
+def test_closure_scales_and_dataset_match_oracle(increment):
+    """fdtd_closure_scales / fdtd_closure_dataset against the FP64 oracle
+    (oracle/closure_data.py): scales to FP64 rounding, inputs and targets to
+    one FP32 rounding (both sides form them in FP64), on a ragged count."""
+    import torch
+    from oracle import closure_data as CD
+    from paper_2211_05647_gb300 import closure as C
+    s = _random_samples(300_001, 8)
+    dt, nu = 1.25e-12, 0.01 * OMEGA0
+    sd = torch.from_numpy(s).cuda()
+    sc = C.scales(sd, OMEGA0, dt, nu, increment=increment)
+    so = CD.scales(s, OMEGA0, dt, nu, increment=increment)
+    for k in so:
+        assert abs(sc[k] - so[k]) <= 1e-12 * abs(so[k]), (k, sc[k], so[k])
+    x, t = C.dataset(sd, sc)
+    xo, to = CD.dataset(s, so)
+    x, t = x.cpu().numpy().astype(np.float64), t.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(x, xo, rtol=2.4e-7, atol=0)
+    np.testing.assert_allclose(t, to, rtol=2.4e-7, atol=1e-30)
+    print(f"closure scales (increment={increment}): {sc}")
+
+
+def test_mlp_gather_is_a_seeded_permutation():
+    """Every batch of an epoch is a disjoint slice of one permutation of the
+    samples (all of them when the batch divides n); rows are copied whole;
+    another epoch gives another order, the same epoch the same one."""
+    import torch
+    from paper_2211_05647_gb300 import fdtd_plasma as F
+    lib = F.load_library()
+    for n, batch in ((8192, 1024), (10_007, 1000)):
+        x = torch.arange(n * 17, dtype=torch.float32, device="cuda").view(n, 17)
+        t = torch.arange(n, dtype=torch.float32, device="cuda")
+        xb = torch.empty(batch, 17, dtype=torch.float32, device="cuda")
+        tb = torch.empty(batch, dtype=torch.float32, device="cuda")
+
+        def order(epoch):
+            idx = []
+            for b in range(n // batch):
+                assert lib.fdtd_mlp_gather(x.data_ptr(), t.data_ptr(), n, 77, epoch, b * batch, batch, xb.data_ptr(),
+                                           tb.data_ptr(), None) == 0
+                torch.cuda.synchronize()
+                i = tb.cpu().numpy().astype(np.int64)
+                assert np.array_equal(xb.cpu().numpy(), x.cpu().numpy()[i])
+                idx.append(i)
+            return np.concatenate(idx)
+
+        o0, o0b, o1 = order(0), order(0), order(1)
+        assert np.unique(o0).size == o0.size == (n // batch) * batch
+        assert o0.min() >= 0 and o0.max() < n
+        if n % batch == 0:
+            assert np.array_equal(np.sort(o0), np.arange(n))
+        assert np.array_equal(o0, o0b) and not np.array_equal(o0, o1)
+        assert abs(np.corrcoef(np.arange(o0.size), o0)[0, 1]) < 0.05     # shuffled, not near-identity
+
+
+def test_mlp_init_statistics():
+    """He-style initial weights: zero biases, per-layer standard deviations
+    sqrt(2/17), sqrt(2/128), sqrt(1/128), zero mean; seeded."""
+    from paper_2211_05647_gb300 import closure as C
+    p = C.init_params(5, "cuda").cpu().numpy().astype(np.float64)
+    q = C.init_params(5, "cuda").cpu().numpy()
+    r = C.init_params(6, "cuda").cpu().numpy()
+    assert np.array_equal(p.astype(np.float32), q) and not np.array_equal(q, r)
+    P = _oracle_params(p.astype(np.float32))
+    for b in ("b1", "b2", "b3"):
+        assert np.all(P[b] == 0)
+    for w, sd in (("W1", math.sqrt(2 / 17)), ("W2", math.sqrt(2 / 128)), ("W3", math.sqrt(1 / 128))):
+        v = P[w].ravel()
+        assert abs(v.std() / sd - 1) < 6 / math.sqrt(v.size) + 0.01, w
+        assert abs(v.mean()) < 5 * sd / math.sqrt(v.size), w
+
+
+def test_train_epoch_equals_its_steps():
+    """fdtd_mlp_train_epoch = gather + loss/grad + Adam (cosine-decayed rate,
+    step count iter0 + b + 1) per batch, bit for bit; its mean loss is the
+    mean of the batch losses."""
+    import torch
+    from paper_2211_05647_gb300 import MlpTrainer
+    from paper_2211_05647_gb300 import closure as C
+    from paper_2211_05647_gb300 import fdtd_plasma as F
+    lib = F.load_library()
+    rng = np.random.default_rng(12)
+    n, batch, lr, total = 5000, 1024, 2e-3, 12
+    x = torch.from_numpy(rng.standard_normal((n, 17)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal(n).astype(np.float32)).cuda()
+    pa = C.init_params(3, "cuda")
+    pb = pa.clone()
+    ta = MlpTrainer(pa, batch, lr=lr)
+    mean = float(ta.epoch(x, t, 9, 1, 4, total).item())
+    tb_ = MlpTrainer(pb, batch, lr=lr)
+    xb = torch.empty(batch, 17, dtype=torch.float32, device="cuda")
+    tb = torch.empty(batch, dtype=torch.float32, device="cuda")
+    losses = []
+    for b in range(n // batch):
+        assert lib.fdtd_mlp_gather(x.data_ptr(), t.data_ptr(), n, 9, 1, b * batch, batch, xb.data_ptr(), tb.data_ptr(),
+                                   None) == 0
+        tb_.t = 4 + b
+        loss = tb_.step(xb, tb, lr=lr * 0.5 * (1 + math.cos(math.pi * (4 + b) / total)))
+        losses.append(float(loss.item()))
+    torch.cuda.synchronize()
+    assert torch.equal(pa, pb)
+    assert abs(mean - np.mean(losses)) <= 1e-6 * abs(np.mean(losses))
