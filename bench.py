@@ -45,6 +45,8 @@ def parse():
                     help="2-D / 3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload at N = 1: skip the other configurations' entries (configs)")
     return ap.parse_args()
 
 
@@ -206,14 +208,33 @@ def ncu_traffic(kernel: str, workload: str, shape=None):
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_throughput(name: str, steps: int, warmup: int, budget_s: float | None):
-    """Time the FP64 oracle on a bounded sample of the workload.  Returns
-    (Gcell-updates/s, phase-space updates/s, steps timed, sample text)."""
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_throughput(name: str, steps: int, warmup: int, budget_s: float | None, omp: bool = False):
+    """Time the FP64 oracle on a bounded sample of the workload (omp: the
+    all-core build of the same source).  Returns (Gcell-updates/s, phase-space
+    updates/s, steps timed, sample text, cells, nodes)."""
     from oracle import oracle as O
     from tests.adapters import oracle_sim
     spec, text = sample_spec(name)
     specs = spec if isinstance(spec, list) else [spec]
-    sims = [oracle_sim(O, sp) for sp in specs]
+    sims = [oracle_sim(O, sp, omp=omp) for sp in specs]
     for sim in sims:
         sim.step(warmup)
     n = 0
@@ -230,6 +251,244 @@ def oracle_throughput(name: str, steps: int, warmup: int, budget_s: float | None
     return cells * n / dt / 1e9, nodes * n / dt, n, text, cells, nodes
 
 
+# ------------------------------------------------- the other configurations
+def _peak(key="hbm_gbs", fallback=6800.0):
+    peaks = measured_peaks()
+    return (peaks[key], f"MEASURED_PEAKS.json {key}") if peaks else (fallback, "fallback")
+
+
+def _release():
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
+def solver_config(workload: str, steps: int, warmup: int, autotune: bool, local: int) -> dict:
+    """One single-grid workload: autotune (untimed), W warm-up steps, K steps
+    timed with CUDA events on the solver stream, per-kernel launch times, the
+    kinetic kernel's roofline and the step's algorithmic HBM fraction."""
+    import torch
+    from paper_2211_05647_gb300 import Solver
+    spec = make_spec(workload)
+    s = Solver.from_spec(spec, device=local)
+    ns, nn = s.plasma_shape()
+    cells = cells_of(spec)
+    if autotune:
+        s.autotune()
+    shapes = s.launch_shapes()
+    s.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = s.time_kernels(min(steps, 50))
+    s.close()
+    del s
+    _release()
+    fbytes = {"f32": 4, "bf16": 2, "f64": 8}[spec["plasma"]["f_dtype"]]
+    evolve = bool(spec["plasma"].get("evolve_f0"))
+    alg = 2 * fbytes * ns * nn * (2 if evolve else 1)
+    peak, src = _peak()
+    kname = "k_kinetic_f0" if evolve else "k_kinetic"
+    fb = 8 if spec["grid"].get("precision", "f32") == "f64" else 4
+    ncomp = {1: 2, 2: 3, 3: 6}[spec["grid"]["ndim"]]
+    step_alg = 2 * fb * ncomp * cells + alg
+    ms_step = ms / steps
+    achieved = alg / (kt["kinetic"] / 1e3) / 1e9
+    return {"workload": workload, "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
+            "gcell_updates_per_s": cells * steps / (ms / 1e3) / 1e9,
+            "phase_space_updates_per_s": ns * nn * steps / (ms / 1e3),
+            "cells": cells, "plasma_cells": ns, "nodes_per_cell": nn, "f_dtype": spec["plasma"]["f_dtype"],
+            "precision": spec["grid"].get("precision", "f32"), "kernel_ms": kt, "launch_shapes": shapes,
+            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "alg_bytes_per_launch": alg, "launch_ms": kt["kinetic"],
+                         "traffic": ncu_traffic(kname, workload, None if evolve else
+                                                (shapes["kin_vpl"], shapes["kin_l"]) if shapes["kin_vpl"] else (8, 32)),
+                         "peak_source": src},
+            "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
+            "gpu_launches": step_launches(steps, 1 if ns else 0, False)}
+
+
+def batch_config(workload: str, specs, steps: int, warmup: int, autotune: bool, local: int) -> dict:
+    """Batched independent 1-D runs: one persistent launch per chunk of up to
+    100 steps (graph replay); per-launch times with events between chunks."""
+    import torch
+    from paper_2211_05647_gb300 import Batch
+    b = Batch(specs, device=local)
+    tune = b.autotune() if autotune else None
+    info = b.info()
+    cells, nodes = info["cells"], info["nodes"]
+    st = b.stream
+    chunk = min(100, steps)
+    rem = steps % chunk
+    b.step(max(warmup, 1))
+    b.step(chunk)                 # captures the chunk graph outside the timed region
+    if rem:
+        b.step(rem)
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps // chunk + 2)]
+    evs[0].record(st)
+    for i in range(steps // chunk):
+        b.step(chunk)
+        evs[i + 1].record(st)
+    if rem:
+        b.step(rem)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_end.record(st)
+    torch.cuda.synchronize()
+    ms = evs[0].elapsed_time(e_end)
+    launch_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps // chunk)]
+    b.close()
+    del b
+    _release()
+    fdt = specs[0]["plasma"]["f_dtype"]
+    fb = {"f32": 4, "bf16": 2, "f64": 8}[fdt]
+    eb = 8 if specs[0]["grid"]["precision"] == "f64" else 4
+    alg_step = 2 * eb * (2 * cells + len(specs)) + 2 * fb * nodes
+    per_launch_ms = statistics.median(launch_ms) if launch_ms else ms
+    achieved = alg_step * chunk / (per_launch_ms / 1e3) / 1e9
+    peak, src = _peak()
+    return {"workload": workload, "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+            "gcell_updates_per_s": cells * steps / (ms / 1e3) / 1e9,
+            "phase_space_updates_per_s": nodes * steps / (ms / 1e3),
+            "runs": len(specs), "cells": cells, "phase_space_nodes": nodes, "f_dtype": fdt,
+            "clusters": info["clusters"], "ctas_per_cluster": info["cluster_ctas"], "steps_per_launch": chunk,
+            "row_shape": tune,
+            "roofline": {"bound": "hbm", "kernel": "k_batch1d", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg_step * chunk,
+                         "launch_ms": per_launch_ms, "peak_source": src},
+            "step_hbm_frac_algorithmic": alg_step / (ms / steps / 1e3) / 1e9 / peak,
+            "gpu_launches": 2 * (steps // chunk + (1 if rem else 0))}
+
+
+def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: int) -> dict:
+    """Learned closure vs the kinetic solve on the same 8192^2 grid: the
+    trained weights are the committed ones (paper_2211_05647_gb300/data,
+    written by train_closure.py with the library's own training kernels).
+    Each run does W warm-up steps, K steps timed with events, then the rest of
+    the workload's 4000 steps untimed; the closure's fields after 4000 steps
+    are compared with the kinetic run's (relative L2 per component)."""
+    import numpy as np
+    import torch
+    from paper_2211_05647_gb300 import Solver
+    from paper_2211_05647_gb300.train_closure import load
+    w = load()
+    spec = make_spec("2d_tmz_8192_closure")
+    total = int(spec["steps"])
+    cells = cells_of(spec)
+
+    def run(with_closure):
+        s = Solver.from_spec(spec, device=local)
+        if with_closure:
+            s.set_closure(w["params"], e_scale=w["e_scale"], j_scale=w["j_scale"], n_scale=w["n_scale"],
+                          rho=w["rho"], beta=w["beta"], n_train_max=w["n_train_max"], engine=engine)
+        if autotune:
+            s.autotune()
+        shape = s.closure_shape() if with_closure else s.plasma_shape()
+        s.step(warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(steps)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.step(max(total - warmup - steps, 0))
+        fields = {f: s.read(f, device=False).astype(np.float64) for f in ("ez", "hx", "hy")}
+        kt = s.time_kernels(20)
+        shapes = s.launch_shapes()
+        s.close()
+        del s
+        _release()
+        return ms, fields, kt, shape, shapes
+
+    ms_c, f_c, kt_c, (n_kin, n_cl), sh_c = run(True)
+    ms_k, f_k, kt_k, (ns_k, nn_k), sh_k = run(False)
+    err = {f: float(np.linalg.norm(f_c[f] - f_k[f]) / np.linalg.norm(f_k[f])) for f in f_c}
+    flops = 2 * (17 * 128 + 128 * 128 + 128) * n_cl
+    tpk, tsrc = _peak("bf16_tflops_sustained", 1700.0)
+    hpk, _ = _peak()
+    achieved = flops / (kt_c["closure"] / 1e3) / 1e12 if kt_c["closure"] > 0 else 0.0
+    # closure step bytes: fields (24 B a cell) + per closure cell history ring (64 B read, 4 B write),
+    # density, J state and E gather / scatter (16 B) + the kinetic fallback rows (8 B a node)
+    ms_step_c = ms_c / steps
+    step_alg = 24 * cells + 84 * n_cl + 8 * n_kin * nn_k
+    return {"workload": "2d_tmz_8192_closure", "steps": steps, "warmup": warmup, "run_steps": total,
+            "ms_per_step": ms_step_c, "gcell_updates_per_s": cells * steps / (ms_c / 1e3) / 1e9,
+            "closure_engine": engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
+            "weights": {k: w["record"][k] for k in ("runs", "samples", "epochs", "batch") if k in w["record"]},
+            "closure_vs_kinetic": {"kinetic_ms_per_step": ms_k / steps, "closure_ms_per_step": ms_step_c,
+                                   "speedup": ms_k / ms_c, "field_rel_l2_after_run": err,
+                                   "kinetic_gcell_updates_per_s": cells * steps / (ms_k / 1e3) / 1e9,
+                                   "kinetic_phase_space_updates_per_s": ns_k * nn_k * steps / (ms_k / 1e3)},
+            "kernel_ms": {"closure_run": kt_c, "kinetic_run": kt_k},
+            "launch_shapes": {"closure_run": sh_c, "kinetic_run": sh_k},
+            "roofline": {"bound": "tensor", "kernel": "k_closure_tc" if engine == "tcgen05" else "k_closure",
+                         "achieved": achieved, "peak": tpk, "unit": "TFLOP/s", "frac": achieved / tpk,
+                         "traffic": None, "alg_flops_per_launch": flops, "launch_ms": kt_c["closure"],
+                         "peak_source": tsrc},
+            "step_hbm_frac_algorithmic": step_alg / (ms_step_c / 1e3) / 1e9 / hpk,
+            "gpu_launches": step_launches(steps, 2 if n_kin else 1, False)}
+
+
+def other_configs(args, local: int) -> dict:
+    """The other configurations of the benchmark, each at its full size: the
+    1-D FP64 slab (its full 2000 steps: a few microseconds each), the 3-D 512^3
+    BF16 slab, the 256 batched 1-D runs (FP32 and BF16 delta f) and the
+    learned closure against the kinetic solve at 8192^2."""
+    out = {}
+    auto = not args.no_autotune
+    W, K = max(args.warmup, 3), args.steps
+    jobs = [
+        ("cfg1_1d_slab_fp64", lambda: solver_config("1d_slab_fp64", max(K, 2000), W, auto, local)),
+        ("cfg3_3d_512_bf16", lambda: solver_config("3d_512_kinetic_bf16", K, W, auto, local)),
+        ("cfg4_batch1d_256_f32", lambda: batch_config("batch1d_256_f32", make_spec("batch1d_256_f32"), K, W, auto,
+                                                      local)),
+        ("cfg4_batch1d_256_bf16", lambda: batch_config("batch1d_256_bf16", make_spec("batch1d_256_bf16"), K, W, auto,
+                                                       local)),
+        ("cfg5_closure_8192", lambda: closure_config(K, W, args.engine, auto, local)),
+    ]
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    for name, job in jobs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = job()
+        except Exception as exc:       # reported, not hidden: the entry says what failed
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            _release()
+        out[name]["wall_s"] = time.perf_counter() - t0
+    out["clocks"] = clocks.stop()
+    return out
+
+
+def all_core_oracle():
+    """(use the all-core oracle build?, threads it uses); the single-thread
+    build when -fopenmp is not available."""
+    try:
+        from oracle import oracle as O
+        O.build(omp=True)
+        return True, O.threads(omp=True)
+    except Exception:
+        return False, 1
+
+
+def cpu_baseline(workload: str) -> dict:
+    """The oracle as it stands on the host cores: the all-core build (value)
+    and the single-thread build beside it, each ~15 s of a bounded sample."""
+    omp, cores = all_core_oracle()
+    g, psr, n, text, _, _ = oracle_throughput(workload, 10 ** 6, 2, budget_s=15.0, omp=omp)
+    g1, psr1, n1, _, _, _ = oracle_throughput(workload, 10 ** 6, 2, budget_s=15.0, omp=False)
+    return {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": f"{text}; {n} oracle steps in ~15 s on {cores} threads"
+                      f"{'' if omp else ' (all-core build unavailable)'}",
+            "phase_space_updates_per_s": psr,
+            "single_thread": {"value": g1, "unit": UNIT, "cores": 1, "steps": n1, "phase_space_updates_per_s": psr1}}
+
+
 # --------------------------------------------------------------------- main
 def main():
     args = parse()
@@ -240,14 +499,15 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        g, ps, n, text, cells, nodes = oracle_throughput(args.workload, args.steps, args.warmup, None)
+        omp, cores = all_core_oracle()
+        g, ps, n, text, cells, nodes = oracle_throughput(args.workload, args.steps, args.warmup, None, omp=omp)
         line = {"impl": "reference", "metric": METRIC, "value": g, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": n, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
                 "config": {"workload": args.workload, "sample": text},
                 "phase_space_updates_per_s": ps,
-                "cpu_baseline": {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "sample": f"{text}; {n} oracle steps, single thread"},
+                "cpu_baseline": {"value": g, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+                                 "sample": f"{text}; {n} oracle steps, {cores} threads"},
                 "e2e": {"value": g, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return 0
@@ -314,14 +574,22 @@ def main():
                 torch.empty(ns, dtype=torch.float64 if s.precision == "f64" else torch.float32).pin_memory()
                 for n in outs}
     barrier()
+    # phase boundaries are synchronised so the window splits into set-up (plasma set-up from the host density:
+    # upload, slot compaction, velocity tables, graph re-capture), field upload, steps and read-back
     t_e2e0 = time.perf_counter()
     p = dict(spec["plasma"])
     p["density"] = dens_h.numpy()
     s.set_plasma(**p)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter()
     qid = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6}
     for n, v in init.items():   # host -> device through the C ABI
         assert s.lib.fdtd_plasma_write_fields(s.h, qid[n], v.data_ptr(), v.numel() * v.element_size(), 0) == 0
+    torch.cuda.synchronize()
+    t_h2d = time.perf_counter()
     s.step(args.steps)
+    torch.cuda.synchronize()
+    t_steps = time.perf_counter()
     h2d = dens_h.numel() * 8 + sum(v.numel() * v.element_size() for v in init.values())
     d2h = 0
     for n in outs:
@@ -330,7 +598,10 @@ def main():
         assert rc == 0, rc
         d2h += o.numel() * o.element_size()
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t_e2e0
+    t_end = time.perf_counter()
+    t_e2e = t_end - t_e2e0
+    e2e_breakdown_ms = {"setup_incl_density_h2d": (t_setup - t_e2e0) * 1e3, "fields_h2d": (t_h2d - t_setup) * 1e3,
+                        "steps": (t_steps - t_h2d) * 1e3, "d2h": (t_end - t_steps) * 1e3}
     e2e_value = job_rate(cells * args.steps, world, reduce_max(t_e2e, world, f"cuda:{local}")) / 1e9
 
     if rank != 0:
@@ -378,12 +649,14 @@ def main():
             "gpu_launches": step_launches(args.steps, 1 if ns else 0, fused),
             "clocks": clk,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
-                    "d2h_bytes_per_step": d2h / args.steps}}
+                    "d2h_bytes_per_step": d2h / args.steps, "breakdown_ms": e2e_breakdown_ms}}
+    if world == 1 and not args.no_configs and args.workload == "2d_tmz_4096_kinetic":
+        s.close()
+        del s
+        _release()
+        line["configs"] = other_configs(args, local)
     if world == 1 and not args.no_cpu_baseline:
-        g, psr, n, text, _, _ = oracle_throughput(args.workload, 10 ** 6, 2, budget_s=15.0)
-        line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{text}; {n} oracle steps in ~15 s, single thread",
-                                "phase_space_updates_per_s": psr}
+        line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -391,85 +664,24 @@ def main():
 
 
 def closure_bench(args, spec, rank, world, local):
-    """Learned J closure vs the kinetic solve on the same grid.  Training data
-    come from kinetic runs of the 4096^2 cylinder recipe (three density seeds,
-    in-kernel recorder), training uses the library's own loss/grad and Adam
-    kernels (not timed); then the closure run and the kinetic run each do W
-    warm-up + K timed steps, their fields are compared, and the closure and
-    kinetic kernels are timed with events."""
-    import numpy as np
-    import torch
-    from fdtd_inputs import OMEGA0, closure_training_specs
-    from paper_2211_05647_gb300 import Solver
-    from paper_2211_05647_gb300 import closure as C
-    t_train0 = time.perf_counter()
-    tspecs = closure_training_specs()
-    samples = torch.cat([C.record_samples(sp, sp["steps"], 1e-3, 77 + i, 2_500_000, device=local)
-                         for i, sp in enumerate(tspecs)])
-    dt = spec["grid"]["courant"] * spec["grid"]["dx"] / 299792458.0
-    sc = C.scales(samples, OMEGA0, dt, spec["plasma"]["nu0"])
-    x, t = C.dataset(samples, sc)
-    params, hist = C.train(x, t, epochs=8, batch=4096, lr=2e-3, seed=5)
-    del x, t, samples
-    t_train = time.perf_counter() - t_train0
-    nmax = float(max(np.max(sp["plasma"]["density"]) for sp in tspecs))
-
-    def timed(with_closure):
-        s = Solver.from_spec(spec, device=local)
-        if with_closure:
-            s.set_closure(params, n_train_max=nmax, engine=args.engine, **sc)
-        if not args.no_autotune:
-            s.autotune()                   # untimed: stencil (and fallback kinetic) launch shapes
-        s.step(args.warmup)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s.stream)
-        s.step(args.steps)
-        e1.record(s.stream)
-        torch.cuda.synchronize()
-        fields = {f: s.read(f, device=False) for f in ("ez", "hx", "hy")}
-        kt = s.time_kernels(20)
-        kt["launch_shapes"] = s.launch_shapes()
-        shape = s.closure_shape() if with_closure else (s.plasma_shape()[0], 0)
-        s.close()
-        torch.cuda.empty_cache()
-        return e0.elapsed_time(e1), fields, kt, shape
-
-    clocks = ClockSampler(gpu_uuid(local))
-    clocks.start()
-    ms_c, f_c, kt_c, (n_kin, n_cl) = timed(True)
-    clk = clocks.stop()
-    ms_k, f_k, kt_k, _ = timed(False)
-    err = {f: float(np.linalg.norm(f_c[f].astype(np.float64) - f_k[f]) / np.linalg.norm(f_k[f].astype(np.float64)))
-           for f in f_c}
-    ms_c = reduce_max(ms_c, world, f"cuda:{local}")
-    ms_k = reduce_max(ms_k, world, f"cuda:{local}")
+    """Learned J closure vs the kinetic solve on the same 8192^2 grid, with
+    the committed trained weights (see closure_config)."""
+    r = closure_config(args.steps, args.warmup, args.engine, not args.no_autotune, local)
+    ms_c = reduce_max(r["ms_per_step"] * args.steps, world, f"cuda:{local}")
     if rank != 0:
         return 0
     cells = cells_of(spec)
-    flops = 2 * (17 * 128 + 128 * 128 + 128) * n_cl
-    peaks = measured_peaks()
-    peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
-    achieved = flops / (kt_c["closure"] / 1e3) / 1e12 if kt_c["closure"] > 0 else 0.0
     line = {"metric": METRIC, "value": job_rate(cells * args.steps, world, ms_c / 1e3) / 1e9, "unit": UNIT,
-            "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
-            "data": "synthetic (seeded density fields; training data from kinetic runs)",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_c / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
+            "data": "synthetic (seeded density fields; weights trained on kinetic runs of seeded fields)",
             "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"]],
-                       "closure_engine": args.engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
-                       "training": {"runs": len(tspecs), "final_mse": hist[-1], "seconds": t_train},
+                       "closure_engine": args.engine, "closure_cells": r["closure_cells"],
+                       "kinetic_fallback_cells": r["kinetic_fallback_cells"], "weights": r["weights"],
                        "l2": "inputs larger than L2"},
-            "closure_vs_kinetic": {"kinetic_ms_per_step": ms_k / args.steps, "closure_ms_per_step": ms_c / args.steps,
-                                   "speedup": ms_k / ms_c, "field_rel_l2": err,
-                                   "kinetic_gcell_per_s": job_rate(cells * args.steps, world, ms_k / 1e3) / 1e9},
-            "kernel_ms": {"closure_run": kt_c, "kinetic_run": kt_k},
-            "roofline": {"bound": "tensor", "kernel": "k_closure", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "alg_flops_per_launch": flops, "launch_ms": kt_c["closure"],
-                         "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
-            "gpu_launches": step_launches(args.steps, 2 if n_kin else 1, False),
-            "clocks": clk}
+            "closure_vs_kinetic": r["closure_vs_kinetic"], "kernel_ms": r["kernel_ms"],
+            "launch_shapes": r["launch_shapes"], "roofline": r["roofline"],
+            "step_hbm_frac_algorithmic": r["step_hbm_frac_algorithmic"], "gpu_launches": r["gpu_launches"]}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -601,10 +813,7 @@ def batch_bench(args, specs, rank, world, local):
             "e2e": {"value": job_rate(cells * args.steps, world, te) / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps}}
     if world == 1 and not args.no_cpu_baseline:
-        g, psr, n, text, _, _ = oracle_throughput(args.workload, 10 ** 6, 2, budget_s=15.0)
-        line["cpu_baseline"] = {"value": g, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"{text}; {n} oracle steps in ~15 s, single thread",
-                                "phase_space_updates_per_s": psr}
+        line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -17,6 +17,11 @@
  *   4. E^{n+1} with the Yee curl, psi_e and the -dt/eps0 J^{n+1/2} term (Eq. 2-6).
  *   5. a soft source g(t^{n+1}) added at the source node(s).
  *   6. first-order Mur ends (1-D only).
+ * Threads: built plainly it is single-threaded.  Built with -fopenmp (the
+ * all-core CPU baseline) the per-cell field loops and the per-slot kinetic
+ * loop are shared among threads; every cell and slot is still computed by
+ * the same expressions in the same order, so both builds give identical
+ * results bit for bit.
  * Readings of the paper where it is garbled or silent (signs of the curl
  * coefficients, CPML kappa subscripts, psi time levels, the sign of e, the
  * velocity grids and the collision model) are the ones listed with the
@@ -40,6 +45,19 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads the step loops use (1 unless built with -fopenmp). */
+int64_t or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /* SI constants (CODATA 2018); e > 0 is the elementary charge magnitude. */
 #define OR_C0 299792458.0
@@ -541,9 +559,12 @@ static void kinetic_step(or_sim *s)
 {
     const int64_t nn = s->nnode;
     double *Ep = s->f[pol_component(&s->p)];
-    double *old = (double *)malloc(sizeof(double) * nn);
-    double *A = (double *)malloc(sizeof(double) * nn);
     const double dt = s->dt;
+#pragma omp parallel
+    {
+    double *old = (double *)malloc(sizeof(double) * nn);   /* scratch rows, one pair per thread */
+    double *A = (double *)malloc(sizeof(double) * nn);
+#pragma omp for schedule(static)
     for (int64_t q = 0; q < s->nslots; ++q) {
         const int64_t c = s->slot_cell[q];
         const double E = Ep[c];
@@ -594,6 +615,7 @@ static void kinetic_step(or_sim *s)
     }
     free(old);
     free(A);
+    }
 }
 
 /* ---------------------------------------------------------- field steps */
@@ -608,10 +630,12 @@ static void step1d(or_sim *s)
     const double dt = s->dt, dz = s->p.dx;
     const double mu0 = 1.0 / (OR_EPS0 * OR_C0 * OR_C0);
     /* H: mu0 dHy/dt = -(curl E)_y = -dEx/dz */
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < nz; ++k) hy[k] -= dt / (mu0 * dz) * (ex[k + 1] - ex[k]);
     const double e0 = ex[0], e1 = ex[1], en = ex[nz], enm1 = ex[nz - 1];
     kinetic_step(s);
     /* E: eps0 dEx/dt = (curl H)_x - Jx = -dHy/dz - Jx  (Eq. 1, 2, 6) */
+#pragma omp parallel for schedule(static)
     for (int64_t k = 1; k < nz; ++k)
         ex[k] += -dt / (OR_EPS0 * dz) * (hy[k] - hy[k - 1]) - dt / OR_EPS0 * s->jnode[k];
     if (s->p.src_kind) ex[s->p.src_k] += or_source(&s->p, (double)(s->step + 1) * dt);
@@ -631,6 +655,7 @@ static void step2d(or_sim *s)
     const double mu0 = 1.0 / (OR_EPS0 * OR_C0 * OR_C0);
     const int pml = s->p.cpml > 0;
     /* psi slots for 2-D: 0 psi_ez_x, 1 psi_ez_y, 2 psi_hx_y, 3 psi_hy_x */
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < ny; ++j)
         for (int64_t i = 0; i < nx; ++i) {
             double e = ez[ID2(i, j)];
@@ -650,6 +675,7 @@ static void step2d(or_sim *s)
         }
     kinetic_step(s);
     /* eps0 dEz/dt = dHy/dx - dHx/dy - Jz */
+#pragma omp parallel for schedule(static)
     for (int64_t j = 1; j < ny; ++j)
         for (int64_t i = 1; i < nx; ++i) {
             double dHx = hy[ID2(i, j)] - hy[ID2(i - 1, j)];
@@ -696,6 +722,7 @@ static void step3d(or_sim *s)
     const int pml = s->p.cpml > 0;
 #define EV(arr, i, j, k) (((i) < nx && (j) < ny && (k) < nz) ? arr[ID3(i, j, k)] : 0.0)
     /* H update:  mu0 dH/dt = -curl E */
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < nz; ++k)
         for (int64_t j = 0; j < ny; ++j)
             for (int64_t i = 0; i < nx; ++i) {
@@ -724,6 +751,7 @@ static void step3d(or_sim *s)
             }
     kinetic_step(s);
     /* E update:  eps0 dE/dt = curl H - J  (J on Ex only) */
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < nz; ++k)
         for (int64_t j = 0; j < ny; ++j)
             for (int64_t i = 0; i < nx; ++i) {

@@ -21,8 +21,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fdtd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
+_LIB_OMP = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 FIELDS = {"ex": 0, "ey": 1, "ez": 2, "hx": 3, "hy": 4, "hz": 5, "j": 6, "df": 7, "f0": 8}
 VGRID = {"signed1d": 0, "cart2d": 1, "speed3d": 2}
@@ -31,15 +33,18 @@ NU = {"nsv": 0, "const": 1, "table": 2}
 F0 = {"maxwell": 0, "druyvesteyn": 1}
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction)."""
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no fast-math, no FMA contraction);
+    omp=True builds the all-core variant of the same source (-fopenmp: the
+    per-cell and per-slot loops shared among threads, results identical)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    lib = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11"] +
+                              (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, lib)
+    return lib
 
 
 class Params(ctypes.Structure):
@@ -68,12 +73,12 @@ class Params(ctypes.Structure):
     ]
 
 
-def _load():
-    global _lib
+def _load(omp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = ctypes.CDLL(build())
+        if (_lib_omp if omp else _lib) is not None:
+            return _lib_omp if omp else _lib
+        lib = ctypes.CDLL(build(omp=omp))
         P = ctypes.POINTER(Params)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int64)
@@ -103,8 +108,18 @@ def _load():
         lib.or_source.argtypes = [P, ctypes.c_double]
         lib.or_kinetic_drive.argtypes = [P, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64, dp, dp, dp]
         lib.or_poynting.argtypes = [vp, ip, dp]
-        _lib = lib
+        lib.or_threads.restype = ctypes.c_int64
+        lib.or_threads.argtypes = []
+        if omp:
+            _lib_omp = lib
+        else:
+            _lib = lib
         return lib
+
+
+def threads(omp: bool = False) -> int:
+    """Threads the step loops of the (all-core) build use."""
+    return int(_load(omp).or_threads())
 
 
 def _dp(a: np.ndarray):
@@ -162,8 +177,8 @@ class Sim:
     """One oracle simulation.  ``density`` lives on the polarisation E nodes:
     length nz+1 (1-D Ex), nx*ny (2-D Ez) or nx*ny*nz (3-D Ex), x fastest."""
 
-    def __init__(self, p: Params, density: np.ndarray | None = None):
-        self._lib = _load()
+    def __init__(self, p: Params, density: np.ndarray | None = None, omp: bool = False):
+        self._lib = _load(omp)
         self.p = p
         self._dens = None if density is None else np.ascontiguousarray(density, dtype=np.float64).ravel()
         self._h = self._lib.or_create(ctypes.byref(p), None if self._dens is None else _dp(self._dens))

@@ -32,9 +32,9 @@ def oracle_params(O, spec):
     return O.params(**kw)
 
 
-def oracle_sim(O, spec):
+def oracle_sim(O, spec, omp: bool = False):
     p = spec.get("plasma")
-    return O.Sim(oracle_params(O, spec), None if p is None else p["density"])
+    return O.Sim(oracle_params(O, spec), None if p is None else p["density"], omp=omp)
 
 
 def rel_l2(a, b) -> float:
