@@ -303,7 +303,9 @@ def solver_config(workload: str, steps: int, warmup: int, autotune: bool, local:
             "phase_space_updates_per_s": ns * nn * steps / (ms / 1e3),
             "cells": cells, "plasma_cells": ns, "nodes_per_cell": nn, "f_dtype": spec["plasma"]["f_dtype"],
             "precision": spec["grid"].get("precision", "f32"), "kernel_ms": kt, "launch_shapes": shapes,
-            "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            # a 1-D grid (0.3 MB a step) stays in L2: its steps are bound by launch and L2 latency, not HBM
+            "roofline": {"bound": "latency" if spec["grid"]["ndim"] == 1 else "hbm", "kernel": kname,
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "alg_bytes_per_launch": alg, "launch_ms": kt["kinetic"],
                          "traffic": ncu_traffic(kname, workload, None if evolve else
                                                 (shapes["kin_vpl"], shapes["kin_l"]) if shapes["kin_vpl"] else (8, 32)),
