@@ -45,6 +45,8 @@ def parse():
                     help="2-D / 3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
+    ap.add_argument("--kin-shape", default="",
+                    help="VPL,L[,BPS]: force the kinetic kernel's launch shape after autotuning (profiling)")
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload at N = 1: skip the other configurations' entries (configs)")
     return ap.parse_args()
@@ -534,6 +536,9 @@ def main():
     st = s.stream
     s.set_option("fused_stencils", args.fused)
     tune = None if args.no_autotune else s.autotune()   # untimed: picks the launch shapes
+    if args.kin_shape:
+        v = [int(x) for x in args.kin_shape.split(",")] + [0]
+        s.set_option("kinetic_shape", v[0] * 1000000 + v[1] * 1000 + v[2])
     shapes = s.launch_shapes()                           # the shapes in use (tuned, cached or default)
 
     def barrier():

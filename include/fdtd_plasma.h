@@ -258,8 +258,13 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * planes / chunks are staged in shared memory by tensor copies.  The
  * autotuner sets it too (fdtd_tune_result.stencil_tz).  Results equal the
  * one-cell-per-thread kernels bit for bit.
+ * FDTD_OPT_KINETIC_SHAPE: the kinetic kernel's launch shape, value =
+ * vpl * 1000000 + l * 1000 + bps (vectors per lane, lanes per row, CTAs per
+ * SM cap or 0), which must be one of the row length's candidates (the ones
+ * fdtd_plasma_autotune times); 0 returns to the built-in default.  Needs a
+ * plasma (after set_plasma).  The autotuner overwrites it.
  * FDTD_ERR_INVAL for an unknown option or value. */
-enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2 };
+enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);
 
 /* The launch shapes the handle uses now (tuned, cached or default; kinetic

@@ -859,6 +859,25 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
         if (value > 0) { h->st_bx = 32; h->st_by = 8; h->st_bz = 1; h->st_cpt = 1; }
         return FDTD_OK;
     }
+    if (option == FDTD_OPT_KINETIC_SHAPE) {
+        if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "FDTD_OPT_KINETIC_SHAPE needs a plasma (set_plasma first)");
+        const int vpl = (int)(value / 1000000), l = (int)(value / 1000 % 1000), bps = (int)(value % 1000);
+        if (value != 0) {
+            int cand[32][2];
+            const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
+            bool ok = false;
+            for (int c = 0; c < nc; ++c) ok |= cand[c][0] == vpl && cand[c][1] == l;
+            if (value < 0 || !ok)
+                return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_KINETIC_SHAPE: %lld is not a candidate shape of this row length",
+                            (long long)value);
+        }
+        CK(h, cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        h->kin_vpl = vpl;
+        h->kin_l = l;
+        h->kin_bps = bps;
+        return FDTD_OK;
+    }
     return fail(h, FDTD_ERR_INVAL, "unknown option %d", option);
 }
 

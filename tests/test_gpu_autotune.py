@@ -50,3 +50,23 @@ def test_autotune_restores_state_and_caches(tmp_path, monkeypatch, kind):
         # other shapes (one or four cells per thread) differ only in rounding order
         assert rel_l2(s.read(n, device=False), ref.read(n, device=False)) <= 1e-5, n
         assert rel_l2(s.read(n, device=False), dflt.read(n, device=False)) <= 1e-5, n
+
+
+def test_forced_kinetic_shape(tmp_path, monkeypatch):
+    """FDTD_OPT_KINETIC_SHAPE: every candidate shape of the row length runs
+    and gives the default shape's fields to FP32 rounding order; a shape that
+    is not a candidate is refused."""
+    from paper_2211_05647_gb300 import FdtdError, Solver
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "none.txt"))
+    spec = spec_2d_cylinder(n=160, ny=120, R=30, center=(95, 60), src=(50, 60), steps=150, seed=2)
+    ref = Solver.from_spec(spec)
+    ref.step(150)
+    for vpl, l in ((8, 32), (16, 16)):
+        s = Solver.from_spec(spec)
+        s.set_option("kinetic_shape", vpl * 1000000 + l * 1000)
+        assert (s.launch_shapes()["kin_vpl"], s.launch_shapes()["kin_l"]) == (vpl, l)
+        s.step(150)
+        for n in FIELDS[2] + ["j"]:
+            assert rel_l2(s.read(n, device=False), ref.read(n, device=False)) <= 1e-5, (vpl, l, n)
+    with pytest.raises(FdtdError):
+        Solver.from_spec(spec).set_option("kinetic_shape", 3 * 1000000 + 5 * 1000)
