@@ -548,6 +548,62 @@ typedef struct {
 
 int fdtd_diagnostics_noalloc(const fdtd_diag_arrays *in, double *out, int out_is_device, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Domain decomposition (several GPUs, or several sub-domains on one).  The
+ * curl stencils (Sec. 2, Eq. 1-6) couple a cell only to its neighbours, so a
+ * grid splits along its slowest axis (y of a 2-D TMz grid, z of a 3-D one)
+ * into slabs that exchange one plane of tangential fields per half step: the
+ * H update of plane k needs E on plane k + 1 (Eq. 1), the E update of plane k
+ * needs H on plane k - 1 (Eq. 2-6).  The delta-f rows, the J moment and the
+ * Ampere term are cell-local and never move.
+ *
+ * fdtd_plasma_create_subdomain: a handle for the owned planes
+ *   [offset, offset + extent) of the global grid `global` along `axis`, plus
+ *   one ghost plane below (when offset > 0) and one above (when offset +
+ *   extent < n_global).  The split axis's CPML profile is the global one at the
+ *   planes' global positions, so a sub-domain computes its owned cells bit for
+ *   bit as the whole grid does.  set_source takes global coordinates (only the
+ *   owner of the source's plane keeps it); set_plasma takes the GLOBAL density
+ *   array (pol nodes of the whole grid) and keeps its owned planes, numbering
+ *   its plasma slots after the global slots below it (stochastic-rounding
+ *   draws equal the whole grid's); read/write_fields and FDTD_J/FDTD_DF cover
+ *   the local arrays, ghost planes included (local plane l is global plane
+ *   offset - (offset > 0) + l).  Not on sub-domains: the closure, the recorder,
+ *   ports, the fused stencil pass.  Errors: FDTD_ERR_INVAL (1-D grids, axis not
+ *   the slowest, extent < 2, range outside the axis), as fdtd_plasma_create.
+ * fdtd_plasma_step_half: half 0 = H^{n+1/2}; half 1 = delta f, J, E^{n+1}
+ *   (and the step counter).  A sub-domain with neighbours steps only this way
+ *   (fdtd_plasma_step returns FDTD_ERR_STATE):
+ *     unpack E from above; half 0; unpack H from below; half 1
+ *   with the neighbours' pack calls before each unpack.  Halves must
+ *   alternate, starting with 0 (FDTD_ERR_STATE otherwise).  Stream-ordered.
+ * fdtd_plasma_halo_pack / _unpack: copy a halo between the handle's fields and
+ *   a caller buffer of fdtd_plasma_halo_bytes(h, which) bytes (device:
+ *   stream-ordered on the handle's stream; host: synchronous).
+ *   FDTD_HALO_E: pack = the tangential E of the first owned plane (for the
+ *     neighbour below), unpack = into the ghost plane above (from the
+ *     neighbour above);
+ *   FDTD_HALO_H: pack = the tangential H of the last owned plane (for the
+ *     neighbour above), unpack = into the ghost plane below.
+ *   Layout: the components one after another (3-D: Ex, Ey or Hx, Hy planes of
+ *   nx * ny values; 2-D: the Ez or Hx row of nx values), field precision.
+ *   FDTD_ERR_STATE when the handle has no neighbour on that side or is not a
+ *   sub-domain. */
+typedef struct {
+    int32_t axis;          /* 1 (2-D grids, y) or 2 (3-D grids, z): the slowest axis */
+    int32_t reserved;
+    int64_t n_global;      /* cells of the global grid along the axis (= nz or ny of `global`) */
+    int64_t offset;        /* first owned cell along the axis */
+    int64_t extent;        /* owned cells along the axis (>= 2) */
+} fdtd_subdomain_desc;
+enum { FDTD_HALO_E = 0, FDTD_HALO_H = 1 };
+int fdtd_plasma_create_subdomain(const fdtd_grid_desc *global, const fdtd_subdomain_desc *sd,
+                                 const fdtd_runtime_desc *rt, fdtd_plasma_t *out);
+int fdtd_plasma_step_half(fdtd_plasma_t h, int half);
+size_t fdtd_plasma_halo_bytes(fdtd_plasma_t h, int which);
+int fdtd_plasma_halo_pack(fdtd_plasma_t h, int which, void *dst, int dst_is_device);
+int fdtd_plasma_halo_unpack(fdtd_plasma_t h, int which, const void *src, int src_is_device);
+
 /* Last error message of the handle (or of the last failed create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *fdtd_plasma_last_error(fdtd_plasma_t h);

@@ -267,6 +267,7 @@ KinArgs<T> kin_args(fdtd_plasma *h, int kstep)
     a.seed = h->pl.seed;
     a.d_step = h->d_step;
     a.kstep = kstep;
+    a.slot_base = h->slot_base;
     return a;
 }
 
@@ -679,7 +680,20 @@ int fp_set_global_error(int code, const char *msg)
 
 extern "C" {
 
-int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdtd_plasma_t *out)
+}  // extern "C"
+
+namespace {
+
+// Sub-domain of a grid decomposed along its slowest axis: the grid desc given
+// to create_impl is then the GLOBAL grid; the handle holds the owned planes
+// [offset, offset + extent) plus one ghost plane on each side that has a
+// neighbour.
+struct SubInfo {
+    int axis;
+    int64_t n_global, offset, extent;
+};
+
+int create_impl(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdtd_plasma_t *out, const SubInfo *sd)
 {
     if (!out) return fail(nullptr, FDTD_ERR_INVAL, "out is NULL");
     *out = nullptr;
@@ -691,6 +705,18 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     if (g->courant * g->courant * g->ndim >= 1.0)
         return fail(nullptr, FDTD_ERR_UNSTABLE, "Courant number %g violates S^2 ndim < 1", g->courant);
     int64_t n[3] = {g->ndim >= 2 ? g->nx : 1, g->ndim >= 2 ? g->ny : 1, g->ndim == 2 ? 1 : g->nz};
+    const int64_t n_full[3] = {n[0], n[1], n[2]};   // the global grid (= n unless a sub-domain)
+    int64_t sd_lo = 0, sd_hi = 0;
+    if (sd) {
+        // the slowest axis of the grid is split: y in 2-D (TMz), z in 3-D
+        if (g->ndim < 2 || sd->axis != g->ndim - 1)
+            return fail(nullptr, FDTD_ERR_INVAL, "sub-domains split 2-D grids along y (axis 1), 3-D grids along z (axis 2)");
+        if (sd->n_global != n[sd->axis] || sd->offset < 0 || sd->extent < 2 || sd->offset + sd->extent > sd->n_global)
+            return fail(nullptr, FDTD_ERR_INVAL, "sub-domain [offset, offset + extent) must lie in the global axis, extent >= 2");
+        sd_lo = sd->offset > 0 ? 1 : 0;
+        sd_hi = sd->offset + sd->extent < sd->n_global ? 1 : 0;
+        n[sd->axis] = sd->extent + sd_lo + sd_hi;
+    }
     for (int ax = 0; ax < 3; ++ax) {
         const bool used = (g->ndim == 1) ? ax == 2 : (g->ndim == 2 ? ax < 2 : true);
         if (used && (n[ax] < 3 || n[ax] > (int64_t)1 << 30))
@@ -703,7 +729,7 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     if (g->ndim >= 2 && g->mur) return fail(nullptr, FDTD_ERR_INVAL, "Mur ends are 1-D only");
     if (g->cpml_cells) {
         for (int ax = 0; ax < g->ndim; ++ax)
-            if (3 * (int64_t)g->cpml_cells >= n[ax])
+            if (3 * (int64_t)g->cpml_cells >= n_full[ax])
                 return fail(nullptr, FDTD_ERR_INVAL, "CPML thicker than a third of axis %d", ax);
         if (!(g->cpml_order > 0) || !(g->cpml_kappa_max >= 1.0) || !(g->cpml_sigma_factor >= 0) ||
             g->cpml_alpha_min < 0 || g->cpml_alpha_max < g->cpml_alpha_min)
@@ -718,6 +744,17 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     }
     if (!h) return fail(nullptr, FDTD_ERR_NOMEM, "host allocation failed");
     h->g = *g;
+    if (sd) {
+        h->sd_on = 1;
+        h->sd_axis = sd->axis;
+        h->sd_nglobal = sd->n_global;
+        h->sd_extent = sd->extent;
+        h->sd_lo = sd_lo;
+        h->sd_hi = sd_hi;
+        h->sd_origin = sd->offset - sd_lo;
+        if (sd->axis == 1) h->g.ny = n[1];     // the handle's grid desc is the local one
+        else h->g.nz = n[2];
+    }
     if (rt) h->rt = *rt;
     h->stream = (cudaStream_t)h->rt.stream;
     h->nx = n[0]; h->ny = n[1]; h->nz = n[2];
@@ -757,15 +794,17 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
         const int64_t L2 = 2 * (int64_t)g->cpml_cells;
         std::vector<double> tabs;
         for (int ax = 0; ax < g->ndim; ++ax) {
-            std::vector<double> b, a, ik;
-            cpml_axis(*g, h->dt, n[ax], false, b, a, ik);
-            tabs.insert(tabs.end(), b.begin(), b.end());
-            tabs.insert(tabs.end(), a.begin(), a.end());
-            tabs.insert(tabs.end(), ik.begin(), ik.end());
-            cpml_axis(*g, h->dt, n[ax], true, b, a, ik);
-            tabs.insert(tabs.end(), b.begin(), b.end());
-            tabs.insert(tabs.end(), a.begin(), a.end());
-            tabs.insert(tabs.end(), ik.begin(), ik.end());
+            // a sub-domain's split axis takes the global profile at its planes' global positions: its local
+            // layer planes that are not in a global layer get b = a = 0, 1/kappa = 1, so psi stays 0 there and
+            // the update equals the interior one exactly
+            const int64_t off = (h->sd_on && ax == h->sd_axis) ? h->sd_origin : 0;
+            for (int at_h = 0; at_h < 2; ++at_h) {
+                std::vector<double> b, a, ik;
+                cpml_axis(*g, h->dt, n_full[ax], at_h != 0, b, a, ik);
+                tabs.insert(tabs.end(), b.begin() + off, b.begin() + off + n[ax]);
+                tabs.insert(tabs.end(), a.begin() + off, a.begin() + off + n[ax]);
+                tabs.insert(tabs.end(), ik.begin() + off, ik.begin() + off + n[ax]);
+            }
         }
         h->prof_len = (int64_t)tabs.size();
         h->prof = dalloc(h, tabs.size() * h->esz);
@@ -813,6 +852,23 @@ int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdt
     return FDTD_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int fdtd_plasma_create(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdtd_plasma_t *out)
+{
+    return create_impl(g, rt, out, nullptr);
+}
+
+int fdtd_plasma_create_subdomain(const fdtd_grid_desc *global, const fdtd_subdomain_desc *sd,
+                                 const fdtd_runtime_desc *rt, fdtd_plasma_t *out)
+{
+    if (!sd) return fail(nullptr, FDTD_ERR_INVAL, "subdomain desc is NULL");
+    SubInfo si{sd->axis, sd->n_global, sd->offset, sd->extent};
+    return create_impl(global, rt, out, &si);
+}
+
 int fdtd_plasma_check_canaries(fdtd_plasma_t h, int64_t *corrupted)
 {
     NvtxRange nvtx_("fdtd_plasma_check_canaries");
@@ -839,6 +895,7 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
     if (!h) return FDTD_ERR_INVAL;
     if (option == FDTD_OPT_FUSED_STENCILS) {
         if (value != 0 && value != 1) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_FUSED_STENCILS takes 0 or 1");
+        if (value && h->sd_on) return fail(h, FDTD_ERR_STATE, "sub-domains exchange halos between the E and H passes");
         CK(h, cudaStreamSynchronize(h->stream));
         drop_graphs(h);
         h->fuse = (int)value;
@@ -916,6 +973,7 @@ int fdtd_plasma_reset(fdtd_plasma_t h)
     CK(h, cudaMemsetAsync(h->d_step, 0, sizeof(int64_t), h->stream));
     CK(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
     h->steps_done = 0;
+    h->sd_half = 0;
     return FDTD_OK;
 }
 
@@ -931,6 +989,20 @@ int fdtd_plasma_set_source(fdtd_plasma_t h, const fdtd_source_desc *s)
     if (!(s->tau > 0) || !std::isfinite(s->amp) || !std::isfinite(s->fc) || !std::isfinite(s->t0) || !std::isfinite(s->tau))
         return fail(h, FDTD_ERR_INVAL, "source parameters must be finite, tau > 0");
     const int nd = h->g.ndim;
+    fdtd_source_desc loc = *s;
+    if (h->sd_on) {
+        // global coordinates: a sub-domain keeps the source only when it owns the source's plane
+        int64_t &c = h->sd_axis == 1 ? loc.j : loc.k;
+        if (c < 1 || c >= h->sd_nglobal) return fail(h, FDTD_ERR_INVAL, "source node outside the updated nodes");
+        c -= h->sd_origin;
+        if (c < h->sd_lo || c >= h->sd_lo + h->sd_extent) {
+            h->src = *s;
+            h->has_source = 0;
+            drop_graphs(h);
+            return FDTD_OK;
+        }
+        s = &loc;
+    }
     if (s->location == FDTD_LOC_POINT) {
         bool ok;
         if (nd == 1) ok = s->k >= 1 && s->k <= h->nz - 1;
@@ -981,8 +1053,31 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     // density: compact the plasma cells
     const int64_t np = pol_len(h);
     std::vector<double> dens(np);
-    if (p->density_on_device) CK(h, cudaMemcpy(dens.data(), p->density, np * 8, cudaMemcpyDeviceToHost));
-    else std::memcpy(dens.data(), p->density, np * 8);
+    int64_t slot_base = 0;
+    if (h->sd_on) {
+        // a sub-domain reads its planes of the global density array; its slots are numbered after the
+        // global plasma slots below its first owned plane
+        const int64_t plane = h->sd_axis == 1 ? h->nx : h->nx * h->ny;
+        const int64_t npg = plane * h->sd_nglobal;
+        std::vector<double> all(npg);
+        if (p->density_on_device) CK(h, cudaMemcpy(all.data(), p->density, npg * 8, cudaMemcpyDeviceToHost));
+        else std::memcpy(all.data(), p->density, npg * 8);
+        const int64_t first = (h->sd_origin + h->sd_lo) * plane;
+        for (int64_t c = 0; c < first; ++c) {
+            const int64_t i = c % h->nx, j = (c / h->nx) % h->ny, k = c / plane;
+            const bool upd = h->sd_axis == 1 ? (i >= 1 && c / h->nx >= 1) : (j >= 1 && k >= 1);
+            if (all[c] > 0.0 && upd) ++slot_base;
+        }
+        std::memcpy(dens.data(), all.data() + h->sd_origin * plane, np * 8);
+        for (int64_t c = 0; c < np; ++c) {     // ghost planes carry no plasma
+            const int64_t l = c / plane;
+            if (l < h->sd_lo || l >= h->sd_lo + h->sd_extent) dens[c] = 0.0;
+        }
+    } else if (p->density_on_device) {
+        CK(h, cudaMemcpy(dens.data(), p->density, np * 8, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(dens.data(), p->density, np * 8);
+    }
     std::vector<int32_t> cells;
     std::vector<double> dslot;
     double nmax = 0.0;
@@ -1061,6 +1156,7 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
         return fail(h, FDTD_ERR_NOMEM, "plasma allocation failed (%zu cells x %d nodes)", ns, pitch);
     }
     h->has_plasma = 1;
+    h->slot_base = slot_base;
     h->nkin = (int64_t)ns;
     h->kin_vpl = h->kin_l = h->kin_bps = 0;
     apply_cached_kinetic(h);
@@ -1096,6 +1192,8 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
     NvtxRange nvtx_("fdtd_plasma_step");
     if (!h) return FDTD_ERR_INVAL;
     if (nsteps < 0) return fail(h, FDTD_ERR_INVAL, "nsteps < 0");
+    if (h->sd_on && (h->sd_lo || h->sd_hi || h->sd_half))
+        return fail(h, FDTD_ERR_STATE, "a sub-domain with neighbours steps by fdtd_plasma_step_half, exchanging halos");
     if (nsteps == 0) return FDTD_OK;
     if (!h->graphs_valid) {
         ensure_second_set(h);
@@ -1121,10 +1219,104 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
     return FDTD_OK;
 }
 
+int fdtd_plasma_step_half(fdtd_plasma_t h, int half)
+{
+    NvtxRange nvtx_("fdtd_plasma_step_half");
+    if (!h || (half != 0 && half != 1)) return FDTD_ERR_INVAL;
+    if (h->fuse) return fail(h, FDTD_ERR_STATE, "half steps do not run the fused stencil pass (FDTD_OPT_FUSED_STENCILS)");
+    if (half != h->sd_half)
+        return fail(h, FDTD_ERR_STATE, half ? "half 1 needs half 0 of the step first" : "half 1 of the step is pending");
+    const FieldSet<float> f32 = field_set<float>(h, 0);
+    const FieldSet<double> f64 = field_set<double>(h, 0);
+    const bool dbl = h->g.precision == FDTD_F64;
+    cudaError_t e;
+    if (half == 0) {
+        e = dbl ? part_h<double>(h, h->stream, 0, f64) : part_h<float>(h, h->stream, 0, f32);
+        if (e != cudaSuccess) return cuda_fail(h, e, "H half step");
+        h->sd_half = 1;
+        return FDTD_OK;
+    }
+    e = dbl ? part_mid<double>(h, h->stream, 0, f64, nullptr) : part_mid<float>(h, h->stream, 0, f32, nullptr);
+    if (e == cudaSuccess) e = dbl ? part_e<double>(h, h->stream, 0, f64) : part_e<float>(h, h->stream, 0, f32);
+    if (e == cudaSuccess) e = dbl ? part_ports<double>(h, h->stream, 0, f64) : part_ports<float>(h, h->stream, 0, f32);
+    if (e == cudaSuccess) {
+        launch_advance(h->stream, h->d_step, 1);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "E half step");
+    h->sd_half = 0;
+    h->steps_done += 1;
+    return FDTD_OK;
+}
+
+namespace {
+// the field planes a halo carries: 3-D (split along z) the x- and y-components of the plane, 2-D TMz (split
+// along y) Ez or Hx of the row; E: the tangential E the neighbour below needs for its H update, H: the
+// tangential H the neighbour above needs for its E update
+int halo_comps(const fdtd_plasma *h, int which, int comp[2])
+{
+    if (h->g.ndim == 3) {
+        comp[0] = which == FDTD_HALO_E ? FDTD_EX : FDTD_HX;
+        comp[1] = which == FDTD_HALO_E ? FDTD_EY : FDTD_HY;
+        return 2;
+    }
+    comp[0] = which == FDTD_HALO_E ? FDTD_EZ : FDTD_HX;
+    return 1;
+}
+
+int64_t halo_plane(const fdtd_plasma *h) { return h->g.ndim == 3 ? h->nx * h->ny : h->nx; }
+
+int halo_copy(fdtd_plasma *h, int which, bool pack, void *buf, int buf_is_device)
+{
+    if (!h || !buf || (which != FDTD_HALO_E && which != FDTD_HALO_H)) return FDTD_ERR_INVAL;
+    if (!h->sd_on) return fail(h, FDTD_ERR_STATE, "halos belong to sub-domains (fdtd_plasma_create_subdomain)");
+    // pack E: first owned plane (for the neighbour below); unpack E: top ghost plane (from the neighbour above);
+    // pack H: last owned plane (for the neighbour above); unpack H: bottom ghost plane (from the neighbour below)
+    const bool need_below = (which == FDTD_HALO_E) == pack;
+    if (need_below ? !h->sd_lo : !h->sd_hi)
+        return fail(h, FDTD_ERR_STATE, "no neighbour %s this sub-domain for that halo", need_below ? "below" : "above");
+    int64_t l;
+    if (which == FDTD_HALO_E) l = pack ? h->sd_lo : h->sd_lo + h->sd_extent;
+    else l = pack ? h->sd_lo + h->sd_extent - 1 : 0;
+    int comp[2];
+    const int nc = halo_comps(h, which, comp);
+    const size_t bytes = (size_t)halo_plane(h) * h->esz;
+    for (int q = 0; q < nc; ++q) {
+        char *field = static_cast<char *>(h->f[comp[q]]) + (size_t)l * bytes;
+        char *b = static_cast<char *>(buf) + (size_t)q * bytes;
+        const cudaMemcpyKind kind = buf_is_device ? cudaMemcpyDeviceToDevice
+                                                  : (pack ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+        CK(h, pack ? cudaMemcpyAsync(b, field, bytes, kind, h->stream) : cudaMemcpyAsync(field, b, bytes, kind, h->stream));
+    }
+    if (!buf_is_device) CK(h, cudaStreamSynchronize(h->stream));
+    return FDTD_OK;
+}
+}  // namespace
+
+size_t fdtd_plasma_halo_bytes(fdtd_plasma_t h, int which)
+{
+    if (!h || !h->sd_on || (which != FDTD_HALO_E && which != FDTD_HALO_H)) return 0;
+    int comp[2];
+    return (size_t)halo_comps(h, which, comp) * (size_t)halo_plane(h) * h->esz;
+}
+
+int fdtd_plasma_halo_pack(fdtd_plasma_t h, int which, void *dst, int dst_is_device)
+{
+    NvtxRange nvtx_("fdtd_plasma_halo_pack");
+    return halo_copy(h, which, true, dst, dst_is_device);
+}
+
+int fdtd_plasma_halo_unpack(fdtd_plasma_t h, int which, const void *src, int src_is_device)
+{
+    NvtxRange nvtx_("fdtd_plasma_halo_unpack");
+    return halo_copy(h, which, false, const_cast<void *>(src), src_is_device);
+}
+
 int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
 {
     NvtxRange nvtx_("fdtd_plasma_set_closure");
     if (!h || !c || !c->params) return FDTD_ERR_INVAL;
+    if (h->sd_on) return fail(h, FDTD_ERR_STATE, "the closure runs on whole grids, not on sub-domains");
     if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "set_closure needs a plasma (set_plasma first)");
     if (h->steps_done != 0) return fail(h, FDTD_ERR_STATE, "set_closure after stepping: call fdtd_plasma_reset first");
     if (h->g.precision != FDTD_F32) return fail(h, FDTD_ERR_INVAL, "the closure runs on FP32 grids");
@@ -1192,6 +1384,7 @@ int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity,
                               double rate, uint64_t seed)
 {
     if (!h) return FDTD_ERR_INVAL;
+    if (h->sd_on) return fail(h, FDTD_ERR_STATE, "the recorder runs on whole grids, not on sub-domains");
     if (!h->has_plasma || h->has_closure) return fail(h, FDTD_ERR_STATE, "recording needs a kinetic plasma, no closure");
     if (h->g.precision != FDTD_F32) return fail(h, FDTD_ERR_INVAL, "recording runs on FP32 grids");
     if (!samples || !count || capacity < 1 || !(rate > 0) || rate > 1)
@@ -1527,6 +1720,7 @@ int fdtd_plasma_set_ports(fdtd_plasma_t h, int32_t nports, const int64_t *port_o
 {
     NvtxRange nvtx_("fdtd_plasma_set_ports");
     if (!h) return FDTD_ERR_INVAL;
+    if (h->sd_on && nports) return fail(h, FDTD_ERR_STATE, "ports run on whole grids, not on sub-domains");
     if (nports == 0) {
         drop_graphs(h);
         free_ports(h);

@@ -110,6 +110,8 @@ struct KinArgs {
     uint64_t seed;
     const int64_t *d_step;     // steps done before the chunk
     int kstep;                 // step offset inside the chunk
+    int64_t slot_base;         // global index of slot 0 (a sub-domain's rows count the stochastic-rounding
+                               // draws like the whole grid's)
 };
 
 // Isotropic-F0 evolution (speed grid): per-node tables, each `pitch` long,
@@ -374,6 +376,12 @@ struct fdtd_plasma {
     double *d_src;            // g(t^{n+1}) of the step in flight
     int *d_err;               // device error word (bounded waits that gave up)
     int64_t steps_done;
+    // domain decomposition along the slowest axis (fdtd_plasma_create_subdomain; sd_on = 0: a whole grid):
+    // local plane l is global plane sd_origin + l; sd_lo / sd_hi ghost planes (0 or 1) below / above the
+    // sd_extent owned ones; sd_half: 1 between the two halves of a step (fdtd_plasma_step_half)
+    int sd_on, sd_axis, sd_half;
+    int64_t sd_nglobal, sd_origin, sd_extent, sd_lo, sd_hi;
+    int64_t slot_base;        // global plasma-slot index of local slot 0
     // plasma
     int has_plasma;
     fdtd_plasma_desc pl;

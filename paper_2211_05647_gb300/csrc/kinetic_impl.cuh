@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
         const int64_t row_next = row + nw * R;
         cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
         TA s = TA(0), c = TA(0);
-        if (valid) row_update<TS, TA, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)row, step, key, s, c);
+        if (valid) row_update<TS, TA, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)(row + a.slot_base), step, key, s, c);
         const TA J = row_reduce<TA, L>(s, c);
         if (valid && l == 0) {
             a.jslot[row] = J;

@@ -102,6 +102,14 @@ class fdtd_closure_desc(ctypes.Structure):
                 ("rho", ctypes.c_double), ("n_train_max", ctypes.c_double), ("beta", ctypes.c_double)]
 
 
+class fdtd_subdomain_desc(ctypes.Structure):
+    _fields_ = [("axis", ctypes.c_int32), ("reserved", ctypes.c_int32), ("n_global", ctypes.c_int64),
+                ("offset", ctypes.c_int64), ("extent", ctypes.c_int64)]
+
+
+HALO = {"e": 0, "h": 1}
+
+
 class fdtd_closure_scales_t(ctypes.Structure):
     _fields_ = [("e_scale", ctypes.c_double), ("j_scale", ctypes.c_double), ("n_scale", ctypes.c_double),
                 ("rho", ctypes.c_double), ("beta", ctypes.c_double)]
@@ -204,6 +212,12 @@ SIGNATURES = {
     "fdtd_batch_destroy": (None, [ctypes.c_void_p]),
     "fdtd_diagnostics_noalloc": (ctypes.c_int, [ctypes.POINTER(fdtd_diag_arrays), ctypes.POINTER(ctypes.c_double),
                                                 ctypes.c_int, ctypes.c_void_p]),
+    "fdtd_plasma_create_subdomain": (ctypes.c_int, [ctypes.POINTER(fdtd_grid_desc), ctypes.POINTER(fdtd_subdomain_desc),
+                                                    ctypes.POINTER(fdtd_runtime_desc), ctypes.POINTER(ctypes.c_void_p)]),
+    "fdtd_plasma_step_half": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "fdtd_plasma_halo_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int]),
+    "fdtd_plasma_halo_pack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
+    "fdtd_plasma_halo_unpack": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]),
     "fdtd_plasma_destroy": (None, [ctypes.c_void_p]),
 }
 
@@ -499,7 +513,9 @@ class Batch:
 class Solver:
     """Owns one ``fdtd_plasma_t``.  All work runs on the given torch stream."""
 
-    def __init__(self, grid: dict, device: int = 0, stream=None, torch_allocator: bool = True):
+    def __init__(self, grid: dict, device: int = 0, stream=None, torch_allocator: bool = True, subdomain=None):
+        """subdomain = (offset, extent): the owned planes of the grid's slowest
+        axis (fdtd_plasma_create_subdomain); `grid` is then the global grid."""
         import torch
         self.torch = torch
         self.lib = load_library()
@@ -507,17 +523,7 @@ class Solver:
         torch.cuda.set_device(self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.grid = dict(grid)
-        g = fdtd_grid_desc()
-        g.ndim = int(grid["ndim"])
-        g.precision = PRECISION[grid.get("precision", "f32")]
-        g.nx, g.ny, g.nz = int(grid.get("nx", 1)), int(grid.get("ny", 1)), int(grid.get("nz", 1))
-        g.dx, g.courant = float(grid["dx"]), float(grid.get("courant", 0.5))
-        g.cpml_cells, g.mur = int(grid.get("cpml_cells", 0)), int(grid.get("mur", 0))
-        g.cpml_order = float(grid.get("cpml_order", 3.0))
-        g.cpml_sigma_factor = float(grid.get("cpml_sigma_factor", 1.3))
-        g.cpml_kappa_max = float(grid.get("cpml_kappa_max", 7.0))
-        g.cpml_alpha_min = float(grid.get("cpml_alpha_min", 0.0))
-        g.cpml_alpha_max = float(grid.get("cpml_alpha_max", 0.05))
+        g = _grid_desc(grid)
         self._alloc = _TorchAllocator(self.device) if torch_allocator else None
         rt = fdtd_runtime_desc()
         rt.stream = self.stream.cuda_stream
@@ -525,15 +531,29 @@ class Solver:
             rt.alloc, rt.free = self._alloc.alloc_cb, self._alloc.free_cb
         rt.alloc_ctx = None
         h = ctypes.c_void_p()
-        rc = self.lib.fdtd_plasma_create(ctypes.byref(g), ctypes.byref(rt), ctypes.byref(h))
+        self.subdomain = None
+        if subdomain is None:
+            rc = self.lib.fdtd_plasma_create(ctypes.byref(g), ctypes.byref(rt), ctypes.byref(h))
+        else:
+            axis = int(grid["ndim"]) - 1
+            n_global = int(grid["ny"] if axis == 1 else grid["nz"])
+            off, ext = int(subdomain[0]), int(subdomain[1])
+            sd = fdtd_subdomain_desc(axis, 0, n_global, off, ext)
+            rc = self.lib.fdtd_plasma_create_subdomain(ctypes.byref(g), ctypes.byref(sd), ctypes.byref(rt),
+                                                       ctypes.byref(h))
+            lo, hi = int(off > 0), int(off + ext < n_global)
+            self.subdomain = dict(axis=axis, n_global=n_global, offset=off, extent=ext, lo=lo, hi=hi,
+                                  origin=off - lo, planes=ext + lo + hi)
         _check(self.lib, None, rc)
         self.h = h
         self.precision = grid.get("precision", "f32")
         self.f_dtype = None
 
     @classmethod
-    def from_spec(cls, spec: dict, device: int = 0, stream=None) -> "Solver":
-        s = cls(spec["grid"], device=device, stream=stream)
+    def from_spec(cls, spec: dict, device: int = 0, stream=None, subdomain=None) -> "Solver":
+        """subdomain = (offset, extent) makes a sub-domain of the spec's grid
+        (source and density stay global: the library keeps its part)."""
+        s = cls(spec["grid"], device=device, stream=stream, subdomain=subdomain)
         if spec.get("source"):
             s.set_source(**spec["source"])
         if spec.get("plasma") is not None:
@@ -596,6 +616,24 @@ class Solver:
     # ---- stepping
     def step(self, n: int = 1):
         _check(self.lib, self.h, self.lib.fdtd_plasma_step(self.h, int(n)))
+
+    def step_half(self, half: int):
+        """Half 0: H^{n+1/2}; half 1: delta f, J and E^{n+1} (fdtd_plasma_step_half)."""
+        _check(self.lib, self.h, self.lib.fdtd_plasma_step_half(self.h, int(half)))
+
+    def halo_bytes(self, which: str) -> int:
+        return self.lib.fdtd_plasma_halo_bytes(self.h, HALO[which])
+
+    def halo_pack(self, which: str, out):
+        """Copy halo `which` ("e": first owned plane's tangential E, "h": last
+        owned plane's tangential H) into the torch tensor `out` (device:
+        stream-ordered; host: synchronous)."""
+        _check(self.lib, self.h, self.lib.fdtd_plasma_halo_pack(self.h, HALO[which], out.data_ptr(), int(out.is_cuda)))
+        return out
+
+    def halo_unpack(self, which: str, buf):
+        """Write a neighbour's halo into the ghost plane ("e": above, "h": below)."""
+        _check(self.lib, self.h, self.lib.fdtd_plasma_halo_unpack(self.h, HALO[which], buf.data_ptr(), int(buf.is_cuda)))
 
     def time_kernels(self, n: int) -> dict:
         """Eager, event-timed steps: average ms per launch of each kernel."""
