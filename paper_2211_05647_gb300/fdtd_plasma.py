@@ -692,6 +692,10 @@ class Solver:
         nb = self.quantity_bytes(name)
         dt = self._dtype(name)
         n = nb // torch.empty((), dtype=dt).element_size()
+        if nb == 0:     # no plasma (J, delta f) on this grid or sub-domain
+            out = torch.empty((0, self.plasma_shape()[1]) if name in ("df", "f0") else 0, dtype=dt,
+                              device=self.device if device else "cpu")
+            return out if device else (out.float().numpy() if dt == torch.bfloat16 else out.numpy())
         if device:
             out = torch.empty(n, dtype=dt, device=self.device)
             _check(self.lib, self.h, self.lib.fdtd_plasma_read_fields(self.h, QUANTITY[name], out.data_ptr(), nb, 1))
