@@ -41,8 +41,6 @@ def parse():
     ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--engine", default="tcgen05", choices=["mma", "tcgen05"], help="closure MLP engine")
-    ap.add_argument("--closure-act", type=int, default=0, choices=[0, 1, 2],
-                    help="tcgen05 closure activation arithmetic: 0 FP32, 1 / 2 BF16 pairs in the first / both layers")
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="2-D / 3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -370,7 +368,7 @@ def batch_config(workload: str, specs, steps: int, warmup: int, autotune: bool, 
             "gpu_launches": 2 * (steps // chunk + (1 if rem else 0))}
 
 
-def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: int, act: int = 0) -> dict:
+def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: int) -> dict:
     """Learned closure vs the kinetic solve on the same 8192^2 grid: the
     trained weights are the committed ones (paper_2211_05647_gb300/data,
     written by train_closure.py with the library's own training kernels).
@@ -391,7 +389,6 @@ def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: 
         if with_closure:
             s.set_closure(w["params"], e_scale=w["e_scale"], j_scale=w["j_scale"], n_scale=w["n_scale"],
                           rho=w["rho"], beta=w["beta"], n_train_max=w["n_train_max"], engine=engine)
-            s.set_option("closure_activation", act)
         if autotune:
             s.autotune()
         shape = s.closure_shape() if with_closure else s.plasma_shape()
@@ -425,8 +422,8 @@ def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: 
     step_alg = 24 * cells + 84 * n_cl + 8 * n_kin * nn_k
     return {"workload": "2d_tmz_8192_closure", "steps": steps, "warmup": warmup, "run_steps": total,
             "ms_per_step": ms_step_c, "gcell_updates_per_s": cells * steps / (ms_c / 1e3) / 1e9,
-            "closure_engine": engine, "closure_activation": act, "closure_cells": n_cl,
-            "kinetic_fallback_cells": n_kin, "weights": {k: w["record"][k] for k in ("runs", "samples", "epochs", "batch") if k in w["record"]},
+            "closure_engine": engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
+            "weights": {k: w["record"][k] for k in ("runs", "samples", "epochs", "batch") if k in w["record"]},
             "closure_vs_kinetic": {"kinetic_ms_per_step": ms_k / steps, "closure_ms_per_step": ms_step_c,
                                    "speedup": ms_k / ms_c, "field_rel_l2_after_run": err,
                                    "kinetic_gcell_updates_per_s": cells * steps / (ms_k / 1e3) / 1e9,
@@ -456,7 +453,7 @@ def other_configs(args, local: int) -> dict:
                                                       local)),
         ("cfg4_batch1d_256_bf16", lambda: batch_config("batch1d_256_bf16", make_spec("batch1d_256_bf16"), K, W, auto,
                                                        local)),
-        ("cfg5_closure_8192", lambda: closure_config(K, W, args.engine, auto, local, args.closure_act)),
+        ("cfg5_closure_8192", lambda: closure_config(K, W, args.engine, auto, local)),
     ]
     clocks = ClockSampler(gpu_uuid(local))
     clocks.start()
@@ -676,7 +673,7 @@ def main():
 def closure_bench(args, spec, rank, world, local):
     """Learned J closure vs the kinetic solve on the same 8192^2 grid, with
     the committed trained weights (see closure_config)."""
-    r = closure_config(args.steps, args.warmup, args.engine, not args.no_autotune, local, args.closure_act)
+    r = closure_config(args.steps, args.warmup, args.engine, not args.no_autotune, local)
     ms_c = reduce_max(r["ms_per_step"] * args.steps, world, f"cuda:{local}")
     if rank != 0:
         return 0
@@ -708,7 +705,6 @@ def closure_cost_bench(args, spec, rank, world, local):
     params = (np.random.default_rng(20221201).standard_normal(18945) * 0.05).astype(np.float32)
     s.set_closure(params, e_scale=1.0, j_scale=1e-3, n_scale=1e18, rho=0.9, n_train_max=1e30, beta=1e-21,
                   engine=args.engine)
-    s.set_option("closure_activation", args.closure_act)
     n_kin, n_cl = s.closure_shape()
     s.step(max(args.warmup, 3))
     torch.cuda.synchronize()
@@ -734,8 +730,8 @@ def closure_cost_bench(args, spec, rank, world, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 fields, bf16 MLP operands",
             "data": "synthetic (seeded density field, seeded random closure weights)",
             "config": {"workload": args.workload, "grid": [spec["grid"]["nx"], spec["grid"]["ny"]],
-                       "closure_engine": args.engine, "closure_activation": args.closure_act, "closure_cells": n_cl,
-                       "kinetic_fallback_cells": n_kin, "l2": "inputs larger than L2"},
+                       "closure_engine": args.engine, "closure_cells": n_cl, "kinetic_fallback_cells": n_kin,
+                       "l2": "inputs larger than L2"},
             "kernel_ms": kt,
             "roofline": {"bound": "tensor", "kernel": "k_closure", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,

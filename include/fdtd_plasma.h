@@ -263,16 +263,8 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * SM cap or 0), which must be one of the row length's candidates (the ones
  * fdtd_plasma_autotune times); 0 returns to the built-in default.  Needs a
  * plasma (after set_plasma).  The autotuner overwrites it.
- * FDTD_OPT_CLOSURE_ACTIVATION (tcgen05 closure engine): 0 forms every GELU of
- * the network in FP32 with tanh.approx.f32 (default); 1 forms the first
- * hidden layer's activations on BF16 pairs (tanh.approx.bf16x2 and one BF16
- * fused multiply-add, their result being the next layer's BF16 operand); 2
- * does the same for both hidden layers.  1 and 2 add a few BF16 units in the
- * last place to each activation (network output within 1e-2 of the FP64
- * forward, like 0) for half the tanh instructions.
  * FDTD_ERR_INVAL for an unknown option or value. */
-enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3,
-       FDTD_OPT_CLOSURE_ACTIVATION = 4 };
+enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);
 
 /* The launch shapes the handle uses now (tuned, cached or default; kinetic

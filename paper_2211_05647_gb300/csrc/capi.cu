@@ -488,7 +488,6 @@ cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<
         c.d_step = h->d_step;
         c.kstep = kstep;
         c.engine = h->cl.engine;
-        c.act = h->cl_act;
         c.err = h->d_err;
         cudaError_t e = launch_closure(st, c, h->num_sms);
         if (e != cudaSuccess) return e;
@@ -915,13 +914,6 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
         drop_graphs(h);
         h->st_tz = (int)value;
         if (value > 0) { h->st_bx = 32; h->st_by = 8; h->st_bz = 1; h->st_cpt = 1; }
-        return FDTD_OK;
-    }
-    if (option == FDTD_OPT_CLOSURE_ACTIVATION) {
-        if (value < 0 || value > 2) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_CLOSURE_ACTIVATION takes 0, 1 or 2");
-        CK(h, cudaStreamSynchronize(h->stream));
-        drop_graphs(h);
-        h->cl_act = (int)value;
         return FDTD_OK;
     }
     if (option == FDTD_OPT_KINETIC_SHAPE) {

@@ -120,7 +120,6 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
 // tiles, one shared copy of the weights); thread r of a warpgroup owns row r
 // of its tile (history push, input row, J and E update).  If a bounded
 // MMA-completion wait gives up, *err is set and the warpgroup stops.
-template <int ACT>
 __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
 {
     pdl_enter();
@@ -159,7 +158,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
             x[16] = a.dens[slot] * a.inv_ns;
         }
         mlp_tc4_put_row(g, r, x);
-        const float y = mlp_tc4_tile<ACT>(s.w, g, gi, r, &phase, &ok);
+        const float y = mlp_tc4_tile(s.w, g, gi, r, &phase, &ok);
         if (!ok) break;
         if (valid) {
             const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * e + a.js * y;
@@ -178,14 +177,13 @@ cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
 {
     if (a.n == 0) return cudaSuccess;
     if (a.engine == 1) {
-        void (*kern)(ClosureArgs) = a.act == 2 ? k_closure_tc<2> : (a.act == 1 ? k_closure_tc<1> : k_closure_tc<0>);
         const size_t smem = sizeof(MlpTcSmem4);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_closure_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         // one CTA per SM: it allocates all 512 TMEM columns
         const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
         const int64_t grid = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, (int64_t)num_sms);
-        launch_pdl(kern, dim3((unsigned)std::max<int64_t>(grid, 1)), dim3(512), smem, st, a);
+        launch_pdl(k_closure_tc, dim3((unsigned)std::max<int64_t>(grid, 1)), dim3(512), smem, st, a);
         return cudaGetLastError();
     }
     const size_t smem = sizeof(MlpSmem);

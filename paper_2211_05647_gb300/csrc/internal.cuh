@@ -333,7 +333,6 @@ struct ClosureArgs {
     const int64_t *d_step;
     int kstep;
     int engine;        // 0: mma.sync warp tiles, 1: tcgen05 (TMEM accumulator)
-    int act;           // tcgen05 activation arithmetic: 0 FP32, 1 / 2 first / both hidden layers on BF16 pairs
     int *err;          // set to 1 if a bounded wait gave up
 };
 cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms);
@@ -401,7 +400,6 @@ struct fdtd_plasma {
     int64_t ncl;
     float *hist, *jprev, *params;
     fdtd_closure_desc cl;
-    int cl_act;               // FDTD_OPT_CLOSURE_ACTIVATION
     // training-data recorder
     // launch shapes (autotuner / cache): kinetic (vectors per lane, lanes per row, CTAs per SM; 0 = default),
     // stencil block (0 = default)

@@ -252,22 +252,6 @@ __device__ __forceinline__ float2 gelu2_f2(uint64_t z)
     return f2_split(f2_fma(z, f2(tanh_fast(uu.x), tanh_fast(uu.y)), z));
 }
 
-// 2 gelu(z) of two activations as one packed BF16 pair (the next layer's operand): u = z (C + C A z^2) on
-// two FP32 lanes, then tanh.approx.bf16x2 of u rounded to BF16, and z + z t as one BF16 fused multiply-add
-// of z rounded to BF16 -- one tanh instruction for two activations and no separate packing.  Its rounding
-// error (a few BF16 units in the last place) is of the size of the BF16 rounding of the activation itself.
-__device__ __forceinline__ uint32_t gelu2_bf16x2(uint64_t z)
-{
-    const float2 zz = f2_split(z);
-    const float2 u = f2_split(f2_mul(z, f2_fma(f2(kGeluCA, kGeluCA), f2_mul(z, z), f2(kGeluC, kGeluC))));
-    uint32_t ub, zb, tb, g;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(ub) : "f"(u.y), "f"(u.x));
-    asm("tanh.approx.bf16x2 %0, %1;" : "=r"(tb) : "r"(ub));
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(zb) : "f"(zz.y), "f"(zz.x));
-    asm("fma.rn.bf16x2 %0, %1, %2, %1;" : "=r"(g) : "r"(zb), "r"(tb));
-    return g;
-}
-
 // The epilogues form 2 gelu(z) = z + z tanh(u) (one multiply fewer than gelu); W2 and w3 are stored at
 // half scale to compensate.  Both scalings are by a power of two, so the BF16 operands and every product
 // equal those of the unscaled form exactly.
@@ -334,10 +318,7 @@ __device__ __forceinline__ void mlp_tc4_put_row(MlpTcGroup &g, int r, const floa
 
 // forward of warpgroup gi's tile (rows in g.x); thread r (0..127 inside the
 // warpgroup) gets row r's output.  Returns false in every thread of the
-// warpgroup if one of its bounded waits gave up.  ACT selects the activation
-// arithmetic: 0 FP32 (tanh.approx.f32), 1 the first hidden layer on
-// gelu2_bf16x2, 2 both hidden layers on it.
-template <int ACT>
+// warpgroup if one of its bounded waits gave up.
 __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, int gi, int r, uint32_t *phase,
                                               bool *ok_out)
 {
@@ -371,23 +352,15 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
             const int k0 = c * 32 + q * 8;
             const float4 ba = *reinterpret_cast<const float4 *>(&w.b1[k0]);
             const float4 bb = *reinterpret_cast<const float4 *>(&w.b1[k0 + 4]);
-            const uint64_t z0 = f2_add(f2(v[q * 8 + 0], v[q * 8 + 1]), f2(ba.x, ba.y));
-            const uint64_t z1 = f2_add(f2(v[q * 8 + 2], v[q * 8 + 3]), f2(ba.z, ba.w));
-            const uint64_t z2 = f2_add(f2(v[q * 8 + 4], v[q * 8 + 5]), f2(bb.x, bb.y));
-            const uint64_t z3 = f2_add(f2(v[q * 8 + 6], v[q * 8 + 7]), f2(bb.z, bb.w));
+            const float2 g0 = gelu2_f2(f2_add(f2(v[q * 8 + 0], v[q * 8 + 1]), f2(ba.x, ba.y)));
+            const float2 g1 = gelu2_f2(f2_add(f2(v[q * 8 + 2], v[q * 8 + 3]), f2(ba.z, ba.w)));
+            const float2 g2 = gelu2_f2(f2_add(f2(v[q * 8 + 4], v[q * 8 + 5]), f2(bb.x, bb.y)));
+            const float2 g3 = gelu2_f2(f2_add(f2(v[q * 8 + 6], v[q * 8 + 7]), f2(bb.z, bb.w)));
             uint4 pk;
-            if constexpr (ACT >= 1) {
-                pk.x = gelu2_bf16x2(z0);
-                pk.y = gelu2_bf16x2(z1);
-                pk.z = gelu2_bf16x2(z2);
-                pk.w = gelu2_bf16x2(z3);
-            } else {
-                const float2 g0 = gelu2_f2(z0), g1 = gelu2_f2(z1), g2 = gelu2_f2(z2), g3 = gelu2_f2(z3);
-                pk.x = pack_bf16(g0.x, g0.y);
-                pk.y = pack_bf16(g1.x, g1.y);
-                pk.z = pack_bf16(g2.x, g2.y);
-                pk.w = pack_bf16(g3.x, g3.y);
-            }
+            pk.x = pack_bf16(g0.x, g0.y);
+            pk.y = pack_bf16(g1.x, g1.y);
+            pk.z = pack_bf16(g2.x, g2.y);
+            pk.w = pack_bf16(g3.x, g3.y);
             *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
         }
     }
@@ -415,16 +388,8 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
         for (int i = 0; i < 32; i += 4) {
             const float4 b = *reinterpret_cast<const float4 *>(&w.b2[c * 32 + i]);
             const float4 o = *reinterpret_cast<const float4 *>(&w.w3[c * 32 + i]);
-            float2 g0, g1;
-            if constexpr (ACT >= 2) {
-                const uint32_t p0 = gelu2_bf16x2(f2_add(f2(v[i + 0], v[i + 1]), f2(b.x, b.y)));
-                const uint32_t p1 = gelu2_bf16x2(f2_add(f2(v[i + 2], v[i + 3]), f2(b.z, b.w)));
-                g0 = make_float2(__uint_as_float(p0 << 16), __uint_as_float(p0 & 0xffff0000u));
-                g1 = make_float2(__uint_as_float(p1 << 16), __uint_as_float(p1 & 0xffff0000u));
-            } else {
-                g0 = gelu2_f2(f2_add(f2(v[i + 0], v[i + 1]), f2(b.x, b.y)));
-                g1 = gelu2_f2(f2_add(f2(v[i + 2], v[i + 3]), f2(b.z, b.w)));
-            }
+            const float2 g0 = gelu2_f2(f2_add(f2(v[i + 0], v[i + 1]), f2(b.x, b.y)));
+            const float2 g1 = gelu2_f2(f2_add(f2(v[i + 2], v[i + 3]), f2(b.z, b.w)));
             y = fmaf(g0.x, o.x, y);
             y = fmaf(g0.y, o.y, y);
             y = fmaf(g1.x, o.z, y);

@@ -657,10 +657,8 @@ class Solver:
     def set_option(self, option: str, value: int):
         """Runtime option: "fused_stencils" (0 / 1, default 0; FDTD_OPT_FUSED_STENCILS),
         "stencil_tz" (0 / planes per block of the TMA column stencils; FDTD_OPT_STENCIL_TZ) or
-        "kinetic_shape" (vpl * 1000000 + l * 1000 + bps, 0 = default; FDTD_OPT_KINETIC_SHAPE) or
-        "closure_activation" (0 FP32, 1 / 2 BF16 pairs in the first / both hidden layers;
-        FDTD_OPT_CLOSURE_ACTIVATION)."""
-        code = {"fused_stencils": 1, "stencil_tz": 2, "kinetic_shape": 3, "closure_activation": 4}[option]
+        "kinetic_shape" (vpl * 1000000 + l * 1000 + bps, 0 = default; FDTD_OPT_KINETIC_SHAPE)."""
+        code = {"fused_stencils": 1, "stencil_tz": 2, "kinetic_shape": 3}[option]
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_option(self.h, code, int(value)))
 
     def launch_shapes(self) -> dict:

@@ -160,16 +160,14 @@ def test_closure_constant_network():
     assert np.allclose(J, want, rtol=1e-5)
 
 
-@pytest.mark.parametrize("engine,act", [("mma", 0), ("tcgen05", 0), ("tcgen05", 1), ("tcgen05", 2)])
-def test_closure_inference_matches_oracle_forward(engine, act):
+@pytest.mark.parametrize("engine", ["mma", "tcgen05"])
+def test_closure_inference_matches_oracle_forward(engine):
     """In-solver closure: after stepping, J of every closure cell equals
     rho J_prev + beta n E^n + J_s MLP(x) with x rebuilt from the E history it
-    saw (FP64 oracle forward); act = the tcgen05 activation arithmetic (FP32,
-    BF16 pairs in the first / both hidden layers)."""
+    saw (FP64 oracle forward)."""
     from paper_2211_05647_gb300 import Solver
     spec = _closure_spec()
     s = Solver.from_spec(spec)
-    s.set_option("closure_activation", act)
     flat = _flat_params(11, scale=0.5)
     dens = spec["plasma"]["density"]
     cells = np.nonzero(dens > 0)[0]
@@ -189,7 +187,7 @@ def test_closure_inference_matches_oracle_forward(engine, act):
             y, _ = M.forward(_oracle_params(flat), x)
             want = rho * Jprev + beta * dens[cells] * hist[-1] + j_s * y
             err = rel_l2(J, want)
-            print(f"closure ({engine}, activation {act}) J vs oracle forward: {err:.3e}")
+            print(f"closure ({engine}) J vs oracle forward: {err:.3e}")
             assert err <= 1e-2
         Jprev = J
     assert s.diagnostics()["finite"]
