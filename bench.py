@@ -438,6 +438,41 @@ def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: 
             "gpu_launches": step_launches(steps, 2 if n_kin else 1, False)}
 
 
+def training_config(local: int, n: int = 1 << 20, batch: int = 4096, epochs: int = 3) -> dict:
+    """Closure training throughput: `epochs` epochs of minibatch Adam
+    (fdtd_mlp_train_epoch: gather, forward + backward on BF16 tensor-core
+    tiles, Adam) over n seeded synthetic samples, timed with CUDA events after
+    one untimed epoch."""
+    import torch
+    from paper_2211_05647_gb300 import MlpTrainer
+    from paper_2211_05647_gb300 import closure as C
+    g = torch.Generator(device="cpu").manual_seed(11)
+    x = torch.randn(n, 17, generator=g).to(f"cuda:{local}")
+    t = torch.randn(n, generator=g).to(f"cuda:{local}")
+    tr = MlpTrainer(C.init_params(3, x.device), batch, lr=1e-3)
+    nb = n // batch
+    tr.epoch(x, t, 7, 0, 0, (epochs + 1) * nb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for ep in range(1, epochs + 1):
+        tr.epoch(x, t, 7, ep, ep * nb, (epochs + 1) * nb)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    samples = epochs * nb * batch
+    # per sample: forward 2 (17*128 + 128*128 + 128), backward 2 (128*128 + 128*128 + 17*128) multiply-adds
+    flop = 2 * (17 * 128 + 128 * 128 + 128) + 2 * (2 * 128 * 128 + 17 * 128)
+    tf = samples * flop / (ms / 1e3) / 1e12
+    pk, src = _peak("bf16_tflops_sustained", 1700.0)
+    del x, t, tr
+    _release()
+    return {"samples_per_s": samples / (ms / 1e3), "ms_per_batch_step": ms / (epochs * nb), "batch": batch,
+            "samples": n, "epochs_timed": epochs, "alg_flop_per_sample": flop, "tflops": tf,
+            "roofline": {"bound": "tensor", "kernel": "k_mlp_train_tile", "achieved": tf, "peak": pk,
+                         "unit": "TFLOP/s", "frac": tf / pk, "peak_source": src}}
+
+
 def other_configs(args, local: int) -> dict:
     """The other configurations of the benchmark, each at its full size: the
     1-D FP64 slab (its full 2000 steps: a few microseconds each), the 3-D 512^3
@@ -454,6 +489,7 @@ def other_configs(args, local: int) -> dict:
         ("cfg4_batch1d_256_bf16", lambda: batch_config("batch1d_256_bf16", make_spec("batch1d_256_bf16"), K, W, auto,
                                                        local)),
         ("cfg5_closure_8192", lambda: closure_config(K, W, args.engine, auto, local)),
+        ("closure_training", lambda: training_config(local)),
     ]
     clocks = ClockSampler(gpu_uuid(local))
     clocks.start()

@@ -393,8 +393,11 @@ int fdtd_plasma_set_recording(fdtd_plasma_t h, float *samples, int64_t capacity,
  * buffers (stream-ordered on `stream`):
  *   forward  : y[b] = MLP(x[b]) for x [batch][17]
  *   loss_grad: loss = mean (y - target)^2 and its gradient (packed like the
- *              parameters, overwritten) -- BF16 tensor-core forward, FP32
- *              backward; workspace of fdtd_mlp_workspace_bytes(batch) bytes
+ *              parameters, overwritten) -- forward and backward contractions
+ *              on BF16 tensor-core tiles with FP32 accumulation, one CTA per
+ *              128-row tile, the tiles' gradients summed in a fixed order
+ *              (deterministic); workspace of fdtd_mlp_workspace_bytes(batch)
+ *              bytes (one gradient per tile: about 74 KB per 128 rows)
  *   adam     : one Adam step (Kingma & Ba, bias-corrected, step count t >= 1)
  *              on params with first / second moments m, v. */
 size_t fdtd_mlp_workspace_bytes(int64_t batch);

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
                 *reinterpret_cast<uint32_t *>(&s.x[r][k]) = pack_bf16(x[k], x[k + 1]);
         }
         __syncthreads();
-        mlp_tile_forward(s, nullptr);
+        mlp_tile_forward(s);
         __syncthreads();
         if (r < kMlpRows) {
             const int64_t slot = row0 + r;

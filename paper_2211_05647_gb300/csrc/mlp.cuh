@@ -102,17 +102,9 @@ __device__ __forceinline__ void mlp_load_weights(MlpSmem &s, const float *__rest
     if (threadIdx.x == 0) s.b3 = P[kOffB3];
 }
 
-// Optional per-element outputs of the forward pass (training): pre- and
-// post-activation values of both hidden layers, FP32, [row][128] with row
-// counted from `row0` (rows >= nrows are not written).
-struct MlpTrace {
-    float *z1, *h1, *z2, *h2;
-    int64_t row0, nrows;
-};
-
 // Forward pass of the 128-row tile in s.x; y[row] lands in s.y.  Requires a
 // __syncthreads() between writing s.x and the call and before reading s.y.
-__device__ __forceinline__ void mlp_tile_forward(MlpSmem &s, const MlpTrace *trace)
+__device__ __forceinline__ void mlp_tile_forward(MlpSmem &s)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
@@ -142,21 +134,6 @@ __device__ __forceinline__ void mlp_tile_forward(MlpSmem &s, const MlpTrace *tra
         const uint32_t p0 = pack_bf16(gelu_f(z00), gelu_f(z01)), p1 = pack_bf16(gelu_f(z10), gelu_f(z11));
         *reinterpret_cast<uint32_t *>(&s.h1[r0 + g][col]) = p0;
         *reinterpret_cast<uint32_t *>(&s.h1[r0 + g + 8][col]) = p1;
-        if (trace) {
-            const int64_t ra = trace->row0 + r0 + g, rb = ra + 8;
-            const __nv_bfloat162 q0 = *reinterpret_cast<const __nv_bfloat162 *>(&p0);
-            const __nv_bfloat162 q1 = *reinterpret_cast<const __nv_bfloat162 *>(&p1);
-            if (ra < trace->nrows) {
-                *reinterpret_cast<float2 *>(trace->z1 + ra * kMlpH + col) = make_float2(z00, z01);
-                *reinterpret_cast<float2 *>(trace->h1 + ra * kMlpH + col) =
-                    make_float2(__bfloat162float(q0.x), __bfloat162float(q0.y));
-            }
-            if (rb < trace->nrows) {
-                *reinterpret_cast<float2 *>(trace->z1 + rb * kMlpH + col) = make_float2(z10, z11);
-                *reinterpret_cast<float2 *>(trace->h1 + rb * kMlpH + col) =
-                    make_float2(__bfloat162float(q1.x), __bfloat162float(q1.y));
-            }
-        }
     }
     __syncwarp();
     // ---- layer 2: [16 x 128] x [128 x 128]; a warp reads only its own h1 rows
@@ -184,17 +161,6 @@ __device__ __forceinline__ void mlp_tile_forward(MlpSmem &s, const MlpTrace *tra
         const float h00 = gelu_f(z00), h01 = gelu_f(z01), h10 = gelu_f(z10), h11 = gelu_f(z11);
         y0 += h00 * s.w3[col] + h01 * s.w3[col + 1];
         y1 += h10 * s.w3[col] + h11 * s.w3[col + 1];
-        if (trace) {
-            const int64_t ra = trace->row0 + r0 + g, rb = ra + 8;
-            if (ra < trace->nrows) {
-                *reinterpret_cast<float2 *>(trace->z2 + ra * kMlpH + col) = make_float2(z00, z01);
-                *reinterpret_cast<float2 *>(trace->h2 + ra * kMlpH + col) = make_float2(h00, h01);
-            }
-            if (rb < trace->nrows) {
-                *reinterpret_cast<float2 *>(trace->z2 + rb * kMlpH + col) = make_float2(z10, z11);
-                *reinterpret_cast<float2 *>(trace->h2 + rb * kMlpH + col) = make_float2(h10, h11);
-            }
-        }
     }
     y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
     y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
