@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
                                               key, sm, cm);
                 const T J = row_reduce<T, L>(sm, cm);
                 if (cur.valid && l == 0) {
-                    a.jslot[cur.grow] = J;
+                    if (s == a.nsteps - 1) a.jslot[cur.grow] = J;   // J is read between launches only
                     E[cur.node] = cur.e - a.cj * J;
                 }
                 cur = nxt;

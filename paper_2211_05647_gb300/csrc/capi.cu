@@ -268,6 +268,7 @@ KinArgs<T> kin_args(fdtd_plasma *h, int kstep)
     a.d_step = h->d_step;
     a.kstep = kstep;
     a.slot_base = h->slot_base;
+    a.store_j = 1;
     return a;
 }
 
@@ -432,9 +433,12 @@ cudaError_t part_h(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T>
     return cudaGetLastError();
 }
 
-// the work between the H and E updates: E-history push, kinetic update (E -= dt/eps0 J), closure, recorder
+// the work between the H and E updates: E-history push, kinetic update (E -= dt/eps0 J), closure, recorder.
+// J^{n+1/2} per slot is stored on the last step of a sequence (what read_fields and checkpoints see between
+// step calls) and on every step while the recorder, which reads it, is on.
 template <typename T>
-cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs, cudaEvent_t *ev)
+cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<T> &fs, cudaEvent_t *ev,
+                     bool last = true)
 {
     T *E = fs.f[pol_comp(h)];
     const bool rec = h->has_recording && sizeof(T) == 4;
@@ -443,6 +447,7 @@ cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<
     if (h->has_plasma && h->nkin > 0) {
         KinArgs<T> a = kin_args<T>(h, kstep);
         a.E = E;
+        a.store_j = last || rec;
         cudaError_t e;
         if (h->pl.evolve_f0) {
             const double vth = std::sqrt(kQe * h->pl.te_ev / kMe);
@@ -609,9 +614,9 @@ cudaError_t enqueue_seq(fdtd_plasma *h, cudaStream_t st, int nsteps)
     if (e != cudaSuccess) return e;
     for (int k = 0; k < nsteps; ++k) {
         const FieldSet<T> fs = field_set<T>(h, set);
-        e = part_mid<T>(h, st, k, fs, nullptr);
-        if (e != cudaSuccess) return e;
         const bool last = k == nsteps - 1;
+        e = part_mid<T>(h, st, k, fs, nullptr, last);
+        if (e != cudaSuccess) return e;
         if (!last && fuse && k >= unfused_first) {
             const FieldSet<T> to = field_set<T>(h, set ^ 1);
             const double mu0 = 1.0 / (kEps0 * kC0 * kC0);

@@ -112,6 +112,8 @@ struct KinArgs {
     int kstep;                 // step offset inside the chunk
     int64_t slot_base;         // global index of slot 0 (a sub-domain's rows count the stochastic-rounding
                                // draws like the whole grid's)
+    int store_j;               // k_kinetic: store J^{n+1/2} per slot (the last step of a sequence, or
+                               // when something reads it every step); E is updated either way
 };
 
 // Isotropic-F0 evolution (speed grid): per-node tables, each `pitch` long,

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
         if (valid) row_update<TS, TA, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)(row + a.slot_base), step, key, s, c);
         const TA J = row_reduce<TA, L>(s, c);
         if (valid && l == 0) {
-            a.jslot[row] = J;
+            if (a.store_j) a.jslot[row] = J;
             a.E[cell] = E - a.cj * J;
         }
     }
