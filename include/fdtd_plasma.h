@@ -438,12 +438,16 @@ int fdtd_mlp_adam(float *params, const float *grad, float *m, float *v, int64_t 
  *   copied to xb [batch][17], tb [batch]; needs first + batch <= n.
  * fdtd_mlp_train_epoch: one epoch of minibatch training: for each of the
  *   n / batch full batches of the epoch's permuted order (the ragged tail is
- *   left out), gather, fdtd_mlp_loss_grad, and fdtd_mlp_adam with step count
- *   iter0 + b + 1 and the cosine-decayed rate lr (1 + cos(pi (iter0 + b) /
- *   total_iters)) / 2.  *loss_mean (device double) receives the mean of the
- *   batch losses.  grad, m, v: FDTD_MLP_NPARAMS floats each (m, v zeroed by
- *   the caller before the first epoch); workspace of
- *   fdtd_mlp_train_workspace_bytes(batch) bytes.  Nothing is synchronised. */
+ *   left out), the same loss and gradient as fdtd_mlp_loss_grad on the rows
+ *   fdtd_mlp_gather would give, then the Adam step of fdtd_mlp_adam with step
+ *   count iter0 + b + 1 and the cosine-decayed rate lr (1 + cos(pi (iter0 + b)
+ *   / total_iters)) / 2 -- bit for bit those calls, in two kernel launches a
+ *   batch (the rows are read through the permutation; the tiles' gradients
+ *   are summed and applied in one kernel).  *loss_mean (device double)
+ *   receives the mean of the batch losses.  m, v: FDTD_MLP_NPARAMS floats
+ *   each (zeroed by the caller before the first epoch); grad is not used (may
+ *   be NULL); workspace of fdtd_mlp_train_workspace_bytes(batch) bytes.
+ *   Nothing is synchronised. */
 typedef struct {
     double e_scale, j_scale, n_scale, rho, beta;
 } fdtd_closure_scales_t;

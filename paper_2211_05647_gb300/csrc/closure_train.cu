@@ -1,7 +1,7 @@
 // closure_train.cu -- the learned closure's training pipeline on the GPU: the
 // normalisation and Drude part from recorded samples, the network's inputs and
-// residual targets, the initial weights, shuffled minibatches and one call per
-// training epoch (gather, loss and gradient, Adam with a cosine-decayed rate).
+// residual targets, the initial weights and shuffled minibatches (the training
+// epoch itself is in mlp_train.cu).
 //
 // A recorded sample is 19 floats [E^{n-15} .. E^n, n, J^{n+1/2}, J^{n-1/2}].
 // The closure keeps the Crank-Nicolson update of a Drude plasma with the mean
@@ -19,6 +19,7 @@
 #include <cstdio>
 
 #include "mlp.cuh"
+#include "shuffle.cuh"
 
 namespace fp {
 
@@ -113,43 +114,6 @@ __global__ void k_mlp_init(float *__restrict__ P, uint64_t seed)
     P[i] = v;
 }
 
-// Seeded permutation of [0, n) for one epoch: a four-round balanced Feistel
-// network on 2*half bits (round function Philox4x32-7 keyed by the seed and
-// counted by (right half, round, epoch)), which is a bijection of
-// [0, 2^(2 half)), restricted to [0, n) by cycle walking (apply it again
-// while the value is >= n).  The walk from a start below n ends at the first
-// element of its cycle below n, after at most 2^(2 half) - n + 1 applications.
-struct Perm {
-    uint64_t n, limit;
-    int half;
-    uint32_t mask;
-    uint2 key;
-    uint32_t ep_lo, ep_hi;
-};
-
-__device__ __forceinline__ uint64_t feistel(uint64_t x, const Perm &p)
-{
-    uint32_t L = (uint32_t)(x >> p.half), R = (uint32_t)(x & p.mask);
-#pragma unroll
-    for (uint32_t round = 0; round < 4; ++round) {
-        const uint4 h = philox4x32_7(make_uint4(R, round, p.ep_lo, p.ep_hi), p.key);
-        const uint32_t nl = R;
-        R = (L ^ h.x) & p.mask;
-        L = nl;
-    }
-    return ((uint64_t)L << p.half) | R;
-}
-
-__device__ __forceinline__ uint64_t perm_index(uint64_t i, const Perm &p)
-{
-    uint64_t x = i;
-    for (uint64_t it = 0; it < p.limit; ++it) {
-        x = feistel(x, p);
-        if (x < p.n) break;
-    }
-    return x;
-}
-
 // rows first .. first + batch - 1 of the epoch's permuted order
 __global__ void k_mlp_gather(const float *__restrict__ x, const float *__restrict__ t, Perm p, int64_t first,
                              int64_t batch, float *__restrict__ xb, float *__restrict__ tb)
@@ -162,28 +126,6 @@ __global__ void k_mlp_gather(const float *__restrict__ x, const float *__restric
 #pragma unroll
     for (int k = 0; k < kMlpIn; ++k) xd[k] = xs[k];
     tb[i] = t[src];
-}
-
-__global__ void k_loss_accum(const float *__restrict__ loss, double scale, double *__restrict__ acc)
-{
-    if (threadIdx.x == 0 && blockIdx.x == 0) *acc += (double)*loss * scale;
-}
-
-Perm make_perm(int64_t n, uint64_t seed, int64_t epoch)
-{
-    Perm p{};
-    p.n = (uint64_t)n;
-    int bits = 0;
-    while (bits < 62 && (1ull << bits) < (uint64_t)n) ++bits;
-    bits = std::max(bits, 2);
-    bits += bits & 1;
-    p.half = bits / 2;
-    p.mask = (uint32_t)((1ull << p.half) - 1);
-    p.limit = (1ull << bits) - (uint64_t)n + 1;
-    p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    p.ep_lo = (uint32_t)epoch;
-    p.ep_hi = (uint32_t)((uint64_t)epoch >> 32);
-    return p;
 }
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -263,50 +205,6 @@ int fdtd_mlp_gather(const float *x, const float *t, int64_t n, uint64_t seed, in
     k_mlp_gather<<<(unsigned)((batch + 255) / 256), 256, 0, (cudaStream_t)stream>>>(x, t, make_perm(n, seed, epoch),
                                                                                  first, batch, xb, tb);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
-    return FDTD_OK;
-}
-
-size_t fdtd_mlp_train_workspace_bytes(int64_t batch)
-{
-    if (batch < 1) return 0;
-    return align256(fdtd_mlp_workspace_bytes(batch)) + align256((size_t)batch * kMlpIn * sizeof(float)) +
-           align256((size_t)batch * sizeof(float)) + align256(sizeof(float)) + 256;
-}
-
-int fdtd_mlp_train_epoch(float *params, float *grad, float *m, float *v, const float *x, const float *t, int64_t n,
-                         int64_t batch, uint64_t seed, int64_t epoch, int64_t iter0, int64_t total_iters, double lr,
-                         double beta1, double beta2, double eps, double *loss_mean, void *workspace,
-                         size_t workspace_bytes, void *stream)
-{
-    if (!params || !grad || !m || !v || !x || !t || !loss_mean || !workspace || batch < 1 || n < batch ||
-        n > (int64_t)1 << 40 ||
-        epoch < 0 || iter0 < 0 || total_iters < 1 || !(lr > 0) || !std::isfinite(lr))
-        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_train_epoch: bad argument (need n >= batch >= 1)");
-    if (workspace_bytes < fdtd_mlp_train_workspace_bytes(batch))
-        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_train_epoch: workspace too small");
-    cudaStream_t st = (cudaStream_t)stream;
-    unsigned char *w = reinterpret_cast<unsigned char *>(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
-    const size_t lg_bytes = align256(fdtd_mlp_workspace_bytes(batch));
-    void *lg = w;
-    float *xb = reinterpret_cast<float *>(w + lg_bytes);
-    float *tb = reinterpret_cast<float *>(w + lg_bytes + align256((size_t)batch * kMlpIn * sizeof(float)));
-    float *loss = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(tb) + align256((size_t)batch * sizeof(float)));
-    cudaError_t e = cudaMemsetAsync(loss_mean, 0, sizeof(double), st);
-    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
-    const int64_t nb = n / batch;   // the ragged tail of the permuted order is left out this epoch
-    const Perm p = make_perm(n, seed, epoch);
-    for (int64_t b = 0; b < nb; ++b) {
-        k_mlp_gather<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(x, t, p, b * batch, batch, xb, tb);
-        int rc = fdtd_mlp_loss_grad(params, xb, tb, batch, grad, loss, lg, lg_bytes, st);
-        if (rc != FDTD_OK) return rc;
-        const int64_t it = iter0 + b;
-        const double lr_t = lr * 0.5 * (1.0 + std::cos(kPi * (double)std::min(it, total_iters) / (double)total_iters));
-        rc = fdtd_mlp_adam(params, grad, m, v, kMlpNParams, it + 1, lr_t, beta1, beta2, eps, st);
-        if (rc != FDTD_OK) return rc;
-        k_loss_accum<<<1, 32, 0, st>>>(loss, 1.0 / (double)nb, loss_mean);
-    }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
     return FDTD_OK;
 }

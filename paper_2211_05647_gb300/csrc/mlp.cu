@@ -38,12 +38,7 @@ __global__ void k_mlp_adam(float *__restrict__ p, const float *__restrict__ g, f
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.0f - b1) * gi;
-    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    adam_update(p, m, v, i, g[i], lr, b1, b2, eps, c1, c2);
 }
 
 size_t mlp_smem_bytes() { return sizeof(MlpSmem); }

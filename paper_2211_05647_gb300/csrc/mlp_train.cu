@@ -14,10 +14,15 @@
 //   dW1 = x^T dz1, db1 = colsum dz1                MMA, M = 32 (17 used), K over the rows
 // dz2 and dz1 enter the MMAs rounded to BF16; z1, z2 and the column sums stay
 // FP32.  The transposed operands (h1^T, x^T as A; dz2, dz1 as B over rows)
-// are read with ldmatrix .trans from the row-major tiles.
+// are read with ldmatrix .trans from the row-major tiles.  In training the
+// tile kernel takes its rows straight from the sample arrays through the
+// epoch's permutation, and one kernel sums the tiles' gradients and applies
+// Adam: two launches a minibatch.
 #include <algorithm>
+#include <cmath>
 
 #include "mlp_tc.cuh"
+#include "shuffle.cuh"
 
 namespace fp {
 
@@ -33,6 +38,7 @@ struct MlpTrainSmem {
     float b1[kMlpH], b2[kMlpH], w3[kMlpH];
     float colsum[3][8][kMlpH];         // per warp: dW3, db2, db1 partial column sums
     float loss[8], dyb[8];
+    int64_t src[kMlpRows];             // sample index of each row (-1: past the batch)
     float b3;
 };
 
@@ -58,11 +64,13 @@ __device__ __forceinline__ void warp_colsum(float *dst, int col, float v0, float
     }
 }
 
-// One 128-row tile per CTA (256 threads); writes ws[tile][0 .. kMlpNParams) = the tile's
-// gradient contribution and ws[tile][kMlpNParams] = its sum of squared residuals / B.
+// One 128-row tile per CTA (256 threads) of a batch of B rows; writes ws[tile][0 .. kMlpNParams)
+// = the tile's gradient contribution and ws[tile][kMlpNParams] = its sum of squared residuals / B.
+// Row r of the batch is sample r of X / T, or with use_perm sample perm(first + r).
 __global__ void __launch_bounds__(256, 1) k_mlp_train_tile(const float *__restrict__ P, const float *__restrict__ X,
                                                            const float *__restrict__ T, int64_t B,
-                                                           float *__restrict__ ws)
+                                                           float *__restrict__ ws, Perm perm, int64_t first,
+                                                           int use_perm)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTrainSmem &s = *reinterpret_cast<MlpTrainSmem *>(smem_raw);
@@ -89,10 +97,15 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train_tile(const float *__restri
         s.w3[i] = P[kOffW3 + i];
     }
     if (tid == 0) s.b3 = P[kOffB3];
+    if (tid < kMlpRows) {
+        const int64_t row = row0 + tid;
+        s.src[tid] = row < B ? (use_perm ? (int64_t)perm_index((uint64_t)(first + row), perm) : row) : -1;
+    }
+    __syncthreads();
     for (int i = tid; i < kMlpRows * kLd1; i += blockDim.x) {
         const int r = i / kLd1, k = i % kLd1;
-        const int64_t row = row0 + r;
-        s.x[r][k] = __float2bfloat16_rn((k < kMlpIn && row < B) ? X[row * kMlpIn + k] : 0.0f);
+        const int64_t src = s.src[r];
+        s.x[r][k] = __float2bfloat16_rn((k < kMlpIn && src >= 0) ? X[src * kMlpIn + k] : 0.0f);
     }
     __syncthreads();
 
@@ -159,9 +172,9 @@ __global__ void __launch_bounds__(256, 1) k_mlp_train_tile(const float *__restri
     y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
     y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
     y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-    const int64_t ra = row0 + r0 + g, rb = ra + 8;
-    const float e0 = ra < B ? y0 + s.b3 - T[ra] : 0.0f;
-    const float e1 = rb < B ? y1 + s.b3 - T[rb] : 0.0f;
+    const int64_t sa = s.src[r0 + g], sb = s.src[r0 + g + 8];
+    const float e0 = sa >= 0 ? y0 + s.b3 - T[sa] : 0.0f;
+    const float e1 = sb >= 0 ? y1 + s.b3 - T[sb] : 0.0f;
     const float dy0 = 2.0f * e0 / (float)B, dy1 = 2.0f * e1 / (float)B;
 
     // ---- dW3 = h2^T dy, dz2 = dy w3 GELU'(z2) (-> shared, BF16), db2 = colsum dz2
@@ -319,6 +332,34 @@ __global__ void k_mlp_train_reduce(const float *__restrict__ ws, int ntiles, flo
     else *loss = a;
 }
 
+// the same sum per parameter followed by its Adam step (step count t: c1, c2), and the minibatch's loss
+// added to *loss_acc times loss_scale
+__global__ void k_mlp_train_reduce_adam(const float *__restrict__ ws, int ntiles, float *__restrict__ P,
+                                        float *__restrict__ m, float *__restrict__ v, float lr, float b1, float b2,
+                                        float eps, float c1, float c2, double *__restrict__ loss_acc,
+                                        double loss_scale)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kMlpNParams) return;
+    float a = 0.0f;
+    for (int q = 0; q < ntiles; ++q) a += ws[(int64_t)q * kTrainStride + i];
+    if (i < kMlpNParams) adam_update(P, m, v, i, a, lr, b1, b2, eps, c1, c2);
+    else *loss_acc += (double)a * loss_scale;
+}
+
+size_t train_smem_bytes() { return sizeof(MlpTrainSmem); }
+
+cudaError_t launch_train_tile(cudaStream_t st, const float *P, const float *X, const float *T, int64_t B, float *ws,
+                              const Perm *perm, int64_t first)
+{
+    const size_t smem = sizeof(MlpTrainSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (B + kMlpRows - 1) / kMlpRows;
+    k_mlp_train_tile<<<(unsigned)tiles, 256, smem, st>>>(P, X, T, B, ws, perm ? *perm : Perm{}, first, perm ? 1 : 0);
+    return cudaGetLastError();
+}
+
 }  // namespace fp
 
 using namespace fp;
@@ -343,11 +384,45 @@ int fdtd_mlp_loss_grad(const float *params, const float *x, const float *target,
     if (tiles > (1 << 24)) return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_loss_grad: batch too large");
     cudaStream_t st = (cudaStream_t)stream;
     float *ws = reinterpret_cast<float *>(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
-    const size_t smem = sizeof(MlpTrainSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_train_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = launch_train_tile(st, params, x, target, batch, ws, nullptr, 0);
     if (e == cudaSuccess) {
-        k_mlp_train_tile<<<(unsigned)tiles, 256, smem, st>>>(params, x, target, batch, ws);
         k_mlp_train_reduce<<<(kMlpNParams + 1 + 255) / 256, 256, 0, st>>>(ws, (int)tiles, grad, loss);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    return FDTD_OK;
+}
+
+size_t fdtd_mlp_train_workspace_bytes(int64_t batch) { return fdtd_mlp_workspace_bytes(batch); }
+
+int fdtd_mlp_train_epoch(float *params, float *grad, float *m, float *v, const float *x, const float *t, int64_t n,
+                         int64_t batch, uint64_t seed, int64_t epoch, int64_t iter0, int64_t total_iters, double lr,
+                         double beta1, double beta2, double eps, double *loss_mean, void *workspace,
+                         size_t workspace_bytes, void *stream)
+{
+    (void)grad;   // the fused reduction applies each tile-summed gradient directly
+    if (!params || !m || !v || !x || !t || !loss_mean || !workspace || batch < 1 || n < batch ||
+        n > (int64_t)1 << 40 || epoch < 0 || iter0 < 0 || total_iters < 1 || !(lr > 0) || !std::isfinite(lr))
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_train_epoch: bad argument (need n >= batch >= 1)");
+    if (workspace_bytes < fdtd_mlp_train_workspace_bytes(batch))
+        return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_train_epoch: workspace too small");
+    const int64_t tiles = (batch + kMlpRows - 1) / kMlpRows;
+    if (tiles > (1 << 24)) return fp_set_global_error(FDTD_ERR_INVAL, "fdtd_mlp_train_epoch: batch too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    float *ws = reinterpret_cast<float *>(((uintptr_t)workspace + 255) & ~(uintptr_t)255);
+    cudaError_t e = cudaMemsetAsync(loss_mean, 0, sizeof(double), st);
+    if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+    const int64_t nb = n / batch;   // the ragged tail of the permuted order is left out this epoch
+    const Perm p = make_perm(n, seed, epoch);
+    for (int64_t b = 0; b < nb && e == cudaSuccess; ++b) {
+        e = launch_train_tile(st, params, x, t, batch, ws, &p, b * batch);
+        if (e != cudaSuccess) break;
+        const int64_t it = iter0 + b;
+        const double lr_t = lr * 0.5 * (1.0 + std::cos(kPi * (double)std::min(it, total_iters) / (double)total_iters));
+        const double c1 = 1.0 - std::pow(beta1, (double)(it + 1)), c2 = 1.0 - std::pow(beta2, (double)(it + 1));
+        k_mlp_train_reduce_adam<<<(kMlpNParams + 1 + 255) / 256, 256, 0, st>>>(
+            ws, (int)tiles, params, m, v, (float)lr_t, (float)beta1, (float)beta2, (float)eps, (float)c1, (float)c2,
+            loss_mean, 1.0 / (double)nb);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return fp_set_global_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
