@@ -548,14 +548,14 @@ cudaError_t part_ports(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSe
 // the chunk); ev (optional) receives records before H, before the kinetic
 // kernel, before the closure kernel, before E and after E.
 template <typename T>
-cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t *ev = nullptr)
+cudaError_t enqueue_step(fdtd_plasma *h, cudaStream_t st, int kstep, cudaEvent_t *ev = nullptr, bool last = true)
 {
     const FieldSet<T> fs = field_set<T>(h, 0);
     if (ev) cudaEventRecord(ev[0], st);
     cudaError_t e = part_h<T>(h, st, kstep, fs);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
-    e = part_mid<T>(h, st, kstep, fs, ev);
+    e = part_mid<T>(h, st, kstep, fs, ev, last);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[3], st);
     e = part_e<T>(h, st, kstep, fs);
@@ -1574,8 +1574,9 @@ int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out)
     double acc[5] = {0, 0, 0, 0, 0};
     int rc = FDTD_OK;
     for (int64_t s = 0; s < nsteps && rc == FDTD_OK; ++s) {
-        cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_step<double>(h, h->stream, 0, ev)
-                                                   : enqueue_step<float>(h, h->stream, 0, ev);
+        const bool last = s == nsteps - 1;   // J stored on the last step, as in a step sequence
+        cudaError_t e = h->g.precision == FDTD_F64 ? enqueue_step<double>(h, h->stream, 0, ev, last)
+                                                   : enqueue_step<float>(h, h->stream, 0, ev, last);
         if (e == cudaSuccess) {
             launch_advance(h->stream, h->d_step, 1);
             e = cudaEventSynchronize(ev[4]);
