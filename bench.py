@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="2d_tmz_4096_kinetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--engine", default="tcgen05", choices=["mma", "tcgen05", "tcgen05x8"], help="closure MLP engine")
+    ap.add_argument("--engine", default="tcgen05", choices=["mma", "tcgen05"], help="closure MLP engine")
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="2-D / 3-D FP32: fuse each E update with the next H update (default 0: separate passes)")
     ap.add_argument("--no-autotune", action="store_true",

@@ -1331,7 +1331,7 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
         !(c->n_train_max >= 0))
         return fail(h, FDTD_ERR_INVAL, "closure scales must be finite, e_scale and n_scale > 0");
     std::vector<float> P(FDTD_MLP_NPARAMS);
-    if (c->engine < 0 || c->engine > 2) return fail(h, FDTD_ERR_INVAL, "closure engine must be 0, 1 or 2");
+    if (c->engine != 0 && c->engine != 1) return fail(h, FDTD_ERR_INVAL, "closure engine must be 0 or 1");
     if (c->params_on_device) CK(h, cudaMemcpy(P.data(), c->params, P.size() * 4, cudaMemcpyDeviceToHost));
     else std::memcpy(P.data(), c->params, P.size() * 4);
     for (float v : P)

@@ -171,78 +171,11 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
     mlp_tc4_teardown(s);
 }
 
-// The same closure step with eight warpgroups (1024 threads) on the four
-// accumulators: pair p = warpgroups p and p + 4 owns accumulator p; half 0
-// (warpgroups 0..3) stages the inputs and applies J and E, both halves form
-// the activations of half of the columns.
-__global__ void __launch_bounds__(1024, 1) k_closure_tc8(ClosureArgs a)
-{
-    pdl_enter();
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    MlpTcSmem8 &s = *reinterpret_cast<MlpTcSmem8 *>(smem_raw);
-    mlp_tc4_load_weights(s.w, a.P);
-    mlp_tc8_setup(s);
-    const int gi = threadIdx.x >> 7, r = threadIdx.x & 127;
-    const int p = gi & 3, h = gi >> 2;
-    MlpTcPair &g = s.g[p];
-    uint32_t phase = 0;
-    bool ok = true;
-    const int64_t step = *a.d_step + a.kstep;
-    const int ring = (int)(step & 15);
-    const int64_t ntiles = (a.n + kMlpRows - 1) / kMlpRows;
-    for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + p; tile < ntiles; tile += (int64_t)gridDim.x * kTcGroups) {
-        const int64_t slot = tile * kMlpRows + r;
-        const bool valid = slot < a.n;
-        int32_t c = 0;
-        float e = 0.0f;
-        if (h == 0) {
-            float x[kMlpK1];
-#pragma unroll
-            for (int k = 0; k < kMlpK1; ++k) x[k] = 0.0f;
-            if (valid) {
-                c = a.cell[slot];
-                e = a.E[c];
-                float *hp = a.hist + slot * 16;
-                hp[ring] = e;
-                float hv[16];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 v = reinterpret_cast<const float4 *>(hp)[q];
-                    hv[4 * q] = v.x; hv[4 * q + 1] = v.y; hv[4 * q + 2] = v.z; hv[4 * q + 3] = v.w;
-                }
-#pragma unroll
-                for (int k = 0; k < 16; ++k) x[k] = hv[(ring + 1 + k) & 15] * a.inv_es;
-                x[16] = a.dens[slot] * a.inv_ns;
-            }
-            mlp_tc8_put_row(g, r, x);
-        }
-        const float y = mlp_tc8_tile(s.w, g, p, h, r, &phase, &ok);
-        if (!ok) break;
-        if (h == 0 && valid) {
-            const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * e + a.js * y;
-            a.jprev[slot] = J;
-            a.jslot[slot] = J;
-            a.E[c] = e - a.cj * J;
-        }
-    }
-    if (!ok && r == 0 && h == 0) atomicExch(a.err, 1);
-    mlp_tc8_teardown(s);
-}
-
 size_t closure_smem_bytes() { return sizeof(MlpSmem); }
 
 cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
 {
     if (a.n == 0) return cudaSuccess;
-    if (a.engine == 2) {
-        const size_t smem = sizeof(MlpTcSmem8);
-        cudaError_t e = cudaFuncSetAttribute(k_closure_tc8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const int64_t tiles = (a.n + kMlpRows - 1) / kMlpRows;
-        const int64_t grid = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, (int64_t)num_sms);
-        launch_pdl(k_closure_tc8, dim3((unsigned)std::max<int64_t>(grid, 1)), dim3(1024), smem, st, a);
-        return cudaGetLastError();
-    }
     if (a.engine == 1) {
         const size_t smem = sizeof(MlpTcSmem4);
         cudaError_t e = cudaFuncSetAttribute(k_closure_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

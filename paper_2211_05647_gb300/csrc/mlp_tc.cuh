@@ -404,173 +404,4 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
     return y;
 }
 
-// ------------------------------------------------------------------------
-// Eight warpgroups per CTA (1024 threads) on the same four accumulators: the
-// warpgroups gi and gi + 4 form pair gi and share accumulator gi, its input
-// and hidden tiles and its mbarrier; half h = gi >> 2 of a pair forms the
-// activations of columns [64 h, 64 h + 64) of every row (warp w of a
-// warpgroup reads TMEM lanes 32 (w % 4) .. + 31, as before), so twice as many
-// warps hide the epilogue's latencies.  Half 1 hands its share of the output
-// dot product to half 0 through shared memory.  Pair p synchronises on named
-// barrier 1 + p (256 threads).
-
-struct MlpTcPair {
-    __align__(128) __nv_bfloat16 x[kMlpRows * kMlpK1];
-    __align__(128) __nv_bfloat16 a2[kMlpRows * kMlpH];
-    __align__(16) float ys[kMlpRows];   // half 1's partial output per row
-    __align__(8) uint64_t mbar;
-    int flag;
-};
-
-struct MlpTcSmem8 {
-    MlpTcWeights w;
-    MlpTcPair g[kTcGroups];
-};
-
-__device__ __forceinline__ void pair_bar(int p) { asm volatile("bar.sync %0, 256;" ::"r"(1 + p) : "memory"); }
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// all 1024 threads: TMEM (4 x 128 columns), one mbarrier per pair
-__device__ __forceinline__ void mlp_tc8_setup(MlpTcSmem8 &s)
-{
-    if (threadIdx.x < 32) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s.w.tmem)),
-                     "r"(512u)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    if (threadIdx.x < kTcGroups) {
-        mbar_init(&s.g[threadIdx.x].mbar, 1);
-        s.g[threadIdx.x].flag = 0;
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-}
-
-__device__ __forceinline__ void mlp_tc8_teardown(MlpTcSmem8 &s)
-{
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (threadIdx.x < 32)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.w.tmem), "r"(512u) : "memory");
-}
-
-__device__ __forceinline__ void mlp_tc8_put_row(MlpTcPair &g, int r, const float *x)
-{
-    unsigned char *xb = reinterpret_cast<unsigned char *>(g.x);
-#pragma unroll
-    for (int c = 0; c < kMlpK1 / 8; ++c) {
-        uint4 v;
-        v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-        v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-        v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-        v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
-        *reinterpret_cast<uint4 *>(xb + core_off(r, 8 * c, kMlpK1)) = v;
-    }
-}
-
-// forward of pair p's tile (rows in g.x, written by half 0 before the call); thread r of half h forms
-// columns [64 h, 64 h + 64) of row r; returns the row's output in half 0 (half 1: 0).  *ok_out is
-// false in every thread of the pair if one of its bounded waits gave up.
-__device__ __forceinline__ float mlp_tc8_tile(MlpTcWeights &w, MlpTcPair &g, int p, int h, int r, uint32_t *phase,
-                                              bool *ok_out)
-{
-    const int warp = r >> 5;
-    const uint32_t tmem = w.tmem + (uint32_t)(p * 128) + (uint32_t)(h * 64);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    constexpr uint64_t kWaitNs = 1000000000ull;
-    const uint32_t acc = w.tmem + (uint32_t)(p * 128);
-    bool ok = true;
-    fence_proxy_async_smem();
-    tc_fence_before();
-    pair_bar(p);
-    tc_fence_after();
-    if (h == 0 && r == 0) {
-        const uint32_t xa = smem_addr(g.x), wa = smem_addr(w.w1);
-#pragma unroll
-        for (int kk = 0; kk < kMlpK1 / 16; ++kk)
-            tc_mma(acc, tc_desc(xa + kk * 256, 128, (kMlpK1 / 8) * 128), tc_desc(wa + kk * 256, 128, (kMlpK1 / 8) * 128),
-                   kTcIdesc, kk > 0);
-        tc_commit(&g.mbar);
-    }
-    if (!mbar_wait_timed(&g.mbar, *phase, kWaitNs)) ok = false;
-    *phase ^= 1u;
-    tc_fence_after();
-    unsigned char *a2 = reinterpret_cast<unsigned char *>(g.a2);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float v[16];
-        tc_ld16(tmem + lane_base + c * 16, v);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int k0 = h * 64 + c * 16 + q * 8;
-            const float4 ba = *reinterpret_cast<const float4 *>(&w.b1[k0]);
-            const float4 bb = *reinterpret_cast<const float4 *>(&w.b1[k0 + 4]);
-            const float2 g0 = gelu2_f2(f2_add(f2(v[q * 8 + 0], v[q * 8 + 1]), f2(ba.x, ba.y)));
-            const float2 g1 = gelu2_f2(f2_add(f2(v[q * 8 + 2], v[q * 8 + 3]), f2(ba.z, ba.w)));
-            const float2 g2 = gelu2_f2(f2_add(f2(v[q * 8 + 4], v[q * 8 + 5]), f2(bb.x, bb.y)));
-            const float2 g3 = gelu2_f2(f2_add(f2(v[q * 8 + 6], v[q * 8 + 7]), f2(bb.z, bb.w)));
-            uint4 pk;
-            pk.x = pack_bf16(g0.x, g0.y);
-            pk.y = pack_bf16(g1.x, g1.y);
-            pk.z = pack_bf16(g2.x, g2.y);
-            pk.w = pack_bf16(g3.x, g3.y);
-            *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
-        }
-    }
-    fence_proxy_async_smem();
-    tc_fence_before();
-    pair_bar(p);
-    tc_fence_after();
-    if (h == 0 && r == 0) {
-        const uint32_t aa = smem_addr(g.a2), wa = smem_addr(w.w2);
-#pragma unroll
-        for (int kk = 0; kk < kMlpH / 16; ++kk)
-            tc_mma(acc, tc_desc(aa + kk * 256, 128, (kMlpH / 8) * 128), tc_desc(wa + kk * 256, 128, (kMlpH / 8) * 128),
-                   kTcIdesc, kk > 0);
-        tc_commit(&g.mbar);
-    }
-    if (!mbar_wait_timed(&g.mbar, *phase, kWaitNs)) ok = false;
-    *phase ^= 1u;
-    tc_fence_after();
-    float y = 0.0f;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        float v[16];
-        tc_ld16(tmem + lane_base + c * 16, v);
-#pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-            const int k0 = h * 64 + c * 16 + i;
-            const float4 b = *reinterpret_cast<const float4 *>(&w.b2[k0]);
-            const float4 o = *reinterpret_cast<const float4 *>(&w.w3[k0]);
-            const float2 g0 = gelu2_f2(f2_add(f2(v[i + 0], v[i + 1]), f2(b.x, b.y)));
-            const float2 g1 = gelu2_f2(f2_add(f2(v[i + 2], v[i + 3]), f2(b.z, b.w)));
-            y = fmaf(g0.x, o.x, y);
-            y = fmaf(g0.y, o.y, y);
-            y = fmaf(g1.x, o.z, y);
-            y = fmaf(g1.y, o.w, y);
-        }
-    }
-    tc_fence_before();
-    if (h == 1) g.ys[r] = y;
-    if (!ok) g.flag = 1;
-    pair_bar(p);
-    *ok_out = g.flag == 0;
-    return h == 0 ? w.b3 + y + g.ys[r] : 0.0f;
-}
-
 }  // namespace fp

@@ -597,7 +597,7 @@ class Solver:
         n = p.numel() if isinstance(p, torch.Tensor) else p.size
         if n != MLP_NPARAMS:
             raise ValueError("closure needs 18945 parameters")
-        d = fdtd_closure_desc(ptr, dev, {"mma": 0, "tcgen05": 1, "tcgen05x8": 2}[engine], float(e_scale), float(j_scale),
+        d = fdtd_closure_desc(ptr, dev, {"mma": 0, "tcgen05": 1}[engine], float(e_scale), float(j_scale),
                               float(n_scale), float(rho), float(n_train_max), float(beta))
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_closure(self.h, ctypes.byref(d)))
 
