@@ -195,6 +195,72 @@ void free_plasma(fdtd_plasma *h)
     h->h_dens.clear();
 }
 
+// The plasma slots of a whole grid's density array (host or device, pol_len values), compacted on the
+// GPU: cells in increasing index with their densities (FP64) and the largest density; FDTD_ERR_NONFINITE
+// for a value that is not finite or is negative.
+int compact_on_gpu(fdtd_plasma *h, const fdtd_plasma_desc *p, int64_t np, std::vector<int32_t> &cells,
+                   std::vector<double> &dslot, double &nmax)
+{
+    const int64_t nb = (np + kCompactChunk - 1) / kCompactChunk;
+    const CompactGeom g{h->g.ndim, h->nx, h->ny, h->nz, np};
+    void *dtmp = nullptr, *scr = nullptr, *out = nullptr;
+    auto release = [&]() { dfree(h, dtmp); dfree(h, scr); dfree(h, out); };
+    const double *d = static_cast<const double *>(p->density);
+    if (!p->density_on_device) {
+        dtmp = dalloc(h, (size_t)np * 8);
+        if (!dtmp) return fail(h, FDTD_ERR_NOMEM, "density upload buffer (%lld values)", (long long)np);
+        cudaError_t e = cudaMemcpyAsync(dtmp, p->density, (size_t)np * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) { release(); return cuda_fail(h, e, "density upload"); }
+        d = static_cast<const double *>(dtmp);
+    }
+    // scratch: offsets (int64) | maxes (double) | counts (int) | bad (int)
+    scr = dalloc(h, (size_t)nb * 20 + 256);
+    if (!scr) { release(); return fail(h, FDTD_ERR_NOMEM, "compaction scratch"); }
+    int64_t *d_off = static_cast<int64_t *>(scr);
+    double *d_max = reinterpret_cast<double *>(d_off + nb);
+    int *d_cnt = reinterpret_cast<int *>(d_max + nb), *d_bad = d_cnt + nb;
+    std::vector<int> cnt((size_t)nb);
+    std::vector<double> mx((size_t)nb);
+    std::vector<int64_t> off((size_t)nb);
+    int bad = 0;
+    cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = launch_compact_count(h->stream, d, g, d_cnt, d_max, d_bad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, (size_t)nb * 4, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mx.data(), d_max, (size_t)nb * 8, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) { release(); return cuda_fail(h, e, "plasma compaction (count)"); }
+    if (bad) { release(); return fail(h, FDTD_ERR_NONFINITE, "density must be finite and >= 0"); }
+    int64_t ns = 0;
+    nmax = 0.0;
+    for (int64_t b = 0; b < nb; ++b) {
+        off[(size_t)b] = ns;
+        ns += cnt[(size_t)b];
+        nmax = std::max(nmax, mx[(size_t)b]);
+    }
+    cells.resize((size_t)ns);
+    dslot.resize((size_t)ns);
+    if (ns) {
+        out = dalloc(h, (size_t)ns * 12 + 256);
+        if (!out) { release(); return fail(h, FDTD_ERR_NOMEM, "compaction output (%lld cells)", (long long)ns); }
+        double *d_dens = static_cast<double *>(out);
+        int32_t *d_cells = reinterpret_cast<int32_t *>(d_dens + ns);
+        e = cudaMemcpyAsync(d_off, off.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_compact_scatter(h->stream, d, g, d_off, d_cells, d_dens);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(cells.data(), d_cells, (size_t)ns * 4, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dslot.data(), d_dens, (size_t)ns * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { release(); return cuda_fail(h, e, "plasma compaction (scatter)"); }
+    } else {
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) { release(); return cuda_fail(h, e, "plasma compaction"); }
+    }
+    release();
+    return FDTD_OK;
+}
+
 void drop_graphs(fdtd_plasma *h)
 {
     if (h->g1) cudaGraphExecDestroy(h->g1);
@@ -1057,7 +1123,7 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
 
     // density: compact the plasma cells
     const int64_t np = pol_len(h);
-    std::vector<double> dens(np);
+    std::vector<double> dens(h->sd_on ? np : 0);
     int64_t slot_base = 0;
     if (h->sd_on) {
         // a sub-domain reads its planes of the global density array; its slots are numbered after the
@@ -1078,21 +1144,23 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
             const int64_t l = c / plane;
             if (l < h->sd_lo || l >= h->sd_lo + h->sd_extent) dens[c] = 0.0;
         }
-    } else if (p->density_on_device) {
-        CK(h, cudaMemcpy(dens.data(), p->density, np * 8, cudaMemcpyDeviceToHost));
-    } else {
-        std::memcpy(dens.data(), p->density, np * 8);
     }
     std::vector<int32_t> cells;
     std::vector<double> dslot;
     double nmax = 0.0;
-    for (int64_t c = 0; c < np; ++c) {
-        const double d = dens[c];
-        if (!std::isfinite(d) || d < 0.0) return fail(h, FDTD_ERR_NONFINITE, "density must be finite and >= 0");
-        if (d > 0.0 && pol_updated(h, c)) {
-            cells.push_back((int32_t)c);
-            dslot.push_back(d);
-            if (d > nmax) nmax = d;
+    if (!h->sd_on) {
+        // a whole grid: the density stays on (or goes once to) the device and is compacted there
+        const int rc = compact_on_gpu(h, p, np, cells, dslot, nmax);
+        if (rc != FDTD_OK) return rc;
+    } else {
+        for (int64_t c = 0; c < np; ++c) {
+            const double d = dens[c];
+            if (!std::isfinite(d) || d < 0.0) return fail(h, FDTD_ERR_NONFINITE, "density must be finite and >= 0");
+            if (d > 0.0 && pol_updated(h, c)) {
+                cells.push_back((int32_t)c);
+                dslot.push_back(d);
+                if (d > nmax) nmax = d;
+            }
         }
     }
     // plasma-modified stability of Yee + Crank-Nicolson current: (w_p dt/2)^2 + S^2 ndim < 1

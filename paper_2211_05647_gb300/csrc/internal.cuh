@@ -256,6 +256,19 @@ bool launch_eh3d_tma(cudaStream_t st, const TmaMaps *t, float *const fin[6], flo
                      float *const psi_out[12], float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
                      const int64_t *d_step, int kstep, int tz, int *err);
 
+// GPU compaction of a density array into plasma slots (compact.cu): chunks of kCompactChunk nodes; per
+// chunk the number of plasma nodes and the largest density (bad |= 1 on a non-finite or negative value),
+// then, from each chunk's exclusive-scan offset, its plasma nodes and densities in index order
+constexpr int64_t kCompactChunk = 4096;
+struct CompactGeom {
+    int ndim;
+    int64_t nx, ny, nz, n;   // grid cells per axis; n = length of the polarisation array
+};
+cudaError_t launch_compact_count(cudaStream_t st, const double *d, const CompactGeom &g, int *counts, double *maxes,
+                                 int *bad);
+cudaError_t launch_compact_scatter(cudaStream_t st, const double *d, const CompactGeom &g, const int64_t *offsets,
+                                   int32_t *cells, double *dens);
+
 // delta-f row pitch (elements) for nnode nodes of the given storage type
 int kinetic_pitch(int nnode, int f_dtype);
 // launch shape candidates (vectors per lane, lanes per row) for a row pitch; the first is the default
