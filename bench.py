@@ -623,8 +623,8 @@ def main():
     init = {n: torch.zeros(s.quantity_bytes(n) // (8 if s.precision == "f64" else 4),
                            dtype=torch.float64 if s.precision == "f64" else torch.float32).pin_memory()
             for n in outs if n != "j"}
-    host_out = {n: torch.empty_like(init[n]) if n != "j" else
-                torch.empty(ns, dtype=torch.float64 if s.precision == "f64" else torch.float32).pin_memory()
+    host_out = {n: torch.empty(init[n].shape, dtype=init[n].dtype, pin_memory=True) if n != "j" else
+                torch.empty(ns, dtype=torch.float64 if s.precision == "f64" else torch.float32, pin_memory=True)
                 for n in outs}
     barrier()
     # phase boundaries are synchronised so the window splits into set-up (plasma set-up from the host density:
