@@ -47,6 +47,11 @@ def parse():
                     help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
     ap.add_argument("--kin-shape", default="",
                     help="VPL,L[,BPS]: force the kinetic kernel's launch shape after autotuning (profiling)")
+    ap.add_argument("--decompose", action="store_true",
+                    help="N > 1: split the grid along its slowest axis, one slab per rank, halos over NCCL "
+                         "(strong scaling); N = 1 is the whole-grid path")
+    ap.add_argument("--subdomains", type=int, default=0,
+                    help="K > 1: run the grid as K slabs on this one GPU with halo copies (decomposition overhead)")
     ap.add_argument("--no-configs", action="store_true",
                     help="default workload at N = 1: skip the other configurations' entries (configs)")
     return ap.parse_args()
@@ -570,6 +575,8 @@ def main():
                               **{k: v for k, v in r.items() if k not in ("samples_per_s",)}}), flush=True)
         return 0
     spec = make_spec(args.workload)
+    if (args.decompose and world > 1) or args.subdomains > 1:
+        return decomposed_bench(args, spec, rank, world, local)
     if isinstance(spec, list):
         return batch_bench(args, spec, rank, world, local)
     if args.workload.endswith("_closure"):
@@ -786,6 +793,53 @@ def closure_cost_bench(args, spec, rank, world, local):
             "gpu_launches": step_launches(args.steps, 2 if n_kin else 1, False),
             "clocks": clk}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def decomposed_bench(args, spec, rank, world, local):
+    """The grid split along its slowest axis: one slab per rank with halos sent
+    to the neighbouring ranks (--decompose, N > 1: strong scaling, every rank's
+    time is the job's), or K slabs on this GPU with device-to-device halos
+    (--subdomains K: the decomposition's cost on one GPU).  Half steps run
+    eagerly (a halo exchange sits between them); W warm-up steps, K timed."""
+    import torch
+    import torch.distributed as dist
+    from paper_2211_05647_gb300.decomposed import DecomposedSolver, DistributedSolver
+    cells = cells_of(spec)
+    if args.subdomains > 1:
+        d = DecomposedSolver(spec, parts=args.subdomains, device=local)
+        stream, slabs, mode = d.stream, d.bounds, f"{args.subdomains} slabs on one GPU"
+    else:
+        d = DistributedSolver(spec, rank, world, device=local)
+        stream, slabs, mode = d.sub.stream, d.bounds, f"{world} slabs, one per rank (NCCL halos)"
+    d.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(gpu_uuid(local))
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    d.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = reduce_max(e0.elapsed_time(e1), world, f"cuda:{local}")
+    d.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": cells * args.steps / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if args.subdomains <= 1 else "weak", "vs_baseline": None,
+            "dtype": spec["grid"].get("precision", "f32"), "data": "synthetic (seeded density field)",
+            "config": {"workload": args.workload, "decomposition": mode, "slabs": slabs,
+                       "l2": "inputs larger than L2", "parallelism": mode},
+            "gpu_launches": None, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
