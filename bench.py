@@ -825,6 +825,9 @@ def decomposed_bench(args, spec, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = reduce_max(e0.elapsed_time(e1), world, f"cuda:{local}")
+    subs = d.subs if args.subdomains > 1 else [d.sub]
+    # per slab and step: H, the kinetic rows (slabs with plasma), E, the step counter
+    launches = args.steps * sum(3 + (1 if sb.plasma_shape()[0] else 0) for sb in subs)
     d.close()
     if rank != 0:
         if world > 1:
@@ -836,7 +839,7 @@ def decomposed_bench(args, spec, rank, world, local):
             "dtype": spec["grid"].get("precision", "f32"), "data": "synthetic (seeded density field)",
             "config": {"workload": args.workload, "decomposition": mode, "slabs": slabs,
                        "l2": "inputs larger than L2", "parallelism": mode},
-            "gpu_launches": None, "clocks": clk}
+            "gpu_launches": launches, "clocks": clk}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
