@@ -6,8 +6,13 @@ run on the same inputs.  Relative L2 per field component (field-vector
 normalisation) and of J.
 
   2-D TMz 4096^2, 823 k plasma cells x 1024 nodes, FP32, 2000 steps: <= 1e-4
-  3-D 512^3 BF16 delta f, 1000 steps: fields <= 5e-3 (stochastic rounding noise)
-  256 batched 1-D runs, FP32, 5000 steps: every run's E and J <= 1e-4
+  3-D 512^3, FP32 delta f, 1000 steps: <= 1e-4
+  3-D 512^3, BF16 delta f (the benchmark's), 1000 steps: the stochastic-rounding noise of 1000 roundings of
+      every node; two runs with different rounding seeds, whose mean must lie closer to FP64 than either by
+      about 1/sqrt(2) (noise, not bias): fields <= 3e-2, J <= 6e-2
+  256 batched 1-D runs, FP32, 5000 steps: every run's E within 1e-4 of the radiated pulse's norm (many
+      small grids have shed the pulse through their Mur ends by then, leaving a residue far below it) and
+      J within 1e-4 of its own norm (floored as in the batched parity test)
 
 They take minutes of host time (the oracle) and tens of GB of host memory, so
 they run only when FDTD_FULL_RUN_TESTS=1."""
@@ -65,8 +70,45 @@ def test_2d_tmz_4096_full_run(oracle_lib):
     _full_run(oracle_lib, "2d_tmz_4096_kinetic", 1e-4, 1e-4, 24)
 
 
+def test_3d_512_f32_full_run(oracle_lib):
+    _full_run(oracle_lib, "3d_512_kinetic_f32", 1e-4, 1e-4, 60)
+
+
 def test_3d_512_bf16_full_run(oracle_lib):
-    _full_run(oracle_lib, "3d_512_kinetic_bf16", 5e-3, 1e-1, 60)
+    if _mem_available_gb() < 60:
+        pytest.skip("needs 60 GB of host memory for the FP64 oracle at full size")
+    from paper_2211_05647_gb300 import Solver
+    O = oracle_lib
+    O.build(omp=True)
+    spec = WORKLOADS["3d_512_kinetic_bf16"]()
+    steps = int(spec["steps"])
+    sim = oracle_sim(O, spec, omp=True)
+    sim.step(steps)
+    names = ["ex", "ey", "ez", "hx", "hy", "hz", "j"]
+    ref = {n: sim.get(n) for n in names}
+    runs = []
+    for seed in (spec["plasma"]["seed"], spec["plasma"]["seed"] + 1):
+        sp = dict(spec, plasma=dict(spec["plasma"], seed=seed))
+        s = Solver.from_spec(sp)
+        s.autotune()
+        s.step(steps)
+        runs.append({n: s.read(n, device=False).astype(np.float64) for n in names})
+        s.close()
+    def errs(got):
+        ne = np.sqrt(sum(np.sum(ref[n] ** 2) for n in names[:3]))
+        nh = np.sqrt(sum(np.sum(ref[n] ** 2) for n in names[3:6]))
+        out = {n: np.linalg.norm(got[n] - ref[n]) / (ne if n[0] == "e" else nh) for n in names[:6]}
+        out["j"] = rel_l2(got["j"], ref["j"])
+        return out
+    e0, e1 = errs(runs[0]), errs(runs[1])
+    em = errs({n: 0.5 * (runs[0][n] + runs[1][n]) for n in names})
+    print(f"3d_512_kinetic_bf16: {steps} steps; rel L2 vs FP64 oracle, seed 0 {e0}; seed 1 {e1}; "
+          f"mean of the two {em}")
+    for n in names:
+        tol = 6e-2 if n == "j" else 3e-2
+        assert e0[n] <= tol and e1[n] <= tol, (n, e0[n], e1[n])
+    for n in ("ex", "ey", "ez", "j"):
+        assert em[n] <= 0.85 * 0.5 * (e0[n] + e1[n]), (n, em[n], e0[n], e1[n])
 
 
 def _oracle_batch_run(args):
@@ -74,7 +116,11 @@ def _oracle_batch_run(args):
     from oracle import oracle as O
     sim = oracle_sim(O, spec)
     sim.step(steps)
-    return sim.get("ex"), sim.get("j")
+    # the norm of the pulse the source radiates: at Courant 0.5 a soft source sends g(t - |x|/c) both
+    # ways, so on the grid it is sqrt(sum_n g(t_n)^2) (half-cell time steps, two directions)
+    p = sim.p
+    g = np.array([O.source(p, (n + 1) * sim.dt) for n in range(steps)])
+    return sim.get("ex"), sim.get("j"), float(np.sqrt(np.sum(g * g)))
 
 
 def test_batch1d_256_full_run():
@@ -89,8 +135,9 @@ def test_batch1d_256_full_run():
         b.step(steps)
         got = [(b.read(r, "ex"), b.read(r, "j")) for r in range(len(specs))]
         want = pending.get()
-    ee = [rel_l2(g[0], w[0]) for g, w in zip(got, want)]
-    ej = [rel_l2(g[1], w[1]) for g, w in zip(got, want) if w[1].size and np.abs(w[1]).max() > 0]
+    ee = [np.linalg.norm(g[0] - w[0]) / w[2] for g, w in zip(got, want)]
+    ej = [np.linalg.norm(g[1] - w[1]) / max(np.linalg.norm(w[1]), 1e-6 * np.sqrt(w[1].size))
+          for g, w in zip(got, want) if w[1].size]
     print(f"batch1d_256_f32: {len(specs)} runs x {steps} steps; worst rel L2 vs FP64 oracle: E {max(ee):.2e}, "
           f"J {max(ej):.2e} ({len(ej)} runs with current)")
     assert max(ee) <= 1e-4 and max(ej) <= 1e-4
