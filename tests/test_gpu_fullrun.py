@@ -12,7 +12,8 @@ normalisation) and of J.
       about 1/sqrt(2) (noise, not bias): fields <= 3e-2, J <= 6e-2
   256 batched 1-D runs, FP32, 5000 steps: every run's E within 1e-4 of the radiated pulse's norm (many
       small grids have shed the pulse through their Mur ends by then, leaving a residue far below it) and
-      J within 1e-4 of its own norm (floored as in the batched parity test)
+      J within 1e-4 of the largest J norm the run reached (sampled every 500 steps: after the pulse has
+      passed, a slab's current decays by orders of magnitude)
 
 They take minutes of host time (the oracle) and tens of GB of host memory, so
 they run only when FDTD_FULL_RUN_TESTS=1."""
@@ -112,32 +113,45 @@ def test_3d_512_bf16_full_run(oracle_lib):
 
 
 def _oracle_batch_run(args):
-    spec, steps = args
+    spec, steps, chunk = args
     from oracle import oracle as O
     sim = oracle_sim(O, spec)
-    sim.step(steps)
+    js = []
+    for _ in range(steps // chunk):
+        sim.step(chunk)
+        js.append(sim.get("j"))
     # the norm of the pulse the source radiates: at Courant 0.5 a soft source sends g(t - |x|/c) both
     # ways, so on the grid it is sqrt(sum_n g(t_n)^2) (half-cell time steps, two directions)
     p = sim.p
     g = np.array([O.source(p, (n + 1) * sim.dt) for n in range(steps)])
-    return sim.get("ex"), sim.get("j"), float(np.sqrt(np.sum(g * g)))
+    return sim.get("ex"), js, float(np.sqrt(np.sum(g * g)))
 
 
 def test_batch1d_256_full_run():
     from paper_2211_05647_gb300 import Batch
     specs = WORKLOADS["batch1d_256_f32"]()
-    steps = int(specs[0]["steps"])
+    steps, chunk = int(specs[0]["steps"]), 500
     ctx = mp.get_context("spawn")
     with ctx.Pool(os.cpu_count() or 4) as pool:          # oracle workers, started before any GPU call
-        pending = pool.map_async(_oracle_batch_run, [(sp, steps) for sp in specs])
+        pending = pool.map_async(_oracle_batch_run, [(sp, steps, chunk) for sp in specs])
         b = Batch(specs)
         b.autotune()
-        b.step(steps)
-        got = [(b.read(r, "ex"), b.read(r, "j")) for r in range(len(specs))]
+        gj = []
+        for _ in range(steps // chunk):
+            b.step(chunk)
+            gj.append([b.read(r, "j") for r in range(len(specs))])
+        ge = [b.read(r, "ex") for r in range(len(specs))]
         want = pending.get()
-    ee = [np.linalg.norm(g[0] - w[0]) / w[2] for g, w in zip(got, want)]
-    ej = [np.linalg.norm(g[1] - w[1]) / max(np.linalg.norm(w[1]), 1e-6 * np.sqrt(w[1].size))
-          for g, w in zip(got, want) if w[1].size]
-    print(f"batch1d_256_f32: {len(specs)} runs x {steps} steps; worst rel L2 vs FP64 oracle: E {max(ee):.2e}, "
-          f"J {max(ej):.2e} ({len(ej)} runs with current)")
-    assert max(ee) <= 1e-4 and max(ej) <= 1e-4
+    ee = [np.linalg.norm(g - w[0]) / w[2] for g, w in zip(ge, want)]
+    ej = []
+    for r, w in enumerate(want):
+        if not w[1][0].size:
+            continue
+        scale = max(np.linalg.norm(j) for j in w[1])
+        err = max(np.linalg.norm(gj[c][r] - w[1][c]) for c in range(len(gj)))
+        ej.append((err / scale if scale > 0 else err, r, scale, np.linalg.norm(w[1][-1])))
+    worst = max(ej)
+    print(f"batch1d_256_f32: {len(specs)} runs x {steps} steps; worst rel L2 vs FP64 oracle: E {max(ee):.2e} of the "
+          f"pulse norm; J {worst[0]:.2e} of the run's largest J norm (run {worst[1]}: largest {worst[2]:.3e}, "
+          f"final {worst[3]:.3e}; {len(ej)} runs with plasma)")
+    assert max(ee) <= 1e-4 and worst[0] <= 1e-4
