@@ -559,6 +559,7 @@ cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<
         c.d_step = h->d_step;
         c.kstep = kstep;
         c.engine = h->cl.engine;
+        c.store_j = last;
         c.err = h->d_err;
         cudaError_t e = launch_closure(st, c, h->num_sms);
         if (e != cudaSuccess) return e;

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) k_closure(ClosureArgs a)
             if (slot < a.n) {
                 const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * s_e[r] + a.js * s.y[r];
                 a.jprev[slot] = J;
-                a.jslot[slot] = J;
+                if (a.store_j) a.jslot[slot] = J;
                 a.E[s_cell[r]] = s_e[r] - a.cj * J;
             }
         }
@@ -118,52 +118,63 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
 // The same closure step on the tcgen05 tile: one 512-thread CTA per SM with
 // four independent warpgroup pipelines (each its own TMEM accumulator and
 // tiles, one shared copy of the weights); thread r of a warpgroup owns row r
-// of its tile (history push, input row, J and E update).  If a bounded
-// MMA-completion wait gives up, *err is set and the warpgroup stops.
+// of its tile (history push, input row, J and E update).  Its history ring
+// holds the network inputs themselves, E / E_s rounded to BF16 (the rounding
+// the input gets anyway), 32 bytes a cell in slot order: W1's rows are stored
+// in the ring's slot order of the step, so a row is copied, never rotated.  If
+// a bounded MMA-completion wait gives up, *err is set and the warpgroup stops.
 __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
 {
     pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
     MlpTcSmem4 &s = *reinterpret_cast<MlpTcSmem4 *>(smem_raw);
-    mlp_tc4_load_weights(s.w, a.P);
+    const int64_t step = *a.d_step + a.kstep;
+    const int ring = (int)(step & 15);
+    mlp_tc4_load_weights(s.w, a.P, ring);
     mlp_tc4_setup(s);
     const int gi = threadIdx.x >> 7, r = threadIdx.x & 127;
     MlpTcGroup &g = s.g[gi];
     uint32_t phase = 0;
     bool ok = true;
-    const int64_t step = *a.d_step + a.kstep;
-    const int ring = (int)(step & 15);
+    __nv_bfloat16 *hist = reinterpret_cast<__nv_bfloat16 *>(a.hist);
     const int64_t ntiles = (a.n + kMlpRows - 1) / kMlpRows;
     for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + gi; tile < ntiles; tile += (int64_t)gridDim.x * kTcGroups) {
         const int64_t slot = tile * kMlpRows + r;
         const bool valid = slot < a.n;
-        float x[kMlpK1];
-#pragma unroll
-        for (int k = 0; k < kMlpK1; ++k) x[k] = 0.0f;
+        uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
+        float dn = 0.0f, dens = 0.0f;
         int32_t c = 0;
         float e = 0.0f;
         if (valid) {
             c = a.cell[slot];
+            uint4 *hp = reinterpret_cast<uint4 *>(hist + slot * 16);
+            h0 = hp[0];
+            h1 = hp[1];
+            dens = a.dens[slot];
             e = a.E[c];
-            float *h = a.hist + slot * 16;
-            h[ring] = e;
-            float hv[16];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 v = reinterpret_cast<const float4 *>(h)[q];
-                hv[4 * q] = v.x; hv[4 * q + 1] = v.y; hv[4 * q + 2] = v.z; hv[4 * q + 3] = v.w;
-            }
-#pragma unroll
-            for (int k = 0; k < 16; ++k) x[k] = hv[(ring + 1 + k) & 15] * a.inv_es;
-            x[16] = a.dens[slot] * a.inv_ns;
+            const __nv_bfloat16 eb = __float2bfloat16_rn(e * a.inv_es);
+            hist[slot * 16 + ring] = eb;
+            // this step's value into the loaded copy of the ring (slot `ring`: word ring / 2, half ring % 2)
+            const uint32_t bits = (uint32_t)__bfloat16_as_ushort(eb);
+            const uint32_t keep = (ring & 1) ? 0x0000ffffu : 0xffff0000u, put = (ring & 1) ? bits << 16 : bits;
+            const int wi = ring >> 1;
+            h0.x = wi == 0 ? (h0.x & keep) | put : h0.x;
+            h0.y = wi == 1 ? (h0.y & keep) | put : h0.y;
+            h0.z = wi == 2 ? (h0.z & keep) | put : h0.z;
+            h0.w = wi == 3 ? (h0.w & keep) | put : h0.w;
+            h1.x = wi == 4 ? (h1.x & keep) | put : h1.x;
+            h1.y = wi == 5 ? (h1.y & keep) | put : h1.y;
+            h1.z = wi == 6 ? (h1.z & keep) | put : h1.z;
+            h1.w = wi == 7 ? (h1.w & keep) | put : h1.w;
+            dn = dens * a.inv_ns;
         }
-        mlp_tc4_put_row(g, r, x);
+        mlp_tc4_put_row_ring(g, r, h0, h1, dn);
         const float y = mlp_tc4_tile(s.w, g, gi, r, &phase, &ok);
         if (!ok) break;
         if (valid) {
-            const float J = a.rho * a.jprev[slot] + a.beta * a.dens[slot] * e + a.js * y;
+            const float J = a.rho * a.jprev[slot] + a.beta * dens * e + a.js * y;
             a.jprev[slot] = J;
-            a.jslot[slot] = J;
+            if (a.store_j) a.jslot[slot] = J;
             a.E[c] = e - a.cj * J;
         }
     }

@@ -348,6 +348,7 @@ struct ClosureArgs {
     const int64_t *d_step;
     int kstep;
     int engine;        // 0: mma.sync warp tiles, 1: tcgen05 (TMEM accumulator)
+    int store_j;       // store J^{n+1/2} in jslot (jprev, the state, is always written)
     int *err;          // set to 1 if a bounded wait gave up
 };
 cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms);

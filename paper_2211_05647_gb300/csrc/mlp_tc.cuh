@@ -255,13 +255,17 @@ __device__ __forceinline__ float2 gelu2_f2(uint64_t z)
 // The epilogues form 2 gelu(z) = z + z tanh(u) (one multiply fewer than gelu); W2 and w3 are stored at
 // half scale to compensate.  Both scalings are by a power of two, so the BF16 operands and every product
 // equal those of the unscaled form exactly.
-__device__ __forceinline__ void mlp_tc4_load_weights(MlpTcWeights &s, const float *__restrict__ P)
+// ring >= 0: the first 16 inputs arrive in history-ring slot order (slot j holds E^{n-15+k} with
+// k = (j - ring - 1) mod 16, the oldest first in the network's order), so W1's rows are stored in that
+// order: the same products, the ring never rotated per cell.
+__device__ __forceinline__ void mlp_tc4_load_weights(MlpTcWeights &s, const float *__restrict__ P, int ring = -1)
 {
     unsigned char *w1 = reinterpret_cast<unsigned char *>(s.w1), *w2 = reinterpret_cast<unsigned char *>(s.w2);
     for (int i = threadIdx.x; i < kMlpH * kMlpK1; i += blockDim.x) {
         const int n = i / kMlpK1, k = i % kMlpK1;
+        const int kk = (ring >= 0 && k < 16) ? ((k - ring - 1) & 15) : k;
         *reinterpret_cast<__nv_bfloat16 *>(w1 + core_off(n, k, kMlpK1)) =
-            __float2bfloat16_rn(k < kMlpIn ? P[kOffW1 + k * kMlpH + n] : 0.0f);
+            __float2bfloat16_rn(k < kMlpIn ? P[kOffW1 + kk * kMlpH + n] : 0.0f);
     }
     for (int i = threadIdx.x; i < kMlpH * kMlpH; i += blockDim.x) {
         const int k = i / kMlpH, n = i % kMlpH;
@@ -314,6 +318,17 @@ __device__ __forceinline__ void mlp_tc4_put_row(MlpTcGroup &g, int r, const floa
         v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
         *reinterpret_cast<uint4 *>(xb + core_off(r, 8 * c, kMlpK1)) = v;
     }
+}
+
+// Thread r writes row r of the layer-1 input from its history ring (16 BF16 values in slot order, two
+// 16-byte vectors) and its scaled density; columns 17..31 are zero.
+__device__ __forceinline__ void mlp_tc4_put_row_ring(MlpTcGroup &g, int r, uint4 h0, uint4 h1, float dn)
+{
+    unsigned char *xb = reinterpret_cast<unsigned char *>(g.x);
+    *reinterpret_cast<uint4 *>(xb + core_off(r, 0, kMlpK1)) = h0;
+    *reinterpret_cast<uint4 *>(xb + core_off(r, 8, kMlpK1)) = h1;
+    *reinterpret_cast<uint4 *>(xb + core_off(r, 16, kMlpK1)) = make_uint4(pack_bf16(dn, 0.0f), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(xb + core_off(r, 24, kMlpK1)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // forward of warpgroup gi's tile (rows in g.x); thread r (0..127 inside the
