@@ -13,7 +13,7 @@ normalisation) and of J.
   256 batched 1-D runs, FP32, 5000 steps: every run's E within 1e-4 of the radiated pulse's norm (many
       small grids have shed the pulse through their Mur ends by then, leaving a residue far below it) and
       J within 1e-4 of the largest J norm the run reached (sampled every 500 steps: after the pulse has
-      passed, a slab's current decays by orders of magnitude)
+      passed, a slab's current decays by orders of magnitude), floored at 1e-6 A/m^2 per cell
 
 They take minutes of host time (the oracle) and tens of GB of host memory, so
 they run only when FDTD_FULL_RUN_TESTS=1."""
@@ -147,9 +147,11 @@ def test_batch1d_256_full_run():
     for r, w in enumerate(want):
         if not w[1][0].size:
             continue
-        scale = max(np.linalg.norm(j) for j in w[1])
+        # floored at 1e-6 A/m^2 per cell, as in the batched parity test: slabs the pulse reaches only at
+        # amplitudes below FP32's range (1e-59 here) hold J = 0 on the GPU
+        scale = max(max(np.linalg.norm(j) for j in w[1]), 1e-6 * np.sqrt(w[1][0].size))
         err = max(np.linalg.norm(gj[c][r] - w[1][c]) for c in range(len(gj)))
-        ej.append((err / scale if scale > 0 else err, r, scale, np.linalg.norm(w[1][-1])))
+        ej.append((err / scale, r, scale, np.linalg.norm(w[1][-1])))
     worst = max(ej)
     print(f"batch1d_256_f32: {len(specs)} runs x {steps} steps; worst rel L2 vs FP64 oracle: E {max(ee):.2e} of the "
           f"pulse norm; J {worst[0]:.2e} of the run's largest J norm (run {worst[1]}: largest {worst[2]:.3e}, "
