@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the autotuner (the launch shapes come from the tuning cache, else the defaults)")
     ap.add_argument("--kin-shape", default="",
-                    help="VPL,L[,BPS]: force the kinetic kernel's launch shape after autotuning (profiling)")
+                    help="VPL,L[,BPS[,STAGES]]: force the kinetic kernel's launch shape after autotuning (profiling)")
     ap.add_argument("--decompose", action="store_true",
                     help="N > 1: split the grid along its slowest axis, one slab per rank, halos over NCCL "
                          "(strong scaling); N = 1 is the whole-grid path")
@@ -189,7 +189,9 @@ def measured_peaks():
 
 def kinetic_src_sha(kernel: str = "k_kinetic") -> str:
     """Hash of the sources a kinetic kernel is built from (its ncu figures stay valid while it matches)."""
-    files = ("kinetic.cu", "kinetic_row.cuh") if kernel == "k_kinetic_f0" else ("kinetic_impl.cuh", "kinetic_row.cuh")
+    files = {"k_kinetic_f0": ("kinetic.cu", "kinetic_row.cuh"),
+             "k_kinetic_ring": ("kinetic_ring.cu", "kinetic_row.cuh", "async.cuh")}.get(
+        kernel, ("kinetic_impl.cuh", "kinetic_row.cuh"))
     h = hashlib.sha1()
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_2211_05647_gb300", "csrc", f), "rb").read())
@@ -198,7 +200,8 @@ def kinetic_src_sha(kernel: str = "k_kinetic") -> str:
 
 def ncu_traffic(kernel: str, workload: str, shape=None):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel source and the same launch shape (else None)."""
+    the current kernel source and the same launch shape (vpl, l, ring stages)
+    (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
@@ -208,10 +211,19 @@ def ncu_traffic(kernel: str, workload: str, shape=None):
             continue
         kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
         if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("src_sha") == sha:
-            if shape is not None and (int(kv.get("vpl", 0)), int(kv.get("l", 0))) != tuple(shape):
+            got = (int(kv.get("vpl", 0)), int(kv.get("l", 0)), int(kv.get("stages", 0)))
+            if shape is not None and got != tuple(shape):
                 continue
             return float(kv["dram_bytes_per_launch"])
     return None
+
+
+def kinetic_kernel(shapes: dict, evolve: bool):
+    """The kinetic kernel a handle launches and its launch shape (vpl, l, ring stages)."""
+    if evolve:
+        return "k_kinetic_f0", None
+    shape = (shapes["kin_vpl"], shapes["kin_l"], shapes.get("kin_stages", 0)) if shapes["kin_vpl"] else (8, 32, 0)
+    return ("k_kinetic_ring" if shape[2] > 0 else "k_kinetic"), shape
 
 
 # ---------------------------------------------------------------- oracle arm
@@ -299,7 +311,7 @@ def solver_config(workload: str, steps: int, warmup: int, autotune: bool, local:
     evolve = bool(spec["plasma"].get("evolve_f0"))
     alg = 2 * fbytes * ns * nn * (2 if evolve else 1)
     peak, src = _peak()
-    kname = "k_kinetic_f0" if evolve else "k_kinetic"
+    kname, kshape = kinetic_kernel(shapes, evolve)
     fb = 8 if spec["grid"].get("precision", "f32") == "f64" else 4
     ncomp = {1: 2, 2: 3, 3: 6}[spec["grid"]["ndim"]]
     step_alg = 2 * fb * ncomp * cells + alg
@@ -314,8 +326,7 @@ def solver_config(workload: str, steps: int, warmup: int, autotune: bool, local:
             "roofline": {"bound": "latency" if spec["grid"]["ndim"] == 1 else "hbm", "kernel": kname,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "alg_bytes_per_launch": alg, "launch_ms": kt["kinetic"],
-                         "traffic": ncu_traffic(kname, workload, None if evolve else
-                                                (shapes["kin_vpl"], shapes["kin_l"]) if shapes["kin_vpl"] else (8, 32)),
+                         "traffic": ncu_traffic(kname, workload, kshape),
                          "peak_source": src},
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "gpu_launches": step_launches(steps, 1 if ns else 0, False)}
@@ -590,8 +601,8 @@ def main():
     s.set_option("fused_stencils", args.fused)
     tune = None if args.no_autotune else s.autotune()   # untimed: picks the launch shapes
     if args.kin_shape:
-        v = [int(x) for x in args.kin_shape.split(",")] + [0]
-        s.set_option("kinetic_shape", v[0] * 1000000 + v[1] * 1000 + v[2])
+        v = [int(x) for x in args.kin_shape.split(",")] + [0, 0]
+        s.set_option("kinetic_shape", v[3] * 10**9 + v[0] * 1000000 + v[1] * 1000 + v[2])
     shapes = s.launch_shapes()                           # the shapes in use (tuned, cached or default)
 
     def barrier():
@@ -676,12 +687,10 @@ def main():
     achieved = alg_bytes / (kt["kinetic"] / 1e3) / 1e9
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    kname = "k_kinetic_f0" if evolve else "k_kinetic"
+    kname, kshape = kinetic_kernel(shapes, evolve)
     roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": ncu_traffic(kname, args.workload,
-                                   None if evolve else
-                                   (shapes["kin_vpl"], shapes["kin_l"]) if shapes["kin_vpl"] else (8, 32)),
+            "traffic": ncu_traffic(kname, args.workload, kshape),
             "alg_bytes_per_launch": alg_bytes, "launch_ms": kt["kinetic"],
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"}
     fb = 8 if s.precision == "f64" else 4

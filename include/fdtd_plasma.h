@@ -214,6 +214,11 @@ typedef struct {
     int32_t stencil_tz;                          /* FP32, nx a multiple of 4: > 0 when the TMA stencils won
                                                     -- 32 x 8 threads, each block walking stencil_tz planes
                                                     (3-D) or rows (2-D); 0 = grid-of-cells kernels */
+    int32_t kin_stages;                          /* 0 = the register kernel; S > 0 = the bulk-copy ring
+                                                    kernel with S shared-memory stages (FP32 / BF16 rows:
+                                                    a producer warp copies chunks of 256 / kin_l rows, with
+                                                    their cell indices and densities, ahead of eight
+                                                    consumer warps; same results bit for bit) */
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
@@ -259,10 +264,13 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * autotuner sets it too (fdtd_tune_result.stencil_tz).  Results equal the
  * one-cell-per-thread kernels bit for bit.
  * FDTD_OPT_KINETIC_SHAPE: the kinetic kernel's launch shape, value =
- * vpl * 1000000 + l * 1000 + bps (vectors per lane, lanes per row, CTAs per
- * SM cap or 0), which must be one of the row length's candidates (the ones
- * fdtd_plasma_autotune times); 0 returns to the built-in default.  Needs a
- * plasma (after set_plasma).  The autotuner overwrites it.
+ * stages * 10^9 + vpl * 10^6 + l * 1000 + bps (ring stages or 0, vectors per
+ * lane, lanes per row, CTAs per SM cap or 0); (vpl, l) must be one of the row
+ * length's candidates (the ones fdtd_plasma_autotune times), stages 0 (the
+ * register kernel) or 2..64 (the bulk-copy ring kernel: FP32 / BF16 rows of
+ * the linear update, stages that fit in one CTA's shared memory); 0 returns
+ * to the built-in default.
+ * Needs a plasma (after set_plasma).  The autotuner overwrites it.
  * FDTD_ERR_INVAL for an unknown option or value. */
 enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);

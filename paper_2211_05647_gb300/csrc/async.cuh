@@ -70,6 +70,31 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t byte
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(m)), "r"(bytes) : "memory");
 }
 
+// one of the barrier's `count` arrivals (release: this thread's earlier shared-memory reads are done)
+__device__ __forceinline__ void mbar_arrive(uint64_t *m)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(m)) : "memory");
+}
+
+// contiguous bulk copy global -> this CTA's shared memory, completion counted
+// in bytes on mbarrier m; both addresses 16-byte aligned, bytes a multiple of
+// 16.  evict_first: the source is streamed once (an L2 eviction-priority hint).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *m, bool evict_first)
+{
+    if (evict_first) {
+        uint64_t pol;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+            ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m)), "l"(pol)
+            : "memory");
+    } else {
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(m))
+                     : "memory");
+    }
+}
+
 // tiled 2-D tensor load global -> shared (as tma_load_3d, one dimension fewer)
 __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_t *m, int x, int y)
 {

@@ -335,6 +335,7 @@ KinArgs<T> kin_args(fdtd_plasma *h, int kstep)
     a.kstep = kstep;
     a.slot_base = h->slot_base;
     a.store_j = 1;
+    a.err = h->d_err;
     return a;
 }
 
@@ -423,7 +424,10 @@ void apply_cached_kinetic(fdtd_plasma *h)
 {
     auto m = read_cache();
     auto it = m.find(kin_key(h));
-    if (it != m.end()) { h->kin_vpl = it->second[0]; h->kin_l = it->second[1]; h->kin_bps = it->second[2]; }
+    if (it != m.end()) {
+        h->kin_vpl = it->second[0]; h->kin_l = it->second[1]; h->kin_bps = it->second[2];
+        h->kin_stages = it->second.size() >= 4 ? it->second[3] : 0;
+    }
 }
 
 void apply_cached_stencil(fdtd_plasma *h)
@@ -535,7 +539,7 @@ cudaError_t part_mid(fdtd_plasma *h, cudaStream_t st, int kstep, const FieldSet<
             const int nperp = h->pl.vgrid == FDTD_VGRID_CART2D ? h->pl.nv_perp : 1;
             e = launch_kinetic_nl<T>(st, a, h->pl.nv, nperp, dvpar, kQe / kMe, h->dt, h->num_sms);
         } else {
-            e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, h->kin_vpl, h->kin_l, h->kin_bps);
+            e = launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, h->kin_vpl, h->kin_l, h->kin_bps, h->kin_stages);
         }
         if (e != cudaSuccess) return e;
     }
@@ -990,7 +994,8 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
     }
     if (option == FDTD_OPT_KINETIC_SHAPE) {
         if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "FDTD_OPT_KINETIC_SHAPE needs a plasma (set_plasma first)");
-        const int vpl = (int)(value / 1000000), l = (int)(value / 1000 % 1000), bps = (int)(value % 1000);
+        const int stages = (int)(value / 1000000000), vpl = (int)(value / 1000000 % 1000),
+                  l = (int)(value / 1000 % 1000), bps = (int)(value % 1000);
         if (value != 0) {
             int cand[32][2];
             const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
@@ -999,12 +1004,19 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
             if (value < 0 || !ok)
                 return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_KINETIC_SHAPE: %lld is not a candidate shape of this row length",
                             (long long)value);
+            if (stages > 0 && (stages > 64 || h->pl.nonlinear || h->pl.evolve_f0 ||
+                               !kinetic_ring_fits(h->pitch, h->pl.f_dtype, l, stages)))
+                return fail(h, FDTD_ERR_INVAL,
+                            "FDTD_OPT_KINETIC_SHAPE: %d ring stages (2..64 that fit in shared memory; FP32 / BF16 rows "
+                            "of the linear update only)",
+                            stages);
         }
         CK(h, cudaStreamSynchronize(h->stream));
         drop_graphs(h);
         h->kin_vpl = vpl;
         h->kin_l = l;
         h->kin_bps = bps;
+        h->kin_stages = stages;
         return FDTD_OK;
     }
     return fail(h, FDTD_ERR_INVAL, "unknown option %d", option);
@@ -1017,6 +1029,7 @@ int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out)
     out->kin_vpl = h->kin_vpl;
     out->kin_l = h->kin_l;
     out->kin_blocks_per_sm = h->kin_bps;
+    out->kin_stages = h->kin_stages;
     if (h->g.ndim >= 2) {
         const dim3 b = stencil_block(h);
         out->block_x = (int32_t)b.x; out->block_y = (int32_t)b.y; out->block_z = (int32_t)b.z;
@@ -1214,8 +1227,10 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     h->nnode = nnode;
     h->pitch = pitch;
     h->df_esz = p->f_dtype == FDTD_DF_BF16 ? 2 : (p->f_dtype == FDTD_DF_F64 ? 8 : 4);
-    h->slot_cell = (int32_t *)dalloc(h, (ns ? ns : 1) * 4);
-    h->dens = dalloc(h, (ns ? ns : 1) * h->esz);
+    // slot index and density arrays in multiples of four entries: the ring kernel's bulk copies of them are
+    // rounded up to 16 bytes
+    h->slot_cell = (int32_t *)dalloc(h, ((ns + 3) & ~(size_t)3) * 4);
+    h->dens = dalloc(h, ((ns + 3) & ~(size_t)3) * h->esz);
     h->df = dalloc(h, (ns ? ns : 1) * pitch * h->df_esz);
     h->jslot = dalloc(h, (ns ? ns : 1) * h->esz);
     h->tab = dalloc(h, tab.size() * h->esz);
@@ -1232,7 +1247,7 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     h->has_plasma = 1;
     h->slot_base = slot_base;
     h->nkin = (int64_t)ns;
-    h->kin_vpl = h->kin_l = h->kin_bps = 0;
+    h->kin_vpl = h->kin_l = h->kin_bps = h->kin_stages = 0;
     apply_cached_kinetic(h);
     h->h_cells = cells;
     h->h_dens = dslot;
@@ -1417,8 +1432,8 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
     drop_graphs(h);
     free_closure(h);
     dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot);
-    h->slot_cell = (int32_t *)dalloc(h, (ns ? ns : 1) * 4);
-    h->dens = dalloc(h, (ns ? ns : 1) * 4);
+    h->slot_cell = (int32_t *)dalloc(h, ((ns + 3) & ~(int64_t)3) * 4);
+    h->dens = dalloc(h, ((ns + 3) & ~(int64_t)3) * 4);
     h->df = dalloc(h, (nk ? nk : 1) * h->pitch * h->df_esz);
     h->jslot = dalloc(h, (ns ? ns : 1) * 4);
     h->hist = (float *)dalloc(h, (nc ? nc : 1) * 16 * 4);
@@ -1582,28 +1597,34 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
         out->stencil_ms = best;
         m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z, out->cells_per_thread, out->stencil_tz};
     }
-    out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = 0;
+    out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = out->kin_stages = 0;
     out->kin_ms = 0;
     if (h->has_plasma && h->nkin > 0 && !h->pl.nonlinear && !h->pl.evolve_f0) {
         int cand[8][2];
         const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
         const KinArgs<T> a = kin_args<T>(h, 0);
+        // (ring stages, CTAs per SM cap): the register kernel, then the bulk-copy ring (FP32 / BF16 rows)
+        static const int variants[][2] = {{0, 0}, {0, 2}, {0, 3}, {3, 0}, {4, 0}, {6, 0}, {8, 0}};
         double best = 1e30;
         for (int c = 0; c < nc; ++c)
-            for (int bps : {0, 2, 3}) {
+            for (const auto &vr : variants) {
+                if (vr[0] > 0 && h->pl.f_dtype == FDTD_DF_F64) continue;
                 bool bad = false;
                 const double ms = time_ms([&] {
-                    if (launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, cand[c][0], cand[c][1], bps) != cudaSuccess)
+                    if (launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, cand[c][0], cand[c][1], vr[1], vr[0]) !=
+                        cudaSuccess)
                         bad = true;
                 });
                 if (!bad && ms < best * kTuneMargin) {
                     best = ms;
-                    out->kin_vpl = cand[c][0]; out->kin_l = cand[c][1]; out->kin_blocks_per_sm = bps;
+                    out->kin_vpl = cand[c][0]; out->kin_l = cand[c][1]; out->kin_blocks_per_sm = vr[1];
+                    out->kin_stages = vr[0];
                 }
             }
         h->kin_vpl = out->kin_vpl; h->kin_l = out->kin_l; h->kin_bps = out->kin_blocks_per_sm;
+        h->kin_stages = out->kin_stages;
         out->kin_ms = best;
-        m[kin_key(h)] = {out->kin_vpl, out->kin_l, out->kin_blocks_per_sm};
+        m[kin_key(h)] = {out->kin_vpl, out->kin_l, out->kin_blocks_per_sm, out->kin_stages};
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

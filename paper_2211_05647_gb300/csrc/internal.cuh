@@ -114,6 +114,7 @@ struct KinArgs {
                                // draws like the whole grid's)
     int store_j;               // k_kinetic: store J^{n+1/2} per slot (the last step of a sequence, or
                                // when something reads it every step); E is updated either way
+    int *err;                  // set to 1 if a bounded wait of the bulk-copy ring kernel gave up
 };
 
 // Isotropic-F0 evolution (speed grid): per-node tables, each `pitch` long,
@@ -274,10 +275,16 @@ int kinetic_pitch(int nnode, int f_dtype);
 // launch shape candidates (vectors per lane, lanes per row) for a row pitch; the first is the default
 int kinetic_candidates(int pitch, int f_dtype, int (*out)[2]);
 // returns cudaErrorInvalidValue for an unsupported combination; vpl <= 0 picks the default shape,
-// bps > 0 caps the CTAs per SM
+// bps > 0 caps the CTAs per SM; stages > 0 (FP32 / BF16 storage) selects the bulk-copy ring kernel
+// with that many shared-memory stages (kinetic_ring.cu)
 template <typename TA>
 cudaError_t launch_kinetic(cudaStream_t st, const KinArgs<TA> &a, int f_dtype, int num_sms, int vpl = 0, int l = 0,
-                           int bps = 0);
+                           int bps = 0, int stages = 0);
+// whether the ring kernel's tables and stages fit in one CTA's shared memory (FP32 / BF16 rows, stages >= 2)
+bool kinetic_ring_fits(int pitch, int f_dtype, int l, int stages);
+// the bulk-copy ring kernel for an FP32 / BF16 row shape (cudaErrorInvalidValue if the stages do not fit)
+cudaError_t launch_kinetic_ring(cudaStream_t st, const KinArgs<float> &a, int f_dtype, int num_sms, int vpl, int l,
+                                int bps, int stages);
 // nonlinear mode (FP32 / FP64 storage): npar x nperp nodes, v_par spacing dvpar, qm = e/m
 template <typename T>
 cudaError_t launch_kinetic_f0(cudaStream_t st, const KinArgs<T> &a, const F0Args<T> &f, int num_sms);
@@ -419,7 +426,7 @@ struct fdtd_plasma {
     // training-data recorder
     // launch shapes (autotuner / cache): kinetic (vectors per lane, lanes per row, CTAs per SM; 0 = default),
     // stencil block (0 = default)
-    int kin_vpl, kin_l, kin_bps;
+    int kin_vpl, kin_l, kin_bps, kin_stages;   // kinetic launch shape; kin_stages > 0: the bulk-copy ring kernel
     int st_bx, st_by, st_bz, st_cpt;
     int st_tz;                // > 0: 3-D FP32 stencils run the TMA column kernels with tz planes per block
     fp::TmaMaps *tma;         // their tensor maps (field set 0), made on first use

@@ -43,7 +43,7 @@ cudaError_t dispatch_kinetic_f64(cudaStream_t st, const KinArgs<double> &a, int 
 
 template <>
 cudaError_t launch_kinetic<float>(cudaStream_t st, const KinArgs<float> &a, int f_dtype, int num_sms, int vpl, int l,
-                                  int bps)
+                                  int bps, int stages)
 {
     if (a.nslots == 0) return cudaSuccess;
     if (vpl <= 0) {
@@ -52,6 +52,7 @@ cudaError_t launch_kinetic<float>(cudaStream_t st, const KinArgs<float> &a, int 
         vpl = c[0][0];
         l = c[0][1];
     }
+    if (stages > 0) return launch_kinetic_ring(st, a, f_dtype, num_sms, vpl, l, bps, stages);
     if (f_dtype == FDTD_DF_F32) return dispatch_kinetic<float, float>(st, a, num_sms, vpl, l, bps);
     if (f_dtype == FDTD_DF_BF16) return dispatch_kinetic_bf16(st, a, num_sms, vpl, l, bps);
     return cudaErrorInvalidValue;
@@ -59,9 +60,10 @@ cudaError_t launch_kinetic<float>(cudaStream_t st, const KinArgs<float> &a, int 
 
 template <>
 cudaError_t launch_kinetic<double>(cudaStream_t st, const KinArgs<double> &a, int f_dtype, int num_sms, int vpl, int l,
-                                   int bps)
+                                   int bps, int stages)
 {
     if (a.nslots == 0) return cudaSuccess;
+    if (stages > 0) return cudaErrorInvalidValue;   // the ring kernel streams FP32 / BF16 rows only
     if (vpl <= 0) {
         int c[8][2];
         kinetic_candidates(a.pitch, f_dtype, c);
