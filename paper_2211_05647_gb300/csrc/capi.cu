@@ -1604,7 +1604,7 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
         const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
         const KinArgs<T> a = kin_args<T>(h, 0);
         // (ring stages, CTAs per SM cap): the register kernel, then the bulk-copy ring (FP32 / BF16 rows)
-        static const int variants[][2] = {{0, 0}, {0, 2}, {0, 3}, {3, 0}, {4, 0}, {6, 0}, {8, 0}};
+        static const int variants[][2] = {{0, 0}, {0, 2}, {0, 3}, {2, 0}, {3, 0}, {4, 0}, {6, 0}};
         double best = 1e30;
         for (int c = 0; c < nc; ++c)
             for (const auto &vr : variants) {

@@ -8,10 +8,14 @@
 // mbarrier per stage); eight consumer warps update the rows from shared
 // memory and store them back with streaming stores, then release the stage.
 // The bytes in flight per SM are the ring's (several chunks per CTA), not what
-// the consumer threads' registers can hold -- the limit of the register
-// kernel on short rows (64-128 bytes of BF16).  The consumers gather E for
-// the next chunk while they update the current one (each cell has one row, so
+// the consumer threads' registers can hold.  The consumers gather E for the
+// next chunk while they update the current one (each cell has one row, so
 // those E values are not written by this launch before they are read).
+// On GB300 this wins on long FP32 rows (2-D 4096^2, 1024 nodes: 16 rows x
+// 4 KB a chunk, three stages, at the measured copy bandwidth); short BF16 rows
+// (64-128 bytes) are bound by their stochastic-rounding arithmetic at the
+// occupancy they get, and the register kernel stays faster there (the
+// autotuner times both).
 //
 // A chunk is one pass of the consumer threads: 256 / L rows, each row's
 // VPL * L vectors held VPL per lane, exactly as in the register kernel, and
