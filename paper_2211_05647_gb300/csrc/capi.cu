@@ -1602,25 +1602,50 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
     if (h->has_plasma && h->nkin > 0 && !h->pl.nonlinear && !h->pl.evolve_f0) {
         int cand[8][2];
         const int nc = kinetic_candidates(h->pitch, h->pl.f_dtype, cand);
-        const KinArgs<T> a = kin_args<T>(h, 0);
-        // (ring stages, CTAs per SM cap): the register kernel, then the bulk-copy ring (FP32 / BF16 rows)
+        // (ring stages, CTAs per SM cap): the register kernel, then the bulk-copy ring (FP32 / BF16 rows).
+        // Each candidate is timed where it runs, between the H and E stencils of whole steps (events around
+        // the middle part, as fdtd_plasma_time_kernels does): timed back to back on their own, some ring
+        // shapes that lose inside the step looked fastest.
         static const int variants[][2] = {{0, 0}, {0, 2}, {0, 3}, {2, 0}, {3, 0}, {4, 0}, {6, 0}};
+        cudaEvent_t ev[5];
+        for (int q = 0; q < 5; ++q) CK(h, cudaEventCreate(&ev[q]));
+        auto time_in_step = [&](bool &bad) -> double {
+            double acc = 0.0;
+            for (int r = 0; r < 6 && !bad; ++r) {
+                cudaError_t e = enqueue_step<T>(h, st, 0, ev, true);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    bad = true;
+                    break;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev[1], ev[2]);
+                if (r > 0) acc += ms;   // the first step is the warm-up
+            }
+            return acc / 5.0;
+        };
+        const int keep[3] = {h->kin_vpl, h->kin_l, h->kin_bps}, keep_stages = h->kin_stages;
         double best = 1e30;
         for (int c = 0; c < nc; ++c)
             for (const auto &vr : variants) {
-                if (vr[0] > 0 && h->pl.f_dtype == FDTD_DF_F64) continue;
+                if (vr[0] > 0 && (h->pl.f_dtype == FDTD_DF_F64 || !kinetic_ring_fits(h->pitch, h->pl.f_dtype,
+                                                                                       cand[c][1], vr[0])))
+                    continue;
                 bool bad = false;
-                const double ms = time_ms([&] {
-                    if (launch_kinetic<T>(st, a, h->pl.f_dtype, h->num_sms, cand[c][0], cand[c][1], vr[1], vr[0]) !=
-                        cudaSuccess)
-                        bad = true;
-                });
+                h->kin_vpl = cand[c][0]; h->kin_l = cand[c][1]; h->kin_bps = vr[1]; h->kin_stages = vr[0];
+                const double ms = time_in_step(bad);
                 if (!bad && ms < best * kTuneMargin) {
                     best = ms;
                     out->kin_vpl = cand[c][0]; out->kin_l = cand[c][1]; out->kin_blocks_per_sm = vr[1];
                     out->kin_stages = vr[0];
                 }
             }
+        for (int q = 0; q < 5; ++q) cudaEventDestroy(ev[q]);
+        if (best >= 1e30) {   // nothing ran: keep the shape in use
+            out->kin_vpl = keep[0]; out->kin_l = keep[1]; out->kin_blocks_per_sm = keep[2];
+            out->kin_stages = keep_stages;
+        }
         h->kin_vpl = out->kin_vpl; h->kin_l = out->kin_l; h->kin_bps = out->kin_blocks_per_sm;
         h->kin_stages = out->kin_stages;
         out->kin_ms = best;
