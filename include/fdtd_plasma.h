@@ -219,9 +219,6 @@ typedef struct {
                                                     a producer warp copies chunks of 256 / kin_l rows, with
                                                     their cell indices and densities, ahead of eight
                                                     consumer warps; same results bit for bit) */
-    int32_t slot_runs;                           /* runs of consecutive plasma cells of one density the
-                                                    register kernel walks instead of its per-slot index and
-                                                    density arrays (FDTD_OPT_SLOT_RUNS); 0 = per-slot arrays */
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
@@ -274,14 +271,8 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * the linear update, stages that fit in one CTA's shared memory); 0 returns
  * to the built-in default.
  * Needs a plasma (after set_plasma).  The autotuner overwrites it.
- * FDTD_OPT_SLOT_RUNS (default 1): 1 lets the register kinetic kernel walk
- * slot runs -- maximal runs of consecutive kinetic slots whose cells are
- * consecutive and whose stored densities are equal (a slab, a layered
- * profile) -- instead of reading a cell index and a density per slot, when
- * a run averages at least 64 slots; 0 keeps the per-slot arrays.  Results
- * are identical bit for bit (fdtd_tune_result.slot_runs reports the count).
  * FDTD_ERR_INVAL for an unknown option or value. */
-enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3, FDTD_OPT_SLOT_RUNS = 4 };
+enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);
 
 /* The launch shapes the handle uses now (tuned, cached or default; kinetic

@@ -180,65 +180,9 @@ void free_closure(fdtd_plasma *h)
     h->nkin = h->nslots;
 }
 
-void free_slot_runs(fdtd_plasma *h)
-{
-    dfree(h, h->run_slot0); dfree(h, h->run_cell0); dfree(h, h->run_dens);
-    h->run_slot0 = h->run_cell0 = h->run_dens = nullptr;
-    h->nruns = 0;
-}
-
-// Slot runs of the first n slots (the kinetic ones): maximal runs of consecutive slots whose cells are
-// consecutive and whose densities, as stored (FP32 or FP64), are equal -- a slab or any piecewise-uniform
-// layer.  Kept only when a run averages at least kMinRunRows slots (the search stops as soon as there are
-// more runs than that allows); otherwise, or with FDTD_OPT_SLOT_RUNS = 0, the kernel reads the per-slot
-// index and density arrays.
-constexpr int64_t kMinRunRows = 64;
-
-int build_slot_runs(fdtd_plasma *h, int64_t n)
-{
-    free_slot_runs(h);
-    if (n <= 0 || h->slot_runs_off || (int64_t)h->h_cells.size() < n) return FDTD_OK;
-    const std::vector<int32_t> &c = h->h_cells;
-    const std::vector<double> &d = h->h_dens;
-    const bool f32 = h->esz == 4;
-    auto same = [&](int64_t a, int64_t b) { return f32 ? (float)d[a] == (float)d[b] : d[a] == d[b]; };
-    const int64_t cap = n / kMinRunRows;
-    std::vector<int64_t> s0;
-    std::vector<int32_t> c0;
-    std::vector<double> dv;
-    for (int64_t q = 0; q < n; ++q) {
-        if (q > 0 && c[q] == c[q - 1] + 1 && same(q, q - 1)) continue;
-        if ((int64_t)s0.size() >= cap) return FDTD_OK;
-        s0.push_back(q);
-        c0.push_back(c[q]);
-        dv.push_back(d[q]);
-    }
-    const int64_t nr = (int64_t)s0.size();
-    s0.push_back(n);
-    h->run_slot0 = dalloc(h, (size_t)(nr + 1) * 8);
-    h->run_cell0 = dalloc(h, (size_t)nr * 4);
-    h->run_dens = dalloc(h, (size_t)nr * h->esz);
-    if (!h->run_slot0 || !h->run_cell0 || !h->run_dens) {   // the per-slot arrays still serve
-        free_slot_runs(h);
-        h->err.clear();
-        return FDTD_OK;
-    }
-    CK(h, cudaMemcpy(h->run_slot0, s0.data(), s0.size() * 8, cudaMemcpyHostToDevice));
-    CK(h, cudaMemcpy(h->run_cell0, c0.data(), c0.size() * 4, cudaMemcpyHostToDevice));
-    if (f32) {
-        std::vector<float> d32(dv.begin(), dv.end());
-        CK(h, cudaMemcpy(h->run_dens, d32.data(), d32.size() * 4, cudaMemcpyHostToDevice));
-    } else {
-        CK(h, cudaMemcpy(h->run_dens, dv.data(), dv.size() * 8, cudaMemcpyHostToDevice));
-    }
-    h->nruns = nr;
-    return FDTD_OK;
-}
-
 void free_plasma(fdtd_plasma *h)
 {
     free_closure(h);
-    free_slot_runs(h);
     dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot); dfree(h, h->tab);
     dfree(h, h->dV); dfree(h, h->g0); dfree(h, h->tab_f0);
     h->slot_cell = nullptr; h->dens = h->df = h->jslot = h->tab = nullptr; h->dV = nullptr;
@@ -392,10 +336,6 @@ KinArgs<T> kin_args(fdtd_plasma *h, int kstep)
     a.slot_base = h->slot_base;
     a.store_j = 1;
     a.err = h->d_err;
-    a.run_slot0 = static_cast<const int64_t *>(h->run_slot0);
-    a.run_cell0 = static_cast<const int32_t *>(h->run_cell0);
-    a.run_dens = static_cast<const T *>(h->run_dens);
-    a.nruns = h->nruns;
     return a;
 }
 
@@ -1052,13 +992,6 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
         if (value > 0) { h->st_bx = 32; h->st_by = 8; h->st_bz = 1; h->st_cpt = 1; }
         return FDTD_OK;
     }
-    if (option == FDTD_OPT_SLOT_RUNS) {
-        if (value != 0 && value != 1) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_SLOT_RUNS takes 0 or 1");
-        CK(h, cudaStreamSynchronize(h->stream));
-        drop_graphs(h);
-        h->slot_runs_off = value == 0;
-        return h->has_plasma ? build_slot_runs(h, h->nkin) : FDTD_OK;
-    }
     if (option == FDTD_OPT_KINETIC_SHAPE) {
         if (!h->has_plasma) return fail(h, FDTD_ERR_STATE, "FDTD_OPT_KINETIC_SHAPE needs a plasma (set_plasma first)");
         const int stages = (int)(value / 1000000000), vpl = (int)(value / 1000000 % 1000),
@@ -1097,7 +1030,6 @@ int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out)
     out->kin_l = h->kin_l;
     out->kin_blocks_per_sm = h->kin_bps;
     out->kin_stages = h->kin_stages;
-    out->slot_runs = (int32_t)h->nruns;
     if (h->g.ndim >= 2) {
         const dim3 b = stencil_block(h);
         out->block_x = (int32_t)b.x; out->block_y = (int32_t)b.y; out->block_z = (int32_t)b.z;
@@ -1341,7 +1273,6 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     CK(h, cudaMemsetAsync(h->df, 0, (ns ? ns : 1) * pitch * h->df_esz, h->stream));
     CK(h, cudaMemsetAsync(h->jslot, 0, (ns ? ns : 1) * h->esz, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (const int rc = build_slot_runs(h, (int64_t)ns); rc != FDTD_OK) return rc;
     return FDTD_OK;
 }
 
@@ -1527,7 +1458,7 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
     h->cl = *c;
     h->cl.params = nullptr;
     h->has_closure = 1;
-    return build_slot_runs(h, nk);   // the kinetic (fallback) slots were re-laid out
+    return FDTD_OK;
 }
 
 int fdtd_plasma_closure_shape(fdtd_plasma_t h, int64_t *n_kinetic, int64_t *n_closure)
@@ -1667,7 +1598,6 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
         m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z, out->cells_per_thread, out->stencil_tz};
     }
     out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = out->kin_stages = 0;
-    out->slot_runs = (int32_t)h->nruns;
     out->kin_ms = 0;
     if (h->has_plasma && h->nkin > 0 && !h->pl.nonlinear && !h->pl.evolve_f0) {
         int cand[8][2];

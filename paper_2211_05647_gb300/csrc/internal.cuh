@@ -115,31 +115,7 @@ struct KinArgs {
     int store_j;               // k_kinetic: store J^{n+1/2} per slot (the last step of a sequence, or
                                // when something reads it every step); E is updated either way
     int *err;                  // set to 1 if a bounded wait of the bulk-copy ring kernel gave up
-    // slot runs (nruns > 0): runs of consecutive slots whose cells are consecutive and whose stored densities
-    // are equal; run q covers slots [run_slot0[q], run_slot0[q + 1]) from cell run_cell0[q] at density
-    // run_dens[q] (run_slot0 has nruns + 1 entries).  The register kernel then reads neither slot_cell nor dens.
-    const int64_t *run_slot0;
-    const int32_t *run_cell0;
-    const TA *run_dens;
-    int64_t nruns;
 };
-
-// the run holding `row` (rows of one thread only grow): cursor ri moves forward by binary search
-template <typename TA>
-__device__ __forceinline__ void run_locate(const KinArgs<TA> &a, int64_t row, int64_t &ri, int32_t &cell, TA &dens)
-{
-    if (__ldg(a.run_slot0 + ri + 1) <= row) {
-        int64_t lo = ri + 1, hi = a.nruns - 1;   // run_slot0[lo] <= row < run_slot0[nruns]
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(a.run_slot0 + mid) <= row) lo = mid;
-            else hi = mid - 1;
-        }
-        ri = lo;
-    }
-    cell = __ldg(a.run_cell0 + ri) + (int32_t)(row - __ldg(a.run_slot0 + ri));
-    dens = __ldg(a.run_dens + ri);
-}
 
 // Isotropic-F0 evolution (speed grid): per-node tables, each `pitch` long,
 // [f0 | f0' | bq | v^3 | 1/(v^2 gam) | 1/(2 v_e) | (m/M) v_e^3 nu_e | k Tg/(m v_e gam)]
@@ -451,9 +427,6 @@ struct fdtd_plasma {
     // launch shapes (autotuner / cache): kinetic (vectors per lane, lanes per row, CTAs per SM; 0 = default),
     // stencil block (0 = default)
     int kin_vpl, kin_l, kin_bps, kin_stages;   // kinetic launch shape; kin_stages > 0: the bulk-copy ring kernel
-    void *run_slot0, *run_cell0, *run_dens;    // slot runs of the kinetic slots (KinArgs), nruns = 0: none
-    int64_t nruns;
-    int slot_runs_off;                         // FDTD_OPT_SLOT_RUNS = 0
     int st_bx, st_by, st_bz, st_cpt;
     int st_tz;                // > 0: 3-D FP32 stencils run the TMA column kernels with tz planes per block
     fp::TmaMaps *tma;         // their tensor maps (field set 0), made on first use

@@ -27,20 +27,14 @@ __global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
     const int64_t step = *a.d_step + a.kstep;
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
 
-    // per-slot arrays: the slot -> cell index of the next row group is fetched
-    // one iteration ahead, so the E gather of a row issues together with its
-    // delta-f loads.  Slot runs: cell and density follow from the row's run
-    // (a small table that stays in L1), nothing per row is read.
-    const bool runs = a.nruns > 0;
-    int64_t ri = 0;
+    // the slot -> cell index of the next row group is fetched one iteration
+    // ahead, so the E gather of a row issues together with its delta-f loads
     int64_t row = wg * R + sub;
-    int32_t cell_next = (!runs && row < a.nslots) ? __ldg(a.slot_cell + row) : 0;
+    int32_t cell_next = row < a.nslots ? __ldg(a.slot_cell + row) : 0;
     for (int64_t base = wg * R; base < a.nslots; base += nw * R) {
         row = base + sub;
         const bool valid = row < a.nslots;
-        int32_t cell = cell_next;
-        TA dens = TA(0);
-        if (runs && valid) run_locate(a, row, ri, cell, dens);
+        const int32_t cell = cell_next;
         V v[VPL];
         TA E = TA(0), nE = TA(0);
         V *rp = reinterpret_cast<V *>(a.df) + (valid ? row : 0) * (a.pitch / VEC);
@@ -48,10 +42,10 @@ __global__ void __launch_bounds__(256) k_kinetic(KinArgs<TA> a)
 #pragma unroll
             for (int q = 0; q < VPL; ++q) v[q] = __ldcs(rp + q * L + l);
             E = a.E[cell];
-            nE = (runs ? dens : __ldg(a.dens + row)) * E;
+            nE = __ldg(a.dens + row) * E;
         }
         const int64_t row_next = row + nw * R;
-        if (!runs) cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
+        cell_next = row_next < a.nslots ? __ldg(a.slot_cell + row_next) : 0;
         TA s = TA(0), c = TA(0);
         if (valid) row_update<TS, TA, VPL, L>(rp, v, s_al, s_be, s_w, nE, l, (uint32_t)(row + a.slot_base), step, key, s, c);
         const TA J = row_reduce<TA, L>(s, c);
