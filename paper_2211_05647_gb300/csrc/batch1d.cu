@@ -14,11 +14,12 @@
 // (E <- E - dt/eps0 J in place; the run's per-node tables are staged in shared
 // memory, the next row is loaded while the current one is updated), then E,
 // the source and the Mur ends on its range, and the cluster synchronises again.  The H and E
-// loops move 4-node quads (16-byte loads and stores: run arrays are aligned and
-// padded, CTA ranges start on a multiple of 4 nodes), the +-1 neighbour from the
-// adjacent lane; partial quads, the source node and the Mur ends are stored
-// node by node.  Clusters never wait for each
-// other.  Cuts never separate node 0 from node 1 or node nz-1 from node nz,
+// loops move 4-node quads (16-byte copies and stores: run arrays are aligned and
+// padded, CTA ranges start on a multiple of 4 nodes), staged in shared memory by
+// cp.async in three buffers, so two rounds' loads are in flight while a round is
+// computed; the +-1 neighbour is the staged buffer's next or previous value;
+// partial quads, the source node and the Mur ends are stored node by node.
+// Clusters never wait for each other.  Cuts never separate node 0 from node 1 or node nz-1 from node nz,
 // so the thread that advances E_1 (E_{nz-1}) also applies the Mur update to
 // E_0 (E_nz) with values it owns.
 #include <cooperative_groups.h>
@@ -35,6 +36,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "async.cuh"
 #include "kinetic_row.cuh"
 
 namespace cg = cooperative_groups;
@@ -115,17 +117,61 @@ __device__ __forceinline__ void st_quad(T *p, const Quad<T> &q)
     }
 }
 
+// The field phases stage their quads in shared memory, kBatchBufs rounds deep: a round's E and H quads are
+// copied by cp.async (16-byte copies through L2, so values other CTAs of the cluster stored before the last
+// cluster barrier are the ones read) while the rounds before it are computed, so a thread's loads no longer
+// wait one memory latency per round.  Each buffer holds RN nodes of a round at index 4.. and a quad of halo
+// on either side.
+constexpr int kBatchU = 2;                                    // quads per thread per round
+constexpr int kBatchRoundNodes = 4 * kBatchU * kBatchThreads; // RN
+constexpr int kBatchStage = kBatchRoundNodes + 8;             // one buffer, in values
+constexpr int kBatchBufs = 3;                                 // buffers per field (two rounds in flight)
+
+template <typename T>
+__device__ __forceinline__ void cp_quad(T *dst, const T *src)
+{
+#pragma unroll
+    for (int b = 0; b < (int)(4 * sizeof(T)) / 16; ++b)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst + b * 16 / (int)sizeof(T))),
+                     "l"(src + b * 16 / (int)sizeof(T))
+                     : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n (0..2) of this thread's newest copy groups are pending
+__device__ __forceinline__ void cp_wait(int n)
+{
+    if (n >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// dynamic shared memory of the kernel: w' and the segment's alpha / beta tables, then the field stages
+template <typename T>
+__host__ __device__ constexpr size_t batch_tab_bytes(int pitch)
+{
+    return ((3 * (size_t)pitch * sizeof(T)) + 15) / 16 * 16;
+}
+template <typename T>
+__host__ __device__ constexpr size_t batch_smem_bytes(int pitch)
+{
+    return batch_tab_bytes<T>(pitch) + 2 * kBatchBufs * (size_t)kBatchStage * sizeof(T);
+}
+
 template <typename TS, typename T, int VPL, int L>
 __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
 {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s_al = reinterpret_cast<T *>(smem_raw);   // alpha, beta of the segment's run, shared w'
-    T *s_be = s_al + a.pitch, *s_w = s_be + a.pitch;
+    T *s_w = reinterpret_cast<T *>(smem_raw);    // w' (shared by all runs), then alpha, beta tables
+    T *s_tabs = s_w + a.pitch;
     using V = typename Vec<TS>::type;
     constexpr int VEC = Vec<TS>::n;
     constexpr int R = 32 / L;
-    constexpr int U = 2;                         // H / E quads (4 nodes each) per thread per round
+    constexpr int U = kBatchU;                   // H / E quads (4 nodes each) per thread per round
+    // field stages: E buffers [kBatchBufs], then H buffers [kBatchBufs]
+    T *stage_base = reinterpret_cast<T *>(smem_raw + batch_tab_bytes<T>(a.pitch));
+    auto fe = [&](int b) { return stage_base + b * kBatchStage; };
+    auto fh = [&](int b) { return stage_base + (kBatchBufs + b) * kBatchStage; };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int sub = lane / L, l = lane % L;
     const int nwarps = blockDim.x >> 5;
@@ -144,37 +190,44 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
             T *H = a.H + r.h_off;
             const int kend = min(sg.k1, r.nz);
             const int nq = (kend - sg.k0 + 3) / 4;   // quads of H nodes [k0, kend); k0 is a multiple of 4
-            for (int qi0 = 0; qi0 < nq; qi0 += U * blockDim.x) {   // block-uniform rounds
-                Quad<T> e[U], h[U];
-                T e4[U];
+            const int rq = U * (int)blockDim.x;       // quads per round (block-uniform rounds)
+            const int nr = (nq + rq - 1) / rq;
+            // round ri into buffer b: H quads starting below kend, E quads starting at or below kend (E at
+            // kend is the last node's upper neighbour), and the E quad just past the round
+            auto stage = [&](int ri, int b) {
+                const int kr = sg.k0 + 4 * rq * ri;
+                T *se = fe(b) + 4, *sh = fh(b) + 4;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
-                    if (kq < kend) {
-                        e[u] = ld_quad(E + kq);
-                        h[u] = ld_quad(H + kq);
-                    }
+                    const int j = 4 * (u * (int)blockDim.x + (int)threadIdx.x);
+                    if (kr + j <= kend) cp_quad(se + j, E + kr + j);
+                    if (kr + j < kend) cp_quad(sh + j, H + kr + j);
                 }
+                if (threadIdx.x == 0 && kr + 4 * rq <= kend) cp_quad(se + 4 * rq, E + kr + 4 * rq);
+                cp_commit();
+            };
+            for (int ri = 0; ri < kBatchBufs - 1 && ri < nr; ++ri) stage(ri, ri);
+            for (int ri = 0; ri < nr; ++ri) {
+                if (ri + kBatchBufs - 1 < nr) stage(ri + kBatchBufs - 1, (ri + kBatchBufs - 1) % kBatchBufs);
+                cp_wait(min(kBatchBufs - 1, nr - 1 - ri));   // this round's copies have landed
+                __syncthreads();
+                const int kr = sg.k0 + 4 * rq * ri;
+                const T *se = fe(ri % kBatchBufs) + 4, *sh = fh(ri % kBatchBufs) + 4;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    // E at kq + 4: the next lane's first node, loaded here at a warp's end or past kend
-                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
-                    e4[u] = __shfl_down_sync(0xffffffffu, e[u].v[0], 1);
-                    if (kq < kend && (lane == 31 || kq + 4 >= kend)) e4[u] = E[kq + 4];
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    const int j = 4 * (u * (int)blockDim.x + (int)threadIdx.x);
+                    const int kq = kr + j;
                     if (kq >= kend) continue;
                     Quad<T> o;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) o.v[c] = h[u].v[c] - a.ch * ((c < 3 ? e[u].v[c + 1] : e4[u]) - e[u].v[c]);
+                    for (int c = 0; c < 4; ++c) o.v[c] = sh[j + c] - a.ch * (se[j + c + 1] - se[j + c]);
                     if (kq + 4 <= kend) {
                         st_quad(H + kq, o);
                     } else {
                         for (int c = 0; kq + c < kend; ++c) H[kq + c] = o.v[c];
                     }
                 }
+                __syncthreads();   // buffer ri % kBatchBufs is staged again kBatchBufs - 1 rounds on
             }
             if (r.mur && threadIdx.x == 0) {
                 if (sg.k0 <= 1 && 1 < sg.k1) a.mur[2 * sg.run] = E[1];
@@ -190,11 +243,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
             T *E = a.E + r.e_off;
             const T *al = a.tab + (int64_t)sg.run * 2 * a.pitch;
             __syncthreads();                           // previous segment's tables no longer in use
-            for (int t = threadIdx.x; t < a.pitch; t += blockDim.x) {
-                s_al[t] = al[t];
-                s_be[t] = al[a.pitch + t];
-            }
+            for (int t = threadIdx.x; t < 2 * a.pitch; t += blockDim.x) s_tabs[t] = al[t];
             __syncthreads();
+            const T *s_al = s_tabs, *s_be = s_tabs + a.pitch;
             // software pipeline: the next row's node index, delta-f vectors, E and
             // density are loaded before the current row is updated, so a lane
             // keeps two rows of loads in flight (128 registers a thread, two
@@ -249,31 +300,42 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
             const T *H = a.H + r.h_off;
             const int kbeg = max(sg.k0, 1), kend = min(sg.k1, r.nz);   // E nodes updated: [kbeg, kend)
             const int nq = (kend - sg.k0 + 3) / 4;
-            for (int qi0 = 0; qi0 < nq; qi0 += U * blockDim.x) {
-                Quad<T> ev[U], h[U];
-                T hm[U];
+            const int rq = U * (int)blockDim.x;
+            const int nr = (nq + rq - 1) / rq;
+            // round ri into buffer b: E and H quads starting below kend, and the H quad just before the
+            // round (zero before node 0)
+            auto stage = [&](int ri, int b) {
+                const int kr = sg.k0 + 4 * rq * ri;
+                T *se = fe(b) + 4, *sh = fh(b) + 4;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
-                    if (kq < kend) {
-                        ev[u] = ld_quad(E + kq);
-                        h[u] = ld_quad(H + kq);
+                    const int j = 4 * (u * (int)blockDim.x + (int)threadIdx.x);
+                    if (kr + j < kend) {
+                        cp_quad(se + j, E + kr + j);
+                        cp_quad(sh + j, H + kr + j);
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    // H at kq - 1: the previous lane's last node, loaded here at a warp's start
-                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
-                    hm[u] = __shfl_up_sync(0xffffffffu, h[u].v[3], 1);
-                    if (kq < kend && lane == 0) hm[u] = kq > 0 ? H[kq - 1] : T(0);
+                if (threadIdx.x == 0) {
+                    if (kr > 0) cp_quad(sh - 4, H + kr - 4);
+                    else sh[-1] = T(0);
                 }
+                cp_commit();
+            };
+            for (int ri = 0; ri < kBatchBufs - 1 && ri < nr; ++ri) stage(ri, ri);
+            for (int ri = 0; ri < nr; ++ri) {
+                if (ri + kBatchBufs - 1 < nr) stage(ri + kBatchBufs - 1, (ri + kBatchBufs - 1) % kBatchBufs);
+                cp_wait(min(kBatchBufs - 1, nr - 1 - ri));   // this round's copies have landed
+                __syncthreads();
+                const int kr = sg.k0 + 4 * rq * ri;
+                const T *se = fe(ri % kBatchBufs) + 4, *sh = fh(ri % kBatchBufs) + 4;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    const int kq = sg.k0 + 4 * (qi0 + u * (int)blockDim.x + (int)threadIdx.x);
+                    const int j = 4 * (u * (int)blockDim.x + (int)threadIdx.x);
+                    const int kq = kr + j;
                     if (kq >= kend) continue;
-                    Quad<T> o = ev[u];
+                    Quad<T> o;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) o.v[c] = ev[u].v[c] - a.ce * (h[u].v[c] - (c > 0 ? h[u].v[c - 1] : hm[u]));
+                    for (int c = 0; c < 4; ++c) o.v[c] = se[j + c] - a.ce * (sh[j + c] - sh[j + c - 1]);
                     const bool special = kq < kbeg || kq + 4 > kend || (r.src_k >= kq && r.src_k < kq + 4) ||
                                          (r.mur && (kq <= 1 || kq + 4 > r.nz - 1));
                     if (!special) {
@@ -292,6 +354,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
                         }
                     }
                 }
+                __syncthreads();   // buffer ri % kBatchBufs is staged again kBatchBufs - 1 rounds on
             }
         }
         cluster.sync();
@@ -386,7 +449,12 @@ cudaError_t launch_t(fdtd_batch *b, cudaStream_t st, int nsteps)
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(b->nclusters * b->cluster_ctas);
     cfg.blockDim = dim3(kBatchThreads);
-    cfg.dynamicSmemBytes = 3 * (size_t)b->pitch * sizeof(T);
+    cfg.dynamicSmemBytes = batch_smem_bytes<T>(b->pitch);
+    if (cfg.dynamicSmemBytes > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_batch1d<TS, T, VPL, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)cfg.dynamicSmemBytes);
+        if (e != cudaSuccess) return e;
+    }
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -408,7 +476,14 @@ int max_clusters(int ctas)
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(ctas);
     cfg.blockDim = dim3(kBatchThreads);
-    cfg.dynamicSmemBytes = 3 * 128 * 16;   // tables of the largest row (128 vectors of 16 bytes)
+    // tables of the largest row (128 vectors of 16 bytes) and the field stages
+    cfg.dynamicSmemBytes = 3 * 128 * 16 + 2 * kBatchBufs * (size_t)kBatchStage * sizeof(T);
+    if (cfg.dynamicSmemBytes > 48 * 1024 &&
+        cudaFuncSetAttribute(k_batch1d<TS, T, VPL, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)cfg.dynamicSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = ctas;
