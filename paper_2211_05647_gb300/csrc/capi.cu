@@ -1217,6 +1217,15 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     }
 
     drop_graphs(h);
+    // a delta-f array of the same size is kept (set_plasma on a reset solver with the same plasma layout):
+    // only zeroed below, not freed and allocated again
+    const size_t df_need = (cells.empty() ? 1 : cells.size()) * (size_t)pitch *
+                           (p->f_dtype == FDTD_DF_BF16 ? 2 : (p->f_dtype == FDTD_DF_F64 ? 8 : 4));
+    void *keep_df = nullptr;
+    if (h->df && h->df_bytes == df_need) {
+        keep_df = h->df;
+        h->df = nullptr;
+    }
     free_plasma(h);
     const size_t ns = cells.size();
     h->pl = *p;
@@ -1231,7 +1240,8 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     // rounded up to 16 bytes
     h->slot_cell = (int32_t *)dalloc(h, ((ns + 3) & ~(size_t)3) * 4);
     h->dens = dalloc(h, ((ns + 3) & ~(size_t)3) * h->esz);
-    h->df = dalloc(h, (ns ? ns : 1) * pitch * h->df_esz);
+    h->df = keep_df ? keep_df : dalloc(h, df_need);
+    h->df_bytes = df_need;
     h->jslot = dalloc(h, (ns ? ns : 1) * h->esz);
     h->tab = dalloc(h, tab.size() * h->esz);
     h->dV = (double *)dalloc(h, nnode * 8);
@@ -1434,7 +1444,8 @@ int fdtd_plasma_set_closure(fdtd_plasma_t h, const fdtd_closure_desc *c)
     dfree(h, h->slot_cell); dfree(h, h->dens); dfree(h, h->df); dfree(h, h->jslot);
     h->slot_cell = (int32_t *)dalloc(h, ((ns + 3) & ~(int64_t)3) * 4);
     h->dens = dalloc(h, ((ns + 3) & ~(int64_t)3) * 4);
-    h->df = dalloc(h, (nk ? nk : 1) * h->pitch * h->df_esz);
+    h->df_bytes = (nk ? nk : 1) * h->pitch * h->df_esz;
+    h->df = dalloc(h, h->df_bytes);
     h->jslot = dalloc(h, (ns ? ns : 1) * 4);
     h->hist = (float *)dalloc(h, (nc ? nc : 1) * 16 * 4);
     h->jprev = (float *)dalloc(h, (nc ? nc : 1) * 4);

@@ -415,6 +415,7 @@ struct fdtd_plasma {
     void *g0, *tab_f0;        // evolve_f0: F0 correction rows and the F0 tables
     double *dV;               // per node (FP64) for the diagnostics
     size_t df_esz;
+    size_t df_bytes;          // size of the df allocation (kept by a set_plasma of the same size)
     int64_t nkin;             // slots [0, nkin) take the kinetic update (all, unless a closure is set)
     std::vector<int32_t> h_cells;   // host copies of the slot layout
     std::vector<double> h_dens;

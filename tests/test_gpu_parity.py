@@ -397,3 +397,26 @@ def test_nonlinear_mode_2d_cartesian(oracle_lib):
     errs = compare(s, sim, 2)
     _report("2d nonlinear f64", errs)
     assert max(errs.values()) <= 1e-12, errs
+
+
+def test_set_plasma_again_after_reset():
+    """After reset, set_plasma with the same slot layout keeps the delta-f array (zeroed again) and one
+    with another layout allocates a new one; either way the run equals a fresh solver's bit for bit."""
+    import copy
+    spec = _small_2d("f32", "f32", steps=60)
+    other = copy.deepcopy(spec)
+    d = np.array(other["plasma"]["density"], dtype=np.float64)
+    d[np.flatnonzero(d)[::7]] = 0.0                       # fewer plasma cells: another layout
+    other["plasma"]["density"] = d
+    s = _solver(spec)
+    s.step(60)                                            # leaves delta f, J and the fields non-zero
+    for sp in (spec, other, spec):
+        s.reset()
+        s.set_plasma(**dict(sp["plasma"]))
+        s.set_source(**dict(sp["source"]))
+        s.step(60)
+        fresh = _solver(sp)
+        fresh.step(60)
+        for n in FIELDS[2] + ["j", "df"]:
+            assert np.array_equal(s.read(n, device=False), fresh.read(n, device=False)), n
+        fresh.close()
