@@ -198,9 +198,12 @@ void free_plasma(fdtd_plasma *h)
 // The plasma slots of a whole grid's density array (host or device, pol_len values), compacted on the
 // GPU: cells in increasing index with their densities (FP64) and the largest density; FDTD_ERR_NONFINITE
 // for a value that is not finite or is negative.
+// The device copy of the result (densities FP64 [ns], then cells int32 [ns]) is handed to the caller in
+// *dev_slots (to be freed with dfree) when ns > 0, so the slot arrays are filled device to device.
 int compact_on_gpu(fdtd_plasma *h, const fdtd_plasma_desc *p, int64_t np, std::vector<int32_t> &cells,
-                   std::vector<double> &dslot, double &nmax)
+                   std::vector<double> &dslot, double &nmax, void **dev_slots)
 {
+    *dev_slots = nullptr;
     const int64_t nb = (np + kCompactChunk - 1) / kCompactChunk;
     const CompactGeom g{h->g.ndim, h->nx, h->ny, h->nz, np};
     void *dtmp = nullptr, *scr = nullptr, *out = nullptr;
@@ -253,6 +256,8 @@ int compact_on_gpu(fdtd_plasma *h, const fdtd_plasma_desc *p, int64_t np, std::v
             e = cudaMemcpyAsync(dslot.data(), d_dens, (size_t)ns * 8, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { release(); return cuda_fail(h, e, "plasma compaction (scatter)"); }
+        *dev_slots = out;
+        out = nullptr;
     } else {
         e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) { release(); return cuda_fail(h, e, "plasma compaction"); }
@@ -1162,9 +1167,15 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     std::vector<int32_t> cells;
     std::vector<double> dslot;
     double nmax = 0.0;
+    // the compaction's device copy of the slots (whole grids), freed on every way out
+    struct DevSlots {
+        fdtd_plasma *h;
+        void *p = nullptr;
+        ~DevSlots() { dfree(h, p); }
+    } dev_slots{h};
     if (!h->sd_on) {
         // a whole grid: the density stays on (or goes once to) the device and is compacted there
-        const int rc = compact_on_gpu(h, p, np, cells, dslot, nmax);
+        const int rc = compact_on_gpu(h, p, np, cells, dslot, nmax, &dev_slots.p);
         if (rc != FDTD_OK) return rc;
     } else {
         for (int64_t c = 0; c < np; ++c) {
@@ -1259,17 +1270,29 @@ int fdtd_plasma_set_plasma(fdtd_plasma_t h, const fdtd_plasma_desc *p)
     h->nkin = (int64_t)ns;
     h->kin_vpl = h->kin_l = h->kin_bps = h->kin_stages = 0;
     apply_cached_kinetic(h);
-    h->h_cells = cells;
-    h->h_dens = dslot;
-    if (ns) CK(h, cudaMemcpy(h->slot_cell, cells.data(), ns * 4, cudaMemcpyHostToDevice));
+    if (ns && dev_slots.p) {   // device to device from the compaction (densities converted to FP32 there)
+        const double *d_dens = static_cast<const double *>(dev_slots.p);
+        const int32_t *d_cells = reinterpret_cast<const int32_t *>(d_dens + ns);
+        CK(h, cudaMemcpyAsync(h->slot_cell, d_cells, ns * 4, cudaMemcpyDeviceToDevice, h->stream));
+        if (h->esz == 8) CK(h, cudaMemcpyAsync(h->dens, d_dens, ns * 8, cudaMemcpyDeviceToDevice, h->stream));
+        else CK(h, launch_to_f32(h->stream, d_dens, static_cast<float *>(h->dens), (int64_t)ns));
+    } else if (ns) {
+        CK(h, cudaMemcpy(h->slot_cell, cells.data(), ns * 4, cudaMemcpyHostToDevice));
+        if (h->esz == 8) {
+            CK(h, cudaMemcpy(h->dens, dslot.data(), ns * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> d32(dslot.begin(), dslot.end());
+            CK(h, cudaMemcpy(h->dens, d32.data(), ns * 4, cudaMemcpyHostToDevice));
+        }
+    }
     if (h->esz == 8) {
-        if (ns) CK(h, cudaMemcpy(h->dens, dslot.data(), ns * 8, cudaMemcpyHostToDevice));
         CK(h, cudaMemcpy(h->tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice));
     } else {
-        std::vector<float> d32(dslot.begin(), dslot.end()), t32(tab.begin(), tab.end());
-        if (ns) CK(h, cudaMemcpy(h->dens, d32.data(), ns * 4, cudaMemcpyHostToDevice));
+        std::vector<float> t32(tab.begin(), tab.end());
         CK(h, cudaMemcpy(h->tab, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice));
     }
+    h->h_cells = std::move(cells);
+    h->h_dens = std::move(dslot);
     CK(h, cudaMemcpy(h->dV, t.dV.data(), nnode * 8, cudaMemcpyHostToDevice));
     if (p->evolve_f0) {
         if (h->esz == 8) {

@@ -112,4 +112,18 @@ cudaError_t launch_compact_scatter(cudaStream_t st, const double *d, const Compa
     return cudaGetLastError();
 }
 
+__global__ void k_to_f32(const double *__restrict__ src, float *__restrict__ dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+cudaError_t launch_to_f32(cudaStream_t st, const double *src, float *dst, int64_t n)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 152 * 16);
+    k_to_f32<<<(unsigned)blocks, 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 }  // namespace fp

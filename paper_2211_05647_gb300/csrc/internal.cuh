@@ -269,6 +269,8 @@ cudaError_t launch_compact_count(cudaStream_t st, const double *d, const Compact
                                  int *bad);
 cudaError_t launch_compact_scatter(cudaStream_t st, const double *d, const CompactGeom &g, const int64_t *offsets,
                                    int32_t *cells, double *dens);
+// dst[i] = (float)src[i], i < n (round to nearest, as the host conversion)
+cudaError_t launch_to_f32(cudaStream_t st, const double *src, float *dst, int64_t n);
 
 // delta-f row pitch (elements) for nnode nodes of the given storage type
 int kinetic_pitch(int nnode, int f_dtype);
