@@ -218,6 +218,25 @@ def ncu_traffic(kernel: str, workload: str, shape=None):
     return None
 
 
+def batch_traffic(workload: str, steps_per_launch: int):
+    """DRAM bytes per launch of the batched kernel from the committed ncu summary (bytes per step, taken
+    on the current batch1d.cu / kinetic_row.cuh / async.cuh) times the steps a launch covers, else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha1()
+    for f in ("batch1d.cu", "kinetic_row.cuh", "async.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2211_05647_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()[:12]
+    for ln in open(path):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        kv = dict(t.split("=", 1) for t in ln.split() if "=" in t)
+        if kv.get("kernel") == "k_batch1d" and kv.get("workload") == workload and kv.get("src_sha") == sha:
+            return float(kv["dram_bytes_per_step"]) * steps_per_launch
+    return None
+
+
 def kinetic_kernel(shapes: dict, evolve: bool):
     """The kinetic kernel a handle launches and its launch shape (vpl, l, ring stages)."""
     if evolve:
@@ -378,7 +397,8 @@ def batch_config(workload: str, specs, steps: int, warmup: int, autotune: bool, 
             "clusters": info["clusters"], "ctas_per_cluster": info["cluster_ctas"], "steps_per_launch": chunk,
             "row_shape": tune,
             "roofline": {"bound": "hbm", "kernel": "k_batch1d", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg_step * chunk,
+                         "frac": achieved / peak, "traffic": batch_traffic(workload, chunk),
+                         "alg_bytes_per_launch": alg_step * chunk,
                          "launch_ms": per_launch_ms, "peak_source": src},
             "step_hbm_frac_algorithmic": alg_step / (ms / steps / 1e3) / 1e9 / peak,
             "gpu_launches": 2 * (steps // chunk + (1 if rem else 0))}
@@ -924,7 +944,8 @@ def batch_bench(args, specs, rank, world, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "phase_space_updates_per_s": job_rate(nodes * args.steps, world, ms / 1e3),
             "roofline": {"bound": "hbm", "kernel": "k_batch1d", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg_step * chunk,
+                         "frac": achieved / peak, "traffic": batch_traffic(args.workload, chunk),
+                         "alg_bytes_per_launch": alg_step * chunk,
                          "launch_ms": per_launch_ms,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback"},
             "gpu_launches": 2 * (args.steps // chunk + (1 if rem else 0)),
