@@ -47,6 +47,26 @@ def test_2d_decomposed_equals_whole_grid(f_dtype, bounds):
     _equal(dec, whole, FIELDS[2] + ["j", "df"])
 
 
+@pytest.mark.parametrize("f_dtype,shape", [("f32", (16, 16)), ("bf16", (8, 16))])
+def test_2d_decomposed_ring_kernel_equals_whole_grid(f_dtype, shape):
+    """The same with the bulk-copy ring kernel (three stages) on the whole grid and on every sub-domain:
+    its per-slot stochastic-rounding counters are the global slot index, as in the register kernel."""
+    from paper_2211_05647_gb300 import Solver
+    from paper_2211_05647_gb300.decomposed import DecomposedSolver
+    value = 3 * 10**9 + shape[0] * 10**6 + shape[1] * 1000
+    spec = _spec2d(f_dtype)
+    whole = Solver.from_spec(spec)
+    whole.set_option("kinetic_shape", value)
+    whole.step(150)
+    dec = DecomposedSolver(spec, bounds=[(0, 6), (6, 60), (66, 74)])
+    for sub in dec.subs:
+        if sub.plasma_shape()[0]:
+            sub.set_option("kinetic_shape", value)
+    dec.step(150)
+    assert np.abs(whole.read("j", device=False)).max() > 0
+    _equal(dec, whole, FIELDS[2] + ["j", "df"])
+
+
 @pytest.mark.parametrize("bounds", [[(0, 3), (3, 30), (33, 31)], [(0, 22), (22, 21), (43, 21)]])
 def test_3d_decomposed_equals_whole_grid(bounds):
     from paper_2211_05647_gb300 import Solver
