@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
             for (int ri = 0; ri < kBatchBufs - 1 && ri < nr; ++ri) stage(ri, ri);
             for (int ri = 0; ri < nr; ++ri) {
                 if (ri + kBatchBufs - 1 < nr) stage(ri + kBatchBufs - 1, (ri + kBatchBufs - 1) % kBatchBufs);
-                cp_wait(min(kBatchBufs - 1, nr - 1 - ri));   // this round's copies have landed
+                cp_wait(min(kBatchBufs - 1, nr - 1 - ri));   // the copies of quad batch ri have landed
                 __syncthreads();
                 const int kr = sg.k0 + 4 * rq * ri;
                 const T *se = fe(ri % kBatchBufs) + 4, *sh = fh(ri % kBatchBufs) + 4;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
             for (int ri = 0; ri < kBatchBufs - 1 && ri < nr; ++ri) stage(ri, ri);
             for (int ri = 0; ri < nr; ++ri) {
                 if (ri + kBatchBufs - 1 < nr) stage(ri + kBatchBufs - 1, (ri + kBatchBufs - 1) % kBatchBufs);
-                cp_wait(min(kBatchBufs - 1, nr - 1 - ri));   // this round's copies have landed
+                cp_wait(min(kBatchBufs - 1, nr - 1 - ri));   // the copies of quad batch ri have landed
                 __syncthreads();
                 const int kr = sg.k0 + 4 * rq * ri;
                 const T *se = fe(ri % kBatchBufs) + 4, *sh = fh(ri % kBatchBufs) + 4;
