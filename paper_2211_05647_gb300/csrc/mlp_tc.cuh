@@ -221,9 +221,8 @@ __device__ __forceinline__ float mlp_tc_tile(MlpTcSmem &s, uint32_t *phase, bool
 constexpr int kTcGroups = 4;
 
 struct MlpTcWeights {
-    __align__(128) __nv_bfloat16 w1[kMlpH * kMlpK1];
+    __align__(128) __nv_bfloat16 w1[kMlpH * kMlpK1];   // K rows 17 / 18: b1 as a BF16 high and low part
     __align__(128) __nv_bfloat16 w2[kMlpH * kMlpH];
-    __align__(16) float b1[kMlpH];
     __align__(16) float b2[kMlpH];
     __align__(16) float w3[kMlpH];   // half scale (see mlp_tc4_load_weights)
     float b3;
@@ -258,21 +257,29 @@ __device__ __forceinline__ float2 gelu2_f2(uint64_t z)
 // ring >= 0: the first 16 inputs arrive in history-ring slot order (slot j holds E^{n-15+k} with
 // k = (j - ring - 1) mod 16, the oldest first in the network's order), so W1's rows are stored in that
 // order: the same products, the ring never rotated per cell.
+// Layer 1's bias rides in the MMA: input columns 17 and 18 are 1 (mlp_tc4_put_row_ring) and W1's rows 17
+// and 18 hold b1 split into a BF16 high part and the BF16 rounding of the rest, so the FP32 accumulator
+// adds b1 to within 2^-17 of it and the epilogue adds no bias.  (Layer 2's K has no spare columns; a
+// 16-column extension for b2 cost more than the bias adds it saves.)
 __device__ __forceinline__ void mlp_tc4_load_weights(MlpTcWeights &s, const float *__restrict__ P, int ring = -1)
 {
     unsigned char *w1 = reinterpret_cast<unsigned char *>(s.w1), *w2 = reinterpret_cast<unsigned char *>(s.w2);
     for (int i = threadIdx.x; i < kMlpH * kMlpK1; i += blockDim.x) {
         const int n = i / kMlpK1, k = i % kMlpK1;
         const int kk = (ring >= 0 && k < 16) ? ((k - ring - 1) & 15) : k;
-        *reinterpret_cast<__nv_bfloat16 *>(w1 + core_off(n, k, kMlpK1)) =
-            __float2bfloat16_rn(k < kMlpIn ? P[kOffW1 + kk * kMlpH + n] : 0.0f);
+        __nv_bfloat16 v = __float2bfloat16_rn(k < kMlpIn ? P[kOffW1 + kk * kMlpH + n] : 0.0f);
+        if (k == kMlpIn || k == kMlpIn + 1) {
+            const float b = P[kOffB1 + n];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(b);
+            v = k == kMlpIn ? hi : __float2bfloat16_rn(b - __bfloat162float(hi));
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(w1 + core_off(n, k, kMlpK1)) = v;
     }
     for (int i = threadIdx.x; i < kMlpH * kMlpH; i += blockDim.x) {
         const int k = i / kMlpH, n = i % kMlpH;
         *reinterpret_cast<__nv_bfloat16 *>(w2 + core_off(n, k, kMlpH)) = __float2bfloat16_rn(0.5f * P[kOffW2 + i]);
     }
     for (int i = threadIdx.x; i < kMlpH; i += blockDim.x) {
-        s.b1[i] = P[kOffB1 + i];
         s.b2[i] = P[kOffB2 + i];
         s.w3[i] = 0.5f * P[kOffW3 + i];
     }
@@ -306,28 +313,15 @@ __device__ __forceinline__ void mlp_tc4_teardown(MlpTcSmem4 &s)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.w.tmem), "r"(512u) : "memory");
 }
 
-__device__ __forceinline__ void mlp_tc4_put_row(MlpTcGroup &g, int r, const float *x)
-{
-    unsigned char *xb = reinterpret_cast<unsigned char *>(g.x);
-#pragma unroll
-    for (int c = 0; c < kMlpK1 / 8; ++c) {
-        uint4 v;
-        v.x = pack_bf16(x[8 * c + 0], x[8 * c + 1]);
-        v.y = pack_bf16(x[8 * c + 2], x[8 * c + 3]);
-        v.z = pack_bf16(x[8 * c + 4], x[8 * c + 5]);
-        v.w = pack_bf16(x[8 * c + 6], x[8 * c + 7]);
-        *reinterpret_cast<uint4 *>(xb + core_off(r, 8 * c, kMlpK1)) = v;
-    }
-}
-
 // Thread r writes row r of the layer-1 input from its history ring (16 BF16 values in slot order, two
-// 16-byte vectors) and its scaled density; columns 17..31 are zero.
+// 16-byte vectors), its scaled density and the two ones that carry layer 1's bias; columns 19..31 are zero.
 __device__ __forceinline__ void mlp_tc4_put_row_ring(MlpTcGroup &g, int r, uint4 h0, uint4 h1, float dn)
 {
     unsigned char *xb = reinterpret_cast<unsigned char *>(g.x);
     *reinterpret_cast<uint4 *>(xb + core_off(r, 0, kMlpK1)) = h0;
     *reinterpret_cast<uint4 *>(xb + core_off(r, 8, kMlpK1)) = h1;
-    *reinterpret_cast<uint4 *>(xb + core_off(r, 16, kMlpK1)) = make_uint4(pack_bf16(dn, 0.0f), 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(xb + core_off(r, 16, kMlpK1)) =
+        make_uint4(pack_bf16(dn, 1.0f), pack_bf16(1.0f, 0.0f), 0u, 0u);
     *reinterpret_cast<uint4 *>(xb + core_off(r, 24, kMlpK1)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
@@ -364,13 +358,11 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
         tc_ld32(tmem + lane_base + c * 32, v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int k0 = c * 32 + q * 8;
-            const float4 ba = *reinterpret_cast<const float4 *>(&w.b1[k0]);
-            const float4 bb = *reinterpret_cast<const float4 *>(&w.b1[k0 + 4]);
-            const float2 g0 = gelu2_f2(f2_add(f2(v[q * 8 + 0], v[q * 8 + 1]), f2(ba.x, ba.y)));
-            const float2 g1 = gelu2_f2(f2_add(f2(v[q * 8 + 2], v[q * 8 + 3]), f2(ba.z, ba.w)));
-            const float2 g2 = gelu2_f2(f2_add(f2(v[q * 8 + 4], v[q * 8 + 5]), f2(bb.x, bb.y)));
-            const float2 g3 = gelu2_f2(f2_add(f2(v[q * 8 + 6], v[q * 8 + 7]), f2(bb.z, bb.w)));
+            const int k0 = c * 32 + q * 8;   // the accumulator already holds the bias (rows 17, 18 of W1)
+            const float2 g0 = gelu2_f2(f2(v[q * 8 + 0], v[q * 8 + 1]));
+            const float2 g1 = gelu2_f2(f2(v[q * 8 + 2], v[q * 8 + 3]));
+            const float2 g2 = gelu2_f2(f2(v[q * 8 + 4], v[q * 8 + 5]));
+            const float2 g3 = gelu2_f2(f2(v[q * 8 + 6], v[q * 8 + 7]));
             uint4 pk;
             pk.x = pack_bf16(g0.x, g0.y);
             pk.y = pack_bf16(g1.x, g1.y);
