@@ -157,8 +157,17 @@ __host__ __device__ constexpr size_t batch_smem_bytes(int pitch)
     return batch_tab_bytes<T>(pitch) + 2 * kBatchBufs * (size_t)kBatchStage * sizeof(T);
 }
 
+// CTAs per SM the registers are budgeted for: three with FP32 rows (80 registers, no spill: 0.316 -> 0.288 ms a
+// step on the 256-run workload), two otherwise (BF16 rows lost at three: 0.189 -> 0.213 ms, the packing then
+// taking clusters of eight)
+template <typename TS>
+constexpr int batch_min_blocks()
+{
+    return std::is_same<TS, float>::value ? 3 : 2;
+}
+
 template <typename TS, typename T, int VPL, int L>
-__global__ void __launch_bounds__(kBatchThreads, 2) k_batch1d(BatchArgs<T> a)
+__global__ void __launch_bounds__(kBatchThreads, batch_min_blocks<TS>()) k_batch1d(BatchArgs<T> a)
 {
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
