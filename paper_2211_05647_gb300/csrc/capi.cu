@@ -1660,6 +1660,10 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
             return acc / 5.0;
         };
         const int keep[3] = {h->kin_vpl, h->kin_l, h->kin_bps}, keep_stages = h->kin_stages;
+        // the timing steps leave no trace outside the saved state: no port spectra, no recorded samples
+        const int keep_ports = h->nports, keep_rec = h->has_recording;
+        h->nports = 0;
+        h->has_recording = 0;
         double best = 1e30;
         for (int c = 0; c < nc; ++c)
             for (const auto &vr : variants) {
@@ -1676,6 +1680,8 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
                 }
             }
         for (int q = 0; q < 5; ++q) cudaEventDestroy(ev[q]);
+        h->nports = keep_ports;
+        h->has_recording = keep_rec;
         if (best >= 1e30) {   // nothing ran: keep the shape in use
             out->kin_vpl = keep[0]; out->kin_l = keep[1]; out->kin_blocks_per_sm = keep[2];
             out->kin_stages = keep_stages;

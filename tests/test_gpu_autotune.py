@@ -70,3 +70,26 @@ def test_forced_kinetic_shape(tmp_path, monkeypatch):
             assert rel_l2(s.read(n, device=False), ref.read(n, device=False)) <= 1e-5, (vpl, l, n)
     with pytest.raises(FdtdError):
         Solver.from_spec(spec).set_option("kinetic_shape", 3 * 1000000 + 5 * 1000)
+
+
+def test_autotune_leaves_ports_and_recording_untouched(tmp_path, monkeypatch):
+    """The autotuner times kinetic candidates inside whole steps: those steps must add nothing to the port
+    spectra or to the training-sample recorder (neither is part of the saved state it restores)."""
+    import torch
+    from paper_2211_05647_gb300 import Solver
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    spec = spec_2d_cylinder(n=200, ny=160, R=40, center=(110, 80), src=(50, 80), steps=40, seed=8)
+    s = Solver.from_spec(spec)
+    s.set_ports([[80 * 200 + 150], [80 * 200 + 60]], np.linspace(5e9, 15e9, 6))
+    samples = torch.zeros(4096 * 19, dtype=torch.float32, device=s.device)
+    count = torch.zeros(1, dtype=torch.int64, device=s.device)
+    s.set_recording(samples, count, rate=0.01, seed=3)
+    s.step(20)
+    ports0 = s.port_spectra().copy()
+    s.stream.synchronize()
+    n0 = int(count.item())
+    s.autotune()
+    s.stream.synchronize()
+    assert int(count.item()) == n0
+    assert np.array_equal(s.port_spectra(), ports0)
+    assert n0 > 0 and np.abs(ports0).max() > 0
