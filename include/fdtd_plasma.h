@@ -198,7 +198,8 @@ int fdtd_plasma_time_kernels(fdtd_plasma_t h, int64_t nsteps, double *ms_out);
 /* Launch-shape autotuner.  Times, with CUDA events on the handle's stream,
  * every candidate shape of the kinetic kernel (vectors per lane x lanes per
  * row x CTAs per SM) and of the curl-stencil kernels (thread-block shape,
- * cells per thread, and on 3-D FP32 grids the TMA column kernels) on
+ * cells per thread, on FP32 grids the TMA column kernels, and on 2-D FP32
+ * grids the fused E + H column march against the best separate pair) on
  * the handle's own buffers, adopts the fastest, and records them in a text
  * cache ($FDTD_PLASMA_TUNE_CACHE, else $HOME/.cache/fdtd_plasma/autotune.txt)
  * keyed by GPU name, kernel, precision and size class; later handles of the
@@ -219,6 +220,11 @@ typedef struct {
                                                     a producer warp copies chunks of 256 / kin_l rows, with
                                                     their cell indices and densities, ahead of eight
                                                     consumer warps; same results bit for bit) */
+    int32_t fused_rows;                          /* 2-D FP32, nx a multiple of 4, whole grid: > 0 when the
+                                                    fused E + H column march beat the best separate pair
+                                                    (rows per block segment; the step sequence then runs
+                                                    it, with a second field / psi set, same results bit
+                                                    for bit); 0 = separate passes */
 } fdtd_tune_result;
 int fdtd_plasma_autotune(fdtd_plasma_t h, fdtd_tune_result *out);
 
@@ -251,11 +257,14 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * sequence on 2-D and 3-D FP32 grids fuse each E update with the next H update into
  * one pass (fields and CPML psi double-buffered: one extra copy of them is
  * allocated on first use; the fields are back in place when
- * fdtd_plasma_step returns).  It moves a third fewer bytes but is slower than
- * the two separate passes on GB300 at present.  Results equal the unfused
- * sequence up to FP32 rounding order (bit for bit where the TMA column
- * stencils below are selected: their fused pass then runs on TMA-staged
- * planes too).  0 turns it off (and frees the copy).
+ * fdtd_plasma_step returns).  It moves a third fewer bytes; in 3-D it is
+ * slower than the two separate passes on GB300, in 2-D (the column march
+ * below) faster on large grids, where fdtd_plasma_autotune selects it by
+ * itself (fdtd_tune_result.fused_rows; half steps stay allowed then).
+ * Results equal the unfused sequence bit for bit in 2-D and where the 3-D TMA
+ * column stencils below are selected (their fused pass then runs on
+ * TMA-staged planes too), else up to FP32 rounding order.  0 turns the
+ * option off (and frees the copy unless the autotuner chose the fused pass).
  * FDTD_OPT_STENCIL_TZ: 0 selects the grid-of-cells stencil kernels; a value
  * tz in 1..1024 selects the TMA kernels (2-D and 3-D FP32, nx a multiple of 4):
  * 32 x 8 threads per block; in 3-D each block walks tz planes along z, in 2-D
@@ -271,8 +280,13 @@ int fdtd_selftest_timed_wait(uint32_t limit_us, int32_t *gave_up);
  * the linear update, stages that fit in one CTA's shared memory); 0 returns
  * to the built-in default.
  * Needs a plasma (after set_plasma).  The autotuner overwrites it.
+ * FDTD_OPT_FUSED_ROWS (2-D fused pass, nx a multiple of 4): rows per block
+ * segment of the column-march kernel (1..4096, default 8; each warp owns a
+ * 128-column strip and marches up the segment with no shared memory); 0
+ * selects the 64 x 16 shared-memory tiles instead.  Both equal the unfused
+ * sequence up to FP32 rounding order.
  * FDTD_ERR_INVAL for an unknown option or value. */
-enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3 };
+enum { FDTD_OPT_FUSED_STENCILS = 1, FDTD_OPT_STENCIL_TZ = 2, FDTD_OPT_KINETIC_SHAPE = 3, FDTD_OPT_FUSED_ROWS = 4 };
 int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value);
 
 /* The launch shapes the handle uses now (tuned, cached or default; kinetic

@@ -27,6 +27,7 @@ using namespace fp;
 namespace {
 
 constexpr int kChunk = 32;            // steps per replay of the chunk graph
+constexpr int kFuseRowsDefault = 8;   // rows per block segment of the 2-D fused column march
 constexpr uint64_t kStateMagic = 0x4644544450534d31ull;
 
 thread_local std::string g_create_error;
@@ -403,7 +404,7 @@ std::map<std::string, std::vector<int>> read_cache()
         int x;
         if (!(in >> k)) continue;
         while (in >> x) v.push_back(x);
-        if (v.size() >= 3 && v.size() <= 5) m[k] = v;
+        if (v.size() >= 3 && v.size() <= 6) m[k] = v;
     }
     return m;
 }
@@ -441,7 +442,8 @@ void apply_cached_stencil(fdtd_plasma *h)
     auto it = m.find(stencil_key(h));
     if (it != m.end() && it->second.size() >= 4) {
         h->st_bx = it->second[0]; h->st_by = it->second[1]; h->st_bz = it->second[2]; h->st_cpt = it->second[3];
-        h->st_tz = it->second.size() == 5 ? it->second[4] : 0;
+        h->st_tz = it->second.size() >= 5 ? it->second[4] : 0;
+        h->auto_fuse_rows = it->second.size() >= 6 && !h->sd_on ? it->second[5] : 0;
     }
 }
 
@@ -650,7 +652,7 @@ void free_second_set(fdtd_plasma *h)
 // allocate the second field / psi set when the fused sequence applies; on failure the steps run unfused
 void ensure_second_set(fdtd_plasma *h)
 {
-    if (!h->fuse || h->g.ndim < 2 || h->g.precision != FDTD_F32 || h->f2[FDTD_EZ]) return;
+    if ((!h->fuse && h->auto_fuse_rows <= 0) || h->g.ndim < 2 || h->g.precision != FDTD_F32 || h->f2[FDTD_EZ]) return;
     bool ok = true;
     for (int q = 0; q < 6 && ok; ++q)
         if (h->flen[q]) ok = (h->f2[q] = dalloc(h, h->flen[q] * h->esz)) != nullptr;
@@ -662,11 +664,16 @@ void ensure_second_set(fdtd_plasma *h)
     }
 }
 
-// whether the step sequence fuses E^{n+1} with H^{n+3/2} (2-D / 3-D FP32, second field set allocated)
+// whether the step sequence fuses E^{n+1} with H^{n+3/2} (2-D / 3-D FP32 by option, 2-D FP32 by the
+// autotuner's choice; second field set allocated)
 bool fused_stencils(const fdtd_plasma *h)
 {
-    return h->fuse && h->g.ndim >= 2 && h->g.precision == FDTD_F32 && h->f2[FDTD_EZ] != nullptr;
+    const bool on = h->fuse || (h->auto_fuse_rows > 0 && h->g.ndim == 2);
+    return on && h->g.ndim >= 2 && h->g.precision == FDTD_F32 && h->f2[FDTD_EZ] != nullptr;
 }
+
+// rows per segment of the 2-D column march: the option's when fusion was asked for, else the autotuner's
+int fuse_rows_of(const fdtd_plasma *h) { return h->fuse ? h->fuse_rows : h->auto_fuse_rows; }
 
 // nsteps steps: H_0, then per step the middle part and either E_k alone (then
 // H_{k+1} on the same set) or the fused E_k + H_{k+1} from one set into the
@@ -707,7 +714,7 @@ cudaError_t enqueue_seq(fdtd_plasma *h, cudaStream_t st, int nsteps)
                 }
                 else
                     launch_eh2d(st, fs.f, to.f, to.cp.psi, h->nx, h->ny, ce, cpe, ch, cph, fs.cp, source_view(h),
-                                h->d_step, k);
+                                h->d_step, k, fuse_rows_of(h));
             }
             set ^= 1;
             e = part_ports<T>(h, st, k, to);
@@ -820,6 +827,7 @@ int create_impl(const fdtd_grid_desc *g, const fdtd_runtime_desc *rt, fdtd_plasm
     fdtd_plasma *h = new (std::nothrow) fdtd_plasma();
     if (h) {
         h->fuse = 0;
+        h->fuse_rows = kFuseRowsDefault;
         const char *cv = std::getenv("FDTD_PLASMA_CANARIES");
         h->canary = cv && cv[0] == '1';
     }
@@ -980,7 +988,14 @@ int fdtd_plasma_set_option(fdtd_plasma_t h, int option, int64_t value)
         CK(h, cudaStreamSynchronize(h->stream));
         drop_graphs(h);
         h->fuse = (int)value;
-        if (!h->fuse) free_second_set(h);
+        if (!h->fuse && h->auto_fuse_rows <= 0) free_second_set(h);
+        return FDTD_OK;
+    }
+    if (option == FDTD_OPT_FUSED_ROWS) {
+        if (value < 0 || value > 4096) return fail(h, FDTD_ERR_INVAL, "FDTD_OPT_FUSED_ROWS takes 0 .. 4096");
+        CK(h, cudaStreamSynchronize(h->stream));
+        drop_graphs(h);
+        h->fuse_rows = (int)value;
         return FDTD_OK;
     }
     if (option == FDTD_OPT_STENCIL_TZ) {
@@ -1040,6 +1055,9 @@ int fdtd_plasma_launch_shapes(fdtd_plasma_t h, fdtd_tune_result *out)
         out->block_x = (int32_t)b.x; out->block_y = (int32_t)b.y; out->block_z = (int32_t)b.z;
         out->cells_per_thread = stencil_cpt(h);
         out->stencil_tz = h->st_tz;
+        out->fused_rows = h->g.ndim == 2 && h->g.precision == FDTD_F32 && !h->sd_on && (h->fuse || h->auto_fuse_rows > 0)
+                              ? fuse_rows_of(h)
+                              : 0;
     }
     return FDTD_OK;
 }
@@ -1563,7 +1581,7 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
         return ms / 5.0;
     };
     auto m = read_cache();
-    out->block_x = out->block_y = out->block_z = out->cells_per_thread = out->stencil_tz = 0;
+    out->block_x = out->block_y = out->block_z = out->cells_per_thread = out->stencil_tz = out->fused_rows = 0;
     out->stencil_ms = 0;
     if (h->g.ndim >= 2) {
         static const int s2[][3] = {{32, 8, 1}, {64, 4, 1}, {128, 2, 1}, {256, 1, 1}, {32, 4, 1}, {64, 2, 1}};
@@ -1626,10 +1644,36 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
                 }
             }
         }
+        // 2-D FP32 on a whole grid: the fused E + H column march (one launch a step, from this set into the
+        // second) against the best separate pair
+        out->fused_rows = 0;
+        if constexpr (sizeof(T) == 4) {
+            if (h->g.ndim == 2 && h->nx % 4 == 0 && !h->sd_on) {
+                h->auto_fuse_rows = kFuseRowsDefault;   // lets ensure_second_set allocate the second set
+                ensure_second_set(h);
+                if (h->f2[FDTD_EZ]) {
+                    float *fo[6], *po[12];
+                    for (int q = 0; q < 6; ++q) fo[q] = reinterpret_cast<float *>(h->f2[q]);
+                    for (int q = 0; q < 12; ++q) po[q] = reinterpret_cast<float *>(h->psi2[q]);
+                    for (int rows : {8, 16, 32}) {
+                        const double ms = time_ms([&] {
+                            launch_eh2d(st, f, fo, po, h->nx, h->ny, ce, cpe, ch, cph, cp, src, h->d_step, 0, rows);
+                        });
+                        if (ms < best * kTuneMargin) {
+                            best = ms;
+                            out->fused_rows = rows;
+                        }
+                    }
+                }
+                h->auto_fuse_rows = out->fused_rows;
+                if (!h->fuse && h->auto_fuse_rows <= 0) free_second_set(h);
+            }
+        }
         h->st_bx = out->block_x; h->st_by = out->block_y; h->st_bz = out->block_z; h->st_cpt = out->cells_per_thread;
         h->st_tz = out->stencil_tz;
         out->stencil_ms = best;
-        m[stencil_key(h)] = {out->block_x, out->block_y, out->block_z, out->cells_per_thread, out->stencil_tz};
+        m[stencil_key(h)] = {out->block_x,        out->block_y,    out->block_z,
+                             out->cells_per_thread, out->stencil_tz, out->fused_rows};
     }
     out->kin_vpl = out->kin_l = out->kin_blocks_per_sm = out->kin_stages = 0;
     out->kin_ms = 0;

@@ -72,8 +72,8 @@ __global__ void __launch_bounds__(256) k_h2d(const T *__restrict__ ez, T *__rest
     const T dEx = (i + 1 < nx ? ez[c + 1] : T(0)) - e;    // dEz along x at (i+1/2, j)
     T hxv = hx[c], hyv = hy[c];
     if (cp.L == 0) {
-        hxv -= ch * dEy;                                  // mu0 dHx/dt = -dEz/dy
-        hyv += ch * dEx;                                  // mu0 dHy/dt = +dEz/dx
+        hxv = hx_plain(hxv, ch, dEy);                     // mu0 dHx/dt = -dEz/dy
+        hyv = hy_plain(hyv, ch, dEx);                     // mu0 dHy/dt = +dEz/dx
     } else {
         h2d_pml<T>(cp, nx, ny, i, j, ch, cph, dEy, dEx, hxv, hyv);
     }
@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(256) k_e2d(T *__restrict__ ez, const T *__rest
     const T dHx = hy[c] - hy[c - 1];     // dHy along x
     const T dHy = hx[c] - hx[c - nx];    // dHx along y
     // eps0 dEz/dt = dHy/dx - dHx/dy - Jz
-    const T upd = cp.L == 0 ? ce * (dHx - dHy) : e2d_pml<T>(cp, nx, ny, i, j, ce, cpe, dHx, dHy);
-    T v = ezc + upd;
-    if (src.kind && i == src.i && j == src.j) v += (T)*src.val;
+    const T upd = cp.L == 0 ? e2d_term(ce, dHx, dHy) : e2d_pml<T>(cp, nx, ny, i, j, ce, cpe, dHx, dHy);
+    T v = rn_add(ezc, upd);
+    if (src.kind && i == src.i && j == src.j) v = rn_add(v, (T)*src.val);
     ez[c] = v;
 }
 
@@ -241,8 +241,8 @@ __global__ void __launch_bounds__(256) k_h2d_v4(const float *__restrict__ ez, fl
         const float dEy = Ey.v[e] - E.v[e];
         const float dEx = (e < 3 ? E.v[e + 1] : er) - E.v[e];
         if (!pml) {
-            Hx.v[e] -= ch * dEy;
-            Hy.v[e] += ch * dEx;
+            Hx.v[e] = hx_plain(Hx.v[e], ch, dEy);
+            Hy.v[e] = hy_plain(Hy.v[e], ch, dEx);
         } else {
             h2d_pml<float>(cp, nx, ny, i0 + e, j, ch, cph, dEy, dEx, Hx.v[e], Hy.v[e]);
         }
@@ -279,8 +279,8 @@ __global__ void __launch_bounds__(256) k_e2d_v4(float *__restrict__ ez, const fl
         if (i < 1) continue;      // column 0 is the PEC wall
         const float dHx = Hy.v[e] - (e > 0 ? Hy.v[e - 1] : hl);
         const float dHy = Hx.v[e] - Hxm.v[e];
-        E.v[e] += pml ? e2d_pml<float>(cp, nx, ny, i, j, ce, cpe, dHx, dHy) : ce * (dHx - dHy);
-        if (src.kind && i == src.i && j == src.j) E.v[e] += (float)*src.val;
+        E.v[e] = rn_add(E.v[e], pml ? e2d_pml<float>(cp, nx, ny, i, j, ce, cpe, dHx, dHy) : e2d_term(ce, dHx, dHy));
+        if (src.kind && i == src.i && j == src.j) E.v[e] = rn_add(E.v[e], (float)*src.val);
     }
     st4(ez + c, E);
 }
@@ -759,37 +759,11 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
                 const float dHx = sHy[ry + 1][rx + 1] - sHy[ry + 1][rx];   // dHy along x
                 const float dHy = sHx[ry + 1][rx + 1] - sHx[ry][rx + 1];   // dHx along y
                 const bool own = rx < kF2X && ry < kF2Y;
-                float upd;
-                if (!pml) {
-                    upd = ce * (dHx - dHy);
-                } else {
-                    float px = 0.f, py = 0.f, kx = 1.f, ky = 1.f;
-                    if (in_slab<float>(i, nx, L)) {
-                        const int64_t o = j * (2 * L) + slab_slot<float>(i, nx, L);
-                        px = cin.be[0][i] * cin.psi[0][o] + cin.ae[0][i] * dHx;
-                        if (own) pout.psi[0][o] = px;
-                        kx = cin.ike[0][i];
-                    }
-                    if (in_slab<float>(j, ny, L)) {
-                        const int64_t o = (int64_t)slab_slot<float>(j, ny, L) * nx + i;
-                        py = cin.be[1][j] * cin.psi[1][o] + cin.ae[1][j] * dHy;
-                        if (own) pout.psi[1][o] = py;
-                        ky = cin.ike[1][j];
-                    }
-                    upd = ce * (dHx * kx - dHy * ky) + cpe * (px - py);
-                }
-                e += upd;
-                if (src.kind && i == src.i && j == src.j) e += s_g;
+                e = rn_add(e, pml ? e2d_pml_io<float>(cin, pout.psi, own, nx, ny, i, j, ce, cpe, dHx, dHy)
+                                  : e2d_term(ce, dHx, dHy));
+                if (src.kind && i == src.i && j == src.j) e = rn_add(e, s_g);
             } else if (pml && rx < kF2X && ry < kF2Y) {
-                // PEC wall cell: the E update leaves its psi as it is; carry it into the out set
-                if (in_slab<float>(i, nx, L)) {
-                    const int64_t o = j * (2 * L) + slab_slot<float>(i, nx, L);
-                    pout.psi[0][o] = cin.psi[0][o];
-                }
-                if (in_slab<float>(j, ny, L)) {
-                    const int64_t o = (int64_t)slab_slot<float>(j, ny, L) * nx + i;
-                    pout.psi[1][o] = cin.psi[1][o];
-                }
+                e2d_psi_carry<float>(cin, pout.psi, nx, ny, i, j);   // PEC wall: psi unchanged
             }
             if (rx < kF2X && ry < kF2Y) ez_out[j * nx + i] = e;
         }
@@ -806,29 +780,225 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
         const float dEx = sE[ry][rx + 1] - e;   // dEz along x
         float hxv = sHx[ry + 1][rx + 1], hyv = sHy[ry + 1][rx + 1];
         if (!pml) {
-            hxv -= ch * dEy;
-            hyv += ch * dEx;
+            hxv = hx_plain(hxv, ch, dEy);
+            hyv = hy_plain(hyv, ch, dEx);
         } else {
-            if (in_slab<float>(j, ny, L)) {
-                const int64_t o = (int64_t)slab_slot<float>(j, ny, L) * nx + i;
-                const float ps = cin.bh[1][j] * cin.psi[2][o] + cin.ah[1][j] * dEy;
-                pout.psi[2][o] = ps;
-                hxv -= ch * dEy * cin.ikh[1][j] + cph * ps;
-            } else {
-                hxv -= ch * dEy;
-            }
-            if (in_slab<float>(i, nx, L)) {
-                const int64_t o = j * (2 * L) + slab_slot<float>(i, nx, L);
-                const float ps = cin.bh[0][i] * cin.psi[3][o] + cin.ah[0][i] * dEx;
-                pout.psi[3][o] = ps;
-                hyv += ch * dEx * cin.ikh[0][i] + cph * ps;
-            } else {
-                hyv += ch * dEx;
-            }
+            h2d_pml_io<float>(cin, pout.psi, nx, ny, i, j, ch, cph, dEy, dEx, hxv, hyv);
         }
         const int64_t c = j * nx + i;
         hx_out[c] = hxv;
         hy_out[c] = hyv;
+    }
+}
+
+// ------------------------------ 2-D fused E^{n+1} + H^{n+3/2}, column march (FP32)
+// A warp owns a strip of 128 columns (four a lane) and marches up a segment of
+// rows.  At row j it forms E^{n+1}(j) from the H^{n+1/2} rows j and j - 1 (the
+// latter kept in registers from the previous row), then H^{n+3/2}(j - 1) from
+// the E^{n+1} rows j - 1 and j.  x neighbours come from the adjacent lanes; the
+// strip's edge lanes load the one column beyond it (lane 0: H_y at x - 1;
+// lane 31: E', H_x and H_y at x + 128, whose E^{n+1} it forms as well).  A
+// segment re-reads H_x of the row below it and forms, without storing it,
+// E^{n+1} of the row above it.  No shared memory and no barrier; reads set
+// `in` (fields and psi), writes set `out`.  Per cell the arithmetic is that of
+// every 2-D kernel (the fixed-rounding helpers of stencil_common.cuh), so the
+// fused and separate sequences agree bit for bit.
+constexpr int kEh2W = 4;   // warps (128-column strips) per block
+constexpr int kEh2D = 4;   // rows in each lane's copy ring
+
+__device__ __forceinline__ void cpa16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// g(t^{n1}) in FP32, as the separate E kernel reads it; out of line because
+// only the thread at the source node calls it
+__device__ __noinline__ float source_f32(int kind, double amp, double fc, double tau, double t0, double dt, int64_t n1)
+{
+    Source s{};
+    s.kind = kind;
+    s.amp = amp;
+    s.fc = fc;
+    s.tau = tau;
+    s.t0 = t0;
+    s.dt = dt;
+    return (float)source_value(s, (double)n1 * dt);
+}
+
+__global__ void __launch_bounds__(32 * kEh2W, 6)
+    k_eh2d_v4(const float *__restrict__ ez_in, const float *__restrict__ hx_in, const float *__restrict__ hy_in,
+              float *__restrict__ ez_out, float *__restrict__ hx_out, float *__restrict__ hy_out, int64_t nx,
+              int64_t ny, int rows, float ce, float cpe, float ch, float cph, Cpml<float> cin, PsiOut pout, Source src,
+              const int64_t *__restrict__ d_step, int kstep)
+{
+    pdl_enter();
+    const int lane = (int)(threadIdx.x & 31u), w = (int)(threadIdx.x >> 5);
+    const int64_t xs = ((int64_t)blockIdx.x * kEh2W + w) * 128;   // the warp's strip
+    const int64_t i0 = xs + 4 * lane;
+    const int64_t j0 = (int64_t)blockIdx.y * rows;
+    const int64_t j1 = j0 + rows < ny ? j0 + rows : ny;   // owned rows [j0, j1)
+    const int64_t jl = j1 < ny ? j1 : ny - 1;              // last row whose E^{n+1} is formed
+    const int64_t n1 = *d_step + kstep + 1;
+    if (src.kind && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+        *src.val = source_value(src, (double)(n1 + 1) * src.dt);   // g(t^{n+2}) for a following unfused E
+    if (xs >= nx) return;   // the whole warp is past the grid
+    const bool live = i0 < nx;
+    const int64_t xr = xs + 128;   // the column beyond the strip
+    const bool left = lane == 0 && xs > 0, right = lane == 31 && xr < nx;
+    const int L = cin.L;
+    const unsigned full = 0xffffffffu;
+    // per-column parts of the CPML selection and of the source test (the row parts are per row)
+    const bool pml_cols = L > 0 && (i0 < L || i0 + 3 >= nx - L);
+    const bool pml_cols_r = L > 0 && (xr < L || xr + 3 >= nx - L);
+    const int src_e = src.kind && src.i >= i0 && src.i < i0 + 4 ? (int)(src.i - i0) : -1;
+    const bool src_r = src.kind && src.i == xr;
+    const bool wall = i0 == 0;   // the quad holds column 0 (PEC)
+
+    // Each lane streams its own inputs through a ring of kEh2D rows in shared
+    // memory (cp.async; lane 0 and lane 31 add the columns beyond the strip),
+    // so a warp keeps kEh2D - 1 rows of loads in flight while it computes one;
+    // a lane reads back only what it copied itself, so no barrier is needed.
+    __shared__ float4 ring[kEh2W][kEh2D][3][32];
+    __shared__ float halo[kEh2W][kEh2D][4];
+    auto issue = [&](int64_t j, int sl) {   // row j into slot sl, one copy group (empty past the last row)
+        if (j <= jl) {
+            const int64_t c = j * nx + i0, cr = j * nx + xr;
+            if (live) {
+                cpa16(&ring[w][sl][0][lane], ez_in + c);
+                cpa16(&ring[w][sl][1][lane], hx_in + c);
+                cpa16(&ring[w][sl][2][lane], hy_in + c);
+            }
+            if (left) cpa4(&halo[w][sl][0], hy_in + c - 1);
+            if (right) {
+                cpa4(&halo[w][sl][1], ez_in + cr);
+                cpa4(&halo[w][sl][2], hx_in + cr);
+                cpa4(&halo[w][sl][3], hy_in + cr);
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto q4 = [](const float4 &t) { return Q4{{t.x, t.y, t.z, t.w}}; };
+
+    Q4 hxp = ld4_if(live && j0 >= 1, hx_in + (j0 - 1) * nx + i0);   // H_x^{n+1/2} of the row below
+    float hxrp = right && j0 >= 1 ? hx_in[(j0 - 1) * nx + xr] : 0.f;
+    Q4 hyp{}, enp{};         // the previous row's H_y^{n+1/2} and E^{n+1}
+    float erp = 0.f;         // and E^{n+1} right of the quad
+    bool slab_p = false;     // and whether it lies in a y slab
+    // a lane past the grid reads zeros from slots it never fills (its E^{n+1}
+    // stays 0: the last live lane takes it as the node beyond the grid)
+    if (!live) {
+#pragma unroll
+        for (int d = 0; d < kEh2D; ++d)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ring[w][d][a][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int d = 0; d < kEh2D - 1; ++d) issue(j0 + d, d);
+    int sl = 0;   // the slot of row j (rows j0 + kEh2D m + sl use slot sl)
+    for (int64_t j = j0; j <= jl; ++j) {
+        issue(j + kEh2D - 1, sl == 0 ? kEh2D - 1 : sl - 1);   // refills the slot row j - 1 was read from
+        asm volatile("cp.async.wait_group %0;" ::"n"(kEh2D - 1) : "memory");   // row j has landed
+        const Q4 ep = q4(ring[w][sl][0][lane]), hx = q4(ring[w][sl][1][lane]), hy = q4(ring[w][sl][2][lane]);
+        float hl = __shfl_up_sync(full, hy.v[3], 1);
+        if (lane == 0) hl = left ? halo[w][sl][0] : 0.f;
+        const int64_t c = j * nx + i0;
+        const bool own = j < j1;
+        const bool slab = L > 0 && in_slab<float>(j, ny, L);
+        const bool pml = pml_cols || slab;
+        const bool srow = j == src.j;
+        // E^{n+1}(j) on the quad (row 0 and column 0 are the PEC wall)
+        Q4 en = ep;
+        if (live && !pml && j >= 1 && !wall && !(srow && src_e >= 0)) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float dHx = hy.v[e] - (e > 0 ? hy.v[e - 1] : hl);
+                const float dHy = hx.v[e] - hxp.v[e];
+                en.v[e] = rn_add(en.v[e], e2d_term(ce, dHx, dHy));
+            }
+        } else if (live) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t i = i0 + e;
+                if (j >= 1 && i >= 1) {
+                    const float dHx = hy.v[e] - (e > 0 ? hy.v[e - 1] : hl);
+                    const float dHy = hx.v[e] - hxp.v[e];
+                    en.v[e] = rn_add(en.v[e], pml ? e2d_pml_io<float>(cin, pout.psi, own, nx, ny, i, j, ce, cpe, dHx, dHy)
+                                                  : e2d_term(ce, dHx, dHy));
+                    if (srow && e == src_e)
+                        en.v[e] = rn_add(en.v[e], source_f32(src.kind, src.amp, src.fc, src.tau, src.t0, src.dt, n1));
+                } else if (pml && own) {
+                    e2d_psi_carry<float>(cin, pout.psi, nx, ny, i, j);
+                }
+            }
+        }
+        // E^{n+1}(j) of the column beyond the strip, as the next strip's lane 0 forms it
+        float enr = 0.f, hxr = 0.f;
+        if (right) {
+            enr = halo[w][sl][1];
+            hxr = halo[w][sl][2];
+            if (j >= 1) {
+                const float dHx = halo[w][sl][3] - hy.v[3], dHy = hxr - hxrp;
+                enr = rn_add(enr, pml_cols_r || slab ? e2d_pml_io<float>(cin, pout.psi, false, nx, ny, xr, j, ce, cpe,
+                                                                         dHx, dHy)
+                                                     : e2d_term(ce, dHx, dHy));
+                if (srow && src_r)
+                    enr = rn_add(enr, source_f32(src.kind, src.amp, src.fc, src.tau, src.t0, src.dt, n1));
+            }
+        }
+        float er = __shfl_down_sync(full, en.v[0], 1);
+        if (lane == 31) er = enr;
+        if (live && own) st4(ez_out + c, en);
+        // H^{n+3/2}(j - 1)
+        if (live && j > j0) {
+            Q4 hxo = hxp, hyo = hyp;
+            if (!(pml_cols || slab_p)) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    hxo.v[e] = hx_plain(hxo.v[e], ch, en.v[e] - enp.v[e]);
+                    hyo.v[e] = hy_plain(hyo.v[e], ch, (e < 3 ? enp.v[e + 1] : erp) - enp.v[e]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float dEy = en.v[e] - enp.v[e];
+                    const float dEx = (e < 3 ? enp.v[e + 1] : erp) - enp.v[e];
+                    h2d_pml_io<float>(cin, pout.psi, nx, ny, i0 + e, j - 1, ch, cph, dEy, dEx, hxo.v[e], hyo.v[e]);
+                }
+            }
+            st4(hx_out + c - nx, hxo);
+            st4(hy_out + c - nx, hyo);
+        }
+        hxp = hx;
+        hyp = hy;
+        enp = en;
+        erp = er;
+        hxrp = hxr;
+        slab_p = slab;
+        sl = sl + 1 == kEh2D ? 0 : sl + 1;
+    }
+    // the top row: E^{n+1} above it is 0
+    if (live && j1 == ny) {
+        const int64_t j = ny - 1;
+        Q4 hxo = hxp, hyo = hyp;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float dEy = 0.f - enp.v[e];
+            const float dEx = (e < 3 ? enp.v[e + 1] : erp) - enp.v[e];
+            if (!(pml_cols || slab_p)) {
+                hxo.v[e] = hx_plain(hxo.v[e], ch, dEy);
+                hyo.v[e] = hy_plain(hyo.v[e], ch, dEx);
+            } else {
+                h2d_pml_io<float>(cin, pout.psi, nx, ny, i0 + e, j, ch, cph, dEy, dEx, hxo.v[e], hyo.v[e]);
+            }
+        }
+        st4(hx_out + j * nx + i0, hxo);
+        st4(hy_out + j * nx + i0, hyo);
     }
 }
 
@@ -844,11 +1014,17 @@ static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1
 
 void launch_eh2d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
                  int64_t ny, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
-                 const int64_t *d_step, int kstep)
+                 const int64_t *d_step, int kstep, int rows)
 {
-    dim3 g(cdiv(nx, kF2X), cdiv(ny, kF2Y));
     PsiOut po{};
     for (int q = 0; q < 12; ++q) po.psi[q] = psi_out[q];
+    if (rows > 0 && nx % 4 == 0) {   // the column march (16-byte rows)
+        dim3 g(cdiv(nx, 128 * kEh2W), cdiv(ny, rows));
+        launch_pdl(k_eh2d_v4, g, dim3(32 * kEh2W), 0, st, fin[FDTD_EZ], fin[FDTD_HX], fin[FDTD_HY], fout[FDTD_EZ],
+                   fout[FDTD_HX], fout[FDTD_HY], nx, ny, rows, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
+        return;
+    }
+    dim3 g(cdiv(nx, kF2X), cdiv(ny, kF2Y));
     launch_pdl(k_eh2d, dim3(g), dim3(kF2T), 0, st, fin[FDTD_EZ], fin[FDTD_HX], fin[FDTD_HY], fout[FDTD_EZ], fout[FDTD_HX], fout[FDTD_HY],
                                nx, ny, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
 }

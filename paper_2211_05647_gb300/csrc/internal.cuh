@@ -225,9 +225,10 @@ template <typename T>
 void launch_e3d(cudaStream_t st, T *const f[6], int64_t nx, int64_t ny, int64_t nz, T ce, T cpe, Cpml<T> cp,
                 Source src, const int64_t *d_step, int kstep, dim3 block, int cpt);
 // 2-D / 3-D FP32 fused E^{n+1} + H^{n+3/2}: read fields fin and psi cin.psi, write fout and psi_out
+// (2-D: rows > 0 with nx a multiple of 4 selects the column march, rows per block segment)
 void launch_eh2d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
                  int64_t ny, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
-                 const int64_t *d_step, int kstep);
+                 const int64_t *d_step, int kstep, int rows);
 void launch_eh3d(cudaStream_t st, float *const fin[6], float *const fout[6], float *const psi_out[12], int64_t nx,
                  int64_t ny, int64_t nz, float ce, float cpe, float ch, float cph, Cpml<float> cin, Source src,
                  const int64_t *d_step, int kstep);
@@ -391,6 +392,8 @@ struct fdtd_plasma {
     void *f2[6];
     void *psi2[12];
     int fuse;                 // FDTD_OPT_FUSED_STENCILS (default 0)
+    int fuse_rows;            // FDTD_OPT_FUSED_ROWS: 2-D column-march rows per block (0: the 64 x 16 tiles)
+    int auto_fuse_rows;       // the autotuner's choice on 2-D FP32 grids: > 0 runs the fused column march
     // guard bytes around every device allocation ($FDTD_PLASMA_CANARIES=1 at create)
     int canary;
     std::vector<std::pair<char *, size_t>> canary_allocs;   // (user pointer, user bytes)

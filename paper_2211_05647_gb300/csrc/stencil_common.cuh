@@ -1,6 +1,7 @@
 // stencil_common.cuh -- device helpers shared by the curl-stencil kernels:
-// CPML slab indexing, the soft-source value and hit test, and the 3-D CPML
-// cell updates (psi <- b psi + a dF with the 1/kappa-scaled curl, Eq. 7-12).
+// CPML slab indexing, the soft-source value and hit test, the fixed-rounding
+// 2-D cell updates and the 3-D CPML cell updates (psi <- b psi + a dF with the
+// 1/kappa-scaled curl, Eq. 7-12).
 #pragma once
 
 #include "internal.cuh"
@@ -27,50 +28,118 @@ __device__ __forceinline__ void write_source(const Source &src, const int64_t *d
     if (src.kind) *src.val = source_value(src, (double)(*d_step + kstep + 1) * src.dt);
 }
 
-// CPML H update of one 2-D cell (Eq. 7-12): psi <- b psi + a dE, curl scaled by 1/kappa.
+// Fixed-rounding arithmetic of the 2-D TMz updates.  Every 2-D kernel (one
+// cell or four cells a thread, TMA-fed, fused E + H) forms exactly these
+// operations through the helpers below, so their results agree bit for bit
+// whatever the compiler would contract in each of them.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// E_z curl term outside the CPML: ce (dHy/dx - dHx/dy); E_z^{n+1} = E' + term
+// (rn_add), then + g at the source node (rn_add).  e2d_pml_io with kappa 1
+// and psi 0 gives exactly this term.
+template <typename T>
+__device__ __forceinline__ T e2d_term(T ce, T dHx, T dHy)
+{
+    return rn_mul(ce, rn_sub(dHx, dHy));
+}
+// H outside the CPML: mu0 dHx/dt = -dEz/dy, mu0 dHy/dt = +dEz/dx.  Product and
+// sum are rounded apart, so that the CPML form below with b = a = 0 and
+// 1/kappa = 1 (a sub-domain's local layer planes that lie inside the global
+// grid) gives exactly this.
+template <typename T>
+__device__ __forceinline__ T hx_plain(T hx, T ch, T dEy)
+{
+    return rn_sub(hx, rn_mul(ch, dEy));
+}
+template <typename T>
+__device__ __forceinline__ T hy_plain(T hy, T ch, T dEx)
+{
+    return rn_add(hy, rn_mul(ch, dEx));
+}
+
+// CPML H update of one 2-D cell (Eq. 7-12): psi <- b psi + a dE, curl scaled
+// by 1/kappa; psi read from the handle's slabs and written to pout (the same
+// slabs for an in-place update).  Outside a slab the axis takes the plain form.
+template <typename T>
+__device__ __forceinline__ void h2d_pml_io(const Cpml<T> &cp, T *const *pout, int64_t nx, int64_t ny, int64_t i,
+                                           int64_t j, T ch, T cph, T dEy, T dEx, T &hxv, T &hyv)
+{
+    const int L = cp.L;
+    if (in_slab<T>(j, ny, L)) {
+        const int64_t o = (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        const T ps = rn_fma(cp.bh[1][j], cp.psi[2][o], rn_mul(cp.ah[1][j], dEy));
+        pout[2][o] = ps;
+        hxv = rn_sub(hxv, rn_fma(rn_mul(ch, dEy), cp.ikh[1][j], rn_mul(cph, ps)));
+    } else {
+        hxv = hx_plain(hxv, ch, dEy);
+    }
+    if (in_slab<T>(i, nx, L)) {
+        const int64_t o = j * (2 * L) + slab_slot<T>(i, nx, L);
+        const T ps = rn_fma(cp.bh[0][i], cp.psi[3][o], rn_mul(cp.ah[0][i], dEx));
+        pout[3][o] = ps;
+        hyv = rn_add(hyv, rn_fma(rn_mul(ch, dEx), cp.ikh[0][i], rn_mul(cph, ps)));
+    } else {
+        hyv = hy_plain(hyv, ch, dEx);
+    }
+}
 template <typename T>
 __device__ __forceinline__ void h2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ch, T cph,
                                         T dEy, T dEx, T &hxv, T &hyv)
 {
-    const int L = cp.L;
-    if (in_slab<T>(j, ny, L)) {
-        T *p = cp.psi[2] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
-        T ps = cp.bh[1][j] * *p + cp.ah[1][j] * dEy;
-        *p = ps;
-        hxv -= ch * dEy * cp.ikh[1][j] + cph * ps;
-    } else {
-        hxv -= ch * dEy;
-    }
-    if (in_slab<T>(i, nx, L)) {
-        T *p = cp.psi[3] + j * (2 * L) + slab_slot<T>(i, nx, L);
-        T ps = cp.bh[0][i] * *p + cp.ah[0][i] * dEx;
-        *p = ps;
-        hyv += ch * dEx * cp.ikh[0][i] + cph * ps;
-    } else {
-        hyv += ch * dEx;
-    }
+    h2d_pml_io<T>(cp, cp.psi, nx, ny, i, j, ch, cph, dEy, dEx, hxv, hyv);
 }
 
-// CPML curl term of the E update of one 2-D cell.
+// CPML curl term of the E update of one 2-D cell; the new psi goes to pout
+// only when `store` (a cell the caller owns).  With neither slab it equals
+// e2d_term (kappa 1, psi 0).
 template <typename T>
-__device__ __forceinline__ T e2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ce, T cpe,
-                                     T dHx, T dHy)
+__device__ __forceinline__ T e2d_pml_io(const Cpml<T> &cp, T *const *pout, bool store, int64_t nx, int64_t ny,
+                                        int64_t i, int64_t j, T ce, T cpe, T dHx, T dHy)
 {
     const int L = cp.L;
     T px = T(0), py = T(0), kx = T(1), ky = T(1);
     if (in_slab<T>(i, nx, L)) {
-        T *p = cp.psi[0] + j * (2 * L) + slab_slot<T>(i, nx, L);
-        px = cp.be[0][i] * *p + cp.ae[0][i] * dHx;
-        *p = px;
+        const int64_t o = j * (2 * L) + slab_slot<T>(i, nx, L);
+        px = rn_fma(cp.be[0][i], cp.psi[0][o], rn_mul(cp.ae[0][i], dHx));
+        if (store) pout[0][o] = px;
         kx = cp.ike[0][i];
     }
     if (in_slab<T>(j, ny, L)) {
-        T *p = cp.psi[1] + (int64_t)slab_slot<T>(j, ny, L) * nx + i;
-        py = cp.be[1][j] * *p + cp.ae[1][j] * dHy;
-        *p = py;
+        const int64_t o = (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        py = rn_fma(cp.be[1][j], cp.psi[1][o], rn_mul(cp.ae[1][j], dHy));
+        if (store) pout[1][o] = py;
         ky = cp.ike[1][j];
     }
-    return ce * (dHx * kx - dHy * ky) + cpe * (px - py);
+    return rn_fma(ce, rn_fma(dHx, kx, -rn_mul(dHy, ky)), rn_mul(cpe, rn_sub(px, py)));
+}
+template <typename T>
+__device__ __forceinline__ T e2d_pml(const Cpml<T> &cp, int64_t nx, int64_t ny, int64_t i, int64_t j, T ce, T cpe,
+                                     T dHx, T dHy)
+{
+    return e2d_pml_io<T>(cp, cp.psi, true, nx, ny, i, j, ce, cpe, dHx, dHy);
+}
+
+// a PEC wall node keeps its E psi: carry it into another slab set
+template <typename T>
+__device__ __forceinline__ void e2d_psi_carry(const Cpml<T> &cp, T *const *pout, int64_t nx, int64_t ny, int64_t i,
+                                              int64_t j)
+{
+    const int L = cp.L;
+    if (in_slab<T>(i, nx, L)) {
+        const int64_t o = j * (2 * L) + slab_slot<T>(i, nx, L);
+        pout[0][o] = cp.psi[0][o];
+    }
+    if (in_slab<T>(j, ny, L)) {
+        const int64_t o = (int64_t)slab_slot<T>(j, ny, L) * nx + i;
+        pout[1][o] = cp.psi[1][o];
+    }
 }
 
 // 3-D psi slot 2*f + d: f = Ex,Ey,Ez,Hx,Hy,Hz; d = 0 for the lower-numbered of

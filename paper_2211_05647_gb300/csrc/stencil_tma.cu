@@ -491,8 +491,8 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_h2d_tma(const __grid_consta
             const float dEx = Ez[hc + 1] - e;     // dEz along x
             float hxv = Hx[tc], hyv = Hy[tc];
             if (cp.L == 0 || !(in_slab<float>(i, nx, cp.L) || in_slab<float>(j, ny, cp.L))) {
-                hxv -= ch * dEy;
-                hyv += ch * dEx;
+                hxv = hx_plain(hxv, ch, dEy);
+                hyv = hy_plain(hyv, ch, dEx);
             } else {
                 h2d_pml<float>(cp, nx, ny, i, j, ch, cph, dEy, dEx, hxv, hyv);
             }
@@ -544,10 +544,10 @@ __global__ void __launch_bounds__(kTT, kMinBlocks) k_e2d_tma(const __grid_consta
             const float dHx = Hy[hc] - Hy[hc - 1];     // dHy along x
             const float dHy = Hx[hc] - Hx[hc - kBX];   // dHx along y
             const float upd = cp.L == 0 || !(in_slab<float>(i, nx, cp.L) || in_slab<float>(j, ny, cp.L))
-                                  ? ce * (dHx - dHy)
+                                  ? e2d_term(ce, dHx, dHy)
                                   : e2d_pml<float>(cp, nx, ny, i, j, ce, cpe, dHx, dHy);
-            float v = Ezt[ly * kTX + tx] + upd;
-            if (src.kind && i == src.i && j == src.j) v += g;
+            float v = rn_add(Ezt[ly * kTX + tx], upd);
+            if (src.kind && i == src.i && j == src.j) v = rn_add(v, g);
             ez[j * nx + i] = v;
         }
     }

@@ -94,7 +94,7 @@ class fdtd_tune_result(ctypes.Structure):
                 ("block_x", ctypes.c_int32), ("block_y", ctypes.c_int32), ("block_z", ctypes.c_int32),
                 ("kin_ms", ctypes.c_double), ("stencil_ms", ctypes.c_double),
                 ("cells_per_thread", ctypes.c_int32), ("stencil_tz", ctypes.c_int32),
-                ("kin_stages", ctypes.c_int32)]
+                ("kin_stages", ctypes.c_int32), ("fused_rows", ctypes.c_int32)]
 
 
 class fdtd_closure_desc(ctypes.Structure):
@@ -658,8 +658,9 @@ class Solver:
     def set_option(self, option: str, value: int):
         """Runtime option: "fused_stencils" (0 / 1, default 0; FDTD_OPT_FUSED_STENCILS),
         "stencil_tz" (0 / planes per block of the TMA column stencils; FDTD_OPT_STENCIL_TZ) or
-        "kinetic_shape" (stages * 10**9 + vpl * 10**6 + l * 1000 + bps, 0 = default; FDTD_OPT_KINETIC_SHAPE)."""
-        code = {"fused_stencils": 1, "stencil_tz": 2, "kinetic_shape": 3}[option]
+        "kinetic_shape" (stages * 10**9 + vpl * 10**6 + l * 1000 + bps, 0 = default; FDTD_OPT_KINETIC_SHAPE) or
+        "fused_rows" (rows per block of the 2-D fused column march, 0 = the tile kernel; FDTD_OPT_FUSED_ROWS)."""
+        code = {"fused_stencils": 1, "stencil_tz": 2, "kinetic_shape": 3, "fused_rows": 4}[option]
         _check(self.lib, self.h, self.lib.fdtd_plasma_set_option(self.h, code, int(value)))
 
     def launch_shapes(self) -> dict:

@@ -157,3 +157,99 @@ def test_fused_2d_checkpoint():
     r.step(19)
     for q in FIELDS[2] + ["j", "df"]:
         assert np.array_equal(s.read(q, device=False), r.read(q, device=False)), q
+
+
+# ---------------------------------------------- 2-D column march (nx % 4 == 0)
+# 296 x 70 cells: two full 128-column strips and a partial one (dead lanes),
+# segments of 1, 5 and 32 rows (ragged at the top) and one segment for all.
+
+@pytest.mark.parametrize("rows", [1, 5, 32, 4096])
+@pytest.mark.parametrize("src", [(40, 35), (128, 32), (127, 31), (295, 69)])
+def test_fused_2d_march_equals_unfused(rows, src):
+    """The source in the interior, on the first column of a strip (formed as
+    halo by the strip to its left), on a strip's last column, and on the
+    grid's last node (no CPML there); fields bit for bit."""
+    from paper_2211_05647_gb300 import Solver
+    spec = _spec2(70, n=(296, 70), cpml=0 if src == (295, 69) else 8, src=src)
+    fused, plain = Solver.from_spec(spec), Solver.from_spec(spec)
+    fused.set_option("fused_stencils", 1)
+    fused.set_option("fused_rows", rows)
+    for n in (33, 37):
+        fused.step(n)
+        plain.step(n)
+    for q in FIELDS[2] + ["j"]:
+        assert np.array_equal(fused.read(q, device=False), plain.read(q, device=False)), q
+
+
+def test_fused_2d_march_matches_oracle(oracle_lib):
+    spec = _spec2(260, n=(152, 70))
+    from paper_2211_05647_gb300 import Solver
+    s = Solver.from_spec(spec)
+    s.set_option("fused_stencils", 1)
+    s.set_option("fused_rows", 16)
+    s.step(100)
+    s.step(160)
+    sim = oracle_sim(oracle_lib, spec)
+    sim.step(260)
+    errs = compare(s, sim, 2)
+    print("fused 2-D column march f32 vs oracle: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    assert max(errs.values()) <= 1e-4, errs
+
+
+def test_fused_rows_option():
+    from paper_2211_05647_gb300 import FdtdError, Solver
+    s = Solver.from_spec(_spec2(10, n=(152, 70)))
+    for bad in (-1, 4097):
+        with pytest.raises(FdtdError):
+            s.set_option("fused_rows", bad)
+    s.set_option("fused_rows", 0)
+    s.set_option("fused_rows", 4096)
+
+
+def test_every_2d_stencil_path_bit_identical(tmp_path, monkeypatch):
+    """The 2-D kernels share one fixed-rounding form of the cell updates: the
+    default grid-of-cells kernels, the TMA column kernels, the fused column
+    march and the fused 64 x 16 tiles give the same fields, J and delta f bit
+    for bit (CPML, point source, kinetic region)."""
+    from paper_2211_05647_gb300 import Solver
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "none.txt"))
+    spec = _spec2(75, n=(296, 70), src=(130, 33))
+    variants = {"default": {}, "tma": {"stencil_tz": 32}, "march": {"fused_stencils": 1, "fused_rows": 8},
+                "tiles": {"fused_stencils": 1, "fused_rows": 0}}
+    out = {}
+    for name, opts in variants.items():
+        s = Solver.from_spec(spec)
+        for k, v in opts.items():
+            s.set_option(k, v)
+        s.step(40)
+        s.step(35)
+        out[name] = {q: s.read(q, device=False) for q in FIELDS[2] + ["j", "df"]}
+    for name in variants:
+        for q, v in out[name].items():
+            assert np.array_equal(v, out["default"][q]), (name, q)
+
+
+def test_autotuned_fused_choice(tmp_path, monkeypatch):
+    """The autotuner's 2-D choice (fused column march or separate passes) is
+    reported, cached for later handles, and steps bit for bit like a handle
+    on the default kernels; half steps stay allowed."""
+    from paper_2211_05647_gb300 import Solver
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    spec = _spec2(64, n=(1024, 512), src=(300, 256))
+    s = Solver.from_spec(spec)
+    res = s.autotune()
+    assert res["fused_rows"] in (0, 8, 16, 32)
+    assert s.launch_shapes()["fused_rows"] == res["fused_rows"]
+    assert Solver.from_spec(spec).launch_shapes()["fused_rows"] == res["fused_rows"]
+    s.step(64)
+    monkeypatch.setenv("FDTD_PLASMA_TUNE_CACHE", str(tmp_path / "none.txt"))
+    plain = Solver.from_spec(spec)
+    assert plain.launch_shapes()["fused_rows"] == 0
+    # the same kinetic shape (its J reduction order is the one thing shapes may change)
+    plain.set_option("kinetic_shape", res["kin_stages"] * 10**9 + res["kin_vpl"] * 10**6 + res["kin_l"] * 1000
+                     + res["kin_blocks_per_sm"])
+    plain.step(64)
+    for q in FIELDS[2] + ["j"]:
+        assert np.array_equal(s.read(q, device=False), plain.read(q, device=False)), q
+    s.step_half(0)
+    s.step_half(1)
