@@ -92,6 +92,13 @@ def step_launches(steps, mid_per_step, fused):
     return chunks * seq(32) + rem * seq(1)
 
 
+def fused_in_steps(spec: dict, shapes: dict, option: int = 0) -> bool:
+    """Whether the timed steps run the fused E + H pass: asked for by option
+    (2-D / 3-D FP32), or chosen by the autotuner (2-D FP32, fused_rows > 0)."""
+    f32 = spec["grid"].get("precision", "f32") == "f32"
+    return (bool(option) and spec["grid"]["ndim"] >= 2 and f32) or shapes.get("fused_rows", 0) > 0
+
+
 def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     """Whole-job throughput: every rank processes units_per_rank in the job's time."""
     return world * units_per_rank / seconds
@@ -348,7 +355,7 @@ def solver_config(workload: str, steps: int, warmup: int, autotune: bool, local:
                          "traffic": ncu_traffic(kname, workload, kshape),
                          "peak_source": src},
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
-            "gpu_launches": step_launches(steps, 1 if ns else 0, False)}
+            "gpu_launches": step_launches(steps, 1 if ns else 0, fused_in_steps(spec, shapes))}
 
 
 def batch_config(workload: str, specs, steps: int, warmup: int, autotune: bool, local: int) -> dict:
@@ -489,13 +496,16 @@ def closure_config(steps: int, warmup: int, engine: str, autotune: bool, local: 
                                    # against the faster kinetic form, BF16-stored delta f
                                    "kinetic_bf16_ms_per_step": ms_kb / steps, "speedup_vs_bf16_kinetic": ms_kb / ms_c},
             "kernel_ms": {"closure_run": kt_c, "kinetic_run": kt_k},
+            # kernel_ms times one unfused step; with the fused E + H pass in the timed steps the stencils take
+            # the step time less the closure and kinetic-fallback kernels
+            "stencil_ms_in_step": ms_step_c - kt_c["closure"] - kt_c["kinetic"],
             "launch_shapes": {"closure_run": sh_c, "kinetic_run": sh_k},
             "roofline": {"bound": "tensor", "kernel": "k_closure_tc" if engine == "tcgen05" else "k_closure",
                          "achieved": achieved, "peak": tpk, "unit": "TFLOP/s", "frac": achieved / tpk,
                          "traffic": None, "alg_flops_per_launch": flops, "launch_ms": kt_c["closure"],
                          "peak_source": tsrc},
             "step_hbm_frac_algorithmic": step_alg / (ms_step_c / 1e3) / 1e9 / hpk,
-            "gpu_launches": step_launches(steps, 2 if n_kin else 1, False)}
+            "gpu_launches": step_launches(steps, 2 if n_kin else 1, fused_in_steps(spec, sh_c))}
 
 
 def training_config(local: int, n: int = 1 << 20, batch: int = 4096, epochs: int = 3) -> dict:
@@ -673,7 +683,7 @@ def main():
 
     # per-kernel launch durations (eager launches with CUDA events on the solver's stream)
     kt = s.time_kernels(min(args.steps, 200))
-    fused = bool(args.fused) and spec["grid"]["ndim"] >= 2 and s.precision == "f32"
+    fused = fused_in_steps(spec, shapes, args.fused)
 
     # end-to-end through the public API: plasma density and initial fields from
     # pinned host memory, K steps, final fields and J back to pinned host memory
@@ -753,8 +763,9 @@ def main():
             "phase_space_updates_per_s": ps_rate,
             "step_hbm_frac_algorithmic": step_alg / (ms_step / 1e3) / 1e9 / peak,
             "kernel_ms": kt,
-            # kernel_ms times one unfused step; with fused_stencils the timed steps fuse each E update with
-            # the next H update, so their stencil time is the step time less the kinetic and closure kernels
+            # kernel_ms times one unfused step; with the fused pass (the option, or the autotuner's 2-D choice)
+            # the timed steps fuse each E update with the next H update, so their stencil time is the step
+            # time less the kinetic and closure kernels
             "fused_stencils": fused,
             "stencil_ms_in_step": ms_step - kt["kinetic"] - kt["closure"],
             "launch_shapes": dict(shapes, tuned=tune is not None),
@@ -843,7 +854,7 @@ def closure_cost_bench(args, spec, rank, world, local):
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "alg_flops_per_launch": flops, "launch_ms": kt["closure"],
                          "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained" if peaks else "fallback"},
-            "gpu_launches": step_launches(args.steps, 2 if n_kin else 1, False),
+            "gpu_launches": step_launches(args.steps, 2 if n_kin else 1, fused_in_steps(spec, s.launch_shapes())),
             "clocks": clk}
     print(json.dumps(line), flush=True)
     return 0
