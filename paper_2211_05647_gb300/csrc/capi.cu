@@ -1655,7 +1655,7 @@ int autotune_t(fdtd_plasma *h, fdtd_tune_result *out)
                     float *fo[6], *po[12];
                     for (int q = 0; q < 6; ++q) fo[q] = reinterpret_cast<float *>(h->f2[q]);
                     for (int q = 0; q < 12; ++q) po[q] = reinterpret_cast<float *>(h->psi2[q]);
-                    for (int rows : {8, 16, 32}) {
+                    for (int rows : {4, 8, 16, 32}) {
                         const double ms = time_ms([&] {
                             launch_eh2d(st, f, fo, po, h->nx, h->ny, ce, cpe, ch, cph, cp, src, h->d_step, 0, rows);
                         });

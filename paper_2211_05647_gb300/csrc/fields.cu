@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
 // `in` (fields and psi), writes set `out`.  Per cell the arithmetic is that of
 // every 2-D kernel (the fixed-rounding helpers of stencil_common.cuh), so the
 // fused and separate sequences agree bit for bit.
-constexpr int kEh2W = 4;   // warps (128-column strips) per block
+constexpr int kEh2W = 1;   // warps (128-column strips) per block: one, so a strip in a CPML x slab (slower) holds no other strip's block slot
 constexpr int kEh2D = 4;   // rows in each lane's copy ring
 
 __device__ __forceinline__ void cpa16(void *dst, const void *src)
@@ -811,6 +811,7 @@ __device__ __forceinline__ void cpa16(void *dst, const void *src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
 }
+__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 __device__ __forceinline__ void cpa4(void *dst, const void *src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -831,33 +832,40 @@ __device__ __noinline__ float source_f32(int kind, double amp, double fc, double
     return (float)source_value(s, (double)n1 * dt);
 }
 
-__global__ void __launch_bounds__(32 * kEh2W, 6)
+__global__ void __launch_bounds__(32 * kEh2W, 22)
     k_eh2d_v4(const float *__restrict__ ez_in, const float *__restrict__ hx_in, const float *__restrict__ hy_in,
               float *__restrict__ ez_out, float *__restrict__ hx_out, float *__restrict__ hy_out, int64_t nx,
-              int64_t ny, int rows, float ce, float cpe, float ch, float cph, Cpml<float> cin, PsiOut pout, Source src,
-              const int64_t *__restrict__ d_step, int kstep)
+              int64_t ny, int rows, int ktop, float ce, float cpe, float ch, float cph, Cpml<float> cin, PsiOut pout,
+              Source src, const int64_t *__restrict__ d_step, int kstep)
 {
     pdl_enter();
     const int lane = (int)(threadIdx.x & 31u), w = (int)(threadIdx.x >> 5);
     const int64_t xs = ((int64_t)blockIdx.x * kEh2W + w) * 128;   // the warp's strip
     const int64_t i0 = xs + 4 * lane;
-    const int64_t j0 = (int64_t)blockIdx.y * rows;
-    const int64_t j1 = j0 + rows < ny ? j0 + rows : ny;   // owned rows [j0, j1)
-    const int64_t jl = j1 < ny ? j1 : ny - 1;              // last row whose E^{n+1} is formed
+    // rows in 32 bits (the launcher checks ny < 2^31); cell offsets in 64.  The ktop segments at the top
+    // (the slower CPML rows of the upper y slab) are launched first, with those of the lower slab, so
+    // they do not trail the grid's last wave.
+    const int nyi = (int)ny;
+    const int seg = (int)blockIdx.y < ktop ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y - ktop;
+    const int j0 = seg * rows;
+    const int j1 = j0 + rows < nyi ? j0 + rows : nyi;   // owned rows [j0, j1)
+    const int jl = j1 < nyi ? j1 : nyi - 1;             // last row whose E^{n+1} is formed
     const int64_t n1 = *d_step + kstep + 1;
     if (src.kind && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
         *src.val = source_value(src, (double)(n1 + 1) * src.dt);   // g(t^{n+2}) for a following unfused E
     if (xs >= nx) return;   // the whole warp is past the grid
     const bool live = i0 < nx;
-    const int64_t xr = xs + 128;   // the column beyond the strip
+    const int64_t xr = xs + 128;   // the column beyond the strip (lane 31's quad + 4)
     const bool left = lane == 0 && xs > 0, right = lane == 31 && xr < nx;
     const int L = cin.L;
+    const int ylo = L, yhi = nyi - L;   // rows outside [ylo, yhi) are in a y slab
     const unsigned full = 0xffffffffu;
     // per-column parts of the CPML selection and of the source test (the row parts are per row)
     const bool pml_cols = L > 0 && (i0 < L || i0 + 3 >= nx - L);
     const bool pml_cols_r = L > 0 && (xr < L || xr + 3 >= nx - L);
     const int src_e = src.kind && src.i >= i0 && src.i < i0 + 4 ? (int)(src.i - i0) : -1;
     const bool src_r = src.kind && src.i == xr;
+    const int srcj = src.kind && src.j >= 0 && src.j < ny ? (int)src.j : -1;
     const bool wall = i0 == 0;   // the quad holds column 0 (PEC)
 
     // Each lane streams its own inputs through a ring of kEh2D rows in shared
@@ -866,27 +874,31 @@ __global__ void __launch_bounds__(32 * kEh2W, 6)
     // a lane reads back only what it copied itself, so no barrier is needed.
     __shared__ float4 ring[kEh2W][kEh2D][3][32];
     __shared__ float halo[kEh2W][kEh2D][4];
-    auto issue = [&](int64_t j, int sl) {   // row j into slot sl, one copy group (empty past the last row)
-        if (j <= jl) {
-            const int64_t c = j * nx + i0, cr = j * nx + xr;
+    int ji = j0;                              // the next row to copy
+    int64_t ci = (int64_t)j0 * nx + i0;       // and its quad's offset
+    auto issue = [&](int sl) {                // that row into slot sl, one copy group (empty past the last row)
+        if (ji <= jl) {
             if (live) {
-                cpa16(&ring[w][sl][0][lane], ez_in + c);
-                cpa16(&ring[w][sl][1][lane], hx_in + c);
-                cpa16(&ring[w][sl][2][lane], hy_in + c);
+                cpa16(&ring[w][sl][0][lane], ez_in + ci);
+                cpa16(&ring[w][sl][1][lane], hx_in + ci);
+                cpa16(&ring[w][sl][2][lane], hy_in + ci);
             }
-            if (left) cpa4(&halo[w][sl][0], hy_in + c - 1);
+            if (left) cpa4(&halo[w][sl][0], hy_in + ci - 1);
             if (right) {
-                cpa4(&halo[w][sl][1], ez_in + cr);
-                cpa4(&halo[w][sl][2], hx_in + cr);
-                cpa4(&halo[w][sl][3], hy_in + cr);
+                cpa4(&halo[w][sl][1], ez_in + ci + 4);
+                cpa4(&halo[w][sl][2], hx_in + ci + 4);
+                cpa4(&halo[w][sl][3], hy_in + ci + 4);
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
+        ++ji;
+        ci += nx;
     };
     auto q4 = [](const float4 &t) { return Q4{{t.x, t.y, t.z, t.w}}; };
 
-    Q4 hxp = ld4_if(live && j0 >= 1, hx_in + (j0 - 1) * nx + i0);   // H_x^{n+1/2} of the row below
-    float hxrp = right && j0 >= 1 ? hx_in[(j0 - 1) * nx + xr] : 0.f;
+    int64_t c = (int64_t)j0 * nx + i0;   // the current row's quad
+    Q4 hxp = ld4_if(live && j0 >= 1, hx_in + c - nx);   // H_x^{n+1/2} of the row below
+    float hxrp = right && j0 >= 1 ? hx_in[c - nx + 4] : 0.f;
     Q4 hyp{}, enp{};         // the previous row's H_y^{n+1/2} and E^{n+1}
     float erp = 0.f;         // and E^{n+1} right of the quad
     bool slab_p = false;     // and whether it lies in a y slab
@@ -899,19 +911,46 @@ __global__ void __launch_bounds__(32 * kEh2W, 6)
             for (int a = 0; a < 3; ++a) ring[w][d][a][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int d = 0; d < kEh2D - 1; ++d) issue(j0 + d, d);
+    for (int d = 0; d < kEh2D - 1; ++d) issue(d);
+    // The CPML updates read psi from the row they work on: a lane in an x slab
+    // (and every lane in a y-slab row, with the row's y profile) asks for that
+    // psi kEh2D - 1 rows ahead, as its ring does for the fields, so those
+    // reads hit L1 instead of waiting on DRAM in the row loop.
+    const int xslot = pml_cols && live ? slab_slot<float>(i0 < L ? i0 : i0 + 3, nx, L) : 0;
+    auto prefetch_psi = [&](int jj) {
+        if (jj > jl || !live) return;
+        if (pml_cols) {
+            prefetch_l1(cin.psi[0] + (int64_t)jj * (2 * L) + xslot);
+            prefetch_l1(cin.psi[3] + (int64_t)jj * (2 * L) + xslot);
+        }
+        if (L > 0 && (jj < ylo || jj >= yhi)) {
+            const int64_t o = (int64_t)slab_slot<float>(jj, ny, L) * nx + i0;
+            prefetch_l1(cin.psi[1] + o);
+            prefetch_l1(cin.psi[2] + o);
+            if (lane == 0) {   // the row's y profile (one line each, shared by the warp)
+                prefetch_l1(cin.be[1] + jj);
+                prefetch_l1(cin.ae[1] + jj);
+                prefetch_l1(cin.ike[1] + jj);
+                prefetch_l1(cin.bh[1] + jj);
+                prefetch_l1(cin.ah[1] + jj);
+                prefetch_l1(cin.ikh[1] + jj);
+            }
+        }
+    };
+#pragma unroll
+    for (int d = 0; d < kEh2D - 1; ++d) prefetch_psi(j0 + d);
     int sl = 0;   // the slot of row j (rows j0 + kEh2D m + sl use slot sl)
-    for (int64_t j = j0; j <= jl; ++j) {
-        issue(j + kEh2D - 1, sl == 0 ? kEh2D - 1 : sl - 1);   // refills the slot row j - 1 was read from
+    for (int j = j0; j <= jl; ++j, c += nx) {
+        issue(sl == 0 ? kEh2D - 1 : sl - 1);   // refills the slot row j - 1 was read from
+        prefetch_psi(j + kEh2D - 1);
         asm volatile("cp.async.wait_group %0;" ::"n"(kEh2D - 1) : "memory");   // row j has landed
         const Q4 ep = q4(ring[w][sl][0][lane]), hx = q4(ring[w][sl][1][lane]), hy = q4(ring[w][sl][2][lane]);
         float hl = __shfl_up_sync(full, hy.v[3], 1);
         if (lane == 0) hl = left ? halo[w][sl][0] : 0.f;
-        const int64_t c = j * nx + i0;
         const bool own = j < j1;
-        const bool slab = L > 0 && in_slab<float>(j, ny, L);
+        const bool slab = L > 0 && (j < ylo || j >= yhi);
         const bool pml = pml_cols || slab;
-        const bool srow = j == src.j;
+        const bool srow = j == srcj;
         // E^{n+1}(j) on the quad (row 0 and column 0 are the PEC wall)
         Q4 en = ep;
         if (live && !pml && j >= 1 && !wall && !(srow && src_e >= 0)) {
@@ -982,9 +1021,9 @@ __global__ void __launch_bounds__(32 * kEh2W, 6)
         slab_p = slab;
         sl = sl + 1 == kEh2D ? 0 : sl + 1;
     }
-    // the top row: E^{n+1} above it is 0
-    if (live && j1 == ny) {
-        const int64_t j = ny - 1;
+    // the top row: E^{n+1} above it is 0 (c is one row past it)
+    if (live && j1 == nyi) {
+        const int j = nyi - 1;
         Q4 hxo = hxp, hyo = hyp;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -997,8 +1036,8 @@ __global__ void __launch_bounds__(32 * kEh2W, 6)
                 h2d_pml_io<float>(cin, pout.psi, nx, ny, i0 + e, j, ch, cph, dEy, dEx, hxo.v[e], hyo.v[e]);
             }
         }
-        st4(hx_out + j * nx + i0, hxo);
-        st4(hy_out + j * nx + i0, hyo);
+        st4(hx_out + c - nx, hxo);
+        st4(hy_out + c - nx, hyo);
     }
 }
 
@@ -1018,10 +1057,12 @@ void launch_eh2d(cudaStream_t st, float *const fin[6], float *const fout[6], flo
 {
     PsiOut po{};
     for (int q = 0; q < 12; ++q) po.psi[q] = psi_out[q];
-    if (rows > 0 && nx % 4 == 0) {   // the column march (16-byte rows)
-        dim3 g(cdiv(nx, 128 * kEh2W), cdiv(ny, rows));
+    if (rows > 0 && nx % 4 == 0 && ny < (int64_t(1) << 31)) {   // the column march (16-byte rows, 32-bit row index)
+        const unsigned nseg = cdiv(ny, rows);
+        const int ktop = cin.L > 0 ? (int)std::min<int64_t>(nseg, cdiv(cin.L, rows) + 1) : 0;
+        dim3 g(cdiv(nx, 128 * kEh2W), nseg);
         launch_pdl(k_eh2d_v4, g, dim3(32 * kEh2W), 0, st, fin[FDTD_EZ], fin[FDTD_HX], fin[FDTD_HY], fout[FDTD_EZ],
-                   fout[FDTD_HX], fout[FDTD_HY], nx, ny, rows, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
+                   fout[FDTD_HX], fout[FDTD_HY], nx, ny, rows, ktop, ce, cpe, ch, cph, cin, po, src, d_step, kstep);
         return;
     }
     dim3 g(cdiv(nx, kF2X), cdiv(ny, kF2Y));
