@@ -81,15 +81,15 @@ def reduce_max(x: float, world: int, device=None) -> float:
 
 def step_launches(steps, mid_per_step, fused):
     """Kernels the solver launches for `steps` steps: 32-step graph replays,
-    then 1-step graphs.  An n-step sequence runs H_0, per step the middle
-    kernels and E, H for all but the last step, and one step-counter advance;
-    each fused transition (an even number of the n - 1) makes E_k + H_{k+1}
-    one launch."""
+    then one 16-, 8-, 4-, 2- and 1-step graph for each set bit of the
+    remainder.  An n-step sequence runs H_0, per step the middle kernels and
+    E, H for all but the last step, and one step-counter advance; each fused
+    transition (an even number of the n - 1) makes E_k + H_{k+1} one launch."""
     def seq(n):
         f = (n - 1) - (n - 1) % 2 if fused else 0
         return mid_per_step * n + 2 * n - f + 1
     chunks, rem = divmod(steps, 32)
-    return chunks * seq(32) + rem * seq(1)
+    return chunks * seq(32) + sum(seq(1 << b) for b in range(5) if rem >> b & 1)
 
 
 def fused_in_steps(spec: dict, shapes: dict, option: int = 0) -> bool:

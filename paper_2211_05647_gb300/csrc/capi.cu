@@ -272,6 +272,10 @@ void drop_graphs(fdtd_plasma *h)
     if (h->g1) cudaGraphExecDestroy(h->g1);
     if (h->gk) cudaGraphExecDestroy(h->gk);
     h->g1 = h->gk = nullptr;
+    for (auto &g : h->gpow) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
     h->graphs_valid = 0;
 }
 
@@ -1346,15 +1350,21 @@ int fdtd_plasma_step(fdtd_plasma_t h, int64_t nsteps)
         h->gk_steps = kChunk;
         h->graphs_valid = 1;
     }
-    int64_t left = nsteps;
-    while (left >= h->gk_steps) {
-        CK(h, cudaGraphLaunch(h->gk, h->stream));
-        left -= h->gk_steps;
+    // the remainder (< 32 steps) as 16-, 8-, 4-, 2- and 1-step graphs: few launches, and the fused
+    // stencil pass inside each of them; the ones this call needs are captured before anything runs
+    const int64_t rem = nsteps % h->gk_steps;
+    for (int b = 3; b >= 0; --b) {
+        if (!((rem >> (b + 1)) & 1) || h->gpow[b]) continue;
+        const int rc = capture(h, 2 << b, &h->gpow[b]);
+        if (rc != FDTD_OK) {
+            drop_graphs(h);
+            return rc;
+        }
     }
-    while (left > 0) {
-        CK(h, cudaGraphLaunch(h->g1, h->stream));
-        --left;
-    }
+    for (int64_t c = nsteps / h->gk_steps; c > 0; --c) CK(h, cudaGraphLaunch(h->gk, h->stream));
+    for (int b = 3; b >= 0; --b)
+        if ((rem >> (b + 1)) & 1) CK(h, cudaGraphLaunch(h->gpow[b], h->stream));
+    if (rem & 1) CK(h, cudaGraphLaunch(h->g1, h->stream));
     h->steps_done += nsteps;
     return FDTD_OK;
 }

@@ -447,6 +447,7 @@ struct fdtd_plasma {
     fdtd_source_desc src;
     // graphs
     cudaGraphExec_t g1, gk;
+    cudaGraphExec_t gpow[4];   // 2-, 4-, 8- and 16-step graphs for a call's remainder (captured on first use)
     int gk_steps;
     int graphs_valid;
     // running-DFT ports (device arrays; nports = 0: none)

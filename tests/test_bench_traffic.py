@@ -44,3 +44,16 @@ def test_traffic_close_to_algorithmic_bytes():
     alg = 8 * 823473 * 1024
     t = bench.ncu_traffic("k_kinetic_ring", "2d_tmz_4096_kinetic", (16, 16, 3))
     assert 0.95 * alg < t < 1.05 * alg
+
+
+def test_step_launches_counts_remainder_graphs():
+    """32-step chunks, then one graph per set bit of the remainder (16, 8, 4,
+    2, 1 steps); a sequence of n steps launches H_0, (middle, E, H) per step
+    less the last H, one counter advance, and fused transitions merge E + H."""
+    import bench
+    seq = lambda n, mid, f: mid * n + 2 * n - (((n - 1) - (n - 1) % 2) if f else 0) + 1
+    assert bench.step_launches(20, 1, False) == seq(16, 1, False) + seq(4, 1, False)
+    assert bench.step_launches(64, 1, True) == 2 * seq(32, 1, True)
+    assert bench.step_launches(2000, 1, True) == 62 * seq(32, 1, True) + seq(16, 1, True)
+    assert bench.step_launches(7, 2, False) == seq(4, 2, False) + seq(2, 2, False) + seq(1, 2, False)
+    assert bench.step_launches(1, 0, True) == 3

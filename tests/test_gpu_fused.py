@@ -256,3 +256,20 @@ def test_autotuned_fused_choice(tmp_path, monkeypatch):
         assert np.array_equal(s.read(q, device=False), plain.read(q, device=False)), q
     s.step_half(0)
     s.step_half(1)
+
+
+def test_step_counts_split_into_graphs_bit_identical():
+    """A call's steps run as 32-step chunks plus one 16/8/4/2/1-step graph per
+    set bit of the remainder, each with its own fused transitions: any split
+    of the same steps into calls gives the same state bit for bit (2-D)."""
+    from paper_2211_05647_gb300 import Solver
+    spec = _spec2(100, n=(152, 70))
+    a, b = Solver.from_spec(spec), Solver.from_spec(spec)
+    a.set_option("fused_stencils", 1)
+    b.set_option("fused_stencils", 1)
+    for n in (23, 45, 1, 31):
+        a.step(n)
+    for _ in range(100):
+        b.step(1)
+    for q in FIELDS[2] + ["j", "df"]:
+        assert np.array_equal(a.read(q, device=False), b.read(q, device=False)), q
