@@ -17,6 +17,7 @@
 // `rate` of the (cell, step) pairs, and each selected pair appends one sample
 //     [E^{n-15} .. E^n, n, J^{n+1/2}, J^{n-1/2}]   (19 floats)
 // to the caller's buffer.
+#include "cp_async.cuh"
 #include "mlp_tc.cuh"
 
 namespace fp {
@@ -123,22 +124,40 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
 // the input gets anyway), 32 bytes a cell in slot order: W1's rows are stored
 // in the ring's slot order of the step, so a row is copied, never rotated.  If
 // a bounded MMA-completion wait gives up, *err is set and the warpgroup stops.
+// A warpgroup's copy of its next tile's row data: each thread copies its own row (history ring, cell
+// index and density while the current tile's first MMA runs, then the E value the cell index points at,
+// between the two layers) and reads back only that row, so no barrier is needed.
+struct ClosureNext {
+    __align__(16) uint4 h[kMlpRows][2];
+    int32_t cell[kMlpRows];
+    float dens[kMlpRows];
+    float e[kMlpRows];
+};
+struct ClosureTcSmem {
+    MlpTcSmem4 m;
+    ClosureNext next[kTcGroups];
+};
+
 __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
 {
     pdl_enter();
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    MlpTcSmem4 &s = *reinterpret_cast<MlpTcSmem4 *>(smem_raw);
+    ClosureTcSmem &cs = *reinterpret_cast<ClosureTcSmem *>(smem_raw);
+    MlpTcSmem4 &s = cs.m;
     const int64_t step = *a.d_step + a.kstep;
     const int ring = (int)(step & 15);
     mlp_tc4_load_weights(s.w, a.P, ring);
     mlp_tc4_setup(s);
     const int gi = threadIdx.x >> 7, r = threadIdx.x & 127;
     MlpTcGroup &g = s.g[gi];
+    ClosureNext &nx = cs.next[gi];
     uint32_t phase = 0;
     bool ok = true;
     __nv_bfloat16 *hist = reinterpret_cast<__nv_bfloat16 *>(a.hist);
     const int64_t ntiles = (a.n + kMlpRows - 1) / kMlpRows;
-    for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + gi; tile < ntiles; tile += (int64_t)gridDim.x * kTcGroups) {
+    const int64_t stride = (int64_t)gridDim.x * kTcGroups;
+    bool staged = false;   // this tile's row is in nx (copied during the previous tile)
+    for (int64_t tile = (int64_t)blockIdx.x * kTcGroups + gi; tile < ntiles; tile += stride) {
         const int64_t slot = tile * kMlpRows + r;
         const bool valid = slot < a.n;
         uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
@@ -146,12 +165,21 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
         int32_t c = 0;
         float e = 0.0f;
         if (valid) {
-            c = a.cell[slot];
-            uint4 *hp = reinterpret_cast<uint4 *>(hist + slot * 16);
-            h0 = hp[0];
-            h1 = hp[1];
-            dens = a.dens[slot];
-            e = a.E[c];
+            if (staged) {
+                cpa_wait_all();
+                c = nx.cell[r];
+                h0 = nx.h[r][0];
+                h1 = nx.h[r][1];
+                dens = nx.dens[r];
+                e = nx.e[r];
+            } else {
+                c = a.cell[slot];
+                const uint4 *hp = reinterpret_cast<const uint4 *>(hist + slot * 16);
+                h0 = hp[0];
+                h1 = hp[1];
+                dens = a.dens[slot];
+                e = a.E[c];
+            }
             const __nv_bfloat16 eb = __float2bfloat16_rn(e * a.inv_es);
             hist[slot * 16 + ring] = eb;
             // this step's value into the loaded copy of the ring (slot `ring`: word ring / 2, half ring % 2)
@@ -169,7 +197,25 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
             dn = dens * a.inv_ns;
         }
         mlp_tc4_put_row_ring(g, r, h0, h1, dn);
-        const float y = mlp_tc4_tile(s.w, g, gi, r, &phase, &ok);
+        // the next tile's row (its E gather waits for the cell index: between the layers); the cells of
+        // different slots differ, so no E value read ahead is one this launch writes later
+        const int64_t nslot = slot + stride * kMlpRows;
+        const bool nvalid = nslot < a.n;
+        if (nvalid) {
+            cpa16(&nx.h[r][0], hist + nslot * 16);
+            cpa16(&nx.h[r][1], hist + nslot * 16 + 8);
+            cpa4(&nx.cell[r], a.cell + nslot);
+            cpa4(&nx.dens[r], a.dens + nslot);
+            cpa_commit();
+        }
+        const float y = mlp_tc4_tile(s.w, g, gi, r, &phase, &ok, [&] {
+            if (nvalid) {
+                cpa_wait_all();
+                cpa4(&nx.e[r], a.E + nx.cell[r]);
+                cpa_commit();
+            }
+        });
+        staged = true;
         if (!ok) break;
         if (valid) {
             const float J = a.rho * a.jprev[slot] + a.beta * dens * e + a.js * y;
@@ -178,6 +224,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
             a.E[c] = e - a.cj * J;
         }
     }
+    cpa_wait_all();   // no copy into shared memory outlives the loop
     if (!ok && r == 0) atomicExch(a.err, 1);
     mlp_tc4_teardown(s);
 }
@@ -188,7 +235,7 @@ cudaError_t launch_closure(cudaStream_t st, const ClosureArgs &a, int num_sms)
 {
     if (a.n == 0) return cudaSuccess;
     if (a.engine == 1) {
-        const size_t smem = sizeof(MlpTcSmem4);
+        const size_t smem = sizeof(ClosureTcSmem);
         cudaError_t e = cudaFuncSetAttribute(k_closure_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         // one CTA per SM: it allocates all 512 TMEM columns

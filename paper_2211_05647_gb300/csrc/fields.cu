@@ -12,6 +12,7 @@
 // the curl.
 #include <type_traits>
 
+#include "cp_async.cuh"
 #include "stencil_common.cuh"
 
 namespace fp {
@@ -806,17 +807,6 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
 constexpr int kEh2W = 1;   // warps (128-column strips) per block: one, so a strip in a CPML x slab (slower) holds no other strip's block slot
 constexpr int kEh2D = 4;   // rows in each lane's copy ring
 
-__device__ __forceinline__ void cpa16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void prefetch_l1(const void *p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-__device__ __forceinline__ void cpa4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
 
 // g(t^{n1}) in FP32, as the separate E kernel reads it; out of line because
 // only the thread at the source node calls it
@@ -890,7 +880,7 @@ __global__ void __launch_bounds__(32 * kEh2W, 22)
                 cpa4(&halo[w][sl][3], hy_in + ci + 4);
             }
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+        cpa_commit();
         ++ji;
         ci += nx;
     };

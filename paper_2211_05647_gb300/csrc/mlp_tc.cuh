@@ -328,8 +328,15 @@ __device__ __forceinline__ void mlp_tc4_put_row_ring(MlpTcGroup &g, int r, uint4
 // forward of warpgroup gi's tile (rows in g.x); thread r (0..127 inside the
 // warpgroup) gets row r's output.  Returns false in every thread of the
 // warpgroup if one of its bounded waits gave up.
+struct MlpNoMid {
+    __device__ void operator()() const {}
+};
+
+// mid() runs in every thread between the first epilogue and the second MMA (the caller's hook for work
+// that should overlap the tile, e.g. issuing the next tile's loads)
+template <typename Mid = MlpNoMid>
 __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, int gi, int r, uint32_t *phase,
-                                              bool *ok_out)
+                                              bool *ok_out, Mid mid = Mid())
 {
     const int warp = r >> 5;
     const uint32_t tmem = w.tmem + (uint32_t)(gi * 128);
@@ -371,6 +378,7 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
             *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
         }
     }
+    mid();
     fence_proxy_async_smem();
     tc_fence_before();
     wg_bar(gi);
