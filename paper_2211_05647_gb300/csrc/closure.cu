@@ -125,13 +125,14 @@ __global__ void k_record(int64_t n, const float *__restrict__ hist, const float 
 // in the ring's slot order of the step, so a row is copied, never rotated.  If
 // a bounded MMA-completion wait gives up, *err is set and the warpgroup stops.
 // A warpgroup's copy of its next tile's row data: each thread copies its own row (history ring, cell
-// index and density while the current tile's first MMA runs, then the E value the cell index points at,
-// between the two layers) and reads back only that row, so no barrier is needed.
+// index, density and the previous J while the current tile's first MMA runs, then the E value the cell
+// index points at, between the two layers) and reads back only that row, so no barrier is needed.
 struct ClosureNext {
     __align__(16) uint4 h[kMlpRows][2];
     int32_t cell[kMlpRows];
     float dens[kMlpRows];
     float e[kMlpRows];
+    float jp[kMlpRows];
 };
 struct ClosureTcSmem {
     MlpTcSmem4 m;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
         uint4 h0 = make_uint4(0u, 0u, 0u, 0u), h1 = h0;
         float dn = 0.0f, dens = 0.0f;
         int32_t c = 0;
-        float e = 0.0f;
+        float e = 0.0f, jp = 0.0f;
         if (valid) {
             if (staged) {
                 cpa_wait_all();
@@ -172,6 +173,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
                 h1 = nx.h[r][1];
                 dens = nx.dens[r];
                 e = nx.e[r];
+                jp = nx.jp[r];
             } else {
                 c = a.cell[slot];
                 const uint4 *hp = reinterpret_cast<const uint4 *>(hist + slot * 16);
@@ -179,6 +181,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
                 h1 = hp[1];
                 dens = a.dens[slot];
                 e = a.E[c];
+                jp = a.jprev[slot];
             }
             const __nv_bfloat16 eb = __float2bfloat16_rn(e * a.inv_es);
             hist[slot * 16 + ring] = eb;
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
             cpa16(&nx.h[r][1], hist + nslot * 16 + 8);
             cpa4(&nx.cell[r], a.cell + nslot);
             cpa4(&nx.dens[r], a.dens + nslot);
+            cpa4(&nx.jp[r], a.jprev + nslot);
             cpa_commit();
         }
         const float y = mlp_tc4_tile(s.w, g, gi, r, &phase, &ok, [&] {
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(512, 1) k_closure_tc(ClosureArgs a)
         staged = true;
         if (!ok) break;
         if (valid) {
-            const float J = a.rho * a.jprev[slot] + a.beta * dens * e + a.js * y;
+            const float J = a.rho * jp + a.beta * dens * e + a.js * y;
             a.jprev[slot] = J;
             if (a.store_j) a.jslot[slot] = J;
             a.E[c] = e - a.cj * J;
