@@ -84,6 +84,26 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 columns of the thread's TMEM lane without waiting for them; tc_wait_ld16 waits for every load the
+// thread has in flight and ties these registers to the wait, so no use of them moves above it.  With two
+// register sets a warp reads the next 16 columns while it works on the last ones.
+__device__ __forceinline__ void tc_ld16_async(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tc_wait_ld16(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 // weights (FP32 packed) -> BF16 core-matrix tiles; biases -> shared
 __device__ __forceinline__ void mlp_tc_load_weights(MlpTcSmem &s, const float *__restrict__ P)
 {
@@ -359,17 +379,23 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
     *phase ^= 1u;
     tc_fence_after();
     unsigned char *a2 = reinterpret_cast<unsigned char *>(g.a2);
+    // 16 columns at a time, the next 16 in flight from TMEM while these are activated
+    uint32_t ra[16], rb[16];
+    tc_ld16_async(tmem + lane_base, ra);
+    tc_wait_ld16(ra);
 #pragma unroll
-    for (int c = 0; c < kMlpH / 32; ++c) {
-        float v[32];
-        tc_ld32(tmem + lane_base + c * 32, v);
+    for (int c = 0; c < kMlpH / 16; ++c) {
+        uint32_t(&cur)[16] = (c & 1) ? rb : ra;
+        uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
+        if (c + 1 < kMlpH / 16) tc_ld16_async(tmem + lane_base + (c + 1) * 16, nxt);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k0 = c * 32 + q * 8;   // the accumulator already holds the bias (rows 17, 18 of W1)
-            const float2 g0 = gelu2_f2(f2(v[q * 8 + 0], v[q * 8 + 1]));
-            const float2 g1 = gelu2_f2(f2(v[q * 8 + 2], v[q * 8 + 3]));
-            const float2 g2 = gelu2_f2(f2(v[q * 8 + 4], v[q * 8 + 5]));
-            const float2 g3 = gelu2_f2(f2(v[q * 8 + 6], v[q * 8 + 7]));
+        for (int q = 0; q < 2; ++q) {
+            const int k0 = c * 16 + q * 8;   // the accumulator already holds the bias (rows 17, 18 of W1)
+            auto v = [&](int i) { return __uint_as_float(cur[q * 8 + i]); };
+            const float2 g0 = gelu2_f2(f2(v(0), v(1)));
+            const float2 g1 = gelu2_f2(f2(v(2), v(3)));
+            const float2 g2 = gelu2_f2(f2(v(4), v(5)));
+            const float2 g3 = gelu2_f2(f2(v(6), v(7)));
             uint4 pk;
             pk.x = pack_bf16(g0.x, g0.y);
             pk.y = pack_bf16(g1.x, g1.y);
@@ -377,6 +403,7 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
             pk.w = pack_bf16(g3.x, g3.y);
             *reinterpret_cast<uint4 *>(a2 + core_off(r, k0, kMlpH)) = pk;
         }
+        if (c + 1 < kMlpH / 16) tc_wait_ld16(nxt);
     }
     mid();
     fence_proxy_async_smem();
@@ -395,21 +422,26 @@ __device__ __forceinline__ float mlp_tc4_tile(MlpTcWeights &w, MlpTcGroup &g, in
     *phase ^= 1u;
     tc_fence_after();
     float y = w.b3;
+    tc_ld16_async(tmem + lane_base, ra);
+    tc_wait_ld16(ra);
 #pragma unroll
-    for (int c = 0; c < kMlpH / 32; ++c) {
-        float v[32];
-        tc_ld32(tmem + lane_base + c * 32, v);
+    for (int c = 0; c < kMlpH / 16; ++c) {
+        uint32_t(&cur)[16] = (c & 1) ? rb : ra;
+        uint32_t(&nxt)[16] = (c & 1) ? ra : rb;
+        if (c + 1 < kMlpH / 16) tc_ld16_async(tmem + lane_base + (c + 1) * 16, nxt);
+        auto v = [&](int i) { return __uint_as_float(cur[i]); };
 #pragma unroll
-        for (int i = 0; i < 32; i += 4) {
-            const float4 b = *reinterpret_cast<const float4 *>(&w.b2[c * 32 + i]);
-            const float4 o = *reinterpret_cast<const float4 *>(&w.w3[c * 32 + i]);
-            const float2 g0 = gelu2_f2(f2_add(f2(v[i + 0], v[i + 1]), f2(b.x, b.y)));
-            const float2 g1 = gelu2_f2(f2_add(f2(v[i + 2], v[i + 3]), f2(b.z, b.w)));
+        for (int i = 0; i < 16; i += 4) {
+            const float4 b = *reinterpret_cast<const float4 *>(&w.b2[c * 16 + i]);
+            const float4 o = *reinterpret_cast<const float4 *>(&w.w3[c * 16 + i]);
+            const float2 g0 = gelu2_f2(f2_add(f2(v(i + 0), v(i + 1)), f2(b.x, b.y)));
+            const float2 g1 = gelu2_f2(f2_add(f2(v(i + 2), v(i + 3)), f2(b.z, b.w)));
             y = fmaf(g0.x, o.x, y);
             y = fmaf(g0.y, o.y, y);
             y = fmaf(g1.x, o.z, y);
             y = fmaf(g1.y, o.w, y);
         }
+        if (c + 1 < kMlpH / 16) tc_wait_ld16(nxt);
     }
     tc_fence_before();
     // warpgroup-uniform verdict
