@@ -800,13 +800,13 @@ __global__ void __launch_bounds__(kF2T) k_eh2d(const float *__restrict__ ez_in, 
 // strip's edge lanes load the one column beyond it (lane 0: H_y at x - 1;
 // lane 31: E', H_x and H_y at x + 128, whose E^{n+1} it forms as well).  A
 // segment re-reads H_x of the row below it and forms, without storing it,
-// E^{n+1} of the row above it.  No shared memory and no barrier; reads set
-// `in` (fields and psi), writes set `out`.  Per cell the arithmetic is that of
-// every 2-D kernel (the fixed-rounding helpers of stencil_common.cuh), so the
-// fused and separate sequences agree bit for bit.
-constexpr int kEh2W = 1;   // warps (128-column strips) per block: one, so a strip in a CPML x slab (slower) holds no other strip's block slot
+// E^{n+1} of the row above it.  No barrier: each lane's inputs come through its
+// own cp.async ring in shared memory.  Reads set `in` (fields and psi), writes
+// set `out`.  Per cell the arithmetic is that of every 2-D kernel (the
+// fixed-rounding helpers of stencil_common.cuh), so the fused and separate
+// sequences agree bit for bit.
+constexpr int kEh2W = 1;   // warps (128-column strips) per block: a block's slot frees as soon as its strip ends
 constexpr int kEh2D = 4;   // rows in each lane's copy ring
-
 
 // g(t^{n1}) in FP32, as the separate E kernel reads it; out of line because
 // only the thread at the source node calls it
